@@ -1,0 +1,286 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+This package is the slow, obviously correct reference implementation of the
+UltraRay hot path (arXiv 2501.05828): plane-wave ray emission (Sec. 2.3, Eq. 6),
+traversal with reflection/refraction (Eqs. 7-11), transducer sampling with the
+receive directivity (Eq. 13), pulse deposit (Eq. 14), delay-and-sum, envelope
+and log compression (Sec. 2.3, last paragraph).  The arithmetic lives in
+``ur_oracle.c``; this module only builds it and marshals numpy arrays.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It never imports the CUDA package, and the CUDA
+package never imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ur_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liburoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PLANE_Z, SPHERE, CYL_Y = 0, 1, 2
+MODE_MC, MODE_EXPECT = 0, 1
+END_APERTURE, END_ARRAY_MISS, END_BOTTOM, END_PATH, END_TIME, END_MAXB = 1, 2, 3, 4, 5, 6
+
+
+def build(force: bool = False) -> str:
+    """Compile ur_oracle.c into _build/liburoracle.so with gcc (OpenMP, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(os.path.join(_HERE, "ur_oracle.h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Scene(C.Structure):
+    _fields_ = [("n_med", C.c_int32), ("med", C.POINTER(C.c_float)),
+                ("n_bnd", C.c_int32), ("bnd_kind", C.POINTER(C.c_int32)),
+                ("bnd_p", C.POINTER(C.c_float)), ("bnd_med", C.POINTER(C.c_int32)),
+                ("med_array", C.c_int32), ("z_max", C.c_float),
+                ("n_scat", C.c_int32), ("scat", C.POINTER(C.c_float)), ("r_s", C.c_float)]
+
+
+class Array(C.Structure):
+    _fields_ = [("n_el", C.c_int32), ("pitch", C.c_float), ("elev_h", C.c_float),
+                ("f0", C.c_float), ("fs", C.c_float), ("n_s", C.c_int32),
+                ("n_cycles", C.c_float), ("alpha_m_deg", C.c_float), ("alpha_c_deg", C.c_float),
+                ("c_bf", C.c_float), ("tcut_sigmas", C.c_float)]
+
+
+class TraceCfg(C.Structure):
+    _fields_ = [("n_tx", C.c_int32), ("angles", C.POINTER(C.c_float)),
+                ("n_rays", C.c_uint64), ("ray_begin", C.c_uint64), ("ray_end", C.c_uint64),
+                ("seed", C.c_uint64), ("max_bounces", C.c_int32), ("max_path", C.c_float),
+                ("mode", C.c_int32)]
+
+
+class Arrival(C.Structure):
+    _fields_ = [("tx", C.c_int32), ("el", C.c_int32), ("ray", C.c_uint32), ("event", C.c_uint32),
+                ("t", C.c_double), ("amp", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("rays", C.c_uint64), ("segments", C.c_uint64), ("interactions", C.c_uint64),
+                ("candidates", C.c_uint64), ("connections", C.c_uint64), ("arrivals", C.c_uint64)]
+
+
+ARRIVAL_DTYPE = np.dtype([("tx", "<i4"), ("el", "<i4"), ("ray", "<u4"), ("event", "<u4"),
+                          ("t", "<f8"), ("amp", "<f8")])
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            dp = C.POINTER(C.c_double)
+            L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+            L.or_trace.restype = C.c_int64
+            L.or_trace.argtypes = [C.POINTER(Scene), C.POINTER(Array), C.POINTER(TraceCfg),
+                                   C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(Stats), C.c_int]
+            L.or_deposit.argtypes = [C.POINTER(Array), C.c_int32, C.c_void_p, C.c_int64, dp, dp]
+            L.or_beamform.argtypes = [C.POINTER(Array), C.c_int32, C.POINTER(C.c_float), dp, dp,
+                                      C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float), C.c_int32,
+                                      dp, dp, C.c_int]
+            L.or_envelope_log.argtypes = [dp, dp, C.c_int64, C.c_double, dp, dp]
+            L.or_interface.restype = C.c_int
+            L.or_interface.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       dp, dp, dp, dp]
+            L.or_directivity.restype = C.c_double
+            L.or_directivity.argtypes = [C.c_double] * 3
+            L.or_pulse.restype = C.c_double
+            L.or_pulse.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+            L.or_np_per_m.restype = C.c_double
+            L.or_np_per_m.argtypes = [C.c_double, C.c_double]
+            L.or_connection.restype = C.c_double
+            L.or_connection.argtypes = [C.POINTER(Scene), C.POINTER(Array), dp, C.c_int32,
+                                        C.c_double, dp, dp]
+            _lib = L
+    return _lib
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class _Keep:
+    """Holds the numpy buffers a ctypes struct points into."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def make_scene(scene):
+    med = np.ascontiguousarray(scene["media"], dtype=np.float32).reshape(-1, 4)
+    kinds = np.ascontiguousarray([b[0] for b in scene["boundaries"]], dtype=np.int32)
+    bp = np.ascontiguousarray([b[1] for b in scene["boundaries"]], dtype=np.float32).reshape(-1, 4)
+    bm = np.ascontiguousarray([[b[2], b[3]] for b in scene["boundaries"]], dtype=np.int32).reshape(-1, 2)
+    sc = np.ascontiguousarray(scene["scatterers"], dtype=np.float32).reshape(-1, 4)
+    if kinds.size == 0:
+        kinds = np.zeros(1, np.int32)
+        bp = np.zeros((1, 4), np.float32)
+        bm = np.zeros((1, 2), np.int32)
+    if sc.size == 0:
+        sc_buf = np.zeros((1, 4), np.float32)
+    else:
+        sc_buf = sc
+    s = Scene(med.shape[0], _fp(med), len(scene["boundaries"]), _ip(kinds), _fp(bp), _ip(bm),
+              int(scene["med_array"]), float(scene["z_max"]), sc.shape[0], _fp(sc_buf),
+              float(scene["r_s"]))
+    return s, _Keep(med=med, kinds=kinds, bp=bp, bm=bm, sc=sc_buf)
+
+
+def make_array(arr):
+    return Array(int(arr["n_el"]), arr["pitch"], arr["elev_h"], arr["f0"], arr["fs"], int(arr["n_s"]),
+                 arr["n_cycles"], arr["alpha_m_deg"], arr["alpha_c_deg"], arr["c_bf"],
+                 arr["tcut_sigmas"])
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    P = C.POINTER(C.c_uint32)
+    lib().or_philox4x32_10(c.ctypes.data_as(P), k.ctypes.data_as(P), out.ctypes.data_as(P))
+    return out
+
+
+def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_begin=0, ray_end=None,
+          mode=MODE_MC, topo=False, threads=None):
+    """Trace rays [ray_begin, ray_end) of every transmit.
+
+    Returns (arrivals structured array, topology hashes [n_tx, n_sub] or None, stats dict)."""
+    L = lib()
+    if ray_end is None:
+        ray_end = n_rays
+    s, keep_s = make_scene(scene)
+    a = make_array(array)
+    ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
+    cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed),
+                   int(max_bounces), float(max_path), int(mode))
+    n_sub = int(ray_end) - int(ray_begin)
+    topo_arr = np.zeros((ang.size, n_sub), np.uint64) if topo else None
+    threads = threads or (os.cpu_count() or 1)
+    cap = max(1024, n_sub * ang.size // 2)
+    while True:
+        out = np.zeros(cap, ARRIVAL_DTYPE)
+        st = Stats()
+        n = L.or_trace(C.byref(s), C.byref(a), C.byref(cfg), out.ctypes.data, cap,
+                       topo_arr.ctypes.data if topo else None, C.byref(st), int(threads))
+        if n < 0:
+            raise ValueError("or_trace rejected its arguments")
+        if n <= cap:
+            break
+        cap = int(n)
+    del keep_s
+    stats = {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+    return out[:n].copy(), topo_arr, stats
+
+
+def deposit(array, n_tx, arrivals):
+    """Eq. 14 deposit: returns (rf, quad) float64 [n_tx, n_el, n_s]."""
+    a = make_array(array)
+    shape = (int(n_tx), int(array["n_el"]), int(array["n_s"]))
+    rf = np.zeros(shape, np.float64)
+    quad = np.zeros(shape, np.float64)
+    arr = np.ascontiguousarray(arrivals, dtype=ARRIVAL_DTYPE)
+    lib().or_deposit(C.byref(a), int(n_tx), arr.ctypes.data if arr.size else None, arr.size,
+                     _dp(rf), _dp(quad))
+    return rf, quad
+
+
+def beamform(array, angles, rf, quad, x_px, z_px, threads=None):
+    """Plane-wave DAS with coherent compounding: returns complex128 [nz, nx]."""
+    a = make_array(array)
+    ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
+    rf = np.ascontiguousarray(rf, dtype=np.float64)
+    quad = np.ascontiguousarray(quad, dtype=np.float64)
+    xp = np.ascontiguousarray(x_px, dtype=np.float32)
+    zp = np.ascontiguousarray(z_px, dtype=np.float32)
+    re = np.zeros((zp.size, xp.size), np.float64)
+    im = np.zeros_like(re)
+    lib().or_beamform(C.byref(a), ang.size, _fp(ang), _dp(rf), _dp(quad), _fp(xp), xp.size,
+                      _fp(zp), zp.size, _dp(re), _dp(im), int(threads or (os.cpu_count() or 1)))
+    return re + 1j * im
+
+
+def envelope_log(iq, dyn_range_db):
+    """Envelope and log compression: returns (env, dB) float64 arrays like iq."""
+    re = np.ascontiguousarray(iq.real, dtype=np.float64)
+    im = np.ascontiguousarray(iq.imag, dtype=np.float64)
+    env = np.zeros_like(re)
+    db = np.zeros_like(re)
+    lib().or_envelope_log(_dp(re), _dp(im), re.size, float(dyn_range_db), _dp(env), _dp(db))
+    return env, db
+
+
+def interface(d, n, c1, Z1, c2, Z2):
+    """Eqs. 7-11 at one boundary: returns (tir, d_r, d_t, r, R)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    dr = np.zeros(3)
+    dt = np.zeros(3)
+    r = C.c_double()
+    R = C.c_double()
+    tir = lib().or_interface(_dp(d), _dp(n), c1, Z1, c2, Z2, _dp(dr), _dp(dt), C.byref(r), C.byref(R))
+    return bool(tir), dr, dt, r.value, R.value
+
+
+def directivity(alpha, alpha_m, alpha_c):
+    return lib().or_directivity(float(alpha), float(alpha_m), float(alpha_c))
+
+
+def pulse(tau, f0, n_cycles):
+    im = C.c_double()
+    re = lib().or_pulse(float(tau), float(f0), float(n_cycles), C.byref(im))
+    return re, im.value
+
+
+def np_per_m(alpha_db_cm_mhz, f0):
+    return lib().or_np_per_m(float(alpha_db_cm_mhz), float(f0))
+
+
+def connection(scene, array, p, med, x_e):
+    """Straight connection ray p -> (x_e, 0, 0): returns (factor, t_samples, atten_np)."""
+    s, keep = make_scene(scene)
+    a = make_array(array)
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    t = C.c_double()
+    at = C.c_double()
+    f = lib().or_connection(C.byref(s), C.byref(a), _dp(pp), int(med), float(x_e), C.byref(t), C.byref(at))
+    del keep
+    return f, t.value, at.value
+
+
+def simulate(scene, array, angles, n_rays, seed, max_bounces, x_px, z_px, dyn_range_db=60.0,
+             max_path=0.2, ray_begin=0, ray_end=None, threads=None):
+    """Whole chain for one frame: trace, deposit, beamform, envelope, log."""
+    arr, _, st = trace(scene, array, angles, n_rays, seed, max_bounces, max_path, ray_begin, ray_end,
+                       threads=threads)
+    rf, quad = deposit(array, len(np.atleast_1d(angles)), arr)
+    iq = beamform(array, angles, rf, quad, x_px, z_px, threads=threads)
+    env, db = envelope_log(iq, dyn_range_db)
+    return {"arrivals": arr, "stats": st, "rf": rf, "quad": quad, "iq": iq, "env": env, "db": db}

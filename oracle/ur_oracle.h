@@ -1,0 +1,137 @@
+/*
+ * FP64 CPU oracle for full-path Monte Carlo acoustic ray tracing of plane-wave
+ * ultrasound (UltraRay, arXiv 2501.05828).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This tree is the slow, obviously-correct reference
+ * that the CUDA library is checked against.  Only the test suite, the smoke
+ * entry point and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA library and never calls it.
+ *
+ * Every routine takes the method's steps in the paper's order:
+ *   ray emission            Sec. 2.3 "Ray Emission", Eq. 6
+ *   traversal / interaction Sec. 2.3 "Ray Traversal", Eqs. 7-11
+ *   transducer sampling     Sec. 2.3 "Transducer Sampling", Eq. 13
+ *   pulse / signal chain    Sec. 2.3 "Phase Calculation and Signal Processing", Eq. 14
+ * Scatterers and attenuation are not part of the paper's method (Sec. 5 lists
+ * them as future work); the readings used for them are stated in the .c file.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), keyed per ray/event.
+ *
+ * Inputs are float32 (the exact values the GPU receives); all arithmetic is
+ * double precision.  Brute force everywhere: no acceleration structure.
+ */
+#ifndef UR_ORACLE_H
+#define UR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_PLANE_Z = 0, OR_SPHERE = 1, OR_CYL_Y = 2 };
+enum { OR_MODE_MC = 0, OR_MODE_EXPECT = 1 };
+enum { OR_END_APERTURE = 1, OR_END_ARRAY_MISS = 2, OR_END_BOTTOM = 3,
+       OR_END_PATH = 4, OR_END_TIME = 5, OR_END_MAXB = 6 };
+
+typedef struct {
+    int32_t n_med;
+    const float *med;        /* [n_med][4]: c (m/s), Z (MRayl), alpha (dB/cm/MHz), roughness (unused) */
+    int32_t n_bnd;
+    const int32_t *bnd_kind; /* OR_PLANE_Z: z = p0.  OR_SPHERE: centre p0..p2, radius p3.
+                                OR_CYL_Y: axis parallel to y through (x = p0, z = p1), radius p2 */
+    const float *bnd_p;      /* [n_bnd][4] */
+    const int32_t *bnd_med;  /* [n_bnd][2]: medium on the negative side (z < p0, or inside),
+                                medium on the positive side (z > p0, or outside) */
+    int32_t med_array;       /* medium in contact with the array plane z = 0 */
+    float z_max;             /* absorbing plane z = z_max */
+    int32_t n_scat;
+    const float *scat;       /* [n_scat][4]: x, y, z (m), amplitude */
+    float r_s;               /* scatterer capture radius (m) */
+} or_scene;
+
+typedef struct {
+    int32_t n_el;
+    float pitch, elev_h, f0, fs;
+    int32_t n_s;
+    float n_cycles, alpha_m_deg, alpha_c_deg, c_bf, tcut_sigmas;
+} or_array;
+
+typedef struct {
+    int32_t n_tx;
+    const float *angles;     /* [n_tx] steering angles (rad) */
+    uint64_t n_rays;         /* N: rays per transmit */
+    uint64_t ray_begin, ray_end; /* trace only rays i in [ray_begin, ray_end) of each transmit */
+    uint64_t seed;
+    int32_t max_bounces;
+    float max_path;          /* m */
+    int32_t mode;            /* OR_MODE_MC or OR_MODE_EXPECT */
+} or_trace_cfg;
+
+typedef struct {
+    int32_t tx, el;
+    uint32_t ray, event;     /* event: bit31 = aperture arrival, bits 24..30 = segment index b,
+                                bits 0..23 = scatterer index (scatter arrivals) */
+    double t;                /* arrival time in samples */
+    double amp;
+} or_arrival;
+
+typedef struct {
+    uint64_t rays, segments, interactions, candidates, connections, arrivals;
+} or_stats;
+
+/* Philox4x32-10 block: out = philox(ctr, key). */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Traces rays [ray_begin, ray_end) of every transmit.  Writes up to `cap` arrivals
+ * (sorted by tx, ray, emission order) and returns the total number produced
+ * (a return value > cap means the buffer was too small; re-run with more room).
+ * topo (nullable): [n_tx][ray_end - ray_begin] FNV-1a path hashes (MC mode).
+ * Returns -1 on invalid arguments. */
+int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg,
+                 or_arrival *out, int64_t cap, uint64_t *topo, or_stats *st, int n_threads);
+
+/* Eq. 14 deposit of arrivals into the analytic channel data A = rf + j quad
+ * ([n_tx][n_el][n_s], accumulated, not cleared). */
+void or_deposit(const or_array *ar, int32_t n_tx, const or_arrival *arr, int64_t n_arr,
+                double *rf, double *quad);
+
+/* Plane-wave delay-and-sum with coherent compounding over all transmits.
+ * x_px[nx], z_px[nz] pixel coordinates (m); img_re/img_im [nz][nx]. */
+void or_beamform(const or_array *ar, int32_t n_tx, const float *angles,
+                 const double *rf, const double *quad,
+                 const float *x_px, int32_t nx, const float *z_px, int32_t nz,
+                 double *img_re, double *img_im, int n_threads);
+
+/* Envelope |I|, normalisation by its maximum, 20 log10, clip at -dyn_range_db. */
+void or_envelope_log(const double *img_re, const double *img_im, int64_t n_px,
+                     double dyn_range_db, double *env, double *db);
+
+/* ---- single-step routines exposed for the closed-form tests ---- */
+
+/* Boundary interaction (Eqs. 7-11 with the acoustic readings): incident unit
+ * direction d, normal n (either orientation), media (c1, Z1) -> (c2, Z2).
+ * Returns 1 on total internal reflection (r = 1), else 0.  Outputs reflected and
+ * transmitted directions, the pressure reflection coefficient r and R = r^2. */
+int or_interface(const double d[3], const double n[3], double c1, double Z1,
+                 double c2, double Z2, double d_r[3], double d_t[3],
+                 double *r, double *R);
+
+/* Receive directivity Eq. 13; alpha in radians. */
+double or_directivity(double alpha, double alpha_m, double alpha_c);
+
+/* Analytic transmit pulse at lag tau (s): returns real part, writes imaginary part. */
+double or_pulse(double tau, double f0, double n_cycles, double *imag);
+
+/* Amplitude attenuation in Np/m for alpha (dB/cm/MHz) at f0 (Hz). */
+double or_np_per_m(double alpha_db_cm_mhz, double f0);
+
+/* Straight connection from p to element centre (x_e, 0, 0) starting in medium
+ * `med` (Sec. 2.3 "Transducer Sampling").  Returns the product of the
+ * transmission factors (0 if blocked by total internal reflection); writes the
+ * travel time in samples and the summed attenuation exponent. */
+double or_connection(const or_scene *sc, const or_array *ar, const double p[3], int32_t med,
+                     double x_e, double *t_samples, double *atten_np);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

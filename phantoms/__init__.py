@@ -1,0 +1,136 @@
+"""Seeded synthetic workloads for the UltraRay hot path.
+
+Inputs only: media tables, analytic boundaries, scatterer clouds, array and
+imaging-grid parameters, drawn with numpy from a seed.  None of the method's
+arithmetic (delays, Fresnel, pulse, beamforming) lives here, so both the CUDA
+library and the CPU oracle can be fed from it.  The paper's own scenes (a
+CT-derived spine mesh, Sec. 4) are not available; these phantoms follow the
+sizes and tissue parameters of the workloads the library is measured on.
+
+All geometric quantities are in metres, sound speeds in m/s, impedances in
+MRayl, attenuation in dB/cm/MHz.  Every array handed out is float32: the exact
+values both implementations consume.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PLANE_Z, SPHERE, CYL_Y = 0, 1, 2
+
+WATER = (1480.0, 1.48, 0.0, 0.0)
+MUSCLE = (1580.0, 1.70, 1.0, 0.0)
+BONE = (3500.0, 7.8, 10.0, 0.0)
+SKIN = (1615.0, 1.99, 0.0, 0.0)
+FAT = (1450.0, 1.38, 0.6, 0.0)
+
+
+def array_params(n_el, n_s, pitch=0.3e-3, elev_h=4e-3, f0=5e6, fs=40e6, n_cycles=5.0,
+                 alpha_m_deg=2.0, alpha_c_deg=2.0, c_bf=1540.0, tcut_sigmas=5.0):
+    """Linear array: n_el elements of width `pitch` (no kerf), elevation height elev_h."""
+    return {"n_el": int(n_el), "pitch": float(np.float32(pitch)), "elev_h": float(np.float32(elev_h)),
+            "f0": float(np.float32(f0)), "fs": float(np.float32(fs)), "n_s": int(n_s),
+            "n_cycles": float(np.float32(n_cycles)), "alpha_m_deg": float(np.float32(alpha_m_deg)),
+            "alpha_c_deg": float(np.float32(alpha_c_deg)), "c_bf": float(np.float32(c_bf)),
+            "tcut_sigmas": float(np.float32(tcut_sigmas))}
+
+
+def image_grid(array, nx, nz, z0=1e-3, z1=None):
+    """Pixel coordinates: x spans the element centres, z from z0 to the depth of the last sample."""
+    half = 0.5 * (array["n_el"] - 1) * array["pitch"]
+    if z1 is None:
+        z1 = array["c_bf"] * array["n_s"] / (2.0 * array["fs"])
+    x = np.linspace(-half, half, nx).astype(np.float32)
+    z = np.linspace(z0, z1, nz).astype(np.float32)
+    return x, z
+
+
+def uniform_scatterers(rng, n, box):
+    """n points uniform in box = ((x0, x1), (y0, y1), (z0, z1)) with N(0, 1) amplitudes."""
+    (x0, x1), (y0, y1), (z0, z1) = box
+    s = np.empty((n, 4), np.float64)
+    s[:, 0] = rng.uniform(x0, x1, n)
+    s[:, 1] = rng.uniform(y0, y1, n)
+    s[:, 2] = rng.uniform(z0, z1, n)
+    s[:, 3] = rng.standard_normal(n)
+    return s.astype(np.float32)
+
+
+def _scene(media, boundaries, med_array, z_max, scatterers, r_s):
+    return {"media": np.asarray(media, np.float32).reshape(-1, 4),
+            "boundaries": [(int(k), [float(np.float32(v)) for v in p], int(a), int(b))
+                           for k, p, a, b in boundaries],
+            "med_array": int(med_array), "z_max": float(np.float32(z_max)),
+            "scatterers": np.asarray(scatterers, np.float32).reshape(-1, 4),
+            "r_s": float(np.float32(r_s))}
+
+
+def tiny(seed=0, n_scat=200, with_sphere=True, n_rays=100_000):
+    """32-element array, water over muscle (interface at 15 mm), bone sphere r = 3 mm
+    centred at 25 mm, 200 scatterers in x,y,z = [-10,10] x [-2.5,2.5] x [5,25] mm;
+    one 0-degree plane wave, 1536 samples, 4 bounces, 128 x 256 image."""
+    rng = np.random.default_rng(seed)
+    media = [WATER, MUSCLE, BONE]
+    bnd = [(PLANE_Z, [0.015, 0, 0, 0], 0, 1)]
+    if with_sphere:
+        bnd.append((SPHERE, [0.0, 0.0, 0.025, 0.003], 2, 1))
+    sc = uniform_scatterers(rng, n_scat, ((-10e-3, 10e-3), (-2.5e-3, 2.5e-3), (5e-3, 25e-3)))
+    arr = array_params(32, 1536, c_bf=1480.0)
+    x, z = image_grid(arr, 128, 256)
+    return {"name": "tiny", "scene": _scene(media, bnd, 0, 0.040, sc, 1e-4), "array": arr,
+            "angles": np.zeros(1, np.float32), "n_rays": int(n_rays), "seed": 0, "max_bounces": 4,
+            "max_path": 0.2, "x_px": x, "z_px": z, "dyn_range_db": 60.0}
+
+
+def layered(seed=0, n_scat=50_000, n_rays=10_000_000, angles_deg=(0.0,), z_skin=2e-3, z_fat=10e-3,
+            bone_r=6e-3, bone_z=30e-3):
+    """128-element array; skin 0-2 mm, fat 2-10 mm, muscle 10-60 mm; bone cylinder
+    r = 6 mm along elevation at 30 mm depth; 50k scatterers over
+    x,y,z = [-19,19] x [-2.5,2.5] x [0,60] mm; 3200 samples, 8 bounces, 512 x 256 image."""
+    rng = np.random.default_rng(seed)
+    media = [SKIN, FAT, MUSCLE, BONE]
+    bnd = [(PLANE_Z, [z_skin, 0, 0, 0], 0, 1),
+           (PLANE_Z, [z_fat, 0, 0, 0], 1, 2),
+           (CYL_Y, [0.0, bone_z, bone_r, 0], 3, 2)]
+    sc = uniform_scatterers(rng, n_scat, ((-19e-3, 19e-3), (-2.5e-3, 2.5e-3), (0.0, 60e-3)))
+    arr = array_params(128, 3200, c_bf=1540.0)
+    x, z = image_grid(arr, 512, 256)
+    ang = np.deg2rad(np.asarray(angles_deg, np.float64)).astype(np.float32)
+    return {"name": "layered", "scene": _scene(media, bnd, 0, 0.060, sc, 1e-4), "array": arr,
+            "angles": ang, "n_rays": int(n_rays), "seed": 0, "max_bounces": 8, "max_path": 0.2,
+            "x_px": x, "z_px": z, "dyn_range_db": 60.0}
+
+
+def batched_variant(scene_seed):
+    """One jittered layered phantom of the batched workload: layer depths +/- 2 mm,
+    bone radius U(3, 10) mm, scatterer count U{10k..200k}, rays per transmit
+    log-uniform in [1e6, 3e7], 31 plane waves from -15 to +15 degrees."""
+    rng = np.random.default_rng(1000 + int(scene_seed))
+    z_skin = 2e-3 + rng.uniform(-2e-3, 2e-3) * 0.5      # keep the skin layer non-empty
+    z_fat = 10e-3 + rng.uniform(-2e-3, 2e-3)
+    bone_r = rng.uniform(3e-3, 10e-3)
+    n_scat = int(rng.integers(10_000, 200_001))
+    n_rays = int(np.exp(rng.uniform(np.log(1e6), np.log(3e7))))
+    w = layered(seed=int(scene_seed), n_scat=n_scat, n_rays=n_rays,
+                angles_deg=tuple(float(a) for a in range(-15, 16)),
+                z_skin=z_skin, z_fat=z_fat, bone_r=bone_r)
+    w["name"] = "batched-%d" % scene_seed
+    return w
+
+
+def single_plane(depth=0.015, upper=WATER, lower=MUSCLE, n_el=32, n_s=1536, n_rays=3200,
+                 z_max=0.040, c_bf=1480.0, **arr_kw):
+    """One planar interface, no scatterers (normal-incidence echo checks)."""
+    arr = array_params(n_el, n_s, c_bf=c_bf, **arr_kw)
+    sc = _scene([upper, lower], [(PLANE_Z, [depth, 0, 0, 0], 0, 1)], 0, z_max,
+                np.zeros((0, 4), np.float32), 1e-4)
+    return {"name": "plane", "scene": sc, "array": arr, "angles": np.zeros(1, np.float32),
+            "n_rays": int(n_rays), "seed": 0, "max_bounces": 4, "max_path": 0.2}
+
+
+def single_scatterer(pos, amp=1.0, medium=WATER, n_el=32, n_s=1536, n_rays=1_000_000,
+                     r_s=1e-4, z_max=0.040, c_bf=1480.0, **arr_kw):
+    """One point scatterer in a homogeneous medium."""
+    arr = array_params(n_el, n_s, c_bf=c_bf, **arr_kw)
+    sc = _scene([medium], [], 0, z_max, np.asarray([[pos[0], pos[1], pos[2], amp]], np.float32), r_s)
+    return {"name": "scatterer", "scene": sc, "array": arr, "angles": np.zeros(1, np.float32),
+            "n_rays": int(n_rays), "seed": 0, "max_bounces": 4, "max_path": 0.2}
