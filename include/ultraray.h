@@ -1,0 +1,207 @@
+/*
+ * ultraray.h - C ABI of the GB300 (sm_103a) full-path acoustic ray tracer.
+ *
+ * Implements the simulation pipeline of UltraRay (Duelmer et al., "UltraRay:
+ * Introducing Full-Path Ray Tracing in Physics-Based Ultrasound Simulation",
+ * arXiv 2501.05828):
+ *   plane-wave ray emission with per-element transmit delays   Sec. 2.3 "Ray Emission", Eq. 6
+ *   traversal: reflection / refraction at tissue boundaries     Sec. 2.3 "Ray Traversal", Eqs. 7-11
+ *   transducer sampling (connection rays, receive directivity) Sec. 2.3 "Transducer Sampling", Eq. 13
+ *   pulse shaping of the recorded time-pressure signals         Sec. 2.3 "Phase Calculation ...", Eq. 14
+ *   delay-and-sum beamforming, envelope, log compression        same paragraph (last sentences)
+ * The Monte Carlo estimators are those of Sec. 2.2 (Eqs. 4-5).  Point scatterers
+ * and attenuation, which the paper names as future work (Sec. 5), are included:
+ * every scatterer within a capture radius r_s of a primary-ray segment casts a
+ * connection ray to a uniformly chosen element centre.
+ *
+ * Conventions shared by every entry point
+ *  - Units: metres, seconds, m/s, MRayl (only impedance ratios matter),
+ *    attenuation in dB/cm/MHz evaluated at the centre frequency.
+ *  - Coordinates: the array lies in the plane z = 0 along x, centred on x = 0,
+ *    elements of width `pitch` (no kerf) and elevation height `elev_h` along y;
+ *    +z points into the body.
+ *  - Pointers: every input pointer may be host or device memory (the library
+ *    copies what it needs).  Output buffers may be host or device memory too;
+ *    device outputs are written in place on the context's stream, host outputs
+ *    are staged through library-owned device memory.  The caller owns all
+ *    buffers it passes; the library owns the scene copy, the scatterer grid,
+ *    the arrival queues and every other scratch buffer it allocates.
+ *  - Streams: all work is issued on the stream given to ur_create.  Calls that
+ *    return data sizes or statistics synchronise that stream.
+ *  - Errors: no exception crosses the ABI.  Every call returns a ur_status;
+ *    ur_last_error gives a message for the last failing call on that context.
+ *    A context is used by one host thread at a time.
+ */
+#ifndef ULTRARAY_H
+#define ULTRARAY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ur_ctx ur_ctx;
+
+typedef enum {
+    UR_OK = 0,
+    UR_ERR_INVALID_ARG = 1,  /* an argument is out of range or inconsistent */
+    UR_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in ur_last_error) */
+    UR_ERR_OOM = 3,          /* device allocation failed */
+    UR_ERR_OVERFLOW = 4,     /* a caller-sized buffer was too small (required size reported) */
+    UR_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+    UR_ERR_STATE = 6         /* scene, array or transmits not set before use */
+} ur_status;
+
+enum { UR_PLANE_Z = 0, UR_SPHERE = 1, UR_CYL_Y = 2 };
+
+/* One tissue type.  c: sound speed (m/s); Z: acoustic impedance (MRayl);
+ * alpha: amplitude attenuation (dB/cm/MHz, applied at the array's f0);
+ * roughness: reserved for the GGX microfacet boundaries of Sec. 2.3 (Eq. 12),
+ * must be 0 (smooth boundaries). */
+typedef struct {
+    float c, Z, alpha_db_cm_mhz, roughness;
+} ur_medium;
+
+/* One analytic boundary between two media (Sec. 2.3 "Ray Traversal").
+ *   UR_PLANE_Z: the plane z = p[0]; med_neg lies at z < p[0], med_pos at z > p[0].
+ *   UR_SPHERE:  centre (p[0], p[1], p[2]), radius p[3]; med_neg inside, med_pos outside.
+ *   UR_CYL_Y:   infinite cylinder with axis parallel to y through (x = p[0], z = p[1]),
+ *               radius p[2]; med_neg inside, med_pos outside. */
+typedef struct {
+    int32_t kind;
+    int32_t med_neg, med_pos;
+    float p[4];
+} ur_boundary;
+
+/* Linear transducer (Sec. 2.3 "Ray Emission"; parameters of Sec. 4).
+ * n_el elements at x_e = (e - (n_el-1)/2) pitch; f0 centre frequency (Hz);
+ * fs sampling frequency (Hz); n_s samples per channel; n_cycles sets the pulse
+ * width s = n_cycles/(4 f0) of Eq. 14; alpha_m_deg / alpha_c_deg are the
+ * main-beam and cutoff angles of Eq. 13 (equal values give a step);
+ * c_bf is the sound speed used for transmit delays and beamforming;
+ * tcut_sigmas truncates the pulse at |tau| <= tcut_sigmas * s (5 recommended). */
+typedef struct {
+    int32_t n_el;
+    float pitch, elev_h, f0, fs;
+    int32_t n_s;
+    float n_cycles, alpha_m_deg, alpha_c_deg, c_bf, tcut_sigmas;
+} ur_array;
+
+/* Counters of one trace call. */
+typedef struct {
+    uint64_t rays;          /* primary rays emitted */
+    uint64_t segments;      /* straight primary-ray segments traced */
+    uint64_t interactions;  /* boundary interactions (reflect / transmit / TIR) */
+    uint64_t candidates;    /* scatterer events (scatterer within r_s of a segment) */
+    uint64_t connections;   /* connection rays traced (events that pass the directivity) */
+    uint64_t arrivals;      /* arrivals deposited into the channel data */
+} ur_stats;
+
+/* Per-arrival and per-path records for verification (all device pointers,
+ * each array holds `capacity` entries).  An arrival's time in samples is
+ * t_hi + t_lo; row = transmit * n_el + element; event: bit 31 set for a
+ * primary ray crossing the aperture, bits 24..30 the number of boundary
+ * interactions before the event, bits 0..23 the scatterer index for
+ * scatterer events.  path_hash (nullable, [n_tx][n_rays]) is a 64-bit FNV-1a
+ * hash of each primary path's interaction sequence and termination reason. */
+typedef struct {
+    uint64_t capacity;
+    uint64_t count;          /* out: arrivals produced */
+    uint32_t *ray, *event, *row;
+    float *t_hi, *t_lo, *amp;
+    uint64_t *path_hash;
+} ur_debug;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL: the context creates and owns a non-blocking stream).
+ * Errors: UR_ERR_INVALID_ARG (out == NULL, bad device), UR_ERR_CUDA. */
+ur_status ur_create(ur_ctx **out, int device, void *cuda_stream);
+
+/* Release the context and every device buffer it owns (synchronises its stream). */
+ur_status ur_destroy(ur_ctx *ctx);
+
+/* Message describing the last failing call on ctx ("" if none); valid until the next call. */
+const char *ur_last_error(const ur_ctx *ctx);
+
+/* Scene of Sec. 2.3 "Ray Traversal": media table (n_med <= 16), analytic
+ * boundaries (n_bnd <= 32, media indices in [0, n_med)), the medium touching
+ * the array plane, an absorbing plane z = z_max, and n_scat point scatterers
+ * scat_xyza[n_scat][4] = (x, y, z, amplitude) with capture radius r_s > 0.
+ * Copies everything and builds the scatterer grid on the device.
+ * Errors: UR_ERR_INVALID_ARG, UR_ERR_OOM, UR_ERR_CUDA. */
+ur_status ur_scene_upload(ur_ctx *ctx, const ur_medium *media, int n_med,
+                          const ur_boundary *bnd, int n_bnd, int med_array, float z_max,
+                          const float *scat_xyza, int n_scat, float r_s);
+
+/* Transducer description (Sec. 2.3 "Ray Emission").  1 <= n_el <= 4096,
+ * 16 <= n_s <= 8192, positive geometry and frequencies, 0 <= alpha_m <= alpha_c < 90.
+ * Errors: UR_ERR_INVALID_ARG. */
+ur_status ur_set_array(ur_ctx *ctx, const ur_array *arr);
+
+/* Plane-wave transmits (Sec. 2.3, Fig. 3): steering angles in radians,
+ * |angle| < 60 deg, 1 <= n_tx <= 65536.  Element e of transmit k fires at
+ * (x_e sin(a_k) - min_e' x_e' sin(a_k)) / c_bf.
+ * Errors: UR_ERR_INVALID_ARG, UR_ERR_STATE (array not set). */
+ur_status ur_set_plane_waves(ur_ctx *ctx, const float *angles_rad, int n_tx);
+
+/* Trace n_rays_per_tx primary rays for every transmit (Eqs. 4-11, 13) and
+ * deposit the pulse-shaped arrivals (Eq. 14) into the analytic channel data
+ * rf + j quad, both [n_tx][n_el][n_s] float32 (overwritten).  Ray i of
+ * transmit k leaves element i mod n_el at a uniformly random point of its
+ * face; all randomness is Philox4x32-10 keyed by (seed, i, k, event), so the
+ * result is a pure function of the arguments.  max_bounces <= 127 boundary
+ * interactions per path, max_path_m total path length.  st may be NULL.
+ * Errors: UR_ERR_STATE, UR_ERR_INVALID_ARG, UR_ERR_OOM, UR_ERR_CUDA. */
+ur_status ur_trace(ur_ctx *ctx, uint64_t n_rays_per_tx, uint64_t seed, int max_bounces,
+                   float max_path_m, float *rf, float *quad, ur_stats *st);
+
+/* ur_trace plus the arrival list and per-path hashes for verification.
+ * dbg->count receives the number of arrivals; UR_ERR_OVERFLOW if it exceeds
+ * dbg->capacity (rf/quad are still complete). */
+ur_status ur_trace_debug(ur_ctx *ctx, uint64_t n_rays_per_tx, uint64_t seed, int max_bounces,
+                         float max_path_m, float *rf, float *quad, ur_stats *st, ur_debug *dbg);
+
+/* Plane-wave delay-and-sum with coherent compounding over all transmits
+ * (Sec. 2.3, last paragraph): pixel (x_px[ix], z_px[iz]) sums, over transmits
+ * k and elements e, the analytic channel data linearly interpolated at
+ * tau = [x sin a_k + z cos a_k - min_e x_e sin a_k + sqrt(z^2 + (x - x_e)^2)] fs / c_bf.
+ * Outputs (each nullable, [nz][nx], x fastest): iq complex image as float
+ * pairs, env = |iq|, db = max(20 log10(env / max env), -dyn_range_db).
+ * nx, nz in [1, 16384].  Errors: UR_ERR_STATE, UR_ERR_INVALID_ARG, UR_ERR_CUDA. */
+ur_status ur_beamform(ur_ctx *ctx, const float *rf, const float *quad,
+                      const float *x_px, int nx, const float *z_px, int nz, float dyn_range_db,
+                      float *iq, float *env, float *db);
+
+/* Scatterer-grid and launch tuning (0 fields keep the defaults).  Cell sizes in
+ * metres; applied at the next ur_scene_upload. */
+typedef struct {
+    float cell_xy, cell_z;
+    int32_t block, blocks_per_sm;
+} ur_tuning;
+ur_status ur_set_tuning(ur_ctx *ctx, const ur_tuning *t);
+
+/* Device time per pipeline phase, measured with CUDA events recorded on the
+ * context's stream around each phase's kernels while profiling is on.  While
+ * profiling, every call synchronises the stream before returning. */
+enum { UR_PHASE_GRID = 0, UR_PHASE_TRACE = 1, UR_PHASE_SORT = 2, UR_PHASE_DEPOSIT = 3,
+       UR_PHASE_DAS = 4, UR_PHASE_LOG = 5, UR_N_PHASES = 8 };
+typedef struct {
+    double ms[UR_N_PHASES];          /* accumulated device milliseconds */
+    uint64_t launches[UR_N_PHASES];  /* kernels launched */
+    uint64_t calls[UR_N_PHASES];     /* times the phase ran */
+} ur_profile;
+
+/* on != 0 clears the accumulators and starts profiling; on == 0 stops it. */
+ur_status ur_set_profiling(ur_ctx *ctx, int on);
+
+/* Copy the accumulators (valid whether or not profiling is still on). */
+ur_status ur_get_profile(ur_ctx *ctx, ur_profile *out);
+
+/* Wait for all work on the context's stream and report asynchronous errors. */
+ur_status ur_sync(ur_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ULTRARAY_H */

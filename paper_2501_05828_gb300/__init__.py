@@ -1,0 +1,257 @@
+"""GB300 (sm_103a) full-path acoustic ray tracer for plane-wave ultrasound.
+
+Python binding of the C ABI in ``include/ultraray.h`` (UltraRay, arXiv
+2501.05828, Sec. 2.3): argument marshalling only.  Every step of the
+simulation (emission, traversal, transducer sampling, pulse deposit,
+beamforming, envelope, log compression) runs in the CUDA library
+``_build/libultraray.so``; PyTorch only provides device memory and the stream.
+There is no CPU fallback: if the library is missing the import of
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libultraray.so")
+
+PLANE_Z, SPHERE, CYL_Y = 0, 1, 2
+STATUS = {0: "UR_OK", 1: "UR_ERR_INVALID_ARG", 2: "UR_ERR_CUDA", 3: "UR_ERR_OOM", 4: "UR_ERR_OVERFLOW",
+          5: "UR_ERR_TIMEOUT", 6: "UR_ERR_STATE"}
+
+# every entry point include/ultraray.h declares
+EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_set_array", "ur_set_plane_waves",
+           "ur_trace", "ur_trace_debug", "ur_beamform", "ur_set_tuning", "ur_set_profiling", "ur_get_profile",
+           "ur_sync")
+PHASES = ("grid", "trace", "sort", "deposit", "das", "log")
+
+
+class URError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Medium(C.Structure):
+    _fields_ = [("c", C.c_float), ("Z", C.c_float), ("alpha_db_cm_mhz", C.c_float), ("roughness", C.c_float)]
+
+
+class Boundary(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("med_neg", C.c_int32), ("med_pos", C.c_int32), ("p", C.c_float * 4)]
+
+
+class Array(C.Structure):
+    _fields_ = [("n_el", C.c_int32), ("pitch", C.c_float), ("elev_h", C.c_float), ("f0", C.c_float),
+                ("fs", C.c_float), ("n_s", C.c_int32), ("n_cycles", C.c_float), ("alpha_m_deg", C.c_float),
+                ("alpha_c_deg", C.c_float), ("c_bf", C.c_float), ("tcut_sigmas", C.c_float)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("rays", C.c_uint64), ("segments", C.c_uint64), ("interactions", C.c_uint64),
+                ("candidates", C.c_uint64), ("connections", C.c_uint64), ("arrivals", C.c_uint64)]
+
+
+class Debug(C.Structure):
+    _fields_ = [("capacity", C.c_uint64), ("count", C.c_uint64), ("ray", C.c_void_p), ("event", C.c_void_p),
+                ("row", C.c_void_p), ("t_hi", C.c_void_p), ("t_lo", C.c_void_p), ("amp", C.c_void_p),
+                ("path_hash", C.c_void_p)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_uint64 * 8), ("calls", C.c_uint64 * 8)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("cell_xy", C.c_float), ("cell_z", C.c_float), ("block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("CUDA library %s not built: run python -m paper_2501_05828_gb300.build" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            vp, u64, i32, f32 = C.c_void_p, C.c_uint64, C.c_int, C.c_float
+            L.ur_create.argtypes = [C.POINTER(vp), i32, vp]
+            L.ur_destroy.argtypes = [vp]
+            L.ur_last_error.restype = C.c_char_p
+            L.ur_last_error.argtypes = [vp]
+            L.ur_scene_upload.argtypes = [vp, C.POINTER(Medium), i32, C.POINTER(Boundary), i32, i32, f32, vp, i32, f32]
+            L.ur_set_array.argtypes = [vp, C.POINTER(Array)]
+            L.ur_set_plane_waves.argtypes = [vp, vp, i32]
+            L.ur_trace.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats)]
+            L.ur_trace_debug.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats), C.POINTER(Debug)]
+            L.ur_beamform.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, vp, vp]
+            L.ur_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+            L.ur_sync.argtypes = [vp]
+            L.ur_set_profiling.argtypes = [vp, i32]
+            L.ur_get_profile.argtypes = [vp, C.POINTER(Profile)]
+            for name in EXPORTS:
+                if name != "ur_last_error":
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (host or device)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+class Simulator:
+    """One library context bound to a CUDA device and stream.
+
+    Inputs may be numpy arrays (host) or torch tensors (host or device);
+    outputs are torch CUDA tensors allocated here unless passed in."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self._ctx = C.c_void_p()
+        self._call(lib().ur_create(C.byref(self._ctx), int(device), C.c_void_p(stream.cuda_stream)), ctx=False)
+        self.n_tx = 0
+        self.array = None
+
+    def _call(self, code, ctx=True):
+        if code != 0:
+            msg = lib().ur_last_error(self._ctx).decode() if ctx else ""
+            raise URError(code, msg)
+
+    def close(self):
+        if self._ctx:
+            lib().ur_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up -------------------------------------------------------------
+    def upload_scene(self, media, boundaries, med_array, z_max, scatterers, r_s):
+        med = np.ascontiguousarray(media, np.float32).reshape(-1, 4)
+        M = (Medium * len(med))(*[Medium(*map(float, m)) for m in med])
+        B = (Boundary * max(1, len(boundaries)))()
+        for q, (kind, p, neg, pos) in enumerate(boundaries):
+            B[q] = Boundary(int(kind), int(neg), int(pos), (C.c_float * 4)(*[float(v) for v in p]))
+        if hasattr(scatterers, "data_ptr"):
+            sc, n = scatterers, int(scatterers.shape[0])
+        else:
+            sc = np.ascontiguousarray(scatterers, np.float32).reshape(-1, 4)
+            n = sc.shape[0]
+        self._call(lib().ur_scene_upload(self._ctx, M, len(med), B, len(boundaries), int(med_array), float(z_max),
+                                         _ptr(sc) if n else None, n, float(r_s)))
+
+    def set_array(self, arr):
+        self.array = dict(arr)
+        a = Array(int(arr["n_el"]), arr["pitch"], arr["elev_h"], arr["f0"], arr["fs"], int(arr["n_s"]),
+                  arr["n_cycles"], arr["alpha_m_deg"], arr["alpha_c_deg"], arr["c_bf"], arr["tcut_sigmas"])
+        self._call(lib().ur_set_array(self._ctx, C.byref(a)))
+
+    def set_plane_waves(self, angles_rad):
+        a = np.ascontiguousarray(angles_rad, np.float32).reshape(-1)
+        self._call(lib().ur_set_plane_waves(self._ctx, _ptr(a), a.size))
+        self.n_tx = a.size
+
+    def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0):
+        t = Tuning(cell_xy, cell_z, block, blocks_per_sm)
+        self._call(lib().ur_set_tuning(self._ctx, C.byref(t)))
+
+    def load(self, workload):
+        """Scene, array and transmits of a phantoms.* workload dictionary."""
+        s = workload["scene"]
+        self.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], s["scatterers"], s["r_s"])
+        self.set_array(workload["array"])
+        self.set_plane_waves(workload["angles"])
+
+    # -- simulation ---------------------------------------------------------
+    def _channel_shape(self):
+        return (self.n_tx, int(self.array["n_el"]), int(self.array["n_s"]))
+
+    def trace(self, n_rays, seed, max_bounces, max_path=0.2, rf=None, quad=None, stats=False):
+        torch = self._torch
+        shape = self._channel_shape()
+        if rf is None:
+            rf = torch.empty(shape, dtype=torch.float32, device=self.device)
+        if quad is None:
+            quad = torch.empty(shape, dtype=torch.float32, device=self.device)
+        st = Stats()
+        self._call(lib().ur_trace(self._ctx, int(n_rays), int(seed), int(max_bounces), float(max_path),
+                                  _ptr(rf), _ptr(quad), C.byref(st)))
+        if stats:
+            return rf, quad, {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+        return rf, quad
+
+    def trace_debug(self, n_rays, seed, max_bounces, max_path=0.2, capacity=None, path_hash=True):
+        """Trace plus every arrival record and per-path hashes (device tensors)."""
+        torch = self._torch
+        shape = self._channel_shape()
+        rf = torch.empty(shape, dtype=torch.float32, device=self.device)
+        quad = torch.empty(shape, dtype=torch.float32, device=self.device)
+        if capacity is None:
+            capacity = max(4096, int(n_rays) * self.n_tx)
+        dev = self.device
+        out = {k: torch.empty(capacity, dtype=torch.int32, device=dev) for k in ("ray", "event", "row")}
+        out.update({k: torch.empty(capacity, dtype=torch.float32, device=dev) for k in ("t_hi", "t_lo", "amp")})
+        ph = torch.empty((self.n_tx, int(n_rays)), dtype=torch.int64, device=dev) if path_hash else None
+        dbg = Debug(capacity, 0, _ptr(out["ray"]), _ptr(out["event"]), _ptr(out["row"]), _ptr(out["t_hi"]),
+                    _ptr(out["t_lo"]), _ptr(out["amp"]), _ptr(ph))
+        st = Stats()
+        self._call(lib().ur_trace_debug(self._ctx, int(n_rays), int(seed), int(max_bounces), float(max_path),
+                                        _ptr(rf), _ptr(quad), C.byref(st), C.byref(dbg)))
+        n = int(dbg.count)
+        rec = {k: v[:n] for k, v in out.items()}
+        return rf, quad, {f: int(getattr(st, f)) for f, _ in Stats._fields_}, rec, ph
+
+    def beamform(self, rf, quad, x_px, z_px, dyn_range_db=60.0, iq=True, env=True, db=True):
+        torch = self._torch
+        xp = x_px if hasattr(x_px, "data_ptr") else np.ascontiguousarray(x_px, np.float32)
+        zp = z_px if hasattr(z_px, "data_ptr") else np.ascontiguousarray(z_px, np.float32)
+        nx, nz = int(xp.shape[0]), int(zp.shape[0])
+        dev = self.device
+        def out(spec, shape):
+            if spec is True:
+                return torch.empty(shape, dtype=torch.float32, device=dev)
+            return None if spec is None or spec is False else spec
+
+        o_iq, o_env, o_db = out(iq, (nz, nx, 2)), out(env, (nz, nx)), out(db, (nz, nx))
+        self._call(lib().ur_beamform(self._ctx, _ptr(rf), _ptr(quad), _ptr(xp), nx, _ptr(zp), nz, float(dyn_range_db),
+                                     _ptr(o_iq), _ptr(o_env), _ptr(o_db)))
+        return o_iq, o_env, o_db
+
+    def set_profiling(self, on=True):
+        self._call(lib().ur_set_profiling(self._ctx, 1 if on else 0))
+
+    def profile(self):
+        """{phase: (device ms, kernel launches, calls)} accumulated while profiling."""
+        p = Profile()
+        self._call(lib().ur_get_profile(self._ctx, C.byref(p)))
+        return {name: (p.ms[q], int(p.launches[q]), int(p.calls[q])) for q, name in enumerate(PHASES)}
+
+    def sync(self):
+        self._call(lib().ur_sync(self._ctx))
+
+
+def build_library(force=False):
+    """Compile the CUDA library in-tree (see build.py)."""
+    from .build import build as _build
+    return _build(force=force)

@@ -1,0 +1,230 @@
+// Device-side building blocks of the sm_103a acoustic ray tracer: float-float
+// arithmetic for times and delays, Philox4x32-10, parameter blocks shared by
+// the kernels, and host-side launcher declarations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ur {
+
+constexpr int kMaxMed = 16;
+constexpr int kMaxBnd = 32;
+constexpr int kMaxNs = 8192;
+constexpr int kMaxSeg = 4096;      // safety bound on primary segments per path
+constexpr int kMaxCross = 64;      // boundaries a connection ray may cross
+constexpr float kTmin = 1e-7f;     // smallest admissible hit distance (m)
+constexpr uint64_t kFnvOffset = 0xcbf29ce484222325ull;
+constexpr uint64_t kFnvPrime = 0x100000001b3ull;
+
+enum { kPlaneZ = 0, kSphere = 1, kCylY = 2 };
+enum { kEndAperture = 1, kEndArrayMiss = 2, kEndBottom = 3, kEndPath = 4, kEndTime = 5, kEndMaxB = 6 };
+
+// ---------------------------------------------------------------- float-float
+// A value hi + lo with |lo| <= ulp(hi)/2 (Dekker / Knuth error-free transforms).
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_quick(float a, float b) {   // requires |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = ff_two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return ff_quick(s.hi, lo);
+}
+
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    ff s = ff_two_sum(a.hi, b);
+    return ff_quick(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// a (float) times b (ff)
+__device__ __forceinline__ ff ff_mul_f(float a, ff b) {
+    float p = __fmul_rn(a, b.hi);
+    float e = __fmaf_rn(a, b.hi, -p);
+    e = __fmaf_rn(a, b.lo, e);
+    return ff_quick(p, e);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ff_quick(p, e);
+}
+
+__device__ __forceinline__ ff ff_sqr_f(float a) {
+    float p = __fmul_rn(a, a);
+    return ff_quick(p, __fmaf_rn(a, a, -p));
+}
+
+// square root of a non-negative ff (one Newton correction of the float root)
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+    if (a.hi <= 0.f) return {0.f, 0.f};
+    float s = sqrtf(a.hi);
+    float r = __fmaf_rn(-s, s, a.hi);
+    r = __fadd_rn(r, a.lo);
+    return ff_quick(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
+}
+
+__device__ __forceinline__ bool ff_gt(ff a, float b) { return a.hi > b || (a.hi == b && a.lo > 0.f); }
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon et al. (SC'11): ten rounds, each two 32x32
+// multiplies whose high/low halves are mixed with the other counter words and
+// the key; the key advances by the two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hA = __umulhi(0xD2511F53u, c.x), lA = 0xD2511F53u * c.x;
+        const uint32_t hB = __umulhi(0xCD9E8D57u, c.z), lB = 0xCD9E8D57u * c.z;
+        c = make_uint4(hB ^ c.y ^ k.x, lB, hA ^ c.w ^ k.y, lA);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniform in [0, 1) from the top 24 bits (exact in float).
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
+
+__device__ __forceinline__ uint64_t fnv_step(uint64_t h, uint32_t w) { return (h ^ (uint64_t)w) * kFnvPrime; }
+
+// ---------------------------------------------------------------- vectors
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 unit3(float3 a) {
+    float l = sqrtf(dot3(a, a));
+    return make_float3(a.x / l, a.y / l, a.z / l);
+}
+
+// ---------------------------------------------------------------- parameters
+struct Medium {
+    float c, Z, a;          // m/s, MRayl, Np/m
+    ff slow;                // samples per metre (fs / c)
+};
+
+struct Bnd {
+    int kind, med_neg, med_pos, pad;
+    float p[4];
+};
+
+struct SceneP {
+    int n_med, n_bnd, med_array;
+    float z_max;
+    Medium med[kMaxMed];
+    Bnd bnd[kMaxBnd];
+    // scatterer grid
+    int n_scat;
+    float r2;               // capture radius squared
+    float3 g_lo, g_inv_h, g_h;
+    int3 g_dim;
+    const float4 *refs;     // (x, y, z, bits(index)) per cell reference
+    const uint32_t *cell_start;
+    const float *amp;
+};
+
+struct TraceP {
+    SceneP S;
+    // array
+    int n_el, n_s;
+    float pitch, H, x_first;        // element 0 centre
+    float K, t_last;                // pulse half-width and latest useful arrival (samples)
+    float cos_am, cos_ac, am, ac;   // directivity (Eq. 13)
+    // transmits
+    int n_tx;
+    const float2 *txdir;            // (sin, cos) per transmit
+    const ff *delay;                // [n_tx][n_el] transmit delays (samples)
+    // rays
+    uint32_t n_rays, rays_per_el;
+    uint2 key;
+    int max_b;
+    float max_path, inv_n;
+    // outputs
+    uint4 *arr;                     // (row, t_hi, t_lo, amp)
+    uint2 *arr_dbg;                 // (ray, event), debug only
+    unsigned long long *arr_count;
+    uint64_t arr_cap;
+    unsigned long long *path_hash;  // [n_tx][n_rays], debug only
+    unsigned long long *stats;      // 6 counters, nullable
+};
+
+// ---------------------------------------------------------------- launchers
+void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s);
+int trace_occupancy(int block, bool debug);   // resident tracer CTAs per SM
+
+struct BinP {
+    const uint4 *arr;
+    const unsigned long long *arr_count;
+    uint64_t arr_cap;
+    int n_rows, n_s;
+    uint32_t *row_count;    // [n_rows]
+    uint32_t *row_fill;     // [n_rows]
+    uint32_t *row_off;      // [n_rows + 1]
+    uint4 *items;           // (row, begin, end, 0) work items
+    uint32_t *n_items;
+    uint32_t max_items, chunk;
+    float4 *sorted;         // (t_hi, t_lo, amp, 0)
+    float *rf, *quad;       // [n_rows][n_s]
+    float K, inv_2s2, phase_per_sample;   // taps |n - t| <= K; gaussian 1/(2 s^2); 2 f0 / fs (half-cycles per sample)
+};
+void launch_bin_sort(const BinP &B, int sms, cudaStream_t s);      // 3 kernels
+void launch_bin_deposit(const BinP &B, int sms, cudaStream_t s);   // 1 kernel
+
+struct GridBuildP {
+    const float4 *scat;
+    int n_scat;
+    float r_m;
+    float3 lo, inv_h;
+    int3 dim;
+    uint32_t *cell_count;   // [n_cells + 1]
+    uint32_t *cell_start;   // [n_cells + 1]
+    uint32_t *cell_fill;    // [n_cells]
+    float4 *refs;
+    float *amp;
+};
+void launch_bbox(const float4 *scat, int n, float *lohi /* 6 floats as ordered ints */, cudaStream_t s);
+void launch_grid_count(const GridBuildP &G, cudaStream_t s);
+void launch_scan_u32(const uint32_t *in, uint32_t *out, uint32_t *block_sums, uint32_t n, cudaStream_t s);
+void launch_grid_fill(const GridBuildP &G, cudaStream_t s);
+
+struct ImageP {
+    const float *rf, *quad;
+    int n_tx, n_el, n_s;
+    const float *x_px, *z_px;
+    int nx, nz;
+    ff q;                   // fs / c_bf (samples per metre)
+    ff x_first;             // element 0 centre
+    float pitch;
+    const ff *tx_sin, *tx_cos, *tx_m;   // per transmit: sin, cos, min_e x_e sin
+    float2 *iq;
+    float *env, *db;
+    unsigned int *env_max;  // float bits
+    float dyn_range_db;
+};
+void launch_das(const ImageP &I, cudaStream_t s);
+
+struct DebugOut {
+    uint32_t *ray, *event, *row;
+    float *t_hi, *t_lo, *amp;
+    uint64_t cap;
+};
+void launch_unpack_debug(const uint4 *arr, const uint2 *dbg, const unsigned long long *count, uint64_t cap_in,
+                         const DebugOut &D, cudaStream_t s);
+void launch_log(const ImageP &I, cudaStream_t s);
+
+}  // namespace ur

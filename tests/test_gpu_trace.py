@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs: path topology, per-arrival time/amplitude/element, channel data
+and images.  Thresholds: >= 99.99 % identical paths, |dt| <= 1e-3 samples,
+channel data and images within 1e-4 relative L2 (over matched paths)."""
+import numpy as np
+import pytest
+
+import oracle
+import phantoms
+from _parity import compare, drop_rays, gpu_records, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+PATH_FRAC = 0.9999
+DT_MAX = 1e-3
+REL_L2 = 1e-4
+AMP_REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ur():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05828_gb300 as ur
+    ur.lib()
+    return ur
+
+
+def run_gpu(ur, w, n_rays=None, seed=None):
+    sim = ur.Simulator(0)
+    sim.load(w)
+    n = n_rays or w["n_rays"]
+    rf, quad, st, rec, ph = sim.trace_debug(n, w["seed"] if seed is None else seed, w["max_bounces"], w["max_path"])
+    out = {"rf": rf.double().cpu().numpy(), "quad": quad.double().cpu().numpy(), "stats": st,
+           "rec": gpu_records(rec, w["array"]["n_el"]), "hash": ph.cpu().numpy().view(np.uint64), "sim": sim}
+    return out
+
+
+def run_oracle(w, n_rays=None, seed=None, ray_begin=0, ray_end=None):
+    n = n_rays or w["n_rays"]
+    arr, topo, st = oracle.trace(w["scene"], w["array"], w["angles"], n, w["seed"] if seed is None else seed,
+                                 w["max_bounces"], w["max_path"], ray_begin=ray_begin, ray_end=ray_end, topo=True)
+    return arr, topo, st
+
+
+def check_trace_parity(w, G, arr, topo, label=""):
+    n_tx = len(w["angles"])
+    res = compare(G["rec"], arr, G["hash"], topo)
+    assert res["frac_paths"] >= PATH_FRAC, (label, res["frac_paths"], len(res["bad_rays"]))
+    assert res["max_dt"] <= DT_MAX, (label, res["max_dt"])
+    assert res["el_mismatch"] == 0, label
+    assert res["max_amp_rel"] <= AMP_REL, (label, res["max_amp_rel"])
+    orf, oq = oracle.deposit(w["array"], n_tx, arr)
+    bad = res["bad_rays"]
+    if bad:
+        gb_rf, gb_q = oracle.deposit(w["array"], n_tx, G["rec"][[(t, r) in bad for t, r in zip(G["rec"]["tx"], G["rec"]["ray"])]])
+        om_rf, om_q = oracle.deposit(w["array"], n_tx, drop_rays(arr, bad))
+    else:
+        gb_rf = gb_q = 0.0
+        om_rf, om_q = orf, oq
+    if np.linalg.norm(orf) > 0:
+        e_rf = rel_l2(G["rf"] - gb_rf, om_rf)
+        e_q = rel_l2(G["quad"] - gb_q, om_q)
+        assert e_rf <= REL_L2 and e_q <= REL_L2, (label, e_rf, e_q, rel_l2(G["rf"], orf))
+    else:
+        assert np.abs(G["rf"]).max() == 0.0 and np.abs(G["quad"]).max() == 0.0
+    return res
+
+
+def test_tiny_full_parity(ur):
+    w = phantoms.tiny()
+    G = run_gpu(ur, w)
+    arr, topo, ost = run_oracle(w)
+    res = check_trace_parity(w, G, arr, topo, "tiny")
+    assert G["stats"]["rays"] == w["n_rays"]
+    assert G["stats"]["arrivals"] == len(G["rec"])
+    assert abs(G["stats"]["segments"] - ost["segments"]) <= 10
+    assert res["n_matched"] >= 0.999 * len(arr)
+
+
+def test_tiny_steered_transmits(ur):
+    w = phantoms.tiny(n_rays=30_000)
+    w["angles"] = np.deg2rad(np.array([-10.0, 0.0, 7.5], np.float64)).astype(np.float32)
+    G = run_gpu(ur, w, seed=3)
+    arr, topo, _ = run_oracle(w, seed=3)
+    check_trace_parity(w, G, arr, topo, "steered")
+
+
+def test_layered_parity(ur):
+    w = phantoms.layered(n_rays=20_000)
+    G = run_gpu(ur, w)
+    arr, topo, _ = run_oracle(w)
+    check_trace_parity(w, G, arr, topo, "layered")
+
+
+def test_layered_full_size_sampled(ur):
+    """1e7 rays, the benchmarked configuration: sampled rays against the oracle,
+    the deposit of all GPU arrivals against the oracle's deposit of the same
+    records, and the plain trace against the debug trace."""
+    import torch
+    w = phantoms.layered()
+    sim = ur.Simulator(0)
+    sim.load(w)
+    N = w["n_rays"]
+    rf_plain, q_plain = sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])
+    rf, quad, st, rec, ph = sim.trace_debug(N, w["seed"], w["max_bounces"], w["max_path"], capacity=int(0.6 * N))
+    torch.cuda.synchronize()
+    g = gpu_records(rec, w["array"]["n_el"])
+    hashes = ph.cpu().numpy().view(np.uint64)
+    assert st["rays"] == N and st["arrivals"] == g.size
+    # binning of all ~1e6+ arrivals vs the oracle's deposit of the same records
+    drf, dq = oracle.deposit(w["array"], 1, g)
+    assert rel_l2(rf.double().cpu().numpy(), drf) <= 1e-5
+    assert rel_l2(quad.double().cpu().numpy(), dq) <= 1e-5
+    assert rel_l2(rf_plain.double().cpu().numpy(), rf.double().cpu().numpy()) <= 1e-6
+    # sampled rays, traced independently by the oracle
+    for b0, b1 in ((0, 3000), (N // 2, N // 2 + 2000), (N - 3000, N)):
+        arr, topo, _ = run_oracle(w, ray_begin=b0, ray_end=b1)
+        sel = g[(g["ray"] >= b0) & (g["ray"] < b1)]
+        res = compare(sel, arr, hashes[:, b0:b1], topo, ray_begin=b0)
+        assert res["frac_paths"] >= 0.999, res["frac_paths"]      # 1 mismatch in 1000-3000 rays allowed
+        assert res["max_dt"] <= DT_MAX and res["el_mismatch"] == 0
+        assert res["max_amp_rel"] <= AMP_REL
+
+
+def test_beamform_parity(ur):
+    """Same float32 channel data into both beamformers."""
+    import torch
+    w = phantoms.tiny()
+    arr, _, _ = run_oracle(w)
+    orf, oq = oracle.deposit(w["array"], 1, arr)
+    rf32, q32 = orf.astype(np.float32), oq.astype(np.float32)
+    sim = ur.Simulator(0)
+    sim.load(w)
+    iq, env, db = sim.beamform(torch.from_numpy(rf32).cuda(), torch.from_numpy(q32).cuda(), w["x_px"], w["z_px"],
+                               w["dyn_range_db"])
+    oiq = oracle.beamform(w["array"], w["angles"], rf32.astype(np.float64), q32.astype(np.float64), w["x_px"], w["z_px"])
+    oenv, odb = oracle.envelope_log(oiq, w["dyn_range_db"])
+    giq = iq.double().cpu().numpy()
+    giq = giq[..., 0] + 1j * giq[..., 1]
+    assert rel_l2(giq, oiq) <= 1e-5
+    assert rel_l2(env.double().cpu().numpy(), oenv) <= 1e-5
+    gdb = db.double().cpu().numpy()
+    strong = oenv > 1e-3 * oenv.max()
+    assert np.abs(gdb - odb)[strong].max() <= 1e-3
+    assert gdb.max() == 0.0 and gdb.min() >= -w["dyn_range_db"]
+
+
+def test_beamform_compounding_parity(ur):
+    import torch
+    w = phantoms.layered(n_rays=4000, angles_deg=(-12.0, 0.0, 5.0))
+    arr, _, _ = run_oracle(w)
+    orf, oq = oracle.deposit(w["array"], 3, arr)
+    rf32, q32 = orf.astype(np.float32), oq.astype(np.float32)
+    sim = ur.Simulator(0)
+    sim.load(w)
+    x = w["x_px"][::4].copy()
+    z = w["z_px"][::2].copy()
+    iq, env, db = sim.beamform(torch.from_numpy(rf32).cuda(), torch.from_numpy(q32).cuda(), x, z, 60.0)
+    oiq = oracle.beamform(w["array"], w["angles"], rf32.astype(np.float64), q32.astype(np.float64), x, z)
+    giq = iq.double().cpu().numpy()
+    assert rel_l2(giq[..., 0] + 1j * giq[..., 1], oiq) <= 1e-5
+
+
+def test_end_to_end_image_parity(ur):
+    """Whole chain on the tiny phantom: GPU image vs oracle image."""
+    w = phantoms.tiny()
+    G = run_gpu(ur, w)
+    _, env, db = G["sim"].beamform(
+        __import__("torch").from_numpy(G["rf"].astype(np.float32)).cuda(),
+        __import__("torch").from_numpy(G["quad"].astype(np.float32)).cuda(), w["x_px"], w["z_px"], 60.0)
+    arr, topo, _ = run_oracle(w)
+    O = oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
+                        w["z_px"], 60.0)
+    res = compare(G["rec"], arr, G["hash"], topo)
+    if not res["bad_rays"]:
+        assert rel_l2(env.double().cpu().numpy(), O["env"]) <= REL_L2
+
+
+@pytest.mark.parametrize("case", ["empty_scene", "few_rays", "ragged", "no_bounce", "short_window", "one_element",
+                                  "wide_directivity", "sphere_only"])
+def test_edge_cases(ur, case):
+    w = phantoms.tiny(n_rays=4000)
+    seed = 9
+    if case == "empty_scene":
+        w["scene"]["boundaries"] = []
+        w["scene"]["scatterers"] = np.zeros((0, 4), np.float32)
+    elif case == "few_rays":
+        w["n_rays"] = 7
+    elif case == "ragged":
+        w["n_rays"] = 1001
+    elif case == "no_bounce":
+        w["max_bounces"] = 0
+    elif case == "short_window":
+        w["array"]["n_s"] = 64
+    elif case == "one_element":
+        w["array"]["n_el"] = 1
+        w["array"]["pitch"] = float(np.float32(4e-3))
+    elif case == "wide_directivity":
+        w["array"]["alpha_m_deg"] = 10.0
+        w["array"]["alpha_c_deg"] = 30.0
+        w["scene"]["scatterers"] = phantoms.tiny(n_scat=2000)["scene"]["scatterers"]
+    elif case == "sphere_only":
+        w["scene"]["boundaries"] = w["scene"]["boundaries"][1:]
+        w["scene"]["media"][1] = w["scene"]["media"][0]
+    G = run_gpu(ur, w, seed=seed)
+    arr, topo, _ = run_oracle(w, seed=seed)
+    check_trace_parity(w, G, arr, topo, case)
+    if case == "empty_scene":
+        assert len(arr) == 0 and len(G["rec"]) == 0
+
+
+def test_host_buffers_match_device(ur):
+    import torch
+    w = phantoms.tiny(n_rays=20_000)
+    sim = ur.Simulator(0)
+    sim.load(w)
+    rf_d, q_d = sim.trace(w["n_rays"], 0, 4)
+    shape = (1, w["array"]["n_el"], w["array"]["n_s"])
+    rf_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    q_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    sim.trace(w["n_rays"], 0, 4, rf=rf_h, quad=q_h)
+    assert rel_l2(rf_h.double().numpy(), rf_d.double().cpu().numpy()) <= 1e-6
+    db_h = torch.empty((w["z_px"].size, w["x_px"].size), dtype=torch.float32).pin_memory()
+    _, _, db_d = sim.beamform(rf_d, q_d, w["x_px"], w["z_px"], 60.0)
+    sim.beamform(rf_h, q_h, w["x_px"], w["z_px"], 60.0, iq=None, env=None, db=db_h)
+    assert np.abs(db_h.numpy() - db_d.cpu().numpy()).max() <= 1e-3
+
+
+def test_deterministic_arrival_set(ur):
+    w = phantoms.tiny(n_rays=50_000)
+    a = run_gpu(ur, w)["rec"]
+    b = run_gpu(ur, w)["rec"]
+    o1 = np.lexsort((a["event"], a["ray"], a["tx"]))
+    o2 = np.lexsort((b["event"], b["ray"], b["tx"]))
+    assert np.array_equal(a[o1], b[o2])
+
+
+def test_invalid_arguments_and_state(ur):
+    w = phantoms.tiny(n_rays=100)
+    sim = ur.Simulator(0)
+    with pytest.raises(ur.URError) as e:
+        sim.array = w["array"]
+        sim.n_tx = 1
+        sim.trace(100, 0, 4)
+    assert e.value.code == 6                       # UR_ERR_STATE: nothing uploaded
+    sim.load(w)
+    for bad in (dict(n_rays=0), dict(max_bounces=200), dict(max_path=-1.0)):
+        kw = dict(n_rays=100, seed=0, max_bounces=4, max_path=0.2)
+        kw.update(bad)
+        with pytest.raises(ur.URError) as e:
+            sim.trace(kw["n_rays"], kw["seed"], kw["max_bounces"], kw["max_path"])
+        assert e.value.code == 1
+    a = dict(w["array"])
+    a["n_s"] = 8
+    with pytest.raises(ur.URError):
+        sim.set_array(a)
+    med = np.array(w["scene"]["media"])
+    med[0, 3] = 0.5                                # rough boundaries are not supported
+    with pytest.raises(ur.URError):
+        sim.upload_scene(med, w["scene"]["boundaries"], 0, 0.04, w["scene"]["scatterers"], 1e-4)
+    with pytest.raises(ur.URError):
+        sim.set_plane_waves(np.array([1.2], np.float32))   # beyond 60 degrees
