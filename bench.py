@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the full simulation chain on the 128-element layered phantom.
+
+One step = one RF frame: 1e7 primary rays of one 0-degree plane wave traced
+through skin / fat / muscle / bone cylinder with 50k point scatterers
+(emission, reflection/refraction, transducer sampling, aperture returns),
+pulse deposit into [1 x 128 x 3200] analytic channel data, delay-and-sum to a
+512 x 256 image, envelope and log compression.  Metric: rays/s (RF frames/s
+alongside).  Inputs are resident in HBM before the timed region; L2 is
+flushed (256 MiB write, untimed) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same frame.  Under torchrun every rank simulates its own frame
+(independent seeds, no collective on the data path): weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rays/s and RF frames/s at 128 elements"
+UNIT = "rays/s"
+WORKLOAD = ("layered phantom: 128 el, pitch 0.3 mm, f0 5 MHz, fs 40 MHz, 0-deg plane wave, skin/fat/muscle + "
+            "bone cylinder r=6 mm, 50k scatterers, 1e7 rays/frame, 8 bounces, 3200 samples, DAS 512x256, 60 dB")
+
+# Algorithmic FP32 operations per unit of work counted by the tracer's counters
+# (formula arithmetic of one step of the method, independent of the search
+# structure): per primary segment (extend against the scene's primitives,
+# advance, attenuation, interaction), per scatterer event (closest-approach
+# tube test, element draw, directivity), per connection ray (crossings with
+# transmission factors, time and amplitude), per deposited pulse tap.
+FLOPS_PER_SEGMENT = 120
+FLOPS_PER_CANDIDATE = 30
+FLOPS_PER_CONNECTION = 200
+FLOPS_PER_TAP = 30
+FP32_LANES_PER_SM = 128
+
+# DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), per primary ray, valid only while the tracer sources
+# hash to `src_sha`.
+TRACE_TRAFFIC = {"src_sha": "080e7e8fc6b1d2d8", "bytes_per_ray": 2.825, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+
+
+def tracer_sha():
+    h = hashlib.sha256()
+    for f in ("ur_trace.cu", "ur_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2501_05828_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def taps_per_arrival(arr):
+    s = arr["n_cycles"] / (4.0 * arr["f0"]) * arr["fs"]
+    return 2 * int(arr["tcut_sigmas"] * s) + 1
+
+
+def algorithmic_flops(stats, arr):
+    return (stats["segments"] * FLOPS_PER_SEGMENT + stats["candidates"] * FLOPS_PER_CANDIDATE
+            + stats["connections"] * FLOPS_PER_CONNECTION + stats["arrivals"] * taps_per_arrival(arr) * FLOPS_PER_TAP)
+
+
+def trace_flops(stats):
+    return (stats["segments"] * FLOPS_PER_SEGMENT + stats["candidates"] * FLOPS_PER_CANDIDATE
+            + stats["connections"] * FLOPS_PER_CONNECTION)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_index is not None:
+            cmd += ["-i", str(gpu_index)]
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        pmax = max(r[2] for r in rows)
+        loaded = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in loaded for n, v in zip(names, r[3][1:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": pmax, "samples": len(rows), "samples_under_load": len(loaded), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(w, target_s, threads=None):
+    """FP64 oracle on a bounded sample of the frame: returns (rays/s, rays in sample, seconds)."""
+    import oracle
+    threads = threads or (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, 4096, threads=threads)
+    probe = time.perf_counter() - t0
+    n = int(max(1024, min(w["n_rays"], 4096 * target_s / max(probe, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, n, threads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, threads
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import phantoms
+    w = phantoms.layered()
+    threads = os.cpu_count() or 1
+    per_step = max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    rate, n, _, _ = oracle_rate(w, per_step, threads)
+    import oracle
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
+                        w["z_px"], w["dyn_range_db"], w["max_path"], 0, n, threads=threads)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step = sum(times) / len(times)
+    value = n / step
+    sample = "first %d of the frame's 1e7 rays (ray indices 0..%d), full chain incl. deposit and 512x256 DAS" % (n, n - 1)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2501_05828_gb300 as ur
+    import phantoms
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    w = phantoms.layered()
+    if args.rays:
+        w["n_rays"] = args.rays
+    seed = w["seed"] + rank
+    N, A = w["n_rays"], w["array"]
+    sim = ur.Simulator(local_rank)
+    sim.load(w)
+    shape = (1, A["n_el"], A["n_s"])
+    rf = torch.empty(shape, dtype=torch.float32, device=dev)
+    quad = torch.empty(shape, dtype=torch.float32, device=dev)
+    nx, nz = w["x_px"].size, w["z_px"].size
+    x_d = torch.from_numpy(w["x_px"]).to(dev)
+    z_d = torch.from_numpy(w["z_px"]).to(dev)
+    env = torch.empty((nz, nx), dtype=torch.float32, device=dev)
+    db = torch.empty((nz, nx), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    last = {}
+
+    def step():
+        _, _, st = sim.trace(N, seed, w["max_bounces"], w["max_path"], rf=rf, quad=quad, stats=True)
+        sim.beamform(rf, quad, x_d, z_d, w["dyn_range_db"], iq=None, env=env, db=db)
+        last["stats"] = st
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sim.set_profiling(True)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    prof = sim.profile()
+    sim.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = N * world / (ms_max * 1e-3)
+
+    # ---- roofline of the dominant kernel (the tracer) ----
+    st = last["stats"]
+    trace_ms, trace_launches, trace_calls = prof["trace"]
+    t_launch = trace_ms / max(trace_calls, 1) * 1e-3
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = trace_flops(st) / t_launch / 1e12
+    traffic = None
+    if TRACE_TRAFFIC and TRACE_TRAFFIC.get("src_sha") == tracer_sha():
+        traffic = TRACE_TRAFFIC["bytes_per_ray"] * N
+    launches = sum(v[1] for v in prof.values())
+    phase_ms = {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]}
+
+    # ---- end to end through the C ABI with host buffers ----
+    sc_host = torch.from_numpy(w["scene"]["scatterers"]).pin_memory()
+    x_h = torch.from_numpy(w["x_px"]).pin_memory()
+    z_h = torch.from_numpy(w["z_px"]).pin_memory()
+    db_h = torch.empty((nz, nx), dtype=torch.float32).pin_memory()
+    s = w["scene"]
+    h2d = sc_host.numel() * 4 + x_h.numel() * 4 + z_h.numel() * 4 + len(s["media"]) * 16 + len(s["boundaries"]) * 28 + 4
+    d2h = db_h.numel() * 4
+
+    def e2e_step():
+        sim.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], sc_host, s["r_s"])
+        sim.trace(N, seed, w["max_bounces"], w["max_path"], rf=rf, quad=quad)
+        sim.beamform(rf, quad, x_h, z_h, w["dyn_range_db"], iq=None, env=None, db=db_h)
+        torch.cuda.synchronize()
+
+    n_e2e = 0 if args.skip_e2e else max(3, min(args.steps, 20))
+    e2e_s = float("nan")
+    if n_e2e:
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_per_frame": N, "n_el": A["n_el"], "n_s": A["n_s"],
+                       "image": "%dx%d" % (nx, nz), "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "parallelism": "replicas: one frame per GPU"},
+            "frames_per_s": world / (ms_max * 1e-3),
+            "phase_ms": phase_ms,
+            "roofline": {"bound": "alu", "kernel": "k_trace", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
+                             props.multi_processor_count, FP32_LANES_PER_SM, sm_mhz),
+                         "trace_ms_per_launch": t_launch * 1e3,
+                         "algorithmic_flops_per_launch": trace_flops(st)},
+            "stats_per_frame": st,
+            "gpu_launches": launches,
+            "e2e": {"value": N * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+                    "path": "ur_scene_upload(pinned host scatterers, grid build) + ur_trace + ur_beamform(db -> pinned host)"},
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rate, n, dt, thr = oracle_rate(w, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                    "sample": "rays 0..%d of the same frame (%.1f s), trace + deposit + 512x256 DAS + log"
+                                              % (n - 1, dt)}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
+    ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()
