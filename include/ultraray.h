@@ -198,6 +198,38 @@ ur_status ur_set_profiling(ur_ctx *ctx, int on);
 /* Copy the accumulators (valid whether or not profiling is still on). */
 ur_status ur_get_profile(ur_ctx *ctx, ur_profile *out);
 
+/* Allocation-free variant of ur_beamform (the paper has no counterpart).
+ *
+ * Some callers cannot let a library call cudaMalloc: code that runs while a
+ * CUDA stream is being captured into a graph (allocation is not permitted
+ * there), real-time acquisition loops that forbid allocation after start-up,
+ * and hosts that hand the GPU's memory to their own pool up front.  This entry
+ * point computes exactly what ur_beamform computes (same kernels) but allocates
+ * nothing: its scratch (transmit tables, pixel coordinates, the envelope
+ * maximum and, when env is NULL, the envelope) lives in a fixed device array
+ * of UR_NOALLOC_SCRATCH_BYTES (4.5 MiB) that every GPU loading the library
+ * holds until the process exits.
+ *
+ * Requirements: the context's array and transmits are set (UR_ERR_STATE
+ * otherwise); rf, quad and every non-NULL output are device memory; x_px / z_px
+ * may be host or device memory.  Limits: n_tx <= UR_NOALLOC_MAX_TX,
+ * nx, nz <= UR_NOALLOC_MAX_AXIS, and nx * nz <= UR_NOALLOC_MAX_PIXELS when env
+ * is NULL; larger requests return UR_ERR_INVALID_ARG without launching work.
+ * The first call on a device looks up the scratch's device address (once per
+ * device), so make that first call before any stream capture.  All calls share
+ * the one scratch array, which keeps the last call's contents (the envelope
+ * maximum is cleared by each call): calls whose work overlaps on the GPU (for
+ * example on two streams) race and must be serialised by the caller.
+ * Works asynchronously on the context's stream; reports errors through the
+ * status only (ur_last_error is not updated). */
+#define UR_NOALLOC_MAX_TX 1024
+#define UR_NOALLOC_MAX_AXIS 8192
+#define UR_NOALLOC_MAX_PIXELS (1 << 20)
+#define UR_NOALLOC_SCRATCH_BYTES (4608 * 1024)
+ur_status ur_beamform_noalloc(ur_ctx *ctx, const float *rf, const float *quad,
+                              const float *x_px, int nx, const float *z_px, int nz, float dyn_range_db,
+                              float *iq, float *env, float *db);
+
 /* Wait for all work on the context's stream and report asynchronous errors. */
 ur_status ur_sync(ur_ctx *ctx);
 

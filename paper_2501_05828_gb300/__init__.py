@@ -26,7 +26,7 @@ STATUS = {0: "UR_OK", 1: "UR_ERR_INVALID_ARG", 2: "UR_ERR_CUDA", 3: "UR_ERR_OOM"
 # every entry point include/ultraray.h declares
 EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_set_array", "ur_set_plane_waves",
            "ur_trace", "ur_trace_debug", "ur_beamform", "ur_set_tuning", "ur_set_profiling", "ur_get_profile",
-           "ur_sync")
+           "ur_sync", "ur_beamform_noalloc")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log")
 
 
@@ -95,6 +95,7 @@ def lib():
             L.ur_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
             L.ur_sync.argtypes = [vp]
             L.ur_set_profiling.argtypes = [vp, i32]
+            L.ur_beamform_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, vp, vp]
             L.ur_get_profile.argtypes = [vp, C.POINTER(Profile)]
             for name in EXPORTS:
                 if name != "ur_last_error":
@@ -237,6 +238,16 @@ class Simulator:
         self._call(lib().ur_beamform(self._ctx, _ptr(rf), _ptr(quad), _ptr(xp), nx, _ptr(zp), nz, float(dyn_range_db),
                                      _ptr(o_iq), _ptr(o_env), _ptr(o_db)))
         return o_iq, o_env, o_db
+
+    def beamform_noalloc(self, rf, quad, x_px, z_px, dyn_range_db=60.0, iq=None, env=None, db=None):
+        """ur_beamform_noalloc: outputs are caller-allocated device tensors (or None); nothing is allocated."""
+        xp = x_px if hasattr(x_px, "data_ptr") else np.ascontiguousarray(x_px, np.float32)
+        zp = z_px if hasattr(z_px, "data_ptr") else np.ascontiguousarray(z_px, np.float32)
+        code = lib().ur_beamform_noalloc(self._ctx, _ptr(rf), _ptr(quad), _ptr(xp), int(xp.shape[0]), _ptr(zp),
+                                         int(zp.shape[0]), float(dyn_range_db), _ptr(iq), _ptr(env), _ptr(db))
+        if code != 0:
+            raise URError(code, "ur_beamform_noalloc rejected the call")
+        return iq, env, db
 
     def set_profiling(self, on=True):
         self._call(lib().ur_set_profiling(self._ctx, 1 if on else 0))

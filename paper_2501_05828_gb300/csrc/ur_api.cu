@@ -483,6 +483,18 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
 
 }  // namespace
 
+namespace ur {
+bool ctx_view(const ur_ctx *c, CtxView *v) {
+    if (!c || !c->array_ok || c->angles.empty()) return false;
+    v->device = c->device;
+    v->stream = (void *)c->stream;
+    v->arr = c->arr;
+    v->n_tx = (int)c->angles.size();
+    v->angles = c->angles.data();
+    return true;
+}
+}  // namespace ur
+
 extern "C" {
 
 ur_status ur_create(ur_ctx **out, int device, void *cuda_stream) {

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ultraray.h"
+
 namespace ur {
 
 constexpr int kMaxMed = 16;
@@ -226,5 +228,16 @@ struct DebugOut {
 void launch_unpack_debug(const uint4 *arr, const uint2 *dbg, const unsigned long long *count, uint64_t cap_in,
                          const DebugOut &D, cudaStream_t s);
 void launch_log(const ImageP &I, cudaStream_t s);
+
+// Read-only view of a context's set-up for entry points living in other files
+// (false if the array or the transmits are not set).
+struct CtxView {
+    int device;
+    void *stream;
+    ur_array arr;
+    int n_tx;
+    const float *angles;    // host copy, n_tx entries
+};
+bool ctx_view(const ur_ctx *c, CtxView *v);
 
 }  // namespace ur
