@@ -174,10 +174,12 @@ ur_status ur_beamform(ur_ctx *ctx, const float *rf, const float *quad,
                       float *iq, float *env, float *db);
 
 /* Scatterer-grid and launch tuning (0 fields keep the defaults).  Cell sizes in
- * metres; applied at the next ur_scene_upload. */
+ * metres, applied at the next ur_scene_upload; block (multiple of 32, <= 256),
+ * blocks_per_sm and resolve_batch (1..32: the tracer finishes segments and
+ * starts rays once this many lanes of a warp wait) apply at the next trace. */
 typedef struct {
     float cell_xy, cell_z;
-    int32_t block, blocks_per_sm;
+    int32_t block, blocks_per_sm, resolve_batch;
 } ur_tuning;
 ur_status ur_set_tuning(ur_ctx *ctx, const ur_tuning *t);
 

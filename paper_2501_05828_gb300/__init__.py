@@ -66,7 +66,8 @@ class Profile(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("cell_xy", C.c_float), ("cell_z", C.c_float), ("block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+    _fields_ = [("cell_xy", C.c_float), ("cell_z", C.c_float), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("resolve_batch", C.c_int32)]
 
 
 _lib = None
@@ -173,8 +174,8 @@ class Simulator:
         self._call(lib().ur_set_plane_waves(self._ctx, _ptr(a), a.size))
         self.n_tx = a.size
 
-    def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0):
-        t = Tuning(cell_xy, cell_z, block, blocks_per_sm)
+    def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0, resolve_batch=0):
+        t = Tuning(cell_xy, cell_z, block, blocks_per_sm, resolve_batch)
         self._call(lib().ur_set_tuning(self._ctx, C.byref(t)))
 
     def load(self, workload):

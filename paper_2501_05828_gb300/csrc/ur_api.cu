@@ -233,8 +233,8 @@ void build_grid(ur_ctx *c, const float *scat_xyza) {
         if (!std::isfinite(lo[a]) || !std::isfinite(hi[a])) fail(UR_ERR_INVALID_ARG, "scatterer coordinates must be finite");
     // capture box margin: r_s plus a relative and absolute slack far above FP32 rounding
     const float r_m = c->r_s * 1.001f + 1e-7f;
-    float h_xy = c->tune.cell_xy > 0.f ? c->tune.cell_xy : 5.f * c->r_s;
-    float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : 20.f * c->r_s;
+    float h_xy = c->tune.cell_xy > 0.f ? c->tune.cell_xy : 3.f * c->r_s;
+    float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : 40.f * c->r_s;
     int3 dim;
     for (int tries = 0;; ++tries) {
         dim.x = std::max(1, (int)std::ceil((hi[0] - lo[0] + 2.f * r_m) / h_xy));
@@ -316,6 +316,7 @@ ur::TraceP make_trace_params(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_
     S.refs = (const float4 *)c->refs.p;
     S.cell_start = (const uint32_t *)c->cell_start.p;
     S.amp = (const float *)c->amp.p;
+    S.scat = (const float4 *)c->scat.p;
     P.n_el = A.n_el;
     P.n_s = A.n_s;
     P.pitch = A.pitch;
@@ -338,6 +339,7 @@ ur::TraceP make_trace_params(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_
     P.max_b = max_b;
     P.max_path = max_path;
     P.inv_n = (float)(1.0 / (double)n_rays);
+    P.resolve_batch = c->tune.resolve_batch > 0 ? c->tune.resolve_batch : 16;
     return P;
 }
 
@@ -369,6 +371,7 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     unsigned long long *cnt = (unsigned long long *)c->counters.p;
     P.arr_count = cnt;
     P.stats = cnt + 1;
+    P.next_slot = cnt + 7;
     P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
 
     const int block = c->tune.block > 0 ? c->tune.block : 256;
@@ -751,7 +754,7 @@ ur_status ur_set_tuning(ur_ctx *c, const ur_tuning *t) {
     return guarded(c, [&] {
         if (!t) fail(UR_ERR_INVALID_ARG, "tuning is NULL");
         if (t->cell_xy < 0.f || t->cell_z < 0.f || t->block < 0 || t->block > 256 || (t->block % 32) != 0 ||
-            t->blocks_per_sm < 0 || t->blocks_per_sm > 64)
+            t->blocks_per_sm < 0 || t->blocks_per_sm > 64 || t->resolve_batch < 0 || t->resolve_batch > 32)
             fail(UR_ERR_INVALID_ARG, "tuning values out of range (block must be a multiple of 32, <= 256)");
         c->tune = *t;
     });

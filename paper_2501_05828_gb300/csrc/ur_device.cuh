@@ -135,9 +135,10 @@ struct SceneP {
     float r2;               // capture radius squared
     float3 g_lo, g_inv_h, g_h;
     int3 g_dim;
-    const float4 *refs;     // (x, y, z, bits(index)) per cell reference
+    const float4 *refs;     // (x, y, z, bits(index)) per cell reference; cells (x, y, z) with z fastest
     const uint32_t *cell_start;
     const float *amp;
+    const float4 *scat;     // (x, y, z, amplitude) by scatterer index
 };
 
 struct TraceP {
@@ -156,11 +157,13 @@ struct TraceP {
     uint2 key;
     int max_b;
     float max_path, inv_n;
+    int resolve_batch;              // lanes that must wait before a warp resolves segments
     // outputs
     uint4 *arr;                     // (row, t_hi, t_lo, amp)
     uint2 *arr_dbg;                 // (ray, event), debug only
     unsigned long long *arr_count;
     uint64_t arr_cap;
+    unsigned long long *next_slot;  // work counter of the persistent tracer (zeroed per launch)
     unsigned long long *path_hash;  // [n_tx][n_rays], debug only
     unsigned long long *stats;      // 6 counters, nullable
 };

@@ -1,4 +1,5 @@
-// Uniform grid over the point scatterers.  Each scatterer is referenced by every
+// Uniform grid over the point scatterers, cells numbered with z fastest so that
+// a near-vertical ray walks consecutive cells and consecutive references.  Each scatterer is referenced by every
 // cell its capture box [p - r_m, p + r_m] overlaps (r_m slightly above r_s), so a
 // ray segment only has to visit the cells it passes through.  Built on the
 // device: bounding box, per-cell counts, exclusive scan, fill.
@@ -47,7 +48,7 @@ __global__ void k_grid_count(const GridBuildP G) {
         for (int z = c0.z; z <= c1.z; ++z)
             for (int y = c0.y; y <= c1.y; ++y)
                 for (int x = c0.x; x <= c1.x; ++x)
-                    atomicAdd(&G.cell_count[((uint32_t)z * G.dim.y + y) * G.dim.x + x], 1u);
+                    atomicAdd(&G.cell_count[((uint32_t)x * G.dim.y + y) * G.dim.z + z], 1u);
     }
 }
 
@@ -60,7 +61,7 @@ __global__ void k_grid_fill(const GridBuildP G) {
         for (int z = c0.z; z <= c1.z; ++z)
             for (int y = c0.y; y <= c1.y; ++y)
                 for (int x = c0.x; x <= c1.x; ++x) {
-                    const uint32_t c = ((uint32_t)z * G.dim.y + y) * G.dim.x + x;
+                    const uint32_t c = ((uint32_t)x * G.dim.y + y) * G.dim.z + z;
                     const uint32_t slot = atomicAdd(&G.cell_fill[c], 1u);
                     G.refs[G.cell_start[c] + slot] = make_float4(p.x, p.y, p.z, __uint_as_float((uint32_t)j));
                 }

@@ -163,46 +163,57 @@ struct Counters {
     uint32_t rays, segments, interactions, candidates, connections, arrivals;
 };
 
-// A scatterer within r_s of the segment: choose an element uniformly (Philox
-// keyed by ray, transmit, segment and scatterer), weigh by Eq. 13 and cast the
-// connection ray.
-template <bool DBG>
-__device__ __forceinline__ void scatter_event(const TraceP &P, uint32_t i, uint32_t k, float4 q, float tca, ff t,
-                                              float w, int med, int b, Counters &cn) {
-    const uint32_t j = __float_as_uint(q.w);
-    const uint4 x = philox(make_uint4(i, k, 2u | ((uint32_t)b << 8), j), P.key);
-    const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
-    const float xe = P.x_first + (float)e * P.pitch;
-    const float vx = xe - q.x;
-    const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
-    const float fd = directivity(P, q.z / D);
-    cn.candidates++;
-    if (!(fd > 0.f)) return;
-    cn.connections++;
-    ff tc;
-    float att;
-    const float fac = connection(P.S, make_float3(q.x, q.y, q.z), med, xe, tc, att);
-    if (fac == 0.f) return;
-    const Medium &M = P.S.med[med];
-    const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
-    if (ff_gt(ta, P.t_last)) return;
-    const float amp = w * expf(-M.a * tca) * P.S.amp[j] * (float)P.n_el * fd * fac * expf(-att);
-    emit<DBG>(P, k * (uint32_t)P.n_el + e, ta, amp, i, ((uint32_t)b << 24) | j);
-    cn.arrivals++;
-}
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+constexpr int kQueue = 64;     // scatterer-event ring per warp (power of two, >= 63 entries needed)
+constexpr int kPool = 32;      // ray slots a warp claims per atomic
 
-// Every scatterer whose closest approach to the open segment o + t d,
-// 0 < t < seg, is closer than r_s.  Uniform grid walked with a 3D DDA; each
-// cell tests only closest-approach parameters inside its own [t_enter, t_exit)
-// range, so a scatterer referenced by several cells is found exactly once.
-template <bool DBG>
-__device__ void segment_scatterers(const TraceP &P, uint32_t i, uint32_t k, float3 o, float3 d, float seg, ff t,
-                                   float w, int med, int b, Counters &cn) {
+enum { kInSeg = 0, kSegDone = 1, kNeedRay = 2, kFinished = 3 };
+
+// Scatterer events waiting for their connection ray, one ring per warp (SoA).
+struct WarpQueue {
+    uint32_t ray[kQueue], kmb[kQueue], j[kQueue];
+    float tca[kQueue], t_hi[kQueue], t_lo[kQueue], w[kQueue];
+};
+
+// Per-lane state: the primary ray, its current segment and the grid walk over it.
+struct Lane {
+    float3 o, d;
+    ff t;
+    float w, L;
+    int med, b, prev;
+    uint32_t i, k;
+    uint64_t h;
+    float seg;
+    int hit;
+    bool clipped;
+    int cx, cy, cz, sx, sy, sz;
+    float tmx, tmy, tmz, tdx, tdy, tdz, t_enter, t_end;
+    int state;
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+// Segment from the current position to the nearest boundary (clipped by the
+// path-length budget); set up the grid walk over the part inside the grid box.
+__device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S;
+    float th;
+    R.hit = nearest(S, R.o, R.d, R.prev, true, th);
+    R.seg = th;
+    R.clipped = false;
+    if (R.L + R.seg > P.max_path) {
+        R.seg = P.max_path - R.L;
+        R.clipped = true;
+    }
+    cn.segments++;
+    R.state = kSegDone;
+    if (S.n_scat == 0) return;
+    const float3 o = R.o, d = R.d;
     const float hi_x = S.g_lo.x + (float)S.g_dim.x * S.g_h.x;
     const float hi_y = S.g_lo.y + (float)S.g_dim.y * S.g_h.y;
     const float hi_z = S.g_lo.z + (float)S.g_dim.z * S.g_h.z;
-    float t0 = 0.f, t1 = seg;
+    float t0 = 0.f, t1 = R.seg;
     const float ix = 1.f / d.x, iy = 1.f / d.y, iz = 1.f / d.z;
     if (d.x != 0.f) {
         const float ta = (S.g_lo.x - o.x) * ix, tb = (hi_x - o.x) * ix;
@@ -226,184 +237,315 @@ __device__ void segment_scatterers(const TraceP &P, uint32_t i, uint32_t k, floa
         return;
     }
     if (!(t0 < t1)) return;
-
-    int cx = (int)floorf((o.x + t0 * d.x - S.g_lo.x) * S.g_inv_h.x);
-    int cy = (int)floorf((o.y + t0 * d.y - S.g_lo.y) * S.g_inv_h.y);
-    int cz = (int)floorf((o.z + t0 * d.z - S.g_lo.z) * S.g_inv_h.z);
-    cx = min(max(cx, 0), S.g_dim.x - 1);
-    cy = min(max(cy, 0), S.g_dim.y - 1);
-    cz = min(max(cz, 0), S.g_dim.z - 1);
-    const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
-    const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
-    const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
-    const float tdx = sx ? S.g_h.x * fabsf(ix) : INFINITY;
-    const float tdy = sy ? S.g_h.y * fabsf(iy) : INFINITY;
-    const float tdz = sz ? S.g_h.z * fabsf(iz) : INFINITY;
-    float tmx = sx ? (S.g_lo.x + (float)(cx + (sx > 0)) * S.g_h.x - o.x) * ix : INFINITY;
-    float tmy = sy ? (S.g_lo.y + (float)(cy + (sy > 0)) * S.g_h.y - o.y) * iy : INFINITY;
-    float tmz = sz ? (S.g_lo.z + (float)(cz + (sz > 0)) * S.g_h.z - o.z) * iz : INFINITY;
-
-    float t_enter = -INFINITY;
-    const int guard_max = S.g_dim.x + S.g_dim.y + S.g_dim.z + 3;
-    for (int guard = 0; guard < guard_max; ++guard) {
-        const int axis = (tmx <= tmy && tmx <= tmz) ? 0 : (tmy <= tmz ? 1 : 2);
-        const float t_exit = axis == 0 ? tmx : (axis == 1 ? tmy : tmz);
-        bool last = !(t_exit < t1);
-        if (!last) {
-            const int nc = axis == 0 ? cx + sx : (axis == 1 ? cy + sy : cz + sz);
-            const int dm = axis == 0 ? S.g_dim.x : (axis == 1 ? S.g_dim.y : S.g_dim.z);
-            last = nc < 0 || nc >= dm;
-        }
-        const float t_acc = last ? INFINITY : t_exit;
-        const uint32_t cell = ((uint32_t)cz * (uint32_t)S.g_dim.y + (uint32_t)cy) * (uint32_t)S.g_dim.x + (uint32_t)cx;
-        const uint32_t r0 = S.cell_start[cell], r1 = S.cell_start[cell + 1];
-        for (uint32_t r = r0; r < r1; ++r) {
-            const float4 q = S.refs[r];
-            const float3 v = make_float3(q.x - o.x, q.y - o.y, q.z - o.z);
-            const float tca = dot3(v, d);
-            if (!(tca > 0.f && tca < seg)) continue;
-            if (tca < t_enter || !(tca < t_acc)) continue;
-            const float3 pe = v - tca * d;
-            if (!(dot3(pe, pe) < S.r2)) continue;
-            scatter_event<DBG>(P, i, k, q, tca, t, w, med, b, cn);
-        }
-        if (last) break;
-        t_enter = t_exit;
-        if (axis == 0) {
-            cx += sx;
-            tmx += tdx;
-        } else if (axis == 1) {
-            cy += sy;
-            tmy += tdy;
-        } else {
-            cz += sz;
-            tmz += tdz;
-        }
-    }
+    R.cx = min(max((int)floorf((o.x + t0 * d.x - S.g_lo.x) * S.g_inv_h.x), 0), S.g_dim.x - 1);
+    R.cy = min(max((int)floorf((o.y + t0 * d.y - S.g_lo.y) * S.g_inv_h.y), 0), S.g_dim.y - 1);
+    R.cz = min(max((int)floorf((o.z + t0 * d.z - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
+    R.sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
+    R.sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
+    R.sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
+    R.tdx = R.sx ? S.g_h.x * fabsf(ix) : INFINITY;
+    R.tdy = R.sy ? S.g_h.y * fabsf(iy) : INFINITY;
+    R.tdz = R.sz ? S.g_h.z * fabsf(iz) : INFINITY;
+    R.tmx = R.sx ? (S.g_lo.x + (float)(R.cx + (R.sx > 0)) * S.g_h.x - o.x) * ix : INFINITY;
+    R.tmy = R.sy ? (S.g_lo.y + (float)(R.cy + (R.sy > 0)) * S.g_h.y - o.y) * iy : INFINITY;
+    R.tmz = R.sz ? (S.g_lo.z + (float)(R.cz + (R.sz > 0)) * S.g_h.z - o.z) * iz : INFINITY;
+    R.t_enter = -INFINITY;
+    R.t_end = t1;
+    R.state = kInSeg;
 }
 
-// One primary ray: emission (Eq. 6) and traversal until termination.
 template <bool DBG>
-__device__ void trace_ray(const TraceP &P, uint32_t i, uint32_t k, uint32_t e, Counters &cn) {
-    const SceneP &S = P.S;
+__device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Counters &cn) {
+    if (DBG) P.path_hash[(uint64_t)R.k * P.n_rays + R.i] = fnv_step(R.h, 0x20000u | (uint32_t)reason);
+    cn.rays++;
+    R.state = kNeedRay;
+}
+
+// Emission (Eq. 6) of ray i of transmit k from element e.
+__device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t i, uint32_t k, uint32_t e,
+                                          Counters &cn) {
     const uint4 x = philox(make_uint4(i, k, 0u, 0u), P.key);
     const float2 sc = P.txdir[k];
     const float xe = P.x_first + (float)e * P.pitch;
-    float3 o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
-    float3 d = make_float3(sc.x, 0.f, sc.y);
-    ff t = P.delay[k * (uint32_t)P.n_el + e];
-    float w = sc.y * P.inv_n;
-    int med = S.med_array, b = 0, prev = -1, reason = kEndPath;
-    float L = 0.f;
-    uint64_t h = kFnvOffset;
-    for (int guard = 0; guard < kMaxSeg; ++guard) {
-        float th;
-        const int hit = nearest(S, o, d, prev, true, th);
-        float seg = th;
-        bool clipped = false;
-        if (L + seg > P.max_path) {
-            seg = P.max_path - L;
-            clipped = true;
-        }
-        cn.segments++;
-        if (S.n_scat > 0) segment_scatterers<DBG>(P, i, k, o, d, seg, t, w, med, b, cn);
-        const Medium &M = S.med[med];
-        t = ff_add(t, ff_mul_f(seg, M.slow));
-        w *= expf(-M.a * seg);
-        L += seg;
-        o = o + seg * d;
-        if (clipped) {
-            reason = kEndPath;
-            break;
-        }
-        if (hit == S.n_bnd) {  // array plane: only paths returning to the aperture are kept
-            o.z = 0.f;
-            const float xl = P.x_first - 0.5f * P.pitch;
-            if (fabsf(o.y) <= 0.5f * P.H && o.x >= xl && o.x < xl + (float)P.n_el * P.pitch) {
-                int el = (int)floorf((o.x - xl) / P.pitch);
-                if (el > P.n_el - 1) el = P.n_el - 1;
-                const float fd = directivity(P, -d.z);
-                if (fd > 0.f && !ff_gt(t, P.t_last)) {
-                    emit<DBG>(P, k * (uint32_t)P.n_el + (uint32_t)el, t, w * fd, i, 0x80000000u | ((uint32_t)b << 24));
-                    cn.arrivals++;
-                }
-                reason = kEndAperture;
-            } else {
-                reason = kEndArrayMiss;
-            }
-            break;
-        }
-        if (hit == S.n_bnd + 1) {
-            reason = kEndBottom;
-            break;
-        }
-        const Bnd &B = S.bnd[hit];
-        if (B.kind == kPlaneZ) o.z = B.p[0];
-        if (ff_gt(t, P.t_last)) {
-            reason = kEndTime;
-            break;
-        }
-        if (b >= P.max_b) {
-            reason = kEndMaxB;
-            break;
-        }
-        // boundary interaction (Eqs. 7-11), Monte Carlo choice reflect if y < r^2
-        const float3 n_out = outward(B, o);
-        const float dn = dot3(d, n_out);
-        const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
-        const float3 n = dn > 0.f ? make_float3(-n_out.x, -n_out.y, -n_out.z) : n_out;
-        const float cos_i = -dot3(n, d);
-        const float3 dr = unit3(d + (2.f * cos_i) * n);
-        const Medium &M2 = S.med[m2];
-        float r, cos_t;
-        uint32_t branch;
-        if (!fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t)) {
-            branch = 2;
-            d = dr;
-        } else {
-            const float R = r * r;
-            const uint4 y = philox(make_uint4(i, k, 1u | ((uint32_t)b << 8), 0u), P.key);
-            if (u24(y.x) < R) {
-                branch = 0;
-                w *= r / R;
-                d = dr;
-            } else {
-                branch = 1;
-                const float eta = M2.c / M.c;
-                w *= 1.f / sqrtf(1.f - R);
-                d = unit3(eta * d + (eta * cos_i - cos_t) * n);
-                med = m2;
-            }
-        }
-        cn.interactions++;
-        if (DBG) h = fnv_step(h, 0x10000u | ((uint32_t)hit << 4) | branch);
-        b += 1;
-        prev = hit;
-    }
-    if (DBG) P.path_hash[(uint64_t)k * P.n_rays + i] = fnv_step(h, 0x20000u | (uint32_t)reason);
-    cn.rays++;
+    R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
+    R.d = make_float3(sc.x, 0.f, sc.y);
+    R.t = P.delay[k * (uint32_t)P.n_el + e];
+    R.w = sc.y * P.inv_n;
+    R.med = P.S.med_array;
+    R.b = 0;
+    R.prev = -1;
+    R.L = 0.f;
+    R.i = i;
+    R.k = k;
+    R.h = kFnvOffset;
+    start_segment(P, R, cn);
 }
 
-// Slots are element-major so that a warp traces neighbouring rays of one
-// element (coherent scatterer-grid cells); slot -> ray i = m * n_el + e.
+// End of a segment: time of flight and attenuation along it, then the array
+// plane (aperture return), the absorbing bottom, the time window, the bounce
+// budget, or a boundary interaction (Eqs. 7-11) and the next segment.
 template <bool DBG>
-__global__ void __launch_bounds__(256) k_trace(const __grid_constant__ TraceP P, uint64_t n_slots) {
-    Counters cn = {0, 0, 0, 0, 0, 0};
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_slots; g += stride) {
-        const uint32_t m = (uint32_t)(g % P.rays_per_el);
-        const uint64_t q = g / P.rays_per_el;
-        const uint32_t e = (uint32_t)(q % (uint64_t)P.n_el);
-        const uint32_t k = (uint32_t)(q / (uint64_t)P.n_el);
-        const uint32_t i = m * (uint32_t)P.n_el + e;
-        if (i < P.n_rays) trace_ray<DBG>(P, i, k, e, cn);
+__device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
+    const SceneP &S = P.S;
+    const Medium &M = S.med[R.med];
+    R.t = ff_add(R.t, ff_mul_f(R.seg, M.slow));
+    R.w *= expf(-M.a * R.seg);
+    R.L += R.seg;
+    R.o = R.o + R.seg * R.d;
+    if (R.clipped) {
+        end_ray<DBG>(P, R, kEndPath, cn);
+        return;
     }
+    if (R.hit == S.n_bnd) {  // array plane: only paths returning to the aperture are kept
+        R.o.z = 0.f;
+        const float xl = P.x_first - 0.5f * P.pitch;
+        int reason = kEndArrayMiss;
+        if (fabsf(R.o.y) <= 0.5f * P.H && R.o.x >= xl && R.o.x < xl + (float)P.n_el * P.pitch) {
+            int el = (int)floorf((R.o.x - xl) / P.pitch);
+            if (el > P.n_el - 1) el = P.n_el - 1;
+            const float fd = directivity(P, -R.d.z);
+            if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
+                emit<DBG>(P, R.k * (uint32_t)P.n_el + (uint32_t)el, R.t, R.w * fd, R.i,
+                          0x80000000u | ((uint32_t)R.b << 24));
+                cn.arrivals++;
+            }
+            reason = kEndAperture;
+        }
+        end_ray<DBG>(P, R, reason, cn);
+        return;
+    }
+    if (R.hit == S.n_bnd + 1) {
+        end_ray<DBG>(P, R, kEndBottom, cn);
+        return;
+    }
+    const Bnd &B = S.bnd[R.hit];
+    if (B.kind == kPlaneZ) R.o.z = B.p[0];
+    if (ff_gt(R.t, P.t_last)) {
+        end_ray<DBG>(P, R, kEndTime, cn);
+        return;
+    }
+    if (R.b >= P.max_b) {
+        end_ray<DBG>(P, R, kEndMaxB, cn);
+        return;
+    }
+    const float3 n_out = outward(B, R.o);
+    const float dn = dot3(R.d, n_out);
+    const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
+    const float3 n = dn > 0.f ? make_float3(-n_out.x, -n_out.y, -n_out.z) : n_out;
+    const float cos_i = -dot3(n, R.d);
+    const float3 dr = unit3(R.d + (2.f * cos_i) * n);
+    const Medium &M2 = S.med[m2];
+    float r, cos_t;
+    uint32_t branch;
+    if (!fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t)) {
+        branch = 2;
+        R.d = dr;
+    } else {
+        const float Rr = r * r;
+        const uint4 y = philox(make_uint4(R.i, R.k, 1u | ((uint32_t)R.b << 8), 0u), P.key);
+        if (u24(y.x) < Rr) {
+            branch = 0;
+            R.w *= r / Rr;
+            R.d = dr;
+        } else {
+            branch = 1;
+            const float eta = M2.c / M.c;
+            R.w *= 1.f / sqrtf(1.f - Rr);
+            R.d = unit3(eta * R.d + (eta * cos_i - cos_t) * n);
+            R.med = m2;
+        }
+    }
+    cn.interactions++;
+    if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | branch);
+    R.b += 1;
+    R.prev = R.hit;
+    start_segment(P, R, cn);
+}
+
+// A queued scatterer event: element drawn uniformly (Philox keyed by ray,
+// transmit, segment and scatterer), receive directivity (Eq. 13), connection ray.
+template <bool DBG>
+__device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &Q, int slot, Counters &cn) {
+    const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
+    const float tca = Q.tca[slot], w = Q.w[slot];
+    const ff t = {Q.t_hi[slot], Q.t_lo[slot]};
+    const uint32_t k = kmb >> 16;
+    const int med = (int)((kmb >> 8) & 0xffu), b = (int)(kmb & 0xffu);
+    const float4 q = P.S.scat[j];
+    const uint4 x = philox(make_uint4(ray, k, 2u | ((uint32_t)b << 8), j), P.key);
+    const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
+    const float xe = P.x_first + (float)e * P.pitch;
+    const float vx = xe - q.x;
+    const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
+    const float fd = directivity(P, q.z / D);
+    if (!(fd > 0.f)) return;
+    cn.connections++;
+    ff tc;
+    float att;
+    const float fac = connection(P.S, make_float3(q.x, q.y, q.z), med, xe, tc, att);
+    if (fac == 0.f) return;
+    const Medium &M = P.S.med[med];
+    const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
+    if (ff_gt(ta, P.t_last)) return;
+    const float amp = w * expf(-M.a * tca) * q.w * (float)P.n_el * fd * fac * expf(-att);
+    emit<DBG>(P, k * (uint32_t)P.n_el + e, ta, amp, ray, ((uint32_t)b << 24) | j);
+    cn.arrivals++;
+}
+
+// Persistent tracer.  Each iteration of the warp's loop (1) finishes segments
+// and claims new rays for idle lanes, (2) advances every active lane by one
+// grid cell, testing the cell's scatterer references in a warp-uniform loop,
+// (3) hands scatterer events to a per-warp queue that is drained 32 events at
+// a time with all lanes busy.  Ray slots are element-major: a freshly claimed
+// batch of lanes traces neighbouring rays of one element; slot -> ray
+// i = m * n_el + e.
+template <bool DBG>
+__global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P, uint64_t n_slots) {
+    __shared__ WarpQueue s_q[kWarps];
+    WarpQueue &Q = s_q[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const SceneP &S = P.S;
+    Counters cn = {0, 0, 0, 0, 0, 0};
+    Lane R;
+    R.state = kNeedRay;
+    uint64_t pool_next = 0;
+    uint32_t pool_cnt = 0;
+    bool pool_dry = false;
+    int qhead = 0, qn = 0;   // warp-uniform ring bookkeeping
+
+    for (;;) {
+        // (1) resolve finished segments and idle lanes, once enough lanes wait
+        const unsigned waiting = __ballot_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay);
+        const bool resolve = __popc(waiting) >= P.resolve_batch || __ballot_sync(0xffffffffu, R.state == kInSeg) == 0u;
+        for (int guard = 0; resolve && guard < 256; ++guard) {
+            if (R.state == kSegDone) finish_segment<DBG>(P, R, cn);
+            unsigned need = __ballot_sync(0xffffffffu, R.state == kNeedRay);
+            uint64_t my_slot = ~0ull;
+            while (need) {
+                if (pool_cnt == 0) {
+                    if (!pool_dry) {
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(P.next_slot, (unsigned long long)kPool);
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        pool_next = base;
+                        pool_cnt = base >= n_slots ? 0u : (uint32_t)((n_slots - base) < (uint64_t)kPool ? (n_slots - base) : (uint64_t)kPool);
+                        pool_dry = pool_cnt == 0;
+                    }
+                    if (pool_dry) {
+                        if (R.state == kNeedRay) R.state = kFinished;
+                        break;
+                    }
+                }
+                const uint32_t take = min((uint32_t)__popc(need), pool_cnt);
+                const uint32_t rank = (uint32_t)__popc(need & lanemask_lt());
+                if (((need >> lane) & 1u) && rank < take) my_slot = pool_next + rank;
+                pool_next += take;
+                pool_cnt -= take;
+                need = __ballot_sync(0xffffffffu, R.state == kNeedRay && my_slot == ~0ull);
+            }
+            if (my_slot != ~0ull) {
+                const uint32_t m = (uint32_t)(my_slot % P.rays_per_el);
+                const uint64_t qq = my_slot / P.rays_per_el;
+                const uint32_t e = (uint32_t)(qq % (uint64_t)P.n_el);
+                const uint32_t k = (uint32_t)(qq / (uint64_t)P.n_el);
+                const uint32_t i = m * (uint32_t)P.n_el + e;
+                if (i < P.n_rays) start_ray(P, R, i, k, e, cn);
+            }
+            if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
+        }
+        if (__all_sync(0xffffffffu, R.state == kFinished)) break;
+
+        // (2) one grid cell per active lane
+        const bool active = R.state == kInSeg;
+        uint32_t r0 = 0, cnt = 0;
+        int axis = 0;
+        float t_exit = 0.f, t_acc = 0.f;
+        bool last = false;
+        if (active) {
+            axis = (R.tmx <= R.tmy && R.tmx <= R.tmz) ? 0 : (R.tmy <= R.tmz ? 1 : 2);
+            t_exit = axis == 0 ? R.tmx : (axis == 1 ? R.tmy : R.tmz);
+            last = !(t_exit < R.t_end);
+            if (!last) {
+                const int nc = axis == 0 ? R.cx + R.sx : (axis == 1 ? R.cy + R.sy : R.cz + R.sz);
+                const int dm = axis == 0 ? S.g_dim.x : (axis == 1 ? S.g_dim.y : S.g_dim.z);
+                last = nc < 0 || nc >= dm;
+            }
+            t_acc = last ? INFINITY : t_exit;
+            const uint32_t cell =
+                ((uint32_t)R.cx * (uint32_t)S.g_dim.y + (uint32_t)R.cy) * (uint32_t)S.g_dim.z + (uint32_t)R.cz;
+            r0 = S.cell_start[cell];
+            cnt = S.cell_start[cell + 1] - r0;
+        }
+        const uint32_t maxc = __reduce_max_sync(0xffffffffu, cnt);
+        const uint32_t kmb = (R.k << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b;
+        float4 q_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cnt > 0) q_next = S.refs[r0];
+        for (uint32_t r = 0; r < maxc; ++r) {
+            bool cand = false;
+            float tca = 0.f;
+            uint32_t j = 0;
+            const float4 q = q_next;                 // reference r, loaded one step ahead
+            if (r + 1 < cnt) q_next = S.refs[r0 + r + 1];
+            if (r < cnt) {
+                const float3 v = make_float3(q.x - R.o.x, q.y - R.o.y, q.z - R.o.z);
+                tca = dot3(v, R.d);
+                if (tca > 0.f && tca < R.seg && tca >= R.t_enter && tca < t_acc) {
+                    const float3 pe = v - tca * R.d;
+                    cand = dot3(pe, pe) < S.r2;
+                    j = __float_as_uint(q.w);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, cand);
+            if (m) {
+                if (cand) {
+                    const int slot = (qhead + qn + __popc(m & lanemask_lt())) & (kQueue - 1);
+                    Q.ray[slot] = R.i;
+                    Q.kmb[slot] = kmb;
+                    Q.j[slot] = j;
+                    Q.tca[slot] = tca;
+                    Q.t_hi[slot] = R.t.hi;
+                    Q.t_lo[slot] = R.t.lo;
+                    Q.w[slot] = R.w;
+                    cn.candidates++;
+                }
+                qn += __popc(m);
+                if (qn >= 32) {
+                    __syncwarp();
+                    process_event<DBG>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+                    __syncwarp();
+                    qhead = (qhead + 32) & (kQueue - 1);
+                    qn -= 32;
+                }
+            }
+        }
+        if (active) {
+            if (last) {
+                R.state = kSegDone;
+            } else {
+                R.t_enter = t_exit;
+                if (axis == 0) {
+                    R.cx += R.sx;
+                    R.tmx += R.tdx;
+                } else if (axis == 1) {
+                    R.cy += R.sy;
+                    R.tmy += R.tdy;
+                } else {
+                    R.cz += R.sz;
+                    R.tmz += R.tdz;
+                }
+            }
+        }
+    }
+    // (3) drain the queue
+    __syncwarp();
+    if (lane < qn) process_event<DBG>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+
     if (P.stats) {
         const uint32_t v[6] = {cn.rays, cn.segments, cn.interactions, cn.candidates, cn.connections, cn.arrivals};
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const uint32_t s = __reduce_add_sync(0xffffffffu, v[c]);
-            if ((threadIdx.x & 31) == 0 && s) atomicAdd(&P.stats[c], (unsigned long long)s);
+            if (lane == 0 && s) atomicAdd(&P.stats[c], (unsigned long long)s);
         }
     }
 }
