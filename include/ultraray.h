@@ -114,7 +114,8 @@ typedef struct {
 } ur_debug;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * (NULL: the context creates and owns a non-blocking stream).
+ * (cudaStreamLegacy for the legacy default stream; NULL: the context creates
+ * and owns a non-blocking stream).  Graph capture needs a non-default stream.
  * Errors: UR_ERR_INVALID_ARG (out == NULL, bad device), UR_ERR_CUDA. */
 ur_status ur_create(ur_ctx **out, int device, void *cuda_stream);
 
@@ -125,14 +126,22 @@ ur_status ur_destroy(ur_ctx *ctx);
 const char *ur_last_error(const ur_ctx *ctx);
 
 /* Scene of Sec. 2.3 "Ray Traversal": media table (n_med <= 16), analytic
- * boundaries (n_bnd <= 32, media indices in [0, n_med)), the medium touching
+ * boundaries (n_bnd <= 16, media indices in [0, n_med)), the medium touching
  * the array plane, an absorbing plane z = z_max, and n_scat point scatterers
  * scat_xyza[n_scat][4] = (x, y, z, amplitude) with capture radius r_s > 0.
- * Copies everything and builds the scatterer grid on the device.
+ * Copies everything and builds the scatterer grid on the device.  This is
+ * scene slot 0, the one ur_trace uses.
  * Errors: UR_ERR_INVALID_ARG, UR_ERR_OOM, UR_ERR_CUDA. */
 ur_status ur_scene_upload(ur_ctx *ctx, const ur_medium *media, int n_med,
                           const ur_boundary *bnd, int n_bnd, int med_array, float z_max,
                           const float *scat_xyza, int n_scat, float r_s);
+
+/* Same as ur_scene_upload for scene slot `slot` in [0, 16): a context holds up
+ * to 16 scenes that a batch traces together (simultaneous acquisition events,
+ * Sec. 2.3 "Ray Emission"). */
+ur_status ur_scene_upload_slot(ur_ctx *ctx, int slot, const ur_medium *media, int n_med,
+                               const ur_boundary *bnd, int n_bnd, int med_array, float z_max,
+                               const float *scat_xyza, int n_scat, float r_s);
 
 /* Transducer description (Sec. 2.3 "Ray Emission").  1 <= n_el <= 4096,
  * 16 <= n_s <= 8192, positive geometry and frequencies, 0 <= alpha_m <= alpha_c < 90.
@@ -173,6 +182,55 @@ ur_status ur_beamform(ur_ctx *ctx, const float *rf, const float *quad,
                       const float *x_px, int nx, const float *z_px, int nz, float dyn_range_db,
                       float *iq, float *env, float *db);
 
+/* ---- batches: many (scene, transmit) items in one persistent launch ----
+ * Rays of different transmits and scenes are independent (Sec. 2.3, "Ray
+ * Emission": acquisition events can be simulated at the same time), so a
+ * batch traces all its items in one launch of the persistent tracer, sorts and
+ * deposits all arrivals in one pass, and beamforms one compounded image per
+ * scene.  Item q: scene slot, index into the plane-wave table, n_rays rays,
+ * and `stream`, the Philox counter word that keys its random numbers (ur_trace
+ * uses stream = transmit index; distinct items should use distinct
+ * (scene, stream) pairs). */
+typedef struct {
+    int32_t scene;
+    int32_t tx;
+    uint32_t stream;
+    uint32_t reserved;
+    uint64_t n_rays;
+} ur_batch_item;
+
+/* Validate the items, allocate every buffer a run needs (arrival queue of
+ * arrival_capacity entries, 0 = estimate from earlier traces), upload the item
+ * table and the image grid (x_px[nx], z_px[nz], host or device).  Must run
+ * outside stream capture; it synchronises the stream.  Images are produced for
+ * the scenes present, in increasing slot order.
+ * Errors: UR_ERR_STATE (missing scene/array/transmits), UR_ERR_INVALID_ARG, UR_ERR_OOM. */
+ur_status ur_batch_plan(ur_ctx *ctx, const ur_batch_item *items, int n_items, uint64_t arrival_capacity,
+                        const float *x_px, int nx, const float *z_px, int nz);
+
+/* Trace and deposit the planned batch into rf, quad [n_items][n_el][n_s]
+ * (device memory).  Asynchronous, allocates nothing and may be captured into
+ * a graph (ur_graph_begin).  If the queue overflows, ur_batch_status reports it. */
+ur_status ur_batch_trace(ur_ctx *ctx, uint64_t seed, int max_bounces, float max_path_m, float *rf, float *quad);
+
+/* Synchronise and report the last trace: arrivals produced and counters.
+ * UR_ERR_OVERFLOW if the planned capacity was too small (re-plan larger). */
+ur_status ur_batch_status(ur_ctx *ctx, uint64_t *n_arrivals, ur_stats *st);
+
+/* Delay-and-sum of the planned batch: image i compounds all items of the i-th
+ * scene present (outputs [n_images][nz][nx], device memory, each nullable).
+ * Asynchronous and capturable. */
+ur_status ur_batch_beamform(ur_ctx *ctx, const float *rf, const float *quad, float dyn_range_db,
+                            float *iq, float *env, float *db);
+
+/* CUDA-graph capture of the context's stream: calls between ur_graph_begin and
+ * ur_graph_end (ur_batch_trace, ur_batch_beamform) are recorded, not run;
+ * ur_graph_launch replays them.  Calls that synchronise or allocate fail with
+ * UR_ERR_STATE while capturing. */
+ur_status ur_graph_begin(ur_ctx *ctx);
+ur_status ur_graph_end(ur_ctx *ctx);
+ur_status ur_graph_launch(ur_ctx *ctx);
+
 /* Scatterer-grid and launch tuning (0 fields keep the defaults).  Cell sizes in
  * metres, applied at the next ur_scene_upload; block (multiple of 32, <= 256),
  * blocks_per_sm and resolve_batch (1..32: the tracer finishes segments and
@@ -182,6 +240,13 @@ typedef struct {
     int32_t block, blocks_per_sm, resolve_batch;
 } ur_tuning;
 ur_status ur_set_tuning(ur_ctx *ctx, const ur_tuning *t);
+
+/* Autotuner: coordinate descent over grid cell sizes, resolve batch and CTAs
+ * per SM, timing n_rays rays of transmit 0 of scene slot `scene` with CUDA
+ * events; keeps the fastest setting (rebuilding every scene's grid) and
+ * returns it in *best (nullable).  Synchronous. */
+ur_status ur_autotune(ur_ctx *ctx, int scene, uint64_t n_rays, uint64_t seed, int max_bounces,
+                      float max_path_m, ur_tuning *best);
 
 /* Device time per pipeline phase, measured with CUDA events recorded on the
  * context's stream around each phase's kernels while profiling is on.  While

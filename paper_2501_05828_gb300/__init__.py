@@ -26,7 +26,8 @@ STATUS = {0: "UR_OK", 1: "UR_ERR_INVALID_ARG", 2: "UR_ERR_CUDA", 3: "UR_ERR_OOM"
 # every entry point include/ultraray.h declares
 EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_set_array", "ur_set_plane_waves",
            "ur_trace", "ur_trace_debug", "ur_beamform", "ur_set_tuning", "ur_set_profiling", "ur_get_profile",
-           "ur_sync", "ur_beamform_noalloc")
+           "ur_sync", "ur_beamform_noalloc", "ur_scene_upload_slot", "ur_batch_plan", "ur_batch_trace",
+           "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log")
 
 
@@ -65,6 +66,11 @@ class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("launches", C.c_uint64 * 8), ("calls", C.c_uint64 * 8)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("tx", C.c_int32), ("stream", C.c_uint32), ("reserved", C.c_uint32),
+                ("n_rays", C.c_uint64)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("cell_xy", C.c_float), ("cell_z", C.c_float), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("resolve_batch", C.c_int32)]
@@ -97,6 +103,16 @@ def lib():
             L.ur_sync.argtypes = [vp]
             L.ur_set_profiling.argtypes = [vp, i32]
             L.ur_beamform_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, vp, vp]
+            L.ur_scene_upload_slot.argtypes = [vp, i32, C.POINTER(Medium), i32, C.POINTER(Boundary), i32, i32, f32,
+                                               vp, i32, f32]
+            L.ur_batch_plan.argtypes = [vp, C.POINTER(BatchItem), i32, u64, vp, i32, vp, i32]
+            L.ur_batch_trace.argtypes = [vp, u64, i32, f32, vp, vp]
+            L.ur_batch_status.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(Stats)]
+            L.ur_batch_beamform.argtypes = [vp, vp, vp, f32, vp, vp, vp]
+            L.ur_graph_begin.argtypes = [vp]
+            L.ur_graph_end.argtypes = [vp]
+            L.ur_graph_launch.argtypes = [vp]
+            L.ur_autotune.argtypes = [vp, i32, u64, u64, i32, f32, C.POINTER(Tuning)]
             L.ur_get_profile.argtypes = [vp, C.POINTER(Profile)]
             for name in EXPORTS:
                 if name != "ur_last_error":
@@ -128,7 +144,10 @@ class Simulator:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         self._ctx = C.c_void_p()
-        self._call(lib().ur_create(C.byref(self._ctx), int(device), C.c_void_p(stream.cuda_stream)), ctx=False)
+        # torch's default stream has handle 0: hand the library cudaStreamLegacy (1) so that its
+        # work stays ordered with torch's instead of going to a private stream
+        handle = stream.cuda_stream or 1
+        self._call(lib().ur_create(C.byref(self._ctx), int(device), C.c_void_p(handle)), ctx=False)
         self.n_tx = 0
         self.array = None
 
@@ -149,7 +168,7 @@ class Simulator:
             pass
 
     # -- set-up -------------------------------------------------------------
-    def upload_scene(self, media, boundaries, med_array, z_max, scatterers, r_s):
+    def upload_scene(self, media, boundaries, med_array, z_max, scatterers, r_s, slot=0):
         med = np.ascontiguousarray(media, np.float32).reshape(-1, 4)
         M = (Medium * len(med))(*[Medium(*map(float, m)) for m in med])
         B = (Boundary * max(1, len(boundaries)))()
@@ -160,8 +179,13 @@ class Simulator:
         else:
             sc = np.ascontiguousarray(scatterers, np.float32).reshape(-1, 4)
             n = sc.shape[0]
-        self._call(lib().ur_scene_upload(self._ctx, M, len(med), B, len(boundaries), int(med_array), float(z_max),
-                                         _ptr(sc) if n else None, n, float(r_s)))
+        if slot == 0:
+            self._call(lib().ur_scene_upload(self._ctx, M, len(med), B, len(boundaries), int(med_array), float(z_max),
+                                             _ptr(sc) if n else None, n, float(r_s)))
+        else:
+            self._call(lib().ur_scene_upload_slot(self._ctx, int(slot), M, len(med), B, len(boundaries),
+                                                  int(med_array), float(z_max), _ptr(sc) if n else None, n,
+                                                  float(r_s)))
 
     def set_array(self, arr):
         self.array = dict(arr)
@@ -178,10 +202,10 @@ class Simulator:
         t = Tuning(cell_xy, cell_z, block, blocks_per_sm, resolve_batch)
         self._call(lib().ur_set_tuning(self._ctx, C.byref(t)))
 
-    def load(self, workload):
+    def load(self, workload, slot=0):
         """Scene, array and transmits of a phantoms.* workload dictionary."""
         s = workload["scene"]
-        self.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], s["scatterers"], s["r_s"])
+        self.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], s["scatterers"], s["r_s"], slot)
         self.set_array(workload["array"])
         self.set_plane_waves(workload["angles"])
 
@@ -249,6 +273,67 @@ class Simulator:
         if code != 0:
             raise URError(code, "ur_beamform_noalloc rejected the call")
         return iq, env, db
+
+    # -- batches, graphs, autotuning ---------------------------------------
+    def batch_plan(self, items, x_px, z_px, capacity=0):
+        """items: iterable of (scene, tx, n_rays[, stream]); stream defaults to tx."""
+        its = list(items)
+        arr = (BatchItem * len(its))()
+        for q, it in enumerate(its):
+            scene, tx, n = it[0], it[1], it[2]
+            stream = it[3] if len(it) > 3 else tx
+            arr[q] = BatchItem(int(scene), int(tx), int(stream), 0, int(n))
+        xp = x_px if hasattr(x_px, "data_ptr") else np.ascontiguousarray(x_px, np.float32)
+        zp = z_px if hasattr(z_px, "data_ptr") else np.ascontiguousarray(z_px, np.float32)
+        self._call(lib().ur_batch_plan(self._ctx, arr, len(its), int(capacity), _ptr(xp), int(xp.shape[0]), _ptr(zp),
+                                       int(zp.shape[0])))
+        self.batch_items = its
+        self.batch_images = sorted({int(it[0]) for it in its})
+        self.batch_grid = (int(zp.shape[0]), int(xp.shape[0]))
+
+    def batch_trace(self, seed, max_bounces, max_path=0.2, rf=None, quad=None):
+        torch = self._torch
+        shape = (len(self.batch_items), int(self.array["n_el"]), int(self.array["n_s"]))
+        rf = torch.empty(shape, dtype=torch.float32, device=self.device) if rf is None else rf
+        quad = torch.empty(shape, dtype=torch.float32, device=self.device) if quad is None else quad
+        self._call(lib().ur_batch_trace(self._ctx, int(seed), int(max_bounces), float(max_path), _ptr(rf), _ptr(quad)))
+        return rf, quad
+
+    def batch_status(self):
+        n = C.c_uint64()
+        st = Stats()
+        self._call(lib().ur_batch_status(self._ctx, C.byref(n), C.byref(st)))
+        return int(n.value), {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+
+    def batch_beamform(self, rf, quad, dyn_range_db=60.0, iq=None, env=None, db=True):
+        torch = self._torch
+        nz, nx = self.batch_grid
+        shape = (len(self.batch_images), nz, nx)
+
+        def out(spec, sh):
+            if spec is True:
+                return torch.empty(sh, dtype=torch.float32, device=self.device)
+            return None if spec is None or spec is False else spec
+
+        o_iq, o_env, o_db = out(iq, shape + (2,)), out(env, shape), out(db, shape)
+        self._call(lib().ur_batch_beamform(self._ctx, _ptr(rf), _ptr(quad), float(dyn_range_db), _ptr(o_iq),
+                                           _ptr(o_env), _ptr(o_db)))
+        return o_iq, o_env, o_db
+
+    def graph_begin(self):
+        self._call(lib().ur_graph_begin(self._ctx))
+
+    def graph_end(self):
+        self._call(lib().ur_graph_end(self._ctx))
+
+    def graph_launch(self):
+        self._call(lib().ur_graph_launch(self._ctx))
+
+    def autotune(self, n_rays, seed=0, max_bounces=8, max_path=0.2, scene=0):
+        t = Tuning()
+        self._call(lib().ur_autotune(self._ctx, int(scene), int(n_rays), int(seed), int(max_bounces), float(max_path),
+                                     C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def set_profiling(self, on=True):
         self._call(lib().ur_set_profiling(self._ctx, 1 if on else 0))

@@ -1,7 +1,9 @@
 // C ABI of the acoustic ray tracer (declared in include/ultraray.h): argument
 // validation, device buffers owned by the context, derived constants (media
-// slowness, transmit delays, directivity cosines) and the launch sequence
-// trace -> bin -> deposit and delay-and-sum -> log compression.
+// slowness, transmit delays, directivity cosines), the launch sequence
+// trace -> sort -> deposit and delay-and-sum -> log compression, batches of
+// (scene, transmit) items in one persistent launch, CUDA-graph capture of a
+// batch, and the tracer autotuner.
 #include "ultraray.h"
 #include "ur_device.cuh"
 
@@ -17,11 +19,6 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
-};
-
-struct Status {
-    ur_status code;
-    std::string msg;
 };
 
 struct Fail {
@@ -53,6 +50,21 @@ bool is_device_ptr(const void *p) {
 }
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr uint32_t kChunk = 4096;   // arrivals per deposit work item
+
+// One uploaded scene: host copies of media and boundaries, device scatterers and grid.
+struct SceneData {
+    bool ok = false;
+    std::vector<ur_medium> media;
+    std::vector<ur_boundary> bnd;
+    int med_array = 0;
+    float z_max = 0.f;
+    int n_scat = 0;
+    float r_s = 1e-4f;
+    float3 g_lo{}, g_h{}, g_inv_h{};
+    int3 g_dim{};
+    DevBuf scat, amp, refs, cell_count, cell_start, cell_fill, scan_tmp, bbox;
+};
 
 }  // namespace
 
@@ -64,32 +76,40 @@ struct ur_ctx {
     std::string err;
     unsigned long long *host_scratch = nullptr;  // pinned, 64 words
 
-    // scene (host copies; derived per trace because attenuation and slowness depend on the array)
-    bool scene_ok = false;
-    std::vector<ur_medium> media;
-    std::vector<ur_boundary> bnd;
-    int med_array = 0;
-    float z_max = 0.f;
-    int n_scat = 0;
-    float r_s = 0.f;
-    float3 g_lo{}, g_h{}, g_inv_h{};
-    int3 g_dim{};
-    DevBuf scat, amp, refs, cell_count, cell_start, cell_fill, scan_tmp, bbox;
+    SceneData scenes[ur::kMaxScenes];
 
-    // array and transmits
+    // array and plane-wave table
     bool array_ok = false;
     ur_array arr{};
     std::vector<float> angles;
     bool tx_dirty = true;
-    DevBuf txdir, delay, tx_sin, tx_cos, tx_m;
+    DevBuf delay, tx_sin, tx_cos, tx_m;
+
+    // work items of the last trace or batch plan
+    std::vector<ur::ItemP> items;
+    std::vector<ur_batch_item> batch_items;
+    uint64_t n_slots = 0;
+    DevBuf items_dev;
 
     // trace buffers
-    DevBuf arrivals, arr_dbg, sorted, counters, row_count, row_fill, row_off, items, n_items;
+    DevBuf arrivals, arr_dbg, sorted, counters, row_count, row_fill, row_off, work, n_work;
     uint64_t arr_cap = 0;
     double arr_per_ray = 0.5;
 
-    // staging for host-side inputs/outputs
-    DevBuf stage_rf, stage_quad, pix, stage_iq, stage_env, stage_db, env_max;
+    // images
+    DevBuf stage_rf, stage_quad, pix, stage_iq, stage_env, stage_db, env_max, img_lists;
+
+    // batch plan
+    bool batch_ok = false;
+    uint64_t batch_cap = 0;
+    int batch_nx = 0, batch_nz = 0, batch_images = 0;
+    std::vector<int> batch_image_scene;
+    DevBuf batch_pix, batch_lists, batch_env, batch_max;
+
+    // stream capture into a CUDA graph
+    bool capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 
     ur_tuning tune{};
 
@@ -99,8 +119,9 @@ struct ur_ctx {
     ur_profile acc{};
     bool pending[UR_N_PHASES] = {};
 
+    bool profiling() const { return prof && !capturing; }
     void phase_begin(int p) {
-        if (!prof) return;
+        if (!profiling()) return;
         if (!ev0[p]) {
             ck(cudaEventCreate(&ev0[p]), "cudaEventCreate");
             ck(cudaEventCreate(&ev1[p]), "cudaEventCreate");
@@ -108,7 +129,7 @@ struct ur_ctx {
         ck(cudaEventRecord(ev0[p], stream), "cudaEventRecord");
     }
     void phase_end(int p, int kernels) {
-        if (!prof) return;
+        if (!profiling()) return;
         ck(cudaEventRecord(ev1[p], stream), "cudaEventRecord");
         pending[p] = true;
         acc.launches[p] += (uint64_t)kernels;
@@ -116,7 +137,7 @@ struct ur_ctx {
     }
     // after a stream synchronisation: fold finished phases into the accumulators
     void phase_collect() {
-        if (!prof) return;
+        if (!profiling()) return;
         for (int p = 0; p < UR_N_PHASES; ++p)
             if (pending[p]) {
                 float ms = 0.f;
@@ -126,13 +147,17 @@ struct ur_ctx {
             }
     }
     void prof_sync() {
-        if (!prof) return;
+        if (!profiling()) return;
         ck(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
         phase_collect();
+    }
+    void no_capture(const char *what) {
+        if (capturing) fail(UR_ERR_STATE, std::string(what) + " cannot run while the stream is being captured");
     }
 
     void grow(DevBuf &b, size_t bytes) {
         if (bytes <= b.bytes && b.p) return;
+        if (capturing) fail(UR_ERR_STATE, "a buffer would have to grow during stream capture: plan the batch first");
         if (b.p) {
             ck(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
             ck(cudaFree(b.p), "cudaFree");
@@ -172,17 +197,16 @@ ur_status guarded(ur_ctx *c, F &&f) {
     }
 }
 
-// Transmit tables: direction (sin, cos), per-element delays, DAS constants.
+// Plane-wave tables: per-element delays, and (sin, cos, min_e x_e sin) per angle.
 void prepare_transmits(ur_ctx *c) {
     if (!c->tx_dirty) return;
+    c->no_capture("preparing transmit tables");
     const int nt = (int)c->angles.size(), ne = c->arr.n_el;
-    std::vector<float2> dir(nt);
     std::vector<ur::ff> delay((size_t)nt * ne), s(nt), co(nt), m(nt);
     const double pitch = c->arr.pitch, x0 = -0.5 * (double)(ne - 1) * pitch;
     for (int k = 0; k < nt; ++k) {
         const double th = c->angles[k];
         const double sn = std::sin(th), cs = std::cos(th);
-        dir[k] = make_float2((float)sn, (float)cs);
         double mn = INFINITY;
         for (int e = 0; e < ne; ++e) mn = std::min(mn, (x0 + e * pitch) * sn);
         for (int e = 0; e < ne; ++e)
@@ -191,12 +215,10 @@ void prepare_transmits(ur_ctx *c) {
         co[k] = split(cs);
         m[k] = split(mn);
     }
-    c->grow(c->txdir, sizeof(float2) * nt);
     c->grow(c->delay, sizeof(ur::ff) * delay.size());
     c->grow(c->tx_sin, sizeof(ur::ff) * nt);
     c->grow(c->tx_cos, sizeof(ur::ff) * nt);
     c->grow(c->tx_m, sizeof(ur::ff) * nt);
-    ck(cudaMemcpyAsync(c->txdir.p, dir.data(), sizeof(float2) * nt, cudaMemcpyHostToDevice, c->stream), "copy txdir");
     ck(cudaMemcpyAsync(c->delay.p, delay.data(), sizeof(ur::ff) * delay.size(), cudaMemcpyHostToDevice, c->stream), "copy delay");
     ck(cudaMemcpyAsync(c->tx_sin.p, s.data(), sizeof(ur::ff) * nt, cudaMemcpyHostToDevice, c->stream), "copy sin");
     ck(cudaMemcpyAsync(c->tx_cos.p, co.data(), sizeof(ur::ff) * nt, cudaMemcpyHostToDevice, c->stream), "copy cos");
@@ -205,20 +227,23 @@ void prepare_transmits(ur_ctx *c) {
     c->tx_dirty = false;
 }
 
-void build_grid(ur_ctx *c, const float *scat_xyza) {
-    const int n = c->n_scat;
-    c->grow(c->scat, sizeof(float4) * n);
-    c->grow(c->amp, sizeof(float) * n);
-    ck(cudaMemcpyAsync(c->scat.p, scat_xyza, sizeof(float4) * n, cudaMemcpyDefault, c->stream), "copy scatterers");
-    c->grow(c->bbox, 6 * sizeof(unsigned int));
+// Build (or rebuild) a scene's scatterer grid; src == nullptr reuses the device copy.
+void build_grid(ur_ctx *c, SceneData &sd, const float *src) {
+    const int n = sd.n_scat;
+    if (src) {
+        c->grow(sd.scat, sizeof(float4) * n);
+        c->grow(sd.amp, sizeof(float) * n);
+        ck(cudaMemcpyAsync(sd.scat.p, src, sizeof(float4) * n, cudaMemcpyDefault, c->stream), "copy scatterers");
+    }
+    c->grow(sd.bbox, 6 * sizeof(unsigned int));
     const unsigned int init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
-    ck(cudaMemcpyAsync(c->bbox.p, init, sizeof init, cudaMemcpyHostToDevice, c->stream), "init bbox");
+    ck(cudaMemcpyAsync(sd.bbox.p, init, sizeof init, cudaMemcpyHostToDevice, c->stream), "init bbox");
     c->phase_begin(UR_PHASE_GRID);
-    ur::launch_bbox((const float4 *)c->scat.p, n, (float *)c->bbox.p, c->stream);
+    ur::launch_bbox((const float4 *)sd.scat.p, n, (float *)sd.bbox.p, c->stream);
     c->phase_end(UR_PHASE_GRID, 1);
     ck(cudaGetLastError(), "bbox kernel");
     unsigned int *hb = (unsigned int *)c->host_scratch;
-    ck(cudaMemcpyAsync(hb, c->bbox.p, sizeof init, cudaMemcpyDeviceToHost, c->stream), "read bbox");
+    ck(cudaMemcpyAsync(hb, sd.bbox.p, sizeof init, cudaMemcpyDeviceToHost, c->stream), "read bbox");
     ck(cudaStreamSynchronize(c->stream), "bbox sync");
     c->phase_collect();
     float lo[3], hi[3];
@@ -232,11 +257,11 @@ void build_grid(ur_ctx *c, const float *scat_xyza) {
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(lo[a]) || !std::isfinite(hi[a])) fail(UR_ERR_INVALID_ARG, "scatterer coordinates must be finite");
     // capture box margin: r_s plus a relative and absolute slack far above FP32 rounding
-    const float r_m = c->r_s * 1.001f + 1e-7f;
-    float h_xy = c->tune.cell_xy > 0.f ? c->tune.cell_xy : 3.f * c->r_s;
-    float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : 40.f * c->r_s;
+    const float r_m = sd.r_s * 1.001f + 1e-7f;
+    float h_xy = c->tune.cell_xy > 0.f ? c->tune.cell_xy : 3.f * sd.r_s;
+    float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : 40.f * sd.r_s;
     int3 dim;
-    for (int tries = 0;; ++tries) {
+    for (;;) {
         dim.x = std::max(1, (int)std::ceil((hi[0] - lo[0] + 2.f * r_m) / h_xy));
         dim.y = std::max(1, (int)std::ceil((hi[1] - lo[1] + 2.f * r_m) / h_xy));
         dim.z = std::max(1, (int)std::ceil((hi[2] - lo[2] + 2.f * r_m) / h_z));
@@ -244,40 +269,40 @@ void build_grid(ur_ctx *c, const float *scat_xyza) {
         h_xy *= 1.5f;
         h_z *= 1.5f;
     }
-    c->g_lo = make_float3(lo[0] - r_m, lo[1] - r_m, lo[2] - r_m);
-    c->g_h = make_float3(h_xy, h_xy, h_z);
-    c->g_inv_h = make_float3(1.f / h_xy, 1.f / h_xy, 1.f / h_z);
-    c->g_dim = dim;
+    sd.g_lo = make_float3(lo[0] - r_m, lo[1] - r_m, lo[2] - r_m);
+    sd.g_h = make_float3(h_xy, h_xy, h_z);
+    sd.g_inv_h = make_float3(1.f / h_xy, 1.f / h_xy, 1.f / h_z);
+    sd.g_dim = dim;
     const uint32_t n_cells = (uint32_t)dim.x * dim.y * dim.z;
-    c->grow(c->cell_count, sizeof(uint32_t) * (n_cells + 1));
-    c->grow(c->cell_start, sizeof(uint32_t) * (n_cells + 1));
-    c->grow(c->cell_fill, sizeof(uint32_t) * (n_cells + 1));
-    c->grow(c->scan_tmp, sizeof(uint32_t) * (n_cells / 4096 + 4));
-    ck(cudaMemsetAsync(c->cell_count.p, 0, sizeof(uint32_t) * (n_cells + 1), c->stream), "memset counts");
-    ck(cudaMemsetAsync(c->cell_fill.p, 0, sizeof(uint32_t) * (n_cells + 1), c->stream), "memset fill");
+    c->grow(sd.cell_count, sizeof(uint32_t) * (n_cells + 1));
+    c->grow(sd.cell_start, sizeof(uint32_t) * (n_cells + 1));
+    c->grow(sd.cell_fill, sizeof(uint32_t) * (n_cells + 1));
+    c->grow(sd.scan_tmp, sizeof(uint32_t) * (n_cells / 4096 + 4));
+    ck(cudaMemsetAsync(sd.cell_count.p, 0, sizeof(uint32_t) * (n_cells + 1), c->stream), "memset counts");
+    ck(cudaMemsetAsync(sd.cell_fill.p, 0, sizeof(uint32_t) * (n_cells + 1), c->stream), "memset fill");
     ur::GridBuildP G{};
-    G.scat = (const float4 *)c->scat.p;
+    G.scat = (const float4 *)sd.scat.p;
     G.n_scat = n;
     G.r_m = r_m;
-    G.lo = c->g_lo;
-    G.inv_h = c->g_inv_h;
+    G.lo = sd.g_lo;
+    G.inv_h = sd.g_inv_h;
     G.dim = dim;
-    G.cell_count = (uint32_t *)c->cell_count.p;
-    G.cell_start = (uint32_t *)c->cell_start.p;
-    G.cell_fill = (uint32_t *)c->cell_fill.p;
-    G.amp = (float *)c->amp.p;
+    G.cell_count = (uint32_t *)sd.cell_count.p;
+    G.cell_start = (uint32_t *)sd.cell_start.p;
+    G.cell_fill = (uint32_t *)sd.cell_fill.p;
+    G.amp = (float *)sd.amp.p;
     c->phase_begin(UR_PHASE_GRID);
     ur::launch_grid_count(G, c->stream);
     ck(cudaGetLastError(), "grid count kernel");
-    ur::launch_scan_u32(G.cell_count, G.cell_start, (uint32_t *)c->scan_tmp.p, n_cells, c->stream);
+    ur::launch_scan_u32(G.cell_count, G.cell_start, (uint32_t *)sd.scan_tmp.p, n_cells, c->stream);
     ck(cudaGetLastError(), "scan kernel");
     c->phase_end(UR_PHASE_GRID, 4);
     ck(cudaMemcpyAsync(hb, G.cell_start + n_cells, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream), "read refs");
     ck(cudaStreamSynchronize(c->stream), "grid sync");
     c->phase_collect();
     const uint32_t n_refs = hb[0];
-    c->grow(c->refs, sizeof(float4) * std::max<uint32_t>(n_refs, 1));
-    G.refs = (float4 *)c->refs.p;
+    c->grow(sd.refs, sizeof(float4) * std::max<uint32_t>(n_refs, 1));
+    G.refs = (float4 *)sd.refs.p;
     c->phase_begin(UR_PHASE_GRID);
     ur::launch_grid_fill(G, c->stream);
     ck(cudaGetLastError(), "grid fill kernel");
@@ -285,38 +310,141 @@ void build_grid(ur_ctx *c, const float *scat_xyza) {
     c->prof_sync();
 }
 
-ur::TraceP make_trace_params(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_path) {
-    ur::TraceP P{};
+void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const ur_boundary *bnd, int n_bnd,
+                  int med_array, float z_max, const float *scat_xyza, int n_scat, float r_s) {
+    c->set_device();
+    c->no_capture("ur_scene_upload");
+    if (slot < 0 || slot >= ur::kMaxScenes) fail(UR_ERR_INVALID_ARG, "scene slot must be in [0, 16)");
+    SceneData &sd = c->scenes[slot];
+    sd.ok = false;
+    c->batch_ok = false;
+    if (!media || n_med < 1 || n_med > ur::kMaxMed) fail(UR_ERR_INVALID_ARG, "n_med must be in [1, 16]");
+    if (n_bnd < 0 || n_bnd > ur::kMaxBnd || (n_bnd > 0 && !bnd)) fail(UR_ERR_INVALID_ARG, "n_bnd must be in [0, 16]");
+    if (med_array < 0 || med_array >= n_med) fail(UR_ERR_INVALID_ARG, "med_array out of range");
+    if (!(z_max > 0.f) || !std::isfinite(z_max)) fail(UR_ERR_INVALID_ARG, "z_max must be positive");
+    if (n_scat < 0 || n_scat >= (1 << 24)) fail(UR_ERR_INVALID_ARG, "n_scat must be in [0, 2^24)");
+    if (n_scat > 0 && (!scat_xyza || !(r_s > 0.f) || !std::isfinite(r_s)))
+        fail(UR_ERR_INVALID_ARG, "scatterers need a pointer and a positive capture radius");
+    std::vector<ur_medium> M(media, media + n_med);
+    for (const ur_medium &m : M) {
+        if (!(m.c > 0.f) || !(m.Z > 0.f) || !(m.alpha_db_cm_mhz >= 0.f) || !std::isfinite(m.c) || !std::isfinite(m.Z))
+            fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0");
+        if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "rough (GGX) boundaries are not supported: roughness must be 0");
+    }
+    std::vector<ur_boundary> Bv(bnd, bnd + n_bnd);
+    for (const ur_boundary &b : Bv) {
+        if (b.kind < UR_PLANE_Z || b.kind > UR_CYL_Y) fail(UR_ERR_INVALID_ARG, "unknown boundary kind");
+        if (b.med_neg < 0 || b.med_neg >= n_med || b.med_pos < 0 || b.med_pos >= n_med)
+            fail(UR_ERR_INVALID_ARG, "boundary media out of range");
+        for (float v : b.p)
+            if (!std::isfinite(v)) fail(UR_ERR_INVALID_ARG, "boundary parameters must be finite");
+        if (b.kind == UR_PLANE_Z && !(b.p[0] > 0.f && b.p[0] < z_max))
+            fail(UR_ERR_INVALID_ARG, "planes must lie strictly between the array and z_max");
+        if (b.kind == UR_SPHERE && !(b.p[3] > 0.f)) fail(UR_ERR_INVALID_ARG, "sphere radius must be positive");
+        if (b.kind == UR_CYL_Y && !(b.p[2] > 0.f)) fail(UR_ERR_INVALID_ARG, "cylinder radius must be positive");
+    }
+    sd.media = M;
+    sd.bnd = Bv;
+    sd.med_array = med_array;
+    sd.z_max = z_max;
+    sd.n_scat = n_scat;
+    sd.r_s = n_scat > 0 ? r_s : 1e-4f;
+    if (n_scat > 0) {
+        build_grid(c, sd, scat_xyza);
+    } else {
+        sd.g_dim = make_int3(1, 1, 1);
+        sd.g_lo = make_float3(0.f, 0.f, 0.f);
+        sd.g_h = make_float3(1.f, 1.f, 1.f);
+        sd.g_inv_h = make_float3(1.f, 1.f, 1.f);
+        c->grow(sd.cell_start, 2 * sizeof(uint32_t));
+        ck(cudaMemsetAsync(sd.cell_start.p, 0, 2 * sizeof(uint32_t), c->stream), "memset cells");
+    }
+    sd.ok = true;
+}
+
+void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
     const ur_array &A = c->arr;
-    ur::SceneP &S = P.S;
-    S.n_med = (int)c->media.size();
-    S.n_bnd = (int)c->bnd.size();
-    S.med_array = c->med_array;
-    S.z_max = c->z_max;
+    S.n_med = (int)sd.media.size();
+    S.n_bnd = (int)sd.bnd.size();
+    S.med_array = sd.med_array;
+    S.z_max = sd.z_max;
     const double np_per_db = std::log(10.0) / 20.0;
     for (int m = 0; m < S.n_med; ++m) {
-        const ur_medium &M = c->media[m];
+        const ur_medium &M = sd.media[m];
         S.med[m].c = M.c;
         S.med[m].Z = M.Z;
         S.med[m].a = (float)((double)M.alpha_db_cm_mhz * ((double)A.f0 * 1e-6) * 100.0 * np_per_db);
         S.med[m].slow = split((double)A.fs / (double)M.c);
     }
     for (int b = 0; b < S.n_bnd; ++b) {
-        S.bnd[b].kind = c->bnd[b].kind;
-        S.bnd[b].med_neg = c->bnd[b].med_neg;
-        S.bnd[b].med_pos = c->bnd[b].med_pos;
-        for (int q = 0; q < 4; ++q) S.bnd[b].p[q] = c->bnd[b].p[q];
+        S.bnd[b].kind = sd.bnd[b].kind;
+        S.bnd[b].med_neg = sd.bnd[b].med_neg;
+        S.bnd[b].med_pos = sd.bnd[b].med_pos;
+        for (int q = 0; q < 4; ++q) S.bnd[b].p[q] = sd.bnd[b].p[q];
     }
-    S.n_scat = c->n_scat;
-    S.r2 = c->r_s * c->r_s;
-    S.g_lo = c->g_lo;
-    S.g_h = c->g_h;
-    S.g_inv_h = c->g_inv_h;
-    S.g_dim = c->g_dim;
-    S.refs = (const float4 *)c->refs.p;
-    S.cell_start = (const uint32_t *)c->cell_start.p;
-    S.amp = (const float *)c->amp.p;
-    S.scat = (const float4 *)c->scat.p;
+    S.n_scat = sd.n_scat;
+    S.r2 = sd.r_s * sd.r_s;
+    S.g_lo = sd.g_lo;
+    S.g_h = sd.g_h;
+    S.g_inv_h = sd.g_inv_h;
+    S.g_dim = sd.g_dim;
+    S.refs = (const float4 *)sd.refs.p;
+    S.cell_start = (const uint32_t *)sd.cell_start.p;
+    S.amp = (const float *)sd.amp.p;
+    S.scat = (const float4 *)sd.scat.p;
+}
+
+// Items -> slot ranges (element-major, padded to the tracer's pool size) and hash offsets.
+void set_items(ur_ctx *c, const std::vector<ur_batch_item> &in) {
+    c->no_capture("setting work items");
+    const int n_el = c->arr.n_el;
+    std::vector<ur::ItemP> it(in.size());
+    uint64_t slot = 0, hash = 0;
+    for (size_t q = 0; q < in.size(); ++q) {
+        const ur_batch_item &b = in[q];
+        ur::ItemP &I = it[q];
+        I.slot_begin = slot;
+        I.hash_begin = hash;
+        I.n_rays = (uint32_t)b.n_rays;
+        I.rays_per_el = (uint32_t)((b.n_rays + (uint64_t)n_el - 1) / (uint64_t)n_el);
+        I.scene = b.scene;
+        I.angle = b.tx;
+        I.stream = b.stream;
+        const double th = c->angles[b.tx];
+        I.sin_t = (float)std::sin(th);
+        I.cos_t = (float)std::cos(th);
+        I.inv_n = (float)(1.0 / (double)b.n_rays);
+        const uint64_t s = (uint64_t)I.rays_per_el * (uint64_t)n_el;
+        slot += (s + ur::kTracePool - 1) / ur::kTracePool * ur::kTracePool;
+        hash += b.n_rays;
+    }
+    c->items = it;
+    c->n_slots = slot;
+    c->grow(c->items_dev, sizeof(ur::ItemP) * std::max<size_t>(it.size(), 1));
+    ck(cudaMemcpyAsync(c->items_dev.p, c->items.data(), sizeof(ur::ItemP) * it.size(), cudaMemcpyHostToDevice, c->stream),
+       "copy items");
+    ck(cudaStreamSynchronize(c->stream), "items sync");
+}
+
+void validate_items(ur_ctx *c, const ur_batch_item *items, int n) {
+    if (!items || n < 1 || n > 65536) fail(UR_ERR_INVALID_ARG, "n_items must be in [1, 65536]");
+    for (int q = 0; q < n; ++q) {
+        const ur_batch_item &b = items[q];
+        if (b.scene < 0 || b.scene >= ur::kMaxScenes || !c->scenes[b.scene].ok)
+            fail(UR_ERR_STATE, "batch item refers to a scene slot that holds no scene");
+        if (b.tx < 0 || b.tx >= (int)c->angles.size()) fail(UR_ERR_INVALID_ARG, "batch item transmit out of range");
+        if (b.n_rays == 0 || b.n_rays > 0xFFFFFFFFull) fail(UR_ERR_INVALID_ARG, "n_rays must be in [1, 2^32)");
+    }
+}
+
+ur::TraceP make_trace_params(ur_ctx *c, uint64_t seed, int max_b, float max_path) {
+    ur::TraceP P{};
+    const ur_array &A = c->arr;
+    int n_scenes = 0;
+    for (const ur::ItemP &I : c->items) n_scenes = std::max(n_scenes, I.scene + 1);
+    P.n_scenes = n_scenes;
+    for (int s = 0; s < n_scenes; ++s)
+        if (c->scenes[s].ok) fill_scene(c, c->scenes[s], P.S[s]);
     P.n_el = A.n_el;
     P.n_s = A.n_s;
     P.pitch = A.pitch;
@@ -330,129 +458,90 @@ ur::TraceP make_trace_params(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_
     P.ac = (float)ac;
     P.cos_am = (float)std::cos(am);
     P.cos_ac = (float)std::cos(ac);
-    P.n_tx = (int)c->angles.size();
-    P.txdir = (const float2 *)c->txdir.p;
+    P.items = (const ur::ItemP *)c->items_dev.p;
+    P.n_items = (int)c->items.size();
+    P.n_slots = c->n_slots;
     P.delay = (const ur::ff *)c->delay.p;
-    P.n_rays = (uint32_t)n_rays;
-    P.rays_per_el = (uint32_t)((n_rays + (uint64_t)A.n_el - 1) / (uint64_t)A.n_el);
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.max_b = max_b;
     P.max_path = max_path;
-    P.inv_n = (float)(1.0 / (double)n_rays);
     P.resolve_batch = c->tune.resolve_batch > 0 ? c->tune.resolve_batch : 16;
-    return P;
-}
-
-void check_ready(ur_ctx *c) {
-    if (!c->scene_ok) fail(UR_ERR_STATE, "no scene uploaded");
-    if (!c->array_ok) fail(UR_ERR_STATE, "array not set");
-    if (c->angles.empty()) fail(UR_ERR_STATE, "no transmits set");
-}
-
-void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_path, float *rf, float *quad,
-              ur_stats *st, ur_debug *dbg) {
-    c->set_device();
-    check_ready(c);
-    if (n_rays == 0 || n_rays > 0xFFFFFFFFull) fail(UR_ERR_INVALID_ARG, "n_rays_per_tx must be in [1, 2^32)");
-    if (max_b < 0 || max_b > 127) fail(UR_ERR_INVALID_ARG, "max_bounces must be in [0, 127]");
-    if (!(max_path > 0.f) || !std::isfinite(max_path)) fail(UR_ERR_INVALID_ARG, "max_path_m must be positive");
-    if (!rf || !quad) fail(UR_ERR_INVALID_ARG, "rf and quad are required");
-    prepare_transmits(c);
-    const int n_tx = (int)c->angles.size(), n_el = c->arr.n_el, n_s = c->arr.n_s;
-    const uint64_t n_rows = (uint64_t)n_tx * n_el;
-    if (n_rows > (1ull << 26)) fail(UR_ERR_INVALID_ARG, "n_tx * n_el too large");
-    const size_t out_elems = (size_t)n_rows * n_s;
-    const bool dbg_on = dbg != nullptr;
-    if (dbg_on && dbg->path_hash && !is_device_ptr(dbg->path_hash)) fail(UR_ERR_INVALID_ARG, "debug arrays must be device memory");
-
-    ur::TraceP P = make_trace_params(c, n_rays, seed, max_b, max_path);
-    // counters: [0] arrival count, [1..6] stats
     c->grow(c->counters, 8 * sizeof(unsigned long long));
     unsigned long long *cnt = (unsigned long long *)c->counters.p;
     P.arr_count = cnt;
     P.stats = cnt + 1;
     P.next_slot = cnt + 7;
-    P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
+    return P;
+}
 
+void check_ready(ur_ctx *c) {
+    if (!c->scenes[0].ok) fail(UR_ERR_STATE, "no scene uploaded");
+    if (!c->array_ok) fail(UR_ERR_STATE, "array not set");
+    if (c->angles.empty()) fail(UR_ERR_STATE, "no transmits set");
+}
+
+void check_trace_args(int max_b, float max_path) {
+    if (max_b < 0 || max_b > 127) fail(UR_ERR_INVALID_ARG, "max_bounces must be in [0, 127]");
+    if (!(max_path > 0.f) || !std::isfinite(max_path)) fail(UR_ERR_INVALID_ARG, "max_path_m must be positive");
+}
+
+int trace_grid(ur_ctx *c, bool dbg) {
     const int block = c->tune.block > 0 ? c->tune.block : 256;
-    const int per_sm = c->tune.blocks_per_sm > 0 ? c->tune.blocks_per_sm : ur::trace_occupancy(block, dbg_on);
-    const int grid = std::max(1, c->sms * per_sm);
+    const int per_sm = c->tune.blocks_per_sm > 0 ? c->tune.blocks_per_sm : ur::trace_occupancy(block, dbg);
+    return std::max(1, c->sms * per_sm);
+}
 
-    const double want = c->arr_per_ray * (double)n_rays * (double)n_tx * 1.25 + 4096.0;
-    uint64_t cap = std::max<uint64_t>(c->arr_cap, (uint64_t)want);
-    unsigned long long *h = c->host_scratch;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        if (cap > c->arr_cap) {
-            c->grow(c->arrivals, sizeof(uint4) * cap);
-            if (dbg_on) c->grow(c->arr_dbg, sizeof(uint2) * cap);
-            c->arr_cap = cap;
-        }
-        if (dbg_on && c->arr_dbg.bytes < sizeof(uint2) * c->arr_cap) c->grow(c->arr_dbg, sizeof(uint2) * c->arr_cap);
-        P.arr = (uint4 *)c->arrivals.p;
-        P.arr_dbg = dbg_on ? (uint2 *)c->arr_dbg.p : nullptr;
-        P.arr_cap = c->arr_cap;
-        ck(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
-        c->phase_begin(UR_PHASE_TRACE);
-        ur::launch_trace(P, dbg_on, block, grid, c->stream);
-        ck(cudaGetLastError(), "trace kernel launch");
-        c->phase_end(UR_PHASE_TRACE, 1);
-        ck(cudaMemcpyAsync(h, cnt, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream), "read count");
-        ck(cudaStreamSynchronize(c->stream), "trace kernel");
-        c->phase_collect();
-        const uint64_t n_arr = h[0];
-        c->arr_per_ray = std::max(1e-3, (double)n_arr / ((double)n_rays * (double)n_tx));
-        if (n_arr <= c->arr_cap) break;
-        cap = (uint64_t)((double)n_arr * 1.1) + 4096;
-        if (attempt == 2) fail(UR_ERR_OVERFLOW, "arrival queue kept overflowing");
+// Arrival queue and sort buffers for `cap` arrivals and the current items.
+void size_trace_buffers(ur_ctx *c, uint64_t cap, bool dbg) {
+    const uint64_t n_rows = (uint64_t)c->items.size() * c->arr.n_el;
+    if (cap > c->arr_cap) {
+        c->grow(c->arrivals, sizeof(uint4) * cap);
+        c->arr_cap = cap;
     }
-    const uint64_t n_arr = h[0];
-    if (st) {
-        st->rays = h[1];
-        st->segments = h[2];
-        st->interactions = h[3];
-        st->candidates = h[4];
-        st->connections = h[5];
-        st->arrivals = h[6];
-    }
-
-    // outputs: device in place, or staged for host buffers
-    const bool rf_dev = is_device_ptr(rf), q_dev = is_device_ptr(quad);
-    float *d_rf = rf, *d_q = quad;
-    if (!rf_dev) {
-        c->grow(c->stage_rf, sizeof(float) * out_elems);
-        d_rf = (float *)c->stage_rf.p;
-    }
-    if (!q_dev) {
-        c->grow(c->stage_quad, sizeof(float) * out_elems);
-        d_q = (float *)c->stage_quad.p;
-    }
-    ck(cudaMemsetAsync(d_rf, 0, sizeof(float) * out_elems, c->stream), "memset rf");
-    ck(cudaMemsetAsync(d_q, 0, sizeof(float) * out_elems, c->stream), "memset quad");
-
-    ur::BinP B{};
-    B.arr = (const uint4 *)c->arrivals.p;
-    B.arr_count = cnt;
-    B.arr_cap = c->arr_cap;
-    B.n_rows = (int)n_rows;
-    B.n_s = n_s;
-    B.chunk = 4096;
-    B.max_items = (uint32_t)(n_rows + n_arr / B.chunk + 16);
+    if (dbg) c->grow(c->arr_dbg, sizeof(uint2) * c->arr_cap);
+    c->grow(c->sorted, sizeof(float4) * c->arr_cap);
     c->grow(c->row_count, sizeof(uint32_t) * n_rows);
     c->grow(c->row_fill, sizeof(uint32_t) * n_rows);
     c->grow(c->row_off, sizeof(uint32_t) * (n_rows + 1));
-    c->grow(c->items, sizeof(uint4) * B.max_items);
-    c->grow(c->n_items, sizeof(uint32_t));
-    c->grow(c->sorted, sizeof(float4) * std::max<uint64_t>(n_arr, 1));
+    c->grow(c->work, sizeof(uint4) * (n_rows + c->arr_cap / kChunk + 16));
+    c->grow(c->n_work, sizeof(uint32_t));
+}
+
+void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
+    P.arr = (uint4 *)c->arrivals.p;
+    P.arr_dbg = dbg ? arr_dbg : nullptr;
+    P.arr_cap = c->arr_cap;
+    ck(cudaMemsetAsync(P.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
+    c->phase_begin(UR_PHASE_TRACE);
+    ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream);
+    ck(cudaGetLastError(), "trace kernel launch");
+    c->phase_end(UR_PHASE_TRACE, 1);
+}
+
+// Sort the arrival queue by row and deposit the pulses (asynchronous).
+void launch_binning(ur_ctx *c, float *d_rf, float *d_q) {
+    const uint64_t n_rows = (uint64_t)c->items.size() * c->arr.n_el;
+    const size_t out_elems = (size_t)n_rows * c->arr.n_s;
+    ck(cudaMemsetAsync(d_rf, 0, sizeof(float) * out_elems, c->stream), "memset rf");
+    ck(cudaMemsetAsync(d_q, 0, sizeof(float) * out_elems, c->stream), "memset quad");
+    ur::BinP B{};
+    B.arr = (const uint4 *)c->arrivals.p;
+    B.arr_count = (const unsigned long long *)c->counters.p;
+    B.arr_cap = c->arr_cap;
+    B.n_rows = (int)n_rows;
+    B.n_s = c->arr.n_s;
+    B.chunk = kChunk;
+    B.max_items = (uint32_t)(n_rows + c->arr_cap / kChunk + 16);
     B.row_count = (uint32_t *)c->row_count.p;
     B.row_fill = (uint32_t *)c->row_fill.p;
     B.row_off = (uint32_t *)c->row_off.p;
-    B.items = (uint4 *)c->items.p;
-    B.n_items = (uint32_t *)c->n_items.p;
+    B.items = (uint4 *)c->work.p;
+    B.n_items = (uint32_t *)c->n_work.p;
     B.sorted = (float4 *)c->sorted.p;
     B.rf = d_rf;
     B.quad = d_q;
     const double s_samples = (double)c->arr.n_cycles / (4.0 * (double)c->arr.f0) * (double)c->arr.fs;
-    B.K = P.K;
+    B.K = (float)((double)c->arr.tcut_sigmas * s_samples);
     B.inv_2s2 = (float)(1.0 / (2.0 * s_samples * s_samples));
     B.phase_per_sample = (float)(2.0 * (double)c->arr.f0 / (double)c->arr.fs);
     ck(cudaMemsetAsync(B.row_count, 0, sizeof(uint32_t) * n_rows, c->stream), "memset rows");
@@ -465,15 +554,77 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     ur::launch_bin_deposit(B, c->sms, c->stream);
     ck(cudaGetLastError(), "deposit kernel");
     c->phase_end(UR_PHASE_DEPOSIT, 1);
+}
 
+void read_stats(const unsigned long long *h, ur_stats *st) {
+    if (!st) return;
+    st->rays = h[1];
+    st->segments = h[2];
+    st->interactions = h[3];
+    st->candidates = h[4];
+    st->connections = h[5];
+    st->arrivals = h[6];
+}
+
+void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_path, float *rf, float *quad,
+              ur_stats *st, ur_debug *dbg) {
+    c->set_device();
+    c->no_capture("ur_trace");
+    check_ready(c);
+    if (n_rays == 0 || n_rays > 0xFFFFFFFFull) fail(UR_ERR_INVALID_ARG, "n_rays_per_tx must be in [1, 2^32)");
+    check_trace_args(max_b, max_path);
+    if (!rf || !quad) fail(UR_ERR_INVALID_ARG, "rf and quad are required");
+    prepare_transmits(c);
+    const int n_tx = (int)c->angles.size(), n_el = c->arr.n_el, n_s = c->arr.n_s;
+    const uint64_t n_rows = (uint64_t)n_tx * n_el;
+    if (n_rows > (1ull << 26)) fail(UR_ERR_INVALID_ARG, "n_tx * n_el too large");
+    const size_t out_elems = (size_t)n_rows * n_s;
+    const bool dbg_on = dbg != nullptr;
+    if (dbg_on && dbg->path_hash && !is_device_ptr(dbg->path_hash)) fail(UR_ERR_INVALID_ARG, "debug arrays must be device memory");
+    std::vector<ur_batch_item> items(n_tx);
+    for (int k = 0; k < n_tx; ++k) items[k] = ur_batch_item{0, k, (uint32_t)k, 0u, n_rays};
+    set_items(c, items);
+    c->batch_ok = false;
+    ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
+    P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
+
+    const double want = c->arr_per_ray * (double)n_rays * (double)n_tx * 1.25 + 4096.0;
+    uint64_t cap = std::max<uint64_t>(c->arr_cap, (uint64_t)want);
+    unsigned long long *h = c->host_scratch;
+    for (int attempt = 0;; ++attempt) {
+        size_trace_buffers(c, cap, dbg_on);
+        launch_trace_kernel(c, P, dbg_on, (uint2 *)c->arr_dbg.p);
+        ck(cudaMemcpyAsync(h, P.arr_count, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream), "read count");
+        ck(cudaStreamSynchronize(c->stream), "trace kernel");
+        c->phase_collect();
+        const uint64_t n_arr = h[0];
+        c->arr_per_ray = std::max(1e-3, (double)n_arr / ((double)n_rays * (double)n_tx));
+        if (n_arr <= c->arr_cap) break;
+        if (attempt == 2) fail(UR_ERR_OVERFLOW, "arrival queue kept overflowing");
+        cap = (uint64_t)((double)n_arr * 1.1) + 4096;
+    }
+    const uint64_t n_arr = h[0];
+    read_stats(h, st);
+
+    const bool rf_dev = is_device_ptr(rf), q_dev = is_device_ptr(quad);
+    float *d_rf = rf, *d_q = quad;
+    if (!rf_dev) {
+        c->grow(c->stage_rf, sizeof(float) * out_elems);
+        d_rf = (float *)c->stage_rf.p;
+    }
+    if (!q_dev) {
+        c->grow(c->stage_quad, sizeof(float) * out_elems);
+        d_q = (float *)c->stage_quad.p;
+    }
+    launch_binning(c, d_rf, d_q);
     if (dbg_on) {
         dbg->count = n_arr;
         ur::DebugOut D{dbg->ray, dbg->event, dbg->row, dbg->t_hi, dbg->t_lo, dbg->amp, dbg->capacity};
         if (D.cap > 0) {
             if (!D.ray || !D.event || !D.row || !D.t_hi || !D.t_lo || !D.amp)
                 fail(UR_ERR_INVALID_ARG, "debug arrays must all be set when capacity > 0");
-            ur::launch_unpack_debug((const uint4 *)c->arrivals.p, (const uint2 *)c->arr_dbg.p, cnt, c->arr_cap, D,
-                                    c->stream);
+            ur::launch_unpack_debug((const uint4 *)c->arrivals.p, (const uint2 *)c->arr_dbg.p,
+                                    (const unsigned long long *)c->counters.p, c->arr_cap, D, c->stream);
             ck(cudaGetLastError(), "unpack kernel");
         }
     }
@@ -482,6 +633,20 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     if (!rf_dev || !q_dev || dbg_on) ck(cudaStreamSynchronize(c->stream), "trace outputs");
     c->prof_sync();
     if (dbg_on && n_arr > dbg->capacity) fail(UR_ERR_OVERFLOW, "debug capacity smaller than the arrival count");
+}
+
+// Delay-and-sum constants shared by every beamforming call.
+ur::ImageP image_params(ur_ctx *c) {
+    ur::ImageP I{};
+    I.n_el = c->arr.n_el;
+    I.n_s = c->arr.n_s;
+    I.q = split((double)c->arr.fs / (double)c->arr.c_bf);
+    I.x_first = split(-0.5 * (double)(c->arr.n_el - 1) * (double)c->arr.pitch);
+    I.pitch = c->arr.pitch;
+    I.tx_sin = (const ur::ff *)c->tx_sin.p;
+    I.tx_cos = (const ur::ff *)c->tx_cos.p;
+    I.tx_m = (const ur::ff *)c->tx_m.p;
+    return I;
 }
 
 }  // namespace
@@ -532,16 +697,28 @@ ur_status ur_create(ur_ctx **out, int device, void *cuda_stream) {
 ur_status ur_destroy(ur_ctx *c) {
     if (!c) return UR_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
+    if (c->capturing) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(c->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
     cudaStreamSynchronize(c->stream);
-    DevBuf *all[] = {&c->scat, &c->amp, &c->refs, &c->cell_count, &c->cell_start, &c->cell_fill, &c->scan_tmp,
-                     &c->bbox, &c->txdir, &c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->arrivals, &c->arr_dbg,
-                     &c->sorted, &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->items, &c->n_items,
-                     &c->stage_rf, &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max};
+    for (SceneData &sd : c->scenes) {
+        DevBuf *bs[] = {&sd.scat, &sd.amp, &sd.refs, &sd.cell_count, &sd.cell_start, &sd.cell_fill, &sd.scan_tmp, &sd.bbox};
+        for (DevBuf *b : bs) c->release(*b);
+    }
+    DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
+                     &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
+                     &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
+                     &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max};
     for (DevBuf *b : all) c->release(*b);
     for (int p = 0; p < UR_N_PHASES; ++p) {
         if (c->ev0[p]) cudaEventDestroy(c->ev0[p]);
         if (c->ev1[p]) cudaEventDestroy(c->ev1[p]);
     }
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     if (c->host_scratch) cudaFreeHost(c->host_scratch);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -552,56 +729,17 @@ const char *ur_last_error(const ur_ctx *c) { return c ? c->err.c_str() : "null c
 
 ur_status ur_scene_upload(ur_ctx *c, const ur_medium *media, int n_med, const ur_boundary *bnd, int n_bnd,
                           int med_array, float z_max, const float *scat_xyza, int n_scat, float r_s) {
-    return guarded(c, [&] {
-        c->set_device();
-        c->scene_ok = false;
-        if (!media || n_med < 1 || n_med > ur::kMaxMed) fail(UR_ERR_INVALID_ARG, "n_med must be in [1, 16]");
-        if (n_bnd < 0 || n_bnd > ur::kMaxBnd || (n_bnd > 0 && !bnd)) fail(UR_ERR_INVALID_ARG, "n_bnd must be in [0, 32]");
-        if (med_array < 0 || med_array >= n_med) fail(UR_ERR_INVALID_ARG, "med_array out of range");
-        if (!(z_max > 0.f) || !std::isfinite(z_max)) fail(UR_ERR_INVALID_ARG, "z_max must be positive");
-        if (n_scat < 0 || n_scat >= (1 << 24)) fail(UR_ERR_INVALID_ARG, "n_scat must be in [0, 2^24)");
-        if (n_scat > 0 && (!scat_xyza || !(r_s > 0.f) || !std::isfinite(r_s)))
-            fail(UR_ERR_INVALID_ARG, "scatterers need a pointer and a positive capture radius");
-        std::vector<ur_medium> M(media, media + n_med);
-        for (const ur_medium &m : M) {
-            if (!(m.c > 0.f) || !(m.Z > 0.f) || !(m.alpha_db_cm_mhz >= 0.f) || !std::isfinite(m.c) || !std::isfinite(m.Z))
-                fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0");
-            if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "rough (GGX) boundaries are not supported: roughness must be 0");
-        }
-        std::vector<ur_boundary> Bv(bnd, bnd + n_bnd);
-        for (const ur_boundary &b : Bv) {
-            if (b.kind < UR_PLANE_Z || b.kind > UR_CYL_Y) fail(UR_ERR_INVALID_ARG, "unknown boundary kind");
-            if (b.med_neg < 0 || b.med_neg >= n_med || b.med_pos < 0 || b.med_pos >= n_med)
-                fail(UR_ERR_INVALID_ARG, "boundary media out of range");
-            for (float v : b.p)
-                if (!std::isfinite(v)) fail(UR_ERR_INVALID_ARG, "boundary parameters must be finite");
-            if (b.kind == UR_PLANE_Z && !(b.p[0] > 0.f && b.p[0] < z_max))
-                fail(UR_ERR_INVALID_ARG, "planes must lie strictly between the array and z_max");
-            if (b.kind == UR_SPHERE && !(b.p[3] > 0.f)) fail(UR_ERR_INVALID_ARG, "sphere radius must be positive");
-            if (b.kind == UR_CYL_Y && !(b.p[2] > 0.f)) fail(UR_ERR_INVALID_ARG, "cylinder radius must be positive");
-        }
-        c->media = M;
-        c->bnd = Bv;
-        c->med_array = med_array;
-        c->z_max = z_max;
-        c->n_scat = n_scat;
-        c->r_s = n_scat > 0 ? r_s : 1e-4f;
-        if (n_scat > 0) {
-            build_grid(c, scat_xyza);
-        } else {
-            c->g_dim = make_int3(1, 1, 1);
-            c->g_lo = make_float3(0.f, 0.f, 0.f);
-            c->g_h = make_float3(1.f, 1.f, 1.f);
-            c->g_inv_h = make_float3(1.f, 1.f, 1.f);
-            c->grow(c->cell_start, 2 * sizeof(uint32_t));
-            ck(cudaMemsetAsync(c->cell_start.p, 0, 2 * sizeof(uint32_t), c->stream), "memset cells");
-        }
-        c->scene_ok = true;
-    });
+    return guarded(c, [&] { upload_scene(c, 0, media, n_med, bnd, n_bnd, med_array, z_max, scat_xyza, n_scat, r_s); });
+}
+
+ur_status ur_scene_upload_slot(ur_ctx *c, int slot, const ur_medium *media, int n_med, const ur_boundary *bnd,
+                               int n_bnd, int med_array, float z_max, const float *scat_xyza, int n_scat, float r_s) {
+    return guarded(c, [&] { upload_scene(c, slot, media, n_med, bnd, n_bnd, med_array, z_max, scat_xyza, n_scat, r_s); });
 }
 
 ur_status ur_set_array(ur_ctx *c, const ur_array *a) {
     return guarded(c, [&] {
+        c->no_capture("ur_set_array");
         if (!a) fail(UR_ERR_INVALID_ARG, "array is NULL");
         const ur_array &A = *a;
         if (A.n_el < 1 || A.n_el > 4096) fail(UR_ERR_INVALID_ARG, "n_el must be in [1, 4096]");
@@ -616,12 +754,14 @@ ur_status ur_set_array(ur_ctx *c, const ur_array *a) {
         c->arr = A;
         c->array_ok = true;
         c->tx_dirty = true;
+        c->batch_ok = false;
     });
 }
 
 ur_status ur_set_plane_waves(ur_ctx *c, const float *angles_rad, int n_tx) {
     return guarded(c, [&] {
         c->set_device();
+        c->no_capture("ur_set_plane_waves");
         if (!c->array_ok) fail(UR_ERR_STATE, "set the array before the transmits");
         if (!angles_rad || n_tx < 1 || n_tx > 65536) fail(UR_ERR_INVALID_ARG, "n_tx must be in [1, 65536]");
         std::vector<float> a(n_tx);
@@ -630,6 +770,7 @@ ur_status ur_set_plane_waves(ur_ctx *c, const float *angles_rad, int n_tx) {
             if (!(std::fabs(v) < (float)(kPi / 3.0))) fail(UR_ERR_INVALID_ARG, "|angle| must be below 60 degrees");
         c->angles = a;
         c->tx_dirty = true;
+        c->batch_ok = false;
     });
 }
 
@@ -650,6 +791,7 @@ ur_status ur_beamform(ur_ctx *c, const float *rf, const float *quad, const float
                       int nz, float dyn_range_db, float *iq, float *env, float *db) {
     return guarded(c, [&] {
         c->set_device();
+        c->no_capture("ur_beamform");
         if (!c->array_ok) fail(UR_ERR_STATE, "array not set");
         if (c->angles.empty()) fail(UR_ERR_STATE, "no transmits set");
         if (!rf || !quad || !x_px || !z_px) fail(UR_ERR_INVALID_ARG, "rf, quad and pixel coordinates are required");
@@ -701,27 +843,20 @@ ur_status ur_beamform(ur_ctx *c, const float *rf, const float *quad, const float
         }
         c->grow(c->env_max, sizeof(unsigned int));
         ck(cudaMemsetAsync(c->env_max.p, 0, sizeof(unsigned int), c->stream), "memset max");
-        ur::ImageP I{};
+        ur::ImageP I = image_params(c);
         I.rf = d_rf;
         I.quad = d_q;
         I.n_tx = n_tx;
-        I.n_el = n_el;
-        I.n_s = n_s;
         I.x_px = (const float *)c->pix.p;
         I.z_px = (const float *)c->pix.p + nx;
         I.nx = nx;
         I.nz = nz;
-        I.q = split((double)c->arr.fs / (double)c->arr.c_bf);
-        I.x_first = split(-0.5 * (double)(n_el - 1) * (double)c->arr.pitch);
-        I.pitch = c->arr.pitch;
-        I.tx_sin = (const ur::ff *)c->tx_sin.p;
-        I.tx_cos = (const ur::ff *)c->tx_cos.p;
-        I.tx_m = (const ur::ff *)c->tx_m.p;
         I.iq = d_iq;
         I.env = d_env;
         I.db = d_db;
         I.env_max = (unsigned int *)c->env_max.p;
         I.dyn_range_db = dyn_range_db;
+        I.n_images = 1;
         c->phase_begin(UR_PHASE_DAS);
         ur::launch_das(I, c->stream);
         ck(cudaGetLastError(), "das kernel");
@@ -747,6 +882,264 @@ ur_status ur_beamform(ur_ctx *c, const float *rf, const float *quad, const float
         }
         if (sync || !is_device_ptr(rf) || !is_device_ptr(quad)) ck(cudaStreamSynchronize(c->stream), "beamform outputs");
         c->prof_sync();
+    });
+}
+
+// ------------------------------------------------------------------ batches
+
+ur_status ur_batch_plan(ur_ctx *c, const ur_batch_item *items, int n_items, uint64_t arrival_capacity,
+                        const float *x_px, int nx, const float *z_px, int nz) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_batch_plan");
+        c->batch_ok = false;
+        if (!c->array_ok) fail(UR_ERR_STATE, "array not set");
+        if (c->angles.empty()) fail(UR_ERR_STATE, "no transmits set");
+        validate_items(c, items, n_items);
+        if ((uint64_t)n_items * c->arr.n_el > (1ull << 26)) fail(UR_ERR_INVALID_ARG, "n_items * n_el too large");
+        if (!x_px || !z_px || nx < 1 || nz < 1 || nx > 16384 || nz > 16384)
+            fail(UR_ERR_INVALID_ARG, "pixel coordinates with 1 <= nx, nz <= 16384 are required");
+        prepare_transmits(c);
+        c->batch_items.assign(items, items + n_items);
+        set_items(c, c->batch_items);
+        double rays = 0.0;
+        for (int q = 0; q < n_items; ++q) rays += (double)items[q].n_rays;
+        const uint64_t cap = arrival_capacity ? arrival_capacity : (uint64_t)(c->arr_per_ray * rays * 1.5 + 4096.0);
+        size_trace_buffers(c, cap, false);
+        c->batch_cap = c->arr_cap;
+        // images: one per scene present, in slot order, compounding that scene's items
+        std::vector<int> lists, begin, angle(n_items), scenes;
+        for (int s = 0; s < ur::kMaxScenes; ++s) {
+            std::vector<int> mine;
+            for (int q = 0; q < n_items; ++q)
+                if (items[q].scene == s) mine.push_back(q);
+            if (mine.empty()) continue;
+            scenes.push_back(s);
+            begin.push_back((int)lists.size());
+            lists.insert(lists.end(), mine.begin(), mine.end());
+        }
+        begin.push_back((int)lists.size());
+        for (int q = 0; q < n_items; ++q) angle[q] = items[q].tx;
+        std::vector<int> packed;
+        packed.insert(packed.end(), lists.begin(), lists.end());
+        packed.insert(packed.end(), begin.begin(), begin.end());
+        packed.insert(packed.end(), angle.begin(), angle.end());
+        c->grow(c->batch_lists, sizeof(int) * packed.size());
+        ck(cudaMemcpyAsync(c->batch_lists.p, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy image lists");
+        c->batch_images = (int)scenes.size();
+        c->batch_image_scene = scenes;
+        c->batch_nx = nx;
+        c->batch_nz = nz;
+        c->grow(c->batch_pix, sizeof(float) * (nx + nz));
+        ck(cudaMemcpyAsync(c->batch_pix.p, x_px, sizeof(float) * nx, cudaMemcpyDefault, c->stream), "copy x");
+        ck(cudaMemcpyAsync((float *)c->batch_pix.p + nx, z_px, sizeof(float) * nz, cudaMemcpyDefault, c->stream), "copy z");
+        c->grow(c->batch_env, sizeof(float) * (size_t)c->batch_images * nx * nz);
+        c->grow(c->batch_max, sizeof(unsigned int) * c->batch_images);
+        c->grow(c->counters, 8 * sizeof(unsigned long long));
+        ck(cudaStreamSynchronize(c->stream), "batch plan");
+        c->batch_ok = true;
+    });
+}
+
+ur_status ur_batch_trace(ur_ctx *c, uint64_t seed, int max_b, float max_path, float *rf, float *quad) {
+    return guarded(c, [&] {
+        c->set_device();
+        if (!c->batch_ok) fail(UR_ERR_STATE, "no batch planned (ur_batch_plan)");
+        check_trace_args(max_b, max_path);
+        if (!rf || !quad || !is_device_ptr(rf) || !is_device_ptr(quad))
+            fail(UR_ERR_INVALID_ARG, "batch rf and quad must be device memory");
+        if (c->items.size() != c->batch_items.size() || c->arr_cap < c->batch_cap)
+            fail(UR_ERR_STATE, "the batch plan was replaced by another trace: plan again");
+        ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
+        launch_trace_kernel(c, P, false, nullptr);
+        launch_binning(c, rf, quad);
+        c->prof_sync();
+    });
+}
+
+ur_status ur_batch_status(ur_ctx *c, uint64_t *n_arrivals, ur_stats *st) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_batch_status");
+        if (!c->counters.p) fail(UR_ERR_STATE, "no trace has run");
+        unsigned long long *h = c->host_scratch;
+        ck(cudaMemcpyAsync(h, c->counters.p, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+           "read counters");
+        ck(cudaStreamSynchronize(c->stream), "batch status");
+        if (n_arrivals) *n_arrivals = h[0];
+        read_stats(h, st);
+        if (h[0] > c->arr_cap) fail(UR_ERR_OVERFLOW, "arrival capacity exceeded: plan with a larger capacity");
+    });
+}
+
+ur_status ur_batch_beamform(ur_ctx *c, const float *rf, const float *quad, float dyn_range_db, float *iq, float *env,
+                            float *db) {
+    return guarded(c, [&] {
+        c->set_device();
+        if (!c->batch_ok) fail(UR_ERR_STATE, "no batch planned (ur_batch_plan)");
+        if (!rf || !quad || !is_device_ptr(rf) || !is_device_ptr(quad))
+            fail(UR_ERR_INVALID_ARG, "batch rf and quad must be device memory");
+        if (!iq && !env && !db) fail(UR_ERR_INVALID_ARG, "no output requested");
+        if ((iq && !is_device_ptr(iq)) || (env && !is_device_ptr(env)) || (db && !is_device_ptr(db)))
+            fail(UR_ERR_INVALID_ARG, "batch outputs must be device memory");
+        if (db && !(dyn_range_db > 0.f)) fail(UR_ERR_INVALID_ARG, "dyn_range_db must be positive");
+        const int n_items = (int)c->batch_items.size();
+        const int *lists = (const int *)c->batch_lists.p;
+        ck(cudaMemsetAsync(c->batch_max.p, 0, sizeof(unsigned int) * c->batch_images, c->stream), "memset max");
+        ur::ImageP I = image_params(c);
+        I.rf = rf;
+        I.quad = quad;
+        I.n_tx = n_items;
+        I.img_items = lists;
+        I.img_begin = lists + n_items;
+        I.item_angle = lists + n_items + c->batch_images + 1;
+        I.n_images = c->batch_images;
+        I.x_px = (const float *)c->batch_pix.p;
+        I.z_px = (const float *)c->batch_pix.p + c->batch_nx;
+        I.nx = c->batch_nx;
+        I.nz = c->batch_nz;
+        I.iq = (float2 *)iq;
+        I.env = env ? env : (float *)c->batch_env.p;
+        I.db = db;
+        I.env_max = (unsigned int *)c->batch_max.p;
+        I.dyn_range_db = dyn_range_db;
+        c->phase_begin(UR_PHASE_DAS);
+        ur::launch_das(I, c->stream);
+        ck(cudaGetLastError(), "das kernel");
+        c->phase_end(UR_PHASE_DAS, 1);
+        if (db) {
+            c->phase_begin(UR_PHASE_LOG);
+            ur::launch_log(I, c->stream);
+            ck(cudaGetLastError(), "log kernel");
+            c->phase_end(UR_PHASE_LOG, 1);
+        }
+        c->prof_sync();
+    });
+}
+
+ur_status ur_graph_begin(ur_ctx *c) {
+    return guarded(c, [&] {
+        c->set_device();
+        if (c->capturing) fail(UR_ERR_STATE, "already capturing");
+        ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        c->capturing = true;
+    });
+}
+
+ur_status ur_graph_end(ur_ctx *c) {
+    return guarded(c, [&] {
+        c->set_device();
+        if (!c->capturing) fail(UR_ERR_STATE, "not capturing");
+        c->capturing = false;
+        cudaGraph_t g = nullptr;
+        ck(cudaStreamEndCapture(c->stream, &g), "cudaStreamEndCapture");
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->graph = g;
+        c->graph_exec = nullptr;
+        ck(cudaGraphInstantiate(&c->graph_exec, g, 0), "cudaGraphInstantiate");
+    });
+}
+
+ur_status ur_graph_launch(ur_ctx *c) {
+    return guarded(c, [&] {
+        c->set_device();
+        if (!c->graph_exec) fail(UR_ERR_STATE, "no graph captured");
+        c->no_capture("ur_graph_launch");
+        ck(cudaGraphLaunch(c->graph_exec, c->stream), "cudaGraphLaunch");
+    });
+}
+
+// ------------------------------------------------------------------ autotuner
+
+ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int max_b, float max_path,
+                      ur_tuning *best_out) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_autotune");
+        if (scene < 0 || scene >= ur::kMaxScenes || !c->scenes[scene].ok) fail(UR_ERR_STATE, "scene slot holds no scene");
+        if (!c->array_ok || c->angles.empty()) fail(UR_ERR_STATE, "array and transmits must be set");
+        if (n_rays == 0 || n_rays > 0xFFFFFFFFull) fail(UR_ERR_INVALID_ARG, "n_rays must be in [1, 2^32)");
+        check_trace_args(max_b, max_path);
+        prepare_transmits(c);
+        c->batch_ok = false;
+        SceneData &sd = c->scenes[scene];
+        const bool prof_was = c->prof;
+        c->prof = false;
+        cudaEvent_t e0, e1;
+        ck(cudaEventCreate(&e0), "cudaEventCreate");
+        ck(cudaEventCreate(&e1), "cudaEventCreate");
+        std::vector<ur_batch_item> items(1, ur_batch_item{scene, 0, 0u, 0u, n_rays});
+        set_items(c, items);
+        const ur_tuning base = c->tune;
+        // device time of one trace of n_rays rays with tuning t (grid rebuilt when its cells change)
+        auto measure = [&](const ur_tuning &t) {
+            const bool regrid = sd.n_scat > 0 && (t.cell_xy != c->tune.cell_xy || t.cell_z != c->tune.cell_z);
+            c->tune = t;
+            if (regrid) build_grid(c, sd, nullptr);
+            ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
+            size_trace_buffers(c, (uint64_t)(c->arr_per_ray * (double)n_rays * 1.5) + 4096, false);
+            float best = INFINITY;
+            for (int rep = 0; rep < 3; ++rep) {
+                launch_trace_kernel(c, P, false, nullptr);
+                ck(cudaEventRecord(e0, c->stream), "event");
+                launch_trace_kernel(c, P, false, nullptr);
+                ck(cudaEventRecord(e1, c->stream), "event");
+                ck(cudaEventSynchronize(e1), "event sync");
+                float ms = 0.f;
+                ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+                best = std::min(best, ms);
+            }
+            ck(cudaMemcpy(c->host_scratch, c->counters.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost), "count");
+            c->arr_per_ray = std::max(1e-3, (double)c->host_scratch[0] / (double)n_rays);
+            return best;
+        };
+        ur_tuning cur = base;
+        const float r = sd.r_s;
+        if (cur.cell_xy <= 0.f) cur.cell_xy = 3.f * r;
+        if (cur.cell_z <= 0.f) cur.cell_z = 40.f * r;
+        if (cur.resolve_batch <= 0) cur.resolve_batch = 16;
+        if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = ur::trace_occupancy(256, false);
+        float t_cur = measure(cur);
+        // coordinate descent over the knobs
+        const float z_mult[] = {20.f, 30.f, 40.f, 60.f, 80.f};
+        const float xy_mult[] = {2.f, 3.f, 4.f, 5.f};
+        const int batches[] = {8, 12, 16, 20, 24};
+        for (int pass = 0; pass < 2; ++pass) {
+            for (float m : z_mult) {
+                ur_tuning t = cur;
+                t.cell_z = m * r;
+                const float v = measure(t);
+                if (v < t_cur) { t_cur = v; cur = t; }
+            }
+            for (float m : xy_mult) {
+                ur_tuning t = cur;
+                t.cell_xy = m * r;
+                const float v = measure(t);
+                if (v < t_cur) { t_cur = v; cur = t; }
+            }
+            for (int b : batches) {
+                ur_tuning t = cur;
+                t.resolve_batch = b;
+                const float v = measure(t);
+                if (v < t_cur) { t_cur = v; cur = t; }
+            }
+            for (int bps = 2; bps <= 4; ++bps) {
+                ur_tuning t = cur;
+                t.blocks_per_sm = bps;
+                const float v = measure(t);
+                if (v < t_cur) { t_cur = v; cur = t; }
+            }
+        }
+        c->tune = cur;
+        if (sd.n_scat > 0) build_grid(c, sd, nullptr);
+        for (int s = 0; s < ur::kMaxScenes; ++s)
+            if (s != scene && c->scenes[s].ok && c->scenes[s].n_scat > 0) build_grid(c, c->scenes[s], nullptr);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->prof = prof_was;
+        if (best_out) *best_out = cur;
     });
 }
 
@@ -782,6 +1175,7 @@ ur_status ur_get_profile(ur_ctx *c, ur_profile *out) {
 ur_status ur_sync(ur_ctx *c) {
     return guarded(c, [&] {
         c->set_device();
+        c->no_capture("ur_sync");
         ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
         ck(cudaGetLastError(), "asynchronous error");
     });

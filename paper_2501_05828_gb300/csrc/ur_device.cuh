@@ -11,7 +11,9 @@
 namespace ur {
 
 constexpr int kMaxMed = 16;
-constexpr int kMaxBnd = 32;
+constexpr int kMaxBnd = 16;
+constexpr int kMaxScenes = 16;   // scenes traced together in one launch
+constexpr int kTracePool = 32;   // ray slots a tracer warp claims at once (item slot ranges are multiples)
 constexpr int kMaxNs = 8192;
 constexpr int kMaxSeg = 4096;      // safety bound on primary segments per path
 constexpr int kMaxCross = 64;      // boundaries a connection ray may cross
@@ -141,30 +143,41 @@ struct SceneP {
     const float4 *scat;     // (x, y, z, amplitude) by scatterer index
 };
 
+// One transmit of one scene: a contiguous range of ray slots (element-major,
+// padded to a multiple of the tracer's per-warp slot pool).
+struct ItemP {
+    uint64_t slot_begin;    // first slot of the item
+    uint64_t hash_begin;    // first path-hash index (debug output)
+    uint32_t n_rays, rays_per_el;
+    int scene, angle;
+    float sin_t, cos_t, inv_n;
+    uint32_t stream;        // Philox counter word identifying the transmit's random stream
+};
+
 struct TraceP {
-    SceneP S;
+    SceneP S[kMaxScenes];           // scene table (parameter space, indexed per lane)
+    int n_scenes;
     // array
     int n_el, n_s;
     float pitch, H, x_first;        // element 0 centre
     float K, t_last;                // pulse half-width and latest useful arrival (samples)
     float cos_am, cos_ac, am, ac;   // directivity (Eq. 13)
-    // transmits
-    int n_tx;
-    const float2 *txdir;            // (sin, cos) per transmit
-    const ff *delay;                // [n_tx][n_el] transmit delays (samples)
-    // rays
-    uint32_t n_rays, rays_per_el;
+    // work: items (transmit x scene) and their slots
+    const ItemP *items;
+    int n_items;
+    uint64_t n_slots;
+    const ff *delay;                // [n_angles][n_el] transmit delays (samples)
     uint2 key;
     int max_b;
-    float max_path, inv_n;
+    float max_path;
     int resolve_batch;              // lanes that must wait before a warp resolves segments
     // outputs
-    uint4 *arr;                     // (row, t_hi, t_lo, amp)
+    uint4 *arr;                     // (row, t_hi, t_lo, amp), row = item * n_el + element
     uint2 *arr_dbg;                 // (ray, event), debug only
     unsigned long long *arr_count;
     uint64_t arr_cap;
     unsigned long long *next_slot;  // work counter of the persistent tracer (zeroed per launch)
-    unsigned long long *path_hash;  // [n_tx][n_rays], debug only
+    unsigned long long *path_hash;  // per item and ray, debug only
     unsigned long long *stats;      // 6 counters, nullable
 };
 
@@ -207,18 +220,24 @@ void launch_grid_count(const GridBuildP &G, cudaStream_t s);
 void launch_scan_u32(const uint32_t *in, uint32_t *out, uint32_t *block_sums, uint32_t n, cudaStream_t s);
 void launch_grid_fill(const GridBuildP &G, cudaStream_t s);
 
+// Delay-and-sum of items (transmits) into images.  rf/quad hold [n_items][n_el][n_s];
+// image z compounds items img_items[img_begin[z] .. img_begin[z+1]); with
+// img_items == nullptr there is one image made of items 0..n_tx-1 and item k
+// uses angle k.  Outputs are [n_images][nz][nx].
 struct ImageP {
     const float *rf, *quad;
     int n_tx, n_el, n_s;
+    const int *img_items, *img_begin, *item_angle;
+    int n_images;
     const float *x_px, *z_px;
     int nx, nz;
     ff q;                   // fs / c_bf (samples per metre)
     ff x_first;             // element 0 centre
     float pitch;
-    const ff *tx_sin, *tx_cos, *tx_m;   // per transmit: sin, cos, min_e x_e sin
+    const ff *tx_sin, *tx_cos, *tx_m;   // per angle: sin, cos, min_e x_e sin
     float2 *iq;
     float *env, *db;
-    unsigned int *env_max;  // float bits
+    unsigned int *env_max;  // float bits, one per image
     float dyn_range_db;
 };
 void launch_das(const ImageP &I, cudaStream_t s);

@@ -26,18 +26,23 @@ __global__ void __launch_bounds__(256) k_das(const ImageP I) {
     __syncthreads();
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
     const int ix = blockIdx.y;
+    const int img = blockIdx.z;
+    const int q0 = I.img_items ? I.img_begin[img] : 0;
+    const int q1 = I.img_items ? I.img_begin[img + 1] : I.n_tx;
     float env = 0.f;
     if (iz < I.nz) {
         const float x = I.x_px[ix], z = I.z_px[iz];
         const ff zz = ff_sqr_f(z);
         const float top = (float)(I.n_s - 1);
         float sr = 0.f, si = 0.f;
-        for (int k = 0; k < I.n_tx; ++k) {
+        for (int qi = q0; qi < q1; ++qi) {
+            const int item = I.img_items ? I.img_items[qi] : qi;
+            const int k = I.img_items ? I.item_angle[item] : item;
             // transmit delay: plane wave reaches (x, z)
             ff T = ff_add(ff_mul_f(x, I.tx_sin[k]), ff_mul_f(z, I.tx_cos[k]));
             T = ff_mul(ff_add(T, ff_neg(I.tx_m[k])), I.q);
-            const float *rf = I.rf + (size_t)k * I.n_el * I.n_s;
-            const float *qd = I.quad + (size_t)k * I.n_el * I.n_s;
+            const float *rf = I.rf + (size_t)item * I.n_el * I.n_s;
+            const float *qd = I.quad + (size_t)item * I.n_el * I.n_s;
             for (int e = 0; e < I.n_el; ++e) {
                 const ff dx = ff_add_f(ff_neg(s_xe[e]), x);
                 const ff r2 = ff_add(zz, ff_mul(dx, dx));
@@ -53,35 +58,39 @@ __global__ void __launch_bounds__(256) k_das(const ImageP I) {
                 si += b0 * (1.f - f) + b1 * f;
             }
         }
-        const size_t px = (size_t)iz * I.nx + ix;
+        const size_t px = ((size_t)img * I.nz + iz) * I.nx + ix;
         if (I.iq) I.iq[px] = make_float2(sr, si);
         env = sqrtf(sr * sr + si * si);
         if (I.env) I.env[px] = env;
     }
     const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(env));
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(I.env_max, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&I.env_max[img], m);
 }
 
 __global__ void k_log(const ImageP I) {
     const int n = I.nx * I.nz;
-    const float mx = __uint_as_float(*I.env_max);
+    const int img = blockIdx.y;
+    const float mx = __uint_as_float(I.env_max[img]);
+    const float *env = I.env + (size_t)img * n;
+    float *db = I.db + (size_t)img * n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const float e = I.env[p];
+        const float e = env[p];
         float v = (mx > 0.f && e > 0.f) ? 20.f * log10f(e / mx) : -I.dyn_range_db;
-        I.db[p] = fmaxf(v, -I.dyn_range_db);
+        db[p] = fmaxf(v, -I.dyn_range_db);
     }
 }
 
 }  // namespace
 
 void launch_das(const ImageP &I, cudaStream_t s) {
-    dim3 grid((I.nz + 255) / 256, I.nx);
+    dim3 grid((I.nz + 255) / 256, I.nx, I.img_items ? I.n_images : 1);
     k_das<<<grid, 256, I.n_el * sizeof(ff), s>>>(I);
 }
 
 void launch_log(const ImageP &I, cudaStream_t s) {
     const int n = I.nx * I.nz;
-    k_log<<<min(4096, (n + 255) / 256), 256, 0, s>>>(I);
+    dim3 grid(min(4096, (n + 255) / 256), I.img_items ? I.n_images : 1);
+    k_log<<<grid, 256, 0, s>>>(I);
 }
 
 }  // namespace ur

@@ -166,7 +166,7 @@ struct Counters {
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kQueue = 64;     // scatterer-event ring per warp (power of two, >= 63 entries needed)
-constexpr int kPool = 32;      // ray slots a warp claims per atomic
+constexpr int kPool = kTracePool;
 
 enum { kInSeg = 0, kSegDone = 1, kNeedRay = 2, kFinished = 3 };
 
@@ -181,8 +181,8 @@ struct Lane {
     float3 o, d;
     ff t;
     float w, L;
-    int med, b, prev;
-    uint32_t i, k;
+    int med, b, prev, scene;
+    uint32_t i, item, stream;
     uint64_t h;
     float seg;
     int hit;
@@ -197,7 +197,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x &
 // Segment from the current position to the nearest boundary (clipped by the
 // path-length budget); set up the grid walk over the part inside the grid box.
 __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
-    const SceneP &S = P.S;
+    const SceneP &S = P.S[R.scene];
     float th;
     R.hit = nearest(S, R.o, R.d, R.prev, true, th);
     R.seg = th;
@@ -256,27 +256,28 @@ __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters
 
 template <bool DBG>
 __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Counters &cn) {
-    if (DBG) P.path_hash[(uint64_t)R.k * P.n_rays + R.i] = fnv_step(R.h, 0x20000u | (uint32_t)reason);
+    if (DBG) P.path_hash[P.items[R.item].hash_begin + R.i] = fnv_step(R.h, 0x20000u | (uint32_t)reason);
     cn.rays++;
     R.state = kNeedRay;
 }
 
-// Emission (Eq. 6) of ray i of transmit k from element e.
-__device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t i, uint32_t k, uint32_t e,
-                                          Counters &cn) {
-    const uint4 x = philox(make_uint4(i, k, 0u, 0u), P.key);
-    const float2 sc = P.txdir[k];
+// Emission (Eq. 6) of ray i of item `item` (a transmit of one scene) from element e.
+__device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &IT, uint32_t i,
+                                          uint32_t e, Counters &cn) {
+    const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
-    R.d = make_float3(sc.x, 0.f, sc.y);
-    R.t = P.delay[k * (uint32_t)P.n_el + e];
-    R.w = sc.y * P.inv_n;
-    R.med = P.S.med_array;
+    R.d = make_float3(IT.sin_t, 0.f, IT.cos_t);
+    R.t = P.delay[(uint32_t)IT.angle * (uint32_t)P.n_el + e];
+    R.w = IT.cos_t * IT.inv_n;
+    R.scene = IT.scene;
+    R.med = P.S[IT.scene].med_array;
     R.b = 0;
     R.prev = -1;
     R.L = 0.f;
     R.i = i;
-    R.k = k;
+    R.item = item;
+    R.stream = IT.stream;
     R.h = kFnvOffset;
     start_segment(P, R, cn);
 }
@@ -286,7 +287,7 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t i, 
 // budget, or a boundary interaction (Eqs. 7-11) and the next segment.
 template <bool DBG>
 __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
-    const SceneP &S = P.S;
+    const SceneP &S = P.S[R.scene];
     const Medium &M = S.med[R.med];
     R.t = ff_add(R.t, ff_mul_f(R.seg, M.slow));
     R.w *= expf(-M.a * R.seg);
@@ -305,7 +306,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
             if (el > P.n_el - 1) el = P.n_el - 1;
             const float fd = directivity(P, -R.d.z);
             if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
-                emit<DBG>(P, R.k * (uint32_t)P.n_el + (uint32_t)el, R.t, R.w * fd, R.i,
+                emit<DBG>(P, R.item * (uint32_t)P.n_el + (uint32_t)el, R.t, R.w * fd, R.i,
                           0x80000000u | ((uint32_t)R.b << 24));
                 cn.arrivals++;
             }
@@ -342,7 +343,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         R.d = dr;
     } else {
         const float Rr = r * r;
-        const uint4 y = philox(make_uint4(R.i, R.k, 1u | ((uint32_t)R.b << 8), 0u), P.key);
+        const uint4 y = philox(make_uint4(R.i, R.stream, 1u | ((uint32_t)R.b << 8), 0u), P.key);
         if (u24(y.x) < Rr) {
             branch = 0;
             R.w *= r / Rr;
@@ -369,10 +370,12 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
     const float tca = Q.tca[slot], w = Q.w[slot];
     const ff t = {Q.t_hi[slot], Q.t_lo[slot]};
-    const uint32_t k = kmb >> 16;
+    const uint32_t item = kmb >> 16;
     const int med = (int)((kmb >> 8) & 0xffu), b = (int)(kmb & 0xffu);
-    const float4 q = P.S.scat[j];
-    const uint4 x = philox(make_uint4(ray, k, 2u | ((uint32_t)b << 8), j), P.key);
+    const ItemP &IT = P.items[item];
+    const SceneP &S = P.S[IT.scene];
+    const float4 q = S.scat[j];
+    const uint4 x = philox(make_uint4(ray, IT.stream, 2u | ((uint32_t)b << 8), j), P.key);
     const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     const float xe = P.x_first + (float)e * P.pitch;
     const float vx = xe - q.x;
@@ -382,13 +385,13 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     cn.connections++;
     ff tc;
     float att;
-    const float fac = connection(P.S, make_float3(q.x, q.y, q.z), med, xe, tc, att);
+    const float fac = connection(S, make_float3(q.x, q.y, q.z), med, xe, tc, att);
     if (fac == 0.f) return;
-    const Medium &M = P.S.med[med];
+    const Medium &M = S.med[med];
     const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
     if (ff_gt(ta, P.t_last)) return;
     const float amp = w * expf(-M.a * tca) * q.w * (float)P.n_el * fd * fac * expf(-att);
-    emit<DBG>(P, k * (uint32_t)P.n_el + e, ta, amp, ray, ((uint32_t)b << 24) | j);
+    emit<DBG>(P, item * (uint32_t)P.n_el + e, ta, amp, ray, ((uint32_t)b << 24) | j);
     cn.arrivals++;
 }
 
@@ -400,16 +403,16 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
 template <bool DBG>
-__global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P, uint64_t n_slots) {
+__global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const SceneP &S = P.S;
+    const uint64_t n_slots = P.n_slots;
     Counters cn = {0, 0, 0, 0, 0, 0};
     Lane R;
     R.state = kNeedRay;
     uint64_t pool_next = 0;
-    uint32_t pool_cnt = 0;
+    uint32_t pool_cnt = 0, pool_item = 0;
     bool pool_dry = false;
     int qhead = 0, qn = 0;   // warp-uniform ring bookkeeping
 
@@ -428,8 +431,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                         if (lane == 0) base = atomicAdd(P.next_slot, (unsigned long long)kPool);
                         base = __shfl_sync(0xffffffffu, base, 0);
                         pool_next = base;
-                        pool_cnt = base >= n_slots ? 0u : (uint32_t)((n_slots - base) < (uint64_t)kPool ? (n_slots - base) : (uint64_t)kPool);
+                        pool_cnt = base >= n_slots ? 0u : (uint32_t)kPool;
                         pool_dry = pool_cnt == 0;
+                        if (!pool_dry) {   // the item holding this pool (item slot ranges are pool-aligned)
+                            int lo = 0, hi = P.n_items - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (P.items[mid].slot_begin <= base) lo = mid; else hi = mid - 1;
+                            }
+                            pool_item = (uint32_t)lo;
+                        }
                     }
                     if (pool_dry) {
                         if (R.state == kNeedRay) R.state = kFinished;
@@ -444,12 +455,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 need = __ballot_sync(0xffffffffu, R.state == kNeedRay && my_slot == ~0ull);
             }
             if (my_slot != ~0ull) {
-                const uint32_t m = (uint32_t)(my_slot % P.rays_per_el);
-                const uint64_t qq = my_slot / P.rays_per_el;
-                const uint32_t e = (uint32_t)(qq % (uint64_t)P.n_el);
-                const uint32_t k = (uint32_t)(qq / (uint64_t)P.n_el);
-                const uint32_t i = m * (uint32_t)P.n_el + e;
-                if (i < P.n_rays) start_ray(P, R, i, k, e, cn);
+                const ItemP &IT = P.items[pool_item];
+                const uint64_t local = my_slot - IT.slot_begin;
+                const uint32_t m = (uint32_t)(local % IT.rays_per_el);
+                const uint64_t e = local / IT.rays_per_el;
+                const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
+                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray(P, R, pool_item, IT, i, (uint32_t)e, cn);
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
@@ -457,6 +468,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
 
         // (2) one grid cell per active lane
         const bool active = R.state == kInSeg;
+        const SceneP &S = P.S[active ? R.scene : 0];
         uint32_t r0 = 0, cnt = 0;
         int axis = 0;
         float t_exit = 0.f, t_acc = 0.f;
@@ -477,7 +489,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
             cnt = S.cell_start[cell + 1] - r0;
         }
         const uint32_t maxc = __reduce_max_sync(0xffffffffu, cnt);
-        const uint32_t kmb = (R.k << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b;
+        const uint32_t kmb = (R.item << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b;
         float4 q_next = make_float4(0.f, 0.f, 0.f, 0.f);
         if (cnt > 0) q_next = S.refs[r0];
         for (uint32_t r = 0; r < maxc; ++r) {
@@ -562,11 +574,10 @@ int trace_occupancy(int block, bool debug) {
 }
 
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
-    const uint64_t n_slots = (uint64_t)P.n_tx * (uint64_t)P.n_el * (uint64_t)P.rays_per_el;
     if (debug)
-        k_trace<true><<<grid, block, 0, s>>>(P, n_slots);
+        k_trace<true><<<grid, block, 0, s>>>(P);
     else
-        k_trace<false><<<grid, block, 0, s>>>(P, n_slots);
+        k_trace<false><<<grid, block, 0, s>>>(P);
 }
 
 }  // namespace ur
