@@ -49,7 +49,7 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), per primary ray, valid only while the tracer sources
 # hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "080e7e8fc6b1d2d8", "bytes_per_ray": 2.825, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+TRACE_TRAFFIC = {"src_sha": "9820680b5a9320ed", "bytes_per_ray": 10.10, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
 
 
 def tracer_sha():
@@ -316,6 +316,97 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+BATCH_WORKLOAD = ("batched: 8 jittered layered phantoms (skin +-1 mm, fat +-2 mm, bone r U(3,10) mm, 10k-200k "
+                  "scatterers) x 31 plane waves -15..15 deg, log-uniform 1e6-3e7 rays per transmit, one persistent "
+                  "launch replayed as a CUDA graph, per-scene coherent compounding to 512x256, 60 dB")
+
+
+def run_batched(args, rank, world, local_rank):
+    """All 248 (scene, transmit) items traced, deposited and beamformed per step
+    through one captured CUDA graph."""
+    import torch
+
+    import paper_2501_05828_gb300 as ur
+    import phantoms
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    side = torch.cuda.Stream(dev)
+    scenes = [phantoms.batched_variant(s) for s in range(1, 9)]
+    scale = args.batch_scale
+    with torch.cuda.stream(side):
+        sim = ur.Simulator(local_rank)
+        w0 = scenes[0]
+        sim.set_array(w0["array"])
+        sim.set_plane_waves(w0["angles"])
+        for slot, w in enumerate(scenes):
+            s = w["scene"]
+            sim.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], s["scatterers"], s["r_s"], slot)
+        items = [(slot, k, max(1, int(w["n_rays"] * scale)), (slot << 16) | k)
+                 for slot, w in enumerate(scenes) for k in range(len(w["angles"]))]
+        total_rays = sum(it[2] for it in items)
+        sim.batch_plan(items, w0["x_px"], w0["z_px"], capacity=int(0.35 * total_rays) + 4096)
+        n_items = len(items)
+        A = w0["array"]
+        rf = torch.empty((n_items, A["n_el"], A["n_s"]), dtype=torch.float32, device=dev)
+        quad = torch.empty_like(rf)
+        db = torch.empty((len(scenes), w0["z_px"].size, w0["x_px"].size), dtype=torch.float32, device=dev)
+        seed = rank
+        for _ in range(args.warmup):
+            sim.batch_trace(seed, 8, 0.2, rf=rf, quad=quad)
+            sim.batch_beamform(rf, quad, 60.0, db=db)
+        n_arr, st = sim.batch_status()
+        # one profiled direct run for the tracer's own launch time
+        sim.set_profiling(True)
+        sim.batch_trace(seed, 8, 0.2, rf=rf, quad=quad)
+        sim.batch_beamform(rf, quad, 60.0, db=db)
+        prof = sim.profile()
+        sim.set_profiling(False)
+        side.synchronize()
+        sim.graph_begin()
+        sim.batch_trace(seed, 8, 0.2, rf=rf, quad=quad)
+        sim.batch_beamform(rf, quad, 60.0, db=db)
+        sim.graph_end()
+        sim.graph_launch()
+        side.synchronize()
+        clocks = ClockSampler(local_rank) if rank == 0 else None
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(side)
+            sim.graph_launch()
+            ev[k][1].record(side)
+        side.synchronize()
+        clk = clocks.stop() if clocks else None
+        n_arr2, _ = sim.batch_status()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    trace_ms = prof["trace"][0] / max(prof["trace"][2], 1)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = trace_flops(st) / (trace_ms * 1e-3) / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": total_rays / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "items": n_items, "rays_per_step": total_rays,
+                       "ray_scale": scale, "l2": "flushed before every timed step (256 MiB write, untimed)"},
+            "frames_per_s": n_items / (ms * 1e-3), "images_per_s": len(scenes) / (ms * 1e-3),
+            "arrivals_per_step": n_arr2, "stats_per_step": st,
+            "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
+            "roofline": {"bound": "alu", "kernel": "k_trace", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
+            "gpu_launches": 7 * args.steps, "clocks": clk}), flush=True)
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,6 +417,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
+    ap.add_argument("--workload", default="layered", choices=("layered", "batched"))
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -333,6 +426,8 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args, rank)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
