@@ -51,7 +51,8 @@ class Scene(C.Structure):
                 ("n_bnd", C.c_int32), ("bnd_kind", C.POINTER(C.c_int32)),
                 ("bnd_p", C.POINTER(C.c_float)), ("bnd_med", C.POINTER(C.c_int32)),
                 ("med_array", C.c_int32), ("z_max", C.c_float),
-                ("n_scat", C.c_int32), ("scat", C.POINTER(C.c_float)), ("r_s", C.c_float)]
+                ("n_scat", C.c_int32), ("scat", C.POINTER(C.c_float)), ("r_s", C.c_float),
+                ("med_sampling", C.POINTER(C.c_float))]
 
 
 class Array(C.Structure):
@@ -110,6 +111,8 @@ def lib():
             L.or_connection.restype = C.c_double
             L.or_connection.argtypes = [C.POINTER(Scene), C.POINTER(Array), dp, C.c_int32,
                                         C.c_double, dp, dp]
+            L.or_grad.restype = C.c_int
+            L.or_grad.argtypes = [C.POINTER(Scene), C.POINTER(Array), C.POINTER(TraceCfg), dp, dp, dp, dp, C.c_int]
             _lib = L
     return _lib
 
@@ -147,10 +150,12 @@ def make_scene(scene):
         sc_buf = np.zeros((1, 4), np.float32)
     else:
         sc_buf = sc
+    ms = scene.get("media_sampling")
+    ms = None if ms is None else np.ascontiguousarray(ms, dtype=np.float32).reshape(-1, 4)
     s = Scene(med.shape[0], _fp(med), len(scene["boundaries"]), _ip(kinds), _fp(bp), _ip(bm),
               int(scene["med_array"]), float(scene["z_max"]), sc.shape[0], _fp(sc_buf),
-              float(scene["r_s"]))
-    return s, _Keep(med=med, kinds=kinds, bp=bp, bm=bm, sc=sc_buf)
+              float(scene["r_s"]), _fp(ms) if ms is not None else None)
+    return s, _Keep(med=med, kinds=kinds, bp=bp, bm=bm, sc=sc_buf, ms=ms)
 
 
 def make_array(arr):
@@ -198,6 +203,31 @@ def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_beg
     del keep_s
     stats = {f: int(getattr(st, f)) for f, _ in Stats._fields_}
     return out[:n].copy(), topo_arr, stats
+
+
+def grad(scene, array, angles, n_rays, seed, max_bounces, g_rf, g_q, max_path=0.2, ray_begin=0, ray_end=None,
+         threads=None):
+    """Pathwise gradient of L (given dL/drf, dL/dquad) w.r.t. the media (c, Z, alpha) and the
+    scatterer amplitudes: returns (grad_media [n_med, 3], grad_amp [n_scat])."""
+    if ray_end is None:
+        ray_end = n_rays
+    s, keep = make_scene(scene)
+    a = make_array(array)
+    ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
+    cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed), int(max_bounces),
+                   float(max_path), MODE_MC)
+    gr = np.ascontiguousarray(g_rf, dtype=np.float64)
+    gq = np.ascontiguousarray(g_q, dtype=np.float64)
+    n_med = len(scene["media"])
+    gm = np.zeros((n_med, 3), np.float64)
+    n_scat = len(scene["scatterers"])
+    ga = np.zeros(max(n_scat, 1), np.float64)
+    rc = lib().or_grad(C.byref(s), C.byref(a), C.byref(cfg), _dp(gr), _dp(gq), _dp(gm), _dp(ga),
+                       int(threads or (os.cpu_count() or 1)))
+    del keep
+    if rc != 0:
+        raise ValueError("or_grad rejected its arguments")
+    return gm, ga[:n_scat]
 
 
 def deposit(array, n_tx, arrivals):

@@ -145,6 +145,7 @@ typedef struct {
     const or_array *ar;
     const or_trace_cfg *cfg;
     double *c, *Z, *a, *slow;   /* per medium; slow in samples per metre */
+    double *cs, *Zs;            /* per medium: c and Z deciding the Monte Carlo branches */
     double *delay;              /* [n_tx][n_el] transmit delays in samples */
     double *sin_t, *cos_t;      /* per transmit */
     double x0, pitch, H;        /* centre of element 0, pitch, elevation height */
@@ -420,21 +421,29 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
         outward_normal(C, hit, o, n_out);
         int m2 = far_medium(C, hit, d, n_out);
         int tir = or_interface(d, n_out, C->c[med], C->Z[med], C->c[m2], C->Z[m2], dr, dt, &r, &R);
+        /* the branch is drawn with the sampling media (the same media unless overridden) */
+        double drs[3], dts[3], rs = r, Rs = R;
+        int tir_s = tir;
+        if (sc->med_sampling)
+            tir_s = or_interface(d, n_out, C->cs[med], C->Zs[med], C->cs[m2], C->Zs[m2], drs, dts, &rs, &Rs);
         J->st.interactions++;
         int branch;
-        if (tir) {
+        if (tir_s && cfg->mode == OR_MODE_MC) {
+            branch = 2;
+            memcpy(d, dr, sizeof dr);
+        } else if (tir) {
             branch = 2;
             memcpy(d, dr, sizeof dr);
         } else if (cfg->mode == OR_MODE_MC) {
             uint32_t x[4];
             draw(cfg->seed, J->i, (uint32_t)J->k, 1u | ((uint32_t)b << 8), 0u, x);
-            if (u24(x[0]) < R) {            /* reflect if y < A_r^2 */
+            if (u24(x[0]) < Rs) {           /* reflect if y < A_r^2 */
                 branch = 0;
-                w *= r / R;
+                w *= r / Rs;
                 memcpy(d, dr, sizeof dr);
             } else {
                 branch = 1;
-                w *= sqrt(1.0 - R) / (1.0 - R);
+                w *= sqrt(1.0 - R) / (1.0 - Rs);
                 memcpy(d, dt, sizeof dt);
                 med = m2;
             }
@@ -480,13 +489,15 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
     memset(C, 0, sizeof *C);
     C->sc = sc; C->ar = ar; C->cfg = cfg;
     int nm = sc->n_med;
-    C->c = (double *)malloc(sizeof(double) * 4 * nm);
-    C->Z = C->c + nm; C->a = C->Z + nm; C->slow = C->a + nm;
+    C->c = (double *)malloc(sizeof(double) * 6 * nm);
+    C->Z = C->c + nm; C->a = C->Z + nm; C->slow = C->a + nm; C->cs = C->slow + nm; C->Zs = C->cs + nm;
     for (int m = 0; m < nm; ++m) {
         C->c[m] = sc->med[4 * m + 0];
         C->Z[m] = sc->med[4 * m + 1];
         C->a[m] = or_np_per_m(sc->med[4 * m + 2], ar->f0);
         C->slow[m] = (double)ar->fs / C->c[m];
+        C->cs[m] = sc->med_sampling ? sc->med_sampling[4 * m + 0] : C->c[m];
+        C->Zs[m] = sc->med_sampling ? sc->med_sampling[4 * m + 1] : C->Z[m];
     }
     int nt = cfg ? cfg->n_tx : 0;
     C->delay = (double *)malloc(sizeof(double) * ((size_t)nt * ar->n_el + 2 * (size_t)nt + 1));
@@ -688,4 +699,383 @@ void or_envelope_log(const double *img_re, const double *img_im, int64_t n_px,
         double v = (mx > 0.0 && env[q] > 0.0) ? 20.0 * log10(env[q] / mx) : -dyn_range_db;
         db[q] = v < -dyn_range_db ? -dyn_range_db : v;
     }
+}
+
+/* ==================================================================== *
+ * Pathwise gradient with FP64 dual numbers (forward mode).              *
+ * Parameters: index 3m + 0 = c_m, 3m + 1 = Z_m, 3m + 2 = alpha_m.       *
+ * The path is the Monte Carlo path of trace_ray; branch decisions and   *
+ * the branch probabilities dividing the weights are held at their       *
+ * values (they carry no derivative), everything else is differentiated, *
+ * including hit distances, normals and refracted directions.            *
+ * ==================================================================== */
+
+#define OR_NP 12
+
+typedef struct { double v, d[OR_NP]; } dnum;
+typedef struct { dnum x, y, z; } dvec;
+
+static dnum dn_c(double v) { dnum r; r.v = v; memset(r.d, 0, sizeof r.d); return r; }
+static dnum dn_add(dnum a, dnum b) { for (int q = 0; q < OR_NP; ++q) a.d[q] += b.d[q]; a.v += b.v; return a; }
+static dnum dn_sub(dnum a, dnum b) { for (int q = 0; q < OR_NP; ++q) a.d[q] -= b.d[q]; a.v -= b.v; return a; }
+static dnum dn_scale(dnum a, double s) { for (int q = 0; q < OR_NP; ++q) a.d[q] *= s; a.v *= s; return a; }
+static dnum dn_mul(dnum a, dnum b)
+{
+    dnum r;
+    r.v = a.v * b.v;
+    for (int q = 0; q < OR_NP; ++q) r.d[q] = a.d[q] * b.v + a.v * b.d[q];
+    return r;
+}
+static dnum dn_div(dnum a, dnum b)
+{
+    dnum r;
+    r.v = a.v / b.v;
+    for (int q = 0; q < OR_NP; ++q) r.d[q] = (a.d[q] - r.v * b.d[q]) / b.v;
+    return r;
+}
+static dnum dn_sqrt(dnum a)
+{
+    dnum r;
+    r.v = sqrt(a.v);
+    for (int q = 0; q < OR_NP; ++q) r.d[q] = a.d[q] / (2.0 * r.v);
+    return r;
+}
+static dnum dn_exp(dnum a)
+{
+    dnum r;
+    r.v = exp(a.v);
+    for (int q = 0; q < OR_NP; ++q) r.d[q] = a.d[q] * r.v;
+    return r;
+}
+static dnum dn_acos(dnum a)
+{
+    dnum r;
+    r.v = acos(a.v);
+    double s = -1.0 / sqrt(1.0 - a.v * a.v);
+    for (int q = 0; q < OR_NP; ++q) r.d[q] = a.d[q] * s;
+    return r;
+}
+static dvec dv_c(double x, double y, double z) { dvec r = {dn_c(x), dn_c(y), dn_c(z)}; return r; }
+static dvec dv_add(dvec a, dvec b) { dvec r = {dn_add(a.x, b.x), dn_add(a.y, b.y), dn_add(a.z, b.z)}; return r; }
+static dvec dv_sub(dvec a, dvec b) { dvec r = {dn_sub(a.x, b.x), dn_sub(a.y, b.y), dn_sub(a.z, b.z)}; return r; }
+static dvec dv_smul(dnum s, dvec a) { dvec r = {dn_mul(s, a.x), dn_mul(s, a.y), dn_mul(s, a.z)}; return r; }
+static dnum dv_dot(dvec a, dvec b) { return dn_add(dn_add(dn_mul(a.x, b.x), dn_mul(a.y, b.y)), dn_mul(a.z, b.z)); }
+static dvec dv_unit(dvec a)
+{
+    dnum l = dn_sqrt(dv_dot(a, a));
+    dvec r = {dn_div(a.x, l), dn_div(a.y, l), dn_div(a.z, l)};
+    return r;
+}
+static void dv_val(dvec a, double out[3]) { out[0] = a.x.v; out[1] = a.y.v; out[2] = a.z.v; }
+
+typedef struct {
+    const ctx_t *C;
+    dnum *c, *Z, *a, *slow;         /* media as dual numbers */
+    const double *g_rf, *g_q;
+    double grad[OR_NP];
+    double *grad_amp;               /* thread-private [n_scat] */
+    double s_n, K, om;              /* pulse width (samples), half-width, rad per sample */
+} gctx_t;
+
+/* dL/d amplitude and dL/d time of one arrival, from dL/dA over its taps. */
+static void arrival_sens(const gctx_t *G, int k, int e, double t, double amp, double *g_amp, double *g_t)
+{
+    const or_array *ar = G->C->ar;
+    const double *gr = G->g_rf + ((size_t)k * ar->n_el + e) * ar->n_s;
+    const double *gq = G->g_q + ((size_t)k * ar->n_el + e) * ar->n_s;
+    long n0 = (long)ceil(t - G->K), n1 = (long)floor(t + G->K);
+    if (n0 < 0) n0 = 0;
+    if (n1 > ar->n_s - 1) n1 = ar->n_s - 1;
+    double sa = 0.0, st = 0.0;
+    for (long n = n0; n <= n1; ++n) {
+        double tau = (double)n - t;
+        double g = exp(-tau * tau / (2.0 * G->s_n * G->s_n));
+        double sn = sin(G->om * tau), cs = cos(G->om * tau);
+        double p_re = g * sn, p_im = -g * cs;
+        double dp_re = g * (G->om * cs - tau / (G->s_n * G->s_n) * sn);   /* d/dtau */
+        double dp_im = g * (G->om * sn + tau / (G->s_n * G->s_n) * cs);
+        sa += gr[n] * p_re + gq[n] * p_im;
+        st -= amp * (gr[n] * dp_re + gq[n] * dp_im);                      /* d/dt = -d/dtau */
+    }
+    *g_amp = sa;
+    *g_t = st;
+}
+
+static void accumulate(gctx_t *G, int k, int e, dnum t, dnum amp_wo_a, double a_j, int j)
+{
+    double g_amp, g_t;
+    double amp = amp_wo_a.v * a_j;
+    arrival_sens(G, k, e, t.v, amp, &g_amp, &g_t);
+    for (int q = 0; q < OR_NP; ++q) G->grad[q] += g_amp * a_j * amp_wo_a.d[q] + g_t * t.d[q];
+    if (j >= 0) G->grad_amp[j] += g_amp * amp_wo_a.v;
+}
+
+/* Dual hit distance along o + t d for primitive `hit` (chosen on values). */
+static dnum dual_hit(const gctx_t *G, int hit, dvec o, dvec d, int skip)
+{
+    const ctx_t *C = G->C;
+    if (hit == C->top) return dn_div(dn_scale(o.z, -1.0), d.z);
+    if (hit == C->bot) return dn_div(dn_sub(dn_c(C->sc->z_max), o.z), d.z);
+    const float *q = &C->sc->bnd_p[4 * hit];
+    int kind = C->sc->bnd_kind[hit];
+    if (kind == OR_PLANE_Z) return dn_div(dn_sub(dn_c(q[0]), o.z), d.z);
+    if (kind == OR_SPHERE) {
+        dvec oc = dv_sub(o, dv_c(q[0], q[1], q[2]));
+        dnum b = dv_dot(oc, d);
+        if (hit == skip) return dn_scale(b, -2.0);
+        dvec f = dv_sub(oc, dv_smul(b, d));
+        dnum s = dn_sqrt(dn_sub(dn_c((double)q[3] * q[3]), dv_dot(f, f)));
+        dnum t = dn_sub(dn_scale(b, -1.0), s);
+        if (!(t.v > OR_TMIN)) t = dn_add(dn_scale(b, -1.0), s);
+        return t;
+    }
+    dnum ocx = dn_sub(o.x, dn_c(q[0])), ocz = dn_sub(o.z, dn_c(q[1]));
+    dnum a = dn_add(dn_mul(d.x, d.x), dn_mul(d.z, d.z));
+    dnum b = dn_div(dn_add(dn_mul(ocx, d.x), dn_mul(ocz, d.z)), a);
+    if (hit == skip) return dn_scale(b, -2.0);
+    dnum fx = dn_sub(ocx, dn_mul(b, d.x)), fz = dn_sub(ocz, dn_mul(b, d.z));
+    dnum disc = dn_div(dn_sub(dn_c((double)q[2] * q[2]), dn_add(dn_mul(fx, fx), dn_mul(fz, fz))), a);
+    dnum s = dn_sqrt(disc);
+    dnum t = dn_sub(dn_scale(b, -1.0), s);
+    if (!(t.v > OR_TMIN)) t = dn_add(dn_scale(b, -1.0), s);
+    return t;
+}
+
+static dvec dual_normal(const gctx_t *G, int p, dvec h)
+{
+    const float *q = &G->C->sc->bnd_p[4 * p];
+    int kind = G->C->sc->bnd_kind[p];
+    if (kind == OR_PLANE_Z) return dv_c(0.0, 0.0, 1.0);
+    if (kind == OR_SPHERE) return dv_unit(dv_sub(h, dv_c(q[0], q[1], q[2])));
+    dvec v = {dn_sub(h.x, dn_c(q[0])), dn_c(0.0), dn_sub(h.z, dn_c(q[1]))};
+    return dv_unit(v);
+}
+
+/* Connection ray p -> element centre with dual factors, time and attenuation
+ * (its geometry does not depend on the parameters). */
+static dnum dual_connection(const gctx_t *G, const double p[3], int med, double x_e, dnum *t_out, dnum *att_out)
+{
+    const ctx_t *C = G->C;
+    double o[3] = {p[0], p[1], p[2]};
+    double w[3] = {x_e - p[0], -p[1], -p[2]};
+    double rem = sqrt(dot3(w, w));
+    w[0] /= rem; w[1] /= rem; w[2] /= rem;
+    dnum fac = dn_c(1.0), t = dn_c(0.0), att = dn_c(0.0);
+    int m = med, skip = -1;
+    for (int it = 0; it < OR_MAX_CROSS; ++it) {
+        double th;
+        int hit = nearest_boundary(C, o, w, skip, 0, &th);
+        if (hit < 0 || th >= rem) {
+            t = dn_add(t, dn_scale(G->slow[m], rem));
+            att = dn_add(att, dn_scale(G->a[m], rem));
+            break;
+        }
+        t = dn_add(t, dn_scale(G->slow[m], th));
+        att = dn_add(att, dn_scale(G->a[m], th));
+        double h[3] = {o[0] + th * w[0], o[1] + th * w[1], o[2] + th * w[2]};
+        if (C->sc->bnd_kind[hit] == OR_PLANE_Z) h[2] = C->sc->bnd_p[4 * hit];
+        double n_out[3];
+        outward_normal(C, hit, h, n_out);
+        int m2 = far_medium(C, hit, w, n_out);
+        double ci = fabs(dot3(w, n_out));
+        dnum eta = dn_div(G->c[m2], G->c[m]);
+        dnum k = dn_sub(dn_c(1.0), dn_mul(dn_mul(eta, eta), dn_c(1.0 - ci * ci)));
+        if (k.v < 0.0) return dn_c(0.0);
+        dnum ct = dn_sqrt(k);
+        dnum num = dn_sub(dn_scale(G->Z[m2], ci), dn_mul(G->Z[m], ct));
+        dnum den = dn_add(dn_scale(G->Z[m2], ci), dn_mul(G->Z[m], ct));
+        dnum r = dn_div(num, den);
+        fac = dn_mul(fac, dn_sqrt(dn_sub(dn_c(1.0), dn_mul(r, r))));
+        m = m2;
+        o[0] = h[0]; o[1] = h[1]; o[2] = h[2];
+        rem -= th;
+        skip = hit;
+    }
+    *t_out = t;
+    *att_out = att;
+    return fac;
+}
+
+static dnum dual_directivity(const ctx_t *C, dnum cos_a)
+{
+    double al = acos(cos_a.v);
+    if (al > C->ac) return dn_c(0.0);
+    if (al > C->am) return dn_scale(dn_sub(dn_c(C->ac), dn_acos(cos_a)), 1.0 / (C->ac - C->am));
+    return dn_c(1.0);
+}
+
+static void grad_ray(gctx_t *G, uint32_t i, int k)
+{
+    const ctx_t *C = G->C;
+    const or_scene *sc = C->sc;
+    const or_array *ar = C->ar;
+    const or_trace_cfg *cfg = C->cfg;
+    int e = (int)(i % (uint32_t)ar->n_el);
+    uint32_t x[4];
+    draw(cfg->seed, i, (uint32_t)k, 0u, 0u, x);
+    dvec o = dv_c(elem_x(C, e) + (u24(x[0]) - 0.5) * C->pitch, (u24(x[1]) - 0.5) * C->H, 0.0);
+    dvec d = dv_c(C->sin_t[k], 0.0, C->cos_t[k]);
+    dnum t = dn_c(C->delay[k * ar->n_el + e]);
+    dnum w = dn_c(C->cos_t[k] / (double)cfg->n_rays);
+    dnum L = dn_c(0.0);
+    int med = sc->med_array, b = 0, prev = -1;
+    double r2 = (double)sc->r_s * sc->r_s;
+    for (int guard = 0; guard < OR_MAX_SEG; ++guard) {
+        double ov[3], dv[3], th;
+        dv_val(o, ov);
+        dv_val(d, dv);
+        int hit = nearest_boundary(C, ov, dv, prev, 1, &th);
+        dnum seg = hit >= 0 ? dual_hit(G, hit, o, d, prev) : dn_c(th);
+        int clipped = 0;
+        if (L.v + seg.v > (double)cfg->max_path) { seg = dn_sub(dn_c(cfg->max_path), L); clipped = 1; }
+        /* scatterer events on the segment */
+        for (int j = 0; j < sc->n_scat; ++j) {
+            const float *s = &sc->scat[4 * j];
+            dvec v = dv_sub(dv_c(s[0], s[1], s[2]), o);
+            dnum tca = dv_dot(v, d);
+            if (!(tca.v > 0.0 && tca.v < seg.v)) continue;
+            double qv[3] = {v.x.v - tca.v * d.x.v, v.y.v - tca.v * d.y.v, v.z.v - tca.v * d.z.v};
+            if (!(dot3(qv, qv) < r2)) continue;
+            draw(cfg->seed, i, (uint32_t)k, 2u | ((uint32_t)b << 8), (uint32_t)j, x);
+            int e2 = (int)((((uint64_t)(x[0] >> 8)) * (uint64_t)ar->n_el) >> 24);
+            double xe = elem_x(C, e2);
+            double p[3] = {s[0], s[1], s[2]};
+            double vv[3] = {xe - p[0], -p[1], -p[2]};
+            double D = sqrt(dot3(vv, vv));
+            double fd = or_directivity(acos(-vv[2] / D), C->am, C->ac);
+            if (!(fd > 0.0)) continue;
+            dnum tc, ac;
+            dnum fac = dual_connection(G, p, med, xe, &tc, &ac);
+            if (fac.v == 0.0) continue;
+            dnum ta = dn_add(dn_add(t, dn_mul(tca, G->slow[med])), tc);
+            if (ta.v > C->t_last) continue;
+            dnum amp = dn_mul(dn_mul(w, dn_exp(dn_scale(dn_mul(G->a[med], tca), -1.0))),
+                              dn_mul(dn_scale(fac, (double)ar->n_el * fd), dn_exp(dn_scale(ac, -1.0))));
+            accumulate(G, k, e2, ta, amp, (double)s[3], j);
+        }
+        /* advance */
+        t = dn_add(t, dn_mul(seg, G->slow[med]));
+        w = dn_mul(w, dn_exp(dn_scale(dn_mul(G->a[med], seg), -1.0)));
+        L = dn_add(L, seg);
+        o = dv_add(o, dv_smul(seg, d));
+        if (clipped) return;
+        if (hit == C->top) {
+            o.z = dn_c(0.0);
+            double xl = C->x0 - 0.5 * C->pitch;
+            if (fabs(o.y.v) <= 0.5 * C->H && o.x.v >= xl && o.x.v < xl + ar->n_el * C->pitch) {
+                int el = (int)floor((o.x.v - xl) / C->pitch);
+                if (el > ar->n_el - 1) el = ar->n_el - 1;
+                dnum fd = dual_directivity(C, dn_scale(d.z, -1.0));
+                if (fd.v > 0.0 && t.v <= C->t_last) accumulate(G, k, el, t, dn_mul(w, fd), 1.0, -1);
+            }
+            return;
+        }
+        if (hit == C->bot || hit < 0) return;
+        if (sc->bnd_kind[hit] == OR_PLANE_Z) o.z = dn_c(sc->bnd_p[4 * hit]);
+        if (t.v > C->t_last) return;
+        if (b >= cfg->max_bounces) return;
+        /* interaction: same decisions as trace_ray, derivatives of everything else */
+        dvec n_out = dual_normal(G, hit, o);
+        double nv[3], dvv[3];
+        dv_val(n_out, nv);
+        dv_val(d, dvv);
+        int out_side = dot3(dvv, nv) > 0.0;
+        int m2 = out_side ? sc->bnd_med[2 * hit + 1] : sc->bnd_med[2 * hit];
+        dvec n = out_side ? dv_smul(dn_c(-1.0), n_out) : n_out;
+        dnum ci = dn_scale(dv_dot(n, d), -1.0);
+        dvec dr = dv_unit(dv_add(d, dv_smul(dn_scale(ci, 2.0), n)));
+        dnum eta = dn_div(G->c[m2], G->c[med]);
+        dnum kk = dn_sub(dn_c(1.0), dn_mul(dn_mul(eta, eta), dn_sub(dn_c(1.0), dn_mul(ci, ci))));
+        double d_r[3], d_t[3], rr, RR;
+        int tir = or_interface(dvv, nv, C->c[med], C->Z[med], C->c[m2], C->Z[m2], d_r, d_t, &rr, &RR);
+        if (tir) {
+            d = dr;
+        } else {
+            draw(cfg->seed, i, (uint32_t)k, 1u | ((uint32_t)b << 8), 0u, x);
+            dnum ct = dn_sqrt(kk);
+            dnum num = dn_sub(dn_mul(G->Z[m2], ci), dn_mul(G->Z[med], ct));
+            dnum den = dn_add(dn_mul(G->Z[m2], ci), dn_mul(G->Z[med], ct));
+            dnum r = dn_div(num, den);
+            double Rv = r.v * r.v;
+            if (u24(x[0]) < Rv) {
+                w = dn_mul(w, dn_scale(r, 1.0 / Rv));
+                d = dr;
+            } else {
+                w = dn_mul(w, dn_scale(dn_sqrt(dn_sub(dn_c(1.0), dn_mul(r, r))), 1.0 / (1.0 - Rv)));
+                dvec tv = dv_add(dv_smul(eta, d), dv_smul(dn_sub(dn_mul(eta, ci), ct), n));
+                d = dv_unit(tv);
+                med = m2;
+            }
+        }
+        b += 1;
+        prev = hit;
+    }
+}
+
+int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, const double *g_rf,
+            const double *g_q, double *grad_media, double *grad_amp, int n_threads)
+{
+    if (!sc || !ar || !cfg || !g_rf || !g_q || !grad_media || sc->n_med > 4 || cfg->mode != OR_MODE_MC ||
+        cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling)
+        return -1;
+    ctx_t C;
+    setup(&C, sc, ar, cfg);
+    int nm = sc->n_med;
+    dnum c[4], Z[4], a[4], slow[4];
+    double k_a = (double)ar->f0 * 1e-6 * 100.0 / (20.0 * log10(exp(1.0)));
+    for (int m = 0; m < nm; ++m) {
+        c[m] = dn_c(C.c[m]); c[m].d[3 * m + 0] = 1.0;
+        Z[m] = dn_c(C.Z[m]); Z[m].d[3 * m + 1] = 1.0;
+        dnum alpha = dn_c(sc->med[4 * m + 2]); alpha.d[3 * m + 2] = 1.0;
+        a[m] = dn_scale(alpha, k_a);
+        slow[m] = dn_div(dn_c((double)ar->fs), c[m]);
+    }
+    if (n_threads <= 0) n_threads = 1;
+    uint64_t n_sub = cfg->ray_end - cfg->ray_begin;
+    int64_t total = (int64_t)(n_sub * (uint64_t)cfg->n_tx);
+    double s_n = (double)ar->n_cycles / (4.0 * (double)ar->f0) * (double)ar->fs;
+    double *g_all = (double *)calloc((size_t)n_threads * OR_NP, sizeof(double));
+    double *ga_all = (double *)calloc((size_t)n_threads * (size_t)(sc->n_scat > 0 ? sc->n_scat : 1), sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads)
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        gctx_t G;
+        memset(&G, 0, sizeof G);
+        G.C = &C;
+        G.c = c; G.Z = Z; G.a = a; G.slow = slow;
+        G.g_rf = g_rf; G.g_q = g_q;
+        G.grad_amp = ga_all + (size_t)tid * (size_t)(sc->n_scat > 0 ? sc->n_scat : 1);
+        G.s_n = s_n;
+        G.K = (double)ar->tcut_sigmas * s_n;
+        G.om = 2.0 * OR_PI * (double)ar->f0 / (double)ar->fs;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t g = 0; g < total; ++g) {
+            int k = (int)(g / (int64_t)n_sub);
+            uint32_t i = (uint32_t)(cfg->ray_begin + (uint64_t)(g % (int64_t)n_sub));
+            grad_ray(&G, i, k);
+        }
+        for (int q = 0; q < OR_NP; ++q) g_all[(size_t)tid * OR_NP + q] = G.grad[q];
+    }
+    for (int q = 0; q < 3 * nm; ++q) {
+        double s = 0.0;
+        for (int th = 0; th < n_threads; ++th) s += g_all[(size_t)th * OR_NP + q];
+        grad_media[q] = s;
+    }
+    if (grad_amp)
+        for (int j = 0; j < sc->n_scat; ++j) {
+            double s = 0.0;
+            for (int th = 0; th < n_threads; ++th) s += ga_all[(size_t)th * sc->n_scat + j];
+            grad_amp[j] = s;
+        }
+    free(g_all);
+    free(ga_all);
+    teardown(&C);
+    return 0;
 }

@@ -46,6 +46,8 @@ typedef struct {
     int32_t n_scat;
     const float *scat;       /* [n_scat][4]: x, y, z (m), amplitude */
     float r_s;               /* scatterer capture radius (m) */
+    const float *med_sampling; /* nullable [n_med][4]: c, Z used for the Monte Carlo branch decisions
+                                  and the branch probabilities in the weights (default: med) */
 } or_scene;
 
 typedef struct {
@@ -104,6 +106,15 @@ void or_beamform(const or_array *ar, int32_t n_tx, const float *angles,
 /* Envelope |I|, normalisation by its maximum, 20 log10, clip at -dyn_range_db. */
 void or_envelope_log(const double *img_re, const double *img_im, int64_t n_px,
                      double dyn_range_db, double *env, double *db);
+
+/* Pathwise gradient (forward mode, FP64 dual numbers) of L with respect to the
+ * media parameters (c, Z, alpha of every medium, n_med <= 4) and the scatterer
+ * amplitudes, for the Monte Carlo estimate of or_trace (MC mode) with the branch
+ * decisions and branch probabilities held fixed.  g_rf, g_q = dL/d rf,
+ * dL/d quad [n_tx][n_el][n_s].  grad_media[n_med][3] (c, Z, alpha) and
+ * grad_amp[n_scat] are overwritten.  Returns 0, or -1 on invalid arguments. */
+int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, const double *g_rf,
+            const double *g_q, double *grad_media, double *grad_amp, int n_threads);
 
 /* ---- single-step routines exposed for the closed-form tests ---- */
 
