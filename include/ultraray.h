@@ -182,6 +182,32 @@ ur_status ur_beamform(ur_ctx *ctx, const float *rf, const float *quad,
                       const float *x_px, int nx, const float *z_px, int nz, float dyn_range_db,
                       float *iq, float *env, float *db);
 
+/* ---- differentiation (the paper builds on a differentiable renderer and names
+ * gradient-based optimisation as the goal, Sec. 1 and Sec. 3) ---- */
+
+/* Replace the media of a scene slot without re-uploading its geometry
+ * (n_med must match).  `sampling` (nullable) sets the media that decide the
+ * Monte Carlo branches and the branch probabilities in the weights; by default
+ * they are the media themselves.  Holding them fixed while `media` moves gives
+ * the estimator whose derivative ur_trace_adjoint returns. */
+ur_status ur_scene_set_media(ur_ctx *ctx, int slot, const ur_medium *media, int n_med, const ur_medium *sampling);
+
+/* Replace the scatterer amplitudes of a scene slot (n_scat must match). */
+ur_status ur_scene_set_amplitudes(ur_ctx *ctx, int slot, const float *amp, int n_scat);
+
+/* Path-replay adjoint of ur_trace on scene slot 0 (at most 4 media): given
+ * g_rf = dL/d rf and g_quad = dL/d quad ([n_tx][n_el][n_s], host or device),
+ * replays every ray from its Philox stream with the same branch decisions and
+ * returns dL/d(c, Z, alpha) of each medium in grad_media[n_med][3] and
+ * dL/d(amplitude) of each scatterer in grad_amp[n_scat] (nullable).  The
+ * derivative runs through hit distances, normals, refracted directions,
+ * reflection/transmission factors, attenuation and times of flight (primary
+ * and connection rays); branch probabilities dividing the weights are held
+ * fixed (detached sampling), as are the branch decisions.  Synchronous. */
+ur_status ur_trace_adjoint(ur_ctx *ctx, uint64_t n_rays_per_tx, uint64_t seed, int max_bounces,
+                           float max_path_m, const float *g_rf, const float *g_quad,
+                           float *grad_media, float *grad_amp);
+
 /* ---- batches: many (scene, transmit) items in one persistent launch ----
  * Rays of different transmits and scenes are independent (Sec. 2.3, "Ray
  * Emission": acquisition events can be simulated at the same time), so a
@@ -252,7 +278,7 @@ ur_status ur_autotune(ur_ctx *ctx, int scene, uint64_t n_rays, uint64_t seed, in
  * context's stream around each phase's kernels while profiling is on.  While
  * profiling, every call synchronises the stream before returning. */
 enum { UR_PHASE_GRID = 0, UR_PHASE_TRACE = 1, UR_PHASE_SORT = 2, UR_PHASE_DEPOSIT = 3,
-       UR_PHASE_DAS = 4, UR_PHASE_LOG = 5, UR_N_PHASES = 8 };
+       UR_PHASE_DAS = 4, UR_PHASE_LOG = 5, UR_PHASE_ADJOINT = 6, UR_N_PHASES = 8 };
 typedef struct {
     double ms[UR_N_PHASES];          /* accumulated device milliseconds */
     uint64_t launches[UR_N_PHASES];  /* kernels launched */

@@ -929,13 +929,19 @@ static void grad_ray(gctx_t *G, uint32_t i, int k)
         int clipped = 0;
         if (L.v + seg.v > (double)cfg->max_path) { seg = dn_sub(dn_c(cfg->max_path), L); clipped = 1; }
         /* scatterer events on the segment */
+        double ov2[3], dv2[3];
+        dv_val(o, ov2);
+        dv_val(d, dv2);
         for (int j = 0; j < sc->n_scat; ++j) {
             const float *s = &sc->scat[4 * j];
+            /* candidate test on values (as in segment_scatterers), dual only for candidates */
+            double vv0[3] = {s[0] - ov2[0], s[1] - ov2[1], s[2] - ov2[2]};
+            double tv = dot3(vv0, dv2);
+            if (!(tv > 0.0 && tv < seg.v)) continue;
+            double qv[3] = {vv0[0] - tv * dv2[0], vv0[1] - tv * dv2[1], vv0[2] - tv * dv2[2]};
+            if (!(dot3(qv, qv) < r2)) continue;
             dvec v = dv_sub(dv_c(s[0], s[1], s[2]), o);
             dnum tca = dv_dot(v, d);
-            if (!(tca.v > 0.0 && tca.v < seg.v)) continue;
-            double qv[3] = {v.x.v - tca.v * d.x.v, v.y.v - tca.v * d.y.v, v.z.v - tca.v * d.z.v};
-            if (!(dot3(qv, qv) < r2)) continue;
             draw(cfg->seed, i, (uint32_t)k, 2u | ((uint32_t)b << 8), (uint32_t)j, x);
             int e2 = (int)((((uint64_t)(x[0] >> 8)) * (uint64_t)ar->n_el) >> 24);
             double xe = elem_x(C, e2);

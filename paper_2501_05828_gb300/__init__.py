@@ -27,8 +27,9 @@ STATUS = {0: "UR_OK", 1: "UR_ERR_INVALID_ARG", 2: "UR_ERR_CUDA", 3: "UR_ERR_OOM"
 EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_set_array", "ur_set_plane_waves",
            "ur_trace", "ur_trace_debug", "ur_beamform", "ur_set_tuning", "ur_set_profiling", "ur_get_profile",
            "ur_sync", "ur_beamform_noalloc", "ur_scene_upload_slot", "ur_batch_plan", "ur_batch_trace",
-           "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune")
-PHASES = ("grid", "trace", "sort", "deposit", "das", "log")
+           "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune",
+           "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint")
+PHASES = ("grid", "trace", "sort", "deposit", "das", "log", "adjoint")
 
 
 class URError(RuntimeError):
@@ -113,6 +114,9 @@ def lib():
             L.ur_graph_end.argtypes = [vp]
             L.ur_graph_launch.argtypes = [vp]
             L.ur_autotune.argtypes = [vp, i32, u64, u64, i32, f32, C.POINTER(Tuning)]
+            L.ur_scene_set_media.argtypes = [vp, i32, C.POINTER(Medium), i32, C.POINTER(Medium)]
+            L.ur_scene_set_amplitudes.argtypes = [vp, i32, vp, i32]
+            L.ur_trace_adjoint.argtypes = [vp, u64, u64, i32, f32, vp, vp, vp, vp]
             L.ur_get_profile.argtypes = [vp, C.POINTER(Profile)]
             for name in EXPORTS:
                 if name != "ur_last_error":
@@ -274,6 +278,31 @@ class Simulator:
             raise URError(code, "ur_beamform_noalloc rejected the call")
         return iq, env, db
 
+    # -- differentiation ----------------------------------------------------
+    def set_media(self, media, sampling=None, slot=0):
+        med = np.ascontiguousarray(media, np.float32).reshape(-1, 4)
+        M = (Medium * len(med))(*[Medium(*map(float, m)) for m in med])
+        Ms = None
+        if sampling is not None:
+            sm = np.ascontiguousarray(sampling, np.float32).reshape(-1, 4)
+            Ms = (Medium * len(sm))(*[Medium(*map(float, m)) for m in sm])
+        self._call(lib().ur_scene_set_media(self._ctx, int(slot), M, len(med), Ms))
+
+    def set_amplitudes(self, amp, slot=0):
+        a = amp if hasattr(amp, "data_ptr") else np.ascontiguousarray(amp, np.float32)
+        self._call(lib().ur_scene_set_amplitudes(self._ctx, int(slot), _ptr(a), int(a.shape[0])))
+
+    def trace_adjoint(self, n_rays, seed, max_bounces, g_rf, g_quad, max_path=0.2, n_med=None, n_scat=None):
+        """dL/d(c, Z, alpha) per medium [n_med, 3] and dL/d(amplitude) [n_scat] (torch CUDA tensors)."""
+        torch = self._torch
+        n_med = n_med or 4
+        gm = torch.zeros((n_med, 3), dtype=torch.float32, device=self.device)
+        ga = torch.zeros((n_scat,), dtype=torch.float32, device=self.device) if n_scat else None
+        g_rf, g_quad = g_rf.contiguous(), g_quad.contiguous()
+        self._call(lib().ur_trace_adjoint(self._ctx, int(n_rays), int(seed), int(max_bounces), float(max_path),
+                                          _ptr(g_rf), _ptr(g_quad), _ptr(gm), _ptr(ga)))
+        return gm, ga
+
     # -- batches, graphs, autotuning ---------------------------------------
     def batch_plan(self, items, x_px, z_px, capacity=0):
         """items: iterable of (scene, tx, n_rays[, stream]); stream defaults to tx."""
@@ -352,3 +381,42 @@ def build_library(force=False):
     """Compile the CUDA library in-tree (see build.py)."""
     from .build import build as _build
     return _build(force=force)
+
+
+def _trace_function():
+    import torch
+
+    class TraceFunction(torch.autograd.Function):
+        """Differentiable ur_trace on scene slot 0: (media [n_med, 4] = c, Z, alpha, roughness;
+        scatterer amplitudes [n_scat]) -> (rf, quad).  Backward calls the path-replay adjoint
+        (ur_trace_adjoint); roughness gets no gradient."""
+
+        @staticmethod
+        def forward(ctx, media, amplitudes, sim, n_rays, seed, max_bounces, max_path):
+            sim.set_media(media.detach().cpu().numpy())
+            sim.set_amplitudes(amplitudes.detach().to(sim.device, torch.float32).contiguous())
+            rf, quad = sim.trace(n_rays, seed, max_bounces, max_path)
+            ctx.sim, ctx.cfg = sim, (n_rays, seed, max_bounces, max_path)
+            ctx.shapes = (media.shape, amplitudes.shape[0], media.device, amplitudes.device)
+            return rf, quad
+
+        @staticmethod
+        def backward(ctx, g_rf, g_quad):
+            n_rays, seed, max_bounces, max_path = ctx.cfg
+            mshape, n_scat, mdev, adev = ctx.shapes
+            if g_rf is None:
+                g_rf = torch.zeros_like(g_quad)
+            if g_quad is None:
+                g_quad = torch.zeros_like(g_rf)
+            gm, ga = ctx.sim.trace_adjoint(n_rays, seed, max_bounces, g_rf, g_quad, max_path, n_med=mshape[0],
+                                           n_scat=n_scat)
+            grad_media = torch.zeros(mshape, dtype=torch.float32, device=mdev)
+            grad_media[:, :3] = gm.to(mdev)
+            return grad_media, ga.to(adev), None, None, None, None, None
+
+    return TraceFunction
+
+
+def trace_differentiable(sim, media, amplitudes, n_rays, seed, max_bounces, max_path=0.2):
+    """rf, quad = ur_trace with autograd support for media and scatterer amplitudes."""
+    return _trace_function().apply(media, amplitudes, sim, n_rays, seed, max_bounces, max_path)

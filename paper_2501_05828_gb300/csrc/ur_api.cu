@@ -56,6 +56,7 @@ constexpr uint32_t kChunk = 4096;   // arrivals per deposit work item
 struct SceneData {
     bool ok = false;
     std::vector<ur_medium> media;
+    std::vector<ur_medium> sampling;   // media deciding Monte Carlo branches (same as media unless overridden)
     std::vector<ur_boundary> bnd;
     int med_array = 0;
     float z_max = 0.f;
@@ -98,6 +99,9 @@ struct ur_ctx {
 
     // images
     DevBuf stage_rf, stage_quad, pix, stage_iq, stage_env, stage_db, env_max, img_lists;
+
+    // adjoint
+    DevBuf adj_grad, adj_amp, adj_g;
 
     // batch plan
     bool batch_ok = false;
@@ -344,6 +348,7 @@ void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const 
         if (b.kind == UR_CYL_Y && !(b.p[2] > 0.f)) fail(UR_ERR_INVALID_ARG, "cylinder radius must be positive");
     }
     sd.media = M;
+    sd.sampling = M;
     sd.bnd = Bv;
     sd.med_array = med_array;
     sd.z_max = z_max;
@@ -375,6 +380,8 @@ void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
         S.med[m].Z = M.Z;
         S.med[m].a = (float)((double)M.alpha_db_cm_mhz * ((double)A.f0 * 1e-6) * 100.0 * np_per_db);
         S.med[m].slow = split((double)A.fs / (double)M.c);
+        S.cs[m] = sd.sampling[m].c;
+        S.Zs[m] = sd.sampling[m].Z;
     }
     for (int b = 0; b < S.n_bnd; ++b) {
         S.bnd[b].kind = sd.bnd[b].kind;
@@ -711,7 +718,8 @@ ur_status ur_destroy(ur_ctx *c) {
     DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
-                     &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max};
+                     &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
+                     &c->adj_g};
     for (DevBuf *b : all) c->release(*b);
     for (int p = 0; p < UR_N_PHASES; ++p) {
         if (c->ev0[p]) cudaEventDestroy(c->ev0[p]);
@@ -735,6 +743,38 @@ ur_status ur_scene_upload(ur_ctx *c, const ur_medium *media, int n_med, const ur
 ur_status ur_scene_upload_slot(ur_ctx *c, int slot, const ur_medium *media, int n_med, const ur_boundary *bnd,
                                int n_bnd, int med_array, float z_max, const float *scat_xyza, int n_scat, float r_s) {
     return guarded(c, [&] { upload_scene(c, slot, media, n_med, bnd, n_bnd, med_array, z_max, scat_xyza, n_scat, r_s); });
+}
+
+ur_status ur_scene_set_media(ur_ctx *c, int slot, const ur_medium *media, int n_med, const ur_medium *sampling) {
+    return guarded(c, [&] {
+        c->no_capture("ur_scene_set_media");
+        if (slot < 0 || slot >= ur::kMaxScenes || !c->scenes[slot].ok) fail(UR_ERR_STATE, "scene slot holds no scene");
+        SceneData &sd = c->scenes[slot];
+        if (!media || n_med != (int)sd.media.size()) fail(UR_ERR_INVALID_ARG, "n_med must match the uploaded scene");
+        std::vector<ur_medium> M(media, media + n_med), Ms = M;
+        if (sampling) Ms.assign(sampling, sampling + n_med);
+        for (int q = 0; q < n_med; ++q)
+            for (const ur_medium *m : {&M[q], &Ms[q]})
+                if (!(m->c > 0.f) || !(m->Z > 0.f) || !(m->alpha_db_cm_mhz >= 0.f) || m->roughness != 0.f)
+                    fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0, roughness 0");
+        sd.media = M;
+        sd.sampling = Ms;
+    });
+}
+
+ur_status ur_scene_set_amplitudes(ur_ctx *c, int slot, const float *amp, int n_scat) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_scene_set_amplitudes");
+        if (slot < 0 || slot >= ur::kMaxScenes || !c->scenes[slot].ok) fail(UR_ERR_STATE, "scene slot holds no scene");
+        SceneData &sd = c->scenes[slot];
+        if (n_scat != sd.n_scat || (n_scat > 0 && !amp)) fail(UR_ERR_INVALID_ARG, "n_scat must match the uploaded scene");
+        if (n_scat == 0) return;
+        ck(cudaMemcpy2DAsync((char *)sd.scat.p + 12, sizeof(float4), amp, sizeof(float), sizeof(float), (size_t)n_scat,
+                             cudaMemcpyDefault, c->stream), "copy amplitudes");
+        ck(cudaMemcpyAsync(sd.amp.p, amp, sizeof(float) * n_scat, cudaMemcpyDefault, c->stream), "copy amplitudes");
+        ck(cudaStreamSynchronize(c->stream), "amplitudes");
+    });
 }
 
 ur_status ur_set_array(ur_ctx *c, const ur_array *a) {
@@ -882,6 +922,74 @@ ur_status ur_beamform(ur_ctx *c, const float *rf, const float *quad, const float
         }
         if (sync || !is_device_ptr(rf) || !is_device_ptr(quad)) ck(cudaStreamSynchronize(c->stream), "beamform outputs");
         c->prof_sync();
+    });
+}
+
+// ------------------------------------------------------------------ adjoint
+
+ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_path, const float *g_rf,
+                           const float *g_quad, float *grad_media, float *grad_amp) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_trace_adjoint");
+        check_ready(c);
+        if (n_rays == 0 || n_rays > 0xFFFFFFFFull) fail(UR_ERR_INVALID_ARG, "n_rays_per_tx must be in [1, 2^32)");
+        check_trace_args(max_b, max_path);
+        if (!g_rf || !g_quad || !grad_media) fail(UR_ERR_INVALID_ARG, "g_rf, g_quad and grad_media are required");
+        const SceneData &sd = c->scenes[0];
+        const int n_med = (int)sd.media.size();
+        if (n_med > ur::kAdjMed) fail(UR_ERR_INVALID_ARG, "the adjoint supports scenes with at most 4 media");
+        prepare_transmits(c);
+        const int n_tx = (int)c->angles.size();
+        std::vector<ur_batch_item> items(n_tx);
+        for (int k = 0; k < n_tx; ++k) items[k] = ur_batch_item{0, k, (uint32_t)k, 0u, n_rays};
+        set_items(c, items);
+        c->batch_ok = false;
+        const size_t n_out = (size_t)n_tx * c->arr.n_el * c->arr.n_s;
+        const float *d_g[2] = {g_rf, g_quad};
+        if (!is_device_ptr(g_rf) || !is_device_ptr(g_quad)) {
+            c->grow(c->adj_g, 2 * sizeof(float) * n_out);
+            for (int q = 0; q < 2; ++q) {
+                float *dst = (float *)c->adj_g.p + q * n_out;
+                ck(cudaMemcpyAsync(dst, q ? g_quad : g_rf, sizeof(float) * n_out, cudaMemcpyDefault, c->stream), "copy g");
+                d_g[q] = dst;
+            }
+        }
+        ur::AdjP A{};
+        A.T = make_trace_params(c, seed, max_b, max_path);
+        A.g_rf = d_g[0];
+        A.g_q = d_g[1];
+        c->grow(c->adj_grad, sizeof(double) * 3 * ur::kAdjMed);
+        ck(cudaMemsetAsync(c->adj_grad.p, 0, sizeof(double) * 3 * ur::kAdjMed, c->stream), "memset grad");
+        A.grad = (double *)c->adj_grad.p;
+        if (grad_amp && sd.n_scat > 0) {
+            c->grow(c->adj_amp, sizeof(float) * sd.n_scat);
+            ck(cudaMemsetAsync(c->adj_amp.p, 0, sizeof(float) * sd.n_scat, c->stream), "memset grad_amp");
+            A.grad_amp = (float *)c->adj_amp.p;
+        }
+        const ur_array &Ar = c->arr;
+        const double s_n = (double)Ar.n_cycles / (4.0 * (double)Ar.f0) * (double)Ar.fs;
+        A.K = (float)((double)Ar.tcut_sigmas * s_n);
+        A.inv_2s2 = (float)(1.0 / (2.0 * s_n * s_n));
+        A.inv_s2 = (float)(1.0 / (s_n * s_n));
+        A.half_cycles = (float)(2.0 * (double)Ar.f0 / (double)Ar.fs);
+        A.om = (float)(2.0 * kPi * (double)Ar.f0 / (double)Ar.fs);
+        A.fs = Ar.fs;
+        A.k_alpha = (float)((double)Ar.f0 * 1e-6 * 100.0 * std::log(10.0) / 20.0);
+        c->phase_begin(UR_PHASE_ADJOINT);
+        ur::launch_adjoint(A, c->sms, c->stream);
+        ck(cudaGetLastError(), "adjoint kernel");
+        c->phase_end(UR_PHASE_ADJOINT, 1);
+        double g[3 * ur::kAdjMed];
+        ck(cudaMemcpyAsync(c->host_scratch, c->adj_grad.p, sizeof g, cudaMemcpyDeviceToHost, c->stream), "read grad");
+        ck(cudaStreamSynchronize(c->stream), "adjoint");
+        c->phase_collect();
+        std::memcpy(g, c->host_scratch, sizeof g);
+        float gf[3 * ur::kAdjMed];
+        for (int q = 0; q < 3 * n_med; ++q) gf[q] = (float)g[q];
+        ck(cudaMemcpy(grad_media, gf, sizeof(float) * 3 * n_med, cudaMemcpyDefault), "write grad_media");
+        if (grad_amp && sd.n_scat > 0)
+            ck(cudaMemcpy(grad_amp, c->adj_amp.p, sizeof(float) * sd.n_scat, cudaMemcpyDefault), "write grad_amp");
     });
 }
 

@@ -13,6 +13,7 @@ namespace ur {
 constexpr int kMaxMed = 16;
 constexpr int kMaxBnd = 16;
 constexpr int kMaxScenes = 16;   // scenes traced together in one launch
+constexpr int kAdjMed = 4;       // media the adjoint differentiates (c, Z, alpha each)
 constexpr int kTracePool = 32;   // ray slots a tracer warp claims at once (item slot ranges are multiples)
 constexpr int kMaxNs = 8192;
 constexpr int kMaxSeg = 4096;      // safety bound on primary segments per path
@@ -131,6 +132,7 @@ struct SceneP {
     int n_med, n_bnd, med_array;
     float z_max;
     Medium med[kMaxMed];
+    float cs[kMaxMed], Zs[kMaxMed];   // c and Z that decide Monte Carlo branches (normally = med)
     Bnd bnd[kMaxBnd];
     // scatterer grid
     int n_scat;
@@ -181,9 +183,116 @@ struct TraceP {
     unsigned long long *stats;      // 6 counters, nullable
 };
 
+// ---------------------------------------------------------------- geometry shared by tracer and adjoint
+// Nearest boundary hit along o + t d, t in (kTmin, inf).  `skip` is the
+// primitive the ray is leaving: a plane cannot be met again, a sphere or
+// cylinder only at its far root.  With `terminals`, the array plane z = 0
+// (id n_bnd, upward rays) and the absorbing plane z = z_max (id n_bnd + 1,
+// downward rays) take part.
+__device__ __forceinline__ int nearest(const SceneP &S, float3 o, float3 d, int skip, bool terminals,
+                                       float &t_out) {
+    float best = INFINITY;
+    int hit = -1;
+    for (int p = 0; p < S.n_bnd; ++p) {
+        const Bnd &B = S.bnd[p];
+        float t;
+        if (B.kind == kPlaneZ) {
+            if (p == skip || d.z == 0.f) continue;
+            t = (B.p[0] - o.z) / d.z;
+        } else if (B.kind == kSphere) {
+            const float3 oc = make_float3(o.x - B.p[0], o.y - B.p[1], o.z - B.p[2]);
+            const float b = dot3(oc, d);
+            if (p == skip) {
+                t = -2.f * b;
+            } else {
+                const float3 f = oc - b * d;
+                const float disc = B.p[3] * B.p[3] - dot3(f, f);
+                if (disc < 0.f) continue;
+                const float s = sqrtf(disc);
+                t = -b - s;
+                if (!(t > kTmin)) t = -b + s;
+            }
+        } else {
+            const float ocx = o.x - B.p[0], ocz = o.z - B.p[1];
+            const float a = d.x * d.x + d.z * d.z;
+            if (a == 0.f) continue;
+            const float b = (ocx * d.x + ocz * d.z) / a;
+            if (p == skip) {
+                t = -2.f * b;
+            } else {
+                const float fx = ocx - b * d.x, fz = ocz - b * d.z;
+                const float disc = (B.p[2] * B.p[2] - (fx * fx + fz * fz)) / a;
+                if (disc < 0.f) continue;
+                const float s = sqrtf(disc);
+                t = -b - s;
+                if (!(t > kTmin)) t = -b + s;
+            }
+        }
+        if (t > kTmin && t < best) {
+            best = t;
+            hit = p;
+        }
+    }
+    if (terminals) {
+        if (d.z < 0.f) {
+            const float t = -o.z / d.z;
+            if (t > kTmin && t < best) {
+                best = t;
+                hit = S.n_bnd;
+            }
+        } else if (d.z > 0.f) {
+            const float t = (S.z_max - o.z) / d.z;
+            if (t > kTmin && t < best) {
+                best = t;
+                hit = S.n_bnd + 1;
+            }
+        }
+    }
+    t_out = best;
+    return hit;
+}
+
+__device__ __forceinline__ float3 outward(const Bnd &B, float3 h) {
+    if (B.kind == kPlaneZ) return make_float3(0.f, 0.f, 1.f);
+    if (B.kind == kSphere) return unit3(make_float3(h.x - B.p[0], h.y - B.p[1], h.z - B.p[2]));
+    return unit3(make_float3(h.x - B.p[0], 0.f, h.z - B.p[1]));
+}
+
+// Snell (speed ratio) and the fluid-fluid pressure reflection coefficient.
+// Returns false on total internal reflection.
+__device__ __forceinline__ bool fresnel(float cos_i, float c1, float Z1, float c2, float Z2, float &r,
+                                        float &cos_t) {
+    const float eta = c2 / c1;
+    const float k = 1.f - eta * eta * (1.f - cos_i * cos_i);
+    if (k < 0.f) return false;
+    cos_t = sqrtf(k);
+    r = (Z2 * cos_i - Z1 * cos_t) / (Z2 * cos_i + Z1 * cos_t);
+    return true;
+}
+
+// Eq. 13 through cosines: 1 inside the main beam, 0 beyond the cutoff, linear in angle between.
+__device__ __forceinline__ float directivity(const TraceP &P, float cos_a) {
+    if (cos_a >= P.cos_am) return 1.f;
+    if (cos_a < P.cos_ac) return 0.f;
+    const float al = acosf(fminf(cos_a, 1.f));
+    return (P.ac - al) / (P.ac - P.am);
+}
+
+
 // ---------------------------------------------------------------- launchers
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s);
 int trace_occupancy(int block, bool debug);   // resident tracer CTAs per SM
+
+// Path-replay adjoint: loss sensitivities in, parameter gradients out.
+struct AdjP {
+    TraceP T;                   // scene table, array, items, Philox key, limits
+    const float *g_rf, *g_q;    // dL/d rf, dL/d quad  [n_items][n_el][n_s]
+    double *grad;               // [3 * kAdjMed]: (c, Z, alpha) per medium, accumulated
+    float *grad_amp;            // [n_scat] of scene 0, accumulated (nullable)
+    float K, inv_2s2, inv_s2, half_cycles, om;   // pulse: half-width, 1/(2 s^2), 1/s^2 (samples), 2 f0/fs, rad/sample
+    float fs, k_alpha;          // sampling frequency; d(Np/m)/d(dB/cm/MHz) at f0
+};
+void launch_adjoint(const AdjP &A, int sms, cudaStream_t s);
 
 struct BinP {
     const uint4 *arr;

@@ -8,100 +8,6 @@
 namespace ur {
 namespace {
 
-// Nearest boundary hit along o + t d, t in (kTmin, inf).  `skip` is the
-// primitive the ray is leaving: a plane cannot be met again, a sphere or
-// cylinder only at its far root.  With `terminals`, the array plane z = 0
-// (id n_bnd, upward rays) and the absorbing plane z = z_max (id n_bnd + 1,
-// downward rays) take part.
-__device__ __forceinline__ int nearest(const SceneP &S, float3 o, float3 d, int skip, bool terminals,
-                                       float &t_out) {
-    float best = INFINITY;
-    int hit = -1;
-    for (int p = 0; p < S.n_bnd; ++p) {
-        const Bnd &B = S.bnd[p];
-        float t;
-        if (B.kind == kPlaneZ) {
-            if (p == skip || d.z == 0.f) continue;
-            t = (B.p[0] - o.z) / d.z;
-        } else if (B.kind == kSphere) {
-            const float3 oc = make_float3(o.x - B.p[0], o.y - B.p[1], o.z - B.p[2]);
-            const float b = dot3(oc, d);
-            if (p == skip) {
-                t = -2.f * b;
-            } else {
-                const float3 f = oc - b * d;
-                const float disc = B.p[3] * B.p[3] - dot3(f, f);
-                if (disc < 0.f) continue;
-                const float s = sqrtf(disc);
-                t = -b - s;
-                if (!(t > kTmin)) t = -b + s;
-            }
-        } else {
-            const float ocx = o.x - B.p[0], ocz = o.z - B.p[1];
-            const float a = d.x * d.x + d.z * d.z;
-            if (a == 0.f) continue;
-            const float b = (ocx * d.x + ocz * d.z) / a;
-            if (p == skip) {
-                t = -2.f * b;
-            } else {
-                const float fx = ocx - b * d.x, fz = ocz - b * d.z;
-                const float disc = (B.p[2] * B.p[2] - (fx * fx + fz * fz)) / a;
-                if (disc < 0.f) continue;
-                const float s = sqrtf(disc);
-                t = -b - s;
-                if (!(t > kTmin)) t = -b + s;
-            }
-        }
-        if (t > kTmin && t < best) {
-            best = t;
-            hit = p;
-        }
-    }
-    if (terminals) {
-        if (d.z < 0.f) {
-            const float t = -o.z / d.z;
-            if (t > kTmin && t < best) {
-                best = t;
-                hit = S.n_bnd;
-            }
-        } else if (d.z > 0.f) {
-            const float t = (S.z_max - o.z) / d.z;
-            if (t > kTmin && t < best) {
-                best = t;
-                hit = S.n_bnd + 1;
-            }
-        }
-    }
-    t_out = best;
-    return hit;
-}
-
-__device__ __forceinline__ float3 outward(const Bnd &B, float3 h) {
-    if (B.kind == kPlaneZ) return make_float3(0.f, 0.f, 1.f);
-    if (B.kind == kSphere) return unit3(make_float3(h.x - B.p[0], h.y - B.p[1], h.z - B.p[2]));
-    return unit3(make_float3(h.x - B.p[0], 0.f, h.z - B.p[1]));
-}
-
-// Snell (speed ratio) and the fluid-fluid pressure reflection coefficient.
-// Returns false on total internal reflection.
-__device__ __forceinline__ bool fresnel(float cos_i, float c1, float Z1, float c2, float Z2, float &r,
-                                        float &cos_t) {
-    const float eta = c2 / c1;
-    const float k = 1.f - eta * eta * (1.f - cos_i * cos_i);
-    if (k < 0.f) return false;
-    cos_t = sqrtf(k);
-    r = (Z2 * cos_i - Z1 * cos_t) / (Z2 * cos_i + Z1 * cos_t);
-    return true;
-}
-
-// Eq. 13 through cosines: 1 inside the main beam, 0 beyond the cutoff, linear in angle between.
-__device__ __forceinline__ float directivity(const TraceP &P, float cos_a) {
-    if (cos_a >= P.cos_am) return 1.f;
-    if (cos_a < P.cos_ac) return 0.f;
-    const float al = acosf(fminf(cos_a, 1.f));
-    return (P.ac - al) / (P.ac - P.am);
-}
-
 // Straight connection ray from p to the element centre (x_e, 0, 0): product of
 // sqrt(1 - R) over the boundaries it crosses (0 if one reflects totally),
 // travel time (samples) and attenuation exponent.
@@ -336,22 +242,24 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const float cos_i = -dot3(n, R.d);
     const float3 dr = unit3(R.d + (2.f * cos_i) * n);
     const Medium &M2 = S.med[m2];
-    float r, cos_t;
+    float r, cos_t, rs, cts;
     uint32_t branch;
-    if (!fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t)) {
+    // the sampling media (normally the same) decide the branch and its probability
+    const bool tir_s = !fresnel(cos_i, S.cs[R.med], S.Zs[R.med], S.cs[m2], S.Zs[m2], rs, cts);
+    if (tir_s || !fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t)) {
         branch = 2;
         R.d = dr;
     } else {
-        const float Rr = r * r;
+        const float Rs = rs * rs;
         const uint4 y = philox(make_uint4(R.i, R.stream, 1u | ((uint32_t)R.b << 8), 0u), P.key);
-        if (u24(y.x) < Rr) {
+        if (u24(y.x) < Rs) {
             branch = 0;
-            R.w *= r / Rr;
+            R.w *= r / Rs;
             R.d = dr;
         } else {
             branch = 1;
             const float eta = M2.c / M.c;
-            R.w *= 1.f / sqrtf(1.f - Rr);
+            R.w *= sqrtf(1.f - r * r) / (1.f - Rs);
             R.d = unit3(eta * R.d + (eta * cos_i - cos_t) * n);
             R.med = m2;
         }
