@@ -407,6 +407,66 @@ def run_batched(args, rank, world, local_rank):
     sim.close()
 
 
+def run_adjoint(args, rank, world, local_rank):
+    """Differentiation workload: forward trace of the layered frame against a target simulated
+    with speeds +2 %, impedances +5 %, attenuation +10 % (same seed), then the path-replay
+    adjoint for the gradient w.r.t. 4 media x (c, Z, alpha) and 50k scatterer amplitudes."""
+    import numpy as np
+    import torch
+
+    import paper_2501_05828_gb300 as ur
+    import phantoms
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = phantoms.layered()
+    N = w["n_rays"] if not args.rays else args.rays
+    sim = ur.Simulator(local_rank)
+    sim.load(w)
+    med0 = np.array(w["scene"]["media"], np.float32)
+    tgt_med = med0.astype(np.float64).copy()
+    tgt_med[:, 0] *= 1.02
+    tgt_med[:, 1] *= 1.05
+    tgt_med[:, 2] *= 1.10
+    sim.set_media(tgt_med.astype(np.float32))
+    trf, tq = sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])
+    sim.set_media(med0)
+    n_scat = len(w["scene"]["scatterers"])
+
+    def step():
+        rf, q = sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])
+        g_rf, g_q = 2 * (rf - trf), 2 * (q - tq)
+        return sim.trace_adjoint(N, w["seed"], w["max_bounces"], g_rf, g_q, w["max_path"], n_med=len(med0),
+                                 n_scat=n_scat)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sim.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        gm, ga = step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    prof = sim.profile()
+    sim.set_profiling(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    per = {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "rays/s of forward + gradient (path-replay adjoint)", "value": N / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "differentiation: " + WORKLOAD, "rays_per_step": N, "parameters": 12 + n_scat,
+                       "l2": "flushed before every timed step (256 MiB write, untimed)"},
+            "phase_ms": per, "adjoint_over_trace": per.get("adjoint", 0.0) / max(per.get("trace", 1e-9), 1e-9),
+            "grad_media_norm": float(gm.norm()), "grad_amp_norm": float(ga.norm())}), flush=True)
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,7 +477,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
-    ap.add_argument("--workload", default="layered", choices=("layered", "batched"))
+    ap.add_argument("--workload", default="layered", choices=("layered", "batched", "adjoint"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -428,6 +488,8 @@ def main():
         run_reference(args, rank)
     elif args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.workload == "adjoint":
+        run_adjoint(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
