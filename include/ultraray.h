@@ -208,6 +208,48 @@ ur_status ur_trace_adjoint(ur_ctx *ctx, uint64_t n_rays_per_tx, uint64_t seed, i
                            float max_path_m, const float *g_rf, const float *g_quad,
                            float *grad_media, float *grad_amp);
 
+/* ---- learned denoiser of the channel data ----
+ * The paper names neural-network integration as a goal of a differentiable
+ * simulator (Abstract); this library adds a small network that maps the
+ * channel data of a low-ray-count trace to that of a high-ray-count trace.
+ * Architecture: 4-level 2D U-Net over one transmit's channel data viewed as an
+ * n_el x n_s image with 2 channels (rf, quad): two 3x3 convolutions with ReLU
+ * per level, 2x2 average pooling, nearest upsampling and skip concatenation,
+ * widths w, 2w, 4w, 8w, and a 1x1 head added to the input (residual).  BF16
+ * weights and activations, FP32 accumulation on the tensor cores, FP32 master
+ * weights and Adam.  The loss is the mean squared error of the normalised
+ * channel data (channel data / scale). */
+typedef struct ur_nn ur_nn;
+
+/* Network for images of n_el x n_s (multiples of 8), up to max_batch frames,
+ * width w in {32, 64} (w = 32: about 2M parameters), He-initialised from seed. */
+ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch, int n_el, int n_s, int width,
+                       uint64_t seed);
+ur_status ur_nn_destroy(ur_nn *nn);
+const char *ur_nn_last_error(const ur_nn *nn);
+
+/* Number of parameters of the packed FP32 vector: per convolution l (order
+ * e1a e1b e2a e2b e3a e3b e4a e4b d3a d3b d2a d2b d1a d1b) the weights
+ * [9 taps][c_out][c_in] (the first convolution's c_in padded to 32 with zero
+ * weights beyond the 2 real channels) then the bias [c_out], each tensor
+ * starting at a multiple of 8 entries; then the head [2][w] and its bias [2]. */
+ur_status ur_nn_param_count(const ur_nn *nn, uint64_t *n);
+
+/* Copy the parameters out (get, nullable) and/or in (set, nullable; resets Adam). */
+ur_status ur_nn_params(ur_nn *nn, float *get, const float *set);
+
+/* Normalisation: the network sees channel data / scale. */
+ur_status ur_nn_set_scale(ur_nn *nn, float scale);
+
+/* Denoise `batch` frames: rf, quad [batch][n_el][n_s] (device) -> out_rf, out_quad (device). */
+ur_status ur_nn_forward(ur_nn *nn, const float *rf, const float *quad, int batch, float *out_rf, float *out_quad);
+
+/* One training step on `batch` pairs (inputs rf, quad; targets t_rf, t_quad; device):
+ * forward, loss, backward, then Adam with learning rate lr (lr = 0: no update).
+ * loss (nullable, host) receives the loss; grad_out (nullable) the parameter gradient. */
+ur_status ur_nn_train_step(ur_nn *nn, const float *rf, const float *quad, const float *t_rf, const float *t_quad,
+                           int batch, float lr, float *loss, float *grad_out);
+
 /* ---- batches: many (scene, transmit) items in one persistent launch ----
  * Rays of different transmits and scenes are independent (Sec. 2.3, "Ray
  * Emission": acquisition events can be simulated at the same time), so a

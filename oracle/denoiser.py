@@ -106,22 +106,35 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 # ------------------------------------------------------------------ network
 
-def forward(p, x):
-    """x [N, H, W, 2] -> (output [N, H, W, 2], cache)."""
+def forward(p, x, q=None):
+    """x [N, H, W, 2] -> (output [N, H, W, 2], cache).  With q (a rounding
+    function, e.g. bf16) the stored tensors are rounded where a BF16 network
+    stores them: input, convolution weights, every convolution output after
+    ReLU and every pooled tensor; accumulation stays exact."""
+    r = q if q is not None else (lambda v: v)
+    x = r(x)
     c = {"x": x}
 
     def block(name_a, name_b, inp):
-        a = relu(conv3x3(inp, p[name_a + ".w"], p[name_a + ".b"]))
-        bb = relu(conv3x3(a, p[name_b + ".w"], p[name_b + ".b"]))
+        a = r(relu(conv3x3(inp, r(p[name_a + ".w"]), p[name_a + ".b"])))
+        bb = r(relu(conv3x3(a, r(p[name_b + ".w"]), p[name_b + ".b"])))
         c[name_a + ".in"], c[name_a + ".out"], c[name_b + ".out"] = inp, a, bb
         return bb
 
     e1 = block("e1a", "e1b", x)
-    e2 = block("e2a", "e2b", pool2(e1))
-    e3 = block("e3a", "e3b", pool2(e2))
-    e4 = block("e4a", "e4b", pool2(e3))
+    e2 = block("e2a", "e2b", r(pool2(e1)))
+    e3 = block("e3a", "e3b", r(pool2(e2)))
+    e4 = block("e4a", "e4b", r(pool2(e3)))
     d3 = block("d3a", "d3b", np.concatenate([up2(e4), e3], axis=3))
     d2 = block("d2a", "d2b", np.concatenate([up2(d3), e2], axis=3))
     d1 = block("d1a", "d1b", np.concatenate([up2(d2), e1], axis=3))

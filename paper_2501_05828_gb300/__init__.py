@@ -28,7 +28,9 @@ EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_se
            "ur_trace", "ur_trace_debug", "ur_beamform", "ur_set_tuning", "ur_set_profiling", "ur_get_profile",
            "ur_sync", "ur_beamform_noalloc", "ur_scene_upload_slot", "ur_batch_plan", "ur_batch_trace",
            "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune",
-           "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint")
+           "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint", "ur_nn_create", "ur_nn_destroy",
+           "ur_nn_last_error", "ur_nn_param_count", "ur_nn_params", "ur_nn_set_scale", "ur_nn_forward",
+           "ur_nn_train_step")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log", "adjoint")
 
 
@@ -117,9 +119,18 @@ def lib():
             L.ur_scene_set_media.argtypes = [vp, i32, C.POINTER(Medium), i32, C.POINTER(Medium)]
             L.ur_scene_set_amplitudes.argtypes = [vp, i32, vp, i32]
             L.ur_trace_adjoint.argtypes = [vp, u64, u64, i32, f32, vp, vp, vp, vp]
+            L.ur_nn_create.argtypes = [C.POINTER(vp), i32, vp, i32, i32, i32, i32, u64]
+            L.ur_nn_destroy.argtypes = [vp]
+            L.ur_nn_last_error.restype = C.c_char_p
+            L.ur_nn_last_error.argtypes = [vp]
+            L.ur_nn_param_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+            L.ur_nn_params.argtypes = [vp, vp, vp]
+            L.ur_nn_set_scale.argtypes = [vp, f32]
+            L.ur_nn_forward.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.ur_nn_train_step.argtypes = [vp, vp, vp, vp, vp, i32, f32, C.POINTER(C.c_float), vp]
             L.ur_get_profile.argtypes = [vp, C.POINTER(Profile)]
             for name in EXPORTS:
-                if name != "ur_last_error":
+                if name not in ("ur_last_error", "ur_nn_last_error"):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -420,3 +431,89 @@ def _trace_function():
 def trace_differentiable(sim, media, amplitudes, n_rays, seed, max_bounces, max_path=0.2):
     """rf, quad = ur_trace with autograd support for media and scatterer amplitudes."""
     return _trace_function().apply(media, amplitudes, sim, n_rays, seed, max_bounces, max_path)
+
+
+NN_LAYERS = ("e1a", "e1b", "e2a", "e2b", "e3a", "e3b", "e4a", "e4b", "d3a", "d3b", "d2a", "d2b", "d1a", "d1b")
+
+
+def nn_layout(width=32):
+    """Offsets of the packed parameter vector documented in ultraray.h:
+    {name: (w_offset, (9, c_out, c_in), b_offset, c_out)} plus ('head': ...)."""
+    C = width
+    cin = (32, C, C, 2 * C, 2 * C, 4 * C, 4 * C, 8 * C, 12 * C, 4 * C, 6 * C, 2 * C, 3 * C, C)
+    cout = (C, C, 2 * C, 2 * C, 4 * C, 4 * C, 8 * C, 8 * C, 4 * C, 4 * C, 2 * C, 2 * C, C, C)
+    lay, off = {}, 0
+    for name, ci, co in zip(NN_LAYERS, cin, cout):
+        w_off = off
+        off += 9 * ci * co
+        b_off = off
+        off += co
+        off = (off + 7) // 8 * 8
+        lay[name] = (w_off, (9, co, ci), b_off, co)
+    lay["head"] = (off, (1, 2, C), off + 2 * C, 2)
+    return lay
+
+
+class Denoiser:
+    """The library's U-Net denoiser of channel data (ur_nn_* entry points)."""
+
+    def __init__(self, device=0, max_batch=4, n_el=128, n_s=3200, width=32, seed=0, stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self._h = C.c_void_p()
+        code = lib().ur_nn_create(C.byref(self._h), int(device), C.c_void_p(stream.cuda_stream or 1), int(max_batch),
+                                  int(n_el), int(n_s), int(width), int(seed))
+        if code != 0:
+            raise URError(code, "ur_nn_create failed")
+        n = C.c_uint64()
+        lib().ur_nn_param_count(self._h, C.byref(n))
+        self.n_params = int(n.value)
+        self.shape = (int(n_el), int(n_s))
+        self.width = width
+
+    def _call(self, code):
+        if code != 0:
+            raise URError(code, lib().ur_nn_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib().ur_nn_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._call(lib().ur_nn_params(self._h, _ptr(out), None))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.n_params
+        self._call(lib().ur_nn_params(self._h, None, _ptr(p)))
+
+    def set_scale(self, scale):
+        self._call(lib().ur_nn_set_scale(self._h, float(scale)))
+
+    def forward(self, rf, quad):
+        torch = self._torch
+        rf, quad = rf.contiguous(), quad.contiguous()
+        o_rf, o_q = torch.empty_like(rf), torch.empty_like(quad)
+        self._call(lib().ur_nn_forward(self._h, _ptr(rf), _ptr(quad), int(rf.shape[0]), _ptr(o_rf), _ptr(o_q)))
+        return o_rf, o_q
+
+    def train_step(self, rf, quad, t_rf, t_quad, lr, grad=False):
+        torch = self._torch
+        rf, quad, t_rf, t_quad = (t.contiguous() for t in (rf, quad, t_rf, t_quad))
+        loss = C.c_float()
+        g = torch.empty(self.n_params, dtype=torch.float32, device=self.device) if grad else None
+        self._call(lib().ur_nn_train_step(self._h, _ptr(rf), _ptr(quad), _ptr(t_rf), _ptr(t_quad), int(rf.shape[0]),
+                                          float(lr), C.byref(loss), _ptr(g)))
+        return (float(loss.value), g) if grad else float(loss.value)

@@ -1,0 +1,910 @@
+// Channel-data denoiser: a 4-level 2D U-Net over the analytic channel data of
+// one transmit (an n_el x n_s image with 2 channels, rf and quad), trained to
+// map low-ray-count channel data to high-ray-count channel data.  BF16 weights
+// and activations (NHWC), FP32 accumulation on the tensor cores (mma.sync
+// m16n8k16 fed by ldmatrix from cp.async-filled shared memory), FP32 master
+// weights with Adam.  Decoder convolutions gather their input on the fly from
+// the half-resolution tensor (nearest-neighbour upsampling) and the skip
+// tensor (concatenation), so neither is materialised.
+#include "ultraray.h"
+#include "ur_device.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Convolution input: channels [0, c1) from x1 (at half resolution when low1),
+// channels [c1, c1 + c2) from x2 (full resolution).
+struct ConvIn {
+    const bf16 *x1;
+    int c1, low1;
+    const bf16 *x2;
+    int c2;
+};
+
+__device__ __forceinline__ const bf16 *gather(const ConvIn &in, int n, int H, int W, int yy, int xx, int c) {
+    if (c < in.c1) {
+        if (in.low1) return in.x1 + (((size_t)n * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1)) * in.c1 + c;
+        return in.x1 + (((size_t)n * H + yy) * W + xx) * in.c1 + c;
+    }
+    return in.x2 + (((size_t)n * H + yy) * W + xx) * in.c2 + (c - in.c1);
+}
+
+struct ConvP {
+    ConvIn in;
+    int N, H, W, Cin, Cout;
+    const bf16 *w;        // [9][Cout][Cin]
+    const float *bias;    // [Cout], nullable
+    bf16 *y;              // [N][H][W][Cout]
+    float *y32;           // nullable fp32 copy (tests)
+    int relu;
+};
+
+// Implicit-GEMM 3x3 convolution (zero padding): rows = pixels of one image row,
+// columns = output channels, K = 9 taps x input channels.  WM x WN warps, each
+// a 32 x 32 tile (2 m16 x 4 n8 MMA tiles); K advances 32 channels per stage
+// with two shared-memory stages filled by cp.async.
+template <int WM, int WN>
+__global__ void __launch_bounds__(128) k_conv3x3(const ConvP P) {
+    constexpr int BM = 32 * WM, BN = 32 * WN, BK = 32, LDS = 40;
+    __shared__ __align__(16) bf16 sA[2][BM * LDS];
+    __shared__ __align__(16) bf16 sB[2][BN * LDS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp % WM, wn = warp / WM;
+    const int nxb = (P.W + BM - 1) / BM;
+    int b = blockIdx.x;
+    const int xb = b % nxb;
+    b /= nxb;
+    const int y = b % P.H, n = b / P.H;
+    const int x0 = xb * BM, co0 = blockIdx.y * BN;
+    const int kc = P.Cin / BK, nk = 9 * kc;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    auto load = [&](int kt, int buf) {
+        const int tap = kt / kc, ci0 = (kt % kc) * BK;
+        const int ky = tap / 3, kx = tap % 3, yy = y + ky - 1;
+        for (int idx = tid; idx < BM * 4; idx += 128) {
+            const int px = idx >> 2, part = idx & 3, xx = x0 + px + kx - 1;
+            const bool ok = yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
+            const bf16 *src = ok ? gather(P.in, n, P.H, P.W, yy, xx, ci0 + part * 8) : P.in.x1;
+            cp_async16(&sA[buf][px * LDS + part * 8], src, ok ? 16 : 0);
+        }
+        for (int idx = tid; idx < BN * 4; idx += 128) {
+            const int r = idx >> 2, part = idx & 3;
+            cp_async16(&sB[buf][r * LDS + part * 8], P.w + ((size_t)tap * P.Cout + co0 + r) * P.Cin + ci0 + part * 8, 16);
+        }
+        cp_async_commit();
+    };
+
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) {
+            load(kt + 1, (kt + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const bf16 *A = sA[kt & 1];
+        const bf16 *B = sB[kt & 1];
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t a[2][4], bb[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+                ldsm_x4(a[mi], &A[(wm * 32 + mi * 16 + (lane & 15)) * LDS + ks + (lane >> 4) * 8]);
+#pragma unroll
+            for (int nj = 0; nj < 4; nj += 2) {
+                uint32_t r4[4];
+                ldsm_x4(r4, &B[(wn * 32 + nj * 8 + (lane & 7) + ((lane >> 4) << 3)) * LDS + ks + ((lane >> 3) & 1) * 8]);
+                bb[nj][0] = r4[0];
+                bb[nj][1] = r4[1];
+                bb[nj + 1][0] = r4[2];
+                bb[nj + 1][1] = r4[3];
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], a[mi], bb[nj][0], bb[nj][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + wm * 32 + mi * 16 + (lane >> 2) + h * 8;
+                if (x >= P.W) continue;
+                const int co = co0 + wn * 32 + nj * 8 + (lane & 3) * 2;
+                float v0 = acc[mi][nj][2 * h], v1 = acc[mi][nj][2 * h + 1];
+                if (P.bias) {
+                    v0 += P.bias[co];
+                    v1 += P.bias[co + 1];
+                }
+                if (P.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const size_t o = (((size_t)n * P.H + y) * P.W + x) * P.Cout + co;
+                *reinterpret_cast<__nv_bfloat162 *>(P.y + o) = __floats2bfloat162_rn(v0, v1);
+                if (P.y32) *reinterpret_cast<float2 *>(P.y32 + o) = make_float2(v0, v1);
+            }
+}
+
+struct WgradP {
+    ConvIn in;             // forward input
+    const bf16 *dy;        // [N][H][W][Cout] gradient at the pre-activation
+    int N, H, W, Cin, Cout;
+    float *dw;             // [9][Cout][Cin], accumulated
+    int px_per_warp;       // pixels per warp (multiple of 32)
+};
+
+// dw[tap][co][ci] += sum_p dy[p][co] x[p + offset(tap)][ci].  Each warp owns a
+// 32 (co) x 32 (ci) tile and a slice of pixels (split K), staging 32-pixel
+// chunks of dy and of the shifted input in its own shared memory and reading
+// both transposed with ldmatrix.trans.
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradP P) {
+    constexpr int LDS = 40;
+    __shared__ __align__(16) bf16 sA[4][2][32 * LDS];
+    __shared__ __align__(16) bf16 sB[4][2][32 * LDS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int co0 = blockIdx.y * 32;
+    const int kci = P.Cin / 32;
+    const int tap = blockIdx.z / kci, ci0 = (blockIdx.z % kci) * 32;
+    const int ky = tap / 3, kx = tap % 3;
+    const long long P_tot = (long long)P.N * P.H * P.W;
+    const long long p_begin = ((long long)blockIdx.x * 4 + warp) * P.px_per_warp;
+    const long long p_end = min(P_tot, p_begin + P.px_per_warp);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    if (p_begin < p_end) {
+        bf16 *A0 = sA[warp][0], *B0 = sB[warp][0];
+        auto load = [&](long long p0, int buf) {
+            bf16 *As = buf ? sA[warp][1] : A0;
+            bf16 *Bs = buf ? sB[warp][1] : B0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = lane + 32 * q, px = idx >> 2, part = idx & 3;
+                const long long p = p0 + px;
+                const bool in_range = p < p_end;
+                const int x = in_range ? (int)(p % P.W) : 0;
+                const long long ny = in_range ? p / P.W : 0;
+                const int yrow = (int)(ny % P.H), n = (int)(ny / P.H);
+                cp_async16(&As[px * LDS + part * 8], in_range ? P.dy + (size_t)p * P.Cout + co0 + part * 8 : P.dy,
+                           in_range ? 16 : 0);
+                const int yy = yrow + ky - 1, xx = x + kx - 1;
+                const bool ok = in_range && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
+                const bf16 *src = ok ? gather(P.in, n, P.H, P.W, yy, xx, ci0 + part * 8) : P.dy;
+                cp_async16(&Bs[px * LDS + part * 8], src, ok ? 16 : 0);
+            }
+            cp_async_commit();
+        };
+        const int nch = (int)((p_end - p_begin + 31) / 32);
+        load(p_begin, 0);
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) {
+                load(p_begin + 32ll * (c + 1), (c + 1) & 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const bf16 *A = sA[warp][c & 1];
+            const bf16 *B = sB[warp][c & 1];
+#pragma unroll
+            for (int ks = 0; ks < 32; ks += 16) {
+                uint32_t a[2][4], bb[4][2];
+                const int q = lane >> 3, r = lane & 7;
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi)   // A = dy^T: rows co, cols pixels
+                    ldsm_x4_t(a[mi], &A[(ks + ((q >> 1) << 3) + r) * LDS + mi * 16 + ((q & 1) << 3)]);
+#pragma unroll
+                for (int nj = 0; nj < 4; nj += 2) {   // B = x: rows pixels, cols ci
+                    uint32_t r4[4];
+                    ldsm_x4_t(r4, &B[(ks + ((q & 1) << 3) + r) * LDS + nj * 8 + ((q >> 1) << 3)]);
+                    bb[nj][0] = r4[0];
+                    bb[nj][1] = r4[1];
+                    bb[nj + 1][0] = r4[2];
+                    bb[nj + 1][1] = r4[3];
+                }
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                    for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], a[mi], bb[nj][0], bb[nj][1]);
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int co = co0 + mi * 16 + (lane >> 2) + h * 8;
+                const int ci = ci0 + nj * 8 + (lane & 3) * 2;
+                float *dst = P.dw + ((size_t)tap * P.Cout + co) * P.Cin + ci;
+                if (acc[mi][nj][2 * h] != 0.f) atomicAdd(dst, acc[mi][nj][2 * h]);
+                if (acc[mi][nj][2 * h + 1] != 0.f) atomicAdd(dst + 1, acc[mi][nj][2 * h + 1]);
+            }
+}
+
+// ------------------------------------------------------------------ small kernels
+
+// rf, quad [B][H][W] (fp32, the tracer's layout) -> x bf16 NHWC with 32 channels
+// (rf, quad, zeros) and the normalised input fp32 NHWC [B][H][W][2].
+__global__ void k_prep(const float *rf, const float *quad, int B, int H, int W, float inv_scale, bf16 *x,
+                       float *xn) {
+    const long long n = (long long)B * H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const float a = rf[p] * inv_scale, q = quad[p] * inv_scale;
+        const bf16 ab = __float2bfloat16_rn(a), qb = __float2bfloat16_rn(q);
+        uint4 *dst = reinterpret_cast<uint4 *>(x + (size_t)p * 32);
+        __nv_bfloat162 head = __halves2bfloat162(ab, qb);
+        uint4 first = make_uint4(*reinterpret_cast<uint32_t *>(&head), 0u, 0u, 0u);
+        dst[0] = first;
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+        dst[2] = make_uint4(0u, 0u, 0u, 0u);
+        dst[3] = make_uint4(0u, 0u, 0u, 0u);
+        xn[2 * p] = __bfloat162float(ab);
+        xn[2 * p + 1] = __bfloat162float(qb);
+    }
+}
+
+// 2x2 average pooling, NHWC bf16.
+__global__ void k_pool2(const bf16 *x, bf16 *y, int B, int H, int W, int C) {
+    const int Ho = H / 2, Wo = W / 2;
+    const long long n = (long long)B * Ho * Wo * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long r = i / C;
+        const int xo = (int)(r % Wo);
+        r /= Wo;
+        const int yo = (int)(r % Ho), b = (int)(r / Ho);
+        const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * C + c;
+        const float s = __bfloat162float(x[base]) + __bfloat162float(x[base + C]) +
+                        __bfloat162float(x[base + (size_t)W * C]) + __bfloat162float(x[base + (size_t)W * C + C]);
+        y[i] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// d[i] = d[i] * (act[i] > 0)
+__global__ void k_relu_mask(bf16 *d, const bf16 *act, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(act[i]) > 0.f)) d[i] = __float2bfloat16_rn(0.f);
+}
+
+// Split the gradient of a concatenated decoder input [B][H][W][C1 + C2]: the
+// first C1 channels came from the nearest-upsampled half-resolution tensor (sum
+// over each 2x2 block), the rest from the skip tensor (copied).
+__global__ void k_unconcat(const bf16 *dcat, int B, int H, int W, int C1, int C2, bf16 *dlow, bf16 *dskip) {
+    const int Ho = H / 2, Wo = W / 2, C = C1 + C2;
+    const long long nlow = (long long)B * Ho * Wo * C1, nskip = (long long)B * H * W * C2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlow + nskip;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < nlow) {
+            const int c = (int)(i % C1);
+            long long r = i / C1;
+            const int xo = (int)(r % Wo);
+            r /= Wo;
+            const int yo = (int)(r % Ho), b = (int)(r / Ho);
+            const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * C + c;
+            const float s = __bfloat162float(dcat[base]) + __bfloat162float(dcat[base + C]) +
+                            __bfloat162float(dcat[base + (size_t)W * C]) + __bfloat162float(dcat[base + (size_t)W * C + C]);
+            dlow[i] = __float2bfloat16_rn(s);
+        } else {
+            const long long j = i - nlow;
+            const int c = (int)(j % C2);
+            const long long p = j / C2;
+            dskip[j] = dcat[(size_t)p * C + C1 + c];
+        }
+    }
+}
+
+// d[b, y, x, c] += dp[b, y/2, x/2, c] / 4 (gradient of 2x2 average pooling)
+__global__ void k_pool2_bwd_add(bf16 *d, const bf16 *dp, int B, int H, int W, int C) {
+    const long long n = (long long)B * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long r = i / C;
+        const int x = (int)(r % W);
+        r /= W;
+        const int y = (int)(r % H), b = (int)(r / H);
+        const float add = 0.25f * __bfloat162float(dp[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c]);
+        d[i] = __float2bfloat16_rn(__bfloat162float(d[i]) + add);
+    }
+}
+
+// W'[tap][ci][co] = W[8 - tap][co][ci]: weights of the data gradient.
+__global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
+    const long long n = 9ll * Cout * Cin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(i % Cout);
+        long long r = i / Cout;
+        const int ci = (int)(r % Cin);
+        const int tap = (int)(r / Cin);
+        wt[i] = w[((size_t)(8 - tap) * Cout + co) * Cin + ci];
+    }
+}
+
+// db[c] += sum over pixels of d[p][c]; thread t owns channel t % C (C divides the
+// block, which has max(256, C) <= 1024 threads).
+__global__ void __launch_bounds__(1024) k_bias_grad(const bf16 *d, long long P, int C, float *db) {
+    __shared__ float s[1024];
+    const int c = threadIdx.x % C, lanes = blockDim.x / C, pl = threadIdx.x / C;
+    float acc = 0.f;
+    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes)
+        acc += __bfloat162float(d[(size_t)p * C + c]);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int q = 0; q < lanes; ++q) t += s[q * C + threadIdx.x];
+        if (t != 0.f) atomicAdd(&db[threadIdx.x], t);
+    }
+}
+
+// Residual head: y = x + W d1 + b (1x1, C -> 2), fp32; also writes the output
+// back in the tracer's layout, rescaled.
+__global__ void k_head_fwd(const bf16 *d1, const float *xn, const float *wh, const float *bh, int C, long long P,
+                           float scale, float *yn, float *out_rf, float *out_quad) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        float s0 = bh[0] + xn[2 * p], s1 = bh[1] + xn[2 * p + 1];
+        const bf16 *f = d1 + (size_t)p * C;
+        for (int c = 0; c < C; ++c) {
+            const float v = __bfloat162float(f[c]);
+            s0 += wh[c] * v;
+            s1 += wh[C + c] * v;
+        }
+        yn[2 * p] = s0;
+        yn[2 * p + 1] = s1;
+        if (out_rf) {
+            out_rf[p] = s0 * scale;
+            out_quad[p] = s1 * scale;
+        }
+    }
+}
+
+// Mean squared error against the (normalised) target and its gradient.
+__global__ void k_loss(const float *yn, const float *t_rf, const float *t_quad, long long P, float inv_scale,
+                       float *g, double *loss) {
+    const float inv_n = 1.f / (2.f * (float)P);
+    float local = 0.f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const float d0 = yn[2 * p] - t_rf[p] * inv_scale, d1 = yn[2 * p + 1] - t_quad[p] * inv_scale;
+        local += d0 * d0 + d1 * d1;
+        g[2 * p] = 2.f * d0 * inv_n;
+        g[2 * p + 1] = 2.f * d1 * inv_n;
+    }
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_down_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0 && local != 0.f) atomicAdd(loss, (double)(local * inv_n));
+}
+
+// Head backward: dWh, dbh (fp32) and the masked gradient of d1 (bf16).  One
+// warp walks a range of pixels; lane l owns channels l and l + 32 (C <= 64).
+__global__ void __launch_bounds__(256) k_head_bwd(const float *g, const bf16 *d1, const float *wh, int C, long long P,
+                                                  float *dwh, float *dbh, bf16 *dd1) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    float a0[2] = {0.f, 0.f}, a1[2] = {0.f, 0.f}, b0 = 0.f, b1 = 0.f;
+    for (long long p = wid; p < P; p += warps) {
+        const float g0 = g[2 * p], g1 = g[2 * p + 1];
+        b0 += g0;
+        b1 += g1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c >= C) continue;
+            const float v = __bfloat162float(d1[(size_t)p * C + c]);
+            a0[h] += g0 * v;
+            a1[h] += g1 * v;
+            dd1[(size_t)p * C + c] = __float2bfloat16_rn(v > 0.f ? g0 * wh[c] + g1 * wh[C + c] : 0.f);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        if (c >= C) continue;
+        if (a0[h] != 0.f) atomicAdd(&dwh[c], a0[h]);
+        if (a1[h] != 0.f) atomicAdd(&dwh[C + c], a1[h]);
+    }
+    if (lane == 0) {
+        atomicAdd(&dbh[0], b0);
+        atomicAdd(&dbh[1], b1);
+    }
+}
+
+// Adam (bias-corrected moments) on the fp32 master parameters; refreshes the bf16 copies.
+__global__ void k_adam(float *p, const float *g, float *m, float *v, bf16 *pb, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        pb[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void k_to_bf16(const float *p, bf16 *pb, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+int grid_for(long long n, int block = 256) { return (int)std::min<long long>(4096, (n + block - 1) / block + 1); }
+
+// ------------------------------------------------------------------ network
+
+constexpr int kNumConv = 14;
+
+struct Fail {
+    ur_status code;
+    std::string msg;
+};
+[[noreturn]] void fail(ur_status c, const std::string &m) { throw Fail{c, m}; }
+void ck(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? UR_ERR_OOM : UR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+struct Tensor {
+    bf16 *p = nullptr;
+    int H = 0, W = 0, C = 0;
+};
+
+}  // namespace
+
+struct ur_nn {
+    int device = 0, sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int max_batch = 0, H = 0, W = 0, width = 32;
+    float scale = 1.f;
+    long long step = 0;
+    // parameters: per conv [9][Cout][Cin] then [Cout]; head [2][C] then [2]
+    int cin[kNumConv], cout[kNumConv];
+    size_t woff[kNumConv], boff[kNumConv], hw_off = 0, hb_off = 0, n_params = 0;
+    float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    bf16 *pbf = nullptr, *wt = nullptr;   // bf16 copies; transposed weights scratch
+    // activations and gradients
+    bf16 *x = nullptr;
+    float *xn = nullptr, *yn = nullptr, *gy = nullptr;
+    Tensor act[kNumConv];    // post-ReLU outputs of every conv
+    Tensor pool[3];          // pooled e1, e2, e3
+    Tensor gbuf[4];          // gradient scratch per level (two of the largest sizes)
+    bf16 *gcat = nullptr, *gA = nullptr, *gB = nullptr, *gSkip[3] = {nullptr, nullptr, nullptr}, *gLow = nullptr;
+    double *loss = nullptr;
+    std::vector<void *> allocs;
+
+    void *alloc(size_t bytes) {
+        void *p = nullptr;
+        ck(cudaMalloc(&p, std::max<size_t>(bytes, 256)), "cudaMalloc");
+        allocs.push_back(p);
+        return p;
+    }
+};
+
+namespace {
+
+template <class F>
+ur_status nn_guard(ur_nn *nn, F &&f) {
+    if (!nn) return UR_ERR_INVALID_ARG;
+    try {
+        nn->err.clear();
+        f();
+        return UR_OK;
+    } catch (const Fail &e) {
+        nn->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        nn->err = "host allocation failed";
+        return UR_ERR_OOM;
+    } catch (...) {
+        nn->err = "unexpected host exception";
+        return UR_ERR_CUDA;
+    }
+}
+
+void conv_fwd(ur_nn *nn, const ConvIn &in, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
+              bf16 *y, float *y32, bool relu) {
+    ConvP P{in, B, H, W, Cin, Cout, w, bias, y, y32, relu ? 1 : 0};
+    if (Cout % 64 == 0) {
+        dim3 grid(B * H * ((W + 63) / 64), Cout / 64);
+        k_conv3x3<2, 2><<<grid, 128, 0, nn->stream>>>(P);
+    } else {
+        dim3 grid(B * H * ((W + 127) / 128), Cout / 32);
+        k_conv3x3<4, 1><<<grid, 128, 0, nn->stream>>>(P);
+    }
+    ck(cudaGetLastError(), "conv kernel");
+}
+
+void conv_wgrad(ur_nn *nn, const ConvIn &in, const bf16 *dy, int B, int H, int W, int Cin, int Cout, float *dw) {
+    const long long P_tot = (long long)B * H * W;
+    const int px_per_warp = (int)std::max<long long>(128, std::min<long long>(4096, (P_tot / 2048 + 31) / 32 * 32));
+    const long long warps = (P_tot + px_per_warp - 1) / px_per_warp;
+    WgradP W_{in, dy, B, H, W, Cin, Cout, dw, px_per_warp};
+    dim3 grid((unsigned)((warps + 3) / 4), Cout / 32, 9 * (Cin / 32));
+    k_conv3x3_wgrad<<<grid, 128, 0, nn->stream>>>(W_);
+    ck(cudaGetLastError(), "wgrad kernel");
+}
+
+void bias_grad(ur_nn *nn, const bf16 *d, long long P, int C, float *db) {
+    const int block = std::max(256, C);
+    k_bias_grad<<<(int)std::min<long long>(1024, (P * C + block - 1) / block), block, 0, nn->stream>>>(d, P, C, db);
+    ck(cudaGetLastError(), "bias gradient kernel");
+}
+
+// Inputs of every conv of the network at batch B.
+struct Layer {
+    ConvIn in;
+    int H, W;
+};
+
+Layer layer_in(ur_nn *nn, int l) {
+    const int H = nn->H, W = nn->W;
+    auto full = [](const Tensor &t) { return ConvIn{t.p, t.C, 0, nullptr, 0}; };
+    switch (l) {
+        case 0: return {ConvIn{nn->x, 32, 0, nullptr, 0}, H, W};
+        case 1: return {full(nn->act[0]), H, W};
+        case 2: return {full(nn->pool[0]), H / 2, W / 2};
+        case 3: return {full(nn->act[2]), H / 2, W / 2};
+        case 4: return {full(nn->pool[1]), H / 4, W / 4};
+        case 5: return {full(nn->act[4]), H / 4, W / 4};
+        case 6: return {full(nn->pool[2]), H / 8, W / 8};
+        case 7: return {full(nn->act[6]), H / 8, W / 8};
+        case 8: return {ConvIn{nn->act[7].p, nn->act[7].C, 1, nn->act[5].p, nn->act[5].C}, H / 4, W / 4};
+        case 9: return {full(nn->act[8]), H / 4, W / 4};
+        case 10: return {ConvIn{nn->act[9].p, nn->act[9].C, 1, nn->act[3].p, nn->act[3].C}, H / 2, W / 2};
+        case 11: return {full(nn->act[10]), H / 2, W / 2};
+        case 12: return {ConvIn{nn->act[11].p, nn->act[11].C, 1, nn->act[1].p, nn->act[1].C}, H, W};
+        default: return {full(nn->act[12]), H, W};
+    }
+}
+
+void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad) {
+    const long long P = (long long)B * nn->H * nn->W;
+    k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, 1.f / nn->scale, nn->x, nn->xn);
+    ck(cudaGetLastError(), "prep kernel");
+    for (int l = 0; l < kNumConv; ++l) {
+        const Layer L = layer_in(nn, l);
+        conv_fwd(nn, L.in, B, L.H, L.W, nn->cin[l], nn->cout[l], nn->pbf + nn->woff[l], nn->params + nn->boff[l],
+                 nn->act[l].p, nullptr, true);
+        if (l == 1 || l == 3 || l == 5) {   // pool after each encoder block
+            const int q = l / 2;
+            k_pool2<<<grid_for((long long)B * L.H * L.W * nn->cout[l] / 4), 256, 0, nn->stream>>>(
+                nn->act[l].p, nn->pool[q].p, B, L.H, L.W, nn->cout[l]);
+            ck(cudaGetLastError(), "pool kernel");
+        }
+    }
+    k_head_fwd<<<grid_for(P), 256, 0, nn->stream>>>(nn->act[13].p, nn->xn, nn->params + nn->hw_off,
+                                                    nn->params + nn->hb_off, nn->width, P, nn->scale,
+                                                    nn->yn, out_rf, out_quad);
+    ck(cudaGetLastError(), "head kernel");
+}
+
+// Backward of one block (convs la, lb) given the gradient at lb's output;
+// leaves the gradient of la's input in `din` (full concatenated channels) if din.
+void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din) {
+    const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
+    const long long nb = (long long)B * Lb.H * Lb.W * nn->cout[lb];
+    k_relu_mask<<<grid_for(nb), 256, 0, nn->stream>>>(d_out, nn->act[lb].p, nb);
+    conv_wgrad(nn, Lb.in, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
+    bias_grad(nn, d_out, (long long)B * Lb.H * Lb.W, nn->cout[lb], nn->grads + nn->boff[lb]);
+    k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
+                                                                                  nn->cout[lb], nn->cin[lb]);
+    conv_fwd(nn, ConvIn{d_out, nn->cout[lb], 0, nullptr, 0}, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr,
+             scratch, nullptr, false);
+    const long long na = (long long)B * La.H * La.W * nn->cout[la];
+    k_relu_mask<<<grid_for(na), 256, 0, nn->stream>>>(scratch, nn->act[la].p, na);
+    conv_wgrad(nn, La.in, scratch, B, La.H, La.W, nn->cin[la], nn->cout[la], nn->grads + nn->woff[la]);
+    bias_grad(nn, scratch, (long long)B * La.H * La.W, nn->cout[la], nn->grads + nn->boff[la]);
+    if (din) {
+        k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
+                                                                                      nn->cout[la], nn->cin[la]);
+        conv_fwd(nn, ConvIn{scratch, nn->cout[la], 0, nullptr, 0}, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt,
+                 nullptr, din, nullptr, false);
+    }
+    ck(cudaGetLastError(), "block backward");
+}
+
+double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *t_rf, const float *t_quad) {
+    forward(nn, B, rf, quad, nullptr, nullptr);
+    const long long P = (long long)B * nn->H * nn->W;
+    ck(cudaMemsetAsync(nn->loss, 0, sizeof(double), nn->stream), "memset loss");
+    ck(cudaMemsetAsync(nn->grads, 0, sizeof(float) * nn->n_params, nn->stream), "memset grads");
+    k_loss<<<grid_for(P), 256, 0, nn->stream>>>(nn->yn, t_rf, t_quad, P, 1.f / nn->scale, nn->gy, nn->loss);
+    const int C = nn->width;
+    // head
+    bf16 *g_full_a = nn->gA, *g_full_b = nn->gB;
+    k_head_bwd<<<nn->sms * 8, 256, 0, nn->stream>>>(nn->gy, nn->act[13].p, nn->params + nn->hw_off, C, P,
+                                                    nn->grads + nn->hw_off, nn->grads + nn->hb_off, g_full_a);
+    ck(cudaGetLastError(), "head backward");
+    // gradient of d1b's output is g_full_a (already masked by d1 > 0; masking again is harmless)
+    const int H = nn->H, W = nn->W;
+    // decoder level 1: concat(up(d2), e1)
+    block_bwd(nn, B, 12, 13, g_full_a, g_full_b, nn->gcat);
+    k_unconcat<<<grid_for((long long)B * H * W * (3 * C)), 256, 0, nn->stream>>>(nn->gcat, B, H, W, 2 * C, C, nn->gLow,
+                                                                                  nn->gSkip[0]);
+    ck(cudaGetLastError(), "unconcat");
+    // decoder level 2: gradient of d2 (half resolution) is gLow
+    bf16 *d2 = nn->gbuf[1].p;
+    ck(cudaMemcpyAsync(d2, nn->gLow, sizeof(bf16) * (size_t)B * (H / 2) * (W / 2) * 2 * C, cudaMemcpyDeviceToDevice,
+                       nn->stream), "copy");
+    block_bwd(nn, B, 10, 11, d2, nn->gbuf[2].p, nn->gcat);
+    k_unconcat<<<grid_for((long long)B * (H / 2) * (W / 2) * (6 * C)), 256, 0, nn->stream>>>(
+        nn->gcat, B, H / 2, W / 2, 4 * C, 2 * C, nn->gLow, nn->gSkip[1]);
+    bf16 *d3 = nn->gbuf[1].p;
+    ck(cudaMemcpyAsync(d3, nn->gLow, sizeof(bf16) * (size_t)B * (H / 4) * (W / 4) * 4 * C, cudaMemcpyDeviceToDevice,
+                       nn->stream), "copy");
+    block_bwd(nn, B, 8, 9, d3, nn->gbuf[2].p, nn->gcat);
+    k_unconcat<<<grid_for((long long)B * (H / 4) * (W / 4) * (12 * C)), 256, 0, nn->stream>>>(
+        nn->gcat, B, H / 4, W / 4, 8 * C, 4 * C, nn->gLow, nn->gSkip[2]);
+    // bottleneck: gradient of e4 is gLow
+    bf16 *d4 = nn->gbuf[1].p;
+    ck(cudaMemcpyAsync(d4, nn->gLow, sizeof(bf16) * (size_t)B * (H / 8) * (W / 8) * 8 * C, cudaMemcpyDeviceToDevice,
+                       nn->stream), "copy");
+    block_bwd(nn, B, 6, 7, d4, nn->gbuf[2].p, nn->gbuf[3].p);   // d(pool3) at H/8
+    k_pool2_bwd_add<<<grid_for((long long)B * (H / 4) * (W / 4) * 4 * C), 256, 0, nn->stream>>>(
+        nn->gSkip[2], nn->gbuf[3].p, B, H / 4, W / 4, 4 * C);
+    block_bwd(nn, B, 4, 5, nn->gSkip[2], nn->gbuf[2].p, nn->gbuf[3].p);   // d(pool2) at H/4
+    k_pool2_bwd_add<<<grid_for((long long)B * (H / 2) * (W / 2) * 2 * C), 256, 0, nn->stream>>>(
+        nn->gSkip[1], nn->gbuf[3].p, B, H / 2, W / 2, 2 * C);
+    block_bwd(nn, B, 2, 3, nn->gSkip[1], nn->gbuf[2].p, nn->gbuf[3].p);   // d(pool1) at H/2
+    k_pool2_bwd_add<<<grid_for((long long)B * H * W * C), 256, 0, nn->stream>>>(nn->gSkip[0], nn->gbuf[3].p, B, H, W, C);
+    block_bwd(nn, B, 0, 1, nn->gSkip[0], nn->gbuf[2].p, nullptr);
+    ck(cudaGetLastError(), "backward");
+    double loss = 0.0;
+    ck(cudaMemcpyAsync(&loss, nn->loss, sizeof(double), cudaMemcpyDeviceToHost, nn->stream), "read loss");
+    ck(cudaStreamSynchronize(nn->stream), "train step");
+    return loss;
+}
+
+// deterministic standard normals for the initial weights (splitmix64 + Box-Muller)
+struct Rng {
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uni() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal() { return std::sqrt(-2.0 * std::log(uni())) * std::cos(6.283185307179586 * uni()); }
+};
+
+}  // namespace
+
+extern "C" {
+
+ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch, int n_el, int n_s, int width,
+                       uint64_t seed) {
+    if (!out) return UR_ERR_INVALID_ARG;
+    *out = nullptr;
+    ur_nn *nn = new (std::nothrow) ur_nn();
+    if (!nn) return UR_ERR_OOM;
+    ur_status st = nn_guard(nn, [&] {
+        if (max_batch < 1 || max_batch > 64 || n_el < 8 || n_s < 8 || n_el % 8 || n_s % 8 || (width != 32 && width != 64))
+            fail(UR_ERR_INVALID_ARG, "need 1 <= batch <= 64, n_el and n_s multiples of 8, width 32 or 64");
+        int n = 0;
+        ck(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+        if (device < 0 || device >= n) fail(UR_ERR_INVALID_ARG, "bad device index");
+        nn->device = device;
+        ck(cudaSetDevice(device), "cudaSetDevice");
+        ck(cudaDeviceGetAttribute(&nn->sms, cudaDevAttrMultiProcessorCount, device), "SM count");
+        if (cuda_stream) {
+            nn->stream = (cudaStream_t)cuda_stream;
+        } else {
+            ck(cudaStreamCreateWithFlags(&nn->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            nn->own_stream = true;
+        }
+        nn->max_batch = max_batch;
+        nn->H = n_el;
+        nn->W = n_s;
+        nn->width = width;
+        const int C = width;
+        const int ci[kNumConv] = {32, C, C, 2 * C, 2 * C, 4 * C, 4 * C, 8 * C, 12 * C, 4 * C, 6 * C, 2 * C, 3 * C, C};
+        const int co[kNumConv] = {C, C, 2 * C, 2 * C, 4 * C, 4 * C, 8 * C, 8 * C, 4 * C, 4 * C, 2 * C, 2 * C, C, C};
+        size_t off = 0;
+        for (int l = 0; l < kNumConv; ++l) {
+            nn->cin[l] = ci[l];
+            nn->cout[l] = co[l];
+            nn->woff[l] = off;
+            off += 9ull * ci[l] * co[l];
+            nn->boff[l] = off;
+            off += co[l];
+            off = (off + 7) / 8 * 8;   // keep every weight tensor 16-byte aligned in bf16
+        }
+        nn->hw_off = off;
+        off += 2ull * C;
+        nn->hb_off = off;
+        off += 2;
+        nn->n_params = (off + 7) / 8 * 8;
+        // He-normal initialisation on the true fan-in (the first conv sees 2 real channels)
+        std::vector<float> h(nn->n_params, 0.f);
+        Rng rng{seed * 0x2545F4914F6CDD1Dull + 1};
+        for (int l = 0; l < kNumConv; ++l) {
+            const int real_ci = l == 0 ? 2 : ci[l];
+            const double sd = std::sqrt(2.0 / (9.0 * real_ci));
+            for (int t = 0; t < 9; ++t)
+                for (int o = 0; o < co[l]; ++o)
+                    for (int i = 0; i < real_ci; ++i) h[nn->woff[l] + ((size_t)t * co[l] + o) * ci[l] + i] = (float)(sd * rng.normal());
+        }
+        for (int i = 0; i < 2 * C; ++i) h[nn->hw_off + i] = (float)(std::sqrt(2.0 / C) * 0.1 * rng.normal());
+        nn->params = (float *)nn->alloc(sizeof(float) * nn->n_params);
+        nn->grads = (float *)nn->alloc(sizeof(float) * nn->n_params);
+        nn->m = (float *)nn->alloc(sizeof(float) * nn->n_params);
+        nn->v = (float *)nn->alloc(sizeof(float) * nn->n_params);
+        nn->pbf = (bf16 *)nn->alloc(sizeof(bf16) * nn->n_params);
+        size_t wt_max = 0;
+        for (int l = 0; l < kNumConv; ++l) wt_max = std::max<size_t>(wt_max, (size_t)9 * ci[l] * co[l]);
+        nn->wt = (bf16 *)nn->alloc(sizeof(bf16) * wt_max);
+        ck(cudaMemcpy(nn->params, h.data(), sizeof(float) * nn->n_params, cudaMemcpyHostToDevice), "copy params");
+        ck(cudaMemset(nn->m, 0, sizeof(float) * nn->n_params), "memset");
+        ck(cudaMemset(nn->v, 0, sizeof(float) * nn->n_params), "memset");
+        k_to_bf16<<<grid_for((long long)nn->n_params), 256, 0, nn->stream>>>(nn->params, nn->pbf, (long long)nn->n_params);
+        ck(cudaGetLastError(), "to bf16");
+        // activations
+        const size_t B = max_batch, H = n_el, W = n_s;
+        const int lh[kNumConv] = {1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1};
+        for (int l = 0; l < kNumConv; ++l) {
+            nn->act[l] = Tensor{(bf16 *)nn->alloc(sizeof(bf16) * B * (H / lh[l]) * (W / lh[l]) * co[l]), (int)(H / lh[l]),
+                                (int)(W / lh[l]), co[l]};
+        }
+        for (int q = 0; q < 3; ++q) {
+            const int f = 2 << q, c = C << q;
+            nn->pool[q] = Tensor{(bf16 *)nn->alloc(sizeof(bf16) * B * (H / f) * (W / f) * c), (int)(H / f), (int)(W / f), c};
+        }
+        nn->x = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 32);
+        nn->xn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
+        nn->yn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
+        nn->gy = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
+        const size_t big = B * H * W * 4 * C;   // largest per-level tensor (full resolution, up to 4C channels)
+        nn->gA = (bf16 *)nn->alloc(sizeof(bf16) * big);
+        nn->gB = (bf16 *)nn->alloc(sizeof(bf16) * big);
+        nn->gcat = (bf16 *)nn->alloc(sizeof(bf16) * big);
+        nn->gLow = (bf16 *)nn->alloc(sizeof(bf16) * big);
+        for (int q = 0; q < 4; ++q) nn->gbuf[q] = Tensor{(bf16 *)nn->alloc(sizeof(bf16) * big), 0, 0, 0};
+        for (int q = 0; q < 3; ++q) nn->gSkip[q] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> q) * (W >> q) * (C << q));
+        nn->loss = (double *)nn->alloc(sizeof(double));
+        ck(cudaStreamSynchronize(nn->stream), "init");
+    });
+    if (st != UR_OK) {
+        for (void *p : nn->allocs) cudaFree(p);
+        if (nn->own_stream) cudaStreamDestroy(nn->stream);
+        delete nn;
+        return st;
+    }
+    *out = nn;
+    return UR_OK;
+}
+
+ur_status ur_nn_destroy(ur_nn *nn) {
+    if (!nn) return UR_ERR_INVALID_ARG;
+    cudaSetDevice(nn->device);
+    cudaStreamSynchronize(nn->stream);
+    for (void *p : nn->allocs) cudaFree(p);
+    if (nn->own_stream) cudaStreamDestroy(nn->stream);
+    delete nn;
+    return UR_OK;
+}
+
+const char *ur_nn_last_error(const ur_nn *nn) { return nn ? nn->err.c_str() : "null network"; }
+
+ur_status ur_nn_param_count(const ur_nn *nn, uint64_t *n) {
+    if (!nn || !n) return UR_ERR_INVALID_ARG;
+    *n = nn->n_params;
+    return UR_OK;
+}
+
+ur_status ur_nn_params(ur_nn *nn, float *get, const float *set) {
+    return nn_guard(nn, [&] {
+        ck(cudaSetDevice(nn->device), "cudaSetDevice");
+        ck(cudaStreamSynchronize(nn->stream), "pending work");
+        if (get) ck(cudaMemcpy(get, nn->params, sizeof(float) * nn->n_params, cudaMemcpyDefault), "get params");
+        if (set) {
+            ck(cudaMemcpy(nn->params, set, sizeof(float) * nn->n_params, cudaMemcpyDefault), "set params");
+            k_to_bf16<<<grid_for((long long)nn->n_params), 256, 0, nn->stream>>>(nn->params, nn->pbf, (long long)nn->n_params);
+            ck(cudaGetLastError(), "to bf16");
+            ck(cudaMemsetAsync(nn->m, 0, sizeof(float) * nn->n_params, nn->stream), "reset m");
+            ck(cudaMemsetAsync(nn->v, 0, sizeof(float) * nn->n_params, nn->stream), "reset v");
+            nn->step = 0;
+            ck(cudaStreamSynchronize(nn->stream), "set params");
+        }
+    });
+}
+
+ur_status ur_nn_set_scale(ur_nn *nn, float scale) {
+    return nn_guard(nn, [&] {
+        if (!(scale > 0.f) || !std::isfinite(scale)) fail(UR_ERR_INVALID_ARG, "scale must be positive");
+        nn->scale = scale;
+    });
+}
+
+ur_status ur_nn_forward(ur_nn *nn, const float *rf, const float *quad, int batch, float *out_rf, float *out_quad) {
+    return nn_guard(nn, [&] {
+        ck(cudaSetDevice(nn->device), "cudaSetDevice");
+        if (batch < 1 || batch > nn->max_batch) fail(UR_ERR_INVALID_ARG, "batch out of range");
+        if (!rf || !quad || !out_rf || !out_quad) fail(UR_ERR_INVALID_ARG, "inputs and outputs are required");
+        forward(nn, batch, rf, quad, out_rf, out_quad);
+    });
+}
+
+ur_status ur_nn_train_step(ur_nn *nn, const float *rf, const float *quad, const float *t_rf, const float *t_quad,
+                           int batch, float lr, float *loss, float *grad_out) {
+    return nn_guard(nn, [&] {
+        ck(cudaSetDevice(nn->device), "cudaSetDevice");
+        if (batch < 1 || batch > nn->max_batch) fail(UR_ERR_INVALID_ARG, "batch out of range");
+        if (!rf || !quad || !t_rf || !t_quad) fail(UR_ERR_INVALID_ARG, "inputs and targets are required");
+        if (!(lr >= 0.f)) fail(UR_ERR_INVALID_ARG, "lr must be >= 0");
+        const double l = train(nn, batch, rf, quad, t_rf, t_quad);
+        if (loss) *loss = (float)l;
+        if (grad_out) ck(cudaMemcpy(grad_out, nn->grads, sizeof(float) * nn->n_params, cudaMemcpyDefault), "grad out");
+        if (lr > 0.f) {
+            nn->step += 1;
+            const float b1 = 0.9f, b2 = 0.999f;
+            const float c1 = 1.f - std::pow(b1, (float)nn->step), c2 = 1.f - std::pow(b2, (float)nn->step);
+            k_adam<<<grid_for((long long)nn->n_params), 256, 0, nn->stream>>>(nn->params, nn->grads, nn->m, nn->v, nn->pbf,
+                                                                            (long long)nn->n_params, lr, b1, b2, 1e-8f, c1, c2);
+            ck(cudaGetLastError(), "adam kernel");
+        }
+    });
+}
+
+}  // extern "C"

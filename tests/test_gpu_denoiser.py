@@ -1,0 +1,125 @@
+"""The BF16 U-Net denoiser through the C ABI against the FP64 reference
+(oracle/denoiser.py) with the same BF16 rounding of stored tensors: forward
+output, full parameter gradient, one Adam update, and that training lowers the
+loss.
+
+Tolerances: both sides round the same 17 stored tensors (input, 14 conv
+outputs, 3 pooled tensors) to BF16 (unit roundoff u = 2^-9), but their sums
+are accumulated in different orders (FP32 on the tensor cores, FP64 here), so
+an element near a rounding boundary can round one ulp (2u) apart and the flip
+spreads through later layers; the output then differs by about u sqrt(17)
+~ 8e-3 relative in the learned part.  A wrong tap, edge, bias or channel
+offset gives errors 10-100x larger.  Gradients also store every data
+gradient in BF16 (28 more roundings) and sum small bias gradients over few
+pixels, hence the looser bounds there."""
+import numpy as np
+import pytest
+
+from oracle import denoiser as D
+from _parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+H, W, B = 16, 64, 2
+
+
+@pytest.fixture(scope="module")
+def net():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05828_gb300 as ur
+    dn = ur.Denoiser(0, max_batch=B, n_el=H, n_s=W, width=32, seed=3)
+    rng = np.random.default_rng(4)
+    p = dn.params()
+    lay = ur.nn_layout(32)
+    for name, (wo, ws, bo, co) in lay.items():   # non-zero biases exercise the bias paths
+        p[bo:bo + co] = rng.standard_normal(co).astype(np.float32) * 0.05
+    wo, ws, bo, co = lay["head"]                 # a head large enough that the residual matters
+    p[wo:wo + 64] = rng.standard_normal(64).astype(np.float32) * 0.3
+    dn.set_params(p)
+    dn.set_scale(2.0)
+    return torch, ur, dn, lay
+
+
+def to_oracle(p, lay):
+    out = {}
+    for name, (wo, ws, bo, co) in lay.items():
+        w = p[wo:wo + int(np.prod(ws))].reshape(ws).astype(np.float64)
+        if name == "e1a":
+            w = w[:, :, :2]
+        out[name + ".w"] = w
+        out[name + ".b"] = p[bo:bo + co].astype(np.float64)
+    return out
+
+
+def inputs(torch, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((B, H, W, 2)).astype(np.float32) * 2.0
+    t = (x * 0.5 + rng.standard_normal((B, H, W, 2)) * 0.3).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return x, t, dev(x[..., 0]), dev(x[..., 1]), dev(t[..., 0]), dev(t[..., 1])
+
+
+def test_forward_matches_oracle(net):
+    torch, ur, dn, lay = net
+    x, t, rf, q, trf, tq = inputs(torch, 0)
+    orf, oq = dn.forward(rf, q)
+    torch.cuda.synchronize()
+    P = to_oracle(dn.params(), lay)
+    y, _ = D.forward(P, x.astype(np.float64) / 2.0, q=D.bf16)
+    gpu = np.stack([orf.cpu().numpy(), oq.cpu().numpy()], -1) / 2.0
+    xb = D.bf16(x.astype(np.float64) / 2.0)
+    e_all, e_res = rel_l2(gpu, y), rel_l2(gpu - xb, y - xb)
+    print(f"forward rel_l2: output {e_all:.2e}, learned part {e_res:.2e}")
+    assert e_all <= 5e-3
+    assert e_res <= 2e-2          # the learned part alone
+
+
+def test_gradient_matches_oracle(net):
+    torch, ur, dn, lay = net
+    x, t, rf, q, trf, tq = inputs(torch, 1)
+    loss, g = dn.train_step(rf, q, trf, tq, 0.0, grad=True)
+    g = g.cpu().numpy()
+    P = to_oracle(dn.params(), lay)
+    y, cache = D.forward(P, x.astype(np.float64) / 2.0, q=D.bf16)
+    ol, og = D.mse(y, t.astype(np.float64) / 2.0)
+    assert loss == pytest.approx(ol, rel=1e-2)
+    G = D.backward(P, cache, og)
+    worst = 0.0
+    for name, (wo, ws, bo, co) in lay.items():
+        gw = g[wo:wo + int(np.prod(ws))].reshape(ws)
+        if name == "e1a":
+            assert np.all(gw[:, :, 2:] == 0.0)      # padded input channels stay untouched
+            gw = gw[:, :, :2]
+        gb = g[bo:bo + co]
+        for kind, a, b in (("w", gw, G[name + ".w"]), ("b", gb, G[name + ".b"])):
+            e = rel_l2(a.astype(np.float64), b)
+            worst = max(worst, e)
+            print(f"{name}.{kind}: rel_l2 {e:.2e}")
+            assert e <= (5e-2 if kind == "w" else 1e-1), (name, kind, e)
+    assert worst > 0.0
+
+
+def test_adam_update_matches_oracle(net):
+    torch, ur, dn, lay = net
+    x, t, rf, q, trf, tq = inputs(torch, 5)
+    p0 = dn.params()
+    lr = 1e-3
+    _, g = dn.train_step(rf, q, trf, tq, lr, grad=True)
+    p1 = dn.params()
+    P = {"all": p0.astype(np.float64)}
+    D.adam_step(P, {"all": g.cpu().numpy().astype(np.float64)}, {}, lr)
+    assert np.max(np.abs(p1 - P["all"])) <= 1e-3 * lr + 1e-7
+    dn.set_params(p0)
+
+
+def test_training_lowers_the_loss(net):
+    torch, ur, dn, lay = net
+    x, t, rf, q, trf, tq = inputs(torch, 2)
+    p0 = dn.params()
+    first = dn.train_step(rf, q, trf, tq, 2e-3)
+    for _ in range(60):
+        last = dn.train_step(rf, q, trf, tq, 2e-3)
+    assert last < 0.2 * first
+    dn.set_params(p0)
