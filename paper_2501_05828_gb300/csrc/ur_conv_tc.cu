@@ -1,0 +1,423 @@
+// 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores.
+//
+// One CTA computes a tile of 128 consecutive pixels of one image row (the M
+// dimension, one TMEM lane per pixel) by BN output channels (N).  The K loop
+// walks the 9 taps and, within each, the input channels in chunks of BK (64:
+// 128-byte rows, or 32: 64-byte rows).  For every K step one thread issues two
+// TMA loads into a ring of shared-memory stages:
+//   A: the 128 x BK box of the NHWC input at (x0 + kx - 1, y + ky - 1), so the
+//      zero padding of the convolution is TMA's out-of-bounds fill,
+//   B: the BN x BK box of the weights [9][Cout][Cin] at this tap,
+// both written in the canonical K-major swizzled layout the tensor core reads.
+// A second thread issues tcgen05.mma (M = 128, N = BN, K = 16, BF16 inputs,
+// FP32 accumulator in TMEM) and releases each stage with tcgen05.commit.  The
+// four warps then read the accumulator with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31) and apply bias, ReLU and an optional ReLU mask (for data
+// gradients) before storing BF16.
+//
+// Every mbarrier wait is bounded by the global timer; a wait that gives up
+// records an error code for the host and the block still frees its TMEM.
+#include "ur_conv_tc.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <mutex>
+
+namespace urnn {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kBM = 128;         // pixels per tile = TMEM lanes
+constexpr int kThreads = 128;    // 4 warps: TMA producer (warp 0), MMA issuer (warp 1), all four in the epilogue
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far above any tile's run time
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity to complete; false once the deadline passed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline) {
+    while (!mbar_test(bar, parity))
+        if (now_ns() > deadline) return false;
+    return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 with BF16 operands and FP32 accumulation.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives on the mbarrier once every MMA this thread issued so far has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory descriptor of a K-major operand in the canonical swizzled layout:
+// rows of `row_bytes` (128: 128-byte swizzle, 64: 64-byte swizzle), 8-row groups
+// 8 * row_bytes apart (stride byte offset); the leading byte offset is unused for
+// swizzled K-major operands; descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t row_bytes) {
+    const uint64_t layout = row_bytes == 128 ? 2ull : 4ull;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)((8u * row_bytes) >> 4) << 32) | (1ull << 46) |
+           (layout << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <int BN, int BK>
+struct Cfg {
+    static constexpr int ROW = BK * 2;                    // bytes per operand row
+    static constexpr int A_BYTES = kBM * ROW;
+    static constexpr int B_BYTES = BN * ROW;
+    static constexpr int A_PAD = (A_BYTES + 1023) / 1024 * 1024;
+    static constexpr int B_PAD = (B_BYTES + 1023) / 1024 * 1024;
+    static constexpr int BUDGET = BN >= 192 ? 200 * 1024 : 100 * 1024;   // two CTAs per SM below 192 columns
+    static constexpr int S_RAW = BUDGET / (A_PAD + B_PAD);
+    static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 6 ? 6 : S_RAW);
+    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr int SMEM = S * (A_PAD + B_PAD) + 1024 + 8 * (2 * S + 1) + 16;
+};
+
+struct Args {
+    int N, H, W, C, Cout, nxb, relu, taps;
+    const float *bias;
+    const bf16 *mask;
+    bf16 *y;
+    int *err;
+};
+
+template <int BN, int BK>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, const Args a) {
+    using K = Cfg<BN, BK>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = s_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;          // swizzled operands want 1024-byte alignment
+    uint8_t *sm = smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + K::S * K::A_PAD;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + K::S * (K::A_PAD + K::B_PAD));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * K::S + 1);
+    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S), accb = s_addr(bars + 2 * K::S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    int t = blockIdx.x;
+    const int xb = t % a.nxb;
+    t /= a.nxb;
+    const int y = t % a.H, n = t / a.H;
+    const int x0 = xb * kBM, co0 = blockIdx.y * BN;
+    const int kc = a.C / BK, nk = a.taps * kc;
+    const uint64_t deadline = now_ns() + kWaitNs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < K::S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(s_addr(tslot), K::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            int issued = 0;
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % K::S;
+                const uint32_t ph = (uint32_t)(kt / K::S) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, deadline)) {
+                    ok = false;
+                    break;
+                }
+                const int tap = kt / kc, c0 = (kt - tap * kc) * BK;
+                const int ky = a.taps == 1 ? 1 : tap / 3, kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
+                mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + K::B_BYTES));
+                tma_load_4d(sA + s * K::A_PAD, &tmx, c0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * s);
+                tma_load_3d(sB + s * K::B_PAD, &tmw, c0, co0, tap, full0 + 8 * s);
+                issued = kt + 1;
+            }
+            if (!ok)   // let the copies already in flight land before the block can exit
+                for (int kt = issued > K::S ? issued - K::S : 0; kt < issued; ++kt)
+                    mbar_wait(full0 + 8 * (kt % K::S), (uint32_t)(kt / K::S) & 1u, deadline + kWaitNs / 20);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16<BN>();
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % K::S;
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)(kt / K::S) & 1u, deadline)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = sA + s * K::A_PAD, b0 = sB + s * K::B_PAD;
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    mma_bf16(tmem, sdesc(a0 + 32 * k, K::ROW), sdesc(b0 + 32 * k, K::ROW), idesc, (kt | k) != 0);
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accb);
+        }
+        __syncwarp();
+    }
+
+    // epilogue: TMEM -> registers -> bias / ReLU / mask -> BF16 NHWC
+    const bool acc_ready = mbar_wait(accb, 0, deadline + kWaitNs / 10);
+    const bool warp_ready = __all_sync(0xffffffffu, acc_ready) != 0;
+    if (!acc_ready) ok = false;
+    tc_fence_after();
+    if (warp_ready) {
+        const int x = x0 + warp * 32 + lane;
+        const size_t pix = ((size_t)n * a.H + y) * a.W + x;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            if (x < a.W) {
+                const int co = co0 + c;
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                if (a.bias) {
+                    const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + co);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 b = b4[j];
+                        v[4 * j] += b.x;
+                        v[4 * j + 1] += b.y;
+                        v[4 * j + 2] += b.z;
+                        v[4 * j + 3] += b.w;
+                    }
+                }
+                if (a.relu) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
+                }
+                if (a.mask) {
+                    const uint4 *m4 = reinterpret_cast<const uint4 *>(a.mask + pix * a.Cout + co);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 mv = m4[q];
+                        const __nv_bfloat162 *mb = reinterpret_cast<const __nv_bfloat162 *>(&mv);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float2 f = __bfloat1622float2(mb[h]);
+                            if (!(f.x > 0.f)) v[8 * q + 2 * h] = 0.f;
+                            if (!(f.y > 0.f)) v[8 * q + 2 * h + 1] = 0.f;
+                        }
+                    }
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + co);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 o;
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * q], v[8 * q + 1]);
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
+                    __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+                    o.x = *reinterpret_cast<uint32_t *>(&h0);
+                    o.y = *reinterpret_cast<uint32_t *>(&h1);
+                    o.z = *reinterpret_cast<uint32_t *>(&h2);
+                    o.w = *reinterpret_cast<uint32_t *>(&h3);
+                    dst[q] = o;
+                }
+            }
+        }
+    }
+    if (!ok) atomicExch(a.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_free(tmem, K::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+template <int BN, int BK>
+cudaError_t launch(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_mtiles, cudaStream_t stream) {
+    using K = Cfg<BN, BK>;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e != cudaSuccess) return e;
+    k_conv_tc<BN, BK><<<dim3((unsigned)n_mtiles, (unsigned)(a.Cout / BN)), kThreads, K::SMEM, stream>>>(mx, mw, a);
+    return cudaGetLastError();
+}
+
+template <int BK>
+cudaError_t launch_bn(int BN, const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_mtiles,
+                      cudaStream_t stream) {
+    switch (BN) {
+        case 32: return launch<32, BK>(mx, mw, a, n_mtiles, stream);
+        case 64: return launch<64, BK>(mx, mw, a, n_mtiles, stream);
+        case 96: return launch<96, BK>(mx, mw, a, n_mtiles, stream);
+        case 128: return launch<128, BK>(mx, mw, a, n_mtiles, stream);
+        case 192: return launch<192, BK>(mx, mw, a, n_mtiles, stream);
+        default: return launch<256, BK>(mx, mw, a, n_mtiles, stream);
+    }
+}
+
+int pick_bn(int cout) {
+    if (cout <= 256) return (cout == 32 || cout == 64 || cout == 96 || cout == 128 || cout == 192 || cout == 256) ? cout : 0;
+    for (int bn : {256, 192, 128, 64, 32})
+        if (cout % bn == 0) return bn;
+    return 0;
+}
+
+}  // namespace
+
+cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, cudaStream_t stream, std::string *why) {
+    const int BK = p.C % 64 == 0 ? 64 : 32;
+    const int BN = pick_bn(p.Cout);
+    if (p.C < 32 || p.C % 32 || BN == 0 || (p.taps != 9 && p.taps != 1) || p.N < 1 || p.H < 1 || p.W < 1 || !p.x || !p.w || !p.y || !d_err ||
+        (reinterpret_cast<uintptr_t>(p.x) & 15) || (reinterpret_cast<uintptr_t>(p.w) & 15) ||
+        (reinterpret_cast<uintptr_t>(p.y) & 15) || (p.bias && (reinterpret_cast<uintptr_t>(p.bias) & 15)) ||
+        (p.mask && (reinterpret_cast<uintptr_t>(p.mask) & 15))) {
+        if (why) *why = "conv3x3_tc: unsupported shape or alignment";
+        return cudaErrorInvalidValue;
+    }
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) {
+        if (why) *why = "cuTensorMapEncodeTiled is not available from the driver";
+        return cudaErrorNotSupported;
+    }
+    const CUtensorMapSwizzle sw = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    alignas(64) CUtensorMap mx, mw;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)p.C, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.N};
+        const cuuint64_t strides[3] = {(cuuint64_t)p.C * 2, (cuuint64_t)p.W * p.C * 2, (cuuint64_t)p.H * p.W * p.C * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)kBM, 1, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        const CUresult r = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(p.x), dims, strides, box, es,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            if (why) *why = "tensor map of the convolution input rejected (" + std::to_string((int)r) + ")";
+            return cudaErrorInvalidValue;
+        }
+    }
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)p.C, (cuuint64_t)p.Cout, (cuuint64_t)p.taps};
+        const cuuint64_t strides[2] = {(cuuint64_t)p.C * 2, (cuuint64_t)p.Cout * p.C * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BN, 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        const CUresult r = enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(p.w), dims, strides, box, es,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            if (why) *why = "tensor map of the weights rejected (" + std::to_string((int)r) + ")";
+            return cudaErrorInvalidValue;
+        }
+    }
+    Args a{p.N, p.H, p.W, p.C, p.Cout, (p.W + kBM - 1) / kBM, p.relu, p.taps, p.bias, p.mask, p.y, d_err};
+    const long long n_mtiles = (long long)p.N * p.H * a.nxb;
+    if (n_mtiles > 0x7fffffffll) {
+        if (why) *why = "conv3x3_tc: too many tiles";
+        return cudaErrorInvalidValue;
+    }
+    return BK == 64 ? launch_bn<64>(BN, mx, mw, a, (int)n_mtiles, stream)
+                    : launch_bn<32>(BN, mx, mw, a, (int)n_mtiles, stream);
+}
+
+}  // namespace urnn

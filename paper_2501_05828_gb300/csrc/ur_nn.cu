@@ -1,12 +1,14 @@
 // Channel-data denoiser: a 4-level 2D U-Net over the analytic channel data of
 // one transmit (an n_el x n_s image with 2 channels, rf and quad), trained to
 // map low-ray-count channel data to high-ray-count channel data.  BF16 weights
-// and activations (NHWC), FP32 accumulation on the tensor cores (mma.sync
-// m16n8k16 fed by ldmatrix from cp.async-filled shared memory), FP32 master
-// weights with Adam.  Decoder convolutions gather their input on the fly from
-// the half-resolution tensor (nearest-neighbour upsampling) and the skip
-// tensor (concatenation), so neither is materialised.
+// and activations (NHWC), FP32 accumulation, FP32 master weights with Adam.
+// Forward and data-gradient convolutions run on the 5th-generation tensor
+// cores (TMA-fed tcgen05.mma with TMEM accumulators, ur_conv_tc.cu); weight
+// gradients use split-K mma.sync tiles fed by cp.async.  Decoder inputs
+// (nearest-neighbour upsampling of the lower level concatenated with the skip
+// tensor) are gathered into one NHWC buffer before their convolution.
 #include "ultraray.h"
+#include "ur_conv_tc.cuh"
 #include "ur_device.cuh"
 
 #include <cuda_bf16.h>
@@ -32,11 +34,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -67,121 +64,13 @@ __device__ __forceinline__ const bf16 *gather(const ConvIn &in, int n, int H, in
     return in.x2 + (((size_t)n * H + yy) * W + xx) * in.c2 + (c - in.c1);
 }
 
-struct ConvP {
-    ConvIn in;
-    int N, H, W, Cin, Cout;
-    const bf16 *w;        // [9][Cout][Cin]
-    const float *bias;    // [Cout], nullable
-    bf16 *y;              // [N][H][W][Cout]
-    float *y32;           // nullable fp32 copy (tests)
-    int relu;
-};
-
-// Implicit-GEMM 3x3 convolution (zero padding): rows = pixels of one image row,
-// columns = output channels, K = 9 taps x input channels.  WM x WN warps, each
-// a 32 x 32 tile (2 m16 x 4 n8 MMA tiles); K advances 32 channels per stage
-// with two shared-memory stages filled by cp.async.
-template <int WM, int WN>
-__global__ void __launch_bounds__(128) k_conv3x3(const ConvP P) {
-    constexpr int BM = 32 * WM, BN = 32 * WN, BK = 32, LDS = 40;
-    __shared__ __align__(16) bf16 sA[2][BM * LDS];
-    __shared__ __align__(16) bf16 sB[2][BN * LDS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp % WM, wn = warp / WM;
-    const int nxb = (P.W + BM - 1) / BM;
-    int b = blockIdx.x;
-    const int xb = b % nxb;
-    b /= nxb;
-    const int y = b % P.H, n = b / P.H;
-    const int x0 = xb * BM, co0 = blockIdx.y * BN;
-    const int kc = P.Cin / BK, nk = 9 * kc;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-
-    auto load = [&](int kt, int buf) {
-        const int tap = kt / kc, ci0 = (kt % kc) * BK;
-        const int ky = tap / 3, kx = tap % 3, yy = y + ky - 1;
-        for (int idx = tid; idx < BM * 4; idx += 128) {
-            const int px = idx >> 2, part = idx & 3, xx = x0 + px + kx - 1;
-            const bool ok = yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
-            const bf16 *src = ok ? gather(P.in, n, P.H, P.W, yy, xx, ci0 + part * 8) : P.in.x1;
-            cp_async16(&sA[buf][px * LDS + part * 8], src, ok ? 16 : 0);
-        }
-        for (int idx = tid; idx < BN * 4; idx += 128) {
-            const int r = idx >> 2, part = idx & 3;
-            cp_async16(&sB[buf][r * LDS + part * 8], P.w + ((size_t)tap * P.Cout + co0 + r) * P.Cin + ci0 + part * 8, 16);
-        }
-        cp_async_commit();
-    };
-
-    load(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        if (kt + 1 < nk) {
-            load(kt + 1, (kt + 1) & 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const bf16 *A = sA[kt & 1];
-        const bf16 *B = sB[kt & 1];
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t a[2][4], bb[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-                ldsm_x4(a[mi], &A[(wm * 32 + mi * 16 + (lane & 15)) * LDS + ks + (lane >> 4) * 8]);
-#pragma unroll
-            for (int nj = 0; nj < 4; nj += 2) {
-                uint32_t r4[4];
-                ldsm_x4(r4, &B[(wn * 32 + nj * 8 + (lane & 7) + ((lane >> 4) << 3)) * LDS + ks + ((lane >> 3) & 1) * 8]);
-                bb[nj][0] = r4[0];
-                bb[nj][1] = r4[1];
-                bb[nj + 1][0] = r4[2];
-                bb[nj + 1][1] = r4[3];
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], a[mi], bb[nj][0], bb[nj][1]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int nj = 0; nj < 4; ++nj)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = x0 + wm * 32 + mi * 16 + (lane >> 2) + h * 8;
-                if (x >= P.W) continue;
-                const int co = co0 + wn * 32 + nj * 8 + (lane & 3) * 2;
-                float v0 = acc[mi][nj][2 * h], v1 = acc[mi][nj][2 * h + 1];
-                if (P.bias) {
-                    v0 += P.bias[co];
-                    v1 += P.bias[co + 1];
-                }
-                if (P.relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                const size_t o = (((size_t)n * P.H + y) * P.W + x) * P.Cout + co;
-                *reinterpret_cast<__nv_bfloat162 *>(P.y + o) = __floats2bfloat162_rn(v0, v1);
-                if (P.y32) *reinterpret_cast<float2 *>(P.y32 + o) = make_float2(v0, v1);
-            }
-}
-
 struct WgradP {
     ConvIn in;             // forward input
     const bf16 *dy;        // [N][H][W][Cout] gradient at the pre-activation
     int N, H, W, Cin, Cout;
-    float *dw;             // [9][Cout][Cin], accumulated
+    float *dw;             // [taps][Cout][Cin], accumulated
     int px_per_warp;       // pixels per warp (multiple of 32)
+    int taps;              // 9, or 1 for an input that already holds the neighbourhood (centre tap only)
 };
 
 // dw[tap][co][ci] += sum_p dy[p][co] x[p + offset(tap)][ci].  Each warp owns a
@@ -195,8 +84,8 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradP P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int co0 = blockIdx.y * 32;
     const int kci = P.Cin / 32;
-    const int tap = blockIdx.z / kci, ci0 = (blockIdx.z % kci) * 32;
-    const int ky = tap / 3, kx = tap % 3;
+    const int tap = P.taps == 1 ? 0 : blockIdx.z / kci, ci0 = (blockIdx.z % kci) * 32;
+    const int ky = P.taps == 1 ? 1 : tap / 3, kx = P.taps == 1 ? 1 : tap % 3;
     const long long P_tot = (long long)P.N * P.H * P.W;
     const long long p_begin = ((long long)blockIdx.x * 4 + warp) * P.px_per_warp;
     const long long p_end = min(P_tot, p_begin + P.px_per_warp);
@@ -281,94 +170,197 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradP P) {
 
 // ------------------------------------------------------------------ small kernels
 
-// rf, quad [B][H][W] (fp32, the tracer's layout) -> x bf16 NHWC with 32 channels
-// (rf, quad, zeros) and the normalised input fp32 NHWC [B][H][W][2].
-__global__ void k_prep(const float *rf, const float *quad, int B, int H, int W, float inv_scale, bf16 *x,
-                       float *xn) {
-    const long long n = (long long)B * H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const float a = rf[p] * inv_scale, q = quad[p] * inv_scale;
-        const bf16 ab = __float2bfloat16_rn(a), qb = __float2bfloat16_rn(q);
-        uint4 *dst = reinterpret_cast<uint4 *>(x + (size_t)p * 32);
-        __nv_bfloat162 head = __halves2bfloat162(ab, qb);
-        uint4 first = make_uint4(*reinterpret_cast<uint32_t *>(&head), 0u, 0u, 0u);
-        dst[0] = first;
-        dst[1] = make_uint4(0u, 0u, 0u, 0u);
-        dst[2] = make_uint4(0u, 0u, 0u, 0u);
-        dst[3] = make_uint4(0u, 0u, 0u, 0u);
-        xn[2 * p] = __bfloat162float(ab);
-        xn[2 * p + 1] = __bfloat162float(qb);
+__device__ __forceinline__ void unpack8(const uint4 &u, float (&f)[8]) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 t = __bfloat1622float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
     }
 }
 
-// 2x2 average pooling, NHWC bf16.
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 u;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    return u;
+}
+
+#define GRID_STRIDE(i, n) \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// rf, quad [B][H][W] (fp32, the tracer's layout) -> the normalised BF16-rounded
+// input xn [B][H][W][2] (fp32) and its 3x3 neighbourhood as 32 BF16 channels per
+// pixel (channel 2 t + c = input channel c at tap t = 3 ky + kx, zero outside the
+// image and from channel 18 on), so the first convolution is one K = 32 GEMM.
+__global__ void k_prep(const float *rf, const float *quad, int B, int H, int W, float inv_scale, bf16 *xcol,
+                       float *xn) {
+    GRID_STRIDE(p, (long long)B * H * W) {
+        const int x = (int)(p % W);
+        const long long r = p / W;
+        const int y = (int)(r % H), b = (int)(r / H);
+        float v[32];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            float a = 0.f, q = 0.f;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const size_t o = ((size_t)b * H + yy) * W + xx;
+                a = __bfloat162float(__float2bfloat16_rn(rf[o] * inv_scale));
+                q = __bfloat162float(__float2bfloat16_rn(quad[o] * inv_scale));
+            }
+            v[2 * t] = a;
+            v[2 * t + 1] = q;
+        }
+#pragma unroll
+        for (int k = 18; k < 32; ++k) v[k] = 0.f;
+        uint4 *dst = reinterpret_cast<uint4 *>(xcol + (size_t)p * 32);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) f[j] = v[8 * g + j];
+            dst[g] = pack8(f);
+        }
+        xn[2 * p] = v[8];
+        xn[2 * p + 1] = v[9];
+    }
+}
+
+// Single-tap weights of the first convolution: wp[co][2 t + c] = w[t][co][c].
+__global__ void k_pack_first(const bf16 *w, int C, bf16 *wp) {
+    GRID_STRIDE(i, (long long)C * 32) {
+        const int co = (int)(i / 32), k = (int)(i % 32);
+        wp[i] = k < 18 ? w[((size_t)(k / 2) * C + co) * 32 + (k % 2)] : __float2bfloat16_rn(0.f);
+    }
+}
+
+// dw[t][co][c] += dwp[co][2 t + c]: gradient of the single-tap form back to [9][C][32].
+__global__ void k_unpack_first_grad(const float *dwp, int C, float *dw) {
+    GRID_STRIDE(i, (long long)C * 18) {
+        const int co = (int)(i / 18), k = (int)(i % 18);
+        dw[((size_t)(k / 2) * C + co) * 32 + (k % 2)] += dwp[(size_t)co * 32 + k];
+    }
+}
+
+// Decoder input: cat[b, y, x, 0:c1] = low[b, y/2, x/2, :] (nearest-neighbour
+// upsampling), cat[b, y, x, c1:c1+c2] = skip[b, y, x, :]; 16-byte granules.
+__global__ void k_upcat(const bf16 *low, int c1, const bf16 *skip, int c2, int B, int H, int W, bf16 *cat) {
+    const int g1 = c1 / 8, G = (c1 + c2) / 8;
+    GRID_STRIDE(i, (long long)B * H * W * G) {
+        const int g = (int)(i % G);
+        const long long p = i / G;
+        const int x = (int)(p % W);
+        const long long r = p / W;
+        const int y = (int)(r % H), b = (int)(r / H);
+        const bf16 *src = g < g1 ? low + (((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * c1 + g * 8
+                                 : skip + (size_t)p * c2 + (g - g1) * 8;
+        reinterpret_cast<uint4 *>(cat)[i] = *reinterpret_cast<const uint4 *>(src);
+    }
+}
+
+// 2x2 average pooling, NHWC bf16, 8 channels per thread.
 __global__ void k_pool2(const bf16 *x, bf16 *y, int B, int H, int W, int C) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long n = (long long)B * Ho * Wo * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long r = i / C;
+    const int Ho = H / 2, Wo = W / 2, G = C / 8;
+    const uint4 *xg = reinterpret_cast<const uint4 *>(x);
+    GRID_STRIDE(i, (long long)B * Ho * Wo * G) {
+        const int g = (int)(i % G);
+        long long r = i / G;
         const int xo = (int)(r % Wo);
         r /= Wo;
         const int yo = (int)(r % Ho), b = (int)(r / Ho);
-        const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * C + c;
-        const float s = __bfloat162float(x[base]) + __bfloat162float(x[base + C]) +
-                        __bfloat162float(x[base + (size_t)W * C]) + __bfloat162float(x[base + (size_t)W * C + C]);
-        y[i] = __float2bfloat16_rn(0.25f * s);
+        const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * G + g;
+        float s[8], t[8];
+        unpack8(xg[base], s);
+        unpack8(xg[base + G], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] += t[j];
+        unpack8(xg[base + (size_t)W * G], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] += t[j];
+        unpack8(xg[base + (size_t)W * G + G], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = 0.25f * (s[j] + t[j]);
+        reinterpret_cast<uint4 *>(y)[i] = pack8(s);
     }
 }
 
-// d[i] = d[i] * (act[i] > 0)
-__global__ void k_relu_mask(bf16 *d, const bf16 *act, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        if (!(__bfloat162float(act[i]) > 0.f)) d[i] = __float2bfloat16_rn(0.f);
+// d[i] = d[i] * (act[i] > 0), 8 channels per thread (n8 granules).
+__global__ void k_relu_mask(bf16 *d, const bf16 *act, long long n8) {
+    uint4 *dg = reinterpret_cast<uint4 *>(d);
+    const uint4 *ag = reinterpret_cast<const uint4 *>(act);
+    GRID_STRIDE(i, n8) {
+        float a[8], v[8];
+        unpack8(ag[i], a);
+        unpack8(dg[i], v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (!(a[j] > 0.f)) v[j] = 0.f;
+        dg[i] = pack8(v);
+    }
 }
 
 // Split the gradient of a concatenated decoder input [B][H][W][C1 + C2]: the
 // first C1 channels came from the nearest-upsampled half-resolution tensor (sum
 // over each 2x2 block), the rest from the skip tensor (copied).
 __global__ void k_unconcat(const bf16 *dcat, int B, int H, int W, int C1, int C2, bf16 *dlow, bf16 *dskip) {
-    const int Ho = H / 2, Wo = W / 2, C = C1 + C2;
-    const long long nlow = (long long)B * Ho * Wo * C1, nskip = (long long)B * H * W * C2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlow + nskip;
-         i += (long long)gridDim.x * blockDim.x) {
+    const int Ho = H / 2, Wo = W / 2, G1 = C1 / 8, G2 = C2 / 8, G = G1 + G2;
+    const long long nlow = (long long)B * Ho * Wo * G1, nskip = (long long)B * H * W * G2;
+    const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
+    GRID_STRIDE(i, nlow + nskip) {
         if (i < nlow) {
-            const int c = (int)(i % C1);
-            long long r = i / C1;
+            const int g = (int)(i % G1);
+            long long r = i / G1;
             const int xo = (int)(r % Wo);
             r /= Wo;
             const int yo = (int)(r % Ho), b = (int)(r / Ho);
-            const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * C + c;
-            const float s = __bfloat162float(dcat[base]) + __bfloat162float(dcat[base + C]) +
-                            __bfloat162float(dcat[base + (size_t)W * C]) + __bfloat162float(dcat[base + (size_t)W * C + C]);
-            dlow[i] = __float2bfloat16_rn(s);
+            const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * G + g;
+            float s[8], t[8];
+            unpack8(dg[base], s);
+            unpack8(dg[base + G], t);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += t[j];
+            unpack8(dg[base + (size_t)W * G], t);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += t[j];
+            unpack8(dg[base + (size_t)W * G + G], t);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += t[j];
+            reinterpret_cast<uint4 *>(dlow)[i] = pack8(s);
         } else {
             const long long j = i - nlow;
-            const int c = (int)(j % C2);
-            const long long p = j / C2;
-            dskip[j] = dcat[(size_t)p * C + C1 + c];
+            const int g = (int)(j % G2);
+            const long long p = j / G2;
+            reinterpret_cast<uint4 *>(dskip)[j] = dg[(size_t)p * G + G1 + g];
         }
     }
 }
 
-// d[b, y, x, c] += dp[b, y/2, x/2, c] / 4 (gradient of 2x2 average pooling)
+// d[b, y, x, c] += dp[b, y/2, x/2, c] / 4 (gradient of 2x2 average pooling), 8 channels per thread.
 __global__ void k_pool2_bwd_add(bf16 *d, const bf16 *dp, int B, int H, int W, int C) {
-    const long long n = (long long)B * H * W * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        long long r = i / C;
+    const int G = C / 8;
+    uint4 *dg = reinterpret_cast<uint4 *>(d);
+    const uint4 *pg = reinterpret_cast<const uint4 *>(dp);
+    GRID_STRIDE(i, (long long)B * H * W * G) {
+        const int g = (int)(i % G);
+        long long r = i / G;
         const int x = (int)(r % W);
         r /= W;
         const int y = (int)(r % H), b = (int)(r / H);
-        const float add = 0.25f * __bfloat162float(dp[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c]);
-        d[i] = __float2bfloat16_rn(__bfloat162float(d[i]) + add);
+        float v[8], a[8];
+        unpack8(dg[i], v);
+        unpack8(pg[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * G + g], a);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += 0.25f * a[j];
+        dg[i] = pack8(v);
     }
 }
 
 // W'[tap][ci][co] = W[8 - tap][co][ci]: weights of the data gradient.
 __global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
-    const long long n = 9ll * Cout * Cin;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    GRID_STRIDE(i, 9ll * Cout * Cin) {
         const int co = (int)(i % Cout);
         long long r = i / Cout;
         const int ci = (int)(r % Cin);
@@ -377,20 +369,30 @@ __global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
     }
 }
 
-// db[c] += sum over pixels of d[p][c]; thread t owns channel t % C (C divides the
-// block, which has max(256, C) <= 1024 threads).
-__global__ void __launch_bounds__(1024) k_bias_grad(const bf16 *d, long long P, int C, float *db) {
-    __shared__ float s[1024];
-    const int c = threadIdx.x % C, lanes = blockDim.x / C, pl = threadIdx.x / C;
-    float acc = 0.f;
-    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes)
-        acc += __bfloat162float(d[(size_t)p * C + c]);
-    s[threadIdx.x] = acc;
+// db[c] += sum over pixels of d[p][c].  Thread t owns channels 8 (t % G) .. +8
+// (G = C / 8 divides the 256-thread block) for every (256 / G)-th pixel.
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16 *d, long long P, int C, float *db) {
+    __shared__ float s[256][9];
+    const int G = C / 8, g = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint4 *dg = reinterpret_cast<const uint4 *>(d);
+    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
+        float v[8];
+        unpack8(dg[(size_t)p * G + g], v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[threadIdx.x][j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < C) {
-        float t = 0.f;
-        for (int q = 0; q < lanes; ++q) t += s[q * C + threadIdx.x];
-        if (t != 0.f) atomicAdd(&db[threadIdx.x], t);
+    if (threadIdx.x < G) {
+        float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < lanes; ++q)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) t[j] += s[q * G + threadIdx.x][j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (t[j] != 0.f) atomicAdd(&db[8 * threadIdx.x + j], t[j]);
     }
 }
 
@@ -398,13 +400,18 @@ __global__ void __launch_bounds__(1024) k_bias_grad(const bf16 *d, long long P, 
 // back in the tracer's layout, rescaled.
 __global__ void k_head_fwd(const bf16 *d1, const float *xn, const float *wh, const float *bh, int C, long long P,
                            float scale, float *yn, float *out_rf, float *out_quad) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const int G = C / 8;
+    const uint4 *fg = reinterpret_cast<const uint4 *>(d1);
+    GRID_STRIDE(p, P) {
         float s0 = bh[0] + xn[2 * p], s1 = bh[1] + xn[2 * p + 1];
-        const bf16 *f = d1 + (size_t)p * C;
-        for (int c = 0; c < C; ++c) {
-            const float v = __bfloat162float(f[c]);
-            s0 += wh[c] * v;
-            s1 += wh[C + c] * v;
+        for (int g = 0; g < G; ++g) {
+            float v[8];
+            unpack8(fg[(size_t)p * G + g], v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                s0 += wh[8 * g + j] * v[j];
+                s1 += wh[C + 8 * g + j] * v[j];
+            }
         }
         yn[2 * p] = s0;
         yn[2 * p + 1] = s1;
@@ -530,7 +537,11 @@ struct ur_nn {
     Tensor pool[3];          // pooled e1, e2, e3
     Tensor gbuf[4];          // gradient scratch per level (two of the largest sizes)
     bf16 *gcat = nullptr, *gA = nullptr, *gB = nullptr, *gSkip[3] = {nullptr, nullptr, nullptr}, *gLow = nullptr;
+    bf16 *cat = nullptr;     // decoder input (upsampled lower level ++ skip)
+    bf16 *wfirst = nullptr;  // first convolution as one tap over the 32 neighbourhood channels [C][32]
+    float *dwfirst = nullptr;
     double *loss = nullptr;
+    int *d_err = nullptr, *h_err = nullptr;   // bounded-wait failures inside the convolution kernels
     std::vector<void *> allocs;
 
     void *alloc(size_t bytes) {
@@ -562,32 +573,47 @@ ur_status nn_guard(ur_nn *nn, F &&f) {
     }
 }
 
-void conv_fwd(ur_nn *nn, const ConvIn &in, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
-              bf16 *y, float *y32, bool relu) {
-    ConvP P{in, B, H, W, Cin, Cout, w, bias, y, y32, relu ? 1 : 0};
-    if (Cout % 64 == 0) {
-        dim3 grid(B * H * ((W + 63) / 64), Cout / 64);
-        k_conv3x3<2, 2><<<grid, 128, 0, nn->stream>>>(P);
-    } else {
-        dim3 grid(B * H * ((W + 127) / 128), Cout / 32);
-        k_conv3x3<4, 1><<<grid, 128, 0, nn->stream>>>(P);
+void conv_fwd(ur_nn *nn, const bf16 *x, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
+              const bf16 *mask, bf16 *y, bool relu, int taps = 9) {
+    urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0};
+    std::string why;
+    const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->stream, &why);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(e == cudaErrorInvalidValue ? UR_ERR_INVALID_ARG : UR_ERR_CUDA,
+             why.empty() ? std::string("conv kernel: ") + cudaGetErrorString(e) : why);
     }
-    ck(cudaGetLastError(), "conv kernel");
 }
 
-void conv_wgrad(ur_nn *nn, const ConvIn &in, const bf16 *dy, int B, int H, int W, int Cin, int Cout, float *dw) {
+// Synchronises the network's stream and reports a convolution that gave up waiting.
+void sync_check(ur_nn *nn, const char *what) {
+    ck(cudaMemcpyAsync(nn->h_err, nn->d_err, sizeof(int), cudaMemcpyDeviceToHost, nn->stream), "read status");
+    ck(cudaStreamSynchronize(nn->stream), what);
+    if (*nn->h_err) {
+        *nn->h_err = 0;
+        ck(cudaMemsetAsync(nn->d_err, 0, sizeof(int), nn->stream), "reset status");
+        fail(UR_ERR_TIMEOUT, std::string(what) + ": a convolution pipeline wait timed out");
+    }
+}
+
+// Split K over pixels: about 16k warps in total, so each output element takes a
+// bounded number of atomic additions whatever the layer's size.
+void conv_wgrad(ur_nn *nn, const ConvIn &in, const bf16 *dy, int B, int H, int W, int Cin, int Cout, float *dw,
+                int taps = 9) {
     const long long P_tot = (long long)B * H * W;
-    const int px_per_warp = (int)std::max<long long>(128, std::min<long long>(4096, (P_tot / 2048 + 31) / 32 * 32));
+    const long long tiles = (long long)(Cout / 32) * taps * (Cin / 32);
+    const long long slices = std::max<long long>(1, 16384 / tiles);
+    const int px_per_warp = (int)std::max<long long>(128, ((P_tot + slices - 1) / slices + 31) / 32 * 32);
     const long long warps = (P_tot + px_per_warp - 1) / px_per_warp;
-    WgradP W_{in, dy, B, H, W, Cin, Cout, dw, px_per_warp};
-    dim3 grid((unsigned)((warps + 3) / 4), Cout / 32, 9 * (Cin / 32));
+    WgradP W_{in, dy, B, H, W, Cin, Cout, dw, px_per_warp, taps};
+    dim3 grid((unsigned)((warps + 3) / 4), Cout / 32, taps * (Cin / 32));
     k_conv3x3_wgrad<<<grid, 128, 0, nn->stream>>>(W_);
     ck(cudaGetLastError(), "wgrad kernel");
 }
 
 void bias_grad(ur_nn *nn, const bf16 *d, long long P, int C, float *db) {
-    const int block = std::max(256, C);
-    k_bias_grad<<<(int)std::min<long long>(1024, (P * C + block - 1) / block), block, 0, nn->stream>>>(d, P, C, db);
+    const int lanes = 256 / (C / 8);
+    k_bias_grad<<<(int)std::min<long long>(1024, (P + lanes - 1) / lanes), 256, 0, nn->stream>>>(d, P, C, db);
     ck(cudaGetLastError(), "bias gradient kernel");
 }
 
@@ -622,10 +648,23 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
     const long long P = (long long)B * nn->H * nn->W;
     k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, 1.f / nn->scale, nn->x, nn->xn);
     ck(cudaGetLastError(), "prep kernel");
+    k_pack_first<<<grid_for(32ll * nn->width), 256, 0, nn->stream>>>(nn->pbf + nn->woff[0], nn->width, nn->wfirst);
+    ck(cudaGetLastError(), "pack kernel");
     for (int l = 0; l < kNumConv; ++l) {
         const Layer L = layer_in(nn, l);
-        conv_fwd(nn, L.in, B, L.H, L.W, nn->cin[l], nn->cout[l], nn->pbf + nn->woff[l], nn->params + nn->boff[l],
-                 nn->act[l].p, nullptr, true);
+        const bf16 *in = L.in.x1;
+        if (L.in.x2) {   // decoder: materialise upsample ++ skip
+            k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(
+                L.in.x1, L.in.c1, L.in.x2, L.in.c2, B, L.H, L.W, nn->cat);
+            ck(cudaGetLastError(), "upcat kernel");
+            in = nn->cat;
+        }
+        if (l == 0)   // neighbourhood already in the 32 input channels: one tap
+            conv_fwd(nn, in, B, L.H, L.W, 32, nn->cout[0], nn->wfirst, nn->params + nn->boff[0], nullptr, nn->act[0].p,
+                     true, 1);
+        else
+            conv_fwd(nn, in, B, L.H, L.W, nn->cin[l], nn->cout[l], nn->pbf + nn->woff[l], nn->params + nn->boff[l],
+                     nullptr, nn->act[l].p, true);
         if (l == 1 || l == 3 || l == 5) {   // pool after each encoder block
             const int q = l / 2;
             k_pool2<<<grid_for((long long)B * L.H * L.W * nn->cout[l] / 4), 256, 0, nn->stream>>>(
@@ -643,23 +682,27 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
 // leaves the gradient of la's input in `din` (full concatenated channels) if din.
 void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din) {
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
-    const long long nb = (long long)B * Lb.H * Lb.W * nn->cout[lb];
+    const long long nb = (long long)B * Lb.H * Lb.W * nn->cout[lb] / 8;
     k_relu_mask<<<grid_for(nb), 256, 0, nn->stream>>>(d_out, nn->act[lb].p, nb);
     conv_wgrad(nn, Lb.in, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
     bias_grad(nn, d_out, (long long)B * Lb.H * Lb.W, nn->cout[lb], nn->grads + nn->boff[lb]);
     k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
                                                                                   nn->cout[lb], nn->cin[lb]);
-    conv_fwd(nn, ConvIn{d_out, nn->cout[lb], 0, nullptr, 0}, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr,
-             scratch, nullptr, false);
-    const long long na = (long long)B * La.H * La.W * nn->cout[la];
-    k_relu_mask<<<grid_for(na), 256, 0, nn->stream>>>(scratch, nn->act[la].p, na);
-    conv_wgrad(nn, La.in, scratch, B, La.H, La.W, nn->cin[la], nn->cout[la], nn->grads + nn->woff[la]);
+    // gradient at la's output, masked by la's ReLU in the epilogue
+    conv_fwd(nn, d_out, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p, scratch, false);
+    if (la == 0) {   // first layer: single-tap gradient over the neighbourhood channels, then back to [9][C][32]
+        ck(cudaMemsetAsync(nn->dwfirst, 0, sizeof(float) * 32 * nn->width, nn->stream), "memset");
+        conv_wgrad(nn, La.in, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
+        k_unpack_first_grad<<<grid_for(18ll * nn->width), 256, 0, nn->stream>>>(nn->dwfirst, nn->width,
+                                                                               nn->grads + nn->woff[0]);
+    } else {
+        conv_wgrad(nn, La.in, scratch, B, La.H, La.W, nn->cin[la], nn->cout[la], nn->grads + nn->woff[la]);
+    }
     bias_grad(nn, scratch, (long long)B * La.H * La.W, nn->cout[la], nn->grads + nn->boff[la]);
     if (din) {
         k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
                                                                                       nn->cout[la], nn->cin[la]);
-        conv_fwd(nn, ConvIn{scratch, nn->cout[la], 0, nullptr, 0}, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt,
-                 nullptr, din, nullptr, false);
+        conv_fwd(nn, scratch, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din, false);
     }
     ck(cudaGetLastError(), "block backward");
 }
@@ -712,7 +755,7 @@ double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *
     ck(cudaGetLastError(), "backward");
     double loss = 0.0;
     ck(cudaMemcpyAsync(&loss, nn->loss, sizeof(double), cudaMemcpyDeviceToHost, nn->stream), "read loss");
-    ck(cudaStreamSynchronize(nn->stream), "train step");
+    sync_check(nn, "train step");
     return loss;
 }
 
@@ -822,11 +865,19 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         nn->gLow = (bf16 *)nn->alloc(sizeof(bf16) * big);
         for (int q = 0; q < 4; ++q) nn->gbuf[q] = Tensor{(bf16 *)nn->alloc(sizeof(bf16) * big), 0, 0, 0};
         for (int q = 0; q < 3; ++q) nn->gSkip[q] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> q) * (W >> q) * (C << q));
+        nn->cat = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 3 * C);   // largest decoder input (level 1, 3C)
+        nn->wfirst = (bf16 *)nn->alloc(sizeof(bf16) * 32 * C);
+        nn->dwfirst = (float *)nn->alloc(sizeof(float) * 32 * C);
         nn->loss = (double *)nn->alloc(sizeof(double));
+        nn->d_err = (int *)nn->alloc(sizeof(int));
+        ck(cudaMemset(nn->d_err, 0, sizeof(int)), "memset status");
+        ck(cudaMallocHost(&nn->h_err, sizeof(int)), "cudaMallocHost");
+        *nn->h_err = 0;
         ck(cudaStreamSynchronize(nn->stream), "init");
     });
     if (st != UR_OK) {
         for (void *p : nn->allocs) cudaFree(p);
+        if (nn->h_err) cudaFreeHost(nn->h_err);
         if (nn->own_stream) cudaStreamDestroy(nn->stream);
         delete nn;
         return st;
@@ -840,6 +891,7 @@ ur_status ur_nn_destroy(ur_nn *nn) {
     cudaSetDevice(nn->device);
     cudaStreamSynchronize(nn->stream);
     for (void *p : nn->allocs) cudaFree(p);
+    if (nn->h_err) cudaFreeHost(nn->h_err);
     if (nn->own_stream) cudaStreamDestroy(nn->stream);
     delete nn;
     return UR_OK;
@@ -883,6 +935,7 @@ ur_status ur_nn_forward(ur_nn *nn, const float *rf, const float *quad, int batch
         if (batch < 1 || batch > nn->max_batch) fail(UR_ERR_INVALID_ARG, "batch out of range");
         if (!rf || !quad || !out_rf || !out_quad) fail(UR_ERR_INVALID_ARG, "inputs and outputs are required");
         forward(nn, batch, rf, quad, out_rf, out_quad);
+        sync_check(nn, "forward");
     });
 }
 
