@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -320,6 +321,160 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ------------------------------------------------------------------ weight gradient
+//
+// dW[tap][co][ci] = sum_p dy[p][co] x[p + offset(tap)][ci] as D = A B^T with
+// M = (tap, ci) rows, N = co, K = pixels.  Both operands are read MN-major from
+// the NHWC tensors: a K step is 64 consecutive pixels of one image row; A is
+// made of four 32-row groups, each the TMA box of the tap-shifted input for 32
+// input channels (zero padding from the out-of-bounds fill), B of BN/32 boxes
+// of dy.  Boxes are 64 pixels x 32 channels with 64-byte swizzle: 32-element
+// MN chunks 4 KB apart (leading byte offset), 8-pixel K groups 512 B apart
+// (stride byte offset).  K is split across CTAs; partial tiles are added into
+// dW (FP32) with atomics, 32 consecutive ci per warp instruction.
+constexpr int kWK = 64;                 // pixels per K step
+constexpr int kChunk = 32 * kWK * 2;    // one 32-channel x 64-pixel box: 4 KB
+
+__device__ __forceinline__ uint64_t sdesc_mn64(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kChunk >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+           (1ull << 46) | (4ull << 61);
+}
+
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_bf16_mn() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <int BN>
+struct WCfg {
+    static constexpr int A_BYTES = 4 * kChunk;
+    static constexpr int B_BYTES = (BN / 32) * kChunk;
+    static constexpr int S_RAW = (BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
+    static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 6 ? 6 : S_RAW);
+    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr int SMEM = S * (A_BYTES + B_BYTES) + 1024 + 8 * (2 * S + 1) + 16;
+};
+
+struct WArgs {
+    int N, H, W, Cin, Cout, taps, nxb, steps, per_split;
+    float *dw;
+    int *err;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmd, const WArgs a) {
+    using K = WCfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = s_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sm = smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + K::S * K::A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + K::S * (K::A_BYTES + K::B_BYTES));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * K::S + 1);
+    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S), accb = s_addr(bars + 2 * K::S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int rows = a.taps * a.Cin;
+    const int r0 = blockIdx.x * kBM;
+    const int n_groups = min(4, (rows - r0) / 32);
+    const int co0 = blockIdx.y * BN;
+    const int s_begin = blockIdx.z * a.per_split;
+    const int s_end = min(a.steps, s_begin + a.per_split);
+    const int nk = s_end - s_begin;
+    const uint64_t deadline = now_ns() + kWaitNs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < K::S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(s_addr(tslot), K::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0 && nk > 0) {   // TMA producer
+            int issued = 0;
+            const uint32_t bytes = (uint32_t)(n_groups * kChunk + K::B_BYTES);
+            for (int kt = 0; kt < nk; ++kt) {
+                const int st = kt % K::S;
+                if (!mbar_wait(empty0 + 8 * st, ((uint32_t)(kt / K::S) & 1u) ^ 1u, deadline)) {
+                    ok = false;
+                    break;
+                }
+                int q = s_begin + kt;
+                const int xb = q % a.nxb;
+                q /= a.nxb;
+                const int y = q % a.H, n = q / a.H, x0 = xb * kWK;
+                mbar_expect_tx(full0 + 8 * st, bytes);
+                for (int g = 0; g < n_groups; ++g) {
+                    const int r = r0 + 32 * g, tap = r / a.Cin, ci0 = r - tap * a.Cin;
+                    const int ky = a.taps == 1 ? 1 : tap / 3, kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
+                    tma_load_4d(sA + st * K::A_BYTES + g * kChunk, &tmx, ci0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * st);
+                }
+                for (int c = 0; c < BN / 32; ++c)
+                    tma_load_4d(sB + st * K::B_BYTES + c * kChunk, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
+                issued = kt + 1;
+            }
+            if (!ok)
+                for (int kt = issued > K::S ? issued - K::S : 0; kt < issued; ++kt)
+                    mbar_wait(full0 + 8 * (kt % K::S), (uint32_t)(kt / K::S) & 1u, deadline + kWaitNs / 20);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && nk > 0) {   // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16_mn<BN>();
+            for (int kt = 0; kt < nk; ++kt) {
+                const int st = kt % K::S;
+                if (!mbar_wait(full0 + 8 * st, (uint32_t)(kt / K::S) & 1u, deadline)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = sA + st * K::A_BYTES, b0 = sB + st * K::B_BYTES;
+#pragma unroll
+                for (int k = 0; k < kWK / 16; ++k)   // 16 pixels = two 8-row K groups = 1 KB
+                    mma_bf16(tmem, sdesc_mn64(a0 + 1024 * k), sdesc_mn64(b0 + 1024 * k), idesc, (kt | k) != 0);
+                mma_commit(empty0 + 8 * st);
+            }
+            mma_commit(accb);
+        }
+        __syncwarp();
+    }
+
+    const bool acc_ready = nk > 0 && mbar_wait(accb, 0, deadline + kWaitNs / 10);
+    const bool warp_ready = __all_sync(0xffffffffu, acc_ready) != 0;
+    if (nk > 0 && !acc_ready) ok = false;
+    tc_fence_after();
+    if (warp_ready && warp < n_groups) {
+        const int r = r0 + 32 * warp, tap = r / a.Cin, ci = r - tap * a.Cin + lane;
+        float *dst = a.dw + (size_t)tap * a.Cout * a.Cin + ci;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) atomicAdd(dst + (size_t)(co0 + c + j) * a.Cin, __uint_as_float(v[j]));
+        }
+    }
+    if (!ok) atomicExch(a.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_free(tmem, K::TMEM_COLS);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -418,6 +573,72 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, cudaStream_t stream, std::st
     }
     return BK == 64 ? launch_bn<64>(BN, mx, mw, a, (int)n_mtiles, stream)
                     : launch_bn<32>(BN, mx, mw, a, (int)n_mtiles, stream);
+}
+
+namespace {
+
+template <int BN>
+cudaError_t launch_w(const CUtensorMap &mx, const CUtensorMap &md, const WArgs &a, dim3 grid, cudaStream_t stream) {
+    using K = WCfg<BN>;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e != cudaSuccess) return e;
+    k_wgrad_tc<BN><<<grid, kThreads, K::SMEM, stream>>>(mx, md, a);
+    return cudaGetLastError();
+}
+
+bool encode_nhwc(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *m, const bf16 *p, int C, int N, int H, int W,
+                 int box_c, int box_px, CUtensorMapSwizzle sw) {
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)box_px, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t stream, std::string *why) {
+    const int BN = p.Cout <= 256 ? p.Cout : 0;
+    if (p.Cin < 32 || p.Cin % 32 || (BN != 32 && BN != 64 && BN != 128 && BN != 256) || (p.taps != 9 && p.taps != 1) ||
+        p.N < 1 || p.H < 1 || p.W < 1 || !p.x || !p.dy || !p.dw || !d_err || (reinterpret_cast<uintptr_t>(p.x) & 15) ||
+        (reinterpret_cast<uintptr_t>(p.dy) & 15)) {
+        if (why) *why = "wgrad3x3_tc: unsupported shape or alignment";
+        return cudaErrorInvalidValue;
+    }
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) {
+        if (why) *why = "cuTensorMapEncodeTiled is not available from the driver";
+        return cudaErrorNotSupported;
+    }
+    alignas(64) CUtensorMap mx, md;
+    if (!encode_nhwc(enc, &mx, p.x, p.Cin, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B)) {
+        if (why) *why = "wgrad3x3_tc: tensor map rejected";
+        return cudaErrorInvalidValue;
+    }
+    const int nxb = (p.W + kWK - 1) / kWK;
+    const long long steps = (long long)p.N * p.H * nxb;
+    const int m_tiles = (p.taps * p.Cin + kBM - 1) / kBM;
+    if (steps > 0x7fffffffll) {
+        if (why) *why = "wgrad3x3_tc: too many pixels";
+        return cudaErrorInvalidValue;
+    }
+    // about eight waves of CTAs, at least 8 K steps each
+    const long long target = 8ll * (n_sm > 0 ? n_sm : 148);
+    long long splits = std::max<long long>(1, target / m_tiles);
+    splits = std::min<long long>(splits, std::max<long long>(1, steps / 8));
+    const int per = (int)((steps + splits - 1) / splits);
+    splits = (steps + per - 1) / per;
+    WArgs a{p.N, p.H, p.W, p.Cin, p.Cout, p.taps, nxb, (int)steps, per, p.dw, d_err};
+    const dim3 grid((unsigned)m_tiles, 1, (unsigned)splits);
+    switch (BN) {
+        case 32: return launch_w<32>(mx, md, a, grid, stream);
+        case 64: return launch_w<64>(mx, md, a, grid, stream);
+        case 128: return launch_w<128>(mx, md, a, grid, stream);
+        default: return launch_w<256>(mx, md, a, grid, stream);
+    }
 }
 
 }  // namespace urnn

@@ -27,4 +27,18 @@ struct ConvTC {
 // launch failures and fills `why` for rejected shapes.
 cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, cudaStream_t stream, std::string *why);
 
+// dw[tap][co][ci] += sum over pixels of dy[p][co] x[p + offset(tap)][ci]
+// (zero outside the image), FP32 accumulation on the tensor cores, atomically
+// added into dw (the caller zeroes it).  taps = 1 uses the centre tap only and
+// writes dw[0][co][ci].
+struct WgradTC {
+    const __nv_bfloat16 *x;      // forward input NHWC [N][H][W][Cin]
+    int Cin, N, H, W;
+    const __nv_bfloat16 *dy;     // gradient at the convolution's output NHWC [N][H][W][Cout], Cout in {32, 64, 128, 256}
+    int Cout, taps;
+    float *dw;                   // [taps][Cout][Cin]
+};
+
+cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t stream, std::string *why);
+
 }  // namespace urnn

@@ -2,11 +2,11 @@
 // one transmit (an n_el x n_s image with 2 channels, rf and quad), trained to
 // map low-ray-count channel data to high-ray-count channel data.  BF16 weights
 // and activations (NHWC), FP32 accumulation, FP32 master weights with Adam.
-// Forward and data-gradient convolutions run on the 5th-generation tensor
-// cores (TMA-fed tcgen05.mma with TMEM accumulators, ur_conv_tc.cu); weight
-// gradients use split-K mma.sync tiles fed by cp.async.  Decoder inputs
-// (nearest-neighbour upsampling of the lower level concatenated with the skip
-// tensor) are gathered into one NHWC buffer before their convolution.
+// Forward, data-gradient and weight-gradient convolutions run on the
+// 5th-generation tensor cores (TMA-fed tcgen05.mma with TMEM accumulators,
+// ur_conv_tc.cu).  Decoder inputs (nearest-neighbour upsampling of the lower
+// level concatenated with the skip tensor) are gathered into one NHWC buffer
+// before their convolution.
 #include "ultraray.h"
 #include "ur_conv_tc.cuh"
 #include "ur_device.cuh"
@@ -24,29 +24,6 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
-// ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // Convolution input: channels [0, c1) from x1 (at half resolution when low1),
 // channels [c1, c1 + c2) from x2 (full resolution).
 struct ConvIn {
@@ -55,118 +32,6 @@ struct ConvIn {
     const bf16 *x2;
     int c2;
 };
-
-__device__ __forceinline__ const bf16 *gather(const ConvIn &in, int n, int H, int W, int yy, int xx, int c) {
-    if (c < in.c1) {
-        if (in.low1) return in.x1 + (((size_t)n * (H >> 1) + (yy >> 1)) * (W >> 1) + (xx >> 1)) * in.c1 + c;
-        return in.x1 + (((size_t)n * H + yy) * W + xx) * in.c1 + c;
-    }
-    return in.x2 + (((size_t)n * H + yy) * W + xx) * in.c2 + (c - in.c1);
-}
-
-struct WgradP {
-    ConvIn in;             // forward input
-    const bf16 *dy;        // [N][H][W][Cout] gradient at the pre-activation
-    int N, H, W, Cin, Cout;
-    float *dw;             // [taps][Cout][Cin], accumulated
-    int px_per_warp;       // pixels per warp (multiple of 32)
-    int taps;              // 9, or 1 for an input that already holds the neighbourhood (centre tap only)
-};
-
-// dw[tap][co][ci] += sum_p dy[p][co] x[p + offset(tap)][ci].  Each warp owns a
-// 32 (co) x 32 (ci) tile and a slice of pixels (split K), staging 32-pixel
-// chunks of dy and of the shifted input in its own shared memory and reading
-// both transposed with ldmatrix.trans.
-__global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradP P) {
-    constexpr int LDS = 40;
-    __shared__ __align__(16) bf16 sA[4][2][32 * LDS];
-    __shared__ __align__(16) bf16 sB[4][2][32 * LDS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int co0 = blockIdx.y * 32;
-    const int kci = P.Cin / 32;
-    const int tap = P.taps == 1 ? 0 : blockIdx.z / kci, ci0 = (blockIdx.z % kci) * 32;
-    const int ky = P.taps == 1 ? 1 : tap / 3, kx = P.taps == 1 ? 1 : tap % 3;
-    const long long P_tot = (long long)P.N * P.H * P.W;
-    const long long p_begin = ((long long)blockIdx.x * 4 + warp) * P.px_per_warp;
-    const long long p_end = min(P_tot, p_begin + P.px_per_warp);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    if (p_begin < p_end) {
-        bf16 *A0 = sA[warp][0], *B0 = sB[warp][0];
-        auto load = [&](long long p0, int buf) {
-            bf16 *As = buf ? sA[warp][1] : A0;
-            bf16 *Bs = buf ? sB[warp][1] : B0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int idx = lane + 32 * q, px = idx >> 2, part = idx & 3;
-                const long long p = p0 + px;
-                const bool in_range = p < p_end;
-                const int x = in_range ? (int)(p % P.W) : 0;
-                const long long ny = in_range ? p / P.W : 0;
-                const int yrow = (int)(ny % P.H), n = (int)(ny / P.H);
-                cp_async16(&As[px * LDS + part * 8], in_range ? P.dy + (size_t)p * P.Cout + co0 + part * 8 : P.dy,
-                           in_range ? 16 : 0);
-                const int yy = yrow + ky - 1, xx = x + kx - 1;
-                const bool ok = in_range && yy >= 0 && yy < P.H && xx >= 0 && xx < P.W;
-                const bf16 *src = ok ? gather(P.in, n, P.H, P.W, yy, xx, ci0 + part * 8) : P.dy;
-                cp_async16(&Bs[px * LDS + part * 8], src, ok ? 16 : 0);
-            }
-            cp_async_commit();
-        };
-        const int nch = (int)((p_end - p_begin + 31) / 32);
-        load(p_begin, 0);
-        for (int c = 0; c < nch; ++c) {
-            if (c + 1 < nch) {
-                load(p_begin + 32ll * (c + 1), (c + 1) & 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncwarp();
-            const bf16 *A = sA[warp][c & 1];
-            const bf16 *B = sB[warp][c & 1];
-#pragma unroll
-            for (int ks = 0; ks < 32; ks += 16) {
-                uint32_t a[2][4], bb[4][2];
-                const int q = lane >> 3, r = lane & 7;
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi)   // A = dy^T: rows co, cols pixels
-                    ldsm_x4_t(a[mi], &A[(ks + ((q >> 1) << 3) + r) * LDS + mi * 16 + ((q & 1) << 3)]);
-#pragma unroll
-                for (int nj = 0; nj < 4; nj += 2) {   // B = x: rows pixels, cols ci
-                    uint32_t r4[4];
-                    ldsm_x4_t(r4, &B[(ks + ((q & 1) << 3) + r) * LDS + nj * 8 + ((q >> 1) << 3)]);
-                    bb[nj][0] = r4[0];
-                    bb[nj][1] = r4[1];
-                    bb[nj + 1][0] = r4[2];
-                    bb[nj + 1][1] = r4[3];
-                }
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                    for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], a[mi], bb[nj][0], bb[nj][1]);
-            }
-            __syncwarp();
-        }
-    }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int nj = 0; nj < 4; ++nj)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int co = co0 + mi * 16 + (lane >> 2) + h * 8;
-                const int ci = ci0 + nj * 8 + (lane & 3) * 2;
-                float *dst = P.dw + ((size_t)tap * P.Cout + co) * P.Cin + ci;
-                if (acc[mi][nj][2 * h] != 0.f) atomicAdd(dst, acc[mi][nj][2 * h]);
-                if (acc[mi][nj][2 * h + 1] != 0.f) atomicAdd(dst + 1, acc[mi][nj][2 * h + 1]);
-            }
-}
 
 // ------------------------------------------------------------------ small kernels
 
@@ -596,19 +461,16 @@ void sync_check(ur_nn *nn, const char *what) {
     }
 }
 
-// Split K over pixels: about 16k warps in total, so each output element takes a
-// bounded number of atomic additions whatever the layer's size.
-void conv_wgrad(ur_nn *nn, const ConvIn &in, const bf16 *dy, int B, int H, int W, int Cin, int Cout, float *dw,
+void conv_wgrad(ur_nn *nn, const bf16 *x, const bf16 *dy, int B, int H, int W, int Cin, int Cout, float *dw,
                 int taps = 9) {
-    const long long P_tot = (long long)B * H * W;
-    const long long tiles = (long long)(Cout / 32) * taps * (Cin / 32);
-    const long long slices = std::max<long long>(1, 16384 / tiles);
-    const int px_per_warp = (int)std::max<long long>(128, ((P_tot + slices - 1) / slices + 31) / 32 * 32);
-    const long long warps = (P_tot + px_per_warp - 1) / px_per_warp;
-    WgradP W_{in, dy, B, H, W, Cin, Cout, dw, px_per_warp, taps};
-    dim3 grid((unsigned)((warps + 3) / 4), Cout / 32, taps * (Cin / 32));
-    k_conv3x3_wgrad<<<grid, 128, 0, nn->stream>>>(W_);
-    ck(cudaGetLastError(), "wgrad kernel");
+    urnn::WgradTC P{x, Cin, B, H, W, dy, Cout, taps, dw};
+    std::string why;
+    const cudaError_t e = urnn::wgrad3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(e == cudaErrorInvalidValue ? UR_ERR_INVALID_ARG : UR_ERR_CUDA,
+             why.empty() ? std::string("wgrad kernel: ") + cudaGetErrorString(e) : why);
+    }
 }
 
 void bias_grad(ur_nn *nn, const bf16 *d, long long P, int C, float *db) {
@@ -644,6 +506,16 @@ Layer layer_in(ur_nn *nn, int l) {
     }
 }
 
+// Plain NHWC input of conv l; a decoder input (upsample ++ skip) is materialised in nn->cat.
+const bf16 *conv_input(ur_nn *nn, int B, int l) {
+    const Layer L = layer_in(nn, l);
+    if (!L.in.x2) return L.in.x1;
+    k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(L.in.x1, L.in.c1, L.in.x2,
+                                                                                      L.in.c2, B, L.H, L.W, nn->cat);
+    ck(cudaGetLastError(), "upcat kernel");
+    return nn->cat;
+}
+
 void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad) {
     const long long P = (long long)B * nn->H * nn->W;
     k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, 1.f / nn->scale, nn->x, nn->xn);
@@ -652,13 +524,7 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
     ck(cudaGetLastError(), "pack kernel");
     for (int l = 0; l < kNumConv; ++l) {
         const Layer L = layer_in(nn, l);
-        const bf16 *in = L.in.x1;
-        if (L.in.x2) {   // decoder: materialise upsample ++ skip
-            k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(
-                L.in.x1, L.in.c1, L.in.x2, L.in.c2, B, L.H, L.W, nn->cat);
-            ck(cudaGetLastError(), "upcat kernel");
-            in = nn->cat;
-        }
+        const bf16 *in = conv_input(nn, B, l);
         if (l == 0)   // neighbourhood already in the 32 input channels: one tap
             conv_fwd(nn, in, B, L.H, L.W, 32, nn->cout[0], nn->wfirst, nn->params + nn->boff[0], nullptr, nn->act[0].p,
                      true, 1);
@@ -684,7 +550,7 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
     const long long nb = (long long)B * Lb.H * Lb.W * nn->cout[lb] / 8;
     k_relu_mask<<<grid_for(nb), 256, 0, nn->stream>>>(d_out, nn->act[lb].p, nb);
-    conv_wgrad(nn, Lb.in, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
+    conv_wgrad(nn, nn->act[la].p, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
     bias_grad(nn, d_out, (long long)B * Lb.H * Lb.W, nn->cout[lb], nn->grads + nn->boff[lb]);
     k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
                                                                                   nn->cout[lb], nn->cin[lb]);
@@ -692,11 +558,12 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
     conv_fwd(nn, d_out, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p, scratch, false);
     if (la == 0) {   // first layer: single-tap gradient over the neighbourhood channels, then back to [9][C][32]
         ck(cudaMemsetAsync(nn->dwfirst, 0, sizeof(float) * 32 * nn->width, nn->stream), "memset");
-        conv_wgrad(nn, La.in, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
+        conv_wgrad(nn, nn->x, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
         k_unpack_first_grad<<<grid_for(18ll * nn->width), 256, 0, nn->stream>>>(nn->dwfirst, nn->width,
                                                                                nn->grads + nn->woff[0]);
     } else {
-        conv_wgrad(nn, La.in, scratch, B, La.H, La.W, nn->cin[la], nn->cout[la], nn->grads + nn->woff[la]);
+        conv_wgrad(nn, conv_input(nn, B, la), scratch, B, La.H, La.W, nn->cin[la], nn->cout[la],
+                   nn->grads + nn->woff[la]);
     }
     bias_grad(nn, scratch, (long long)B * La.H * La.W, nn->cout[la], nn->grads + nn->boff[la]);
     if (din) {
