@@ -467,6 +467,134 @@ def run_adjoint(args, rank, world, local_rank):
     sim.close()
 
 
+DENOISER_WORKLOAD = ("denoiser: 4-level U-Net (widths 32-256, 1.95M parameters) on [128 x 3200] analytic channel "
+                     "data, batch 8 pairs traced from jittered layered phantoms (1e6-ray input, 3e7-ray target), "
+                     "BF16 weights/activations, FP32 accumulation, one step = forward + loss + backward + Adam")
+NN_LAUNCHES_PER_TRAIN_STEP = 97   # kernels of one ur_nn_train_step (launch list in profiles/)
+
+
+def unet_forward_flops(batch, h, w, c=32):
+    """Algorithmic multiply-adds x 2 of one forward pass (3x3 convolutions; the
+    first sees its 2 real input channels)."""
+    res = (1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1)
+    cin = (2, c, c, 2 * c, 2 * c, 4 * c, 4 * c, 8 * c, 12 * c, 4 * c, 6 * c, 2 * c, 3 * c, c)
+    cout = (c, c, 2 * c, 2 * c, 4 * c, 4 * c, 8 * c, 8 * c, 4 * c, 4 * c, 2 * c, 2 * c, c, c)
+    return sum(2 * 9 * ci * co * batch * (h // r) * (w // r) for r, ci, co in zip(res, cin, cout))
+
+
+def oracle_denoiser_rate(target_s):
+    """FP64 reference U-Net: forward + backward on a 128 x 400 crop, scaled to
+    [128 x 3200] samples/s."""
+    import numpy as np
+    from oracle import denoiser as D
+    rng = np.random.default_rng(0)
+    p = D.init_params(rng)
+    x = rng.standard_normal((1, 128, 400, 2))
+    t = rng.standard_normal((1, 128, 400, 2))
+    n, t0 = 0, time.perf_counter()
+    while True:
+        y, cache = D.forward(p, x)
+        _, g = D.mse(y, t)
+        D.backward(p, cache, g)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return n / 8.0 / dt, n, dt
+
+
+def run_denoiser(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2501_05828_gb300 as ur
+    from paper_2501_05828_gb300 import denoise as dz
+    import phantoms
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B = 8
+    sim = ur.Simulator(local_rank)
+    xr, xq, tr, tq, _ = dz.make_pairs(sim, phantoms.batched_variant, range(1 + 8 * rank, 9 + 8 * rank), 1e6, 3e7)
+    sim.close()
+    H, W = int(xr.shape[1]), int(xr.shape[2])
+    net = ur.Denoiser(local_rank, max_batch=B, n_el=H, n_s=W, width=32, seed=1)
+    net.set_scale(dz.channel_scale(tr, tq))
+    lr = 1e-4
+    for _ in range(args.warmup):
+        net.train_step(xr, xq, tr, tq, lr)
+        net.forward(xr, xq)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        loss = net.train_step(xr, xq, tr, tq, lr)
+        ev[k][1].record()
+        flush.zero_()
+        fe[k][0].record()
+        net.forward(xr, xq)
+        fe[k][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ms_fwd = sum(a.elapsed_time(b) for a, b in fe) / args.steps
+    # end to end through the C ABI with pinned host buffers (inputs + targets in, loss out)
+    hx = [t.cpu().pin_memory() for t in (xr, xq, tr, tq)]
+    h2d = sum(t.numel() * 4 for t in hx)
+    n_e2e = 0 if args.skip_e2e else max(3, min(args.steps, 20))
+    e2e_ms = float("nan")
+    if n_e2e:
+        net.train_step(*hx, lr)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            net.train_step(*hx, lr)
+        e2e_ms = (time.perf_counter() - t0) / n_e2e * 1e3
+    F = unet_forward_flops(B, H, W)
+    F_first = 2 * 9 * 2 * 32 * B * H * W
+    train_flops = 3 * F - F_first           # forward, data gradients (none for the input), weight gradients
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak_sus = peaks.get("bf16_tflops_sustained", 1700.0)
+    peak_burst = peaks.get("bf16_tflops", 1900.0)
+    ach = train_flops / (ms * 1e-3) / 1e12
+    ach_fwd = F / (ms_fwd * 1e-3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": "denoiser training samples/s ([128 x 3200] channel data)", "value": B * world / (ms * 1e-3),
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": DENOISER_WORKLOAD, "batch": B, "n_el": H, "n_s": W,
+                       "l2": "flushed before every timed call (256 MiB write, untimed)"},
+            "inference_samples_per_s": B * world / (ms_fwd * 1e-3), "ms_forward": ms_fwd, "loss": loss,
+            "roofline": {"bound": "tensor", "kernel": "train step (tcgen05 convolutions + elementwise kernels)",
+                         "achieved": ach, "peak": peak_sus, "unit": "TFLOP/s", "frac": ach / peak_sus,
+                         "traffic": None, "peak_note": "bf16_tflops_sustained of measured",
+                         "algorithmic_flops_per_step": train_flops,
+                         "forward": {"achieved": ach_fwd, "peak": peak_burst, "frac": ach_fwd / peak_burst,
+                                     "peak_note": "bf16_tflops (burst) of measured", "flops": F}},
+            "gpu_launches": NN_LAUNCHES_PER_TRAIN_STEP * args.steps + 23 * args.steps,
+            "e2e": {"value": B * world / (e2e_ms * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms,
+                    "path": "ur_nn_train_step with pinned host inputs/targets (staged copies) and the loss to host"},
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rate, n, dt = oracle_denoiser_rate(min(args.cpu_seconds, 20.0))
+            line["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                                    "sample": "%d forward+backward passes of the FP64 reference on a 128x400 crop "
+                                              "(1/8 sample) in %.1f s, numpy threads" % (n, dt)}
+        print(json.dumps(line), flush=True)
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,7 +605,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
-    ap.add_argument("--workload", default="layered", choices=("layered", "batched", "adjoint"))
+    ap.add_argument("--workload", default="layered", choices=("layered", "batched", "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -490,6 +618,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.workload == "adjoint":
         run_adjoint(args, rank, world, local_rank)
+    elif args.workload == "denoiser":
+        run_denoiser(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -241,12 +241,20 @@ ur_status ur_nn_params(ur_nn *nn, float *get, const float *set);
 /* Normalisation: the network sees channel data / scale. */
 ur_status ur_nn_set_scale(ur_nn *nn, float scale);
 
-/* Denoise `batch` frames: rf, quad [batch][n_el][n_s] (device) -> out_rf, out_quad (device). */
+/* Denoise `batch` frames: rf, quad [batch][n_el][n_s] -> out_rf, out_quad (same
+ * layout).  Each pointer may be device or host memory (host buffers are staged
+ * through device copies on the network's stream; pinned memory keeps the copies
+ * asynchronous).  Synchronises the stream before returning.
+ * Errors: UR_ERR_INVALID_ARG (batch outside 1..max_batch, null pointers),
+ * UR_ERR_TIMEOUT (a convolution pipeline wait gave up), UR_ERR_CUDA. */
 ur_status ur_nn_forward(ur_nn *nn, const float *rf, const float *quad, int batch, float *out_rf, float *out_quad);
 
-/* One training step on `batch` pairs (inputs rf, quad; targets t_rf, t_quad; device):
- * forward, loss, backward, then Adam with learning rate lr (lr = 0: no update).
- * loss (nullable, host) receives the loss; grad_out (nullable) the parameter gradient. */
+/* One training step on `batch` pairs (inputs rf, quad; targets t_rf, t_quad;
+ * host or device, as for ur_nn_forward): forward, loss, backward, then Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr
+ * (lr = 0: no update).  loss (nullable, host) receives the loss; grad_out
+ * (nullable, host or device, ur_nn_param_count floats) the parameter gradient
+ * before the update.  Same errors as ur_nn_forward. */
 ur_status ur_nn_train_step(ur_nn *nn, const float *rf, const float *quad, const float *t_rf, const float *t_quad,
                            int batch, float lr, float *loss, float *grad_out);
 

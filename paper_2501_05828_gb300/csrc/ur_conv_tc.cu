@@ -1,7 +1,7 @@
 // 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores.
 //
-// One CTA computes a tile of 128 consecutive pixels of one image row (the M
-// dimension, one TMEM lane per pixel) by BN output channels (N).  The K loop
+// A tile is 128 consecutive pixels of one image row (the M dimension, one TMEM
+// lane per pixel) by BN output channels (N); persistent CTAs stride over tiles.  The K loop
 // walks the 9 taps and, within each, the input channels in chunks of BK (64:
 // 128-byte rows, or 32: 64-byte rows).  For every K step one thread issues two
 // TMA loads into a ring of shared-memory stages:
@@ -10,10 +10,11 @@
 //   B: the BN x BK box of the weights [9][Cout][Cin] at this tap,
 // both written in the canonical K-major swizzled layout the tensor core reads.
 // A second thread issues tcgen05.mma (M = 128, N = BN, K = 16, BF16 inputs,
-// FP32 accumulator in TMEM) and releases each stage with tcgen05.commit.  The
-// four warps then read the accumulator with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31) and apply bias, ReLU and an optional ReLU mask (for data
-// gradients) before storing BF16.
+// FP32 accumulator in TMEM, two accumulators in turn) and releases each stage
+// with tcgen05.commit.  Four epilogue warps read a finished accumulator with
+// tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) .. +31) and apply bias, ReLU and
+// an optional ReLU mask (for data gradients) before storing BF16, while the
+// next tile's MMAs run.
 //
 // Every mbarrier wait is bounded by the global timer; a wait that gives up
 // records an error code for the host and the block still frees its TMEM.
@@ -146,6 +147,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
+constexpr int kConvThreads = 192;   // warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 epilogue
+
 template <int BN, int BK>
 struct Cfg {
     static constexpr int ROW = BK * 2;                    // bytes per operand row
@@ -153,23 +156,33 @@ struct Cfg {
     static constexpr int B_BYTES = BN * ROW;
     static constexpr int A_PAD = (A_BYTES + 1023) / 1024 * 1024;
     static constexpr int B_PAD = (B_BYTES + 1023) / 1024 * 1024;
-    static constexpr int BUDGET = BN >= 192 ? 200 * 1024 : 100 * 1024;   // two CTAs per SM below 192 columns
+    static constexpr int BUDGET = BN >= 192 ? 200 * 1024 : 100 * 1024;   // one CTA per SM from 192 columns on
     static constexpr int S_RAW = BUDGET / (A_PAD + B_PAD);
     static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 6 ? 6 : S_RAW);
-    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-    static constexpr int SMEM = S * (A_PAD + B_PAD) + 1024 + 8 * (2 * S + 1) + 16;
+    static constexpr int ACC_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;   // one accumulator
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;                                            // double-buffered
+    static constexpr int N_BARS = 2 * S + 4;   // full[S], empty[S], acc_full[2], acc_empty[2]
+    static constexpr int SMEM = S * (A_PAD + B_PAD) + 1024 + 8 * N_BARS + 16;
 };
 
 struct Args {
-    int N, H, W, C, Cout, nxb, relu, taps;
+    int N, H, W, C, Cout, nxb, relu, taps, n_tiles, n_ntiles;
     const float *bias;
     const bf16 *mask;
     bf16 *y;
     int *err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ...; tile t = (M tile, N tile) with the N
+// tile fastest, M tile = (image n, row y, 128-pixel block).  The producer runs ahead across
+// tiles; the accumulator is double-buffered in TMEM so the epilogue of one tile overlaps the
+// MMAs of the next.
 template <int BN, int BK>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kConvThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, const Args a) {
     using K = Cfg<BN, BK>;
     extern __shared__ uint8_t smem_raw[];
@@ -178,15 +191,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sm = smem_raw + (base - raw);
     const uint32_t sA = base, sB = base + K::S * K::A_PAD;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + K::S * (K::A_PAD + K::B_PAD));
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * K::S + 1);
-    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S), accb = s_addr(bars + 2 * K::S);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + K::N_BARS);
+    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S);
+    const uint32_t accf0 = s_addr(bars + 2 * K::S), acce0 = s_addr(bars + 2 * K::S + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    int t = blockIdx.x;
-    const int xb = t % a.nxb;
-    t /= a.nxb;
-    const int y = t % a.H, n = t / a.H;
-    const int x0 = xb * kBM, co0 = blockIdx.y * BN;
     const int kc = a.C / BK, nk = a.taps * kc;
     const uint64_t deadline = now_ns() + kWaitNs;
 
@@ -195,127 +203,162 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 4);   // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(s_addr(tslot), K::TMEM_COLS);
+    if (warp == 1) tmem_alloc(s_addr(tslot), K::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
     bool ok = true;
 
+    auto decode = [&](int t, int &n, int &y, int &x0, int &co0) {
+        const int nt = t % a.n_ntiles;
+        int m = t / a.n_ntiles;
+        const int xb = m % a.nxb;
+        m /= a.nxb;
+        y = m % a.H;
+        n = m / a.H;
+        x0 = xb * kBM;
+        co0 = nt * BN;
+    };
+
     if (warp == 0) {
         if (lane == 0) {   // TMA producer
-            int issued = 0;
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % K::S;
-                const uint32_t ph = (uint32_t)(kt / K::S) & 1u;
-                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, deadline)) {
-                    ok = false;
-                    break;
+            int it = 0;
+            for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+                int n, y, x0, co0;
+                decode(t, n, y, x0, co0);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % K::S;
+                    if (!mbar_wait(empty0 + 8 * s, ((uint32_t)(it / K::S) & 1u) ^ 1u, deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    const int tap = kt / kc, c0 = (kt - tap * kc) * BK;
+                    const int ky = a.taps == 1 ? 1 : tap / 3, kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + K::B_BYTES));
+                    tma_load_4d(sA + s * K::A_PAD, &tmx, c0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * s);
+                    tma_load_3d(sB + s * K::B_PAD, &tmw, c0, co0, tap, full0 + 8 * s);
                 }
-                const int tap = kt / kc, c0 = (kt - tap * kc) * BK;
-                const int ky = a.taps == 1 ? 1 : tap / 3, kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
-                mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + K::B_BYTES));
-                tma_load_4d(sA + s * K::A_PAD, &tmx, c0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * s);
-                tma_load_3d(sB + s * K::B_PAD, &tmw, c0, co0, tap, full0 + 8 * s);
-                issued = kt + 1;
             }
             if (!ok)   // let the copies already in flight land before the block can exit
-                for (int kt = issued > K::S ? issued - K::S : 0; kt < issued; ++kt)
-                    mbar_wait(full0 + 8 * (kt % K::S), (uint32_t)(kt / K::S) & 1u, deadline + kWaitNs / 20);
+                for (int j = it > K::S ? it - K::S : 0; j < it; ++j)
+                    mbar_wait(full0 + 8 * (j % K::S), (uint32_t)(j / K::S) & 1u, deadline + kWaitNs / 20);
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
             constexpr uint32_t idesc = idesc_bf16<BN>();
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % K::S;
-                if (!mbar_wait(full0 + 8 * s, (uint32_t)(kt / K::S) & 1u, deadline)) {
+            int it = 0, i = 0;
+            for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (!mbar_wait(acce0 + 8 * b, ((uint32_t)(i >> 1) & 1u) ^ 1u, deadline)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = sA + s * K::A_PAD, b0 = sB + s * K::B_PAD;
+                const uint32_t d = tmem + (uint32_t)(b * K::ACC_COLS);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % K::S;
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(it / K::S) & 1u, deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = sA + s * K::A_PAD, b0 = sB + s * K::B_PAD;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k)
-                    mma_bf16(tmem, sdesc(a0 + 32 * k, K::ROW), sdesc(b0 + 32 * k, K::ROW), idesc, (kt | k) != 0);
-                mma_commit(empty0 + 8 * s);
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(d, sdesc(a0 + 32 * k, K::ROW), sdesc(b0 + 32 * k, K::ROW), idesc, (kt | k) != 0);
+                    mma_commit(empty0 + 8 * s);
+                }
+                mma_commit(accf0 + 8 * b);   // accumulator b complete (or abandoned: the status word says so)
             }
-            mma_commit(accb);
         }
         __syncwarp();
-    }
-
-    // epilogue: TMEM -> registers -> bias / ReLU / mask -> BF16 NHWC
-    const bool acc_ready = mbar_wait(accb, 0, deadline + kWaitNs / 10);
-    const bool warp_ready = __all_sync(0xffffffffu, acc_ready) != 0;
-    if (!acc_ready) ok = false;
-    tc_fence_after();
-    if (warp_ready) {
-        const int x = x0 + warp * 32 + lane;
-        const size_t pix = ((size_t)n * a.H + y) * a.W + x;
+    } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+        const int q = warp & 3;
+        int i = 0;
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ready = mbar_wait(accf0 + 8 * b, (uint32_t)(i >> 1) & 1u, deadline);
+            if (__all_sync(0xffffffffu, ready) == 0) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            int n, y, x0, co0;
+            decode(t, n, y, x0, co0);
+            const int x = x0 + q * 32 + lane;
+            const size_t pix = ((size_t)n * a.H + y) * a.W + x;
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-            if (x < a.W) {
-                const int co = co0 + c;
-                float v[32];
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+                if (x < a.W) {
+                    const int co = co0 + c;
+                    float v[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                if (a.bias) {
-                    const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + co);
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                    if (a.bias) {
+                        const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + co);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 b = b4[j];
-                        v[4 * j] += b.x;
-                        v[4 * j + 1] += b.y;
-                        v[4 * j + 2] += b.z;
-                        v[4 * j + 3] += b.w;
-                    }
-                }
-                if (a.relu) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
-                }
-                if (a.mask) {
-                    const uint4 *m4 = reinterpret_cast<const uint4 *>(a.mask + pix * a.Cout + co);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint4 mv = m4[q];
-                        const __nv_bfloat162 *mb = reinterpret_cast<const __nv_bfloat162 *>(&mv);
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            const float2 f = __bfloat1622float2(mb[h]);
-                            if (!(f.x > 0.f)) v[8 * q + 2 * h] = 0.f;
-                            if (!(f.y > 0.f)) v[8 * q + 2 * h + 1] = 0.f;
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 bb = b4[j];
+                            v[4 * j] += bb.x;
+                            v[4 * j + 1] += bb.y;
+                            v[4 * j + 2] += bb.z;
+                            v[4 * j + 3] += bb.w;
                         }
                     }
-                }
-                uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + co);
+                    if (a.relu) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4 o;
-                    __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * q], v[8 * q + 1]);
-                    __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
-                    __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
-                    o.x = *reinterpret_cast<uint32_t *>(&h0);
-                    o.y = *reinterpret_cast<uint32_t *>(&h1);
-                    o.z = *reinterpret_cast<uint32_t *>(&h2);
-                    o.w = *reinterpret_cast<uint32_t *>(&h3);
-                    dst[q] = o;
+                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
+                    }
+                    if (a.mask) {
+                        const uint4 *m4 = reinterpret_cast<const uint4 *>(a.mask + pix * a.Cout + co);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            const uint4 mv = m4[g];
+                            const __nv_bfloat162 *mb = reinterpret_cast<const __nv_bfloat162 *>(&mv);
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const float2 f = __bfloat1622float2(mb[h]);
+                                if (!(f.x > 0.f)) v[8 * g + 2 * h] = 0.f;
+                                if (!(f.y > 0.f)) v[8 * g + 2 * h + 1] = 0.f;
+                            }
+                        }
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + co);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint4 o;
+                        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * g], v[8 * g + 1]);
+                        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * g + 2], v[8 * g + 3]);
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * g + 4], v[8 * g + 5]);
+                        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * g + 6], v[8 * g + 7]);
+                        o.x = *reinterpret_cast<uint32_t *>(&h0);
+                        o.y = *reinterpret_cast<uint32_t *>(&h1);
+                        o.z = *reinterpret_cast<uint32_t *>(&h2);
+                        o.w = *reinterpret_cast<uint32_t *>(&h3);
+                        dst[g] = o;
+                    }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);   // accumulator b may be overwritten
         }
     }
     if (!ok) atomicExch(a.err, 1);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         tmem_free(tmem, K::TMEM_COLS);
     }
@@ -491,25 +534,41 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
+// Persistent grid: as many CTAs as fit on the SMs at once (shared memory and TMEM), at most one per tile.
 template <int BN, int BK>
-cudaError_t launch(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_mtiles, cudaStream_t stream) {
+cudaError_t launch(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_sm, cudaStream_t stream) {
     using K = Cfg<BN, BK>;
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e == cudaSuccess)   // all of the unified L1/shared array as shared memory, so several CTAs fit per SM
+        e = cudaFuncSetAttribute(k_conv_tc<BN, BK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    k_conv_tc<BN, BK><<<dim3((unsigned)n_mtiles, (unsigned)(a.Cout / BN)), kThreads, K::SMEM, stream>>>(mx, mw, a);
+    // co-resident CTAs per SM from shared memory (with the per-block reserve), registers, warps and TMEM
+    int dev = 0, smem_sm = 0, reserve = 0;
+    cudaFuncAttributes fa{};
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, k_conv_tc<BN, BK>)) != cudaSuccess)
+        return e;
+    const int regs = ((std::max(fa.numRegs, 1) + 7) / 8) * 8 * kConvThreads;
+    int occ = std::min({smem_sm / (K::SMEM + reserve), 65536 / regs, 64 / (kConvThreads / 32), 512 / K::TMEM_COLS});
+    occ = std::max(1, occ);
+    const int grid = (int)std::min<long long>(a.n_tiles, (long long)occ * std::max(1, n_sm));
+    k_conv_tc<BN, BK><<<grid, kConvThreads, K::SMEM, stream>>>(mx, mw, a);
     return cudaGetLastError();
 }
 
 template <int BK>
-cudaError_t launch_bn(int BN, const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_mtiles,
+cudaError_t launch_bn(int BN, const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_sm,
                       cudaStream_t stream) {
     switch (BN) {
-        case 32: return launch<32, BK>(mx, mw, a, n_mtiles, stream);
-        case 64: return launch<64, BK>(mx, mw, a, n_mtiles, stream);
-        case 96: return launch<96, BK>(mx, mw, a, n_mtiles, stream);
-        case 128: return launch<128, BK>(mx, mw, a, n_mtiles, stream);
-        case 192: return launch<192, BK>(mx, mw, a, n_mtiles, stream);
-        default: return launch<256, BK>(mx, mw, a, n_mtiles, stream);
+        case 32: return launch<32, BK>(mx, mw, a, n_sm, stream);
+        case 64: return launch<64, BK>(mx, mw, a, n_sm, stream);
+        case 96: return launch<96, BK>(mx, mw, a, n_sm, stream);
+        case 128: return launch<128, BK>(mx, mw, a, n_sm, stream);
+        case 192: return launch<192, BK>(mx, mw, a, n_sm, stream);
+        default: return launch<256, BK>(mx, mw, a, n_sm, stream);
     }
 }
 
@@ -522,7 +581,7 @@ int pick_bn(int cout) {
 
 }  // namespace
 
-cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, cudaStream_t stream, std::string *why) {
+cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t stream, std::string *why) {
     const int BK = p.C % 64 == 0 ? 64 : 32;
     const int BN = pick_bn(p.Cout);
     if (p.C < 32 || p.C % 32 || BN == 0 || (p.taps != 9 && p.taps != 1) || p.N < 1 || p.H < 1 || p.W < 1 || !p.x || !p.w || !p.y || !d_err ||
@@ -565,14 +624,14 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, cudaStream_t stream, std::st
             return cudaErrorInvalidValue;
         }
     }
-    Args a{p.N, p.H, p.W, p.C, p.Cout, (p.W + kBM - 1) / kBM, p.relu, p.taps, p.bias, p.mask, p.y, d_err};
-    const long long n_mtiles = (long long)p.N * p.H * a.nxb;
-    if (n_mtiles > 0x7fffffffll) {
+    const int nxb = (p.W + kBM - 1) / kBM;
+    const long long n_tiles = (long long)p.N * p.H * nxb * (p.Cout / BN);
+    if (n_tiles > 0x7fffffffll) {
         if (why) *why = "conv3x3_tc: too many tiles";
         return cudaErrorInvalidValue;
     }
-    return BK == 64 ? launch_bn<64>(BN, mx, mw, a, (int)n_mtiles, stream)
-                    : launch_bn<32>(BN, mx, mw, a, (int)n_mtiles, stream);
+    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, p.bias, p.mask, p.y, d_err};
+    return BK == 64 ? launch_bn<64>(BN, mx, mw, a, n_sm, stream) : launch_bn<32>(BN, mx, mw, a, n_sm, stream);
 }
 
 namespace {

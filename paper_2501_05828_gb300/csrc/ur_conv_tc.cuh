@@ -25,7 +25,7 @@ struct ConvTC {
 // non-zero code if a pipeline wait inside the kernel gave up (bounded waits);
 // the caller reads it at its next synchronisation.  Returns a CUDA error for
 // launch failures and fills `why` for rejected shapes.
-cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, cudaStream_t stream, std::string *why);
+cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t stream, std::string *why);
 
 // dw[tap][co][ci] += sum over pixels of dy[p][co] x[p + offset(tap)][ci]
 // (zero outside the image), FP32 accumulation on the tensor cores, atomically

@@ -400,13 +400,16 @@ struct ur_nn {
     float *xn = nullptr, *yn = nullptr, *gy = nullptr;
     Tensor act[kNumConv];    // post-ReLU outputs of every conv
     Tensor pool[3];          // pooled e1, e2, e3
-    Tensor gbuf[4];          // gradient scratch per level (two of the largest sizes)
+    // training buffers (allocated by the first training step), in units of B*H*W*C BF16 values:
+    // gA gradient at d1b's output (1), gB block scratch (1), gcat input gradient of a block (3),
+    // gLow gradient of the half-resolution decoder input (1/2), gSkip skip-tensor gradients (1, 1/2, 1/4)
     bf16 *gcat = nullptr, *gA = nullptr, *gB = nullptr, *gSkip[3] = {nullptr, nullptr, nullptr}, *gLow = nullptr;
     bf16 *cat = nullptr;     // decoder input (upsampled lower level ++ skip)
     bf16 *wfirst = nullptr;  // first convolution as one tap over the 32 neighbourhood channels [C][32]
     float *dwfirst = nullptr;
     double *loss = nullptr;
     int *d_err = nullptr, *h_err = nullptr;   // bounded-wait failures inside the convolution kernels
+    float *stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // host-buffer staging
     std::vector<void *> allocs;
 
     void *alloc(size_t bytes) {
@@ -442,12 +445,34 @@ void conv_fwd(ur_nn *nn, const bf16 *x, int B, int H, int W, int Cin, int Cout, 
               const bf16 *mask, bf16 *y, bool relu, int taps = 9) {
     urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0};
     std::string why;
-    const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->stream, &why);
+    const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(e == cudaErrorInvalidValue ? UR_ERR_INVALID_ARG : UR_ERR_CUDA,
              why.empty() ? std::string("conv kernel: ") + cudaGetErrorString(e) : why);
     }
+}
+
+bool dev_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a [batch][n_el][n_s] FP32 argument: the pointer itself, or a
+// staging buffer (slot) filled from host memory on the network's stream.
+float *staged(ur_nn *nn, int slot, const float *p, int batch, bool copy_in) {
+    if (dev_ptr(p)) return const_cast<float *>(p);
+    const size_t n = (size_t)nn->max_batch * nn->H * nn->W;
+    if (!nn->stage[slot]) nn->stage[slot] = (float *)nn->alloc(sizeof(float) * n);
+    if (copy_in)
+        ck(cudaMemcpyAsync(nn->stage[slot], p, sizeof(float) * (size_t)batch * nn->H * nn->W, cudaMemcpyHostToDevice,
+                           nn->stream),
+           "copy input");
+    return nn->stage[slot];
 }
 
 // Synchronises the network's stream and reports a convolution that gave up waiting.
@@ -574,7 +599,19 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
     ck(cudaGetLastError(), "block backward");
 }
 
+void ensure_train_buffers(ur_nn *nn) {
+    if (nn->gA) return;
+    const size_t B = nn->max_batch, H = nn->H, W = nn->W, C = nn->width, unit = B * H * W * C;
+    nn->gy = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
+    nn->gA = (bf16 *)nn->alloc(sizeof(bf16) * unit);
+    nn->gB = (bf16 *)nn->alloc(sizeof(bf16) * unit);
+    nn->gcat = (bf16 *)nn->alloc(sizeof(bf16) * 3 * unit);
+    nn->gLow = (bf16 *)nn->alloc(sizeof(bf16) * unit / 2);
+    for (int q = 0; q < 3; ++q) nn->gSkip[q] = (bf16 *)nn->alloc(sizeof(bf16) * (unit >> q));
+}
+
 double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *t_rf, const float *t_quad) {
+    ensure_train_buffers(nn);
     forward(nn, B, rf, quad, nullptr, nullptr);
     const long long P = (long long)B * nn->H * nn->W;
     ck(cudaMemsetAsync(nn->loss, 0, sizeof(double), nn->stream), "memset loss");
@@ -582,43 +619,33 @@ double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *
     k_loss<<<grid_for(P), 256, 0, nn->stream>>>(nn->yn, t_rf, t_quad, P, 1.f / nn->scale, nn->gy, nn->loss);
     const int C = nn->width;
     // head
-    bf16 *g_full_a = nn->gA, *g_full_b = nn->gB;
     k_head_bwd<<<nn->sms * 8, 256, 0, nn->stream>>>(nn->gy, nn->act[13].p, nn->params + nn->hw_off, C, P,
-                                                    nn->grads + nn->hw_off, nn->grads + nn->hb_off, g_full_a);
+                                                    nn->grads + nn->hw_off, nn->grads + nn->hb_off, nn->gA);
     ck(cudaGetLastError(), "head backward");
-    // gradient of d1b's output is g_full_a (already masked by d1 > 0; masking again is harmless)
+    // gradient of d1b's output is gA (already masked by d1 > 0; masking again is harmless)
     const int H = nn->H, W = nn->W;
-    // decoder level 1: concat(up(d2), e1)
-    block_bwd(nn, B, 12, 13, g_full_a, g_full_b, nn->gcat);
-    k_unconcat<<<grid_for((long long)B * H * W * (3 * C)), 256, 0, nn->stream>>>(nn->gcat, B, H, W, 2 * C, C, nn->gLow,
-                                                                                  nn->gSkip[0]);
+    // decoder level 1: input concat(up(d2), e1)
+    block_bwd(nn, B, 12, 13, nn->gA, nn->gB, nn->gcat);
+    k_unconcat<<<grid_for((long long)B * H * W * (3 * C) / 8), 256, 0, nn->stream>>>(nn->gcat, B, H, W, 2 * C, C, nn->gLow,
+                                                                                      nn->gSkip[0]);
     ck(cudaGetLastError(), "unconcat");
-    // decoder level 2: gradient of d2 (half resolution) is gLow
-    bf16 *d2 = nn->gbuf[1].p;
-    ck(cudaMemcpyAsync(d2, nn->gLow, sizeof(bf16) * (size_t)B * (H / 2) * (W / 2) * 2 * C, cudaMemcpyDeviceToDevice,
-                       nn->stream), "copy");
-    block_bwd(nn, B, 10, 11, d2, nn->gbuf[2].p, nn->gcat);
-    k_unconcat<<<grid_for((long long)B * (H / 2) * (W / 2) * (6 * C)), 256, 0, nn->stream>>>(
+    // decoder level 2: the gradient of d2 (half resolution) is gLow
+    block_bwd(nn, B, 10, 11, nn->gLow, nn->gB, nn->gcat);
+    k_unconcat<<<grid_for((long long)B * (H / 2) * (W / 2) * (6 * C) / 8), 256, 0, nn->stream>>>(
         nn->gcat, B, H / 2, W / 2, 4 * C, 2 * C, nn->gLow, nn->gSkip[1]);
-    bf16 *d3 = nn->gbuf[1].p;
-    ck(cudaMemcpyAsync(d3, nn->gLow, sizeof(bf16) * (size_t)B * (H / 4) * (W / 4) * 4 * C, cudaMemcpyDeviceToDevice,
-                       nn->stream), "copy");
-    block_bwd(nn, B, 8, 9, d3, nn->gbuf[2].p, nn->gcat);
-    k_unconcat<<<grid_for((long long)B * (H / 4) * (W / 4) * (12 * C)), 256, 0, nn->stream>>>(
+    block_bwd(nn, B, 8, 9, nn->gLow, nn->gB, nn->gcat);
+    k_unconcat<<<grid_for((long long)B * (H / 4) * (W / 4) * (12 * C) / 8), 256, 0, nn->stream>>>(
         nn->gcat, B, H / 4, W / 4, 8 * C, 4 * C, nn->gLow, nn->gSkip[2]);
-    // bottleneck: gradient of e4 is gLow
-    bf16 *d4 = nn->gbuf[1].p;
-    ck(cudaMemcpyAsync(d4, nn->gLow, sizeof(bf16) * (size_t)B * (H / 8) * (W / 8) * 8 * C, cudaMemcpyDeviceToDevice,
-                       nn->stream), "copy");
-    block_bwd(nn, B, 6, 7, d4, nn->gbuf[2].p, nn->gbuf[3].p);   // d(pool3) at H/8
-    k_pool2_bwd_add<<<grid_for((long long)B * (H / 4) * (W / 4) * 4 * C), 256, 0, nn->stream>>>(
-        nn->gSkip[2], nn->gbuf[3].p, B, H / 4, W / 4, 4 * C);
-    block_bwd(nn, B, 4, 5, nn->gSkip[2], nn->gbuf[2].p, nn->gbuf[3].p);   // d(pool2) at H/4
-    k_pool2_bwd_add<<<grid_for((long long)B * (H / 2) * (W / 2) * 2 * C), 256, 0, nn->stream>>>(
-        nn->gSkip[1], nn->gbuf[3].p, B, H / 2, W / 2, 2 * C);
-    block_bwd(nn, B, 2, 3, nn->gSkip[1], nn->gbuf[2].p, nn->gbuf[3].p);   // d(pool1) at H/2
-    k_pool2_bwd_add<<<grid_for((long long)B * H * W * C), 256, 0, nn->stream>>>(nn->gSkip[0], nn->gbuf[3].p, B, H, W, C);
-    block_bwd(nn, B, 0, 1, nn->gSkip[0], nn->gbuf[2].p, nullptr);
+    // bottleneck: the gradient of e4 is gLow; encoder blocks leave d(pooled input) in gcat
+    block_bwd(nn, B, 6, 7, nn->gLow, nn->gB, nn->gcat);
+    k_pool2_bwd_add<<<grid_for((long long)B * (H / 4) * (W / 4) * 4 * C / 8), 256, 0, nn->stream>>>(
+        nn->gSkip[2], nn->gcat, B, H / 4, W / 4, 4 * C);
+    block_bwd(nn, B, 4, 5, nn->gSkip[2], nn->gB, nn->gcat);
+    k_pool2_bwd_add<<<grid_for((long long)B * (H / 2) * (W / 2) * 2 * C / 8), 256, 0, nn->stream>>>(
+        nn->gSkip[1], nn->gcat, B, H / 2, W / 2, 2 * C);
+    block_bwd(nn, B, 2, 3, nn->gSkip[1], nn->gB, nn->gcat);
+    k_pool2_bwd_add<<<grid_for((long long)B * H * W * C / 8), 256, 0, nn->stream>>>(nn->gSkip[0], nn->gcat, B, H, W, C);
+    block_bwd(nn, B, 0, 1, nn->gSkip[0], nn->gB, nullptr);
     ck(cudaGetLastError(), "backward");
     double loss = 0.0;
     ck(cudaMemcpyAsync(&loss, nn->loss, sizeof(double), cudaMemcpyDeviceToHost, nn->stream), "read loss");
@@ -724,14 +751,6 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         nn->x = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 32);
         nn->xn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
         nn->yn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
-        nn->gy = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
-        const size_t big = B * H * W * 4 * C;   // largest per-level tensor (full resolution, up to 4C channels)
-        nn->gA = (bf16 *)nn->alloc(sizeof(bf16) * big);
-        nn->gB = (bf16 *)nn->alloc(sizeof(bf16) * big);
-        nn->gcat = (bf16 *)nn->alloc(sizeof(bf16) * big);
-        nn->gLow = (bf16 *)nn->alloc(sizeof(bf16) * big);
-        for (int q = 0; q < 4; ++q) nn->gbuf[q] = Tensor{(bf16 *)nn->alloc(sizeof(bf16) * big), 0, 0, 0};
-        for (int q = 0; q < 3; ++q) nn->gSkip[q] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> q) * (W >> q) * (C << q));
         nn->cat = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 3 * C);   // largest decoder input (level 1, 3C)
         nn->wfirst = (bf16 *)nn->alloc(sizeof(bf16) * 32 * C);
         nn->dwfirst = (float *)nn->alloc(sizeof(float) * 32 * C);
@@ -801,7 +820,11 @@ ur_status ur_nn_forward(ur_nn *nn, const float *rf, const float *quad, int batch
         ck(cudaSetDevice(nn->device), "cudaSetDevice");
         if (batch < 1 || batch > nn->max_batch) fail(UR_ERR_INVALID_ARG, "batch out of range");
         if (!rf || !quad || !out_rf || !out_quad) fail(UR_ERR_INVALID_ARG, "inputs and outputs are required");
-        forward(nn, batch, rf, quad, out_rf, out_quad);
+        const size_t n = (size_t)batch * nn->H * nn->W;
+        float *o_rf = staged(nn, 4, out_rf, batch, false), *o_q = staged(nn, 5, out_quad, batch, false);
+        forward(nn, batch, staged(nn, 0, rf, batch, true), staged(nn, 1, quad, batch, true), o_rf, o_q);
+        if (o_rf != out_rf) ck(cudaMemcpyAsync(out_rf, o_rf, sizeof(float) * n, cudaMemcpyDeviceToHost, nn->stream), "copy out");
+        if (o_q != out_quad) ck(cudaMemcpyAsync(out_quad, o_q, sizeof(float) * n, cudaMemcpyDeviceToHost, nn->stream), "copy out");
         sync_check(nn, "forward");
     });
 }
@@ -813,7 +836,8 @@ ur_status ur_nn_train_step(ur_nn *nn, const float *rf, const float *quad, const 
         if (batch < 1 || batch > nn->max_batch) fail(UR_ERR_INVALID_ARG, "batch out of range");
         if (!rf || !quad || !t_rf || !t_quad) fail(UR_ERR_INVALID_ARG, "inputs and targets are required");
         if (!(lr >= 0.f)) fail(UR_ERR_INVALID_ARG, "lr must be >= 0");
-        const double l = train(nn, batch, rf, quad, t_rf, t_quad);
+        const double l = train(nn, batch, staged(nn, 0, rf, batch, true), staged(nn, 1, quad, batch, true),
+                               staged(nn, 2, t_rf, batch, true), staged(nn, 3, t_quad, batch, true));
         if (loss) *loss = (float)l;
         if (grad_out) ck(cudaMemcpy(grad_out, nn->grads, sizeof(float) * nn->n_params, cudaMemcpyDefault), "grad out");
         if (lr > 0.f) {

@@ -130,3 +130,44 @@ def evaluate(sim, net, scene_fn, scene_seeds, n_in, n_ref, max_bounces=8, ray_se
                      "err_equal_time": rel_err(er, eq, rr, rq), "n_equal_time": n_eq,
                      "t_trace_s": t_trace, "t_net_s": t_nn, "t_equal_time_s": t_eq})
     return rows
+
+
+def main(argv=None):
+    """Command line: trace pairs from jittered layered phantoms, train, evaluate on held-out scenes.
+
+    Run from the repository root (the seeded phantom generators live in phantoms/ there)."""
+    import argparse
+    import json
+
+    import phantoms
+
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--pairs", type=int, default=256, help="training scenes (seeds 1..pairs)")
+    ap.add_argument("--n-in", type=float, default=1e6, help="rays of the network input")
+    ap.add_argument("--n-tgt", type=float, default=3e8, help="rays of the training target")
+    ap.add_argument("--n-ref", type=float, default=1e9, help="rays of the evaluation reference")
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval", type=int, default=8, help="held-out scenes (seeds 2001..)")
+    ap.add_argument("--out", default=None, help="JSON report path")
+    a = ap.parse_args(argv)
+    sim = Simulator(0)
+    xr, xq, tr, tq, gen_s = make_pairs(sim, phantoms.batched_variant, range(1, a.pairs + 1), a.n_in, a.n_tgt)
+    net = Denoiser(0, max_batch=a.batch, n_el=int(xr.shape[1]), n_s=int(xr.shape[2]), width=32, seed=1)
+    net.set_scale(channel_scale(tr, tq))
+    t0 = time.perf_counter()
+    hist = train(net, xr, xq, tr, tq, a.epochs, a.batch, a.lr, log=lambda m: print(m, flush=True))
+    train_s = time.perf_counter() - t0
+    rows = evaluate(sim, net, phantoms.batched_variant, range(2001, 2001 + a.eval), a.n_in, a.n_ref)
+    keys = ("err_input", "err_denoised", "err_equal_time")
+    rep = {"args": vars(a), "generation_s": gen_s, "training_s": train_s, "loss": hist, "eval": rows,
+           "mean": {k: float(np.mean([r[k] for r in rows])) for k in keys}}
+    print(json.dumps(rep["mean"]))
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(rep, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
