@@ -89,6 +89,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -170,8 +178,26 @@ struct Args {
     const float *bias;
     const bf16 *mask;
     bf16 *y;
+    float *dbias;   // nullable: += column sums of the output over all pixels
     int *err;
 };
+
+// Sum over the 32 lanes of each of the 32 values v[j]; lane l ends with the total of
+// v[l] (recursive halving: 31 shuffles).
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int j = 0; j < w; ++j) {
+            // keep the half of the values whose index bit w matches this lane's bit w
+            const float send = upper ? v[j] : v[j + w];
+            const float keep = upper ? v[j + w] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -283,6 +309,10 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         __syncwarp();
     } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
         const int q = warp & 3;
+        float dsum[BN / 32];   // lane l: running column sum of channel c + l of this CTA's N tile
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) dsum[c] = 0.f;
+        int dsum_co0 = -1;
         int i = 0;
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
             const int b = i & 1;
@@ -294,17 +324,26 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             tc_fence_after();
             int n, y, x0, co0;
             decode(t, n, y, x0, co0);
+            if (a.dbias && co0 != dsum_co0) {   // N tile changed: flush the running column sums
+                if (dsum_co0 >= 0)
+#pragma unroll
+                    for (int c = 0; c < BN / 32; ++c) atomicAdd(a.dbias + dsum_co0 + 32 * c + lane, dsum[c]);
+#pragma unroll
+                for (int c = 0; c < BN / 32; ++c) dsum[c] = 0.f;
+                dsum_co0 = co0;
+            }
             const int x = x0 + q * 32 + lane;
             const size_t pix = ((size_t)n * a.H + y) * a.W + x;
-#pragma unroll 1
+#pragma unroll
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
-                if (x < a.W) {
-                    const int co = co0 + c;
-                    float v[32];
+                const bool in = x < a.W;
+                const int co = co0 + c;
+                float v[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 32; ++j) v[j] = in ? __uint_as_float(r[j]) : 0.f;
+                if (in) {
                     if (a.bias) {
                         const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + co);
 #pragma unroll
@@ -349,11 +388,269 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                         dst[g] = o;
                     }
                 }
+                if (a.dbias) dsum[c / 32] += warp_transpose_sum(v, lane);   // column sums over the warp's pixels
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * b);   // accumulator b may be overwritten
         }
+        if (a.dbias && dsum_co0 >= 0)
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) atomicAdd(a.dbias + dsum_co0 + 32 * c + lane, dsum[c]);
+    }
+    if (!ok) atomicExch(a.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_free(tmem, K::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------ kx-fused convolution
+//
+// For C_out = BN in {32, 64}: the three kx taps of one kernel row ky are consecutive rows of
+// the weight view [9 C_out][C_in], so one MMA with N = 3 BN computes, for the 128 pixels
+// x0 - 1 .. x0 + 126 of input row y + ky - 1, the three partial products P_kx[r] side by
+// side in TMEM.  Output pixel x0 + j takes P_0[j] + P_1[j + 1] + P_2[j + 2] (summed over
+// ky and channel chunks by the MMAs), so a tile yields 126 outputs; the epilogue adds the
+// shifted rows with warp shuffles and, across TMEM lane quadrants, through shared memory.
+// The input is read once per kernel row instead of once per tap.
+constexpr int kKxOut = kBM - 2;   // valid outputs per tile
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <int BN, int BK>
+struct KxCfg {
+    static constexpr int ROW = BK * 2;
+    static constexpr int NB = 3 * BN;                      // MMA N: three taps
+    static constexpr int A_BYTES = kBM * ROW;
+    static constexpr int B_BYTES = NB * ROW;
+    static constexpr int A_PAD = (A_BYTES + 1023) / 1024 * 1024;
+    static constexpr int B_PAD = (B_BYTES + 1023) / 1024 * 1024;
+    static constexpr int BUDGET = BN == 64 ? 200 * 1024 : 100 * 1024;
+    static constexpr int S_RAW = BUDGET / (A_PAD + B_PAD);
+    static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 8 ? 8 : S_RAW);
+    static constexpr int ACC_COLS = NB <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;
+    static constexpr int N_BARS = 2 * S + 4;
+    static constexpr int XCH = 2 * 4 * 2 * 2 * 32 * 4;     // 2 x [quadrant][lane 0/1][P1/P2][32 columns] floats
+    static constexpr int SMEM = S * (A_PAD + B_PAD) + 1024 + 8 * N_BARS + 16 + XCH;
+};
+
+template <int NB>
+__host__ __device__ constexpr uint32_t idesc_bf16_n() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <int BN, int BK>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    k_conv_kx(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, const Args a) {
+    using K = KxCfg<BN, BK>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = s_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *sm = smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + K::S * K::A_PAD;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + K::S * (K::A_PAD + K::B_PAD));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + K::N_BARS);
+    float *xch = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tslot) + 16);
+    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S);
+    const uint32_t accf0 = s_addr(bars + 2 * K::S), acce0 = s_addr(bars + 2 * K::S + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kc = a.C / BK, nk = 3 * kc;   // stages per tile: kernel rows x channel chunks
+    const uint64_t deadline = now_ns() + kWaitNs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < K::S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(s_addr(tslot), K::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
+    bool ok = true;
+
+    auto decode = [&](int t, int &n, int &y, int &x0) {
+        const int xb = t % a.nxb;
+        const int m = t / a.nxb;
+        y = m % a.H;
+        n = m / a.H;
+        x0 = xb * kKxOut;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            int it = 0;
+            for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
+                int n, y, x0;
+                decode(t, n, y, x0);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % K::S;
+                    if (!mbar_wait(empty0 + 8 * s, ((uint32_t)(it / K::S) & 1u) ^ 1u, deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    const int ky = kt / kc, c0 = (kt - ky * kc) * BK;
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + K::B_BYTES));
+                    tma_load_4d(sA + s * K::A_PAD, &tmx, c0, x0 - 1, y + ky - 1, n, full0 + 8 * s);
+                    tma_load_2d(sB + s * K::B_PAD, &tmw, c0, 3 * ky * BN, full0 + 8 * s);
+                }
+            }
+            if (!ok)
+                for (int j = it > K::S ? it - K::S : 0; j < it; ++j)
+                    mbar_wait(full0 + 8 * (j % K::S), (uint32_t)(j / K::S) & 1u, deadline + kWaitNs / 20);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16_n<K::NB>();
+            int it = 0, i = 0;
+            for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (!mbar_wait(acce0 + 8 * b, ((uint32_t)(i >> 1) & 1u) ^ 1u, deadline)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * K::ACC_COLS);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % K::S;
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(it / K::S) & 1u, deadline)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = sA + s * K::A_PAD, b0 = sB + s * K::B_PAD;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(d, sdesc(a0 + 32 * k, K::ROW), sdesc(b0 + 32 * k, K::ROW), idesc, (kt | k) != 0);
+                    mma_commit(empty0 + 8 * s);
+                }
+                mma_commit(accf0 + 8 * b);
+            }
+        }
+        __syncwarp();
+    } else {   // epilogue warps; every warp runs the same tiles and barriers (no early exit)
+        const int q = warp & 3, r = q * 32 + lane;
+        float dsum[BN / 32];
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) dsum[c] = 0.f;
+        int i = 0;
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ready = mbar_wait(accf0 + 8 * b, (uint32_t)(i >> 1) & 1u, deadline);
+            if (__all_sync(0xffffffffu, ready) == 0) ok = false;
+            tc_fence_after();
+            int n, y, x0;
+            decode(t, n, y, x0);
+            const int o = x0 + r;
+            const bool in = r < kKxOut && o < a.W;
+            const size_t pix = ((size_t)n * a.H + y) * a.W + o;
+            const uint32_t tb = tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+            for (int c = 0; c < BN; c += 32) {
+                // v[j] = P_1[r + 1] + P_2[r + 2] + P_0[r]; rows beyond this quadrant come from shared memory
+                float *xb = xch + ((i * (BN / 32) + c / 32) & 1) * (4 * 2 * 2 * 32);   // double-buffered
+                float v[32];
+                {
+                    uint32_t p[32];
+                    tmem_ld32(tb + (uint32_t)(BN + c), p);
+                    if (lane < 2)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) xb[((q * 2 + lane) * 2 + 0) * 32 + j] = __uint_as_float(p[j]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float n1 = __shfl_down_sync(0xffffffffu, __uint_as_float(p[j]), 1);
+                        v[j] = lane < 31 ? n1 : 0.f;
+                    }
+                    tmem_ld32(tb + (uint32_t)(2 * BN + c), p);
+                    if (lane < 2)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) xb[((q * 2 + lane) * 2 + 1) * 32 + j] = __uint_as_float(p[j]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float n2 = __shfl_down_sync(0xffffffffu, __uint_as_float(p[j]), 2);
+                        v[j] += lane < 30 ? n2 : 0.f;
+                    }
+                    tmem_ld32(tb + (uint32_t)c, p);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] += __uint_as_float(p[j]);
+                }
+                epi_barrier();   // the neighbouring quadrant's first two rows are in shared memory
+                if (q < 3 && lane >= 30) {
+                    const float *n1 = xb + (((q + 1) * 2 + 0) * 2 + 0) * 32;
+                    const float *n2 = xb + (((q + 1) * 2 + (lane - 30)) * 2 + 1) * 32;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] += (lane == 31 ? n1[j] : 0.f) + n2[j];
+                }
+                if (!in)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                if (in) {
+                    const int co = c;
+                    if (a.bias) {
+                        const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + co);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 bb = b4[j];
+                            v[4 * j] += bb.x;
+                            v[4 * j + 1] += bb.y;
+                            v[4 * j + 2] += bb.z;
+                            v[4 * j + 3] += bb.w;
+                        }
+                    }
+                    if (a.relu) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
+                    }
+                    if (a.mask) {
+                        const uint4 *m4 = reinterpret_cast<const uint4 *>(a.mask + pix * a.Cout + co);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            const uint4 mv = m4[g];
+                            const __nv_bfloat162 *mb = reinterpret_cast<const __nv_bfloat162 *>(&mv);
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const float2 f = __bfloat1622float2(mb[h]);
+                                if (!(f.x > 0.f)) v[8 * g + 2 * h] = 0.f;
+                                if (!(f.y > 0.f)) v[8 * g + 2 * h + 1] = 0.f;
+                            }
+                        }
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + co);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint4 o4;
+                        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * g], v[8 * g + 1]);
+                        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * g + 2], v[8 * g + 3]);
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * g + 4], v[8 * g + 5]);
+                        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * g + 6], v[8 * g + 7]);
+                        o4.x = *reinterpret_cast<uint32_t *>(&h0);
+                        o4.y = *reinterpret_cast<uint32_t *>(&h1);
+                        o4.z = *reinterpret_cast<uint32_t *>(&h2);
+                        o4.w = *reinterpret_cast<uint32_t *>(&h3);
+                        dst[g] = o4;
+                    }
+                }
+                if (a.dbias) dsum[c / 32] += warp_transpose_sum(v, lane);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        }
+        if (a.dbias)
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) atomicAdd(a.dbias + 32 * c + lane, dsum[c]);
     }
     if (!ok) atomicExch(a.err, 1);
     tc_fence_before();
@@ -534,6 +831,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
+template <typename KernelT>
+cudaError_t ctas_per_sm(KernelT kernel, int smem, int tmem_cols, int *occ);
+
 // Persistent grid: as many CTAs as fit on the SMs at once (shared memory and TMEM), at most one per tile.
 template <int BN, int BK>
 cudaError_t launch(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_sm, cudaStream_t stream) {
@@ -543,19 +843,41 @@ cudaError_t launch(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, 
         e = cudaFuncSetAttribute(k_conv_tc<BN, BK>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    // co-resident CTAs per SM from shared memory (with the per-block reserve), registers, warps and TMEM
+    int occ = 1;
+    if ((e = ctas_per_sm(k_conv_tc<BN, BK>, K::SMEM, K::TMEM_COLS, &occ)) != cudaSuccess) return e;
+    const int grid = (int)std::min<long long>(a.n_tiles, (long long)occ * std::max(1, n_sm));
+    k_conv_tc<BN, BK><<<grid, kConvThreads, K::SMEM, stream>>>(mx, mw, a);
+    return cudaGetLastError();
+}
+
+// co-resident CTAs per SM from shared memory (with the per-block reserve), registers, warps and TMEM
+template <typename KernelT>
+cudaError_t ctas_per_sm(KernelT kernel, int smem, int tmem_cols, int *occ) {
     int dev = 0, smem_sm = 0, reserve = 0;
     cudaFuncAttributes fa{};
+    cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa, k_conv_tc<BN, BK>)) != cudaSuccess)
+        (e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess)
         return e;
     const int regs = ((std::max(fa.numRegs, 1) + 7) / 8) * 8 * kConvThreads;
-    int occ = std::min({smem_sm / (K::SMEM + reserve), 65536 / regs, 64 / (kConvThreads / 32), 512 / K::TMEM_COLS});
-    occ = std::max(1, occ);
+    *occ = std::max(1, std::min({smem_sm / (smem + reserve), 65536 / regs, 64 / (kConvThreads / 32), 512 / tmem_cols}));
+    return cudaSuccess;
+}
+
+template <int BN, int BK>
+cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_sm, cudaStream_t stream) {
+    using K = KxCfg<BN, BK>;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    int occ = 1;
+    if (e == cudaSuccess) e = ctas_per_sm(k_conv_kx<BN, BK>, K::SMEM, K::TMEM_COLS, &occ);
+    if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long long>(a.n_tiles, (long long)occ * std::max(1, n_sm));
-    k_conv_tc<BN, BK><<<grid, kConvThreads, K::SMEM, stream>>>(mx, mw, a);
+    k_conv_kx<BN, BK><<<grid, kConvThreads, K::SMEM, stream>>>(mx, mw, a);
     return cudaGetLastError();
 }
 
@@ -624,13 +946,36 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
             return cudaErrorInvalidValue;
         }
     }
+    if (p.taps == 9 && (p.Cout == 32 || p.Cout == 64)) {   // kx taps fused into one N = 3 C_out MMA
+        alignas(64) CUtensorMap mw2;
+        const cuuint64_t dims[2] = {(cuuint64_t)p.C, 9ull * p.Cout};
+        const cuuint64_t strides[1] = {(cuuint64_t)p.C * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(3 * p.Cout)};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&mw2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p.w), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            if (why) *why = "tensor map of the stacked weights rejected";
+            return cudaErrorInvalidValue;
+        }
+        const int nxk = (p.W + kKxOut - 1) / kKxOut;
+        const long long nt = (long long)p.N * p.H * nxk;
+        if (nt > 0x7fffffffll) {
+            if (why) *why = "conv3x3_tc: too many tiles";
+            return cudaErrorInvalidValue;
+        }
+        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, p.bias, p.mask, p.y, p.dbias, d_err};
+        if (p.Cout == 32) return BK == 64 ? launch_kx<32, 64>(mx, mw2, a, n_sm, stream) : launch_kx<32, 32>(mx, mw2, a, n_sm, stream);
+        return BK == 64 ? launch_kx<64, 64>(mx, mw2, a, n_sm, stream) : launch_kx<64, 32>(mx, mw2, a, n_sm, stream);
+    }
     const int nxb = (p.W + kBM - 1) / kBM;
     const long long n_tiles = (long long)p.N * p.H * nxb * (p.Cout / BN);
     if (n_tiles > 0x7fffffffll) {
         if (why) *why = "conv3x3_tc: too many tiles";
         return cudaErrorInvalidValue;
     }
-    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, p.bias, p.mask, p.y, d_err};
+    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, p.bias, p.mask, p.y, p.dbias,
+           d_err};
     return BK == 64 ? launch_bn<64>(BN, mx, mw, a, n_sm, stream) : launch_bn<32>(BN, mx, mw, a, n_sm, stream);
 }
 

@@ -19,6 +19,7 @@ struct ConvTC {
     const __nv_bfloat16 *mask;   // [N][H][W][Cout] or null: outputs where mask <= 0 become 0
     __nv_bfloat16 *y;            // output NHWC [N][H][W][Cout]
     int relu;                    // max(0, .) after the bias
+    float *dbias = nullptr;      // [Cout] or null: += sum over pixels of the (masked) output, FP32
 };
 
 // Enqueues the convolution on `stream`.  `d_err` (device int) receives a

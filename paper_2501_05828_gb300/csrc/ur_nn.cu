@@ -152,21 +152,6 @@ __global__ void k_pool2(const bf16 *x, bf16 *y, int B, int H, int W, int C) {
     }
 }
 
-// d[i] = d[i] * (act[i] > 0), 8 channels per thread (n8 granules).
-__global__ void k_relu_mask(bf16 *d, const bf16 *act, long long n8) {
-    uint4 *dg = reinterpret_cast<uint4 *>(d);
-    const uint4 *ag = reinterpret_cast<const uint4 *>(act);
-    GRID_STRIDE(i, n8) {
-        float a[8], v[8];
-        unpack8(ag[i], a);
-        unpack8(dg[i], v);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (!(a[j] > 0.f)) v[j] = 0.f;
-        dg[i] = pack8(v);
-    }
-}
-
 // Split the gradient of a concatenated decoder input [B][H][W][C1 + C2]: the
 // first C1 channels came from the nearest-upsampled half-resolution tensor (sum
 // over each 2x2 block), the rest from the skip tensor (copied).
@@ -234,18 +219,26 @@ __global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
     }
 }
 
-// db[c] += sum over pixels of d[p][c].  Thread t owns channels 8 (t % G) .. +8
-// (G = C / 8 divides the 256-thread block) for every (256 / G)-th pixel.
-__global__ void __launch_bounds__(256) k_bias_grad(const bf16 *d, long long P, int C, float *db) {
+// d[p][c] *= (act[p][c] > 0) in place and db[c] += sum over pixels of the masked d.  Thread t
+// owns channels 8 (t % G) .. +8 (G = C / 8 divides the 256-thread block) for every
+// (256 / G)-th pixel.
+__global__ void __launch_bounds__(256) k_mask_bias(bf16 *d, const bf16 *act, long long P, int C, float *db) {
     __shared__ float s[256][9];
     const int G = C / 8, g = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const uint4 *dg = reinterpret_cast<const uint4 *>(d);
+    uint4 *dg = reinterpret_cast<uint4 *>(d);
+    const uint4 *ag = reinterpret_cast<const uint4 *>(act);
     for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
-        float v[8];
-        unpack8(dg[(size_t)p * G + g], v);
+        const size_t i = (size_t)p * G + g;
+        float v[8], m[8];
+        unpack8(dg[i], v);
+        unpack8(ag[i], m);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] += v[j];
+        for (int j = 0; j < 8; ++j) {
+            if (!(m[j] > 0.f)) v[j] = 0.f;
+            acc[j] += v[j];
+        }
+        dg[i] = pack8(v);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) s[threadIdx.x][j] = acc[j];
@@ -404,7 +397,7 @@ struct ur_nn {
     // gA gradient at d1b's output (1), gB block scratch (1), gcat input gradient of a block (3),
     // gLow gradient of the half-resolution decoder input (1/2), gSkip skip-tensor gradients (1, 1/2, 1/4)
     bf16 *gcat = nullptr, *gA = nullptr, *gB = nullptr, *gSkip[3] = {nullptr, nullptr, nullptr}, *gLow = nullptr;
-    bf16 *cat = nullptr;     // decoder input (upsampled lower level ++ skip)
+    bf16 *cat[3] = {nullptr, nullptr, nullptr};   // decoder inputs (upsampled lower level ++ skip) of d3a, d2a, d1a
     bf16 *wfirst = nullptr;  // first convolution as one tap over the 32 neighbourhood channels [C][32]
     float *dwfirst = nullptr;
     double *loss = nullptr;
@@ -442,8 +435,8 @@ ur_status nn_guard(ur_nn *nn, F &&f) {
 }
 
 void conv_fwd(ur_nn *nn, const bf16 *x, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
-              const bf16 *mask, bf16 *y, bool relu, int taps = 9) {
-    urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0};
+              const bf16 *mask, bf16 *y, bool relu, int taps = 9, float *dbias = nullptr) {
+    urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0, dbias};
     std::string why;
     const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
     if (e != cudaSuccess) {
@@ -498,10 +491,11 @@ void conv_wgrad(ur_nn *nn, const bf16 *x, const bf16 *dy, int B, int H, int W, i
     }
 }
 
-void bias_grad(ur_nn *nn, const bf16 *d, long long P, int C, float *db) {
+// d *= (act > 0) in place and db += sum over pixels of the masked d.
+void mask_bias(ur_nn *nn, bf16 *d, const bf16 *act, long long P, int C, float *db) {
     const int lanes = 256 / (C / 8);
-    k_bias_grad<<<(int)std::min<long long>(1024, (P + lanes - 1) / lanes), 256, 0, nn->stream>>>(d, P, C, db);
-    ck(cudaGetLastError(), "bias gradient kernel");
+    k_mask_bias<<<(int)std::min<long long>(2048, (P + lanes - 1) / lanes), 256, 0, nn->stream>>>(d, act, P, C, db);
+    ck(cudaGetLastError(), "mask/bias kernel");
 }
 
 // Inputs of every conv of the network at batch B.
@@ -531,14 +525,18 @@ Layer layer_in(ur_nn *nn, int l) {
     }
 }
 
-// Plain NHWC input of conv l; a decoder input (upsample ++ skip) is materialised in nn->cat.
-const bf16 *conv_input(ur_nn *nn, int B, int l) {
+// Plain NHWC input of conv l; a decoder input (upsample ++ skip) lives in nn->cat[(l - 8) / 2],
+// built by the forward pass (build = true) and reused by the backward pass.
+const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
     const Layer L = layer_in(nn, l);
     if (!L.in.x2) return L.in.x1;
-    k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(L.in.x1, L.in.c1, L.in.x2,
-                                                                                      L.in.c2, B, L.H, L.W, nn->cat);
-    ck(cudaGetLastError(), "upcat kernel");
-    return nn->cat;
+    bf16 *cat = nn->cat[(l - 8) / 2];
+    if (build) {
+        k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(
+            L.in.x1, L.in.c1, L.in.x2, L.in.c2, B, L.H, L.W, cat);
+        ck(cudaGetLastError(), "upcat kernel");
+    }
+    return cat;
 }
 
 void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad) {
@@ -549,7 +547,7 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
     ck(cudaGetLastError(), "pack kernel");
     for (int l = 0; l < kNumConv; ++l) {
         const Layer L = layer_in(nn, l);
-        const bf16 *in = conv_input(nn, B, l);
+        const bf16 *in = conv_input(nn, B, l, true);
         if (l == 0)   // neighbourhood already in the 32 input channels: one tap
             conv_fwd(nn, in, B, L.H, L.W, 32, nn->cout[0], nn->wfirst, nn->params + nn->boff[0], nullptr, nn->act[0].p,
                      true, 1);
@@ -573,24 +571,22 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
 // leaves the gradient of la's input in `din` (full concatenated channels) if din.
 void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din) {
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
-    const long long nb = (long long)B * Lb.H * Lb.W * nn->cout[lb] / 8;
-    k_relu_mask<<<grid_for(nb), 256, 0, nn->stream>>>(d_out, nn->act[lb].p, nb);
+    mask_bias(nn, d_out, nn->act[lb].p, (long long)B * Lb.H * Lb.W, nn->cout[lb], nn->grads + nn->boff[lb]);
     conv_wgrad(nn, nn->act[la].p, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
-    bias_grad(nn, d_out, (long long)B * Lb.H * Lb.W, nn->cout[lb], nn->grads + nn->boff[lb]);
     k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
                                                                                   nn->cout[lb], nn->cin[lb]);
-    // gradient at la's output, masked by la's ReLU in the epilogue
-    conv_fwd(nn, d_out, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p, scratch, false);
+    // gradient at la's output, masked by la's ReLU in the epilogue, which also sums la's bias gradient
+    conv_fwd(nn, d_out, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p, scratch, false, 9,
+             nn->grads + nn->boff[la]);
     if (la == 0) {   // first layer: single-tap gradient over the neighbourhood channels, then back to [9][C][32]
         ck(cudaMemsetAsync(nn->dwfirst, 0, sizeof(float) * 32 * nn->width, nn->stream), "memset");
         conv_wgrad(nn, nn->x, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
         k_unpack_first_grad<<<grid_for(18ll * nn->width), 256, 0, nn->stream>>>(nn->dwfirst, nn->width,
                                                                                nn->grads + nn->woff[0]);
     } else {
-        conv_wgrad(nn, conv_input(nn, B, la), scratch, B, La.H, La.W, nn->cin[la], nn->cout[la],
+        conv_wgrad(nn, conv_input(nn, B, la, false), scratch, B, La.H, La.W, nn->cin[la], nn->cout[la],
                    nn->grads + nn->woff[la]);
     }
-    bias_grad(nn, scratch, (long long)B * La.H * La.W, nn->cout[la], nn->grads + nn->boff[la]);
     if (din) {
         k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
                                                                                       nn->cout[la], nn->cin[la]);
@@ -751,7 +747,8 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         nn->x = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 32);
         nn->xn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
         nn->yn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
-        nn->cat = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 3 * C);   // largest decoder input (level 1, 3C)
+        for (int q = 0; q < 3; ++q)   // d3a: [H/4][W/4][12C], d2a: [H/2][W/2][6C], d1a: [H][W][3C]
+            nn->cat[q] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> (2 - q)) * (W >> (2 - q)) * (12 * C >> q));
         nn->wfirst = (bf16 *)nn->alloc(sizeof(bf16) * 32 * C);
         nn->dwfirst = (float *)nn->alloc(sizeof(float) * 32 * C);
         nn->loss = (double *)nn->alloc(sizeof(double));
