@@ -49,7 +49,7 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), per primary ray, valid only while the tracer sources
 # hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "9820680b5a9320ed", "bytes_per_ray": 10.10, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+TRACE_TRAFFIC = {"src_sha": "dd7c92c0da1b3e20", "bytes_per_ray": 10.07, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
 
 
 def tracer_sha():

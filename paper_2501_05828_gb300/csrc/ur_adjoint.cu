@@ -417,9 +417,18 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
         }
         const float3 dr = unit3(V.d + (2.f * ci) * n);
         const Medium &M2 = S.med[m2];
-        float r, ct, rs, cts;
-        const bool tir_s = !fresnel(ci, S.cs[V.med], S.Zs[V.med], S.cs[m2], S.Zs[m2], rs, cts);
-        if (tir_s || !fresnel(ci, M.c, M.Z, M2.c, M2.Z, r, ct)) {
+        float r, ct, Rs;
+        bool tir;
+        if (!S.split_sampling) {
+            tir = !fresnel(ci, M.c, M.Z, M2.c, M2.Z, r, ct);
+            Rs = r * r;
+        } else {   // frozen sampling media decide the branch and its probability
+            float rs, cts;
+            tir = !fresnel(ci, S.cs[V.med], S.Zs[V.med], S.cs[m2], S.Zs[m2], rs, cts) ||
+                  !fresnel(ci, M.c, M.Z, M2.c, M2.Z, r, ct);
+            Rs = rs * rs;
+        }
+        if (tir) {
 #pragma unroll
             for (int m = 0; m < kAM; ++m) T.dD[m] = T.dD[m] + (2.f * dci[m]) * n + (2.f * ci) * dn[m];
             V.d = dr;
@@ -434,7 +443,6 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
                 drc[m] = D.r_ct * dct[m] + D.r_ci * dci[m];
             }
             const uint4 y = philox(make_uint4(i, IT.stream, 1u | ((uint32_t)V.b << 8), 0u), P.key);
-            const float Rs = rs * rs;
             // d log(branch factor) / dr: 1/r on reflection, -r/(1 - r^2) on transmission
             const bool refl = u24(y.x) < Rs;
             const float coef = refl ? 1.f / r : -r / (1.f - r * r);

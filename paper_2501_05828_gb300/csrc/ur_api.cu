@@ -383,6 +383,9 @@ void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
         S.cs[m] = sd.sampling[m].c;
         S.Zs[m] = sd.sampling[m].Z;
     }
+    S.split_sampling = 0;
+    for (int m = 0; m < S.n_med; ++m)
+        if (S.cs[m] != S.med[m].c || S.Zs[m] != S.med[m].Z) S.split_sampling = 1;
     for (int b = 0; b < S.n_bnd; ++b) {
         S.bnd[b].kind = sd.bnd[b].kind;
         S.bnd[b].med_neg = sd.bnd[b].med_neg;

@@ -132,7 +132,6 @@ struct SceneP {
     int n_med, n_bnd, med_array;
     float z_max;
     Medium med[kMaxMed];
-    float cs[kMaxMed], Zs[kMaxMed];   // c and Z that decide Monte Carlo branches (normally = med)
     Bnd bnd[kMaxBnd];
     // scatterer grid
     int n_scat;
@@ -143,6 +142,9 @@ struct SceneP {
     const uint32_t *cell_start;
     const float *amp;
     const float4 *scat;     // (x, y, z, amplitude) by scatterer index
+    // rarely read (after the fields every segment reads, which keep their offsets):
+    int split_sampling;               // 1 if some (cs, Zs) differs from the media
+    float cs[kMaxMed], Zs[kMaxMed];   // c and Z that decide Monte Carlo branches (normally = med)
 };
 
 // One transmit of one scene: a contiguous range of ray slots (element-major,

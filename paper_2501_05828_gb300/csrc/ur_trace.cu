@@ -191,7 +191,7 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
 // End of a segment: time of flight and attenuation along it, then the array
 // plane (aperture return), the absorbing bottom, the time window, the bounce
 // budget, or a boundary interaction (Eqs. 7-11) and the next segment.
-template <bool DBG>
+template <bool DBG, bool SPLIT>
 __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S[R.scene];
     const Medium &M = S.med[R.med];
@@ -242,15 +242,22 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const float cos_i = -dot3(n, R.d);
     const float3 dr = unit3(R.d + (2.f * cos_i) * n);
     const Medium &M2 = S.med[m2];
-    float r, cos_t, rs, cts;
+    float r, cos_t, Rs;
+    bool tir;
     uint32_t branch;
-    // the sampling media (normally the same) decide the branch and its probability
-    const bool tir_s = !fresnel(cos_i, S.cs[R.med], S.Zs[R.med], S.cs[m2], S.Zs[m2], rs, cts);
-    if (tir_s || !fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t)) {
+    if (!SPLIT) {   // the media decide their own branches
+        tir = !fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t);
+        Rs = r * r;
+    } else {        // frozen sampling media decide the branch and its probability
+        float rs, cts;
+        tir = !fresnel(cos_i, S.cs[R.med], S.Zs[R.med], S.cs[m2], S.Zs[m2], rs, cts) ||
+              !fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t);
+        Rs = rs * rs;
+    }
+    if (tir) {
         branch = 2;
         R.d = dr;
     } else {
-        const float Rs = rs * rs;
         const uint4 y = philox(make_uint4(R.i, R.stream, 1u | ((uint32_t)R.b << 8), 0u), P.key);
         if (u24(y.x) < Rs) {
             branch = 0;
@@ -259,7 +266,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         } else {
             branch = 1;
             const float eta = M2.c / M.c;
-            R.w *= sqrtf(1.f - r * r) / (1.f - Rs);
+            R.w *= SPLIT ? sqrtf(1.f - r * r) / (1.f - Rs) : 1.f / sqrtf(1.f - Rs);
             R.d = unit3(eta * R.d + (eta * cos_i - cos_t) * n);
             R.med = m2;
         }
@@ -310,7 +317,7 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
 // a time with all lanes busy.  Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
-template <bool DBG>
+template <bool DBG, bool SPLIT>
 __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
         const unsigned waiting = __ballot_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay);
         const bool resolve = __popc(waiting) >= P.resolve_batch || __ballot_sync(0xffffffffu, R.state == kInSeg) == 0u;
         for (int guard = 0; resolve && guard < 256; ++guard) {
-            if (R.state == kSegDone) finish_segment<DBG>(P, R, cn);
+            if (R.state == kSegDone) finish_segment<DBG, SPLIT>(P, R, cn);
             unsigned need = __ballot_sync(0xffffffffu, R.state == kNeedRay);
             uint64_t my_slot = ~0ull;
             while (need) {
@@ -475,17 +482,21 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
 int trace_occupancy(int block, bool debug) {
     int n = 0;
     if (debug)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false>, block, 0);
     return n > 0 ? n : 1;
 }
 
+// The variant with frozen sampling media is compiled separately so the usual
+// kernel carries none of its code.
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
+    bool split = false;
+    for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) split = split || P.S[q].split_sampling != 0;
     if (debug)
-        k_trace<true><<<grid, block, 0, s>>>(P);
+        split ? k_trace<true, true><<<grid, block, 0, s>>>(P) : k_trace<true, false><<<grid, block, 0, s>>>(P);
     else
-        k_trace<false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true><<<grid, block, 0, s>>>(P) : k_trace<false, false><<<grid, block, 0, s>>>(P);
 }
 
 }  // namespace ur
