@@ -11,6 +11,8 @@
 // chained into the parameter gradient.
 #include "ur_device.cuh"
 
+#include <algorithm>
+
 namespace ur {
 namespace {
 
@@ -476,7 +478,9 @@ __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A)
 #pragma unroll
     for (int k = 0; k < kNP; ++k) acc[k] = 0.f;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P.n_slots; g += stride) {
+    const uint64_t n_work = A.active ? (uint64_t)*A.n_active : P.n_slots;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_work; k += stride) {
+        const uint64_t g = A.active ? A.active[k] : k;
         int lo = 0, hi = P.n_items - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -500,6 +504,24 @@ __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A)
 }
 
 }  // namespace
+
+__global__ void k_compact_mask(const uint32_t *mask, uint64_t n_words, uint64_t *list, unsigned long long *n) {
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t bits = mask[w];
+        if (!bits) continue;
+        unsigned long long at = atomicAdd(n, (unsigned long long)__popc(bits));
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            list[at++] = w * 32u + (uint64_t)b;
+            bits &= bits - 1u;
+        }
+    }
+}
+
+void launch_compact_mask(const uint32_t *mask, uint64_t n_words, uint64_t *list, unsigned long long *n, cudaStream_t s) {
+    const uint64_t blocks = std::min<uint64_t>(4096, (n_words + 255) / 256 + 1);
+    k_compact_mask<<<(unsigned)blocks, 256, 0, s>>>(mask, n_words, list, n);
+}
 
 void launch_adjoint(const AdjP &A, int sms, cudaStream_t s) {
     int per_sm = 0;

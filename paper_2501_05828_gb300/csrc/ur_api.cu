@@ -55,6 +55,7 @@ constexpr uint32_t kChunk = 4096;   // arrivals per deposit work item
 // One uploaded scene: host copies of media and boundaries, device scatterers and grid.
 struct SceneData {
     bool ok = false;
+    uint64_t version = 0;              // changes with every upload and media change (paths may change)
     std::vector<ur_medium> media;
     std::vector<ur_medium> sampling;   // media deciding Monte Carlo branches (same as media unless overridden)
     std::vector<ur_boundary> bnd;
@@ -101,7 +102,21 @@ struct ur_ctx {
     DevBuf stage_rf, stage_quad, pix, stage_iq, stage_env, stage_db, env_max, img_lists;
 
     // adjoint
-    DevBuf adj_grad, adj_amp, adj_g;
+    DevBuf adj_grad, adj_amp, adj_g, adj_mask, adj_list, adj_nact;
+    // ray mask of the last ur_trace (recorded once an adjoint has been asked for), and what it was traced with
+    bool want_mask = false;
+    uint64_t versions = 0;
+    struct MaskKey {
+        bool valid = false;
+        uint64_t seed = 0, n_rays = 0, scene_version = 0, n_slots = 0;
+        int max_b = 0;
+        float max_path = 0.f;
+        std::vector<float> angles;
+        bool operator==(const MaskKey &o) const {
+            return valid && o.valid && seed == o.seed && n_rays == o.n_rays && scene_version == o.scene_version &&
+                   n_slots == o.n_slots && max_b == o.max_b && max_path == o.max_path && angles == o.angles;
+        }
+    } mask_key;
 
     // batch plan
     bool batch_ok = false;
@@ -365,6 +380,7 @@ void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const 
         ck(cudaMemsetAsync(sd.cell_start.p, 0, 2 * sizeof(uint32_t), c->stream), "memset cells");
     }
     sd.ok = true;
+    sd.version = ++c->versions;
 }
 
 void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
@@ -576,6 +592,19 @@ void read_stats(const unsigned long long *h, ur_stats *st) {
     st->arrivals = h[6];
 }
 
+ur_ctx::MaskKey trace_key(const ur_ctx *c, uint64_t seed, uint64_t n_rays, int max_b, float max_path) {
+    ur_ctx::MaskKey k;
+    k.valid = true;
+    k.seed = seed;
+    k.n_rays = n_rays;
+    k.scene_version = c->scenes[0].version;
+    k.n_slots = c->n_slots;
+    k.max_b = max_b;
+    k.max_path = max_path;
+    k.angles = c->angles;
+    return k;
+}
+
 void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_path, float *rf, float *quad,
               ur_stats *st, ur_debug *dbg) {
     c->set_device();
@@ -597,12 +626,21 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     c->batch_ok = false;
     ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
     P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
+    const bool record_mask = c->want_mask && !dbg_on;
+    const uint64_t n_words = (c->n_slots + 31) / 32;
+    c->mask_key.valid = false;
+    if (record_mask) {   // rays that deposit, for a following ur_trace_adjoint with the same settings
+        c->grow(c->adj_mask, sizeof(uint32_t) * n_words);
+        P.ray_mask = (uint32_t *)c->adj_mask.p;
+        P.mask_only = 0;
+    }
 
     const double want = c->arr_per_ray * (double)n_rays * (double)n_tx * 1.25 + 4096.0;
     uint64_t cap = std::max<uint64_t>(c->arr_cap, (uint64_t)want);
     unsigned long long *h = c->host_scratch;
     for (int attempt = 0;; ++attempt) {
         size_trace_buffers(c, cap, dbg_on);
+        if (record_mask) ck(cudaMemsetAsync(c->adj_mask.p, 0, sizeof(uint32_t) * n_words, c->stream), "memset mask");
         launch_trace_kernel(c, P, dbg_on, (uint2 *)c->arr_dbg.p);
         ck(cudaMemcpyAsync(h, P.arr_count, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream), "read count");
         ck(cudaStreamSynchronize(c->stream), "trace kernel");
@@ -615,6 +653,7 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     }
     const uint64_t n_arr = h[0];
     read_stats(h, st);
+    if (record_mask) c->mask_key = trace_key(c, seed, n_rays, max_b, max_path);
 
     const bool rf_dev = is_device_ptr(rf), q_dev = is_device_ptr(quad);
     float *d_rf = rf, *d_q = quad;
@@ -722,7 +761,7 @@ ur_status ur_destroy(ur_ctx *c) {
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
                      &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
-                     &c->adj_g};
+                     &c->adj_g, &c->adj_mask, &c->adj_list, &c->adj_nact};
     for (DevBuf *b : all) c->release(*b);
     for (int p = 0; p < UR_N_PHASES; ++p) {
         if (c->ev0[p]) cudaEventDestroy(c->ev0[p]);
@@ -762,6 +801,7 @@ ur_status ur_scene_set_media(ur_ctx *c, int slot, const ur_medium *media, int n_
                     fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0, roughness 0");
         sd.media = M;
         sd.sampling = Ms;
+        sd.version = ++c->versions;
     });
 }
 
@@ -980,6 +1020,32 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
         A.fs = Ar.fs;
         A.k_alpha = (float)((double)Ar.f0 * 1e-6 * 100.0 * std::log(10.0) / 20.0);
         c->phase_begin(UR_PHASE_ADJOINT);
+        {   // rays whose paths deposit into the channel data: with the branch decisions held
+            // fixed, no other path has a gradient, so only these are replayed
+            const uint64_t n_words = (c->n_slots + 31) / 32;
+            c->grow(c->adj_list, sizeof(uint64_t) * std::max<uint64_t>(c->n_slots, 1));
+            c->grow(c->adj_nact, sizeof(unsigned long long));
+            ck(cudaMemsetAsync(c->adj_nact.p, 0, sizeof(unsigned long long), c->stream), "memset count");
+            const ur_ctx::MaskKey key = trace_key(c, seed, n_rays, max_b, max_path);
+            if (!(c->mask_key == key)) {   // the last ur_trace ran otherwise: trace the mask here
+                c->grow(c->adj_mask, sizeof(uint32_t) * n_words);
+                ck(cudaMemsetAsync(c->adj_mask.p, 0, sizeof(uint32_t) * n_words, c->stream), "memset mask");
+                ur::TraceP Pm = A.T;
+                Pm.ray_mask = (uint32_t *)c->adj_mask.p;
+                Pm.mask_only = 1;
+                Pm.stats = nullptr;
+                ck(cudaMemsetAsync(Pm.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
+                ur::launch_trace(Pm, false, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, false), c->stream);
+                ck(cudaGetLastError(), "mask trace launch");
+                c->mask_key = key;
+            }
+            c->want_mask = true;   // later ur_trace calls record the mask as they go
+            ur::launch_compact_mask((const uint32_t *)c->adj_mask.p, n_words, (uint64_t *)c->adj_list.p,
+                                    (unsigned long long *)c->adj_nact.p, c->stream);
+            ck(cudaGetLastError(), "compact kernel");
+            A.active = (const uint64_t *)c->adj_list.p;
+            A.n_active = (const unsigned long long *)c->adj_nact.p;
+        }
         ur::launch_adjoint(A, c->sms, c->stream);
         ck(cudaGetLastError(), "adjoint kernel");
         c->phase_end(UR_PHASE_ADJOINT, 1);

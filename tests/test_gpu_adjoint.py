@@ -141,3 +141,27 @@ def test_autograd_backward_equals_adjoint(ur):
     rf2, q2 = ur.trace_differentiable(sim, new, amp.detach(), N, w["seed"], w["max_bounces"], w["max_path"])
     loss2 = ((rf2 - tgt[0]) ** 2).sum() + ((q2 - tgt[1]) ** 2).sum()
     assert float(loss2.detach()) < float(loss.detach())
+
+
+def test_adjoint_replays_only_depositing_rays_consistently(ur):
+    """Only rays that deposit carry a gradient, so the adjoint replays just those: first from a
+    mask it traces itself, then from the mask recorded by a matching ur_trace; a forward trace
+    with other settings must not be reused.  All three gradients agree (up to FP32 summation
+    order), and against the oracle as in the tests above."""
+    w = phantoms.layered(n_rays=200_000)
+    N = w["n_rays"]
+    sim, med0, tgt, cur, (g_rf, g_q) = setup_loss(ur, w, N)
+    n_med, n_scat = len(med0), len(w["scene"]["scatterers"])
+    args = (N, w["seed"], w["max_bounces"], g_rf, g_q, w["max_path"])
+    gm1, ga1 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)            # own mask pass
+    sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])                  # records the mask
+    gm2, ga2 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)            # reuses it
+    sim.trace(N, w["seed"] + 1, w["max_bounces"], w["max_path"])              # other seed: not reusable
+    gm3, ga3 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)
+    for gm, ga in ((gm2, ga2), (gm3, ga3)):
+        assert rel_l2(gm.double().cpu().numpy(), gm1.double().cpu().numpy()) <= 1e-5
+        assert rel_l2(ga.double().cpu().numpy(), ga1.double().cpu().numpy()) <= 1e-5
+    om, oa = oracle.grad(w["scene"], w["array"], w["angles"], N, w["seed"], w["max_bounces"],
+                         g_rf.double().cpu().numpy(), g_q.double().cpu().numpy(), w["max_path"])
+    assert rel_l2(gm2.double().cpu().numpy(), om) <= 2e-3
+    assert rel_l2(ga2.double().cpu().numpy(), oa) <= 2e-3
