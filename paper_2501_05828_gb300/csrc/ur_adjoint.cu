@@ -212,89 +212,12 @@ __device__ void event(const AdjP &A, const SceneP &S, uint32_t item, uint32_t st
     if (A.grad_amp) atomicAdd(&A.grad_amp[j], g_amp * amp_wo);
 }
 
-// Scatterers within r_s of the segment (uniform-grid walk, each found once).
-__device__ void segment_events(const AdjP &A, const SceneP &S, uint32_t item, uint32_t stream, uint32_t i,
-                               const RayVal &V, const Tan &T, float seg, float *acc) {
-    const float3 o = V.o, d = V.d;
-    const float hi_x = S.g_lo.x + (float)S.g_dim.x * S.g_h.x;
-    const float hi_y = S.g_lo.y + (float)S.g_dim.y * S.g_h.y;
-    const float hi_z = S.g_lo.z + (float)S.g_dim.z * S.g_h.z;
-    float t0 = 0.f, t1 = seg;
-    const float ix = 1.f / d.x, iy = 1.f / d.y, iz = 1.f / d.z;
-    if (d.x != 0.f) {
-        const float ta = (S.g_lo.x - o.x) * ix, tb = (hi_x - o.x) * ix;
-        t0 = fmaxf(t0, fminf(ta, tb));
-        t1 = fminf(t1, fmaxf(ta, tb));
-    } else if (o.x < S.g_lo.x || o.x > hi_x) {
-        return;
-    }
-    if (d.y != 0.f) {
-        const float ta = (S.g_lo.y - o.y) * iy, tb = (hi_y - o.y) * iy;
-        t0 = fmaxf(t0, fminf(ta, tb));
-        t1 = fminf(t1, fmaxf(ta, tb));
-    } else if (o.y < S.g_lo.y || o.y > hi_y) {
-        return;
-    }
-    if (d.z != 0.f) {
-        const float ta = (S.g_lo.z - o.z) * iz, tb = (hi_z - o.z) * iz;
-        t0 = fmaxf(t0, fminf(ta, tb));
-        t1 = fminf(t1, fmaxf(ta, tb));
-    } else if (o.z < S.g_lo.z || o.z > hi_z) {
-        return;
-    }
-    if (!(t0 < t1)) return;
-    int cx = min(max((int)floorf((o.x + t0 * d.x - S.g_lo.x) * S.g_inv_h.x), 0), S.g_dim.x - 1);
-    int cy = min(max((int)floorf((o.y + t0 * d.y - S.g_lo.y) * S.g_inv_h.y), 0), S.g_dim.y - 1);
-    int cz = min(max((int)floorf((o.z + t0 * d.z - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
-    const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
-    const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
-    const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
-    const float tdx = sx ? S.g_h.x * fabsf(ix) : INFINITY;
-    const float tdy = sy ? S.g_h.y * fabsf(iy) : INFINITY;
-    const float tdz = sz ? S.g_h.z * fabsf(iz) : INFINITY;
-    float tmx = sx ? (S.g_lo.x + (float)(cx + (sx > 0)) * S.g_h.x - o.x) * ix : INFINITY;
-    float tmy = sy ? (S.g_lo.y + (float)(cy + (sy > 0)) * S.g_h.y - o.y) * iy : INFINITY;
-    float tmz = sz ? (S.g_lo.z + (float)(cz + (sz > 0)) * S.g_h.z - o.z) * iz : INFINITY;
-    float t_enter = -INFINITY;
-    const int guard_max = S.g_dim.x + S.g_dim.y + S.g_dim.z + 3;
-    for (int guard = 0; guard < guard_max; ++guard) {
-        const int axis = (tmx <= tmy && tmx <= tmz) ? 0 : (tmy <= tmz ? 1 : 2);
-        const float t_exit = axis == 0 ? tmx : (axis == 1 ? tmy : tmz);
-        bool last = !(t_exit < t1);
-        if (!last) {
-            const int nc = axis == 0 ? cx + sx : (axis == 1 ? cy + sy : cz + sz);
-            const int dm = axis == 0 ? S.g_dim.x : (axis == 1 ? S.g_dim.y : S.g_dim.z);
-            last = nc < 0 || nc >= dm;
-        }
-        const float t_acc = last ? INFINITY : t_exit;
-        const uint32_t cell = ((uint32_t)cx * (uint32_t)S.g_dim.y + (uint32_t)cy) * (uint32_t)S.g_dim.z + (uint32_t)cz;
-        const uint32_t r0 = S.cell_start[cell], r1 = S.cell_start[cell + 1];
-        for (uint32_t r = r0; r < r1; ++r) {
-            const float4 q = S.refs[r];
-            const float3 v = make_float3(q.x - o.x, q.y - o.y, q.z - o.z);
-            const float tca = dot3(v, d);
-            if (!(tca > 0.f && tca < seg) || tca < t_enter || !(tca < t_acc)) continue;
-            const float3 pe = v - tca * d;
-            if (!(dot3(pe, pe) < S.r2)) continue;
-            event(A, S, item, stream, i, V, T, q, tca, acc);
-        }
-        if (last) break;
-        t_enter = t_exit;
-        if (axis == 0) {
-            cx += sx;
-            tmx += tdx;
-        } else if (axis == 1) {
-            cy += sy;
-            tmy += tdy;
-        } else {
-            cz += sz;
-            tmz += tdz;
-        }
-    }
-}
-
-// Replay of ray i of `item` with tangents.
-__device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i, uint32_t e, float *acc) {
+// Replay of ray i of `item` with tangents up to the arrival recorded by the
+// forward trace: event word ev = b << 24 | j for the connection from scatterer j
+// on the segment after b interactions, 0x80000000 | b << 24 for the return to
+// the aperture at the end of that segment.
+__device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i, uint32_t e, uint32_t ev,
+                       float *acc) {
     const TraceP &P = A.T;
     const SceneP &S = P.S[IT.scene];
     const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
@@ -331,7 +254,13 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
 #pragma unroll
             for (int m = 0; m < kAM; ++m) dseg[m] = -T.dL[m];
         }
-        if (S.n_scat > 0) segment_events(A, S, item, IT.stream, i, V, T, seg, acc);
+        if (!(ev & 0x80000000u) && (uint32_t)V.b == ((ev >> 24) & 0x7fu)) {   // the recorded scatterer event
+            const uint32_t j = ev & 0xffffffu;
+            const float4 sj = S.scat[j];
+            const float3 v = make_float3(sj.x - V.o.x, sj.y - V.o.y, sj.z - V.o.z);
+            event(A, S, item, IT.stream, i, V, T, make_float4(sj.x, sj.y, sj.z, __uint_as_float(j)), dot3(v, V.d), acc);
+            return;
+        }
         // advance along the segment
         const Medium &M = S.med[V.med];
         const float slow = M.slow.hi;
@@ -472,28 +401,22 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
     }
 }
 
+// One thread per recorded arrival (only depositing paths have a gradient).
 __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A) {
     const TraceP &P = A.T;
     float acc[kNP];
 #pragma unroll
     for (int k = 0; k < kNP; ++k) acc[k] = 0.f;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n_work = A.active ? (uint64_t)*A.n_active : P.n_slots;
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_work; k += stride) {
-        const uint64_t g = A.active ? A.active[k] : k;
-        int lo = 0, hi = P.n_items - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.items[mid].slot_begin <= g) lo = mid; else hi = mid - 1;
-        }
-        const ItemP &IT = P.items[lo];
-        const uint64_t local = g - IT.slot_begin;
-        const uint32_t m = (uint32_t)(local % IT.rays_per_el);
-        const uint64_t e = local / IT.rays_per_el;
-        if (e >= (uint64_t)P.n_el) continue;
-        const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-        if (i >= IT.n_rays) continue;
-        replay(A, (uint32_t)lo, IT, i, (uint32_t)e, acc);
+    const uint64_t n = min((uint64_t)*A.n_arr, A.arr_cap);
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const uint32_t row = A.arr[k].x;
+        const uint2 rec = A.rec[k];
+        const uint32_t item = row / (uint32_t)P.n_el;
+        if (item >= (uint32_t)P.n_items) continue;
+        const ItemP &IT = P.items[item];
+        if (rec.x >= IT.n_rays) continue;
+        replay(A, item, IT, rec.x, rec.x % (uint32_t)P.n_el, rec.y, acc);
     }
 #pragma unroll
     for (int k = 0; k < kNP; ++k) {
@@ -504,24 +427,6 @@ __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A)
 }
 
 }  // namespace
-
-__global__ void k_compact_mask(const uint32_t *mask, uint64_t n_words, uint64_t *list, unsigned long long *n) {
-    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t bits = mask[w];
-        if (!bits) continue;
-        unsigned long long at = atomicAdd(n, (unsigned long long)__popc(bits));
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            list[at++] = w * 32u + (uint64_t)b;
-            bits &= bits - 1u;
-        }
-    }
-}
-
-void launch_compact_mask(const uint32_t *mask, uint64_t n_words, uint64_t *list, unsigned long long *n, cudaStream_t s) {
-    const uint64_t blocks = std::min<uint64_t>(4096, (n_words + 255) / 256 + 1);
-    k_compact_mask<<<(unsigned)blocks, 256, 0, s>>>(mask, n_words, list, n);
-}
 
 void launch_adjoint(const AdjP &A, int sms, cudaStream_t s) {
     int per_sm = 0;

@@ -102,9 +102,10 @@ struct ur_ctx {
     DevBuf stage_rf, stage_quad, pix, stage_iq, stage_env, stage_db, env_max, img_lists;
 
     // adjoint
-    DevBuf adj_grad, adj_amp, adj_g, adj_mask, adj_list, adj_nact;
-    // ray mask of the last ur_trace (recorded once an adjoint has been asked for), and what it was traced with
-    bool want_mask = false;
+    DevBuf adj_grad, adj_amp, adj_g;
+    // (ray, event) words of the last ur_trace's arrivals (recorded once an adjoint has been asked
+    // for) and the settings they were traced with
+    bool want_rec = false;
     uint64_t versions = 0;
     struct MaskKey {
         bool valid = false;
@@ -116,7 +117,7 @@ struct ur_ctx {
             return valid && o.valid && seed == o.seed && n_rays == o.n_rays && scene_version == o.scene_version &&
                    n_slots == o.n_slots && max_b == o.max_b && max_path == o.max_path && angles == o.angles;
         }
-    } mask_key;
+    } rec_key;
 
     // batch plan
     bool batch_ok = false;
@@ -534,8 +535,9 @@ void size_trace_buffers(ur_ctx *c, uint64_t cap, bool dbg) {
 }
 
 void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
+    c->rec_key.valid = false;   // the arrival buffers are about to change
     P.arr = (uint4 *)c->arrivals.p;
-    P.arr_dbg = dbg ? arr_dbg : nullptr;
+    P.arr_dbg = (dbg || P.record) ? arr_dbg : nullptr;
     P.arr_cap = c->arr_cap;
     ck(cudaMemsetAsync(P.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
     c->phase_begin(UR_PHASE_TRACE);
@@ -626,21 +628,14 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     c->batch_ok = false;
     ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
     P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
-    const bool record_mask = c->want_mask && !dbg_on;
-    const uint64_t n_words = (c->n_slots + 31) / 32;
-    c->mask_key.valid = false;
-    if (record_mask) {   // rays that deposit, for a following ur_trace_adjoint with the same settings
-        c->grow(c->adj_mask, sizeof(uint32_t) * n_words);
-        P.ray_mask = (uint32_t *)c->adj_mask.p;
-        P.mask_only = 0;
-    }
+    const bool record = c->want_rec && !dbg_on;   // (ray, event) of each arrival, for ur_trace_adjoint
+    P.record = record ? 1 : 0;
 
     const double want = c->arr_per_ray * (double)n_rays * (double)n_tx * 1.25 + 4096.0;
     uint64_t cap = std::max<uint64_t>(c->arr_cap, (uint64_t)want);
     unsigned long long *h = c->host_scratch;
     for (int attempt = 0;; ++attempt) {
-        size_trace_buffers(c, cap, dbg_on);
-        if (record_mask) ck(cudaMemsetAsync(c->adj_mask.p, 0, sizeof(uint32_t) * n_words, c->stream), "memset mask");
+        size_trace_buffers(c, cap, dbg_on || record);
         launch_trace_kernel(c, P, dbg_on, (uint2 *)c->arr_dbg.p);
         ck(cudaMemcpyAsync(h, P.arr_count, 7 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream), "read count");
         ck(cudaStreamSynchronize(c->stream), "trace kernel");
@@ -653,7 +648,7 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     }
     const uint64_t n_arr = h[0];
     read_stats(h, st);
-    if (record_mask) c->mask_key = trace_key(c, seed, n_rays, max_b, max_path);
+    if (record) c->rec_key = trace_key(c, seed, n_rays, max_b, max_path);
 
     const bool rf_dev = is_device_ptr(rf), q_dev = is_device_ptr(quad);
     float *d_rf = rf, *d_q = quad;
@@ -761,7 +756,7 @@ ur_status ur_destroy(ur_ctx *c) {
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
                      &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
-                     &c->adj_g, &c->adj_mask, &c->adj_list, &c->adj_nact};
+                     &c->adj_g};
     for (DevBuf *b : all) c->release(*b);
     for (int p = 0; p < UR_N_PHASES; ++p) {
         if (c->ev0[p]) cudaEventDestroy(c->ev0[p]);
@@ -970,6 +965,27 @@ ur_status ur_beamform(ur_ctx *c, const float *rf, const float *quad, const float
 
 // ------------------------------------------------------------------ adjoint
 
+// A forward trace that keeps (ray, event) of every arrival (queue grown until it fits).
+void record_arrivals(ur_ctx *c, ur::TraceP P, uint64_t n_rays, int n_tx) {
+    P.record = 1;
+    P.path_hash = nullptr;
+    const double want = c->arr_per_ray * (double)n_rays * (double)n_tx * 1.25 + 4096.0;
+    uint64_t cap = std::max<uint64_t>(c->arr_cap, (uint64_t)want);
+    unsigned long long *h = c->host_scratch;
+    for (int attempt = 0;; ++attempt) {
+        size_trace_buffers(c, cap, true);
+        launch_trace_kernel(c, P, false, (uint2 *)c->arr_dbg.p);
+        ck(cudaMemcpyAsync(h, P.arr_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream), "read count");
+        ck(cudaStreamSynchronize(c->stream), "recording trace");
+        c->phase_collect();
+        const uint64_t n_arr = h[0];
+        c->arr_per_ray = std::max(1e-3, (double)n_arr / ((double)n_rays * (double)n_tx));
+        if (n_arr <= c->arr_cap) break;
+        if (attempt == 2) fail(UR_ERR_OVERFLOW, "arrival queue kept overflowing");
+        cap = (uint64_t)((double)n_arr * 1.1) + 4096;
+    }
+}
+
 ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_path, const float *g_rf,
                            const float *g_quad, float *grad_media, float *grad_amp) {
     return guarded(c, [&] {
@@ -1019,33 +1035,17 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
         A.om = (float)(2.0 * kPi * (double)Ar.f0 / (double)Ar.fs);
         A.fs = Ar.fs;
         A.k_alpha = (float)((double)Ar.f0 * 1e-6 * 100.0 * std::log(10.0) / 20.0);
-        c->phase_begin(UR_PHASE_ADJOINT);
-        {   // rays whose paths deposit into the channel data: with the branch decisions held
-            // fixed, no other path has a gradient, so only these are replayed
-            const uint64_t n_words = (c->n_slots + 31) / 32;
-            c->grow(c->adj_list, sizeof(uint64_t) * std::max<uint64_t>(c->n_slots, 1));
-            c->grow(c->adj_nact, sizeof(unsigned long long));
-            ck(cudaMemsetAsync(c->adj_nact.p, 0, sizeof(unsigned long long), c->stream), "memset count");
-            const ur_ctx::MaskKey key = trace_key(c, seed, n_rays, max_b, max_path);
-            if (!(c->mask_key == key)) {   // the last ur_trace ran otherwise: trace the mask here
-                c->grow(c->adj_mask, sizeof(uint32_t) * n_words);
-                ck(cudaMemsetAsync(c->adj_mask.p, 0, sizeof(uint32_t) * n_words, c->stream), "memset mask");
-                ur::TraceP Pm = A.T;
-                Pm.ray_mask = (uint32_t *)c->adj_mask.p;
-                Pm.mask_only = 1;
-                Pm.stats = nullptr;
-                ck(cudaMemsetAsync(Pm.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
-                ur::launch_trace(Pm, false, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, false), c->stream);
-                ck(cudaGetLastError(), "mask trace launch");
-                c->mask_key = key;
-            }
-            c->want_mask = true;   // later ur_trace calls record the mask as they go
-            ur::launch_compact_mask((const uint32_t *)c->adj_mask.p, n_words, (uint64_t *)c->adj_list.p,
-                                    (unsigned long long *)c->adj_nact.p, c->stream);
-            ck(cudaGetLastError(), "compact kernel");
-            A.active = (const uint64_t *)c->adj_list.p;
-            A.n_active = (const unsigned long long *)c->adj_nact.p;
+        // only paths that deposit have a gradient: the arrivals of the matching forward trace name them
+        if (!(c->rec_key == trace_key(c, seed, n_rays, max_b, max_path))) {
+            record_arrivals(c, A.T, n_rays, n_tx);
+            c->rec_key = trace_key(c, seed, n_rays, max_b, max_path);
         }
+        c->want_rec = true;   // later ur_trace calls record as they go
+        A.arr = (const uint4 *)c->arrivals.p;
+        A.rec = (const uint2 *)c->arr_dbg.p;
+        A.n_arr = (const unsigned long long *)c->counters.p;
+        A.arr_cap = c->arr_cap;
+        c->phase_begin(UR_PHASE_ADJOINT);
         ur::launch_adjoint(A, c->sms, c->stream);
         ck(cudaGetLastError(), "adjoint kernel");
         c->phase_end(UR_PHASE_ADJOINT, 1);
@@ -1224,6 +1224,7 @@ ur_status ur_graph_launch(ur_ctx *c) {
         c->set_device();
         if (!c->graph_exec) fail(UR_ERR_STATE, "no graph captured");
         c->no_capture("ur_graph_launch");
+        c->rec_key.valid = false;   // the captured traces overwrite the arrival buffers
         ck(cudaGraphLaunch(c->graph_exec, c->stream), "cudaGraphLaunch");
     });
 }

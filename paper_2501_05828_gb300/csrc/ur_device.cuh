@@ -183,8 +183,7 @@ struct TraceP {
     unsigned long long *next_slot;  // work counter of the persistent tracer (zeroed per launch)
     unsigned long long *path_hash;  // per item and ray, debug only
     unsigned long long *stats;      // 6 counters, nullable
-    uint32_t *ray_mask;             // nullable: bit per slot, set for rays that deposit
-    int mask_only;                  // with ray_mask: 1 = only the mask (no arrivals stored)
+    int record;                     // 1: store (ray, event) of every arrival in arr_dbg (the adjoint's work)
 };
 
 // ---------------------------------------------------------------- geometry shared by tracer and adjoint
@@ -295,11 +294,11 @@ struct AdjP {
     float *grad_amp;            // [n_scat] of scene 0, accumulated (nullable)
     float K, inv_2s2, inv_s2, half_cycles, om;   // pulse: half-width, 1/(2 s^2), 1/s^2 (samples), 2 f0/fs, rad/sample
     float fs, k_alpha;          // sampling frequency; d(Np/m)/d(dB/cm/MHz) at f0
-    const uint64_t *active;     // nullable: the slots to replay (rays that deposit), else every slot
-    const unsigned long long *n_active;
+    const uint4 *arr;           // arrivals of the forward trace (row, t_hi, t_lo, amp)
+    const uint2 *rec;           // their (ray, event) words
+    const unsigned long long *n_arr;
+    uint64_t arr_cap;
 };
-// slots whose bit is set in mask[n_words] -> list (order unspecified), count in *n
-void launch_compact_mask(const uint32_t *mask, uint64_t n_words, uint64_t *list, unsigned long long *n, cudaStream_t s);
 void launch_adjoint(const AdjP &A, int sms, cudaStream_t s);
 
 struct BinP {

@@ -49,17 +49,10 @@ __device__ float connection(const SceneP &S, float3 p, int med, float xe, ff &t_
     return fac;
 }
 
-// Warp-aggregated append to the arrival queue (one atomic per converged group).
-// With MASK the bit of the ray's slot is also set in P.ray_mask (the rays whose
-// paths reach the channel data); with MASK == 1 the arrival itself is not stored.
-template <bool DBG, int MASK>
+// Warp-aggregated append to the arrival queue (one atomic per converged group);
+// with DBG or REC the arrival's (ray, event) words go to arr_dbg as well.
+template <bool DBG, bool REC>
 __device__ __forceinline__ void emit(const TraceP &P, uint32_t row, ff t, float amp, uint32_t ray, uint32_t ev) {
-    if (MASK) {
-        const ItemP &IT = P.items[row / (uint32_t)P.n_el];
-        const uint64_t slot = IT.slot_begin + (uint64_t)(ray % (uint32_t)P.n_el) * IT.rays_per_el + ray / (uint32_t)P.n_el;
-        atomicOr(P.ray_mask + (slot >> 5), 1u << (slot & 31u));
-        if (MASK == 1) return;
-    }
     const unsigned mask = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
@@ -69,7 +62,7 @@ __device__ __forceinline__ void emit(const TraceP &P, uint32_t row, ff t, float 
     const unsigned long long idx = base + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
     if (idx < P.arr_cap) {
         P.arr[idx] = make_uint4(row, __float_as_uint(t.hi), __float_as_uint(t.lo), __float_as_uint(amp));
-        if (DBG) P.arr_dbg[idx] = make_uint2(ray, ev);
+        if (DBG || REC) P.arr_dbg[idx] = make_uint2(ray, ev);
     }
 }
 
@@ -199,7 +192,7 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
 // End of a segment: time of flight and attenuation along it, then the array
 // plane (aperture return), the absorbing bottom, the time window, the bounce
 // budget, or a boundary interaction (Eqs. 7-11) and the next segment.
-template <bool DBG, bool SPLIT, int MASK>
+template <bool DBG, bool SPLIT, bool REC>
 __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S[R.scene];
     const Medium &M = S.med[R.med];
@@ -220,7 +213,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
             if (el > P.n_el - 1) el = P.n_el - 1;
             const float fd = directivity(P, -R.d.z);
             if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
-                emit<DBG, MASK>(P, R.item * (uint32_t)P.n_el + (uint32_t)el, R.t, R.w * fd, R.i,
+                emit<DBG, REC>(P, R.item * (uint32_t)P.n_el + (uint32_t)el, R.t, R.w * fd, R.i,
                           0x80000000u | ((uint32_t)R.b << 24));
                 cn.arrivals++;
             }
@@ -288,7 +281,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
 
 // A queued scatterer event: element drawn uniformly (Philox keyed by ray,
 // transmit, segment and scatterer), receive directivity (Eq. 13), connection ray.
-template <bool DBG, int MASK>
+template <bool DBG, bool REC>
 __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &Q, int slot, Counters &cn) {
     const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
     const float tca = Q.tca[slot], w = Q.w[slot];
@@ -314,7 +307,7 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
     if (ff_gt(ta, P.t_last)) return;
     const float amp = w * expf(-M.a * tca) * q.w * (float)P.n_el * fd * fac * expf(-att);
-    emit<DBG, MASK>(P, item * (uint32_t)P.n_el + e, ta, amp, ray, ((uint32_t)b << 24) | j);
+    emit<DBG, REC>(P, item * (uint32_t)P.n_el + e, ta, amp, ray, ((uint32_t)b << 24) | j);
     cn.arrivals++;
 }
 
@@ -325,7 +318,7 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
 // a time with all lanes busy.  Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
-template <bool DBG, bool SPLIT, int MASK>
+template <bool DBG, bool SPLIT, bool REC>
 __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
@@ -344,7 +337,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
         const unsigned waiting = __ballot_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay);
         const bool resolve = __popc(waiting) >= P.resolve_batch || __ballot_sync(0xffffffffu, R.state == kInSeg) == 0u;
         for (int guard = 0; resolve && guard < 256; ++guard) {
-            if (R.state == kSegDone) finish_segment<DBG, SPLIT, MASK>(P, R, cn);
+            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC>(P, R, cn);
             unsigned need = __ballot_sync(0xffffffffu, R.state == kNeedRay);
             uint64_t my_slot = ~0ull;
             while (need) {
@@ -446,7 +439,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 qn += __popc(m);
                 if (qn >= 32) {
                     __syncwarp();
-                    process_event<DBG, MASK>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+                    process_event<DBG, REC>(P, Q, (qhead + lane) & (kQueue - 1), cn);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
@@ -473,7 +466,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
     }
     // (3) drain the queue
     __syncwarp();
-    if (lane < qn) process_event<DBG, MASK>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+    if (lane < qn) process_event<DBG, REC>(P, Q, (qhead + lane) & (kQueue - 1), cn);
 
     if (P.stats) {
         const uint32_t v[6] = {cn.rays, cn.segments, cn.interactions, cn.candidates, cn.connections, cn.arrivals};
@@ -490,25 +483,24 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
 int trace_occupancy(int block, bool debug) {
     int n = 0;
     if (debug)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, 0>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, 0>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false>, block, 0);
     return n > 0 ? n : 1;
 }
 
-// Variants with frozen sampling media and with the ray mask are compiled
-// separately so the usual kernel carries none of their code.
+// Variants with frozen sampling media and with recorded (ray, event) words are
+// compiled separately so the usual kernel carries none of their code.
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
     bool split = false;
     for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) split = split || P.S[q].split_sampling != 0;
-    if (P.ray_mask && P.mask_only) {
-        split ? k_trace<false, true, 1><<<grid, block, 0, s>>>(P) : k_trace<false, false, 1><<<grid, block, 0, s>>>(P);
-    } else if (P.ray_mask) {
-        split ? k_trace<false, true, 2><<<grid, block, 0, s>>>(P) : k_trace<false, false, 2><<<grid, block, 0, s>>>(P);
-    } else if (debug) {
-        split ? k_trace<true, true, 0><<<grid, block, 0, s>>>(P) : k_trace<true, false, 0><<<grid, block, 0, s>>>(P);
+    if (debug) {
+        split ? k_trace<true, true, false><<<grid, block, 0, s>>>(P) : k_trace<true, false, false><<<grid, block, 0, s>>>(P);
+    } else if (P.record) {
+        split ? k_trace<false, true, true><<<grid, block, 0, s>>>(P) : k_trace<false, false, true><<<grid, block, 0, s>>>(P);
     } else {
-        split ? k_trace<false, true, 0><<<grid, block, 0, s>>>(P) : k_trace<false, false, 0><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, false><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false><<<grid, block, 0, s>>>(P);
     }
 }
 

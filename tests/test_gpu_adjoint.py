@@ -144,17 +144,17 @@ def test_autograd_backward_equals_adjoint(ur):
 
 
 def test_adjoint_replays_only_depositing_rays_consistently(ur):
-    """Only rays that deposit carry a gradient, so the adjoint replays just those: first from a
-    mask it traces itself, then from the mask recorded by a matching ur_trace; a forward trace
-    with other settings must not be reused.  All three gradients agree (up to FP32 summation
-    order), and against the oracle as in the tests above."""
+    """Only paths that deposit carry a gradient, so the adjoint replays one thread per arrival
+    of the forward trace: first from arrivals it records itself, then from those recorded by a
+    matching ur_trace; a forward trace with other settings must not be reused.  All three
+    gradients agree (up to FP32 summation order), and against the oracle as in the tests above."""
     w = phantoms.layered(n_rays=200_000)
     N = w["n_rays"]
     sim, med0, tgt, cur, (g_rf, g_q) = setup_loss(ur, w, N)
     n_med, n_scat = len(med0), len(w["scene"]["scatterers"])
     args = (N, w["seed"], w["max_bounces"], g_rf, g_q, w["max_path"])
-    gm1, ga1 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)            # own mask pass
-    sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])                  # records the mask
+    gm1, ga1 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)            # records its own arrivals
+    sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])                  # records as it traces
     gm2, ga2 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)            # reuses it
     sim.trace(N, w["seed"] + 1, w["max_bounces"], w["max_path"])              # other seed: not reusable
     gm3, ga3 = sim.trace_adjoint(*args, n_med=n_med, n_scat=n_scat)
