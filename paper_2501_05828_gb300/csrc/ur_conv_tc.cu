@@ -672,6 +672,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 // MN chunks 4 KB apart (leading byte offset), 8-pixel K groups 512 B apart
 // (stride byte offset).  K is split across CTAs; partial tiles are added into
 // dW (FP32) with atomics, 32 consecutive ci per warp instruction.
+//
+// KX (C_out = BN in {32, 64}, 9 taps): with q = p + (0, kx - 1),
+// dW[3 ky + kx] = sum_q x[q + (ky - 1, 0)] dy[q - (0, kx - 1)], so the rows are
+// (ky, ci) from input boxes shifted by rows only and the N = 3 BN columns are
+// (kx, co) from three dy boxes shifted by -(kx - 1) pixels: each input row is
+// read once per kernel row instead of once per tap.
 constexpr int kWK = 64;                 // pixels per K step
 constexpr int kChunk = 32 * kWK * 2;    // one 32-channel x 64-pixel box: 4 KB
 
@@ -702,10 +708,11 @@ struct WArgs {
     int *err;
 };
 
-template <int BN>
+template <int BN, bool KX>
 __global__ void __launch_bounds__(kThreads, 1)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmd, const WArgs a) {
-    using K = WCfg<BN>;
+    constexpr int NB = KX ? 3 * BN : BN;   // MMA N
+    using K = WCfg<NB>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = s_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S), accb = s_addr(bars + 2 * K::S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int rows = a.taps * a.Cin;
+    const int rows = (KX ? 3 : a.taps) * a.Cin;
     const int r0 = blockIdx.x * kBM;
     const int n_groups = min(4, (rows - r0) / 32);
     const int co0 = blockIdx.y * BN;
@@ -758,11 +765,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_expect_tx(full0 + 8 * st, bytes);
                 for (int g = 0; g < n_groups; ++g) {
                     const int r = r0 + 32 * g, tap = r / a.Cin, ci0 = r - tap * a.Cin;
-                    const int ky = a.taps == 1 ? 1 : tap / 3, kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
+                    int ky, kx;
+                    if (KX) {   // row group (ky, ci0): input shifted by rows only
+                        ky = tap;
+                        kx = 1;
+                    } else {
+                        ky = a.taps == 1 ? 1 : tap / 3;
+                        kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
+                    }
                     tma_load_4d(sA + st * K::A_BYTES + g * kChunk, &tmx, ci0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * st);
                 }
-                for (int c = 0; c < BN / 32; ++c)
-                    tma_load_4d(sB + st * K::B_BYTES + c * kChunk, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
+                if (KX) {   // column chunks (kx, co block): dy shifted by -(kx - 1) pixels
+                    for (int kx = 0; kx < 3; ++kx)
+                        for (int c = 0; c < BN / 32; ++c)
+                            tma_load_4d(sB + st * K::B_BYTES + (kx * (BN / 32) + c) * kChunk, &tmd, 32 * c, x0 - kx + 1,
+                                        y, n, full0 + 8 * st);
+                } else {
+                    for (int c = 0; c < BN / 32; ++c)
+                        tma_load_4d(sB + st * K::B_BYTES + c * kChunk, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
+                }
                 issued = kt + 1;
             }
             if (!ok)
@@ -772,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0 && nk > 0) {   // MMA issuer
-            constexpr uint32_t idesc = idesc_bf16_mn<BN>();
+            constexpr uint32_t idesc = idesc_bf16_mn<NB>();
             for (int kt = 0; kt < nk; ++kt) {
                 const int st = kt % K::S;
                 if (!mbar_wait(full0 + 8 * st, (uint32_t)(kt / K::S) & 1u, deadline)) {
@@ -796,14 +817,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (nk > 0 && !acc_ready) ok = false;
     tc_fence_after();
     if (warp_ready && warp < n_groups) {
-        const int r = r0 + 32 * warp, tap = r / a.Cin, ci = r - tap * a.Cin + lane;
-        float *dst = a.dw + (size_t)tap * a.Cout * a.Cin + ci;
+        const int r = r0 + 32 * warp, tr = r / a.Cin, ci = r - tr * a.Cin + lane;
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 32) {
+        for (int c = 0; c < NB; c += 32) {
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            const int tap = KX ? 3 * tr + c / BN : tr;   // KX: row = ky, column block = (kx, co)
+            const int co = KX ? c % BN : co0 + c;
+            float *dst = a.dw + ((size_t)tap * a.Cout + co) * a.Cin + ci;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) atomicAdd(dst + (size_t)(co0 + c + j) * a.Cin, __uint_as_float(v[j]));
+            for (int j = 0; j < 32; ++j) atomicAdd(dst + (size_t)j * a.Cin, __uint_as_float(v[j]));
         }
     }
     if (!ok) atomicExch(a.err, 1);
@@ -981,12 +1004,12 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
 
 namespace {
 
-template <int BN>
+template <int BN, bool KX>
 cudaError_t launch_w(const CUtensorMap &mx, const CUtensorMap &md, const WArgs &a, dim3 grid, cudaStream_t stream) {
-    using K = WCfg<BN>;
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    using K = WCfg<KX ? 3 * BN : BN>;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
     if (e != cudaSuccess) return e;
-    k_wgrad_tc<BN><<<grid, kThreads, K::SMEM, stream>>>(mx, md, a);
+    k_wgrad_tc<BN, KX><<<grid, kThreads, K::SMEM, stream>>>(mx, md, a);
     return cudaGetLastError();
 }
 
@@ -1024,7 +1047,8 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     const int nxb = (p.W + kWK - 1) / kWK;
     const long long steps = (long long)p.N * p.H * nxb;
-    const int m_tiles = (p.taps * p.Cin + kBM - 1) / kBM;
+    const bool kx = p.taps == 9 && (p.Cout == 32 || p.Cout == 64);
+    const int m_tiles = ((kx ? 3 : p.taps) * p.Cin + kBM - 1) / kBM;
     if (steps > 0x7fffffffll) {
         if (why) *why = "wgrad3x3_tc: too many pixels";
         return cudaErrorInvalidValue;
@@ -1037,11 +1061,12 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     splits = (steps + per - 1) / per;
     WArgs a{p.N, p.H, p.W, p.Cin, p.Cout, p.taps, nxb, (int)steps, per, p.dw, d_err};
     const dim3 grid((unsigned)m_tiles, 1, (unsigned)splits);
+    if (kx) return BN == 32 ? launch_w<32, true>(mx, md, a, grid, stream) : launch_w<64, true>(mx, md, a, grid, stream);
     switch (BN) {
-        case 32: return launch_w<32>(mx, md, a, grid, stream);
-        case 64: return launch_w<64>(mx, md, a, grid, stream);
-        case 128: return launch_w<128>(mx, md, a, grid, stream);
-        default: return launch_w<256>(mx, md, a, grid, stream);
+        case 32: return launch_w<32, false>(mx, md, a, grid, stream);
+        case 64: return launch_w<64, false>(mx, md, a, grid, stream);
+        case 128: return launch_w<128, false>(mx, md, a, grid, stream);
+        default: return launch_w<256, false>(mx, md, a, grid, stream);
     }
 }
 

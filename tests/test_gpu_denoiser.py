@@ -157,3 +157,37 @@ def test_forward_matches_oracle_across_tiles():
     assert e_res <= 2e-2
     assert col.max() <= 0.1
     dn.close()
+
+
+def test_gradient_matches_oracle_across_tiles():
+    """Parameter gradients on an 8 x 320 frame: several 64-pixel K steps per image row, so the
+    x-shifted boxes of the fused-kx weight gradient cross block seams and the image edges."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05828_gb300 as ur
+    h, w = 8, 320
+    dn = ur.Denoiser(0, max_batch=1, n_el=h, n_s=w, width=32, seed=11)
+    lay = ur.nn_layout(32)
+    rng = np.random.default_rng(12)
+    p = dn.params()
+    for name, (wo, ws, bo, co) in lay.items():
+        p[bo:bo + co] = rng.standard_normal(co).astype(np.float32) * 0.05
+    wo, ws, bo, co = lay["head"]
+    p[wo:wo + 64] = rng.standard_normal(64).astype(np.float32) * 0.3
+    dn.set_params(p)
+    x = rng.standard_normal((1, h, w, 2)).astype(np.float32)
+    t = (0.5 * x + 0.3 * rng.standard_normal((1, h, w, 2))).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    _, g = dn.train_step(dev(x[..., 0]), dev(x[..., 1]), dev(t[..., 0]), dev(t[..., 1]), 0.0, grad=True)
+    g = g.cpu().numpy()
+    P = to_oracle(dn.params(), lay)
+    y, cache = D.forward(P, x.astype(np.float64), q=D.bf16)
+    _, og = D.mse(y, t.astype(np.float64))
+    G = D.backward(P, cache, og)
+    for name in ("e1b", "e2a", "e2b", "d2a", "d2b", "d1a", "d1b", "e3b", "d3a"):
+        wo, ws, bo, co = lay[name]
+        e = rel_l2(g[wo:wo + int(np.prod(ws))].reshape(ws).astype(np.float64), G[name + ".w"])
+        print(f"wide {name}.w: rel_l2 {e:.2e}")
+        assert e <= 5e-2, (name, e)
+    dn.close()
