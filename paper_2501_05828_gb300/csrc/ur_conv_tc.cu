@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 // (stride byte offset).  K is split across CTAs; partial tiles are added into
 // dW (FP32) with atomics, 32 consecutive ci per warp instruction.
 //
-// KX (C_out = BN in {32, 64}, 9 taps): with q = p + (0, kx - 1),
+// KX (9 taps; C_out tiles of BN in {32, 64}): with q = p + (0, kx - 1),
 // dW[3 ky + kx] = sum_q x[q + (ky - 1, 0)] dy[q - (0, kx - 1)], so the rows are
 // (ky, ci) from input boxes shifted by rows only and the N = 3 BN columns are
 // (kx, co) from three dy boxes shifted by -(kx - 1) pixels: each input row is
@@ -778,8 +778,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (KX) {   // column chunks (kx, co block): dy shifted by -(kx - 1) pixels
                     for (int kx = 0; kx < 3; ++kx)
                         for (int c = 0; c < BN / 32; ++c)
-                            tma_load_4d(sB + st * K::B_BYTES + (kx * (BN / 32) + c) * kChunk, &tmd, 32 * c, x0 - kx + 1,
-                                        y, n, full0 + 8 * st);
+                            tma_load_4d(sB + st * K::B_BYTES + (kx * (BN / 32) + c) * kChunk, &tmd, co0 + 32 * c,
+                                        x0 - kx + 1, y, n, full0 + 8 * st);
                 } else {
                     for (int c = 0; c < BN / 32; ++c)
                         tma_load_4d(sB + st * K::B_BYTES + c * kChunk, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
             const int tap = KX ? 3 * tr + c / BN : tr;   // KX: row = ky, column block = (kx, co)
-            const int co = KX ? c % BN : co0 + c;
+            const int co = co0 + (KX ? c % BN : c);
             float *dst = a.dw + ((size_t)tap * a.Cout + co) * a.Cin + ci;
 #pragma unroll
             for (int j = 0; j < 32; ++j) atomicAdd(dst + (size_t)j * a.Cin, __uint_as_float(v[j]));
@@ -1047,7 +1047,8 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     const int nxb = (p.W + kWK - 1) / kWK;
     const long long steps = (long long)p.N * p.H * nxb;
-    const bool kx = p.taps == 9 && (p.Cout == 32 || p.Cout == 64);
+    const bool kx = p.taps == 9;   // C_out tiles of 32 (C_out = 32) or 64 columns x 3 taps
+    const int kx_bn = p.Cout == 32 ? 32 : 64;
     const int m_tiles = ((kx ? 3 : p.taps) * p.Cin + kBM - 1) / kBM;
     if (steps > 0x7fffffffll) {
         if (why) *why = "wgrad3x3_tc: too many pixels";
@@ -1055,13 +1056,14 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     // about eight waves of CTAs, at least 8 K steps each
     const long long target = 8ll * (n_sm > 0 ? n_sm : 148);
-    long long splits = std::max<long long>(1, target / m_tiles);
+    const int n_tiles = kx ? p.Cout / kx_bn : 1;
+    long long splits = std::max<long long>(1, target / ((long long)m_tiles * n_tiles));
     splits = std::min<long long>(splits, std::max<long long>(1, steps / 8));
     const int per = (int)((steps + splits - 1) / splits);
     splits = (steps + per - 1) / per;
     WArgs a{p.N, p.H, p.W, p.Cin, p.Cout, p.taps, nxb, (int)steps, per, p.dw, d_err};
-    const dim3 grid((unsigned)m_tiles, 1, (unsigned)splits);
-    if (kx) return BN == 32 ? launch_w<32, true>(mx, md, a, grid, stream) : launch_w<64, true>(mx, md, a, grid, stream);
+    const dim3 grid((unsigned)m_tiles, (unsigned)n_tiles, (unsigned)splits);
+    if (kx) return kx_bn == 32 ? launch_w<32, true>(mx, md, a, grid, stream) : launch_w<64, true>(mx, md, a, grid, stream);
     switch (BN) {
         case 32: return launch_w<32, false>(mx, md, a, grid, stream);
         case 64: return launch_w<64, false>(mx, md, a, grid, stream);
