@@ -152,60 +152,102 @@ __global__ void k_pool2(const bf16 *x, bf16 *y, int B, int H, int W, int C) {
     }
 }
 
-// Split the gradient of a concatenated decoder input [B][H][W][C1 + C2]: the
-// first C1 channels came from the nearest-upsampled half-resolution tensor (sum
-// over each 2x2 block), the rest from the skip tensor (copied).
-__global__ void k_unconcat(const bf16 *dcat, int B, int H, int W, int C1, int C2, bf16 *dlow, bf16 *dskip) {
-    const int Ho = H / 2, Wo = W / 2, G1 = C1 / 8, G2 = C2 / 8, G = G1 + G2;
-    const long long nlow = (long long)B * Ho * Wo * G1, nskip = (long long)B * H * W * G2;
-    const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
-    GRID_STRIDE(i, nlow + nskip) {
-        if (i < nlow) {
-            const int g = (int)(i % G1);
-            long long r = i / G1;
-            const int xo = (int)(r % Wo);
-            r /= Wo;
-            const int yo = (int)(r % Ho), b = (int)(r / Ho);
-            const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * G + g;
-            float s[8], t[8];
-            unpack8(dg[base], s);
-            unpack8(dg[base + G], t);
+// Per-channel sums of a thread block: thread t owns channels 8 (t % G) .. +8 of its
+// pixels (G = C / 8 divides the 256-thread block); db[c] += the block's total.
+__device__ __forceinline__ void flush_channel_sums(float (&acc)[8], int G, float *db) {
+    __shared__ float s[256][9];
+    __syncthreads();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s[j] += t[j];
-            unpack8(dg[base + (size_t)W * G], t);
+    for (int j = 0; j < 8; ++j) s[threadIdx.x][j] = acc[j];
+    __syncthreads();
+    if ((int)threadIdx.x < G) {
+        float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int q = threadIdx.x; q < (int)blockDim.x; q += G)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s[j] += t[j];
-            unpack8(dg[base + (size_t)W * G + G], t);
+            for (int j = 0; j < 8; ++j) t[j] += s[q][j];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s[j] += t[j];
-            reinterpret_cast<uint4 *>(dlow)[i] = pack8(s);
-        } else {
-            const long long j = i - nlow;
-            const int g = (int)(j % G2);
-            const long long p = j / G2;
-            reinterpret_cast<uint4 *>(dskip)[j] = dg[(size_t)p * G + G1 + g];
-        }
+        for (int j = 0; j < 8; ++j)
+            if (t[j] != 0.f) atomicAdd(&db[8 * threadIdx.x + j], t[j]);
     }
 }
 
-// d[b, y, x, c] += dp[b, y/2, x/2, c] / 4 (gradient of 2x2 average pooling), 8 channels per thread.
-__global__ void k_pool2_bwd_add(bf16 *d, const bf16 *dp, int B, int H, int W, int C) {
-    const int G = C / 8;
+// Gradient of a concatenated decoder input [B][H][W][C1 + C2], first part: the C1
+// channels came from the nearest-upsampled half-resolution tensor, so dlow (half
+// resolution) is the sum over each 2x2 block; it is the gradient at the lower
+// level's last ReLU output, so it is masked by that activation `act` here and
+// its column sums (that layer's bias gradient) go to db.
+__global__ void __launch_bounds__(256) k_unconcat_low(const bf16 *dcat, int B, int H, int W, int C1, int C2,
+                                                      const bf16 *act, bf16 *dlow, float *db) {
+    const int Ho = H / 2, Wo = W / 2, G1 = C1 / 8, G = (C1 + C2) / 8;
+    const int gi = threadIdx.x % G1, lanes = blockDim.x / G1, pl = threadIdx.x / G1;
+    const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
+    const uint4 *ag = reinterpret_cast<const uint4 *>(act);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long P = (long long)B * Ho * Wo;
+    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
+        const int xo = (int)(p % Wo);
+        const long long r = p / Wo;
+        const int yo = (int)(r % Ho), b = (int)(r / Ho);
+        const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * G + gi;
+        float v[8], t[8], m[8];
+        unpack8(dg[base], v);
+        unpack8(dg[base + G], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += t[j];
+        unpack8(dg[base + (size_t)W * G], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += t[j];
+        unpack8(dg[base + (size_t)W * G + G], t);
+        unpack8(ag[(size_t)p * G1 + gi], m);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = m[j] > 0.f ? v[j] + t[j] : 0.f;
+            acc[j] += v[j];
+        }
+        reinterpret_cast<uint4 *>(dlow)[(size_t)p * G1 + gi] = pack8(v);
+    }
+    flush_channel_sums(acc, G1, db);
+}
+
+// Second part: the skip channels [C1, C1 + C2), copied.
+__global__ void k_unconcat_skip(const bf16 *dcat, int B, int H, int W, int C1, int C2, bf16 *dskip) {
+    const int G1 = C1 / 8, G2 = C2 / 8, G = G1 + G2;
+    const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
+    GRID_STRIDE(j, (long long)B * H * W * G2) {
+        const int g = (int)(j % G2);
+        const long long p = j / G2;
+        reinterpret_cast<uint4 *>(dskip)[j] = dg[(size_t)p * G + G1 + g];
+    }
+}
+
+// d[b, y, x, c] += dp[b, y/2, x/2, c] / 4 (gradient of 2x2 average pooling); the sum is
+// the gradient at the encoder block's last ReLU output, so it is masked by that
+// activation `act` and its column sums (the layer's bias gradient) go to db.
+__global__ void __launch_bounds__(256) k_pool2_bwd_mask(bf16 *d, const bf16 *dp, const bf16 *act, int B, int H,
+                                                        int W, int C, float *db) {
+    const int G = C / 8, gi = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
     uint4 *dg = reinterpret_cast<uint4 *>(d);
     const uint4 *pg = reinterpret_cast<const uint4 *>(dp);
-    GRID_STRIDE(i, (long long)B * H * W * G) {
-        const int g = (int)(i % G);
-        long long r = i / G;
-        const int x = (int)(r % W);
-        r /= W;
+    const uint4 *ag = reinterpret_cast<const uint4 *>(act);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long P = (long long)B * H * W;
+    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
+        const int x = (int)(p % W);
+        const long long r = p / W;
         const int y = (int)(r % H), b = (int)(r / H);
-        float v[8], a[8];
+        const size_t i = (size_t)p * G + gi;
+        float v[8], a[8], m[8];
         unpack8(dg[i], v);
-        unpack8(pg[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * G + g], a);
+        unpack8(pg[(((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * G + gi], a);
+        unpack8(ag[i], m);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] += 0.25f * a[j];
+        for (int j = 0; j < 8; ++j) {
+            v[j] = m[j] > 0.f ? v[j] + 0.25f * a[j] : 0.f;
+            acc[j] += v[j];
+        }
         dg[i] = pack8(v);
     }
+    flush_channel_sums(acc, G, db);
 }
 
 // W'[tap][ci][co] = W[8 - tap][co][ci]: weights of the data gradient.
@@ -216,41 +258,6 @@ __global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
         const int ci = (int)(r % Cin);
         const int tap = (int)(r / Cin);
         wt[i] = w[((size_t)(8 - tap) * Cout + co) * Cin + ci];
-    }
-}
-
-// d[p][c] *= (act[p][c] > 0) in place and db[c] += sum over pixels of the masked d.  Thread t
-// owns channels 8 (t % G) .. +8 (G = C / 8 divides the 256-thread block) for every
-// (256 / G)-th pixel.
-__global__ void __launch_bounds__(256) k_mask_bias(bf16 *d, const bf16 *act, long long P, int C, float *db) {
-    __shared__ float s[256][9];
-    const int G = C / 8, g = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    uint4 *dg = reinterpret_cast<uint4 *>(d);
-    const uint4 *ag = reinterpret_cast<const uint4 *>(act);
-    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
-        const size_t i = (size_t)p * G + g;
-        float v[8], m[8];
-        unpack8(dg[i], v);
-        unpack8(ag[i], m);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (!(m[j] > 0.f)) v[j] = 0.f;
-            acc[j] += v[j];
-        }
-        dg[i] = pack8(v);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) s[threadIdx.x][j] = acc[j];
-    __syncthreads();
-    if (threadIdx.x < G) {
-        float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int q = 0; q < lanes; ++q)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) t[j] += s[q * G + threadIdx.x][j];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (t[j] != 0.f) atomicAdd(&db[8 * threadIdx.x + j], t[j]);
     }
 }
 
@@ -295,38 +302,49 @@ __global__ void k_loss(const float *yn, const float *t_rf, const float *t_quad, 
     if ((threadIdx.x & 31) == 0 && local != 0.f) atomicAdd(loss, (double)(local * inv_n));
 }
 
-// Head backward: dWh, dbh (fp32) and the masked gradient of d1 (bf16).  One
-// warp walks a range of pixels; lane l owns channels l and l + 32 (C <= 64).
+// Head backward: dWh, dbh (fp32), the gradient at d1 (= d1b's ReLU output) masked
+// by d1 > 0 (bf16), and d1b's bias gradient (its column sums).  Thread t owns
+// channels 8 (t % G) .. +8 of every (256 / G)-th pixel.
 __global__ void __launch_bounds__(256) k_head_bwd(const float *g, const bf16 *d1, const float *wh, int C, long long P,
-                                                  float *dwh, float *dbh, bf16 *dd1) {
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    float a0[2] = {0.f, 0.f}, a1[2] = {0.f, 0.f}, b0 = 0.f, b1 = 0.f;
-    for (long long p = wid; p < P; p += warps) {
-        const float g0 = g[2 * p], g1 = g[2 * p + 1];
-        b0 += g0;
-        b1 += g1;
+                                                  float *dwh, float *dbh, bf16 *dd1, float *db1) {
+    const int G = C / 8, gi = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
+    float w0[8], w1[8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
-            if (c >= C) continue;
-            const float v = __bfloat162float(d1[(size_t)p * C + c]);
-            a0[h] += g0 * v;
-            a1[h] += g1 * v;
-            dd1[(size_t)p * C + c] = __float2bfloat16_rn(v > 0.f ? g0 * wh[c] + g1 * wh[C + c] : 0.f);
+    for (int j = 0; j < 8; ++j) {
+        w0[j] = wh[8 * gi + j];
+        w1[j] = wh[C + 8 * gi + j];
+    }
+    float a0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, a1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float sb[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float b0 = 0.f, b1 = 0.f;
+    const uint4 *fg = reinterpret_cast<const uint4 *>(d1);
+    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
+        const float2 gg = reinterpret_cast<const float2 *>(g)[p];
+        if (gi == 0) {
+            b0 += gg.x;
+            b1 += gg.y;
         }
-    }
+        float v[8], o[8];
+        unpack8(fg[(size_t)p * G + gi], v);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int c = lane + 32 * h;
-        if (c >= C) continue;
-        if (a0[h] != 0.f) atomicAdd(&dwh[c], a0[h]);
-        if (a1[h] != 0.f) atomicAdd(&dwh[C + c], a1[h]);
+        for (int j = 0; j < 8; ++j) {
+            a0[j] += gg.x * v[j];
+            a1[j] += gg.y * v[j];
+            o[j] = v[j] > 0.f ? gg.x * w0[j] + gg.y * w1[j] : 0.f;
+            sb[j] += o[j];
+        }
+        reinterpret_cast<uint4 *>(dd1)[(size_t)p * G + gi] = pack8(o);
     }
-    if (lane == 0) {
-        atomicAdd(&dbh[0], b0);
-        atomicAdd(&dbh[1], b1);
+    flush_channel_sums(a0, G, dwh);
+    flush_channel_sums(a1, G, dwh + C);
+    flush_channel_sums(sb, G, db1);
+    for (int off = 16; off > 0; off >>= 1) {
+        b0 += __shfl_down_sync(0xffffffffu, b0, off);
+        b1 += __shfl_down_sync(0xffffffffu, b1, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (b0 != 0.f) atomicAdd(&dbh[0], b0);
+        if (b1 != 0.f) atomicAdd(&dbh[1], b1);
     }
 }
 
@@ -491,11 +509,10 @@ void conv_wgrad(ur_nn *nn, const bf16 *x, const bf16 *dy, int B, int H, int W, i
     }
 }
 
-// d *= (act > 0) in place and db += sum over pixels of the masked d.
-void mask_bias(ur_nn *nn, bf16 *d, const bf16 *act, long long P, int C, float *db) {
+// Grid of a kernel whose threads own 8 of C channels of every (256 / (C / 8))-th pixel.
+int channel_grid(long long P, int C) {
     const int lanes = 256 / (C / 8);
-    k_mask_bias<<<(int)std::min<long long>(2048, (P + lanes - 1) / lanes), 256, 0, nn->stream>>>(d, act, P, C, db);
-    ck(cudaGetLastError(), "mask/bias kernel");
+    return (int)std::min<long long>(2048, (P + lanes - 1) / lanes);
 }
 
 // Inputs of every conv of the network at batch B.
@@ -567,11 +584,11 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
     ck(cudaGetLastError(), "head kernel");
 }
 
-// Backward of one block (convs la, lb) given the gradient at lb's output;
+// Backward of one block (convs la, lb) given the gradient at lb's output, already
+// masked by lb's ReLU with lb's bias gradient summed by the kernel that produced it;
 // leaves the gradient of la's input in `din` (full concatenated channels) if din.
 void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din) {
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
-    mask_bias(nn, d_out, nn->act[lb].p, (long long)B * Lb.H * Lb.W, nn->cout[lb], nn->grads + nn->boff[lb]);
     conv_wgrad(nn, nn->act[la].p, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
     k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
                                                                                   nn->cout[lb], nn->cin[lb]);
@@ -595,6 +612,22 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
     ck(cudaGetLastError(), "block backward");
 }
 
+// gcat (gradient of a decoder input at H x W) -> gLow (masked by act[l_low], bias sums of
+// layer l_low) and dskip.
+void unconcat(ur_nn *nn, int B, int H, int W, int C1, int C2, int l_low, bf16 *dskip) {
+    k_unconcat_low<<<channel_grid((long long)B * (H / 2) * (W / 2), C1), 256, 0, nn->stream>>>(
+        nn->gcat, B, H, W, C1, C2, nn->act[l_low].p, nn->gLow, nn->grads + nn->boff[l_low]);
+    k_unconcat_skip<<<grid_for((long long)B * H * W * C2 / 8), 256, 0, nn->stream>>>(nn->gcat, B, H, W, C1, C2, dskip);
+    ck(cudaGetLastError(), "unconcat");
+}
+
+// d (gradient at layer l's output, H x W) += pooling gradient of gcat, masked by act[l], bias sums.
+void pool_bwd(ur_nn *nn, int B, int H, int W, int C, int l, bf16 *d) {
+    k_pool2_bwd_mask<<<channel_grid((long long)B * H * W, C), 256, 0, nn->stream>>>(
+        d, nn->gcat, nn->act[l].p, B, H, W, C, nn->grads + nn->boff[l]);
+    ck(cudaGetLastError(), "pooling backward");
+}
+
 void ensure_train_buffers(ur_nn *nn) {
     if (nn->gA) return;
     const size_t B = nn->max_batch, H = nn->H, W = nn->W, C = nn->width, unit = B * H * W * C;
@@ -615,32 +648,27 @@ double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *
     k_loss<<<grid_for(P), 256, 0, nn->stream>>>(nn->yn, t_rf, t_quad, P, 1.f / nn->scale, nn->gy, nn->loss);
     const int C = nn->width;
     // head
-    k_head_bwd<<<nn->sms * 8, 256, 0, nn->stream>>>(nn->gy, nn->act[13].p, nn->params + nn->hw_off, C, P,
-                                                    nn->grads + nn->hw_off, nn->grads + nn->hb_off, nn->gA);
+    float *gb = nn->grads;
+    // head; every block's incoming gradient below arrives masked by its ReLU with its bias gradient summed
+    k_head_bwd<<<channel_grid(P, C), 256, 0, nn->stream>>>(nn->gy, nn->act[13].p, nn->params + nn->hw_off, C, P,
+                                                           gb + nn->hw_off, gb + nn->hb_off, nn->gA, gb + nn->boff[13]);
     ck(cudaGetLastError(), "head backward");
-    // gradient of d1b's output is gA (already masked by d1 > 0; masking again is harmless)
     const int H = nn->H, W = nn->W;
     // decoder level 1: input concat(up(d2), e1)
     block_bwd(nn, B, 12, 13, nn->gA, nn->gB, nn->gcat);
-    k_unconcat<<<grid_for((long long)B * H * W * (3 * C) / 8), 256, 0, nn->stream>>>(nn->gcat, B, H, W, 2 * C, C, nn->gLow,
-                                                                                      nn->gSkip[0]);
-    ck(cudaGetLastError(), "unconcat");
+    unconcat(nn, B, H, W, 2 * C, C, 11, nn->gSkip[0]);
     // decoder level 2: the gradient of d2 (half resolution) is gLow
     block_bwd(nn, B, 10, 11, nn->gLow, nn->gB, nn->gcat);
-    k_unconcat<<<grid_for((long long)B * (H / 2) * (W / 2) * (6 * C) / 8), 256, 0, nn->stream>>>(
-        nn->gcat, B, H / 2, W / 2, 4 * C, 2 * C, nn->gLow, nn->gSkip[1]);
+    unconcat(nn, B, H / 2, W / 2, 4 * C, 2 * C, 9, nn->gSkip[1]);
     block_bwd(nn, B, 8, 9, nn->gLow, nn->gB, nn->gcat);
-    k_unconcat<<<grid_for((long long)B * (H / 4) * (W / 4) * (12 * C) / 8), 256, 0, nn->stream>>>(
-        nn->gcat, B, H / 4, W / 4, 8 * C, 4 * C, nn->gLow, nn->gSkip[2]);
+    unconcat(nn, B, H / 4, W / 4, 8 * C, 4 * C, 7, nn->gSkip[2]);
     // bottleneck: the gradient of e4 is gLow; encoder blocks leave d(pooled input) in gcat
     block_bwd(nn, B, 6, 7, nn->gLow, nn->gB, nn->gcat);
-    k_pool2_bwd_add<<<grid_for((long long)B * (H / 4) * (W / 4) * 4 * C / 8), 256, 0, nn->stream>>>(
-        nn->gSkip[2], nn->gcat, B, H / 4, W / 4, 4 * C);
+    pool_bwd(nn, B, H / 4, W / 4, 4 * C, 5, nn->gSkip[2]);
     block_bwd(nn, B, 4, 5, nn->gSkip[2], nn->gB, nn->gcat);
-    k_pool2_bwd_add<<<grid_for((long long)B * (H / 2) * (W / 2) * 2 * C / 8), 256, 0, nn->stream>>>(
-        nn->gSkip[1], nn->gcat, B, H / 2, W / 2, 2 * C);
+    pool_bwd(nn, B, H / 2, W / 2, 2 * C, 3, nn->gSkip[1]);
     block_bwd(nn, B, 2, 3, nn->gSkip[1], nn->gB, nn->gcat);
-    k_pool2_bwd_add<<<grid_for((long long)B * H * W * C / 8), 256, 0, nn->stream>>>(nn->gSkip[0], nn->gcat, B, H, W, C);
+    pool_bwd(nn, B, H, W, C, 1, nn->gSkip[0]);
     block_bwd(nn, B, 0, 1, nn->gSkip[0], nn->gB, nullptr);
     ck(cudaGetLastError(), "backward");
     double loss = 0.0;
