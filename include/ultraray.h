@@ -235,6 +235,10 @@ const char *ur_nn_last_error(const ur_nn *nn);
  * starting at a multiple of 8 entries; then the head [2][w] and its bias [2]. */
 ur_status ur_nn_param_count(const ur_nn *nn, uint64_t *n);
 
+/* Number of kernels the network has enqueued since ur_nn_create (every
+ * convolution is one launch; memsets and copies are not counted). */
+ur_status ur_nn_launch_count(const ur_nn *nn, uint64_t *n);
+
 /* Copy the parameters out (get, nullable) and/or in (set, nullable; resets Adam). */
 ur_status ur_nn_params(ur_nn *nn, float *get, const float *set);
 
@@ -308,16 +312,21 @@ ur_status ur_graph_end(ur_ctx *ctx);
 ur_status ur_graph_launch(ur_ctx *ctx);
 
 /* Scatterer-grid and launch tuning (0 fields keep the defaults).  Cell sizes in
- * metres, applied at the next ur_scene_upload; block (multiple of 32, <= 256),
- * blocks_per_sm and resolve_batch (1..32: the tracer finishes segments and
- * starts rays once this many lanes of a warp wait) apply at the next trace. */
+ * metres along x (cell_xy), y (cell_y) and z (cell_z), applied at the next
+ * ur_scene_upload.  Defaults: 8 r_s, 0.5 r_s and 60 r_s when every boundary is
+ * a plane z = c or a cylinder along y (plane waves of a linear array then never
+ * gain a y component, so thin y cells add few cell steps and hold fewer
+ * scatterers); 3 r_s, 3 r_s and 40 r_s when the scene holds a sphere.  block (multiple of 32, <= 256), blocks_per_sm and
+ * resolve_batch (1..32: the tracer finishes segments and starts rays once this
+ * many lanes of a warp wait) apply at the next trace. */
 typedef struct {
     float cell_xy, cell_z;
     int32_t block, blocks_per_sm, resolve_batch;
+    float cell_y;
 } ur_tuning;
 ur_status ur_set_tuning(ur_ctx *ctx, const ur_tuning *t);
 
-/* Autotuner: coordinate descent over grid cell sizes, resolve batch and CTAs
+/* Autotuner: coordinate descent over the three grid cell sizes, resolve batch and CTAs
  * per SM, timing n_rays rays of transmit 0 of scene slot `scene` with CUDA
  * events; keeps the fastest setting (rebuilding every scene's grid) and
  * returns it in *best (nullable).  Synchronous. */

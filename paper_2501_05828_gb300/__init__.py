@@ -29,7 +29,7 @@ EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_se
            "ur_sync", "ur_beamform_noalloc", "ur_scene_upload_slot", "ur_batch_plan", "ur_batch_trace",
            "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune",
            "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint", "ur_nn_create", "ur_nn_destroy",
-           "ur_nn_last_error", "ur_nn_param_count", "ur_nn_params", "ur_nn_set_scale", "ur_nn_forward",
+           "ur_nn_last_error", "ur_nn_param_count", "ur_nn_launch_count", "ur_nn_params", "ur_nn_set_scale", "ur_nn_forward",
            "ur_nn_train_step")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log", "adjoint")
 
@@ -76,7 +76,7 @@ class BatchItem(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("cell_xy", C.c_float), ("cell_z", C.c_float), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("resolve_batch", C.c_int32)]
+                ("resolve_batch", C.c_int32), ("cell_y", C.c_float)]
 
 
 _lib = None
@@ -124,6 +124,7 @@ def lib():
             L.ur_nn_last_error.restype = C.c_char_p
             L.ur_nn_last_error.argtypes = [vp]
             L.ur_nn_param_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+            L.ur_nn_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
             L.ur_nn_params.argtypes = [vp, vp, vp]
             L.ur_nn_set_scale.argtypes = [vp, f32]
             L.ur_nn_forward.argtypes = [vp, vp, vp, i32, vp, vp]
@@ -213,8 +214,9 @@ class Simulator:
         self._call(lib().ur_set_plane_waves(self._ctx, _ptr(a), a.size))
         self.n_tx = a.size
 
-    def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0, resolve_batch=0):
-        t = Tuning(cell_xy, cell_z, block, blocks_per_sm, resolve_batch)
+    def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0, resolve_batch=0, cell_y=0.0):
+        """Grid cell sizes along x (cell_xy), y and z in metres, launch shape; 0 keeps a default."""
+        t = Tuning(cell_xy, cell_z, block, blocks_per_sm, resolve_batch, cell_y)
         self._call(lib().ur_set_tuning(self._ctx, C.byref(t)))
 
     def load(self, workload, slot=0):
@@ -473,6 +475,12 @@ class Denoiser:
         self.n_params = int(n.value)
         self.shape = (int(n_el), int(n_s))
         self.width = width
+
+    def launch_count(self):
+        """Kernels the network has enqueued since creation."""
+        n = C.c_uint64()
+        self._call(lib().ur_nn_launch_count(self._h, C.byref(n)))
+        return int(n.value)
 
     def _call(self, code):
         if code != 0:

@@ -53,6 +53,14 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr uint32_t kChunk = 4096;   // arrivals per deposit work item
 
 // One uploaded scene: host copies of media and boundaries, device scatterers and grid.
+// Default scatterer-grid cell sizes (x, y, z) in units of the capture radius
+// r_s.  Plane waves of a linear array travel in the xz plane, and planes z = c
+// and cylinders along y keep them there (their normals have no y component), so
+// in such scenes thin y cells hold few scatterers at almost no extra cell
+// steps; a sphere tilts rays out of the plane, and cubic-ish cells serve better.
+constexpr float kCellSlab[3] = {8.f, 0.5f, 60.f};
+constexpr float kCellIso[3] = {3.f, 3.f, 40.f};
+
 struct SceneData {
     bool ok = false;
     uint64_t version = 0;              // changes with every upload and media change (paths may change)
@@ -247,6 +255,13 @@ void prepare_transmits(ur_ctx *c) {
     c->tx_dirty = false;
 }
 
+// Default cell size along axis a (0 x, 1 y, 2 z) for a scene, in metres.
+float default_cell(const SceneData &sd, int a) {
+    bool y_invariant = true;
+    for (const ur_boundary &b : sd.bnd) y_invariant &= b.kind != UR_SPHERE;
+    return (y_invariant ? kCellSlab : kCellIso)[a] * sd.r_s;
+}
+
 // Build (or rebuild) a scene's scatterer grid; src == nullptr reuses the device copy.
 void build_grid(ur_ctx *c, SceneData &sd, const float *src) {
     const int n = sd.n_scat;
@@ -278,20 +293,22 @@ void build_grid(ur_ctx *c, SceneData &sd, const float *src) {
         if (!std::isfinite(lo[a]) || !std::isfinite(hi[a])) fail(UR_ERR_INVALID_ARG, "scatterer coordinates must be finite");
     // capture box margin: r_s plus a relative and absolute slack far above FP32 rounding
     const float r_m = sd.r_s * 1.001f + 1e-7f;
-    float h_xy = c->tune.cell_xy > 0.f ? c->tune.cell_xy : 3.f * sd.r_s;
-    float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : 40.f * sd.r_s;
+    float h_x = c->tune.cell_xy > 0.f ? c->tune.cell_xy : default_cell(sd, 0);
+    float h_y = c->tune.cell_y > 0.f ? c->tune.cell_y : default_cell(sd, 1);
+    float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : default_cell(sd, 2);
     int3 dim;
     for (;;) {
-        dim.x = std::max(1, (int)std::ceil((hi[0] - lo[0] + 2.f * r_m) / h_xy));
-        dim.y = std::max(1, (int)std::ceil((hi[1] - lo[1] + 2.f * r_m) / h_xy));
+        dim.x = std::max(1, (int)std::ceil((hi[0] - lo[0] + 2.f * r_m) / h_x));
+        dim.y = std::max(1, (int)std::ceil((hi[1] - lo[1] + 2.f * r_m) / h_y));
         dim.z = std::max(1, (int)std::ceil((hi[2] - lo[2] + 2.f * r_m) / h_z));
         if ((double)dim.x * dim.y * dim.z <= (double)(1u << 26)) break;
-        h_xy *= 1.5f;
+        h_x *= 1.5f;
+        h_y *= 1.5f;
         h_z *= 1.5f;
     }
     sd.g_lo = make_float3(lo[0] - r_m, lo[1] - r_m, lo[2] - r_m);
-    sd.g_h = make_float3(h_xy, h_xy, h_z);
-    sd.g_inv_h = make_float3(1.f / h_xy, 1.f / h_xy, 1.f / h_z);
+    sd.g_h = make_float3(h_x, h_y, h_z);
+    sd.g_inv_h = make_float3(1.f / h_x, 1.f / h_y, 1.f / h_z);
     sd.g_dim = dim;
     const uint32_t n_cells = (uint32_t)dim.x * dim.y * dim.z;
     c->grow(sd.cell_count, sizeof(uint32_t) * (n_cells + 1));
@@ -1253,7 +1270,8 @@ ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int 
         const ur_tuning base = c->tune;
         // device time of one trace of n_rays rays with tuning t (grid rebuilt when its cells change)
         auto measure = [&](const ur_tuning &t) {
-            const bool regrid = sd.n_scat > 0 && (t.cell_xy != c->tune.cell_xy || t.cell_z != c->tune.cell_z);
+            const bool regrid = sd.n_scat > 0 && (t.cell_xy != c->tune.cell_xy || t.cell_y != c->tune.cell_y ||
+                                                  t.cell_z != c->tune.cell_z);
             c->tune = t;
             if (regrid) build_grid(c, sd, nullptr);
             ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
@@ -1275,14 +1293,16 @@ ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int 
         };
         ur_tuning cur = base;
         const float r = sd.r_s;
-        if (cur.cell_xy <= 0.f) cur.cell_xy = 3.f * r;
-        if (cur.cell_z <= 0.f) cur.cell_z = 40.f * r;
+        if (cur.cell_xy <= 0.f) cur.cell_xy = default_cell(sd, 0);
+        if (cur.cell_y <= 0.f) cur.cell_y = default_cell(sd, 1);
+        if (cur.cell_z <= 0.f) cur.cell_z = default_cell(sd, 2);
         if (cur.resolve_batch <= 0) cur.resolve_batch = 16;
         if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = ur::trace_occupancy(256, false);
         float t_cur = measure(cur);
         // coordinate descent over the knobs
-        const float z_mult[] = {20.f, 30.f, 40.f, 60.f, 80.f};
-        const float xy_mult[] = {2.f, 3.f, 4.f, 5.f};
+        const float z_mult[] = {20.f, 40.f, 60.f, 80.f, 120.f};
+        const float xy_mult[] = {2.f, 3.f, 4.f, 6.f, 8.f, 10.f};
+        const float y_mult[] = {0.3f, 0.5f, 1.f, 2.f, 3.f, 4.f};
         const int batches[] = {8, 12, 16, 20, 24};
         for (int pass = 0; pass < 2; ++pass) {
             for (float m : z_mult) {
@@ -1294,6 +1314,12 @@ ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int 
             for (float m : xy_mult) {
                 ur_tuning t = cur;
                 t.cell_xy = m * r;
+                const float v = measure(t);
+                if (v < t_cur) { t_cur = v; cur = t; }
+            }
+            for (float m : y_mult) {
+                ur_tuning t = cur;
+                t.cell_y = m * r;
                 const float v = measure(t);
                 if (v < t_cur) { t_cur = v; cur = t; }
             }
@@ -1324,7 +1350,7 @@ ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int 
 ur_status ur_set_tuning(ur_ctx *c, const ur_tuning *t) {
     return guarded(c, [&] {
         if (!t) fail(UR_ERR_INVALID_ARG, "tuning is NULL");
-        if (t->cell_xy < 0.f || t->cell_z < 0.f || t->block < 0 || t->block > 256 || (t->block % 32) != 0 ||
+        if (t->cell_xy < 0.f || t->cell_y < 0.f || t->cell_z < 0.f || t->block < 0 || t->block > 256 || (t->block % 32) != 0 ||
             t->blocks_per_sm < 0 || t->blocks_per_sm > 64 || t->resolve_batch < 0 || t->resolve_batch > 32)
             fail(UR_ERR_INVALID_ARG, "tuning values out of range (block must be a multiple of 32, <= 256)");
         c->tune = *t;
