@@ -470,7 +470,6 @@ def run_adjoint(args, rank, world, local_rank):
 DENOISER_WORKLOAD = ("denoiser: 4-level U-Net (widths 32-256, 1.95M parameters) on [128 x 3200] analytic channel "
                      "data, batch 8 pairs traced from jittered layered phantoms (1e6-ray input, 3e7-ray target), "
                      "BF16 weights/activations, FP32 accumulation, one step = forward + loss + backward + Adam")
-NN_LAUNCHES_PER_TRAIN_STEP = 97   # kernels of one ur_nn_train_step (launch list in profiles/)
 
 
 def unet_forward_flops(batch, h, w, c=32):
@@ -529,6 +528,7 @@ def run_denoiser(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank) if rank == 0 else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = net.launch_count()
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
@@ -539,6 +539,7 @@ def run_denoiser(args, rank, world, local_rank):
         net.forward(xr, xq)
         fe[k][1].record()
     torch.cuda.synchronize()
+    launches = net.launch_count() - launches0
     clk = clocks.stop() if clocks else None
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     ms_fwd = sum(a.elapsed_time(b) for a, b in fe) / args.steps
@@ -580,7 +581,7 @@ def run_denoiser(args, rank, world, local_rank):
                          "algorithmic_flops_per_step": train_flops,
                          "forward": {"achieved": ach_fwd, "peak": peak_burst, "frac": ach_fwd / peak_burst,
                                      "peak_note": "bf16_tflops (burst) of measured", "flops": F}},
-            "gpu_launches": NN_LAUNCHES_PER_TRAIN_STEP * args.steps + 23 * args.steps,
+            "gpu_launches": launches, "launches_per_step": launches / args.steps,
             "e2e": {"value": B * world / (e2e_ms * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms,
                     "path": "ur_nn_train_step with pinned host inputs/targets (staged copies) and the loss to host"},

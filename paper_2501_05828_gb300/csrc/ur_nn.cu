@@ -401,6 +401,7 @@ struct ur_nn {
     int max_batch = 0, H = 0, W = 0, width = 32;
     float scale = 1.f;
     long long step = 0;
+    unsigned long long launches = 0;   // kernels enqueued since creation
     // parameters: per conv [9][Cout][Cin] then [Cout]; head [2][C] then [2]
     int cin[kNumConv], cout[kNumConv];
     size_t woff[kNumConv], boff[kNumConv], hw_off = 0, hb_off = 0, n_params = 0;
@@ -456,6 +457,7 @@ void conv_fwd(ur_nn *nn, const bf16 *x, int B, int H, int W, int Cin, int Cout, 
               const bf16 *mask, bf16 *y, bool relu, int taps = 9, float *dbias = nullptr) {
     urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0, dbias};
     std::string why;
+    ++nn->launches;
     const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -501,6 +503,7 @@ void conv_wgrad(ur_nn *nn, const bf16 *x, const bf16 *dy, int B, int H, int W, i
                 int taps = 9) {
     urnn::WgradTC P{x, Cin, B, H, W, dy, Cout, taps, dw};
     std::string why;
+    ++nn->launches;
     const cudaError_t e = urnn::wgrad3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -549,6 +552,7 @@ const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
     if (!L.in.x2) return L.in.x1;
     bf16 *cat = nn->cat[(l - 8) / 2];
     if (build) {
+        ++nn->launches;
         k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(
             L.in.x1, L.in.c1, L.in.x2, L.in.c2, B, L.H, L.W, cat);
         ck(cudaGetLastError(), "upcat kernel");
@@ -558,8 +562,10 @@ const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
 
 void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad) {
     const long long P = (long long)B * nn->H * nn->W;
+    ++nn->launches;
     k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, 1.f / nn->scale, nn->x, nn->xn);
     ck(cudaGetLastError(), "prep kernel");
+    ++nn->launches;
     k_pack_first<<<grid_for(32ll * nn->width), 256, 0, nn->stream>>>(nn->pbf + nn->woff[0], nn->width, nn->wfirst);
     ck(cudaGetLastError(), "pack kernel");
     for (int l = 0; l < kNumConv; ++l) {
@@ -573,11 +579,13 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
                      nullptr, nn->act[l].p, true);
         if (l == 1 || l == 3 || l == 5) {   // pool after each encoder block
             const int q = l / 2;
+            ++nn->launches;
             k_pool2<<<grid_for((long long)B * L.H * L.W * nn->cout[l] / 4), 256, 0, nn->stream>>>(
                 nn->act[l].p, nn->pool[q].p, B, L.H, L.W, nn->cout[l]);
             ck(cudaGetLastError(), "pool kernel");
         }
     }
+    ++nn->launches;
     k_head_fwd<<<grid_for(P), 256, 0, nn->stream>>>(nn->act[13].p, nn->xn, nn->params + nn->hw_off,
                                                     nn->params + nn->hb_off, nn->width, P, nn->scale,
                                                     nn->yn, out_rf, out_quad);
@@ -590,6 +598,7 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
 void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din) {
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
     conv_wgrad(nn, nn->act[la].p, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
+    ++nn->launches;
     k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
                                                                                   nn->cout[lb], nn->cin[lb]);
     // gradient at la's output, masked by la's ReLU in the epilogue, which also sums la's bias gradient
@@ -598,6 +607,7 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
     if (la == 0) {   // first layer: single-tap gradient over the neighbourhood channels, then back to [9][C][32]
         ck(cudaMemsetAsync(nn->dwfirst, 0, sizeof(float) * 32 * nn->width, nn->stream), "memset");
         conv_wgrad(nn, nn->x, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
+        ++nn->launches;
         k_unpack_first_grad<<<grid_for(18ll * nn->width), 256, 0, nn->stream>>>(nn->dwfirst, nn->width,
                                                                                nn->grads + nn->woff[0]);
     } else {
@@ -605,6 +615,7 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
                    nn->grads + nn->woff[la]);
     }
     if (din) {
+        ++nn->launches;
         k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
                                                                                       nn->cout[la], nn->cin[la]);
         conv_fwd(nn, scratch, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din, false);
@@ -615,14 +626,17 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
 // gcat (gradient of a decoder input at H x W) -> gLow (masked by act[l_low], bias sums of
 // layer l_low) and dskip.
 void unconcat(ur_nn *nn, int B, int H, int W, int C1, int C2, int l_low, bf16 *dskip) {
+    ++nn->launches;
     k_unconcat_low<<<channel_grid((long long)B * (H / 2) * (W / 2), C1), 256, 0, nn->stream>>>(
         nn->gcat, B, H, W, C1, C2, nn->act[l_low].p, nn->gLow, nn->grads + nn->boff[l_low]);
+    ++nn->launches;
     k_unconcat_skip<<<grid_for((long long)B * H * W * C2 / 8), 256, 0, nn->stream>>>(nn->gcat, B, H, W, C1, C2, dskip);
     ck(cudaGetLastError(), "unconcat");
 }
 
 // d (gradient at layer l's output, H x W) += pooling gradient of gcat, masked by act[l], bias sums.
 void pool_bwd(ur_nn *nn, int B, int H, int W, int C, int l, bf16 *d) {
+    ++nn->launches;
     k_pool2_bwd_mask<<<channel_grid((long long)B * H * W, C), 256, 0, nn->stream>>>(
         d, nn->gcat, nn->act[l].p, B, H, W, C, nn->grads + nn->boff[l]);
     ck(cudaGetLastError(), "pooling backward");
@@ -645,11 +659,13 @@ double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *
     const long long P = (long long)B * nn->H * nn->W;
     ck(cudaMemsetAsync(nn->loss, 0, sizeof(double), nn->stream), "memset loss");
     ck(cudaMemsetAsync(nn->grads, 0, sizeof(float) * nn->n_params, nn->stream), "memset grads");
+    ++nn->launches;
     k_loss<<<grid_for(P), 256, 0, nn->stream>>>(nn->yn, t_rf, t_quad, P, 1.f / nn->scale, nn->gy, nn->loss);
     const int C = nn->width;
     // head
     float *gb = nn->grads;
     // head; every block's incoming gradient below arrives masked by its ReLU with its bias gradient summed
+    ++nn->launches;
     k_head_bwd<<<channel_grid(P, C), 256, 0, nn->stream>>>(nn->gy, nn->act[13].p, nn->params + nn->hw_off, C, P,
                                                            gb + nn->hw_off, gb + nn->hb_off, nn->gA, gb + nn->boff[13]);
     ck(cudaGetLastError(), "head backward");
@@ -759,6 +775,7 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         ck(cudaMemcpy(nn->params, h.data(), sizeof(float) * nn->n_params, cudaMemcpyHostToDevice), "copy params");
         ck(cudaMemset(nn->m, 0, sizeof(float) * nn->n_params), "memset");
         ck(cudaMemset(nn->v, 0, sizeof(float) * nn->n_params), "memset");
+        ++nn->launches;
         k_to_bf16<<<grid_for((long long)nn->n_params), 256, 0, nn->stream>>>(nn->params, nn->pbf, (long long)nn->n_params);
         ck(cudaGetLastError(), "to bf16");
         // activations
@@ -816,6 +833,12 @@ ur_status ur_nn_param_count(const ur_nn *nn, uint64_t *n) {
     return UR_OK;
 }
 
+ur_status ur_nn_launch_count(const ur_nn *nn, uint64_t *n) {
+    if (!nn || !n) return UR_ERR_INVALID_ARG;
+    *n = nn->launches;
+    return UR_OK;
+}
+
 ur_status ur_nn_params(ur_nn *nn, float *get, const float *set) {
     return nn_guard(nn, [&] {
         ck(cudaSetDevice(nn->device), "cudaSetDevice");
@@ -823,6 +846,7 @@ ur_status ur_nn_params(ur_nn *nn, float *get, const float *set) {
         if (get) ck(cudaMemcpy(get, nn->params, sizeof(float) * nn->n_params, cudaMemcpyDefault), "get params");
         if (set) {
             ck(cudaMemcpy(nn->params, set, sizeof(float) * nn->n_params, cudaMemcpyDefault), "set params");
+            ++nn->launches;
             k_to_bf16<<<grid_for((long long)nn->n_params), 256, 0, nn->stream>>>(nn->params, nn->pbf, (long long)nn->n_params);
             ck(cudaGetLastError(), "to bf16");
             ck(cudaMemsetAsync(nn->m, 0, sizeof(float) * nn->n_params, nn->stream), "reset m");
@@ -869,6 +893,7 @@ ur_status ur_nn_train_step(ur_nn *nn, const float *rf, const float *quad, const 
             nn->step += 1;
             const float b1 = 0.9f, b2 = 0.999f;
             const float c1 = 1.f - std::pow(b1, (float)nn->step), c2 = 1.f - std::pow(b2, (float)nn->step);
+            ++nn->launches;
             k_adam<<<grid_for((long long)nn->n_params), 256, 0, nn->stream>>>(nn->params, nn->grads, nn->m, nn->v, nn->pbf,
                                                                             (long long)nn->n_params, lr, b1, b2, 1e-8f, c1, c2);
             ck(cudaGetLastError(), "adam kernel");
