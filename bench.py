@@ -49,14 +49,18 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), per primary ray, valid only while the tracer sources
 # hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "dd7c92c0da1b3e20", "bytes_per_ray": 10.07, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+TRACE_TRAFFIC = {"src_sha": "b870aefa86a4adcd", "bytes_per_ray": 11.22, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
 
 
 def tracer_sha():
+    """Hash of the tracer kernel's sources and of the default grid cells (which set its traffic)."""
     h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2501_05828_gb300", "csrc")
     for f in ("ur_trace.cu", "ur_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2501_05828_gb300", "csrc", f), "rb") as fh:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "ur_api.cu"), "rb") as fh:
+        h.update(b"".join(l for l in fh if l.startswith(b"constexpr float kCell")))
     return h.hexdigest()[:16]
 
 
