@@ -125,6 +125,51 @@ class ClockSampler:
                 "power_w_max": pmax, "samples": len(rows), "samples_under_load": len(loaded), "reasons": reasons}
 
 
+# ------------------------------------------------------------------ ranks
+class Ranks:
+    """One process per GPU under torchrun: process group, barrier and max over
+    ranks.  Every rank simulates its own replica (weak scaling); there is no
+    data-path collective, only the timing reduction."""
+
+    def __init__(self, rank, world, local_rank, backend="nccl"):
+        import torch
+        self.torch, self.rank, self.world = torch, rank, world
+        self.cuda = backend == "nccl"
+        self.device = torch.device("cuda", local_rank) if self.cuda else torch.device("cpu")
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+            if self.cuda:
+                dist.init_process_group("nccl", device_id=self.device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+        if self.cuda:
+            self.torch.cuda.synchronize(self.device)
+
+    def max(self, x):
+        """Maximum of a float over ranks (the slowest rank's time)."""
+        if not self.dist:
+            return float(x)
+        t = self.torch.tensor([float(x)], dtype=self.torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank * world / seconds_max
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_rate(w, target_s, threads=None):
     """FP64 oracle on a bounded sample of the frame: returns (rays/s, rays in sample, seconds)."""
@@ -179,11 +224,8 @@ def run_ours(args, rank, world, local_rank):
     import phantoms
 
     torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    dev = torch.device("cuda", local_rank)
+    R = Ranks(rank, world, local_rank)
+    dev = R.device
     w = phantoms.layered()
     if args.rays:
         w["n_rays"] = args.rays
@@ -207,10 +249,7 @@ def run_ours(args, rank, world, local_rank):
         sim.beamform(rf, quad, x_d, z_d, w["dyn_range_db"], iq=None, env=env, db=db)
         last["stats"] = st
 
-    def barrier():
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier = R.barrier
 
     for _ in range(args.warmup):
         step()
@@ -230,12 +269,8 @@ def run_ours(args, rank, world, local_rank):
     sim.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = N * world / (ms_max * 1e-3)
+    ms_max = R.max(ms)
+    value = whole_job_rate(N, world, ms_max * 1e-3)
 
     # ---- roofline of the dominant kernel (the tracer) ----
     st = last["stats"]
@@ -281,10 +316,7 @@ def run_ours(args, rank, world, local_rank):
             e2e_step()
         barrier()
         e2e_s = (time.perf_counter() - t0) / n_e2e
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = R.max(e2e_s)
 
     if rank == 0:
         line = {
@@ -304,7 +336,7 @@ def run_ours(args, rank, world, local_rank):
                          "algorithmic_flops_per_launch": trace_flops(st)},
             "stats_per_frame": st,
             "gpu_launches": launches,
-            "e2e": {"value": N * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": whole_job_rate(N, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
                     "path": "ur_scene_upload(pinned host scatterers, grid build) + ur_trace + ur_beamform(db -> pinned host)"},
             "clocks": clk,
@@ -316,8 +348,7 @@ def run_ours(args, rank, world, local_rank):
                                               % (n - 1, dt)}
         print(json.dumps(line), flush=True)
     sim.close()
-    if dist:
-        dist.destroy_process_group()
+    R.close()
 
 
 BATCH_WORKLOAD = ("batched: 8 jittered layered phantoms (skin +-1 mm, fat +-2 mm, bone r U(3,10) mm, 10k-200k "
@@ -334,7 +365,8 @@ def run_batched(args, rank, world, local_rank):
     import phantoms
 
     torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
+    R = Ranks(rank, world, local_rank)
+    dev = R.device
     side = torch.cuda.Stream(dev)
     scenes = [phantoms.batched_variant(s) for s in range(1, 9)]
     scale = args.batch_scale
@@ -373,6 +405,7 @@ def run_batched(args, rank, world, local_rank):
         sim.graph_end()
         sim.graph_launch()
         side.synchronize()
+        R.barrier()
         clocks = ClockSampler(local_rank) if rank == 0 else None
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -382,9 +415,41 @@ def run_batched(args, rank, world, local_rank):
             sim.graph_launch()
             ev[k][1].record(side)
         side.synchronize()
+        R.barrier()
         clk = clocks.stop() if clocks else None
         n_arr2, _ = sim.batch_status()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+        # ---- end to end through the C ABI: scenes from pinned host memory, plan, trace, images to host
+        sc_host = [torch.from_numpy(w["scene"]["scatterers"]).pin_memory() for w in scenes]
+        x_h = torch.from_numpy(w0["x_px"]).pin_memory()
+        z_h = torch.from_numpy(w0["z_px"]).pin_memory()
+        db_h = torch.empty(tuple(db.shape), dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * 4 + len(w["scene"]["media"]) * 16 + len(w["scene"]["boundaries"]) * 28
+                  for t, w in zip(sc_host, scenes)) + x_h.numel() * 4 + z_h.numel() * 4 + n_items * 24
+        d2h = db_h.numel() * 4
+
+        def e2e_step():
+            for slot, (w, sc) in enumerate(zip(scenes, sc_host)):
+                s = w["scene"]
+                sim.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], sc, s["r_s"], slot)
+            sim.batch_plan(items, x_h, z_h, capacity=int(0.35 * total_rays) + 4096)
+            sim.batch_trace(seed, 8, 0.2, rf=rf, quad=quad)
+            sim.batch_beamform(rf, quad, 60.0, db=db)
+            db_h.copy_(db, non_blocking=True)
+            side.synchronize()
+
+        n_e2e = 0 if args.skip_e2e else max(1, min(args.steps, 3))
+        e2e_s = float("nan")
+        if n_e2e:
+            e2e_step()
+            R.barrier()
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                e2e_step()
+            R.barrier()
+            e2e_s = (time.perf_counter() - t0) / n_e2e
+        e2e_s = R.max(e2e_s)
+    ms = R.max(sum(a.elapsed_time(b) for a, b in ev) / args.steps)
     trace_ms = prof["trace"][0] / max(prof["trace"][2], 1)
     props = torch.cuda.get_device_properties(dev)
     peaks = {}
@@ -396,19 +461,68 @@ def run_batched(args, rank, world, local_rank):
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = trace_flops(st) / (trace_ms * 1e-3) / 1e12
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": total_rays / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {
+            "metric": METRIC, "value": whole_job_rate(total_rays, world, ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "items": n_items, "rays_per_step": total_rays,
                        "ray_scale": scale, "l2": "flushed before every timed step (256 MiB write, untimed)"},
-            "frames_per_s": n_items / (ms * 1e-3), "images_per_s": len(scenes) / (ms * 1e-3),
+            "frames_per_s": whole_job_rate(n_items, world, ms * 1e-3),
+            "images_per_s": whole_job_rate(len(scenes), world, ms * 1e-3),
             "arrivals_per_step": n_arr2, "stats_per_step": st,
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
             "roofline": {"bound": "alu", "kernel": "k_trace", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
-            "gpu_launches": 7 * args.steps, "clocks": clk}), flush=True)
+            "gpu_launches": 7 * args.steps, "clocks": clk,
+            "e2e": {"value": whole_job_rate(total_rays, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+                    "path": "8 x ur_scene_upload_slot (pinned host scatterers, grid builds) + ur_batch_plan + "
+                            "ur_batch_trace + ur_batch_beamform, 8 dB images to pinned host"}}
+        if world == 1 and not args.no_cpu_baseline:
+            w = dict(scenes[0])
+            w["angles"] = scenes[0]["angles"][15:16]
+            rate, n, dt, thr = oracle_rate(w, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                    "sample": "rays 0..%d of scene seed 1's 0-degree transmit (%.1f s), trace + "
+                                              "deposit + 512x256 DAS + log" % (n - 1, dt)}
+        print(json.dumps(line), flush=True)
     sim.close()
+    R.close()
+
+
+def oracle_adjoint_rate(w, tgt_media, target_s, threads=None):
+    """FP64 oracle forward + pathwise gradient on a bounded sample of the frame's rays:
+    returns (rays/s, rays in sample, seconds, threads).  The target channel data of the
+    sample is computed first and not timed, as on the GPU side."""
+    import numpy as np
+    import oracle
+    threads = threads or (os.cpu_count() or 1)
+    wt = dict(w["scene"])
+    wt["media"] = [tuple(float(v) for v in m) for m in tgt_media]
+    n_tx = len(np.atleast_1d(w["angles"]))
+
+    def run(n, timed_scene):
+        arr, _, _ = oracle.trace(timed_scene, w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"],
+                                 w["max_path"], 0, n, threads=threads)
+        return oracle.deposit(w["array"], n_tx, arr)
+
+    def step(n, t_rf, t_q):
+        rf, q = run(n, w["scene"])
+        oracle.grad(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], 2 * (rf - t_rf),
+                    2 * (q - t_q), w["max_path"], 0, n, threads=threads)
+
+    n = 2048
+    t_rf, t_q = run(n, wt)
+    t0 = time.perf_counter()
+    step(n, t_rf, t_q)
+    probe = time.perf_counter() - t0
+    n = int(max(1024, min(w["n_rays"], n * target_s / max(probe, 1e-3))))
+    t_rf, t_q = run(n, wt)
+    t0 = time.perf_counter()
+    step(n, t_rf, t_q)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, threads
 
 
 def run_adjoint(args, rank, world, local_rank):
@@ -422,9 +536,11 @@ def run_adjoint(args, rank, world, local_rank):
     import phantoms
 
     torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
+    R = Ranks(rank, world, local_rank)
+    dev = R.device
     w = phantoms.layered()
     N = w["n_rays"] if not args.rays else args.rays
+    seed = w["seed"] + rank
     sim = ur.Simulator(local_rank)
     sim.load(w)
     med0 = np.array(w["scene"]["media"], np.float32)
@@ -433,42 +549,101 @@ def run_adjoint(args, rank, world, local_rank):
     tgt_med[:, 1] *= 1.05
     tgt_med[:, 2] *= 1.10
     sim.set_media(tgt_med.astype(np.float32))
-    trf, tq = sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])
+    trf, tq = sim.trace(N, seed, w["max_bounces"], w["max_path"])
     sim.set_media(med0)
     n_scat = len(w["scene"]["scatterers"])
+    _, _, st = sim.trace(N, seed, w["max_bounces"], w["max_path"], stats=True)
 
-    def step():
-        rf, q = sim.trace(N, w["seed"], w["max_bounces"], w["max_path"])
-        g_rf, g_q = 2 * (rf - trf), 2 * (q - tq)
-        return sim.trace_adjoint(N, w["seed"], w["max_bounces"], g_rf, g_q, w["max_path"], n_med=len(med0),
+    def step(t_rf=trf, t_q=tq):
+        rf, q = sim.trace(N, seed, w["max_bounces"], w["max_path"])
+        g_rf, g_q = 2 * (rf - t_rf), 2 * (q - t_q)
+        return sim.trace_adjoint(N, seed, w["max_bounces"], g_rf, g_q, w["max_path"], n_med=len(med0),
                                  n_scat=n_scat)
 
     for _ in range(args.warmup):
         step()
-    torch.cuda.synchronize()
+    R.barrier()
     sim.set_profiling(True)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    R.barrier()
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
         gm, ga = step()
         ev[k][1].record()
-    torch.cuda.synchronize()
+    R.barrier()
+    clk = clocks.stop() if clocks else None
     prof = sim.profile()
     sim.set_profiling(False)
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ms = R.max(sum(a.elapsed_time(b) for a, b in ev) / args.steps)
     per = {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]}
+    launches = sum(v[1] for v in prof.values())
+
+    # ---- end to end: target channel data from pinned host memory, gradients back to host
+    trf_h, tq_h = trf.cpu().pin_memory(), tq.cpu().pin_memory()
+    h2d = (trf_h.numel() + tq_h.numel()) * 4
+    d2h = (len(med0) * 3 + n_scat) * 4
+
+    def e2e_step():
+        t_rf = trf_h.to(dev, non_blocking=True)
+        t_q = tq_h.to(dev, non_blocking=True)
+        gm_d, ga_d = step(t_rf, t_q)
+        return gm_d.cpu(), ga_d.cpu()
+
+    n_e2e = 0 if args.skip_e2e else max(3, min(args.steps, 10))
+    e2e_s = float("nan")
+    if n_e2e:
+        e2e_step()
+        R.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        R.barrier()
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_s = R.max(e2e_s)
+
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    t_trace = per.get("trace", float("nan")) * 1e-3
+    achieved = trace_flops(st) / t_trace / 1e12
     if rank == 0:
-        print(json.dumps({
-            "metric": "rays/s of forward + gradient (path-replay adjoint)", "value": N / (ms * 1e-3), "unit": UNIT,
+        line = {
+            "metric": "rays/s of forward + gradient (path-replay adjoint)",
+            "value": whole_job_rate(N, world, ms * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "differentiation: " + WORKLOAD, "rays_per_step": N, "parameters": 12 + n_scat,
-                       "l2": "flushed before every timed step (256 MiB write, untimed)"},
+                       "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "parallelism": "replicas: one frame per GPU"},
             "phase_ms": per, "adjoint_over_trace": per.get("adjoint", 0.0) / max(per.get("trace", 1e-9), 1e-9),
-            "grad_media_norm": float(gm.norm()), "grad_amp_norm": float(ga.norm())}), flush=True)
+            "roofline": {"bound": "alu", "kernel": "k_trace (recording arrivals for the adjoint)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
+                             props.multi_processor_count, FP32_LANES_PER_SM, sm_mhz),
+                         "trace_ms_per_launch": t_trace * 1e3, "algorithmic_flops_per_launch": trace_flops(st)},
+            "gpu_launches": launches, "clocks": clk,
+            "e2e": {"value": whole_job_rate(N, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+                    "path": "target rf/quad from pinned host, ur_trace + loss gradient + ur_trace_adjoint, "
+                            "gradients (12 + %d floats) to host" % n_scat},
+            "grad_media_norm": float(gm.norm()), "grad_amp_norm": float(ga.norm())}
+        if world == 1 and not args.no_cpu_baseline:
+            rate, n, dt, thr = oracle_adjoint_rate(w, tgt_med, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                    "sample": "rays 0..%d of the frame (%.1f s): FP64 trace + deposit + pathwise "
+                                              "gradient (dual numbers), target precomputed" % (n - 1, dt)}
+        print(json.dumps(line), flush=True)
     sim.close()
+    R.close()
 
 
 DENOISER_WORKLOAD = ("denoiser: 4-level U-Net (widths 32-256, 1.95M parameters) on [128 x 3200] analytic channel "
@@ -515,7 +690,8 @@ def run_denoiser(args, rank, world, local_rank):
     import phantoms
 
     torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
+    R = Ranks(rank, world, local_rank)
+    dev = R.device
     B = 8
     sim = ur.Simulator(local_rank)
     xr, xq, tr, tq, _ = dz.make_pairs(sim, phantoms.batched_variant, range(1 + 8 * rank, 9 + 8 * rank), 1e6, 3e7)
@@ -527,8 +703,8 @@ def run_denoiser(args, rank, world, local_rank):
     for _ in range(args.warmup):
         net.train_step(xr, xq, tr, tq, lr)
         net.forward(xr, xq)
-    torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    R.barrier()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -542,11 +718,11 @@ def run_denoiser(args, rank, world, local_rank):
         fe[k][0].record()
         net.forward(xr, xq)
         fe[k][1].record()
-    torch.cuda.synchronize()
+    R.barrier()
     launches = net.launch_count() - launches0
     clk = clocks.stop() if clocks else None
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    ms_fwd = sum(a.elapsed_time(b) for a, b in fe) / args.steps
+    ms = R.max(sum(a.elapsed_time(b) for a, b in ev) / args.steps)
+    ms_fwd = R.max(sum(a.elapsed_time(b) for a, b in fe) / args.steps)
     # end to end through the C ABI with pinned host buffers (inputs + targets in, loss out)
     hx = [t.cpu().pin_memory() for t in (xr, xq, tr, tq)]
     h2d = sum(t.numel() * 4 for t in hx)
@@ -554,11 +730,13 @@ def run_denoiser(args, rank, world, local_rank):
     e2e_ms = float("nan")
     if n_e2e:
         net.train_step(*hx, lr)
-        torch.cuda.synchronize()
+        R.barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             net.train_step(*hx, lr)
+        R.barrier()
         e2e_ms = (time.perf_counter() - t0) / n_e2e * 1e3
+    e2e_ms = R.max(e2e_ms)
     F = unet_forward_flops(B, H, W)
     F_first = 2 * 9 * 2 * 32 * B * H * W
     train_flops = 3 * F - F_first           # forward, data gradients (none for the input), weight gradients
@@ -573,12 +751,12 @@ def run_denoiser(args, rank, world, local_rank):
     ach_fwd = F / (ms_fwd * 1e-3) / 1e12
     if rank == 0:
         line = {
-            "metric": "denoiser training samples/s ([128 x 3200] channel data)", "value": B * world / (ms * 1e-3),
+            "metric": "denoiser training samples/s ([128 x 3200] channel data)", "value": whole_job_rate(B, world, ms * 1e-3),
             "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": DENOISER_WORKLOAD, "batch": B, "n_el": H, "n_s": W,
                        "l2": "flushed before every timed call (256 MiB write, untimed)"},
-            "inference_samples_per_s": B * world / (ms_fwd * 1e-3), "ms_forward": ms_fwd, "loss": loss,
+            "inference_samples_per_s": whole_job_rate(B, world, ms_fwd * 1e-3), "ms_forward": ms_fwd, "loss": loss,
             "roofline": {"bound": "tensor", "kernel": "train step (tcgen05 convolutions + elementwise kernels)",
                          "achieved": ach, "peak": peak_sus, "unit": "TFLOP/s", "frac": ach / peak_sus,
                          "traffic": None, "peak_note": "bf16_tflops_sustained of measured",
@@ -586,7 +764,7 @@ def run_denoiser(args, rank, world, local_rank):
                          "forward": {"achieved": ach_fwd, "peak": peak_burst, "frac": ach_fwd / peak_burst,
                                      "peak_note": "bf16_tflops (burst) of measured", "flops": F}},
             "gpu_launches": launches, "launches_per_step": launches / args.steps,
-            "e2e": {"value": B * world / (e2e_ms * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": whole_job_rate(B, world, e2e_ms * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 8, "ms_per_step": e2e_ms,
                     "path": "ur_nn_train_step with pinned host inputs/targets (staged copies) and the loss to host"},
             "clocks": clk,
@@ -598,12 +776,14 @@ def run_denoiser(args, rank, world, local_rank):
                                               "(1/8 sample) in %.1f s, numpy threads" % (n, dt)}
         print(json.dumps(line), flush=True)
     net.close()
+    R.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (default: 150 layered, 5 batched, 30 adjoint, 30 denoiser)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -617,6 +797,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     args.warmup = max(3, args.warmup)
+    if args.steps <= 0:
+        args.steps = {"layered": 150, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "batched":
