@@ -50,7 +50,8 @@ bool is_device_ptr(const void *p) {
 }
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr uint32_t kChunk = 4096;   // arrivals per deposit work item
+constexpr uint32_t kChunk = 4096;      // most arrivals per deposit work item
+constexpr uint32_t kChunkMin = 512;    // fewest (work items are sized for several deposit waves)
 
 // One uploaded scene: host copies of media and boundaries, device scatterers and grid.
 // Default scatterer-grid cell sizes (x, y, z) in units of the capture radius
@@ -547,7 +548,7 @@ void size_trace_buffers(ur_ctx *c, uint64_t cap, bool dbg) {
     c->grow(c->row_count, sizeof(uint32_t) * n_rows);
     c->grow(c->row_fill, sizeof(uint32_t) * n_rows);
     c->grow(c->row_off, sizeof(uint32_t) * (n_rows + 1));
-    c->grow(c->work, sizeof(uint4) * (n_rows + c->arr_cap / kChunk + 16));
+    c->grow(c->work, sizeof(uint4) * (n_rows + c->arr_cap / kChunkMin + 16));
     c->grow(c->n_work, sizeof(uint32_t));
 }
 
@@ -576,7 +577,10 @@ void launch_binning(ur_ctx *c, float *d_rf, float *d_q) {
     B.n_rows = (int)n_rows;
     B.n_s = c->arr.n_s;
     B.chunk = kChunk;
-    B.max_items = (uint32_t)(n_rows + c->arr_cap / kChunk + 16);
+    B.chunk_min = kChunkMin;
+    B.target_items = (uint32_t)(c->sms * 4 * 8);   // 8 waves of the deposit grid
+    B.max_items = (uint32_t)(n_rows + c->arr_cap / kChunkMin + 16);
+    B.priv_rows = ur::bin_sort_smem((int)n_rows) > 0;
     B.row_count = (uint32_t *)c->row_count.p;
     B.row_fill = (uint32_t *)c->row_fill.p;
     B.row_off = (uint32_t *)c->row_off.p;
@@ -587,8 +591,10 @@ void launch_binning(ur_ctx *c, float *d_rf, float *d_q) {
     B.quad = d_q;
     const double s_samples = (double)c->arr.n_cycles / (4.0 * (double)c->arr.f0) * (double)c->arr.fs;
     B.K = (float)((double)c->arr.tcut_sigmas * s_samples);
-    B.inv_2s2 = (float)(1.0 / (2.0 * s_samples * s_samples));
+    B.inv_2s2_log2e = (float)(1.4426950408889634 / (2.0 * s_samples * s_samples));
     B.phase_per_sample = (float)(2.0 * (double)c->arr.f0 / (double)c->arr.fs);
+    B.rot32_s = (float)std::sin(kPi * 32.0 * (double)B.phase_per_sample);
+    B.rot32_c = (float)std::cos(kPi * 32.0 * (double)B.phase_per_sample);
     ck(cudaMemsetAsync(B.row_count, 0, sizeof(uint32_t) * n_rows, c->stream), "memset rows");
     ck(cudaMemsetAsync(B.row_fill, 0, sizeof(uint32_t) * n_rows, c->stream), "memset rows");
     c->phase_begin(UR_PHASE_SORT);

@@ -311,11 +311,16 @@ struct BinP {
     uint32_t *row_off;      // [n_rows + 1]
     uint4 *items;           // (row, begin, end, 0) work items
     uint32_t *n_items;
-    uint32_t max_items, chunk;
+    uint32_t max_items;
+    uint32_t chunk, chunk_min, target_items;   // work items of chunk_min..chunk arrivals, about target_items of them
+    int priv_rows;          // row histograms in shared memory (n_rows <= kBinPrivRows)
     float4 *sorted;         // (t_hi, t_lo, amp, 0)
     float *rf, *quad;       // [n_rows][n_s]
-    float K, inv_2s2, phase_per_sample;   // taps |n - t| <= K; gaussian 1/(2 s^2); 2 f0 / fs (half-cycles per sample)
+    float K, inv_2s2_log2e, phase_per_sample;   // taps |n - t| <= K; log2(e) / (2 s^2); 2 f0 / fs (half-cycles per sample)
+    float rot32_s, rot32_c;                     // sin, cos of the carrier phase over 32 samples
 };
+constexpr int kBinPrivRows = 4096;                  // largest row count with shared-memory histograms
+int bin_sort_smem(int n_rows);                      // their bytes per CTA (0: global counters)
 void launch_bin_sort(const BinP &B, int sms, cudaStream_t s);      // 3 kernels
 void launch_bin_deposit(const BinP &B, int sms, cudaStream_t s);   // 1 kernel
 
