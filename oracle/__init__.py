@@ -28,7 +28,7 @@ _lib = None
 
 PLANE_Z, SPHERE, CYL_Y = 0, 1, 2
 MODE_MC, MODE_EXPECT = 0, 1
-END_APERTURE, END_ARRAY_MISS, END_BOTTOM, END_PATH, END_TIME, END_MAXB = 1, 2, 3, 4, 5, 6
+END_APERTURE, END_ARRAY_MISS, END_BOTTOM, END_PATH, END_TIME, END_MAXB, END_ROUGH = 1, 2, 3, 4, 5, 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -66,7 +66,7 @@ class TraceCfg(C.Structure):
     _fields_ = [("n_tx", C.c_int32), ("angles", C.POINTER(C.c_float)),
                 ("n_rays", C.c_uint64), ("ray_begin", C.c_uint64), ("ray_end", C.c_uint64),
                 ("seed", C.c_uint64), ("max_bounces", C.c_int32), ("max_path", C.c_float),
-                ("mode", C.c_int32)]
+                ("mode", C.c_int32), ("rough_bsdf_only", C.c_int32)]
 
 
 class Arrival(C.Structure):
@@ -111,6 +111,13 @@ def lib():
             L.or_connection.restype = C.c_double
             L.or_connection.argtypes = [C.POINTER(Scene), C.POINTER(Array), dp, C.c_int32,
                                         C.c_double, dp, dp]
+            L.or_ggx_d.restype = C.c_double
+            L.or_ggx_d.argtypes = [C.c_double, C.c_double]
+            L.or_ggx_g1.restype = C.c_double
+            L.or_ggx_g1.argtypes = [C.c_double, C.c_double]
+            L.or_ggx_sample.argtypes = [dp, C.c_double, C.c_double, C.c_double, dp]
+            L.or_rough_eval.restype = C.c_double
+            L.or_rough_eval.argtypes = [dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, dp]
             L.or_grad.restype = C.c_int
             L.or_grad.argtypes = [C.POINTER(Scene), C.POINTER(Array), C.POINTER(TraceCfg), dp, dp, dp, dp, C.c_int]
             _lib = L
@@ -174,7 +181,7 @@ def philox4x32_10(ctr, key):
 
 
 def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_begin=0, ray_end=None,
-          mode=MODE_MC, topo=False, threads=None):
+          mode=MODE_MC, topo=False, threads=None, rough_bsdf_only=False):
     """Trace rays [ray_begin, ray_end) of every transmit.
 
     Returns (arrivals structured array, topology hashes [n_tx, n_sub] or None, stats dict)."""
@@ -185,7 +192,7 @@ def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_beg
     a = make_array(array)
     ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
     cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed),
-                   int(max_bounces), float(max_path), int(mode))
+                   int(max_bounces), float(max_path), int(mode), int(bool(rough_bsdf_only)))
     n_sub = int(ray_end) - int(ray_begin)
     topo_arr = np.zeros((ang.size, n_sub), np.uint64) if topo else None
     threads = threads or (os.cpu_count() or 1)
@@ -215,7 +222,7 @@ def grad(scene, array, angles, n_rays, seed, max_bounces, g_rf, g_q, max_path=0.
     a = make_array(array)
     ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
     cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed), int(max_bounces),
-                   float(max_path), MODE_MC)
+                   float(max_path), MODE_MC, 0)
     gr = np.ascontiguousarray(g_rf, dtype=np.float64)
     gq = np.ascontiguousarray(g_q, dtype=np.float64)
     n_med = len(scene["media"])
@@ -291,6 +298,31 @@ def pulse(tau, f0, n_cycles):
 
 def np_per_m(alpha_db_cm_mhz, f0):
     return lib().or_np_per_m(float(alpha_db_cm_mhz), float(f0))
+
+
+def ggx_d(cos_m, alpha):
+    """Eq. 12 at n.h = cos_m."""
+    return lib().or_ggx_d(float(cos_m), float(alpha))
+
+
+def ggx_g1(c, alpha):
+    return lib().or_ggx_g1(float(c), float(alpha))
+
+
+def ggx_sample(n, alpha, xi1, xi2):
+    nn = np.ascontiguousarray(n, np.float64)
+    m = np.zeros(3)
+    lib().or_ggx_sample(_dp(nn), float(alpha), float(xi1), float(xi2), _dp(m))
+    return m
+
+
+def rough_eval(d, n, o, alpha, c1, Z1, c2, Z2):
+    """(f |o.n| in the amplitude form, solid-angle density of o under the method's sampling)."""
+    dd, nn, oo = (np.ascontiguousarray(v, np.float64) for v in (d, n, o))
+    pdf = np.zeros(1)
+    f = lib().or_rough_eval(_dp(dd), _dp(nn), _dp(oo), float(alpha), float(c1), float(Z1), float(c2), float(Z2),
+                            _dp(pdf))
+    return f, float(pdf[0])
 
 
 def connection(scene, array, p, med, x_e):

@@ -24,6 +24,23 @@
  *  - Pulse (Eq. 14): analytic pulse exp(-tau^2/(2 s^2)) (sin(w tau) - j cos(w tau)),
  *    s = n_cycles/(4 f0), deposited at the exact arrival time, truncated at
  *    |tau| <= tcut_sigmas * s.
+ *  - Rough boundaries (Sec. 2.3, Eq. 12): a boundary takes the larger GGX
+ *    roughness of its two media.  The paper gives only the distribution D; the
+ *    rest follows the microfacet model it cites (Walter et al. 2007): the
+ *    microfacet normal m is drawn with density D(m)(m.n), the smooth branch of
+ *    Eqs. 7-11 is taken about m, and the weight gains |i.m| G / (|i.n| |m.n|)
+ *    with the separable Smith G; a sample leaving on the wrong side of the
+ *    macro surface ends the ray.  In the amplitude convention above the BSDF
+ *    carries the microfacet's r (reflection) or sqrt(1-R) (transmission) where
+ *    the intensity form has F or 1-F.
+ *  - Transducer sampling at rough boundaries (Sec. 2.3: at each boundary
+ *    encounter, before the BSDF is sampled): a connection to a uniformly drawn
+ *    element centre with the BSDF toward it and the element's solid angle
+ *    A cos / D^2 standing for the integral over the element face.  It and the
+ *    direct aperture hits of paths that left a rough vertex (with only smooth
+ *    transmissions before the array) are combined by the balance heuristic,
+ *    the element's density being 1 / (n_el * solid angle); as the roughness
+ *    goes to 0 the direct hits take all the weight and the smooth result returns.
  */
 #include "ur_oracle.h"
 
@@ -152,6 +169,7 @@ typedef struct {
     double K, t_last;           /* pulse half-width; latest useful arrival time (samples) */
     double am, ac;              /* directivity angles (rad) */
     int top, bot;               /* ids of the terminal planes */
+    double *alpha_b;            /* per boundary: GGX roughness (0: smooth) */
 } ctx_t;
 
 static double elem_x(const ctx_t *C, int e) { return C->x0 + (double)e * C->pitch; }
@@ -237,16 +255,17 @@ static int far_medium(const ctx_t *C, int p, const double d[3], const double n_o
     return dot3(d, n_out) > 0.0 ? C->sc->bnd_med[2 * p + 1] : C->sc->bnd_med[2 * p];
 }
 
-/* Connection (secondary) ray: straight from p to the element centre. */
-static double connection(const ctx_t *C, const double p[3], int med, double x_e,
-                         double *t_samples, double *atten)
+/* Connection (secondary) ray: straight from p to the element centre; `skip0` is
+ * the boundary p lies on (-1 for a point inside a medium). */
+static double connection_from(const ctx_t *C, const double p[3], int med, int skip0, double x_e,
+                              double *t_samples, double *atten)
 {
     double o[3] = {p[0], p[1], p[2]};
     double w[3] = {x_e - p[0], -p[1], -p[2]};
     double rem = sqrt(dot3(w, w));
     w[0] /= rem; w[1] /= rem; w[2] /= rem;
     double fac = 1.0, t = 0.0, att = 0.0;
-    int m = med, skip = -1;
+    int m = med, skip = skip0;
     for (int it = 0; it < OR_MAX_CROSS; ++it) {
         double th;
         int hit = nearest_boundary(C, o, w, skip, 0, &th);
@@ -274,6 +293,103 @@ static double connection(const ctx_t *C, const double p[3], int med, double x_e,
     *t_samples = t;
     *atten = att;
     return fac;
+}
+
+static double connection(const ctx_t *C, const double p[3], int med, double x_e,
+                         double *t_samples, double *atten)
+{
+    return connection_from(C, p, med, -1, x_e, t_samples, atten);
+}
+
+/* ------------------------------------------------------ rough boundaries */
+
+/* Eq. 12: GGX density of microfacet normals, cos_m = n.h. */
+double or_ggx_d(double cos_m, double alpha)
+{
+    if (!(cos_m > 0.0)) return 0.0;
+    double a2 = alpha * alpha;
+    double k = cos_m * cos_m * (a2 - 1.0) + 1.0;
+    return a2 / (OR_PI * k * k);
+}
+
+/* Smith masking of one direction for GGX (Walter et al. 2007, Eq. 34);
+ * c = cosine between that direction and the macro normal (c > 0). */
+double or_ggx_g1(double c, double alpha)
+{
+    double tan2 = (1.0 - c * c) / (c * c);
+    return 2.0 / (1.0 + sqrt(1.0 + alpha * alpha * tan2));
+}
+
+/* Orthonormal basis (t1, t2, n) around a unit n (Duff et al., "Building an
+ * orthonormal basis, revisited", JCGT 6(1), 2017). */
+static void onb(const double n[3], double t1[3], double t2[3])
+{
+    double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n[2]);
+    double b = n[0] * n[1] * a;
+    t1[0] = 1.0 + sg * n[0] * n[0] * a; t1[1] = sg * b; t1[2] = -sg * n[0];
+    t2[0] = b; t2[1] = sg + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+/* Microfacet normal with density D(m)(m.n): tan^2(theta_m) = alpha^2 xi1 / (1 - xi1),
+ * phi_m = 2 pi xi2 (the inversion of its CDF, Walter et al. 2007, Eqs. 35-36). */
+void or_ggx_sample(const double n[3], double alpha, double xi1, double xi2, double m[3])
+{
+    double tan2 = alpha * alpha * xi1 / (1.0 - xi1);
+    double ct = 1.0 / sqrt(1.0 + tan2);
+    double st = sqrt(tan2) * ct;
+    double ph = 2.0 * OR_PI * xi2;
+    double t1[3], t2[3];
+    onb(n, t1, t2);
+    for (int q = 0; q < 3; ++q) m[q] = st * cos(ph) * t1[q] + st * sin(ph) * t2[q] + ct * n[q];
+}
+
+/* Scattering of a rough boundary from incident direction d (unit, travelling
+ * toward the surface; n the unit macro normal facing the incident side) into
+ * o: returns f(i, o) |o.n| in the amplitude form and writes the solid-angle
+ * density *pdf with which microfacet sampling and the reflect-if-y < R branch
+ * produce o.  Reflection (o.n > 0): half vector h = (i + o)/|i + o|,
+ * |dw_h/dw_o| = 1/(4 |o.h|), coefficient r(h), branch probability R(h) (1 on
+ * total internal reflection).  Transmission (o.n < 0): h along -(i/c1 + o/c2),
+ * |dw_h/dw_o| = |o.h| / (c2^2 (i.h/c1 + o.h/c2)^2), coefficient sqrt(1-R(h)),
+ * branch probability 1 - R(h).  f |o.n| = coef G D(h) |i.h| |dw_h/dw_o| / |i.n|. */
+double or_rough_eval(const double d[3], const double n[3], const double o[3], double alpha,
+                     double c1, double Z1, double c2, double Z2, double *pdf)
+{
+    *pdf = 0.0;
+    double i[3] = {-d[0], -d[1], -d[2]};
+    double cos_i = dot3(i, n), cos_o = dot3(o, n);
+    if (!(cos_i > 0.0) || cos_o == 0.0) return 0.0;
+    double h[3], jac, coef, pb;
+    if (cos_o > 0.0) {
+        for (int q = 0; q < 3; ++q) h[q] = i[q] + o[q];
+        normalize3(h);
+        double ih = dot3(i, h);
+        if (!(dot3(h, n) > 0.0) || !(ih > 0.0)) return 0.0;
+        double dr[3], dt[3], r, R;
+        int tir = or_interface(d, h, c1, Z1, c2, Z2, dr, dt, &r, &R);
+        coef = tir ? 1.0 : r;
+        pb = tir ? 1.0 : R;
+        jac = 1.0 / (4.0 * dot3(o, h));
+    } else {
+        for (int q = 0; q < 3; ++q) h[q] = -(i[q] / c1 + o[q] / c2);
+        normalize3(h);
+        if (dot3(h, n) < 0.0) { h[0] = -h[0]; h[1] = -h[1]; h[2] = -h[2]; }
+        double ih = dot3(i, h), oh = dot3(o, h);
+        if (!(dot3(h, n) > 0.0) || !(ih > 0.0) || !(oh < 0.0)) return 0.0;
+        double dr[3], dt[3], r, R;
+        if (or_interface(d, h, c1, Z1, c2, Z2, dr, dt, &r, &R)) return 0.0;
+        double den = ih / c1 + oh / c2;
+        if (den * den < 1e-300) return 0.0;
+        coef = sqrt(1.0 - R);
+        pb = 1.0 - R;
+        jac = -oh / (c2 * c2 * den * den);
+    }
+    double hn = dot3(h, n);
+    double D = or_ggx_d(hn, alpha);
+    double G = or_ggx_g1(cos_i, alpha) * or_ggx_g1(fabs(cos_o), alpha);
+    *pdf = D * hn * jac * pb;
+    return coef * G * D * dot3(i, h) * jac / cos_i;
 }
 
 /* ------------------------------------------------------- arrival buffers */
@@ -373,6 +489,83 @@ static void segment_scatterers(const ctx_t *C, ray_job *J, const double o[3], co
     }
 }
 
+/* Transducer sampling at a rough vertex p on boundary `hit` (d incident, n the
+ * normal facing the incident side; med / m2 the near / far media): connection to
+ * a uniformly drawn element centre, balance-heuristic weight against the BSDF
+ * sampling of the same direction. */
+static void rough_nee(const ctx_t *C, ray_job *J, const double p[3], const double d[3], const double n[3],
+                      int hit, int med, int m2, double t, double w, int b)
+{
+    int n_el = C->ar->n_el;
+    uint32_t x[4];
+    draw(C->cfg->seed, J->i, (uint32_t)J->k, 4u | ((uint32_t)b << 8), 0u, x);
+    int e = (int)((((uint64_t)(x[0] >> 8)) * (uint64_t)n_el) >> 24);
+    double xe = elem_x(C, e);
+    double v[3] = {xe - p[0], -p[1], -p[2]};
+    double D = sqrt(dot3(v, v));
+    double o[3] = {v[0] / D, v[1] / D, v[2] / D};
+    double cos_e = p[2] / D;                               /* at the element, to its normal */
+    double fd = or_directivity(acos(cos_e), C->am, C->ac);  /* Eq. 13 */
+    if (!(fd > 0.0)) return;
+    double pdf_bsdf;
+    double f = or_rough_eval(d, n, o, C->alpha_b[hit], C->c[med], C->Z[med], C->c[m2], C->Z[m2], &pdf_bsdf);
+    if (!(f > 0.0)) return;
+    J->st.connections++;
+    double tc, ac;
+    double fac = connection_from(C, p, dot3(o, n) > 0.0 ? med : m2, hit, xe, &tc, &ac);
+    if (fac == 0.0) return;
+    double t_arr = t + tc;
+    if (t_arr > C->t_last) return;
+    double omega = C->pitch * C->H * cos_e / (D * D);    /* element solid angle seen from p */
+    double p_nee = 1.0 / ((double)n_el * omega);
+    double amp = w * f * fd * fac * exp(-ac) / (p_nee + pdf_bsdf);
+    push(J->buf, J->k, e, J->i, 0x80000000u | ((uint32_t)b << 24) | (uint32_t)(hit + 1), t_arr, amp, J->seq++);
+    J->st.arrivals++;
+}
+
+/* BSDF sampling at a rough vertex: microfacet normal, smooth branch about it,
+ * Walter's weight.  Updates d, w, med; writes the branch (0 reflect, 1 transmit,
+ * 2 total internal reflection) and the solid-angle density of the new direction.
+ * Returns 0, or OR_END_ROUGH if the sample is not admissible. */
+static int rough_scatter(const ctx_t *C, ray_job *J, double d[3], const double n[3], double alpha,
+                         int *med, int m2, double *w, int b, int *branch, double *pdf)
+{
+    double cos_i = -dot3(d, n);
+    uint32_t x[4];
+    draw(C->cfg->seed, J->i, (uint32_t)J->k, 3u | ((uint32_t)b << 8), 0u, x);
+    double m[3];
+    or_ggx_sample(n, alpha, u24(x[0]), u24(x[1]), m);
+    double c_im = -dot3(d, m), mn = dot3(m, n);
+    if (!(c_im > 0.0)) return OR_END_ROUGH;
+    double c1 = C->c[*med], c2 = C->c[m2];
+    double dr[3], dt[3], r, R;
+    int tir = or_interface(d, m, c1, C->Z[*med], c2, C->Z[m2], dr, dt, &r, &R);
+    double o[3], fac, pb, jac;
+    int to_far = 0;
+    if (tir) {
+        *branch = 2; memcpy(o, dr, sizeof o); fac = 1.0; pb = 1.0; jac = 1.0 / (4.0 * c_im);
+    } else {
+        uint32_t y[4];
+        draw(C->cfg->seed, J->i, (uint32_t)J->k, 1u | ((uint32_t)b << 8), 0u, y);
+        if (u24(y[0]) < R) {                                   /* reflect if y < A_r^2 */
+            *branch = 0; memcpy(o, dr, sizeof o); fac = r / R; pb = R; jac = 1.0 / (4.0 * c_im);
+        } else {
+            *branch = 1; memcpy(o, dt, sizeof o); fac = sqrt(1.0 - R) / (1.0 - R); pb = 1.0 - R;
+            double om = dot3(o, m), den = c_im / c1 + om / c2;
+            jac = -om / (c2 * c2 * den * den);
+            to_far = 1;
+        }
+    }
+    double on = dot3(o, n);
+    if (to_far ? !(on < 0.0) : !(on > 0.0)) return OR_END_ROUGH;
+    double G = or_ggx_g1(cos_i, alpha) * or_ggx_g1(fabs(on), alpha);
+    *w *= fac * c_im * G / (cos_i * mn);
+    *pdf = or_ggx_d(mn, alpha) * mn * jac * pb;
+    memcpy(d, o, sizeof o);
+    if (to_far) *med = m2;
+    return 0;
+}
+
 /* ------------------------------------------------------------ primary path */
 
 /* Follows one primary ray (and, in expectation mode, both branches of every
@@ -383,6 +576,8 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
     const or_scene *sc = C->sc;
     const or_array *ar = C->ar;
     const or_trace_cfg *cfg = C->cfg;
+    int mis = 0;                  /* the path left a rough vertex with smooth transmissions since */
+    double mis_p[3] = {0.0, 0.0, 0.0}, mis_pdf = 0.0;
     for (int guard = 0; guard < OR_MAX_SEG; ++guard) {
         double th;
         int hit = nearest_boundary(C, o, d, prev, 1, &th);
@@ -405,7 +600,14 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
                 if (e > ar->n_el - 1) e = ar->n_el - 1;
                 double fd = or_directivity(acos(-d[2]), C->am, C->ac);
                 if (fd > 0.0 && t <= C->t_last) {
-                    push(J->buf, J->k, e, J->i, 0x80000000u | ((uint32_t)b << 24), t, w * fd, J->seq++);
+                    double wa = w * fd;
+                    if (mis && !cfg->rough_bsdf_only) {   /* balance heuristic against transducer sampling */
+                        double v[3] = {elem_x(C, e) - mis_p[0], -mis_p[1], -mis_p[2]};
+                        double D2 = dot3(v, v);
+                        double omega = C->pitch * C->H * (mis_p[2] / sqrt(D2)) / D2;
+                        if (omega > 0.0) wa *= mis_pdf / (mis_pdf + 1.0 / ((double)ar->n_el * omega));
+                    }
+                    push(J->buf, J->k, e, J->i, 0x80000000u | ((uint32_t)b << 24), t, wa, J->seq++);
                     J->st.arrivals++;
                 }
                 return OR_END_APERTURE;
@@ -420,6 +622,23 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
         double n_out[3], dr[3], dt[3], r, R;
         outward_normal(C, hit, o, n_out);
         int m2 = far_medium(C, hit, d, n_out);
+        if (C->alpha_b[hit] > 0.0) {   /* rough boundary (Eq. 12) */
+            double nn[3] = {n_out[0], n_out[1], n_out[2]};
+            if (dot3(d, nn) > 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+            if (!cfg->rough_bsdf_only) rough_nee(C, J, o, d, nn, hit, med, m2, t, w, b);
+            J->st.interactions++;
+            int branch = 0;
+            double pdf = 0.0;
+            int end = rough_scatter(C, J, d, nn, C->alpha_b[hit], &med, m2, &w, b, &branch, &pdf);
+            if (end) return end;
+            mis = 1;
+            memcpy(mis_p, o, sizeof mis_p);
+            mis_pdf = pdf;
+            *h = fnv(*h, 0x10000u | ((uint32_t)hit << 4) | (uint32_t)branch);
+            b += 1;
+            prev = hit;
+            continue;
+        }
         int tir = or_interface(d, n_out, C->c[med], C->Z[med], C->c[m2], C->Z[m2], dr, dt, &r, &R);
         /* the branch is drawn with the sampling media (the same media unless overridden) */
         double drs[3], dts[3], rs = r, Rs = R;
@@ -460,6 +679,7 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
             memcpy(d, dt, sizeof dt);
             med = m2;
         }
+        if (branch != 1) mis = 0;   /* a smooth reflection: transducer sampling cannot produce this path */
         *h = fnv(*h, 0x10000u | ((uint32_t)hit << 4) | (uint32_t)branch);
         b += 1;
         prev = hit;
@@ -527,6 +747,11 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
     C->ac = (double)ar->alpha_c_deg * OR_PI / 180.0;
     C->top = sc->n_bnd;
     C->bot = sc->n_bnd + 1;
+    C->alpha_b = (double *)malloc(sizeof(double) * (size_t)(sc->n_bnd > 0 ? sc->n_bnd : 1));
+    for (int p = 0; p < sc->n_bnd; ++p) {
+        double a0 = sc->med[4 * sc->bnd_med[2 * p] + 3], a1 = sc->med[4 * sc->bnd_med[2 * p + 1] + 3];
+        C->alpha_b[p] = a0 > a1 ? a0 : a1;
+    }
     return 0;
 }
 
@@ -534,6 +759,14 @@ static void teardown(ctx_t *C)
 {
     free(C->c);
     free(C->delay);
+    free(C->alpha_b);
+}
+
+static int scene_is_rough(const or_scene *sc)
+{
+    for (int m = 0; m < sc->n_med; ++m)
+        if (sc->med[4 * m + 3] != 0.0f) return 1;
+    return 0;
 }
 
 int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg,
@@ -543,6 +776,10 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
         cfg->n_rays == 0 || cfg->n_rays > 0xFFFFFFFFull || ar->n_el <= 0 || cfg->n_tx <= 0 ||
         cfg->max_bounces < 0 || cfg->max_bounces > 127 || sc->n_scat > (1 << 24))
         return -1;
+    for (int m = 0; m < sc->n_med; ++m)
+        if (!(sc->med[4 * m + 3] >= 0.0f && sc->med[4 * m + 3] <= 4.0f)) return -1;
+    /* rough boundaries: Monte Carlo mode with the media deciding their own branches */
+    if (scene_is_rough(sc) && (cfg->mode != OR_MODE_MC || sc->med_sampling)) return -1;
     ctx_t C;
     setup(&C, sc, ar, cfg);
     uint64_t n_sub = cfg->ray_end - cfg->ray_begin;
@@ -1022,7 +1259,7 @@ int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, con
             const double *g_q, double *grad_media, double *grad_amp, int n_threads)
 {
     if (!sc || !ar || !cfg || !g_rf || !g_q || !grad_media || sc->n_med > 4 || cfg->mode != OR_MODE_MC ||
-        cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling)
+        cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling || scene_is_rough(sc))
         return -1;
     ctx_t C;
     setup(&C, sc, ar, cfg);

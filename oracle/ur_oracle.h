@@ -30,11 +30,12 @@ extern "C" {
 enum { OR_PLANE_Z = 0, OR_SPHERE = 1, OR_CYL_Y = 2 };
 enum { OR_MODE_MC = 0, OR_MODE_EXPECT = 1 };
 enum { OR_END_APERTURE = 1, OR_END_ARRAY_MISS = 2, OR_END_BOTTOM = 3,
-       OR_END_PATH = 4, OR_END_TIME = 5, OR_END_MAXB = 6 };
+       OR_END_PATH = 4, OR_END_TIME = 5, OR_END_MAXB = 6, OR_END_ROUGH = 7 };
 
 typedef struct {
     int32_t n_med;
-    const float *med;        /* [n_med][4]: c (m/s), Z (MRayl), alpha (dB/cm/MHz), roughness (unused) */
+    const float *med;        /* [n_med][4]: c (m/s), Z (MRayl), alpha (dB/cm/MHz), GGX roughness in
+                                [0, 4] (a boundary takes the larger of its two media; 0: smooth) */
     int32_t n_bnd;
     const int32_t *bnd_kind; /* OR_PLANE_Z: z = p0.  OR_SPHERE: centre p0..p2, radius p3.
                                 OR_CYL_Y: axis parallel to y through (x = p0, z = p1), radius p2 */
@@ -65,13 +66,16 @@ typedef struct {
     uint64_t seed;
     int32_t max_bounces;
     float max_path;          /* m */
-    int32_t mode;            /* OR_MODE_MC or OR_MODE_EXPECT */
+    int32_t mode;            /* OR_MODE_MC or OR_MODE_EXPECT (smooth scenes only) */
+    int32_t rough_bsdf_only; /* 0: transducer sampling at rough boundaries, balance heuristic with the
+                                direct aperture hits (the method); 1: BSDF sampling alone (for tests) */
 } or_trace_cfg;
 
 typedef struct {
     int32_t tx, el;
-    uint32_t ray, event;     /* event: bit31 = aperture arrival, bits 24..30 = segment index b,
-                                bits 0..23 = scatterer index (scatter arrivals) */
+    uint32_t ray, event;     /* event: bits 24..30 = segment index b; scatter arrivals: bits 0..23 =
+                                scatterer index; aperture arrivals: bit31 set, bits 0..23 = 0;
+                                transducer sampling at rough boundary p: bit31 set, bits 0..23 = p + 1 */
     double t;                /* arrival time in samples */
     double amp;
 } or_arrival;
@@ -125,6 +129,23 @@ int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, con
 int or_interface(const double d[3], const double n[3], double c1, double Z1,
                  double c2, double Z2, double d_r[3], double d_t[3],
                  double *r, double *R);
+
+/* Eq. 12: GGX density of microfacet normals at cos_m = n.h (0 for cos_m <= 0). */
+double or_ggx_d(double cos_m, double alpha);
+
+/* Smith masking G1 of GGX for a direction at cosine c > 0 to the macro normal. */
+double or_ggx_g1(double c, double alpha);
+
+/* Microfacet normal m with density D(m)(m.n) about the unit normal n, from two
+ * uniforms in [0, 1). */
+void or_ggx_sample(const double n[3], double alpha, double xi1, double xi2, double m[3]);
+
+/* Rough-boundary scattering from incident direction d (unit; n = unit macro
+ * normal on the incident side) into direction o: returns f(i, o) |o.n| in the
+ * amplitude form, writes the solid-angle density of o under the method's
+ * sampling (microfacet normal, then the reflect-if-y < R branch). */
+double or_rough_eval(const double d[3], const double n[3], const double o[3], double alpha,
+                     double c1, double Z1, double c2, double Z2, double *pdf);
 
 /* Receive directivity Eq. 13; alpha in radians. */
 double or_directivity(double alpha, double alpha_m, double alpha_c);
