@@ -57,8 +57,14 @@ enum { UR_PLANE_Z = 0, UR_SPHERE = 1, UR_CYL_Y = 2 };
 
 /* One tissue type.  c: sound speed (m/s); Z: acoustic impedance (MRayl);
  * alpha: amplitude attenuation (dB/cm/MHz, applied at the array's f0);
- * roughness: reserved for the GGX microfacet boundaries of Sec. 2.3 (Eq. 12),
- * must be 0 (smooth boundaries). */
+ * roughness: GGX parameter of the microfacet boundaries of Sec. 2.3 (Eq. 12),
+ * in [0, 4]; a boundary takes the larger roughness of its two media, 0 keeps it
+ * smooth (specular).  At a rough boundary the microfacet normal is sampled from
+ * D(m)(m.n) and the smooth branch is taken about it (Walter et al. 2007
+ * weights), and a secondary ray goes to a random element centre; these returns
+ * and the direct aperture hits of the same paths are combined by the balance
+ * heuristic (event word bit 31 | b << 24 | boundary + 1).  The adjoint and frozen
+ * sampling media need smooth boundaries. */
 typedef struct {
     float c, Z, alpha_db_cm_mhz, roughness;
 } ur_medium;
@@ -100,11 +106,14 @@ typedef struct {
 
 /* Per-arrival and per-path records for verification (all device pointers,
  * each array holds `capacity` entries).  An arrival's time in samples is
- * t_hi + t_lo; row = transmit * n_el + element; event: bit 31 set for a
- * primary ray crossing the aperture, bits 24..30 the number of boundary
- * interactions before the event, bits 0..23 the scatterer index for
- * scatterer events.  path_hash (nullable, [n_tx][n_rays]) is a 64-bit FNV-1a
- * hash of each primary path's interaction sequence and termination reason. */
+ * t_hi + t_lo; row = transmit * n_el + element; event: bits 24..30 the number
+ * of boundary interactions before the event, and bit 31 set with bits 0..23 = 0
+ * for a primary ray crossing the aperture, bit 31 clear with bits 0..23 the
+ * scatterer index for scatterer events, bit 31 set with bits 0..23 = boundary
+ * index + 1 for the secondary ray of a rough boundary.  path_hash (nullable,
+ * [n_tx][n_rays]) is a 64-bit FNV-1a hash of each primary path's interaction
+ * sequence and termination reason (7: a rough-boundary sample left on the wrong
+ * side of the surface). */
 typedef struct {
     uint64_t capacity;
     uint64_t count;          /* out: arrivals produced */

@@ -367,7 +367,7 @@ void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const 
     for (const ur_medium &m : M) {
         if (!(m.c > 0.f) || !(m.Z > 0.f) || !(m.alpha_db_cm_mhz >= 0.f) || !std::isfinite(m.c) || !std::isfinite(m.Z))
             fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0");
-        if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "rough (GGX) boundaries are not supported: roughness must be 0");
+        if (!(m.roughness >= 0.f && m.roughness <= 4.f)) fail(UR_ERR_INVALID_ARG, "roughness must be in [0, 4]");
     }
     std::vector<ur_boundary> Bv(bnd, bnd + n_bnd);
     for (const ur_boundary &b : Bv) {
@@ -425,6 +425,7 @@ void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
         S.bnd[b].kind = sd.bnd[b].kind;
         S.bnd[b].med_neg = sd.bnd[b].med_neg;
         S.bnd[b].med_pos = sd.bnd[b].med_pos;
+        S.bnd[b].alpha = std::max(sd.media[sd.bnd[b].med_neg].roughness, sd.media[sd.bnd[b].med_pos].roughness);
         for (int q = 0; q < 4; ++q) S.bnd[b].p[q] = sd.bnd[b].p[q];
     }
     S.n_scat = sd.n_scat;
@@ -813,10 +814,15 @@ ur_status ur_scene_set_media(ur_ctx *c, int slot, const ur_medium *media, int n_
         if (!media || n_med != (int)sd.media.size()) fail(UR_ERR_INVALID_ARG, "n_med must match the uploaded scene");
         std::vector<ur_medium> M(media, media + n_med), Ms = M;
         if (sampling) Ms.assign(sampling, sampling + n_med);
-        for (int q = 0; q < n_med; ++q)
+        bool rough = false;
+        for (int q = 0; q < n_med; ++q) {
             for (const ur_medium *m : {&M[q], &Ms[q]})
-                if (!(m->c > 0.f) || !(m->Z > 0.f) || !(m->alpha_db_cm_mhz >= 0.f) || m->roughness != 0.f)
-                    fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0, roughness 0");
+                if (!(m->c > 0.f) || !(m->Z > 0.f) || !(m->alpha_db_cm_mhz >= 0.f) ||
+                    !(m->roughness >= 0.f && m->roughness <= 4.f))
+                    fail(UR_ERR_INVALID_ARG, "media need c > 0, Z > 0, alpha >= 0, roughness in [0, 4]");
+            rough = rough || M[q].roughness != 0.f;
+        }
+        if (sampling && rough) fail(UR_ERR_INVALID_ARG, "frozen sampling media need smooth boundaries");
         sd.media = M;
         sd.sampling = Ms;
         sd.version = ++c->versions;
@@ -1021,6 +1027,8 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
         const SceneData &sd = c->scenes[0];
         const int n_med = (int)sd.media.size();
         if (n_med > ur::kAdjMed) fail(UR_ERR_INVALID_ARG, "the adjoint supports scenes with at most 4 media");
+        for (const ur_medium &m : sd.media)
+            if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports smooth boundaries only");
         prepare_transmits(c);
         const int n_tx = (int)c->angles.size();
         std::vector<ur_batch_item> items(n_tx);

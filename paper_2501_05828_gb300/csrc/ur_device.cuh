@@ -23,7 +23,7 @@ constexpr uint64_t kFnvOffset = 0xcbf29ce484222325ull;
 constexpr uint64_t kFnvPrime = 0x100000001b3ull;
 
 enum { kPlaneZ = 0, kSphere = 1, kCylY = 2 };
-enum { kEndAperture = 1, kEndArrayMiss = 2, kEndBottom = 3, kEndPath = 4, kEndTime = 5, kEndMaxB = 6 };
+enum { kEndAperture = 1, kEndArrayMiss = 2, kEndBottom = 3, kEndPath = 4, kEndTime = 5, kEndMaxB = 6, kEndRough = 7 };
 
 // ---------------------------------------------------------------- float-float
 // A value hi + lo with |lo| <= ulp(hi)/2 (Dekker / Knuth error-free transforms).
@@ -124,7 +124,8 @@ struct Medium {
 };
 
 struct Bnd {
-    int kind, med_neg, med_pos, pad;
+    int kind, med_neg, med_pos;
+    float alpha;            // GGX roughness (Eq. 12): the larger of the two media's; 0 = smooth
     float p[4];
 };
 

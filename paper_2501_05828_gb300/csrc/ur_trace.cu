@@ -10,15 +10,16 @@ namespace {
 
 // Straight connection ray from p to the element centre (x_e, 0, 0): product of
 // sqrt(1 - R) over the boundaries it crosses (0 if one reflects totally),
-// travel time (samples) and attenuation exponent.
-__device__ float connection(const SceneP &S, float3 p, int med, float xe, ff &t_conn, float &att) {
+// travel time (samples) and attenuation exponent.  skip0: the boundary p lies
+// on (-1 inside a medium).
+__device__ float connection(const SceneP &S, float3 p, int med, int skip0, float xe, ff &t_conn, float &att) {
     float3 o = p;
     float3 w = make_float3(xe - p.x, -p.y, -p.z);
     float rem = sqrtf(dot3(w, w));
     w = make_float3(w.x / rem, w.y / rem, w.z / rem);
     float fac = 1.f, a = 0.f;
     ff t = {0.f, 0.f};
-    int m = med, skip = -1;
+    int m = med, skip = skip0;
     for (int it = 0; it < kMaxCross; ++it) {
         float th;
         const int hit = nearest(S, o, w, skip, false, th);
@@ -47,6 +48,89 @@ __device__ float connection(const SceneP &S, float3 p, int med, float xe, ff &t_
     t_conn = t;
     att = a;
     return fac;
+}
+
+// ---------------------------------------------------------------- rough boundaries (Eq. 12)
+constexpr float kPiF = 3.14159265358979f;
+
+// GGX density of microfacet normals at c = n.h, a2 = alpha^2; the denominator
+// written as (1 - c^2) + a2 c^2 stays positive when c rounds to 1.
+__device__ __forceinline__ float ggx_d(float c, float a2) {
+    if (!(c > 0.f)) return 0.f;
+    const float c2 = c * c;
+    const float k = fmaf(a2, c2, 1.f - c2);
+    return a2 / (kPiF * k * k);
+}
+
+// Smith masking of one direction at cosine c to the macro normal.
+__device__ __forceinline__ float ggx_g1(float c, float a2) {
+    const float t2 = (1.f - c * c) / (c * c);
+    return 2.f / (1.f + sqrtf(1.f + a2 * t2));
+}
+
+// Microfacet normal with density D(m)(m.n) about unit n: tan^2 theta = alpha^2 xi1 / (1 - xi1),
+// phi = 2 pi xi2, in the tangent frame of Duff et al. (JCGT 2017).
+__device__ __forceinline__ float3 ggx_sample(float3 n, float a2, float xi1, float xi2, float &ct) {
+    const float tan2 = a2 * xi1 / (1.f - xi1);
+    ct = 1.f / sqrtf(1.f + tan2);
+    const float st = sqrtf(tan2) * ct;
+    float sp, cp;
+    sincospif(2.f * xi2, &sp, &cp);
+    const float sg = n.z >= 0.f ? 1.f : -1.f;
+    const float a = -1.f / (sg + n.z);
+    const float b = n.x * n.y * a;
+    const float3 t1 = make_float3(1.f + sg * n.x * n.x * a, sg * b, -sg * n.x);
+    const float3 t2 = make_float3(b, sg + n.y * n.y * a, -n.y);
+    return (st * cp) * t1 + (st * sp) * t2 + ct * n;
+}
+
+// Transmitted intensity fraction 1 - r^2 of the fluid-fluid interface, written
+// without the cancellation of 1 - r^2 near the critical angle.
+__device__ __forceinline__ float transmitted(float cos_i, float cos_t, float Z1, float Z2) {
+    const float s = fmaf(Z2, cos_i, Z1 * cos_t);
+    return 4.f * Z1 * Z2 * cos_i * cos_t / (s * s);
+}
+
+// Scattering of a rough boundary from incident direction d (n: unit macro normal
+// on the incident side) into o: returns f |o.n| in the amplitude form (r or
+// sqrt(1 - R) of the half-vector microfacet) and the solid-angle density of o
+// under microfacet sampling and the reflect-if-y < R branch.
+__device__ float rough_eval(float3 d, float3 n, float3 o, float a2, const Medium &M1, const Medium &M2,
+                           float &pdf) {
+    pdf = 0.f;
+    const float3 i = make_float3(-d.x, -d.y, -d.z);
+    const float cos_i = dot3(i, n), cos_o = dot3(o, n);
+    if (!(cos_i > 0.f) || cos_o == 0.f) return 0.f;
+    float3 h;
+    float coef, pb, jac;
+    if (cos_o > 0.f) {
+        h = unit3(i + o);
+        const float ih = dot3(i, h);
+        if (!(dot3(h, n) > 0.f) || !(ih > 0.f)) return 0.f;
+        float r, ct;
+        const bool ok = fresnel(ih, M1.c, M1.Z, M2.c, M2.Z, r, ct);
+        coef = ok ? r : 1.f;
+        pb = ok ? r * r : 1.f;
+        jac = 0.25f / dot3(o, h);
+    } else {
+        const float eta = M2.c / M1.c;
+        h = unit3(eta * i + o);   // along i/c1 + o/c2
+        if (dot3(h, n) < 0.f) h = make_float3(-h.x, -h.y, -h.z);
+        const float ih = dot3(i, h), oh = dot3(o, h);
+        if (!(dot3(h, n) > 0.f) || !(ih > 0.f) || !(oh < 0.f)) return 0.f;
+        float r, ct;
+        if (!fresnel(ih, M1.c, M1.Z, M2.c, M2.Z, r, ct)) return 0.f;
+        const float den = fmaf(eta, ih, oh);   // c2 (i.h / c1 + o.h / c2)
+        if (!(den * den > 1e-30f)) return 0.f;
+        pb = transmitted(ih, ct, M1.Z, M2.Z);
+        coef = sqrtf(pb);
+        jac = -oh / (den * den);
+    }
+    const float hn = dot3(h, n);
+    const float D = ggx_d(hn, a2);
+    const float G = ggx_g1(cos_i, a2) * ggx_g1(fabsf(cos_o), a2);
+    pdf = D * hn * jac * pb;
+    return coef * G * D * dot3(i, h) * jac / cos_i;
 }
 
 // Warp-aggregated append to the arrival queue (one atomic per converged group);
@@ -97,6 +181,11 @@ struct Lane {
     int cx, cy, cz, sx, sy, sz;
     float tmx, tmy, tmz, tdx, tdy, tdz, t_enter, t_end;
     int state;
+    // rough boundaries: the path left a rough vertex mp with direction density mpdf and has
+    // crossed only by transmission since (its aperture hit takes a balance-heuristic weight)
+    bool mis;
+    float3 mp;
+    float mpdf;
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
@@ -186,13 +275,103 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
     R.item = item;
     R.stream = IT.stream;
     R.h = kFnvOffset;
+    R.mis = false;
     start_segment(P, R, cn);
+}
+
+// Secondary ray of a rough vertex to a uniformly drawn element centre, weighted
+// against BSDF sampling of the same direction by the balance heuristic.
+template <bool DBG, bool REC>
+__device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R, float3 n, int m2, float a2,
+                                 Counters &cn) {
+    const uint4 x = philox(make_uint4(R.i, R.stream, 4u | ((uint32_t)R.b << 8), 0u), P.key);
+    const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
+    const float xe = P.x_first + (float)e * P.pitch;
+    const float3 v = make_float3(xe - R.o.x, -R.o.y, -R.o.z);
+    const float D = sqrtf(dot3(v, v));
+    const float3 o = make_float3(v.x / D, v.y / D, v.z / D);
+    const float cos_e = R.o.z / D;
+    const float fd = directivity(P, cos_e);
+    if (!(fd > 0.f)) return;
+    const Medium &M = S.med[R.med], &M2 = S.med[m2];
+    float pdf;
+    const float f = rough_eval(R.d, n, o, a2, M, M2, pdf);
+    if (!(f > 0.f)) return;
+    cn.connections++;
+    ff tc;
+    float att;
+    const float fac = connection(S, R.o, dot3(o, n) > 0.f ? R.med : m2, R.hit, xe, tc, att);
+    if (fac == 0.f) return;
+    const ff ta = ff_add(R.t, tc);
+    if (ff_gt(ta, P.t_last)) return;
+    const float omega = P.pitch * P.H * cos_e / (D * D);   // element solid angle seen from the vertex
+    const float p_nee = 1.f / ((float)P.n_el * omega);
+    const float amp = R.w * f * fd * fac * expf(-att) / (p_nee + pdf);
+    emit<DBG, REC>(P, R.item * (uint32_t)P.n_el + e, ta, amp, R.i,
+                   0x80000000u | ((uint32_t)R.b << 24) | (uint32_t)(R.hit + 1));
+    cn.arrivals++;
+}
+
+// Microfacet sampling at a rough vertex: normal from D(m)(m.n), the smooth branch
+// about it, weight |i.m| G / (|i.n| |m.n|).  Returns false if the sample is not
+// admissible (back-facing microfacet or a direction on the wrong side).
+__device__ bool rough_scatter(const TraceP &P, const SceneP &S, Lane &R, float3 n, int m2, float a2,
+                              uint32_t &branch) {
+    const float cos_i = -dot3(n, R.d);
+    const uint4 x = philox(make_uint4(R.i, R.stream, 3u | ((uint32_t)R.b << 8), 0u), P.key);
+    float mn;   // m.n, the sampled cosine (exact where a dot product would cancel for grazing m)
+    const float3 m = ggx_sample(n, a2, u24(x.x), u24(x.y), mn);
+    const float c_im = -dot3(R.d, m);
+    if (!(c_im > 0.f)) return false;
+    const Medium &M = S.med[R.med], &M2 = S.med[m2];
+    float r, cos_t;
+    const bool tir = !fresnel(c_im, M.c, M.Z, M2.c, M2.Z, r, cos_t);
+    float3 o;
+    float fac, pb, jac;
+    bool far = false;
+    if (tir) {
+        branch = 2;
+        o = unit3(R.d + (2.f * c_im) * m);
+        fac = 1.f;
+        pb = 1.f;
+        jac = 0.25f / c_im;
+    } else {
+        const uint4 y = philox(make_uint4(R.i, R.stream, 1u | ((uint32_t)R.b << 8), 0u), P.key);
+        const float Rs = r * r;
+        if (u24(y.x) < Rs) {
+            branch = 0;
+            o = unit3(R.d + (2.f * c_im) * m);
+            fac = r / Rs;
+            pb = Rs;
+            jac = 0.25f / c_im;
+        } else {
+            branch = 1;
+            const float eta = M2.c / M.c;
+            o = unit3(eta * R.d + (eta * c_im - cos_t) * m);
+            pb = transmitted(c_im, cos_t, M.Z, M2.Z);
+            fac = 1.f / sqrtf(pb);
+            const float om = dot3(o, m);
+            const float den = fmaf(eta, c_im, om);
+            jac = -om / (den * den);
+            far = true;
+        }
+    }
+    const float on = dot3(o, n);
+    if (far ? !(on < 0.f) : !(on > 0.f)) return false;
+    const float G = ggx_g1(cos_i, a2) * ggx_g1(fabsf(on), a2);
+    R.w *= fac * c_im * G / (cos_i * mn);
+    R.mis = true;
+    R.mp = R.o;
+    R.mpdf = ggx_d(mn, a2) * mn * jac * pb;
+    R.d = o;
+    if (far) R.med = m2;
+    return true;
 }
 
 // End of a segment: time of flight and attenuation along it, then the array
 // plane (aperture return), the absorbing bottom, the time window, the bounce
 // budget, or a boundary interaction (Eqs. 7-11) and the next segment.
-template <bool DBG, bool SPLIT, bool REC>
+template <bool DBG, bool SPLIT, bool REC, bool ROUGH>
 __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S[R.scene];
     const Medium &M = S.med[R.med];
@@ -213,7 +392,14 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
             if (el > P.n_el - 1) el = P.n_el - 1;
             const float fd = directivity(P, -R.d.z);
             if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
-                emit<DBG, REC>(P, R.item * (uint32_t)P.n_el + (uint32_t)el, R.t, R.w * fd, R.i,
+                float wa = R.w * fd;
+                if (ROUGH && R.mis) {   // balance heuristic against the rough vertex's secondary ray
+                    const float3 v = make_float3(P.x_first + (float)el * P.pitch - R.mp.x, -R.mp.y, -R.mp.z);
+                    const float D2 = dot3(v, v);
+                    const float omega = P.pitch * P.H * (R.mp.z / sqrtf(D2)) / D2;
+                    if (omega > 0.f) wa *= 1.f / (1.f + 1.f / ((float)P.n_el * omega * R.mpdf));
+                }
+                emit<DBG, REC>(P, R.item * (uint32_t)P.n_el + (uint32_t)el, R.t, wa, R.i,
                           0x80000000u | ((uint32_t)R.b << 24));
                 cn.arrivals++;
             }
@@ -240,6 +426,21 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const float dn = dot3(R.d, n_out);
     const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
     const float3 n = dn > 0.f ? make_float3(-n_out.x, -n_out.y, -n_out.z) : n_out;
+    if (ROUGH && B.alpha > 0.f) {   // rough boundary: secondary ray first, then the BSDF sample
+        const float a2 = B.alpha * B.alpha;
+        rough_connection<DBG, REC>(P, S, R, n, m2, a2, cn);
+        cn.interactions++;
+        uint32_t rb = 0;
+        if (!rough_scatter(P, S, R, n, m2, a2, rb)) {
+            end_ray<DBG>(P, R, kEndRough, cn);
+            return;
+        }
+        if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | rb);
+        R.b += 1;
+        R.prev = R.hit;
+        start_segment(P, R, cn);
+        return;
+    }
     const float cos_i = -dot3(n, R.d);
     const float3 dr = unit3(R.d + (2.f * cos_i) * n);
     const Medium &M2 = S.med[m2];
@@ -273,6 +474,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         }
     }
     cn.interactions++;
+    if (ROUGH && branch != 1) R.mis = false;   // a smooth reflection: the secondary ray cannot produce this path
     if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | branch);
     R.b += 1;
     R.prev = R.hit;
@@ -301,7 +503,7 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     cn.connections++;
     ff tc;
     float att;
-    const float fac = connection(S, make_float3(q.x, q.y, q.z), med, xe, tc, att);
+    const float fac = connection(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
     if (fac == 0.f) return;
     const Medium &M = S.med[med];
     const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
@@ -311,6 +513,16 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     cn.arrivals++;
 }
 
+// The item whose slot range holds `slot` (item slot ranges are pool-aligned and ascending).
+__device__ __forceinline__ uint32_t item_of(const TraceP &P, uint64_t slot) {
+    int lo = 0, hi = P.n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.items[mid].slot_begin <= slot) lo = mid; else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
+
 // Persistent tracer.  Each iteration of the warp's loop (1) finishes segments
 // and claims new rays for idle lanes, (2) advances every active lane by one
 // grid cell, testing the cell's scatterer references in a warp-uniform loop,
@@ -318,7 +530,7 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
 // a time with all lanes busy.  Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
-template <bool DBG, bool SPLIT, bool REC>
+template <bool DBG, bool SPLIT, bool REC, bool ROUGH>
 __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
@@ -337,7 +549,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
         const unsigned waiting = __ballot_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay);
         const bool resolve = __popc(waiting) >= P.resolve_batch || __ballot_sync(0xffffffffu, R.state == kInSeg) == 0u;
         for (int guard = 0; resolve && guard < 256; ++guard) {
-            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC>(P, R, cn);
+            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC, ROUGH>(P, R, cn);
             unsigned need = __ballot_sync(0xffffffffu, R.state == kNeedRay);
             uint64_t my_slot = ~0ull;
             while (need) {
@@ -349,14 +561,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                         pool_next = base;
                         pool_cnt = base >= n_slots ? 0u : (uint32_t)kPool;
                         pool_dry = pool_cnt == 0;
-                        if (!pool_dry) {   // the item holding this pool (item slot ranges are pool-aligned)
-                            int lo = 0, hi = P.n_items - 1;
-                            while (lo < hi) {
-                                const int mid = (lo + hi + 1) >> 1;
-                                if (P.items[mid].slot_begin <= base) lo = mid; else hi = mid - 1;
-                            }
-                            pool_item = (uint32_t)lo;
-                        }
+                        if (!pool_dry) pool_item = item_of(P, base);
                     }
                     if (pool_dry) {
                         if (R.state == kNeedRay) R.state = kFinished;
@@ -371,12 +576,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 need = __ballot_sync(0xffffffffu, R.state == kNeedRay && my_slot == ~0ull);
             }
             if (my_slot != ~0ull) {
-                const ItemP &IT = P.items[pool_item];
+                // A warp that used up a pool and claimed the next one in the same pass holds slots
+                // of both; a slot before the current item's range belongs to an earlier item.
+                uint32_t item = pool_item;
+                if (my_slot < P.items[item].slot_begin) item = item_of(P, my_slot);
+                const ItemP &IT = P.items[item];
                 const uint64_t local = my_slot - IT.slot_begin;
                 const uint32_t m = (uint32_t)(local % IT.rays_per_el);
                 const uint64_t e = local / IT.rays_per_el;
                 const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray(P, R, pool_item, IT, i, (uint32_t)e, cn);
+                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray(P, R, item, IT, i, (uint32_t)e, cn);
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
@@ -483,24 +692,36 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
 int trace_occupancy(int block, bool debug) {
     int n = 0;
     if (debug)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false, false>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, false>, block, 0);
     return n > 0 ? n : 1;
 }
 
-// Variants with frozen sampling media and with recorded (ray, event) words are
-// compiled separately so the usual kernel carries none of their code.
+// Variants with frozen sampling media, with recorded (ray, event) words and with
+// rough boundaries are compiled separately so the usual kernel carries none of
+// their code.  Rough scenes never record or freeze sampling media (the adjoint
+// and ur_scene_set_media refuse them).
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
-    bool split = false;
-    for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) split = split || P.S[q].split_sampling != 0;
+    bool split = false, rough = false;
+    for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) {
+        split = split || P.S[q].split_sampling != 0;
+        for (int b = 0; b < P.S[q].n_bnd; ++b) rough = rough || P.S[q].bnd[b].alpha > 0.f;
+    }
+    if (rough) {
+        debug ? k_trace<true, false, false, true><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false, true><<<grid, block, 0, s>>>(P);
+        return;
+    }
     if (debug) {
-        split ? k_trace<true, true, false><<<grid, block, 0, s>>>(P) : k_trace<true, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<true, true, false, false><<<grid, block, 0, s>>>(P)
+              : k_trace<true, false, false, false><<<grid, block, 0, s>>>(P);
     } else if (P.record) {
-        split ? k_trace<false, true, true><<<grid, block, 0, s>>>(P) : k_trace<false, false, true><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, true, false><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, true, false><<<grid, block, 0, s>>>(P);
     } else {
-        split ? k_trace<false, true, false><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, false, false><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false, false><<<grid, block, 0, s>>>(P);
     }
 }
 

@@ -27,10 +27,12 @@ def _sorted(a):
     return a[o]
 
 
-def compare(gpu_arr, orc_arr, gpu_hash=None, orc_hash=None, ray_begin=0, n_rays_sub=None):
+def compare(gpu_arr, orc_arr, gpu_hash=None, orc_hash=None, ray_begin=0, n_rays_sub=None, amp_floor=0.0):
     """Match arrivals by (transmit, ray, event); report path agreement and errors.
 
-    Returns dict with: frac_paths (rays whose path hash and arrival set agree),
+    amp_floor: amplitudes below amp_floor x the largest one are compared against that floor
+    (relative error of tail arrivals).  Returns dict with: frac_paths (rays whose path hash
+    and arrival set agree),
     bad_rays (set of (tx, ray)), max_dt (samples, matched arrivals), max_amp_rel,
     el_mismatch (matched arrivals on different elements), n_gpu, n_orc, n_matched."""
     g = _sorted(gpu_arr)
@@ -52,10 +54,14 @@ def compare(gpu_arr, orc_arr, gpu_hash=None, orc_hash=None, ray_begin=0, n_rays_
         n_paths = orc_hash.size
     gm, om = g[gi], o[oi]
     dt = np.abs(gm["t"] - om["t"])
-    amp_rel = np.abs(gm["amp"] - om["amp"]) / np.maximum(np.abs(om["amp"]), 1e-300)
+    floor = amp_floor * float(np.abs(om["amp"]).max()) if om.size else 0.0
+    amp_rel = np.abs(gm["amp"] - om["amp"]) / np.maximum(np.maximum(np.abs(om["amp"]), floor), 1e-300)
+    worst = int(np.argmax(amp_rel)) if amp_rel.size else -1
     res = {"bad_rays": bad, "n_gpu": int(g.size), "n_orc": int(o.size), "n_matched": int(common.size),
            "max_dt": float(dt.max()) if dt.size else 0.0,
            "max_amp_rel": float(amp_rel.max()) if amp_rel.size else 0.0,
+           "worst_amp": (hex(int(om["event"][worst])), int(om["ray"][worst]), float(om["amp"][worst]),
+                         float(gm["amp"][worst])) if worst >= 0 else None,
            "el_mismatch": int(np.sum(gm["el"] != om["el"]))}
     if n_paths:
         res["frac_paths"] = 1.0 - len(bad) / n_paths

@@ -57,6 +57,22 @@ def test_batch_items_equal_single_traces(env):
         assert rel_l2(q[k].double().cpu().numpy(), sq) <= 1e-6
 
 
+def test_large_items_trace_every_ray(env):
+    """Items of 1e5-4e5 rays: tracer warps claim slot pools of consecutive items within one
+    pass; every planned ray is traced and items still equal single traces."""
+    torch, ur, a, b, items = env
+    big = [(s, tx, 12 * n) for s, tx, n in items]
+    sim = planned(ur, a, b, big)
+    rf, q = sim.batch_trace(0, 4)
+    n, st = sim.batch_status()
+    assert st["rays"] == sum(it[2] for it in big)
+    for k in (0, 2):
+        scene, tx, nr = big[k]
+        srf, sq = single(ur, a if scene == 0 else b, nr, tx)
+        assert rel_l2(rf[k].double().cpu().numpy(), srf) <= 1e-6, (k, scene, tx)
+        assert rel_l2(q[k].double().cpu().numpy(), sq) <= 1e-6
+
+
 def test_batch_item_of_second_scene_matches_oracle(env):
     torch, ur, a, b, items = env
     sim = planned(ur, a, b, items)

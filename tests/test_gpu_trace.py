@@ -27,11 +27,12 @@ def ur():
     return ur
 
 
-def run_gpu(ur, w, n_rays=None, seed=None):
+def run_gpu(ur, w, n_rays=None, seed=None, capacity=None):
     sim = ur.Simulator(0)
     sim.load(w)
     n = n_rays or w["n_rays"]
-    rf, quad, st, rec, ph = sim.trace_debug(n, w["seed"] if seed is None else seed, w["max_bounces"], w["max_path"])
+    rf, quad, st, rec, ph = sim.trace_debug(n, w["seed"] if seed is None else seed, w["max_bounces"], w["max_path"],
+                                            capacity=capacity)
     out = {"rf": rf.double().cpu().numpy(), "quad": quad.double().cpu().numpy(), "stats": st,
            "rec": gpu_records(rec, w["array"]["n_el"]), "hash": ph.cpu().numpy().view(np.uint64), "sim": sim}
     return out
@@ -44,13 +45,13 @@ def run_oracle(w, n_rays=None, seed=None, ray_begin=0, ray_end=None):
     return arr, topo, st
 
 
-def check_trace_parity(w, G, arr, topo, label=""):
+def check_trace_parity(w, G, arr, topo, label="", amp_floor=0.0):
     n_tx = len(w["angles"])
-    res = compare(G["rec"], arr, G["hash"], topo)
+    res = compare(G["rec"], arr, G["hash"], topo, amp_floor=amp_floor)
     assert res["frac_paths"] >= PATH_FRAC, (label, res["frac_paths"], len(res["bad_rays"]))
     assert res["max_dt"] <= DT_MAX, (label, res["max_dt"])
     assert res["el_mismatch"] == 0, label
-    assert res["max_amp_rel"] <= AMP_REL, (label, res["max_amp_rel"])
+    assert res["max_amp_rel"] <= AMP_REL, (label, res["max_amp_rel"], res["worst_amp"])
     orf, oq = oracle.deposit(w["array"], n_tx, arr)
     bad = res["bad_rays"]
     if bad:
@@ -85,6 +86,17 @@ def test_tiny_steered_transmits(ur):
     G = run_gpu(ur, w, seed=3)
     arr, topo, _ = run_oracle(w, seed=3)
     check_trace_parity(w, G, arr, topo, "steered")
+
+
+def test_many_transmits_every_ray(ur):
+    """4 transmits x 150k rays: more slot pools than tracer warps, so warps cross from one
+    transmit's slots to the next; every ray is traced and matches the oracle."""
+    w = phantoms.tiny(n_rays=150_000)
+    w["angles"] = np.deg2rad(np.array([-12.0, -4.0, 3.0, 11.0], np.float64)).astype(np.float32)
+    G = run_gpu(ur, w, seed=4)
+    assert G["stats"]["rays"] == 4 * 150_000
+    arr, topo, _ = run_oracle(w, seed=4)
+    check_trace_parity(w, G, arr, topo, "many transmits")
 
 
 def test_layered_parity(ur):
@@ -257,8 +269,9 @@ def test_invalid_arguments_and_state(ur):
     with pytest.raises(ur.URError):
         sim.set_array(a)
     med = np.array(w["scene"]["media"])
-    med[0, 3] = 0.5                                # rough boundaries are not supported
-    with pytest.raises(ur.URError):
-        sim.upload_scene(med, w["scene"]["boundaries"], 0, 0.04, w["scene"]["scatterers"], 1e-4)
+    for bad_alpha in (-0.5, 5.0, np.nan):          # GGX roughness must lie in [0, 4]
+        med[0, 3] = bad_alpha
+        with pytest.raises(ur.URError):
+            sim.upload_scene(med, w["scene"]["boundaries"], 0, 0.04, w["scene"]["scatterers"], 1e-4)
     with pytest.raises(ur.URError):
         sim.set_plane_waves(np.array([1.2], np.float32))   # beyond 60 degrees
