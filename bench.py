@@ -79,6 +79,30 @@ def trace_flops(stats):
             + stats["connections"] * FLOPS_PER_CONNECTION)
 
 
+def binning_roofline(st, arr, phase_ms, alu_peak, peaks, n_sm, sm_mhz):
+    """Binning of one frame: the deposit kernel against the FP32 ALU peak (FLOPS_PER_TAP per
+    pulse tap), its shared-memory atomics against one 32-lane atomic per SM per clock, and the
+    counting sort's algorithmic bytes (arrival read by count and scatter, sorted write) against HBM."""
+    taps = st["arrivals"] * taps_per_arrival(arr)
+    t_dep = phase_ms.get("deposit", float("nan")) * 1e-3
+    t_sort = phase_ms.get("sort", float("nan")) * 1e-3
+    ach = taps * FLOPS_PER_TAP / t_dep / 1e12
+    atom_peak = n_sm * 32 * sm_mhz * 1e6
+    sort_bytes = st["arrivals"] * 48
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "alu", "kernel": "k_bin_deposit", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": ach / alu_peak, "traffic": None, "algorithmic_flops_per_launch": taps * FLOPS_PER_TAP,
+            "deposit_ms_per_launch": t_dep * 1e3,
+            "shared_atomics": {"achieved_per_s": 2 * taps / t_dep, "peak_per_s": atom_peak,
+                               "frac": 2 * taps / t_dep / atom_peak,
+                               "peak_note": "%d SMs x 32 lanes x %.0f MHz (one warp-wide shared atomic per clock)"
+                                            % (n_sm, sm_mhz)},
+            "sort": {"bound": "hbm", "kernels": "k_bin_count + k_bin_plan + k_bin_scatter",
+                     "algorithmic_bytes": sort_bytes, "achieved": sort_bytes / t_sort / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": sort_bytes / t_sort / 1e9 / hbm, "ms": t_sort * 1e3,
+                     "peak_note": "hbm_gbs of measured"}}
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -226,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     R = Ranks(rank, world, local_rank)
     dev = R.device
-    w = phantoms.layered()
+    w = frame_workload(args)
     if args.rays:
         w["n_rays"] = args.rays
     seed = w["seed"] + rank
@@ -286,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = trace_flops(st) / t_launch / 1e12
     traffic = None
-    if TRACE_TRAFFIC and TRACE_TRAFFIC.get("src_sha") == tracer_sha():
+    if args.workload == "layered" and TRACE_TRAFFIC and TRACE_TRAFFIC.get("src_sha") == tracer_sha():
         traffic = TRACE_TRAFFIC["bytes_per_ray"] * N
     launches = sum(v[1] for v in prof.values())
     phase_ms = {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]}
@@ -328,12 +352,15 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": "replicas: one frame per GPU"},
             "frames_per_s": world / (ms_max * 1e-3),
             "phase_ms": phase_ms,
-            "roofline": {"bound": "alu", "kernel": "k_trace", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": "alu",
+                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload == "rough" else ""),
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
                              props.multi_processor_count, FP32_LANES_PER_SM, sm_mhz),
                          "trace_ms_per_launch": t_launch * 1e3,
                          "algorithmic_flops_per_launch": trace_flops(st)},
+            "roofline_binning": binning_roofline(st, A, phase_ms, peak, peaks, props.multi_processor_count, sm_mhz),
             "stats_per_frame": st,
             "gpu_launches": launches,
             "e2e": {"value": whole_job_rate(N, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -349,6 +376,22 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     sim.close()
     R.close()
+
+
+ROUGH_WORKLOAD = WORKLOAD + "; bone boundary rough (GGX roughness 0.5, the paper's bone value)"
+
+
+def frame_workload(args):
+    """The single-frame phantom of the layered (default) or rough workload."""
+    import phantoms
+    w = phantoms.layered()
+    if args.workload == "rough":
+        s = dict(w["scene"])
+        med = [list(m) for m in s["media"]]
+        med[3][3] = 0.5                      # bone: the rough cylinder
+        s["media"] = [tuple(m) for m in med]
+        w["scene"] = s
+    return w
 
 
 BATCH_WORKLOAD = ("batched: 8 jittered layered phantoms (skin +-1 mm, fat +-2 mm, bone r U(3,10) mm, 10k-200k "
@@ -472,7 +515,9 @@ def run_batched(args, rank, world, local_rank):
             "images_per_s": whole_job_rate(len(scenes), world, ms * 1e-3),
             "arrivals_per_step": n_arr2, "stats_per_step": st,
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
-            "roofline": {"bound": "alu", "kernel": "k_trace", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": "alu",
+                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload == "rough" else ""),
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
             "gpu_launches": 7 * args.steps, "clocks": clk,
             "e2e": {"value": whole_job_rate(total_rays, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -790,7 +835,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
-    ap.add_argument("--workload", default="layered", choices=("layered", "batched", "adjoint", "denoiser"))
+    ap.add_argument("--workload", default="layered", choices=("layered", "rough", "batched", "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -798,7 +843,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     args.warmup = max(3, args.warmup)
     if args.steps <= 0:
-        args.steps = {"layered": 150, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
+        args.steps = {"layered": 150, "rough": 60, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "batched":
