@@ -196,7 +196,9 @@ def whole_job_rate(units_per_rank, world, seconds_max):
 
 # ------------------------------------------------------------------ CPU oracle
 def oracle_rate(w, target_s, threads=None):
-    """FP64 oracle on a bounded sample of the frame: returns (rays/s, rays in sample, seconds)."""
+    """FP64 oracle on a bounded sample of the frame (rays 0..n-1 of every transmit): returns
+    (rays/s, rays per transmit in the sample, seconds, threads)."""
+    import numpy as np
     import oracle
     threads = threads or (os.cpu_count() or 1)
     t0 = time.perf_counter()
@@ -208,7 +210,7 @@ def oracle_rate(w, target_s, threads=None):
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
                     w["z_px"], w["dyn_range_db"], w["max_path"], 0, n, threads=threads)
     dt = time.perf_counter() - t0
-    return n / dt, n, dt, threads
+    return n * len(np.atleast_1d(w["angles"])) / dt, n, dt, threads
 
 
 def run_reference(args, rank):
@@ -255,9 +257,10 @@ def run_ours(args, rank, world, local_rank):
         w["n_rays"] = args.rays
     seed = w["seed"] + rank
     N, A = w["n_rays"], w["array"]
+    n_tx = len(w["angles"])
     sim = ur.Simulator(local_rank)
     sim.load(w)
-    shape = (1, A["n_el"], A["n_s"])
+    shape = (n_tx, A["n_el"], A["n_s"])
     rf = torch.empty(shape, dtype=torch.float32, device=dev)
     quad = torch.empty(shape, dtype=torch.float32, device=dev)
     nx, nz = w["x_px"].size, w["z_px"].size
@@ -294,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     ms_max = R.max(ms)
-    value = whole_job_rate(N, world, ms_max * 1e-3)
+    value = whole_job_rate(N * n_tx, world, ms_max * 1e-3)
 
     # ---- roofline of the dominant kernel (the tracer) ----
     st = last["stats"]
@@ -347,13 +350,14 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rays_per_frame": N, "n_el": A["n_el"], "n_s": A["n_s"],
+            "config": {"workload": FRAME_WORKLOADS[args.workload], "rays_per_step": N * n_tx, "transmits": n_tx, "n_el": A["n_el"], "n_s": A["n_s"],
                        "image": "%dx%d" % (nx, nz), "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "parallelism": "replicas: one frame per GPU"},
-            "frames_per_s": world / (ms_max * 1e-3),
+            "frames_per_s": whole_job_rate(n_tx, world, ms_max * 1e-3),
+            "acquisitions_per_s": whole_job_rate(1, world, ms_max * 1e-3),
             "phase_ms": phase_ms,
             "roofline": {"bound": "alu",
-                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload == "rough" else ""),
+                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
@@ -363,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline_binning": binning_roofline(st, A, phase_ms, peak, peaks, props.multi_processor_count, sm_mhz),
             "stats_per_frame": st,
             "gpu_launches": launches,
-            "e2e": {"value": whole_job_rate(N, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": whole_job_rate(N * n_tx, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
                     "path": "ur_scene_upload(pinned host scatterers, grid build) + ur_trace + ur_beamform(db -> pinned host)"},
             "clocks": clk,
@@ -371,19 +375,27 @@ def run_ours(args, rank, world, local_rank):
         if world == 1 and not args.no_cpu_baseline:
             rate, n, dt, thr = oracle_rate(w, args.cpu_seconds)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                    "sample": "rays 0..%d of the same frame (%.1f s), trace + deposit + 512x256 DAS + log"
-                                              % (n - 1, dt)}
+                                    "sample": "rays 0..%d of each of the %d transmits (%.1f s), trace + deposit + "
+                                              "512x256 DAS + log" % (n - 1, n_tx, dt)}
         print(json.dumps(line), flush=True)
     sim.close()
     R.close()
 
 
 ROUGH_WORKLOAD = WORKLOAD + "; bone boundary rough (GGX roughness 0.5, the paper's bone value)"
+PAPER_WORKLOAD = ("paper settings (Sec. 4) on a synthetic vertebra stand-in: 128 el, 5 MHz, fs 50 MHz, 5 cycles, "
+                  "4 mm elevation, 2-deg directivity, 25 plane waves -30..30 deg x 512k rays (12.8M rays per "
+                  "acquisition), 10 bounces, 20 cm paths; water around a rough bone sphere (r 10 mm, 45 mm) and two "
+                  "rough bone cylinders (GGX 0.5), 20k scatterers in the bone; DAS of all 25 transmits to 512x256, "
+                  "90 dB")
+FRAME_WORKLOADS = {"layered": WORKLOAD, "rough": ROUGH_WORKLOAD, "paper": PAPER_WORKLOAD}
 
 
 def frame_workload(args):
-    """The single-frame phantom of the layered (default) or rough workload."""
+    """The phantom of a frame workload: layered (default), rough or paper."""
     import phantoms
+    if args.workload == "paper":
+        return phantoms.paper_like()
     w = phantoms.layered()
     if args.workload == "rough":
         s = dict(w["scene"])
@@ -516,7 +528,7 @@ def run_batched(args, rank, world, local_rank):
             "arrivals_per_step": n_arr2, "stats_per_step": st,
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
             "roofline": {"bound": "alu",
-                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload == "rough" else ""),
+                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
             "gpu_launches": 7 * args.steps, "clocks": clk,
@@ -567,7 +579,7 @@ def oracle_adjoint_rate(w, tgt_media, target_s, threads=None):
     t0 = time.perf_counter()
     step(n, t_rf, t_q)
     dt = time.perf_counter() - t0
-    return n / dt, n, dt, threads
+    return n * len(np.atleast_1d(w["angles"])) / dt, n, dt, threads
 
 
 def run_adjoint(args, rank, world, local_rank):
@@ -835,7 +847,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
-    ap.add_argument("--workload", default="layered", choices=("layered", "rough", "batched", "adjoint", "denoiser"))
+    ap.add_argument("--workload", default="layered",
+                    choices=("layered", "rough", "paper", "batched", "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -843,7 +856,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     args.warmup = max(3, args.warmup)
     if args.steps <= 0:
-        args.steps = {"layered": 150, "rough": 60, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
+        args.steps = {"layered": 150, "rough": 60, "paper": 30, "batched": 5, "adjoint": 30,
+                      "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "batched":

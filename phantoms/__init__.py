@@ -117,6 +117,39 @@ def batched_variant(scene_seed):
     return w
 
 
+def paper_like(seed=0, n_scat=20_000, n_rays=512_000):
+    """The acquisition of the paper's experiments (Sec. 4) on a synthetic bone-surface stand-in
+    (the CT spine mesh is not available): 128 elements, 5 MHz, fs 50 MHz, 5 cycles, 4 mm
+    elevation, directivity 2 degrees, 25 plane waves over [-30, 30] degrees, 10 bounces, 20 cm
+    paths, 90 dB.  Water (c 1540, Z 1.54) around bone (c 3500, Z 7.8, 10 dB/cm/MHz, GGX roughness
+    0.5): a vertebral body (sphere r = 10 mm at 45 mm depth) and two processes (cylinders along
+    elevation, r = 3 mm, at x = +-12 mm, 28 mm depth); n_scat scatterers uniform inside the bone,
+    none in the water.  n_rays per transmit (25 x 512k = 12.8M rays per acquisition, the paper's
+    128 elements x 100k rays)."""
+    rng = np.random.default_rng(seed)
+    water = (1540.0, 1.54, 0.0, 0.0)
+    bone = (3500.0, 7.8, 10.0, 0.5)
+    body = (0.0, 0.0, 45e-3, 10e-3)
+    procs = ((-12e-3, 28e-3, 3e-3), (12e-3, 28e-3, 3e-3))
+    bnd = [(SPHERE, list(body), 1, 0)] + [(CYL_Y, [x, z, r, 0.0], 1, 0) for x, z, r in procs]
+    pts = []
+    while sum(len(p) for p in pts) < n_scat:   # rejection sampling inside the bone primitives
+        q = np.column_stack([rng.uniform(-15e-3, 15e-3, 4 * n_scat), rng.uniform(-10e-3, 10e-3, 4 * n_scat),
+                             rng.uniform(25e-3, 55e-3, 4 * n_scat)])
+        inside = np.sum((q - np.array(body[:3])) ** 2, axis=1) < body[3] ** 2
+        for x, z, r in procs:
+            inside |= (q[:, 0] - x) ** 2 + (q[:, 2] - z) ** 2 < r * r
+        pts.append(q[inside])
+    xyz = np.concatenate(pts)[:n_scat]
+    sc = np.column_stack([xyz, rng.standard_normal(n_scat)]).astype(np.float32)
+    arr = array_params(128, 4096, fs=50e6, c_bf=1540.0, alpha_m_deg=2.0, alpha_c_deg=2.0)
+    x, z = image_grid(arr, 512, 256, z0=1e-3, z1=60e-3)
+    ang = np.deg2rad(np.linspace(-30.0, 30.0, 25)).astype(np.float32)
+    return {"name": "paper_like", "scene": _scene([water, bone], bnd, 0, 0.080, sc, 1e-4), "array": arr,
+            "angles": ang, "n_rays": int(n_rays), "seed": 0, "max_bounces": 10, "max_path": 0.2,
+            "x_px": x, "z_px": z, "dyn_range_db": 90.0}
+
+
 def single_plane(depth=0.015, upper=WATER, lower=MUSCLE, n_el=32, n_s=1536, n_rays=3200,
                  z_max=0.040, c_bf=1480.0, **arr_kw):
     """One planar interface, no scatterers (normal-incidence echo checks)."""

@@ -57,11 +57,15 @@ def compare(gpu_arr, orc_arr, gpu_hash=None, orc_hash=None, ray_begin=0, n_rays_
     floor = amp_floor * float(np.abs(om["amp"]).max()) if om.size else 0.0
     amp_rel = np.abs(gm["amp"] - om["amp"]) / np.maximum(np.maximum(np.abs(om["amp"]), floor), 1e-300)
     worst = int(np.argmax(amp_rel)) if amp_rel.size else -1
+    wdt = int(np.argmax(dt)) if dt.size else -1
     res = {"bad_rays": bad, "n_gpu": int(g.size), "n_orc": int(o.size), "n_matched": int(common.size),
            "max_dt": float(dt.max()) if dt.size else 0.0,
+           "dt_q99": float(np.quantile(dt, 0.99)) if dt.size else 0.0,
            "max_amp_rel": float(amp_rel.max()) if amp_rel.size else 0.0,
            "worst_amp": (hex(int(om["event"][worst])), int(om["ray"][worst]), float(om["amp"][worst]),
                          float(gm["amp"][worst])) if worst >= 0 else None,
+           "worst_dt": (hex(int(om["event"][wdt])), int(om["tx"][wdt]), int(om["ray"][wdt]), float(om["t"][wdt]),
+                        float(gm["t"][wdt])) if wdt >= 0 else None,
            "el_mismatch": int(np.sum(gm["el"] != om["el"]))}
     if n_paths:
         res["frac_paths"] = 1.0 - len(bad) / n_paths

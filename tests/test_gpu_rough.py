@@ -111,3 +111,18 @@ def test_rough_scenes_refused_where_unsupported(ur):
     with pytest.raises(ur.URError):
         sim.set_media(bad)
     sim.close()
+
+
+def test_paper_settings_phantom(ur):
+    """The paper's acquisition settings (25 plane waves over [-30, 30] degrees, fs 50 MHz, 10 bounces,
+    2-degree directivity) on the rough vertebra stand-in: every transmit against the oracle.
+    Time bar: FP32 hit points carry errors of a few nm; on a 10 mm sphere a normal then tilts by
+    about 1e-7 rad per bounce, and over the tens of millimetres that follow the arrival moves by
+    up to about 1e-8 m = 3e-4 samples at 50 MHz per curved bounce.  Paths with several bounces in the
+    bone reach a few 1e-3 samples: bar 1e-3 samples for 99 % of the arrivals and 1e-2 for all."""
+    w = phantoms.paper_like(n_rays=4000)
+    G = run_gpu(ur, w, capacity=4 * 25 * w["n_rays"])
+    assert G["stats"]["rays"] == 25 * w["n_rays"]
+    arr, topo, _ = run_oracle(w)
+    check_trace_parity(w, G, arr, topo, "paper settings", amp_floor=ROUGH_AMP_FLOOR, dt_max=1e-2, dt_q99=1e-3)
+    assert secondary(arr).size > 0

@@ -45,11 +45,12 @@ def run_oracle(w, n_rays=None, seed=None, ray_begin=0, ray_end=None):
     return arr, topo, st
 
 
-def check_trace_parity(w, G, arr, topo, label="", amp_floor=0.0):
+def check_trace_parity(w, G, arr, topo, label="", amp_floor=0.0, dt_max=DT_MAX, dt_q99=DT_MAX):
     n_tx = len(w["angles"])
     res = compare(G["rec"], arr, G["hash"], topo, amp_floor=amp_floor)
     assert res["frac_paths"] >= PATH_FRAC, (label, res["frac_paths"], len(res["bad_rays"]))
-    assert res["max_dt"] <= DT_MAX, (label, res["max_dt"])
+    assert res["max_dt"] <= dt_max, (label, res["max_dt"], res["worst_dt"])
+    assert res["dt_q99"] <= dt_q99, (label, res["dt_q99"])
     assert res["el_mismatch"] == 0, label
     assert res["max_amp_rel"] <= AMP_REL, (label, res["max_amp_rel"], res["worst_amp"])
     orf, oq = oracle.deposit(w["array"], n_tx, arr)
