@@ -27,6 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 PLANE_Z, SPHERE, CYL_Y = 0, 1, 2
+TX_PLANE, TX_DIVERGING, TX_FOCUSED = 0, 1, 2
 MODE_MC, MODE_EXPECT = 0, 1
 END_APERTURE, END_ARRAY_MISS, END_BOTTOM, END_PATH, END_TIME, END_MAXB, END_ROUGH = 1, 2, 3, 4, 5, 6, 7
 
@@ -66,7 +67,8 @@ class TraceCfg(C.Structure):
     _fields_ = [("n_tx", C.c_int32), ("angles", C.POINTER(C.c_float)),
                 ("n_rays", C.c_uint64), ("ray_begin", C.c_uint64), ("ray_end", C.c_uint64),
                 ("seed", C.c_uint64), ("max_bounces", C.c_int32), ("max_path", C.c_float),
-                ("mode", C.c_int32), ("rough_bsdf_only", C.c_int32)]
+                ("mode", C.c_int32), ("rough_bsdf_only", C.c_int32),
+                ("tx_kind", C.POINTER(C.c_int32)), ("tx_x", C.POINTER(C.c_float)), ("tx_z", C.POINTER(C.c_float))]
 
 
 class Arrival(C.Structure):
@@ -99,6 +101,10 @@ def lib():
                                       C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float), C.c_int32,
                                       dp, dp, C.c_int]
             L.or_envelope_log.argtypes = [dp, dp, C.c_int64, C.c_double, dp, dp]
+            L.or_beamform_tx.argtypes = [C.POINTER(Array), C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_float), C.POINTER(C.c_float), dp, dp,
+                                         C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float), C.c_int32,
+                                         dp, dp, C.c_int]
             L.or_interface.restype = C.c_int
             L.or_interface.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                        dp, dp, dp, dp]
@@ -180,8 +186,20 @@ def philox4x32_10(ctr, key):
     return out
 
 
+def _transmit_arrays(transmits, n_tx):
+    """transmits: None (plane waves of `angles`) or a sequence of (kind, x, z) per transmit."""
+    if transmits is None:
+        return None
+    t = list(transmits)
+    assert len(t) == n_tx
+    kind = np.ascontiguousarray([int(k) for k, _, _ in t], np.int32)
+    tx = np.ascontiguousarray([x for _, x, _ in t], np.float32)
+    tz = np.ascontiguousarray([z for _, _, z in t], np.float32)
+    return kind, tx, tz
+
+
 def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_begin=0, ray_end=None,
-          mode=MODE_MC, topo=False, threads=None, rough_bsdf_only=False):
+          mode=MODE_MC, topo=False, threads=None, rough_bsdf_only=False, transmits=None):
     """Trace rays [ray_begin, ray_end) of every transmit.
 
     Returns (arrivals structured array, topology hashes [n_tx, n_sub] or None, stats dict)."""
@@ -191,8 +209,10 @@ def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_beg
     s, keep_s = make_scene(scene)
     a = make_array(array)
     ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
+    txa = _transmit_arrays(transmits, ang.size)
     cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed),
-                   int(max_bounces), float(max_path), int(mode), int(bool(rough_bsdf_only)))
+                   int(max_bounces), float(max_path), int(mode), int(bool(rough_bsdf_only)),
+                   _ip(txa[0]) if txa else None, _fp(txa[1]) if txa else None, _fp(txa[2]) if txa else None)
     n_sub = int(ray_end) - int(ray_begin)
     topo_arr = np.zeros((ang.size, n_sub), np.uint64) if topo else None
     threads = threads or (os.cpu_count() or 1)
@@ -222,7 +242,7 @@ def grad(scene, array, angles, n_rays, seed, max_bounces, g_rf, g_q, max_path=0.
     a = make_array(array)
     ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
     cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed), int(max_bounces),
-                   float(max_path), MODE_MC, 0)
+                   float(max_path), MODE_MC, 0, None, None, None)
     gr = np.ascontiguousarray(g_rf, dtype=np.float64)
     gq = np.ascontiguousarray(g_q, dtype=np.float64)
     n_med = len(scene["media"])
@@ -249,18 +269,21 @@ def deposit(array, n_tx, arrivals):
     return rf, quad
 
 
-def beamform(array, angles, rf, quad, x_px, z_px, threads=None):
-    """Plane-wave DAS with coherent compounding: returns complex128 [nz, nx]."""
+def beamform(array, angles, rf, quad, x_px, z_px, threads=None, transmits=None):
+    """DAS with coherent compounding (plane waves of `angles`, or the kinds of `transmits`):
+    returns complex128 [nz, nx]."""
     a = make_array(array)
     ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
+    txa = _transmit_arrays(transmits, ang.size)
     rf = np.ascontiguousarray(rf, dtype=np.float64)
     quad = np.ascontiguousarray(quad, dtype=np.float64)
     xp = np.ascontiguousarray(x_px, dtype=np.float32)
     zp = np.ascontiguousarray(z_px, dtype=np.float32)
     re = np.zeros((zp.size, xp.size), np.float64)
     im = np.zeros_like(re)
-    lib().or_beamform(C.byref(a), ang.size, _fp(ang), _dp(rf), _dp(quad), _fp(xp), xp.size,
-                      _fp(zp), zp.size, _dp(re), _dp(im), int(threads or (os.cpu_count() or 1)))
+    lib().or_beamform_tx(C.byref(a), ang.size, _fp(ang), _ip(txa[0]) if txa else None,
+                         _fp(txa[1]) if txa else None, _fp(txa[2]) if txa else None, _dp(rf), _dp(quad),
+                         _fp(xp), xp.size, _fp(zp), zp.size, _dp(re), _dp(im), int(threads or (os.cpu_count() or 1)))
     return re + 1j * im
 
 
@@ -338,11 +361,11 @@ def connection(scene, array, p, med, x_e):
 
 
 def simulate(scene, array, angles, n_rays, seed, max_bounces, x_px, z_px, dyn_range_db=60.0,
-             max_path=0.2, ray_begin=0, ray_end=None, threads=None):
+             max_path=0.2, ray_begin=0, ray_end=None, threads=None, transmits=None):
     """Whole chain for one frame: trace, deposit, beamform, envelope, log."""
     arr, _, st = trace(scene, array, angles, n_rays, seed, max_bounces, max_path, ray_begin, ray_end,
-                       threads=threads)
+                       threads=threads, transmits=transmits)
     rf, quad = deposit(array, len(np.atleast_1d(angles)), arr)
-    iq = beamform(array, angles, rf, quad, x_px, z_px, threads=threads)
+    iq = beamform(array, angles, rf, quad, x_px, z_px, threads=threads, transmits=transmits)
     env, db = envelope_log(iq, dyn_range_db)
     return {"arrivals": arr, "stats": st, "rf": rf, "quad": quad, "iq": iq, "env": env, "db": db}

@@ -12,6 +12,14 @@
  *    reflection and sqrt(1-R)/(1-R) on transmission, so that the expected
  *    amplitude is r (reflected) and sqrt(1-R) (transmitted, energy-normalised).
  *  - Emission (Eq. 6): weight cos(theta)/N with N the rays of one transmit.
+ *  - Diverging and focused transmits (Sec. 2.3 "Ray Emission" names them beside
+ *    plane waves without formulas): element delays make the wavefront of a
+ *    virtual source behind the array, or one converging on a focus in front of
+ *    it, both in the lateral (xz) plane; each element fires at its delay (first
+ *    element at t = 0) and a ray leaves its emission point along the line from
+ *    the virtual source, or toward the focus, projected on the xz plane (the
+ *    delays act laterally only, so directions keep y = 0 as for plane waves);
+ *    the Eq. 6 weight is the cosine to the element normal over N.
  *  - Transducer sampling: delta (smooth) boundaries contribute only through the
  *    primary ray crossing the array plane; point scatterers contribute only
  *    through a straight connection ray to a uniformly chosen element centre,
@@ -170,6 +178,8 @@ typedef struct {
     double am, ac;              /* directivity angles (rad) */
     int top, bot;               /* ids of the terminal planes */
     double *alpha_b;            /* per boundary: GGX roughness (0: smooth) */
+    int *kind;                  /* per transmit: OR_TX_* */
+    double *vx, *vz;            /* per transmit: virtual source or focus (m) */
 } ctx_t;
 
 static double elem_x(const ctx_t *C, int e) { return C->x0 + (double)e * C->pitch; }
@@ -696,8 +706,14 @@ static uint64_t trace_ray(const ctx_t *C, ray_job *J)
     draw(C->cfg->seed, J->i, (uint32_t)J->k, 0u, 0u, x);
     double o[3] = {elem_x(C, e) + (u24(x[0]) - 0.5) * C->pitch, (u24(x[1]) - 0.5) * C->H, 0.0};
     double d[3] = {C->sin_t[J->k], 0.0, C->cos_t[J->k]};
+    if (C->kind[J->k] != OR_TX_PLANE) {   /* along the line from the virtual source / toward the focus */
+        double sg = C->kind[J->k] == OR_TX_DIVERGING ? 1.0 : -1.0;
+        double dx = sg * (o[0] - C->vx[J->k]), dz = sg * (o[2] - C->vz[J->k]);
+        double l = sqrt(dx * dx + dz * dz);
+        d[0] = dx / l; d[1] = 0.0; d[2] = dz / l;
+    }
     double t = C->delay[J->k * ar->n_el + e];
-    double w = C->cos_t[J->k] / (double)C->cfg->n_rays;
+    double w = d[2] / (double)C->cfg->n_rays;   /* Eq. 6: cosine to the element normal over N */
     uint64_t h = OR_FNV_OFFSET;
     int reason = follow(C, J, o, d, t, w, C->sc->med_array, 0, 0.0, -1, &h);
     J->st.rays++;
@@ -720,25 +736,37 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
         C->Zs[m] = sc->med_sampling ? sc->med_sampling[4 * m + 1] : C->Z[m];
     }
     int nt = cfg ? cfg->n_tx : 0;
-    C->delay = (double *)malloc(sizeof(double) * ((size_t)nt * ar->n_el + 2 * (size_t)nt + 1));
+    C->delay = (double *)malloc(sizeof(double) * ((size_t)nt * ar->n_el + 4 * (size_t)nt + 1));
     C->sin_t = C->delay + (size_t)nt * ar->n_el;
     C->cos_t = C->sin_t + nt;
+    C->vx = C->cos_t + nt;
+    C->vz = C->vx + nt;
+    C->kind = (int *)malloc(sizeof(int) * (size_t)(nt + 1));
     C->pitch = ar->pitch;
     C->H = ar->elev_h;
     C->x0 = -0.5 * (double)(ar->n_el - 1) * C->pitch;
     for (int k = 0; k < nt; ++k) {
-        double th = cfg->angles[k];
+        double th = cfg->angles ? cfg->angles[k] : 0.0;
+        C->kind[k] = cfg->tx_kind ? cfg->tx_kind[k] : OR_TX_PLANE;
+        C->vx[k] = cfg->tx_kind ? cfg->tx_x[k] : 0.0;
+        C->vz[k] = cfg->tx_kind ? cfg->tx_z[k] : 0.0;
         C->sin_t[k] = sin(th);
         C->cos_t[k] = cos(th);
-        /* plane-wave transmit delays: each element fires when the steered
-         * wavefront through the first-firing element reaches it */
-        double mn = INFINITY;
+        /* path length from the wave's reference to element e: plane wave: x_e sin(theta);
+         * diverging: distance from the virtual source; focused: minus the distance to the
+         * focus.  Each element fires when the wavefront through the first-firing element
+         * reaches it. */
+        double mn = INFINITY, *len = (double *)malloc(sizeof(double) * (size_t)ar->n_el);
         for (int e = 0; e < ar->n_el; ++e) {
-            double v = elem_x(C, e) * C->sin_t[k];
-            if (v < mn) mn = v;
+            double dx = elem_x(C, e) - C->vx[k], dz = -C->vz[k];
+            if (C->kind[k] == OR_TX_PLANE) len[e] = elem_x(C, e) * C->sin_t[k];
+            else if (C->kind[k] == OR_TX_DIVERGING) len[e] = sqrt(dx * dx + dz * dz);
+            else len[e] = -sqrt(dx * dx + dz * dz);
+            if (len[e] < mn) mn = len[e];
         }
         for (int e = 0; e < ar->n_el; ++e)
-            C->delay[k * ar->n_el + e] = (elem_x(C, e) * C->sin_t[k] - mn) / (double)ar->c_bf * (double)ar->fs;
+            C->delay[k * ar->n_el + e] = (len[e] - mn) / (double)ar->c_bf * (double)ar->fs;
+        free(len);
     }
     double s = (double)ar->n_cycles / (4.0 * (double)ar->f0);
     C->K = (double)ar->tcut_sigmas * s * (double)ar->fs;
@@ -760,6 +788,7 @@ static void teardown(ctx_t *C)
     free(C->c);
     free(C->delay);
     free(C->alpha_b);
+    free(C->kind);
 }
 
 static int scene_is_rough(const or_scene *sc)
@@ -778,6 +807,15 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
         return -1;
     for (int m = 0; m < sc->n_med; ++m)
         if (!(sc->med[4 * m + 3] >= 0.0f && sc->med[4 * m + 3] <= 4.0f)) return -1;
+    if (cfg->tx_kind) {
+        if (!cfg->tx_x || !cfg->tx_z) return -1;
+        for (int k = 0; k < cfg->n_tx; ++k) {
+            int kd = cfg->tx_kind[k];
+            if (kd == OR_TX_DIVERGING ? !(cfg->tx_z[k] < 0.0f) : kd == OR_TX_FOCUSED ? !(cfg->tx_z[k] > 0.0f)
+                                                                                     : kd != OR_TX_PLANE)
+                return -1;
+        }
+    }
     /* rough boundaries: Monte Carlo mode with the media deciding their own branches */
     if (scene_is_rough(sc) && (cfg->mode != OR_MODE_MC || sc->med_sampling)) return -1;
     ctx_t C;
@@ -885,6 +923,14 @@ void or_beamform(const or_array *ar, int32_t n_tx, const float *angles,
                  const float *x_px, int32_t nx, const float *z_px, int32_t nz,
                  double *img_re, double *img_im, int n_threads)
 {
+    or_beamform_tx(ar, n_tx, angles, NULL, NULL, NULL, rf, quad, x_px, nx, z_px, nz, img_re, img_im, n_threads);
+}
+
+void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const int32_t *tx_kind,
+                    const float *tx_x, const float *tx_z, const double *rf, const double *quad,
+                    const float *x_px, int32_t nx, const float *z_px, int32_t nz,
+                    double *img_re, double *img_im, int n_threads)
+{
     int n_el = ar->n_el, n_s = ar->n_s;
     double pitch = ar->pitch, c = ar->c_bf, fs = ar->fs;
     double x0 = -0.5 * (double)(n_el - 1) * pitch;
@@ -897,13 +943,25 @@ void or_beamform(const or_array *ar, int32_t n_tx, const float *angles,
             double x = x_px[ix], z = z_px[iz];
             double sr = 0.0, si = 0.0;
             for (int k = 0; k < n_tx; ++k) {
+                int kd = tx_kind ? tx_kind[k] : OR_TX_PLANE;
                 double st = sin((double)angles[k]), ct = cos((double)angles[k]);
-                double mn = INFINITY;
+                double vx = tx_kind ? tx_x[k] : 0.0, vz = tx_kind ? tx_z[k] : 0.0;
+                double mn = INFINITY, mx = -INFINITY;
                 for (int e = 0; e < n_el; ++e) {
-                    double v = (x0 + e * pitch) * st;
+                    double ex = x0 + e * pitch;
+                    double v = kd == OR_TX_PLANE ? ex * st : sqrt((ex - vx) * (ex - vx) + vz * vz);
                     if (v < mn) mn = v;
+                    if (v > mx) mx = v;
                 }
-                double t_tx = (x * st + z * ct - mn) / c;           /* plane wave reaches the pixel */
+                double t_tx;
+                if (kd == OR_TX_PLANE) {
+                    t_tx = (x * st + z * ct - mn) / c;               /* plane wave reaches the pixel */
+                } else if (kd == OR_TX_DIVERGING) {                  /* from the virtual source */
+                    t_tx = (sqrt((x - vx) * (x - vx) + (z - vz) * (z - vz)) - mn) / c;
+                } else {                                             /* through the focus at mx / c */
+                    double r = sqrt((x - vx) * (x - vx) + (z - vz) * (z - vz));
+                    t_tx = (mx + (z >= vz ? r : -r)) / c;
+                }
                 for (int e = 0; e < n_el; ++e) {
                     double dx = x - (x0 + e * pitch);
                     double t_rx = sqrt(z * z + dx * dx) / c;        /* echo back to element e */

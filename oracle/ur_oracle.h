@@ -28,6 +28,7 @@ extern "C" {
 #endif
 
 enum { OR_PLANE_Z = 0, OR_SPHERE = 1, OR_CYL_Y = 2 };
+enum { OR_TX_PLANE = 0, OR_TX_DIVERGING = 1, OR_TX_FOCUSED = 2 };
 enum { OR_MODE_MC = 0, OR_MODE_EXPECT = 1 };
 enum { OR_END_APERTURE = 1, OR_END_ARRAY_MISS = 2, OR_END_BOTTOM = 3,
        OR_END_PATH = 4, OR_END_TIME = 5, OR_END_MAXB = 6, OR_END_ROUGH = 7 };
@@ -69,6 +70,9 @@ typedef struct {
     int32_t mode;            /* OR_MODE_MC or OR_MODE_EXPECT (smooth scenes only) */
     int32_t rough_bsdf_only; /* 0: transducer sampling at rough boundaries, balance heuristic with the
                                 direct aperture hits (the method); 1: BSDF sampling alone (for tests) */
+    const int32_t *tx_kind;  /* nullable [n_tx]: OR_TX_* per transmit (default: plane waves of angles[]) */
+    const float *tx_x, *tx_z;/* [n_tx] with tx_kind: virtual source (diverging, z < 0) or focus
+                                (focused, z > 0) in the xz plane (m) */
 } or_trace_cfg;
 
 typedef struct {
@@ -106,6 +110,14 @@ void or_beamform(const or_array *ar, int32_t n_tx, const float *angles,
                  const double *rf, const double *quad,
                  const float *x_px, int32_t nx, const float *z_px, int32_t nz,
                  double *img_re, double *img_im, int n_threads);
+
+/* The same with transmit kinds (tx_kind, tx_x, tx_z nullable as in or_trace_cfg): the
+ * transmit delay of a diverging wave is the distance from its virtual source, that of a
+ * focused wave the arrival of the converging then diverging wave through its focus. */
+void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const int32_t *tx_kind,
+                    const float *tx_x, const float *tx_z, const double *rf, const double *quad,
+                    const float *x_px, int32_t nx, const float *z_px, int32_t nz,
+                    double *img_re, double *img_im, int n_threads);
 
 /* Envelope |I|, normalisation by its maximum, 20 log10, clip at -dyn_range_db. */
 void or_envelope_log(const double *img_re, const double *img_im, int64_t n_px,
