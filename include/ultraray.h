@@ -163,6 +163,27 @@ ur_status ur_set_array(ur_ctx *ctx, const ur_array *arr);
  * Errors: UR_ERR_INVALID_ARG, UR_ERR_STATE (array not set). */
 ur_status ur_set_plane_waves(ur_ctx *ctx, const float *angles_rad, int n_tx);
 
+/* Transmit kinds (Sec. 2.3 "Ray Emission": planar, diverging or focused
+ * wavefronts made by element delays).  A transmit is
+ *   UR_TX_PLANE:     steering angle `angle` (rad, |angle| < 60 deg), as ur_set_plane_waves;
+ *   UR_TX_DIVERGING: virtual source (x, 0, z) behind the array (z < 0): element e fires at
+ *                    (|c_e - v| - min_e' |c_e' - v|) / c_bf and its rays leave along the line
+ *                    from v through the emission point;
+ *   UR_TX_FOCUSED:   focus (x, 0, z) in front of the array (z > 0): element e fires at
+ *                    (max_e' |c_e' - f| - |c_e - f|) / c_bf and its rays head for f.
+ * Directions lie in the xz plane (the delays act laterally); the emission weight is the
+ * cosine to the element normal over the rays of the transmit (Eq. 6).  ur_beamform uses
+ * the matching transmit delays.  Host or device array of n_tx entries, 1 <= n_tx <= 65536.
+ * The adjoint and ur_beamform_noalloc take plane waves only.
+ * Errors: UR_ERR_INVALID_ARG, UR_ERR_STATE (array not set). */
+enum { UR_TX_PLANE = 0, UR_TX_DIVERGING = 1, UR_TX_FOCUSED = 2 };
+typedef struct {
+    int32_t kind;
+    float angle;     /* UR_TX_PLANE */
+    float x, z;      /* UR_TX_DIVERGING: virtual source; UR_TX_FOCUSED: focus (m) */
+} ur_transmit;
+ur_status ur_set_transmits(ur_ctx *ctx, const ur_transmit *tx, int n_tx);
+
 /* Trace n_rays_per_tx primary rays for every transmit (Eqs. 4-11, 13) and
  * deposit the pulse-shaped arrivals (Eq. 14) into the analytic channel data
  * rf + j quad, both [n_tx][n_el][n_s] float32 (overwritten).  Ray i of
@@ -372,7 +393,8 @@ ur_status ur_get_profile(ur_ctx *ctx, ur_profile *out);
  * holds until the process exits.
  *
  * Requirements: the context's array and transmits are set (UR_ERR_STATE
- * otherwise); rf, quad and every non-NULL output are device memory; x_px / z_px
+ * otherwise) and the transmits are plane waves (UR_ERR_INVALID_ARG for diverging
+ * or focused ones); rf, quad and every non-NULL output are device memory; x_px / z_px
  * may be host or device memory.  Limits: n_tx <= UR_NOALLOC_MAX_TX,
  * nx, nz <= UR_NOALLOC_MAX_AXIS, and nx * nz <= UR_NOALLOC_MAX_PIXELS when env
  * is NULL; larger requests return UR_ERR_INVALID_ARG without launching work.

@@ -30,7 +30,7 @@ EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_se
            "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune",
            "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint", "ur_nn_create", "ur_nn_destroy",
            "ur_nn_last_error", "ur_nn_param_count", "ur_nn_launch_count", "ur_nn_params", "ur_nn_set_scale", "ur_nn_forward",
-           "ur_nn_train_step")
+           "ur_nn_train_step", "ur_set_transmits")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log", "adjoint")
 
 
@@ -74,6 +74,13 @@ class BatchItem(C.Structure):
                 ("n_rays", C.c_uint64)]
 
 
+TX_PLANE, TX_DIVERGING, TX_FOCUSED = 0, 1, 2
+
+
+class Transmit(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("angle", C.c_float), ("x", C.c_float), ("z", C.c_float)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("cell_xy", C.c_float), ("cell_z", C.c_float), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("resolve_batch", C.c_int32), ("cell_y", C.c_float)]
@@ -99,6 +106,7 @@ def lib():
             L.ur_scene_upload.argtypes = [vp, C.POINTER(Medium), i32, C.POINTER(Boundary), i32, i32, f32, vp, i32, f32]
             L.ur_set_array.argtypes = [vp, C.POINTER(Array)]
             L.ur_set_plane_waves.argtypes = [vp, vp, i32]
+            L.ur_set_transmits.argtypes = [vp, C.POINTER(Transmit), i32]
             L.ur_trace.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats)]
             L.ur_trace_debug.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats), C.POINTER(Debug)]
             L.ur_beamform.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, vp, vp]
@@ -214,6 +222,17 @@ class Simulator:
         self._call(lib().ur_set_plane_waves(self._ctx, _ptr(a), a.size))
         self.n_tx = a.size
 
+    def set_transmits(self, transmits):
+        """transmits: sequence of (kind, x, z) with kind TX_DIVERGING / TX_FOCUSED (virtual source /
+        focus at (x, z) in metres) or (TX_PLANE, angle_rad, 0)."""
+        t = list(transmits)
+        arr = (Transmit * len(t))()
+        for k, (kind, a, b) in enumerate(t):
+            arr[k] = Transmit(int(kind), float(a) if int(kind) == TX_PLANE else 0.0,
+                              float(a) if int(kind) != TX_PLANE else 0.0, float(b) if int(kind) != TX_PLANE else 0.0)
+        self._call(lib().ur_set_transmits(self._ctx, arr, len(t)))
+        self.n_tx = len(t)
+
     def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0, resolve_batch=0, cell_y=0.0):
         """Grid cell sizes along x (cell_xy), y and z in metres, launch shape; 0 keeps a default."""
         t = Tuning(cell_xy, cell_z, block, blocks_per_sm, resolve_batch, cell_y)
@@ -224,7 +243,10 @@ class Simulator:
         s = workload["scene"]
         self.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], s["scatterers"], s["r_s"], slot)
         self.set_array(workload["array"])
-        self.set_plane_waves(workload["angles"])
+        if workload.get("transmits") is not None:
+            self.set_transmits(workload["transmits"])
+        else:
+            self.set_plane_waves(workload["angles"])
 
     # -- simulation ---------------------------------------------------------
     def _channel_shape(self):

@@ -92,9 +92,11 @@ struct ur_ctx {
     // array and plane-wave table
     bool array_ok = false;
     ur_array arr{};
-    std::vector<float> angles;
+    std::vector<float> angles;              // plane-wave angle per transmit (0 for the other kinds)
+    std::vector<int> tx_kinds;              // UR_TX_* per transmit
+    std::vector<float> tx_vx, tx_vz;        // virtual source / focus per transmit
     bool tx_dirty = true;
-    DevBuf delay, tx_sin, tx_cos, tx_m;
+    DevBuf delay, tx_sin, tx_cos, tx_m, tx_kind;
 
     // work items of the last trace or batch plan
     std::vector<ur::ItemP> items;
@@ -226,24 +228,37 @@ ur_status guarded(ur_ctx *c, F &&f) {
     }
 }
 
-// Plane-wave tables: per-element delays, and (sin, cos, min_e x_e sin) per angle.
+// Transmit tables: per-element delays, and per transmit the delay-and-sum constants
+// (plane wave: sin, cos, min_e x_e sin; diverging / focused wave: x, z of the virtual
+// source / focus and the smallest / largest element distance to it).
 void prepare_transmits(ur_ctx *c) {
     if (!c->tx_dirty) return;
     c->no_capture("preparing transmit tables");
     const int nt = (int)c->angles.size(), ne = c->arr.n_el;
     std::vector<ur::ff> delay((size_t)nt * ne), s(nt), co(nt), m(nt);
     const double pitch = c->arr.pitch, x0 = -0.5 * (double)(ne - 1) * pitch;
+    std::vector<double> len(ne);
     for (int k = 0; k < nt; ++k) {
-        const double th = c->angles[k];
+        const int kind = c->tx_kinds[k];
+        const double th = c->angles[k], vx = c->tx_vx[k], vz = c->tx_vz[k];
         const double sn = std::sin(th), cs = std::cos(th);
+        // path from the wave's reference to element e: x_e sin (plane), |c_e - v| (diverging),
+        // -|c_e - f| (focused); each element fires when the wavefront through the first reaches it
         double mn = INFINITY;
-        for (int e = 0; e < ne; ++e) mn = std::min(mn, (x0 + e * pitch) * sn);
+        for (int e = 0; e < ne; ++e) {
+            const double ex = x0 + e * pitch, r = std::sqrt((ex - vx) * (ex - vx) + vz * vz);
+            len[e] = kind == UR_TX_PLANE ? ex * sn : (kind == UR_TX_DIVERGING ? r : -r);
+            mn = std::min(mn, len[e]);
+        }
         for (int e = 0; e < ne; ++e)
-            delay[(size_t)k * ne + e] = split(((x0 + e * pitch) * sn - mn) / (double)c->arr.c_bf * (double)c->arr.fs);
-        s[k] = split(sn);
-        co[k] = split(cs);
-        m[k] = split(mn);
+            delay[(size_t)k * ne + e] = split((len[e] - mn) / (double)c->arr.c_bf * (double)c->arr.fs);
+        s[k] = split(kind == UR_TX_PLANE ? sn : vx);
+        co[k] = split(kind == UR_TX_PLANE ? cs : vz);
+        m[k] = split(kind == UR_TX_FOCUSED ? -mn : mn);
     }
+    c->grow(c->tx_kind, sizeof(int) * std::max(nt, 1));
+    ck(cudaMemcpyAsync(c->tx_kind.p, c->tx_kinds.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->stream),
+       "copy kinds");
     c->grow(c->delay, sizeof(ur::ff) * delay.size());
     c->grow(c->tx_sin, sizeof(ur::ff) * nt);
     c->grow(c->tx_cos, sizeof(ur::ff) * nt);
@@ -459,6 +474,9 @@ void set_items(ur_ctx *c, const std::vector<ur_batch_item> &in) {
         const double th = c->angles[b.tx];
         I.sin_t = (float)std::sin(th);
         I.cos_t = (float)std::cos(th);
+        I.kind = c->tx_kinds[b.tx];
+        I.vx = c->tx_vx[b.tx];
+        I.vz = c->tx_vz[b.tx];
         I.inv_n = (float)(1.0 / (double)b.n_rays);
         const uint64_t s = (uint64_t)I.rays_per_el * (uint64_t)n_el;
         slot += (s + ur::kTracePool - 1) / ur::kTracePool * ur::kTracePool;
@@ -560,7 +578,9 @@ void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
     P.arr_cap = c->arr_cap;
     ck(cudaMemsetAsync(P.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
     c->phase_begin(UR_PHASE_TRACE);
-    ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream);
+    bool point_waves = false;   // diverging or focused transmits take the extended tracer
+    for (const ur::ItemP &it : c->items) point_waves = point_waves || it.kind != UR_TX_PLANE;
+    ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream, point_waves);
     ck(cudaGetLastError(), "trace kernel launch");
     c->phase_end(UR_PHASE_TRACE, 1);
 }
@@ -714,6 +734,7 @@ ur::ImageP image_params(ur_ctx *c) {
     I.tx_sin = (const ur::ff *)c->tx_sin.p;
     I.tx_cos = (const ur::ff *)c->tx_cos.p;
     I.tx_m = (const ur::ff *)c->tx_m.p;
+    I.tx_kind = (const int *)c->tx_kind.p;
     return I;
 }
 
@@ -727,6 +748,8 @@ bool ctx_view(const ur_ctx *c, CtxView *v) {
     v->arr = c->arr;
     v->n_tx = (int)c->angles.size();
     v->angles = c->angles.data();
+    v->plane_waves = true;
+    for (int k : c->tx_kinds) v->plane_waves = v->plane_waves && k == UR_TX_PLANE;
     return true;
 }
 }  // namespace ur
@@ -776,7 +799,7 @@ ur_status ur_destroy(ur_ctx *c) {
         DevBuf *bs[] = {&sd.scat, &sd.amp, &sd.refs, &sd.cell_count, &sd.cell_start, &sd.cell_fill, &sd.scan_tmp, &sd.bbox};
         for (DevBuf *b : bs) c->release(*b);
     }
-    DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
+    DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->tx_kind, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
                      &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
@@ -876,6 +899,46 @@ ur_status ur_set_plane_waves(ur_ctx *c, const float *angles_rad, int n_tx) {
         for (float v : a)
             if (!(std::fabs(v) < (float)(kPi / 3.0))) fail(UR_ERR_INVALID_ARG, "|angle| must be below 60 degrees");
         c->angles = a;
+        c->tx_kinds.assign(n_tx, UR_TX_PLANE);
+        c->tx_vx.assign(n_tx, 0.f);
+        c->tx_vz.assign(n_tx, 0.f);
+        c->tx_dirty = true;
+        c->batch_ok = false;
+    });
+}
+
+ur_status ur_set_transmits(ur_ctx *c, const ur_transmit *tx, int n_tx) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_set_transmits");
+        if (!c->array_ok) fail(UR_ERR_STATE, "set the array before the transmits");
+        if (!tx || n_tx < 1 || n_tx > 65536) fail(UR_ERR_INVALID_ARG, "n_tx must be in [1, 65536]");
+        std::vector<ur_transmit> t(n_tx);
+        ck(cudaMemcpy(t.data(), tx, sizeof(ur_transmit) * n_tx, cudaMemcpyDefault), "copy transmits");
+        std::vector<float> a(n_tx, 0.f), vx(n_tx, 0.f), vz(n_tx, 0.f);
+        std::vector<int> kinds(n_tx);
+        for (int k = 0; k < n_tx; ++k) {
+            const ur_transmit &q = t[k];
+            if (q.kind == UR_TX_PLANE) {
+                if (!(std::fabs(q.angle) < (float)(kPi / 3.0))) fail(UR_ERR_INVALID_ARG, "|angle| must be below 60 degrees");
+                a[k] = q.angle;
+            } else if (q.kind == UR_TX_DIVERGING || q.kind == UR_TX_FOCUSED) {
+                if (!std::isfinite(q.x) || !std::isfinite(q.z)) fail(UR_ERR_INVALID_ARG, "transmit points must be finite");
+                if (q.kind == UR_TX_DIVERGING && !(q.z < 0.f))
+                    fail(UR_ERR_INVALID_ARG, "a diverging wave's virtual source lies behind the array (z < 0)");
+                if (q.kind == UR_TX_FOCUSED && !(q.z > 0.f))
+                    fail(UR_ERR_INVALID_ARG, "a focused wave's focus lies in front of the array (z > 0)");
+                vx[k] = q.x;
+                vz[k] = q.z;
+            } else {
+                fail(UR_ERR_INVALID_ARG, "unknown transmit kind");
+            }
+            kinds[k] = q.kind;
+        }
+        c->angles = a;
+        c->tx_kinds = kinds;
+        c->tx_vx = vx;
+        c->tx_vz = vz;
         c->tx_dirty = true;
         c->batch_ok = false;
     });
@@ -1029,6 +1092,8 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
         if (n_med > ur::kAdjMed) fail(UR_ERR_INVALID_ARG, "the adjoint supports scenes with at most 4 media");
         for (const ur_medium &m : sd.media)
             if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports smooth boundaries only");
+        for (int k : c->tx_kinds)
+            if (k != UR_TX_PLANE) fail(UR_ERR_INVALID_ARG, "the adjoint supports plane-wave transmits only");
         prepare_transmits(c);
         const int n_tx = (int)c->angles.size();
         std::vector<ur_batch_item> items(n_tx);

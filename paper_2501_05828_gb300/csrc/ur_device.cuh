@@ -157,6 +157,8 @@ struct ItemP {
     int scene, angle;
     float sin_t, cos_t, inv_n;
     uint32_t stream;        // Philox counter word identifying the transmit's random stream
+    int kind;               // UR_TX_*: plane wave (sin_t, cos_t), diverging or focused wave
+    float vx, vz;           // virtual source or focus in the xz plane (m)
 };
 
 struct TraceP {
@@ -284,7 +286,7 @@ __device__ __forceinline__ float directivity(const TraceP &P, float cos_a) {
 
 
 // ---------------------------------------------------------------- launchers
-void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s);
+void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves);
 int trace_occupancy(int block, bool debug);   // resident tracer CTAs per SM
 
 // Path-replay adjoint: loss sensitivities in, parameter gradients out.
@@ -356,7 +358,9 @@ struct ImageP {
     ff q;                   // fs / c_bf (samples per metre)
     ff x_first;             // element 0 centre
     float pitch;
-    const ff *tx_sin, *tx_cos, *tx_m;   // per angle: sin, cos, min_e x_e sin
+    const ff *tx_sin, *tx_cos, *tx_m;   // per transmit: plane wave: sin, cos, min_e x_e sin; diverging
+                                        // (focused) wave: source (focus) x, z, min (max) element distance
+    const int *tx_kind;                 // per transmit UR_TX_* (null: plane waves)
     float2 *iq;
     float *env, *db;
     unsigned int *env_max;  // float bits, one per image
@@ -381,6 +385,7 @@ struct CtxView {
     ur_array arr;
     int n_tx;
     const float *angles;    // host copy, n_tx entries
+    bool plane_waves;       // every transmit is a plane wave
 };
 bool ctx_view(const ur_ctx *c, CtxView *v);
 

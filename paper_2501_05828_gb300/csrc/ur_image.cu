@@ -38,9 +38,20 @@ __global__ void __launch_bounds__(256) k_das(const ImageP I) {
         for (int qi = q0; qi < q1; ++qi) {
             const int item = I.img_items ? I.img_items[qi] : qi;
             const int k = I.img_items ? I.item_angle[item] : item;
-            // transmit delay: plane wave reaches (x, z)
-            ff T = ff_add(ff_mul_f(x, I.tx_sin[k]), ff_mul_f(z, I.tx_cos[k]));
-            T = ff_mul(ff_add(T, ff_neg(I.tx_m[k])), I.q);
+            // transmit delay to (x, z): plane wave; distance from a virtual source; through a focus
+            const int kind = I.tx_kind ? I.tx_kind[k] : UR_TX_PLANE;
+            ff T;
+            if (kind == UR_TX_PLANE) {
+                T = ff_add(ff_mul_f(x, I.tx_sin[k]), ff_mul_f(z, I.tx_cos[k]));
+                T = ff_mul(ff_add(T, ff_neg(I.tx_m[k])), I.q);
+            } else {
+                const ff ddx = ff_add_f(ff_neg(I.tx_sin[k]), x), ddz = ff_add_f(ff_neg(I.tx_cos[k]), z);
+                const ff r = ff_sqrt(ff_add(ff_mul(ddx, ddx), ff_mul(ddz, ddz)));
+                if (kind == UR_TX_DIVERGING)
+                    T = ff_mul(ff_add(r, ff_neg(I.tx_m[k])), I.q);
+                else
+                    T = ff_mul(ff_add(I.tx_m[k], (z >= I.tx_cos[k].hi) ? r : ff_neg(r)), I.q);
+            }
             const float *rf = I.rf + (size_t)item * I.n_el * I.n_s;
             const float *qd = I.quad + (size_t)item * I.n_el * I.n_s;
             for (int e = 0; e < I.n_el; ++e) {

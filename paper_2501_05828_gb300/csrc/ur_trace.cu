@@ -258,14 +258,22 @@ __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Co
 }
 
 // Emission (Eq. 6) of ray i of item `item` (a transmit of one scene) from element e.
+template <bool EXT>
 __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &IT, uint32_t i,
                                           uint32_t e, Counters &cn) {
     const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
-    R.d = make_float3(IT.sin_t, 0.f, IT.cos_t);
+    if (!EXT || IT.kind == UR_TX_PLANE) {
+        R.d = make_float3(IT.sin_t, 0.f, IT.cos_t);
+    } else {   // along the line from the virtual source, or toward the focus, in the xz plane
+        const float sg = IT.kind == UR_TX_DIVERGING ? 1.f : -1.f;
+        const float dx = sg * (R.o.x - IT.vx), dz = sg * (0.f - IT.vz);
+        const float l = sqrtf(dx * dx + dz * dz);
+        R.d = make_float3(dx / l, 0.f, dz / l);
+    }
     R.t = P.delay[(uint32_t)IT.angle * (uint32_t)P.n_el + e];
-    R.w = IT.cos_t * IT.inv_n;
+    R.w = R.d.z * IT.inv_n;   // Eq. 6: cosine to the element normal over N
     R.scene = IT.scene;
     R.med = P.S[IT.scene].med_array;
     R.b = 0;
@@ -585,7 +593,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 const uint32_t m = (uint32_t)(local % IT.rays_per_el);
                 const uint64_t e = local / IT.rays_per_el;
                 const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray(P, R, item, IT, i, (uint32_t)e, cn);
+                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<ROUGH>(P, R, item, IT, i, (uint32_t)e, cn);
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
@@ -698,12 +706,13 @@ int trace_occupancy(int block, bool debug) {
     return n > 0 ? n : 1;
 }
 
-// Variants with frozen sampling media, with recorded (ray, event) words and with
-// rough boundaries are compiled separately so the usual kernel carries none of
-// their code.  Rough scenes never record or freeze sampling media (the adjoint
-// and ur_scene_set_media refuse them).
-void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
-    bool split = false, rough = false;
+// Variants with frozen sampling media, with recorded (ray, event) words and the
+// extended variant (rough boundaries, diverging and focused transmits) are
+// compiled separately so the usual kernel carries none of their code.  The
+// extended variant never records or freezes sampling media (the adjoint and
+// ur_scene_set_media refuse such scenes and transmits).
+void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves) {
+    bool split = false, rough = point_waves;
     for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) {
         split = split || P.S[q].split_sampling != 0;
         for (int b = 0; b < P.S[q].n_bnd; ++b) rough = rough || P.S[q].bnd[b].alpha > 0.f;
