@@ -202,13 +202,14 @@ def oracle_rate(w, target_s, threads=None):
     import oracle
     threads = threads or (os.cpu_count() or 1)
     t0 = time.perf_counter()
+    tx = w.get("transmits")   # (kind, x, z) of diverging / focused waves (the oracle's form)
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
-                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, 4096, threads=threads)
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, 4096, threads=threads, transmits=tx)
     probe = time.perf_counter() - t0
     n = int(max(1024, min(w["n_rays"], 4096 * target_s / max(probe, 1e-3))))
     t0 = time.perf_counter()
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
-                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, n, threads=threads)
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, n, threads=threads, transmits=tx)
     dt = time.perf_counter() - t0
     return n * len(np.atleast_1d(w["angles"])) / dt, n, dt, threads
 
@@ -357,7 +358,8 @@ def run_ours(args, rank, world, local_rank):
             "acquisitions_per_s": whole_job_rate(1, world, ms_max * 1e-3),
             "phase_ms": phase_ms,
             "roofline": {"bound": "alu",
-                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload != "layered" else ""),
+                         "kernel": "k_trace" + (" (extended instantiation: rough boundaries, diverging and focused "
+                                                "waves)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
@@ -388,7 +390,10 @@ PAPER_WORKLOAD = ("paper settings (Sec. 4) on a synthetic vertebra stand-in: 128
                   "acquisition), 10 bounces, 20 cm paths; water around a rough bone sphere (r 10 mm, 45 mm) and two "
                   "rough bone cylinders (GGX 0.5), 20k scatterers in the bone; DAS of all 25 transmits to 512x256, "
                   "90 dB")
-FRAME_WORKLOADS = {"layered": WORKLOAD, "rough": ROUGH_WORKLOAD, "paper": PAPER_WORKLOAD}
+DIVERGING_WORKLOAD = ("layered phantom imaged with 9 diverging waves: virtual sources 10 mm behind the array at "
+                      "x = -12..12 mm, 1.11M rays each (1e7 rays per acquisition), compounded DAS to 512x256, 60 dB")
+FRAME_WORKLOADS = {"layered": WORKLOAD, "rough": ROUGH_WORKLOAD, "paper": PAPER_WORKLOAD,
+                   "diverging": DIVERGING_WORKLOAD}
 
 
 def frame_workload(args):
@@ -397,6 +402,13 @@ def frame_workload(args):
     if args.workload == "paper":
         return phantoms.paper_like()
     w = phantoms.layered()
+    if args.workload == "diverging":
+        import numpy as np
+        xs = np.linspace(-12e-3, 12e-3, 9)
+        w["angles"] = np.zeros(xs.size, np.float32)
+        w["transmits"] = [(1, float(x), -10e-3) for x in xs]   # (diverging, virtual source x, z)
+        w["n_rays"] = 10_000_000 // xs.size
+        return w
     if args.workload == "rough":
         s = dict(w["scene"])
         med = [list(m) for m in s["media"]]
@@ -528,7 +540,8 @@ def run_batched(args, rank, world, local_rank):
             "arrivals_per_step": n_arr2, "stats_per_step": st,
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
             "roofline": {"bound": "alu",
-                         "kernel": "k_trace" + (" (rough-boundary instantiation)" if args.workload != "layered" else ""),
+                         "kernel": "k_trace" + (" (extended instantiation: rough boundaries, diverging and focused "
+                                                "waves)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
             "gpu_launches": 7 * args.steps, "clocks": clk,
@@ -848,7 +861,7 @@ def main():
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
     ap.add_argument("--workload", default="layered",
-                    choices=("layered", "rough", "paper", "batched", "adjoint", "denoiser"))
+                    choices=("layered", "rough", "paper", "diverging", "batched", "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -856,7 +869,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     args.warmup = max(3, args.warmup)
     if args.steps <= 0:
-        args.steps = {"layered": 150, "rough": 60, "paper": 30, "batched": 5, "adjoint": 30,
+        args.steps = {"layered": 150, "rough": 60, "paper": 30, "diverging": 60, "batched": 5, "adjoint": 30,
                       "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
