@@ -60,7 +60,7 @@ class Array(C.Structure):
     _fields_ = [("n_el", C.c_int32), ("pitch", C.c_float), ("elev_h", C.c_float),
                 ("f0", C.c_float), ("fs", C.c_float), ("n_s", C.c_int32),
                 ("n_cycles", C.c_float), ("alpha_m_deg", C.c_float), ("alpha_c_deg", C.c_float),
-                ("c_bf", C.c_float), ("tcut_sigmas", C.c_float)]
+                ("c_bf", C.c_float), ("tcut_sigmas", C.c_float), ("radius", C.c_float)]
 
 
 class TraceCfg(C.Structure):
@@ -174,7 +174,7 @@ def make_scene(scene):
 def make_array(arr):
     return Array(int(arr["n_el"]), arr["pitch"], arr["elev_h"], arr["f0"], arr["fs"], int(arr["n_s"]),
                  arr["n_cycles"], arr["alpha_m_deg"], arr["alpha_c_deg"], arr["c_bf"],
-                 arr["tcut_sigmas"])
+                 arr["tcut_sigmas"], float(arr.get("radius", 0.0)))
 
 
 def philox4x32_10(ctr, key):

@@ -20,6 +20,15 @@
  *    the virtual source, or toward the focus, projected on the xz plane (the
  *    delays act laterally only, so directions keep y = 0 as for plane waves);
  *    the Eq. 6 weight is the cosine to the element normal over N.
+ *  - Convex array (Sec. 2.3 describes the transducer by its elements, elevation,
+ *    radius and opening angle): element centres lie `pitch` apart on the arc of
+ *    radius R about (0, 0, -R), apex at the origin, normals radial; the probe is
+ *    the cylinder inside the arc.  A ray leaves a uniform point of its element's
+ *    arc face (weight: cosine to the local normal over N; none if that is not
+ *    positive); returning rays end on the cylinder, inside the aperture at the
+ *    element whose arc holds the hit, and rays passing the probe end on the plane
+ *    z = -R.  Connections, directivities and delays use element centres and
+ *    normals.
  *  - Transducer sampling: delta (smooth) boundaries contribute only through the
  *    primary ray crossing the array plane; point scatterers contribute only
  *    through a straight connection ray to a uniformly chosen element centre,
@@ -178,11 +187,26 @@ typedef struct {
     double am, ac;              /* directivity angles (rad) */
     int top, bot;               /* ids of the terminal planes */
     double *alpha_b;            /* per boundary: GGX roughness (0: smooth) */
+    double R, dphi, phi0;       /* convex array: radius, angle between centres, angle of element 0 */
+    int esc;                    /* id of the escape plane z = -R (convex arrays) */
     int *kind;                  /* per transmit: OR_TX_* */
     double *vx, *vz;            /* per transmit: virtual source or focus (m) */
 } ctx_t;
 
 static double elem_x(const ctx_t *C, int e) { return C->x0 + (double)e * C->pitch; }
+
+/* Centre and unit normal of element e (linear: (x_e, 0, 0), +z). */
+static void elem_frame(const ctx_t *C, int e, double c[3], double n[3])
+{
+    if (C->R > 0.0) {
+        double ph = C->phi0 + (double)e * C->dphi;
+        n[0] = sin(ph); n[1] = 0.0; n[2] = cos(ph);
+        c[0] = C->R * n[0]; c[1] = 0.0; c[2] = C->R * (n[2] - 1.0);
+    } else {
+        c[0] = elem_x(C, e); c[1] = 0.0; c[2] = 0.0;
+        n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+    }
+}
 
 /* Nearest boundary along o + t d with t in (OR_TMIN, inf).  `skip` is the
  * primitive the ray is leaving: a plane cannot be hit again, a sphere or
@@ -231,7 +255,25 @@ static int nearest_boundary(const ctx_t *C, const double o[3], const double d[3]
         }
         if (t > OR_TMIN && t < best) { best = t; hit = p; }
     }
-    if (terminals) {
+    if (terminals && C->R > 0.0) {   /* convex probe: its cylinder, the escape plane z = -R, the bottom */
+        double ox = o[0], oz = o[2] + C->R;
+        double a = d[0] * d[0] + d[2] * d[2];
+        if (a > 0.0) {
+            double b = ox * d[0] + oz * d[2], cc = ox * ox + oz * oz - C->R * C->R;
+            double disc = b * b - a * cc;
+            if (disc >= 0.0 && b < 0.0) {
+                double t = (-b - sqrt(disc)) / a;
+                if (t > OR_TMIN && t < best) { best = t; hit = C->top; }
+            }
+        }
+        if (d[2] < 0.0) {
+            double t = (-C->R - o[2]) / d[2];
+            if (t > OR_TMIN && t < best) { best = t; hit = C->esc; }
+        } else if (d[2] > 0.0) {
+            double t = ((double)sc->z_max - o[2]) / d[2];
+            if (t > OR_TMIN && t < best) { best = t; hit = C->bot; }
+        }
+    } else if (terminals) {
         if (d[2] < 0.0) {
             double t = -o[2] / d[2];
             if (t > OR_TMIN && t < best) { best = t; hit = C->top; }
@@ -267,11 +309,11 @@ static int far_medium(const ctx_t *C, int p, const double d[3], const double n_o
 
 /* Connection (secondary) ray: straight from p to the element centre; `skip0` is
  * the boundary p lies on (-1 for a point inside a medium). */
-static double connection_from(const ctx_t *C, const double p[3], int med, int skip0, double x_e,
-                              double *t_samples, double *atten)
+static double connection_to(const ctx_t *C, const double p[3], int med, int skip0, const double q[3],
+                            double *t_samples, double *atten)
 {
     double o[3] = {p[0], p[1], p[2]};
-    double w[3] = {x_e - p[0], -p[1], -p[2]};
+    double w[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
     double rem = sqrt(dot3(w, w));
     w[0] /= rem; w[1] /= rem; w[2] /= rem;
     double fac = 1.0, t = 0.0, att = 0.0;
@@ -308,7 +350,8 @@ static double connection_from(const ctx_t *C, const double p[3], int med, int sk
 static double connection(const ctx_t *C, const double p[3], int med, double x_e,
                          double *t_samples, double *atten)
 {
-    return connection_from(C, p, med, -1, x_e, t_samples, atten);
+    double q[3] = {x_e, 0.0, 0.0};
+    return connection_to(C, p, med, -1, q, t_samples, atten);
 }
 
 /* ------------------------------------------------------ rough boundaries */
@@ -463,15 +506,16 @@ static void scatter_event(const ctx_t *C, ray_job *J, int j, double t_ca, double
         pick_w = (double)n_el;               /* 1 / p(element) */
     }
     for (int e = e_lo; e < e_hi; ++e) {
-        double xe = elem_x(C, e);
-        double v[3] = {xe - p[0], -p[1], -p[2]};
+        double ce[3], ne[3];
+        elem_frame(C, e, ce, ne);
+        double v[3] = {ce[0] - p[0], ce[1] - p[1], ce[2] - p[2]};
         double D = sqrt(dot3(v, v));
-        double alpha = acos(-v[2] / D);
+        double alpha = acos(-dot3(v, ne) / D);               /* to the element normal */
         double fd = or_directivity(alpha, C->am, C->ac);   /* Eq. 13 */
         if (!(fd > 0.0)) continue;
         J->st.connections++;
         double tc, ac;
-        double fac = connection(C, p, med, xe, &tc, &ac);
+        double fac = connection_to(C, p, med, -1, ce, &tc, &ac);
         if (fac == 0.0) continue;
         double t_arr = t + t_ca * C->slow[med] + tc;
         if (t_arr > C->t_last) continue;
@@ -510,11 +554,12 @@ static void rough_nee(const ctx_t *C, ray_job *J, const double p[3], const doubl
     uint32_t x[4];
     draw(C->cfg->seed, J->i, (uint32_t)J->k, 4u | ((uint32_t)b << 8), 0u, x);
     int e = (int)((((uint64_t)(x[0] >> 8)) * (uint64_t)n_el) >> 24);
-    double xe = elem_x(C, e);
-    double v[3] = {xe - p[0], -p[1], -p[2]};
+    double ce[3], ne[3];
+    elem_frame(C, e, ce, ne);
+    double v[3] = {ce[0] - p[0], ce[1] - p[1], ce[2] - p[2]};
     double D = sqrt(dot3(v, v));
     double o[3] = {v[0] / D, v[1] / D, v[2] / D};
-    double cos_e = p[2] / D;                               /* at the element, to its normal */
+    double cos_e = -dot3(o, ne);                           /* at the element, to its normal */
     double fd = or_directivity(acos(cos_e), C->am, C->ac);  /* Eq. 13 */
     if (!(fd > 0.0)) return;
     double pdf_bsdf;
@@ -522,7 +567,7 @@ static void rough_nee(const ctx_t *C, ray_job *J, const double p[3], const doubl
     if (!(f > 0.0)) return;
     J->st.connections++;
     double tc, ac;
-    double fac = connection_from(C, p, dot3(o, n) > 0.0 ? med : m2, hit, xe, &tc, &ac);
+    double fac = connection_to(C, p, dot3(o, n) > 0.0 ? med : m2, hit, ce, &tc, &ac);
     if (fac == 0.0) return;
     double t_arr = t + tc;
     if (t_arr > C->t_last) return;
@@ -602,19 +647,31 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
         L += seg;
         for (int q = 0; q < 3; ++q) o[q] += seg * d[q];
         if (clipped) return OR_END_PATH;
+        if (hit == C->esc) return OR_END_ARRAY_MISS;
         if (hit == C->top) {
-            o[2] = 0.0;
-            double xl = C->x0 - 0.5 * C->pitch;
-            if (fabs(o[1]) <= 0.5 * C->H && o[0] >= xl && o[0] < xl + ar->n_el * C->pitch) {
-                int e = (int)floor((o[0] - xl) / C->pitch);
-                if (e > ar->n_el - 1) e = ar->n_el - 1;
-                double fd = or_directivity(acos(-d[2]), C->am, C->ac);
+            int e = -1;
+            if (C->R > 0.0) {   /* on the probe's cylinder: the element whose arc holds the hit */
+                double ph = atan2(o[0], o[2] + C->R);
+                double u = (ph - C->phi0) / C->dphi + 0.5;
+                if (fabs(o[1]) <= 0.5 * C->H && u >= 0.0 && u < (double)ar->n_el) e = (int)floor(u);
+            } else {
+                o[2] = 0.0;
+                double xl = C->x0 - 0.5 * C->pitch;
+                if (fabs(o[1]) <= 0.5 * C->H && o[0] >= xl && o[0] < xl + ar->n_el * C->pitch) {
+                    e = (int)floor((o[0] - xl) / C->pitch);
+                    if (e > ar->n_el - 1) e = ar->n_el - 1;
+                }
+            }
+            if (e >= 0) {
+                double ce[3], ne[3];
+                elem_frame(C, e, ce, ne);
+                double fd = or_directivity(acos(-dot3(d, ne)), C->am, C->ac);
                 if (fd > 0.0 && t <= C->t_last) {
                     double wa = w * fd;
                     if (mis && !cfg->rough_bsdf_only) {   /* balance heuristic against transducer sampling */
-                        double v[3] = {elem_x(C, e) - mis_p[0], -mis_p[1], -mis_p[2]};
+                        double v[3] = {ce[0] - mis_p[0], ce[1] - mis_p[1], ce[2] - mis_p[2]};
                         double D2 = dot3(v, v);
-                        double omega = C->pitch * C->H * (mis_p[2] / sqrt(D2)) / D2;
+                        double omega = C->pitch * C->H * (-dot3(v, ne) / sqrt(D2)) / D2;
                         if (omega > 0.0) wa *= mis_pdf / (mis_pdf + 1.0 / ((double)ar->n_el * omega));
                     }
                     push(J->buf, J->k, e, J->i, 0x80000000u | ((uint32_t)b << 24), t, wa, J->seq++);
@@ -705,6 +762,12 @@ static uint64_t trace_ray(const ctx_t *C, ray_job *J)
     uint32_t x[4];
     draw(C->cfg->seed, J->i, (uint32_t)J->k, 0u, 0u, x);
     double o[3] = {elem_x(C, e) + (u24(x[0]) - 0.5) * C->pitch, (u24(x[1]) - 0.5) * C->H, 0.0};
+    double nrm[3] = {0.0, 0.0, 1.0};              /* normal at the emission point */
+    if (C->R > 0.0) {                              /* a point of the element's arc face */
+        double ph = C->phi0 + ((double)e + u24(x[0]) - 0.5) * C->dphi;
+        nrm[0] = sin(ph); nrm[2] = cos(ph);
+        o[0] = C->R * nrm[0]; o[2] = C->R * (nrm[2] - 1.0);
+    }
     double d[3] = {C->sin_t[J->k], 0.0, C->cos_t[J->k]};
     if (C->kind[J->k] != OR_TX_PLANE) {   /* along the line from the virtual source / toward the focus */
         double sg = C->kind[J->k] == OR_TX_DIVERGING ? 1.0 : -1.0;
@@ -713,7 +776,11 @@ static uint64_t trace_ray(const ctx_t *C, ray_job *J)
         d[0] = dx / l; d[1] = 0.0; d[2] = dz / l;
     }
     double t = C->delay[J->k * ar->n_el + e];
-    double w = d[2] / (double)C->cfg->n_rays;   /* Eq. 6: cosine to the element normal over N */
+    double w = dot3(d, nrm) / (double)C->cfg->n_rays;   /* Eq. 6: cosine to the face normal over N */
+    if (!(w > 0.0)) {                              /* aimed into the probe: no ray */
+        J->st.rays++;
+        return fnv(OR_FNV_OFFSET, 0x20000u | (uint32_t)OR_END_ARRAY_MISS);
+    }
     uint64_t h = OR_FNV_OFFSET;
     int reason = follow(C, J, o, d, t, w, C->sc->med_array, 0, 0.0, -1, &h);
     J->st.rays++;
@@ -745,6 +812,9 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
     C->pitch = ar->pitch;
     C->H = ar->elev_h;
     C->x0 = -0.5 * (double)(ar->n_el - 1) * C->pitch;
+    C->R = ar->radius > 0.0f ? (double)ar->radius : 0.0;
+    C->dphi = C->R > 0.0 ? C->pitch / C->R : 0.0;
+    C->phi0 = -0.5 * (double)(ar->n_el - 1) * C->dphi;
     for (int k = 0; k < nt; ++k) {
         double th = cfg->angles ? cfg->angles[k] : 0.0;
         C->kind[k] = cfg->tx_kind ? cfg->tx_kind[k] : OR_TX_PLANE;
@@ -758,8 +828,10 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
          * reaches it. */
         double mn = INFINITY, *len = (double *)malloc(sizeof(double) * (size_t)ar->n_el);
         for (int e = 0; e < ar->n_el; ++e) {
-            double dx = elem_x(C, e) - C->vx[k], dz = -C->vz[k];
-            if (C->kind[k] == OR_TX_PLANE) len[e] = elem_x(C, e) * C->sin_t[k];
+            double ce[3], ne[3];
+            elem_frame(C, e, ce, ne);
+            double dx = ce[0] - C->vx[k], dz = ce[2] - C->vz[k];
+            if (C->kind[k] == OR_TX_PLANE) len[e] = ce[0] * C->sin_t[k] + ce[2] * C->cos_t[k];
             else if (C->kind[k] == OR_TX_DIVERGING) len[e] = sqrt(dx * dx + dz * dz);
             else len[e] = -sqrt(dx * dx + dz * dz);
             if (len[e] < mn) mn = len[e];
@@ -775,6 +847,7 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
     C->ac = (double)ar->alpha_c_deg * OR_PI / 180.0;
     C->top = sc->n_bnd;
     C->bot = sc->n_bnd + 1;
+    C->esc = sc->n_bnd + 2;
     C->alpha_b = (double *)malloc(sizeof(double) * (size_t)(sc->n_bnd > 0 ? sc->n_bnd : 1));
     for (int p = 0; p < sc->n_bnd; ++p) {
         double a0 = sc->med[4 * sc->bnd_med[2 * p] + 3], a1 = sc->med[4 * sc->bnd_med[2 * p + 1] + 3];
@@ -807,6 +880,8 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
         return -1;
     for (int m = 0; m < sc->n_med; ++m)
         if (!(sc->med[4 * m + 3] >= 0.0f && sc->med[4 * m + 3] <= 4.0f)) return -1;
+    if (!(ar->radius >= 0.0f) || (ar->radius > 0.0f && !((double)ar->n_el * ar->pitch < 3.0 * ar->radius)))
+        return -1;   /* convex: the aperture spans less than about 170 degrees */
     if (cfg->tx_kind) {
         if (!cfg->tx_x || !cfg->tx_z) return -1;
         for (int k = 0; k < cfg->n_tx; ++k) {
@@ -932,8 +1007,20 @@ void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const
                     double *img_re, double *img_im, int n_threads)
 {
     int n_el = ar->n_el, n_s = ar->n_s;
-    double pitch = ar->pitch, c = ar->c_bf, fs = ar->fs;
-    double x0 = -0.5 * (double)(n_el - 1) * pitch;
+    double c = ar->c_bf, fs = ar->fs;
+    ctx_t G;                 /* element centres only */
+    memset(&G, 0, sizeof G);
+    G.pitch = ar->pitch;
+    G.x0 = -0.5 * (double)(n_el - 1) * G.pitch;
+    G.R = ar->radius > 0.0f ? (double)ar->radius : 0.0;
+    G.dphi = G.R > 0.0 ? G.pitch / G.R : 0.0;
+    G.phi0 = -0.5 * (double)(n_el - 1) * G.dphi;
+    double *cx = (double *)malloc(sizeof(double) * 2 * (size_t)n_el), *cz = cx + n_el;
+    for (int e = 0; e < n_el; ++e) {
+        double ce[3], ne[3];
+        elem_frame(&G, e, ce, ne);
+        cx[e] = ce[0]; cz[e] = ce[2];
+    }
     if (n_threads <= 0) n_threads = 1;
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(n_threads) schedule(dynamic, 4)
@@ -948,8 +1035,8 @@ void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const
                 double vx = tx_kind ? tx_x[k] : 0.0, vz = tx_kind ? tx_z[k] : 0.0;
                 double mn = INFINITY, mx = -INFINITY;
                 for (int e = 0; e < n_el; ++e) {
-                    double ex = x0 + e * pitch;
-                    double v = kd == OR_TX_PLANE ? ex * st : sqrt((ex - vx) * (ex - vx) + vz * vz);
+                    double v = kd == OR_TX_PLANE ? cx[e] * st + cz[e] * ct
+                                                 : sqrt((cx[e] - vx) * (cx[e] - vx) + (cz[e] - vz) * (cz[e] - vz));
                     if (v < mn) mn = v;
                     if (v > mx) mx = v;
                 }
@@ -963,8 +1050,8 @@ void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const
                     t_tx = (mx + (z >= vz ? r : -r)) / c;
                 }
                 for (int e = 0; e < n_el; ++e) {
-                    double dx = x - (x0 + e * pitch);
-                    double t_rx = sqrt(z * z + dx * dx) / c;        /* echo back to element e */
+                    double dx = x - cx[e], dz = z - cz[e];
+                    double t_rx = sqrt(dz * dz + dx * dx) / c;      /* echo back to element e */
                     double tau = (t_tx + t_rx) * fs;
                     if (tau < 0.0 || tau > (double)(n_s - 1)) continue;
                     long i0 = (long)floor(tau);
@@ -980,6 +1067,7 @@ void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const
             img_im[(size_t)iz * nx + ix] = si;
         }
     }
+    free(cx);
 }
 
 void or_envelope_log(const double *img_re, const double *img_im, int64_t n_px,
@@ -1317,7 +1405,8 @@ int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, con
             const double *g_q, double *grad_media, double *grad_amp, int n_threads)
 {
     if (!sc || !ar || !cfg || !g_rf || !g_q || !grad_media || sc->n_med > 4 || cfg->mode != OR_MODE_MC ||
-        cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling || scene_is_rough(sc))
+        cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling || scene_is_rough(sc) ||
+        ar->radius != 0.0f || cfg->tx_kind)
         return -1;
     ctx_t C;
     setup(&C, sc, ar, cfg);

@@ -30,7 +30,7 @@ extern "C" {
 enum { OR_PLANE_Z = 0, OR_SPHERE = 1, OR_CYL_Y = 2 };
 enum { OR_TX_PLANE = 0, OR_TX_DIVERGING = 1, OR_TX_FOCUSED = 2 };
 enum { OR_MODE_MC = 0, OR_MODE_EXPECT = 1 };
-enum { OR_END_APERTURE = 1, OR_END_ARRAY_MISS = 2, OR_END_BOTTOM = 3,
+enum { OR_END_APERTURE = 1, OR_END_ARRAY_MISS = 2, OR_END_BOTTOM = 3,  /* 2: missed the aperture or escaped past a convex probe */
        OR_END_PATH = 4, OR_END_TIME = 5, OR_END_MAXB = 6, OR_END_ROUGH = 7 };
 
 typedef struct {
@@ -57,6 +57,8 @@ typedef struct {
     float pitch, elev_h, f0, fs;
     int32_t n_s;
     float n_cycles, alpha_m_deg, alpha_c_deg, c_bf, tcut_sigmas;
+    float radius;            /* 0: linear array on z = 0; > 0: convex array, elements on the arc of this
+                                radius about (0, 0, -radius), centres `pitch` apart along the arc */
 } or_array;
 
 typedef struct {
