@@ -80,8 +80,13 @@ typedef struct {
     float p[4];
 } ur_boundary;
 
-/* Linear transducer (Sec. 2.3 "Ray Emission"; parameters of Sec. 4).
- * n_el elements at x_e = (e - (n_el-1)/2) pitch; f0 centre frequency (Hz);
+/* Transducer (Sec. 2.3 "Ray Emission"; parameters of Sec. 4).  Linear
+ * (radius = 0): n_el elements at x_e = (e - (n_el-1)/2) pitch on z = 0, normal +z.
+ * Convex (radius R > 0): element centres `pitch` apart along the arc of radius R
+ * about (0, 0, -R), apex at the origin, normals radial (opening angle
+ * n_el pitch / R, below about 170 degrees); the probe is the cylinder inside the
+ * arc, returning rays are received where they meet it and rays passing beside it
+ * end at z = -R; boundaries must stay out of the probe.  f0 centre frequency (Hz);
  * fs sampling frequency (Hz); n_s samples per channel; n_cycles sets the pulse
  * width s = n_cycles/(4 f0) of Eq. 14; alpha_m_deg / alpha_c_deg are the
  * main-beam and cutoff angles of Eq. 13 (equal values give a step);
@@ -92,6 +97,7 @@ typedef struct {
     float pitch, elev_h, f0, fs;
     int32_t n_s;
     float n_cycles, alpha_m_deg, alpha_c_deg, c_bf, tcut_sigmas;
+    float radius;            /* 0: linear array; > 0: convex array of this radius (m) */
 } ur_array;
 
 /* Counters of one trace call. */
@@ -174,7 +180,7 @@ ur_status ur_set_plane_waves(ur_ctx *ctx, const float *angles_rad, int n_tx);
  * Directions lie in the xz plane (the delays act laterally); the emission weight is the
  * cosine to the element normal over the rays of the transmit (Eq. 6).  ur_beamform uses
  * the matching transmit delays.  Host or device array of n_tx entries, 1 <= n_tx <= 65536.
- * The adjoint and ur_beamform_noalloc take plane waves only.
+ * The adjoint and ur_beamform_noalloc take plane waves (and linear arrays) only.
  * Errors: UR_ERR_INVALID_ARG, UR_ERR_STATE (array not set). */
 enum { UR_TX_PLANE = 0, UR_TX_DIVERGING = 1, UR_TX_FOCUSED = 2 };
 typedef struct {
@@ -393,8 +399,8 @@ ur_status ur_get_profile(ur_ctx *ctx, ur_profile *out);
  * holds until the process exits.
  *
  * Requirements: the context's array and transmits are set (UR_ERR_STATE
- * otherwise) and the transmits are plane waves (UR_ERR_INVALID_ARG for diverging
- * or focused ones); rf, quad and every non-NULL output are device memory; x_px / z_px
+ * otherwise), the transmits are plane waves and the array is linear
+ * (UR_ERR_INVALID_ARG otherwise); rf, quad and every non-NULL output are device memory; x_px / z_px
  * may be host or device memory.  Limits: n_tx <= UR_NOALLOC_MAX_TX,
  * nx, nz <= UR_NOALLOC_MAX_AXIS, and nx * nz <= UR_NOALLOC_MAX_PIXELS when env
  * is NULL; larger requests return UR_ERR_INVALID_ARG without launching work.

@@ -51,7 +51,7 @@ class Boundary(C.Structure):
 class Array(C.Structure):
     _fields_ = [("n_el", C.c_int32), ("pitch", C.c_float), ("elev_h", C.c_float), ("f0", C.c_float),
                 ("fs", C.c_float), ("n_s", C.c_int32), ("n_cycles", C.c_float), ("alpha_m_deg", C.c_float),
-                ("alpha_c_deg", C.c_float), ("c_bf", C.c_float), ("tcut_sigmas", C.c_float)]
+                ("alpha_c_deg", C.c_float), ("c_bf", C.c_float), ("tcut_sigmas", C.c_float), ("radius", C.c_float)]
 
 
 class Stats(C.Structure):
@@ -214,7 +214,8 @@ class Simulator:
     def set_array(self, arr):
         self.array = dict(arr)
         a = Array(int(arr["n_el"]), arr["pitch"], arr["elev_h"], arr["f0"], arr["fs"], int(arr["n_s"]),
-                  arr["n_cycles"], arr["alpha_m_deg"], arr["alpha_c_deg"], arr["c_bf"], arr["tcut_sigmas"])
+                  arr["n_cycles"], arr["alpha_m_deg"], arr["alpha_c_deg"], arr["c_bf"], arr["tcut_sigmas"],
+                  float(arr.get("radius", 0.0)))
         self._call(lib().ur_set_array(self._ctx, C.byref(a)))
 
     def set_plane_waves(self, angles_rad):

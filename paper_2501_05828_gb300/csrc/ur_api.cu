@@ -96,7 +96,7 @@ struct ur_ctx {
     std::vector<int> tx_kinds;              // UR_TX_* per transmit
     std::vector<float> tx_vx, tx_vz;        // virtual source / focus per transmit
     bool tx_dirty = true;
-    DevBuf delay, tx_sin, tx_cos, tx_m, tx_kind;
+    DevBuf delay, tx_sin, tx_cos, tx_m, tx_kind, elem_xz;
 
     // work items of the last trace or batch plan
     std::vector<ur::ItemP> items;
@@ -237,17 +237,23 @@ void prepare_transmits(ur_ctx *c) {
     const int nt = (int)c->angles.size(), ne = c->arr.n_el;
     std::vector<ur::ff> delay((size_t)nt * ne), s(nt), co(nt), m(nt);
     const double pitch = c->arr.pitch, x0 = -0.5 * (double)(ne - 1) * pitch;
-    std::vector<double> len(ne);
+    std::vector<double> len(ne), cx(ne), cz(ne);   // element centres: linear, or on the convex arc
+    const double R = c->arr.radius, dphi = R > 0.0 ? pitch / R : 0.0, phi0 = -0.5 * (double)(ne - 1) * dphi;
+    for (int e = 0; e < ne; ++e) {
+        cx[e] = R > 0.0 ? R * std::sin(phi0 + e * dphi) : x0 + e * pitch;
+        cz[e] = R > 0.0 ? R * (std::cos(phi0 + e * dphi) - 1.0) : 0.0;
+    }
     for (int k = 0; k < nt; ++k) {
         const int kind = c->tx_kinds[k];
         const double th = c->angles[k], vx = c->tx_vx[k], vz = c->tx_vz[k];
         const double sn = std::sin(th), cs = std::cos(th);
-        // path from the wave's reference to element e: x_e sin (plane), |c_e - v| (diverging),
-        // -|c_e - f| (focused); each element fires when the wavefront through the first reaches it
+        // path from the wave's reference to element e: c_e . (sin, cos) (plane), |c_e - v|
+        // (diverging), -|c_e - f| (focused); each element fires when the wavefront through the
+        // first-firing element reaches it
         double mn = INFINITY;
         for (int e = 0; e < ne; ++e) {
-            const double ex = x0 + e * pitch, r = std::sqrt((ex - vx) * (ex - vx) + vz * vz);
-            len[e] = kind == UR_TX_PLANE ? ex * sn : (kind == UR_TX_DIVERGING ? r : -r);
+            const double r = std::sqrt((cx[e] - vx) * (cx[e] - vx) + (cz[e] - vz) * (cz[e] - vz));
+            len[e] = kind == UR_TX_PLANE ? cx[e] * sn + cz[e] * cs : (kind == UR_TX_DIVERGING ? r : -r);
             mn = std::min(mn, len[e]);
         }
         for (int e = 0; e < ne; ++e)
@@ -255,6 +261,17 @@ void prepare_transmits(ur_ctx *c) {
         s[k] = split(kind == UR_TX_PLANE ? sn : vx);
         co[k] = split(kind == UR_TX_PLANE ? cs : vz);
         m[k] = split(kind == UR_TX_FOCUSED ? -mn : mn);
+    }
+    if (R > 0.0) {   // element centres for the convex delay-and-sum
+        std::vector<ur::ff> exz(2 * (size_t)ne);
+        for (int e = 0; e < ne; ++e) {
+            exz[2 * e] = split(cx[e]);
+            exz[2 * e + 1] = split(cz[e]);
+        }
+        c->grow(c->elem_xz, sizeof(ur::ff) * exz.size());
+        ck(cudaMemcpyAsync(c->elem_xz.p, exz.data(), sizeof(ur::ff) * exz.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy element centres");
+        ck(cudaStreamSynchronize(c->stream), "element centres");
     }
     c->grow(c->tx_kind, sizeof(int) * std::max(nt, 1));
     ck(cudaMemcpyAsync(c->tx_kind.p, c->tx_kinds.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->stream),
@@ -514,6 +531,9 @@ ur::TraceP make_trace_params(ur_ctx *c, uint64_t seed, int max_b, float max_path
     P.pitch = A.pitch;
     P.H = A.elev_h;
     P.x_first = (float)(-0.5 * (double)(A.n_el - 1) * (double)A.pitch);
+    P.radius = A.radius;
+    P.dphi = A.radius > 0.f ? (float)((double)A.pitch / (double)A.radius) : 0.f;
+    P.phi0 = (float)(-0.5 * (double)(A.n_el - 1) * (double)P.dphi);
     const double s_samples = (double)A.n_cycles / (4.0 * (double)A.f0) * (double)A.fs;
     P.K = (float)((double)A.tcut_sigmas * s_samples);
     P.t_last = (float)((double)(A.n_s - 1) + (double)P.K);
@@ -735,6 +755,7 @@ ur::ImageP image_params(ur_ctx *c) {
     I.tx_cos = (const ur::ff *)c->tx_cos.p;
     I.tx_m = (const ur::ff *)c->tx_m.p;
     I.tx_kind = (const int *)c->tx_kind.p;
+    I.elem_xz = c->arr.radius > 0.f ? (const ur::ff *)c->elem_xz.p : nullptr;
     return I;
 }
 
@@ -750,6 +771,7 @@ bool ctx_view(const ur_ctx *c, CtxView *v) {
     v->angles = c->angles.data();
     v->plane_waves = true;
     for (int k : c->tx_kinds) v->plane_waves = v->plane_waves && k == UR_TX_PLANE;
+    v->linear = c->arr.radius == 0.f;
     return true;
 }
 }  // namespace ur
@@ -799,7 +821,7 @@ ur_status ur_destroy(ur_ctx *c) {
         DevBuf *bs[] = {&sd.scat, &sd.amp, &sd.refs, &sd.cell_count, &sd.cell_start, &sd.cell_fill, &sd.scan_tmp, &sd.bbox};
         for (DevBuf *b : bs) c->release(*b);
     }
-    DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->tx_kind, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
+    DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->tx_kind, &c->elem_xz, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
                      &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
@@ -881,6 +903,9 @@ ur_status ur_set_array(ur_ctx *c, const ur_array *a) {
             fail(UR_ERR_INVALID_ARG, "need 0 <= alpha_m <= alpha_c < 90 degrees");
         const double K = (double)A.tcut_sigmas * (double)A.n_cycles / (4.0 * (double)A.f0) * (double)A.fs;
         if (K > 2048.0) fail(UR_ERR_INVALID_ARG, "pulse longer than 2048 samples");
+        if (!(A.radius >= 0.f) || !std::isfinite(A.radius) ||
+            (A.radius > 0.f && !((double)A.n_el * A.pitch < 3.0 * (double)A.radius)))
+            fail(UR_ERR_INVALID_ARG, "radius must be 0 (linear) or a convex radius with an opening below 170 degrees");
         c->arr = A;
         c->array_ok = true;
         c->tx_dirty = true;
@@ -1094,6 +1119,7 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
             if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports smooth boundaries only");
         for (int k : c->tx_kinds)
             if (k != UR_TX_PLANE) fail(UR_ERR_INVALID_ARG, "the adjoint supports plane-wave transmits only");
+        if (c->arr.radius != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports linear arrays only");
         prepare_transmits(c);
         const int n_tx = (int)c->angles.size();
         std::vector<ur_batch_item> items(n_tx);

@@ -166,7 +166,8 @@ struct TraceP {
     int n_scenes;
     // array
     int n_el, n_s;
-    float pitch, H, x_first;        // element 0 centre
+    float pitch, H, x_first;        // element 0 centre (linear array)
+    float radius, dphi, phi0;       // convex array (radius > 0): angle between centres, angle of element 0
     float K, t_last;                // pulse half-width and latest useful arrival (samples)
     float cos_am, cos_ac, am, ac;   // directivity (Eq. 13)
     // work: items (transmit x scene) and their slots
@@ -196,7 +197,7 @@ struct TraceP {
 // (id n_bnd, upward rays) and the absorbing plane z = z_max (id n_bnd + 1,
 // downward rays) take part.
 __device__ __forceinline__ int nearest(const SceneP &S, float3 o, float3 d, int skip, bool terminals,
-                                       float &t_out) {
+                                       float &t_out, float radius = 0.f) {
     float best = INFINITY;
     int hit = -1;
     for (int p = 0; p < S.n_bnd; ++p) {
@@ -239,7 +240,34 @@ __device__ __forceinline__ int nearest(const SceneP &S, float3 o, float3 d, int 
             hit = p;
         }
     }
-    if (terminals) {
+    if (terminals && radius > 0.f) {   // convex probe: its cylinder (id n_bnd), the escape plane z = -R (n_bnd + 2)
+        const float ox = o.x, oz = o.z + radius;
+        const float a = d.x * d.x + d.z * d.z;
+        const float b = ox * d.x + oz * d.z;
+        if (a > 0.f && b < 0.f) {
+            const float disc = b * b - a * ((ox - radius) * (ox + radius) + oz * oz);
+            if (disc >= 0.f) {
+                const float t = (-b - sqrtf(disc)) / a;
+                if (t > kTmin && t < best) {
+                    best = t;
+                    hit = S.n_bnd;
+                }
+            }
+        }
+        if (d.z < 0.f) {
+            const float t = (-radius - o.z) / d.z;
+            if (t > kTmin && t < best) {
+                best = t;
+                hit = S.n_bnd + 2;
+            }
+        } else if (d.z > 0.f) {
+            const float t = (S.z_max - o.z) / d.z;
+            if (t > kTmin && t < best) {
+                best = t;
+                hit = S.n_bnd + 1;
+            }
+        }
+    } else if (terminals) {
         if (d.z < 0.f) {
             const float t = -o.z / d.z;
             if (t > kTmin && t < best) {
@@ -361,6 +389,7 @@ struct ImageP {
     const ff *tx_sin, *tx_cos, *tx_m;   // per transmit: plane wave: sin, cos, min_e x_e sin; diverging
                                         // (focused) wave: source (focus) x, z, min (max) element distance
     const int *tx_kind;                 // per transmit UR_TX_* (null: plane waves)
+    const ff *elem_xz;                  // convex array: element centres (x, z) per element (null: linear)
     float2 *iq;
     float *env, *db;
     unsigned int *env_max;  // float bits, one per image
@@ -386,6 +415,7 @@ struct CtxView {
     int n_tx;
     const float *angles;    // host copy, n_tx entries
     bool plane_waves;       // every transmit is a plane wave
+    bool linear;            // the array is linear
 };
 bool ctx_view(const ur_ctx *c, CtxView *v);
 

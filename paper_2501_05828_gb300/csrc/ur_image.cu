@@ -15,13 +15,20 @@ __device__ __forceinline__ int ff_floor_i(ff a) {
 }
 
 // One thread per pixel; threadIdx.x runs along depth so neighbouring threads
-// read neighbouring samples of the same channel.
+// read neighbouring samples of the same channel.  CONVEX: element centres (x, z)
+// from the table of a convex array, else on z = 0 at x_first + e pitch.
+template <bool CONVEX>
 __global__ void __launch_bounds__(256) k_das(const ImageP I) {
-    extern __shared__ ff s_xe[];  // element centres, float-float
+    extern __shared__ ff s_xe[];  // element centres, float-float: x [n_el] (then z [n_el] if CONVEX)
     for (int e = threadIdx.x; e < I.n_el; e += blockDim.x) {
-        const float pe = (float)e * I.pitch;
-        const ff ep = {pe, __fmaf_rn((float)e, I.pitch, -pe)};
-        s_xe[e] = ff_add(I.x_first, ep);
+        if (CONVEX) {
+            s_xe[e] = I.elem_xz[2 * e];
+            s_xe[I.n_el + e] = I.elem_xz[2 * e + 1];
+        } else {
+            const float pe = (float)e * I.pitch;
+            const ff ep = {pe, __fmaf_rn((float)e, I.pitch, -pe)};
+            s_xe[e] = ff_add(I.x_first, ep);
+        }
     }
     __syncthreads();
     const int iz = blockIdx.x * blockDim.x + threadIdx.x;
@@ -56,7 +63,13 @@ __global__ void __launch_bounds__(256) k_das(const ImageP I) {
             const float *qd = I.quad + (size_t)item * I.n_el * I.n_s;
             for (int e = 0; e < I.n_el; ++e) {
                 const ff dx = ff_add_f(ff_neg(s_xe[e]), x);
-                const ff r2 = ff_add(zz, ff_mul(dx, dx));
+                ff r2;
+                if (CONVEX) {
+                    const ff dz = ff_add_f(ff_neg(s_xe[I.n_el + e]), z);
+                    r2 = ff_add(ff_mul(dz, dz), ff_mul(dx, dx));
+                } else {
+                    r2 = ff_add(zz, ff_mul(dx, dx));
+                }
                 const ff tau = ff_add(T, ff_mul(ff_sqrt(r2), I.q));
                 if (tau.hi < 0.f || (tau.hi == 0.f && tau.lo < 0.f) || ff_gt(tau, top)) continue;
                 const int i0 = ff_floor_i(tau);
@@ -95,7 +108,10 @@ __global__ void k_log(const ImageP I) {
 
 void launch_das(const ImageP &I, cudaStream_t s) {
     dim3 grid((I.nz + 255) / 256, I.nx, I.img_items ? I.n_images : 1);
-    k_das<<<grid, 256, I.n_el * sizeof(ff), s>>>(I);
+    if (I.elem_xz)
+        k_das<true><<<grid, 256, 2 * I.n_el * sizeof(ff), s>>>(I);
+    else
+        k_das<false><<<grid, 256, I.n_el * sizeof(ff), s>>>(I);
 }
 
 void launch_log(const ImageP &I, cudaStream_t s) {

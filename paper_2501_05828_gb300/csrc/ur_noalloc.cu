@@ -82,7 +82,7 @@ extern "C" ur_status ur_beamform_noalloc(ur_ctx *ctx, const float *rf, const flo
     ur::CtxView v;
     if (!ctx) return UR_ERR_INVALID_ARG;
     if (!ur::ctx_view(ctx, &v)) return UR_ERR_STATE;
-    if (!v.plane_waves) return UR_ERR_INVALID_ARG;   // its tables hold plane waves only
+    if (!v.plane_waves || !v.linear) return UR_ERR_INVALID_ARG;   // its tables hold plane waves of a linear array
     if (!rf || !quad || !x_px || !z_px || (!iq && !env && !db)) return UR_ERR_INVALID_ARG;
     if (v.n_tx > UR_NOALLOC_MAX_TX || nx < 1 || nz < 1 || nx > UR_NOALLOC_MAX_AXIS || nz > UR_NOALLOC_MAX_AXIS)
         return UR_ERR_INVALID_ARG;

@@ -133,6 +133,61 @@ __device__ float rough_eval(float3 d, float3 n, float3 o, float a2, const Medium
     return coef * G * D * dot3(i, h) * jac / cos_i;
 }
 
+// The same toward an arbitrary element centre q (convex arrays).
+__device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, float3 q, ff &t_conn, float &att) {
+    float3 o = p;
+    float3 w = make_float3(q.x - p.x, q.y - p.y, q.z - p.z);
+    float rem = sqrtf(dot3(w, w));
+    w = make_float3(w.x / rem, w.y / rem, w.z / rem);
+    float fac = 1.f, a = 0.f;
+    ff t = {0.f, 0.f};
+    int m = med, skip = skip0;
+    for (int it = 0; it < kMaxCross; ++it) {
+        float th;
+        const int hit = nearest(S, o, w, skip, false, th);
+        const Medium &M = S.med[m];
+        if (hit < 0 || th >= rem) {
+            t = ff_add(t, ff_mul_f(rem, M.slow));
+            a += M.a * rem;
+            break;
+        }
+        t = ff_add(t, ff_mul_f(th, M.slow));
+        a += M.a * th;
+        float3 h = o + th * w;
+        const Bnd &B = S.bnd[hit];
+        if (B.kind == kPlaneZ) h.z = B.p[0];
+        const float3 n = outward(B, h);
+        const float dn = dot3(w, n);
+        const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
+        float r, ct;
+        if (!fresnel(fabsf(dn), M.c, M.Z, S.med[m2].c, S.med[m2].Z, r, ct)) return 0.f;
+        fac *= sqrtf(1.f - r * r);
+        m = m2;
+        o = h;
+        rem -= th;
+        skip = hit;
+    }
+    t_conn = t;
+    att = a;
+    return fac;
+}
+
+// Centre c and unit normal n of element e: on the arc of a convex array (radius > 0;
+// z written as -2 R sin^2(phi/2) to avoid cancellation near the apex), else (x_e, 0, 0), +z.
+__device__ __forceinline__ void elem_frame(const TraceP &P, uint32_t e, float3 &c, float3 &n) {
+    if (P.radius > 0.f) {
+        const float ph = P.phi0 + (float)e * P.dphi;
+        float sn, cs, sh, ch;
+        sincosf(ph, &sn, &cs);
+        sincosf(0.5f * ph, &sh, &ch);
+        n = make_float3(sn, 0.f, cs);
+        c = make_float3(P.radius * sn, 0.f, -2.f * P.radius * sh * sh);
+    } else {
+        c = make_float3(P.x_first + (float)e * P.pitch, 0.f, 0.f);
+        n = make_float3(0.f, 0.f, 1.f);
+    }
+}
+
 // Warp-aggregated append to the arrival queue (one atomic per converged group);
 // with DBG or REC the arrival's (ray, event) words go to arr_dbg as well.
 template <bool DBG, bool REC>
@@ -192,10 +247,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x &
 
 // Segment from the current position to the nearest boundary (clipped by the
 // path-length budget); set up the grid walk over the part inside the grid box.
+template <bool EXT>
 __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S[R.scene];
     float th;
-    R.hit = nearest(S, R.o, R.d, R.prev, true, th);
+    R.hit = nearest(S, R.o, R.d, R.prev, true, th, EXT ? P.radius : 0.f);
     R.seg = th;
     R.clipped = false;
     if (R.L + R.seg > P.max_path) {
@@ -258,22 +314,31 @@ __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Co
 }
 
 // Emission (Eq. 6) of ray i of item `item` (a transmit of one scene) from element e.
-template <bool EXT>
+template <bool DBG, bool EXT>
 __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &IT, uint32_t i,
                                           uint32_t e, Counters &cn) {
     const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
+    float3 nrm = make_float3(0.f, 0.f, 1.f);   // normal at the emission point
+    if (EXT && P.radius > 0.f) {                // a point of the element's arc face
+        const float ph = P.phi0 + ((float)e + u24(x.x) - 0.5f) * P.dphi;
+        float sn, cs, sh, ch;
+        sincosf(ph, &sn, &cs);
+        sincosf(0.5f * ph, &sh, &ch);
+        nrm = make_float3(sn, 0.f, cs);
+        R.o = make_float3(P.radius * sn, R.o.y, -2.f * P.radius * sh * sh);
+    }
     if (!EXT || IT.kind == UR_TX_PLANE) {
         R.d = make_float3(IT.sin_t, 0.f, IT.cos_t);
     } else {   // along the line from the virtual source, or toward the focus, in the xz plane
         const float sg = IT.kind == UR_TX_DIVERGING ? 1.f : -1.f;
-        const float dx = sg * (R.o.x - IT.vx), dz = sg * (0.f - IT.vz);
+        const float dx = sg * (R.o.x - IT.vx), dz = sg * (R.o.z - IT.vz);
         const float l = sqrtf(dx * dx + dz * dz);
         R.d = make_float3(dx / l, 0.f, dz / l);
     }
     R.t = P.delay[(uint32_t)IT.angle * (uint32_t)P.n_el + e];
-    R.w = R.d.z * IT.inv_n;   // Eq. 6: cosine to the element normal over N
+    R.w = (EXT ? dot3(R.d, nrm) : R.d.z) * IT.inv_n;   // Eq. 6: cosine to the face normal over N
     R.scene = IT.scene;
     R.med = P.S[IT.scene].med_array;
     R.b = 0;
@@ -284,7 +349,11 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
     R.stream = IT.stream;
     R.h = kFnvOffset;
     R.mis = false;
-    start_segment(P, R, cn);
+    if (EXT && !(R.w > 0.f)) {   // aimed into a convex probe: no ray
+        end_ray<DBG>(P, R, kEndArrayMiss, cn);
+        return;
+    }
+    start_segment<EXT>(P, R, cn);
 }
 
 // Secondary ray of a rough vertex to a uniformly drawn element centre, weighted
@@ -294,11 +363,12 @@ __device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R
                                  Counters &cn) {
     const uint4 x = philox(make_uint4(R.i, R.stream, 4u | ((uint32_t)R.b << 8), 0u), P.key);
     const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
-    const float xe = P.x_first + (float)e * P.pitch;
-    const float3 v = make_float3(xe - R.o.x, -R.o.y, -R.o.z);
+    float3 ce, ne;
+    elem_frame(P, e, ce, ne);
+    const float3 v = ce - R.o;
     const float D = sqrtf(dot3(v, v));
     const float3 o = make_float3(v.x / D, v.y / D, v.z / D);
-    const float cos_e = R.o.z / D;
+    const float cos_e = -dot3(o, ne);   // at the element, to its normal
     const float fd = directivity(P, cos_e);
     if (!(fd > 0.f)) return;
     const Medium &M = S.med[R.med], &M2 = S.med[m2];
@@ -308,7 +378,7 @@ __device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R
     cn.connections++;
     ff tc;
     float att;
-    const float fac = connection(S, R.o, dot3(o, n) > 0.f ? R.med : m2, R.hit, xe, tc, att);
+    const float fac = connection_to(S, R.o, dot3(o, n) > 0.f ? R.med : m2, R.hit, ce, tc, att);
     if (fac == 0.f) return;
     const ff ta = ff_add(R.t, tc);
     if (ff_gt(ta, P.t_last)) return;
@@ -391,20 +461,34 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         end_ray<DBG>(P, R, kEndPath, cn);
         return;
     }
-    if (R.hit == S.n_bnd) {  // array plane: only paths returning to the aperture are kept
-        R.o.z = 0.f;
-        const float xl = P.x_first - 0.5f * P.pitch;
+    if (ROUGH && R.hit == S.n_bnd + 2) {   // passed beside a convex probe
+        end_ray<DBG>(P, R, kEndArrayMiss, cn);
+        return;
+    }
+    if (R.hit == S.n_bnd) {  // array surface: only paths returning to the aperture are kept
+        int el = -1;
+        if (ROUGH && P.radius > 0.f) {   // the probe's cylinder: the element whose arc holds the hit
+            const float u = (atan2f(R.o.x, R.o.z + P.radius) - P.phi0) / P.dphi + 0.5f;
+            if (fabsf(R.o.y) <= 0.5f * P.H && u >= 0.f && u < (float)P.n_el) el = min((int)floorf(u), P.n_el - 1);
+        } else {
+            R.o.z = 0.f;
+            const float xl = P.x_first - 0.5f * P.pitch;
+            if (fabsf(R.o.y) <= 0.5f * P.H && R.o.x >= xl && R.o.x < xl + (float)P.n_el * P.pitch) {
+                el = (int)floorf((R.o.x - xl) / P.pitch);
+                if (el > P.n_el - 1) el = P.n_el - 1;
+            }
+        }
         int reason = kEndArrayMiss;
-        if (fabsf(R.o.y) <= 0.5f * P.H && R.o.x >= xl && R.o.x < xl + (float)P.n_el * P.pitch) {
-            int el = (int)floorf((R.o.x - xl) / P.pitch);
-            if (el > P.n_el - 1) el = P.n_el - 1;
-            const float fd = directivity(P, -R.d.z);
+        if (el >= 0) {
+            float3 ce = make_float3(0.f, 0.f, 0.f), ne = make_float3(0.f, 0.f, 1.f);
+            if (ROUGH) elem_frame(P, (uint32_t)el, ce, ne);
+            const float fd = directivity(P, ROUGH ? -dot3(R.d, ne) : -R.d.z);
             if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
                 float wa = R.w * fd;
                 if (ROUGH && R.mis) {   // balance heuristic against the rough vertex's secondary ray
-                    const float3 v = make_float3(P.x_first + (float)el * P.pitch - R.mp.x, -R.mp.y, -R.mp.z);
+                    const float3 v = ce - R.mp;
                     const float D2 = dot3(v, v);
-                    const float omega = P.pitch * P.H * (R.mp.z / sqrtf(D2)) / D2;
+                    const float omega = P.pitch * P.H * (-dot3(v, ne) / sqrtf(D2)) / D2;
                     if (omega > 0.f) wa *= 1.f / (1.f + 1.f / ((float)P.n_el * omega * R.mpdf));
                 }
                 emit<DBG, REC>(P, R.item * (uint32_t)P.n_el + (uint32_t)el, R.t, wa, R.i,
@@ -446,7 +530,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | rb);
         R.b += 1;
         R.prev = R.hit;
-        start_segment(P, R, cn);
+        start_segment<ROUGH>(P, R, cn);
         return;
     }
     const float cos_i = -dot3(n, R.d);
@@ -486,12 +570,12 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | branch);
     R.b += 1;
     R.prev = R.hit;
-    start_segment(P, R, cn);
+    start_segment<ROUGH>(P, R, cn);
 }
 
 // A queued scatterer event: element drawn uniformly (Philox keyed by ray,
 // transmit, segment and scatterer), receive directivity (Eq. 13), connection ray.
-template <bool DBG, bool REC>
+template <bool DBG, bool REC, bool EXT>
 __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &Q, int slot, Counters &cn) {
     const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
     const float tca = Q.tca[slot], w = Q.w[slot];
@@ -504,14 +588,23 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     const uint4 x = philox(make_uint4(ray, IT.stream, 2u | ((uint32_t)b << 8), j), P.key);
     const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     const float xe = P.x_first + (float)e * P.pitch;
-    const float vx = xe - q.x;
-    const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
-    const float fd = directivity(P, q.z / D);
+    float3 ce, ne;
+    float fd;
+    if (EXT && P.radius > 0.f) {   // convex array: directivity to the element's normal
+        elem_frame(P, e, ce, ne);
+        const float3 v = make_float3(q.x - ce.x, q.y - ce.y, q.z - ce.z);
+        fd = directivity(P, dot3(v, ne) / sqrtf(dot3(v, v)));
+    } else {
+        const float vx = xe - q.x;
+        const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
+        fd = directivity(P, q.z / D);
+    }
     if (!(fd > 0.f)) return;
     cn.connections++;
     ff tc;
     float att;
-    const float fac = connection(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
+    const float fac = (EXT && P.radius > 0.f) ? connection_to(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att)
+                                              : connection(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
     if (fac == 0.f) return;
     const Medium &M = S.med[med];
     const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
@@ -593,7 +686,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 const uint32_t m = (uint32_t)(local % IT.rays_per_el);
                 const uint64_t e = local / IT.rays_per_el;
                 const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<ROUGH>(P, R, item, IT, i, (uint32_t)e, cn);
+                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH>(P, R, item, IT, i, (uint32_t)e, cn);
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
@@ -656,7 +749,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 qn += __popc(m);
                 if (qn >= 32) {
                     __syncwarp();
-                    process_event<DBG, REC>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+                    process_event<DBG, REC, ROUGH>(P, Q, (qhead + lane) & (kQueue - 1), cn);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
@@ -683,7 +776,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
     }
     // (3) drain the queue
     __syncwarp();
-    if (lane < qn) process_event<DBG, REC>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+    if (lane < qn) process_event<DBG, REC, ROUGH>(P, Q, (qhead + lane) & (kQueue - 1), cn);
 
     if (P.stats) {
         const uint32_t v[6] = {cn.rays, cn.segments, cn.interactions, cn.candidates, cn.connections, cn.arrivals};
@@ -712,7 +805,7 @@ int trace_occupancy(int block, bool debug) {
 // extended variant never records or freezes sampling media (the adjoint and
 // ur_scene_set_media refuse such scenes and transmits).
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves) {
-    bool split = false, rough = point_waves;
+    bool split = false, rough = point_waves || P.radius > 0.f;   // convex arrays take the extended tracer too
     for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) {
         split = split || P.S[q].split_sampling != 0;
         for (int b = 0; b < P.S[q].n_bnd; ++b) rough = rough || P.S[q].bnd[b].alpha > 0.f;
