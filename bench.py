@@ -359,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
             "phase_ms": phase_ms,
             "roofline": {"bound": "alu",
                          "kernel": "k_trace" + (" (extended instantiation: rough boundaries, diverging and focused "
-                                                "waves)" if args.workload != "layered" else ""),
+                                                "waves, convex arrays)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
@@ -392,15 +392,16 @@ PAPER_WORKLOAD = ("paper settings (Sec. 4) on a synthetic vertebra stand-in: 128
                   "90 dB")
 DIVERGING_WORKLOAD = ("layered phantom imaged with 9 diverging waves: virtual sources 10 mm behind the array at "
                       "x = -12..12 mm, 1.11M rays each (1e7 rays per acquisition), compounded DAS to 512x256, 60 dB")
+CONVEX_WORKLOAD = PAPER_WORKLOAD.replace("128 el,", "128 el on a 70-deg convex arc (R 50 mm, the paper's probe),", 1)
 FRAME_WORKLOADS = {"layered": WORKLOAD, "rough": ROUGH_WORKLOAD, "paper": PAPER_WORKLOAD,
-                   "diverging": DIVERGING_WORKLOAD}
+                   "diverging": DIVERGING_WORKLOAD, "convex": CONVEX_WORKLOAD}
 
 
 def frame_workload(args):
     """The phantom of a frame workload: layered (default), rough or paper."""
     import phantoms
-    if args.workload == "paper":
-        return phantoms.paper_like()
+    if args.workload in ("paper", "convex"):
+        return phantoms.paper_like(convex=args.workload == "convex")
     w = phantoms.layered()
     if args.workload == "diverging":
         import numpy as np
@@ -541,7 +542,7 @@ def run_batched(args, rank, world, local_rank):
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
             "roofline": {"bound": "alu",
                          "kernel": "k_trace" + (" (extended instantiation: rough boundaries, diverging and focused "
-                                                "waves)" if args.workload != "layered" else ""),
+                                                "waves, convex arrays)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
             "gpu_launches": 7 * args.steps, "clocks": clk,
@@ -861,7 +862,7 @@ def main():
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
     ap.add_argument("--workload", default="layered",
-                    choices=("layered", "rough", "paper", "diverging", "batched", "adjoint", "denoiser"))
+                    choices=("layered", "rough", "paper", "convex", "diverging", "batched", "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -869,8 +870,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     args.warmup = max(3, args.warmup)
     if args.steps <= 0:
-        args.steps = {"layered": 150, "rough": 60, "paper": 30, "diverging": 60, "batched": 5, "adjoint": 30,
-                      "denoiser": 30}[args.workload]
+        args.steps = {"layered": 150, "rough": 60, "paper": 30, "convex": 30, "diverging": 60, "batched": 5,
+                      "adjoint": 30, "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "batched":

@@ -174,8 +174,9 @@ __device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, fl
 
 // Centre c and unit normal n of element e: on the arc of a convex array (radius > 0;
 // z written as -2 R sin^2(phi/2) to avoid cancellation near the apex), else (x_e, 0, 0), +z.
+template <bool CVX>
 __device__ __forceinline__ void elem_frame(const TraceP &P, uint32_t e, float3 &c, float3 &n) {
-    if (P.radius > 0.f) {
+    if (CVX) {
         const float ph = P.phi0 + (float)e * P.dphi;
         float sn, cs, sh, ch;
         sincosf(ph, &sn, &cs);
@@ -247,11 +248,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x &
 
 // Segment from the current position to the nearest boundary (clipped by the
 // path-length budget); set up the grid walk over the part inside the grid box.
-template <bool EXT>
+template <bool CVX>
 __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S[R.scene];
     float th;
-    R.hit = nearest(S, R.o, R.d, R.prev, true, th, EXT ? P.radius : 0.f);
+    R.hit = nearest(S, R.o, R.d, R.prev, true, th, CVX ? P.radius : 0.f);
     R.seg = th;
     R.clipped = false;
     if (R.L + R.seg > P.max_path) {
@@ -314,14 +315,14 @@ __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Co
 }
 
 // Emission (Eq. 6) of ray i of item `item` (a transmit of one scene) from element e.
-template <bool DBG, bool EXT>
+template <bool DBG, bool EXT, bool CVX>
 __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &IT, uint32_t i,
                                           uint32_t e, Counters &cn) {
     const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
     float3 nrm = make_float3(0.f, 0.f, 1.f);   // normal at the emission point
-    if (EXT && P.radius > 0.f) {                // a point of the element's arc face
+    if (CVX) {                                  // a point of the element's arc face
         const float ph = P.phi0 + ((float)e + u24(x.x) - 0.5f) * P.dphi;
         float sn, cs, sh, ch;
         sincosf(ph, &sn, &cs);
@@ -353,18 +354,18 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
         end_ray<DBG>(P, R, kEndArrayMiss, cn);
         return;
     }
-    start_segment<EXT>(P, R, cn);
+    start_segment<CVX>(P, R, cn);
 }
 
 // Secondary ray of a rough vertex to a uniformly drawn element centre, weighted
 // against BSDF sampling of the same direction by the balance heuristic.
-template <bool DBG, bool REC>
+template <bool DBG, bool REC, bool CVX>
 __device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R, float3 n, int m2, float a2,
                                  Counters &cn) {
     const uint4 x = philox(make_uint4(R.i, R.stream, 4u | ((uint32_t)R.b << 8), 0u), P.key);
     const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     float3 ce, ne;
-    elem_frame(P, e, ce, ne);
+    elem_frame<CVX>(P, e, ce, ne);
     const float3 v = ce - R.o;
     const float D = sqrtf(dot3(v, v));
     const float3 o = make_float3(v.x / D, v.y / D, v.z / D);
@@ -449,7 +450,7 @@ __device__ bool rough_scatter(const TraceP &P, const SceneP &S, Lane &R, float3 
 // End of a segment: time of flight and attenuation along it, then the array
 // plane (aperture return), the absorbing bottom, the time window, the bounce
 // budget, or a boundary interaction (Eqs. 7-11) and the next segment.
-template <bool DBG, bool SPLIT, bool REC, bool ROUGH>
+template <bool DBG, bool SPLIT, bool REC, bool ROUGH, bool CVX>
 __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const SceneP &S = P.S[R.scene];
     const Medium &M = S.med[R.med];
@@ -461,13 +462,13 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         end_ray<DBG>(P, R, kEndPath, cn);
         return;
     }
-    if (ROUGH && R.hit == S.n_bnd + 2) {   // passed beside a convex probe
+    if (CVX && R.hit == S.n_bnd + 2) {   // passed beside a convex probe
         end_ray<DBG>(P, R, kEndArrayMiss, cn);
         return;
     }
     if (R.hit == S.n_bnd) {  // array surface: only paths returning to the aperture are kept
         int el = -1;
-        if (ROUGH && P.radius > 0.f) {   // the probe's cylinder: the element whose arc holds the hit
+        if (CVX) {   // the probe's cylinder: the element whose arc holds the hit
             const float u = (atan2f(R.o.x, R.o.z + P.radius) - P.phi0) / P.dphi + 0.5f;
             if (fabsf(R.o.y) <= 0.5f * P.H && u >= 0.f && u < (float)P.n_el) el = min((int)floorf(u), P.n_el - 1);
         } else {
@@ -481,7 +482,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         int reason = kEndArrayMiss;
         if (el >= 0) {
             float3 ce = make_float3(0.f, 0.f, 0.f), ne = make_float3(0.f, 0.f, 1.f);
-            if (ROUGH) elem_frame(P, (uint32_t)el, ce, ne);
+            if (ROUGH) elem_frame<CVX>(P, (uint32_t)el, ce, ne);
             const float fd = directivity(P, ROUGH ? -dot3(R.d, ne) : -R.d.z);
             if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
                 float wa = R.w * fd;
@@ -520,7 +521,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const float3 n = dn > 0.f ? make_float3(-n_out.x, -n_out.y, -n_out.z) : n_out;
     if (ROUGH && B.alpha > 0.f) {   // rough boundary: secondary ray first, then the BSDF sample
         const float a2 = B.alpha * B.alpha;
-        rough_connection<DBG, REC>(P, S, R, n, m2, a2, cn);
+        rough_connection<DBG, REC, CVX>(P, S, R, n, m2, a2, cn);
         cn.interactions++;
         uint32_t rb = 0;
         if (!rough_scatter(P, S, R, n, m2, a2, rb)) {
@@ -530,7 +531,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | rb);
         R.b += 1;
         R.prev = R.hit;
-        start_segment<ROUGH>(P, R, cn);
+        start_segment<CVX>(P, R, cn);
         return;
     }
     const float cos_i = -dot3(n, R.d);
@@ -570,12 +571,12 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | branch);
     R.b += 1;
     R.prev = R.hit;
-    start_segment<ROUGH>(P, R, cn);
+    start_segment<CVX>(P, R, cn);
 }
 
 // A queued scatterer event: element drawn uniformly (Philox keyed by ray,
 // transmit, segment and scatterer), receive directivity (Eq. 13), connection ray.
-template <bool DBG, bool REC, bool EXT>
+template <bool DBG, bool REC, bool EXT, bool CVX>
 __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &Q, int slot, Counters &cn) {
     const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
     const float tca = Q.tca[slot], w = Q.w[slot];
@@ -590,8 +591,8 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     const float xe = P.x_first + (float)e * P.pitch;
     float3 ce, ne;
     float fd;
-    if (EXT && P.radius > 0.f) {   // convex array: directivity to the element's normal
-        elem_frame(P, e, ce, ne);
+    if (CVX) {   // convex array: directivity to the element's normal
+        elem_frame<CVX>(P, e, ce, ne);
         const float3 v = make_float3(q.x - ce.x, q.y - ce.y, q.z - ce.z);
         fd = directivity(P, dot3(v, ne) / sqrtf(dot3(v, v)));
     } else {
@@ -603,7 +604,7 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     cn.connections++;
     ff tc;
     float att;
-    const float fac = (EXT && P.radius > 0.f) ? connection_to(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att)
+    const float fac = CVX ? connection_to(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att)
                                               : connection(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
     if (fac == 0.f) return;
     const Medium &M = S.med[med];
@@ -631,7 +632,7 @@ __device__ __forceinline__ uint32_t item_of(const TraceP &P, uint64_t slot) {
 // a time with all lanes busy.  Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
-template <bool DBG, bool SPLIT, bool REC, bool ROUGH>
+template <bool DBG, bool SPLIT, bool REC, bool ROUGH, bool CVX>
 __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
         const unsigned waiting = __ballot_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay);
         const bool resolve = __popc(waiting) >= P.resolve_batch || __ballot_sync(0xffffffffu, R.state == kInSeg) == 0u;
         for (int guard = 0; resolve && guard < 256; ++guard) {
-            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC, ROUGH>(P, R, cn);
+            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC, ROUGH, CVX>(P, R, cn);
             unsigned need = __ballot_sync(0xffffffffu, R.state == kNeedRay);
             uint64_t my_slot = ~0ull;
             while (need) {
@@ -686,7 +687,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 const uint32_t m = (uint32_t)(local % IT.rays_per_el);
                 const uint64_t e = local / IT.rays_per_el;
                 const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH>(P, R, item, IT, i, (uint32_t)e, cn);
+                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH, CVX>(P, R, item, IT, i, (uint32_t)e, cn);
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
@@ -749,7 +750,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 qn += __popc(m);
                 if (qn >= 32) {
                     __syncwarp();
-                    process_event<DBG, REC, ROUGH>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+                    process_event<DBG, REC, ROUGH, CVX>(P, Q, (qhead + lane) & (kQueue - 1), cn);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
@@ -776,7 +777,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
     }
     // (3) drain the queue
     __syncwarp();
-    if (lane < qn) process_event<DBG, REC, ROUGH>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+    if (lane < qn) process_event<DBG, REC, ROUGH, CVX>(P, Q, (qhead + lane) & (kQueue - 1), cn);
 
     if (P.stats) {
         const uint32_t v[6] = {cn.rays, cn.segments, cn.interactions, cn.candidates, cn.connections, cn.arrivals};
@@ -793,9 +794,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
 int trace_occupancy(int block, bool debug) {
     int n = 0;
     if (debug)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false, false, false>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, false, false>, block, 0);
     return n > 0 ? n : 1;
 }
 
@@ -810,20 +811,25 @@ void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t
         split = split || P.S[q].split_sampling != 0;
         for (int b = 0; b < P.S[q].n_bnd; ++b) rough = rough || P.S[q].bnd[b].alpha > 0.f;
     }
+    if (rough && P.radius > 0.f) {   // convex arrays: their own extended instantiation
+        debug ? k_trace<true, false, false, true, true><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false, true, true><<<grid, block, 0, s>>>(P);
+        return;
+    }
     if (rough) {
-        debug ? k_trace<true, false, false, true><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, false, true><<<grid, block, 0, s>>>(P);
+        debug ? k_trace<true, false, false, true, false><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false, true, false><<<grid, block, 0, s>>>(P);
         return;
     }
     if (debug) {
-        split ? k_trace<true, true, false, false><<<grid, block, 0, s>>>(P)
-              : k_trace<true, false, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<true, true, false, false, false><<<grid, block, 0, s>>>(P)
+              : k_trace<true, false, false, false, false><<<grid, block, 0, s>>>(P);
     } else if (P.record) {
-        split ? k_trace<false, true, true, false><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, true, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, true, false, false><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, true, false, false><<<grid, block, 0, s>>>(P);
     } else {
-        split ? k_trace<false, true, false, false><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, false, false, false><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false, false, false><<<grid, block, 0, s>>>(P);
     }
 }
 

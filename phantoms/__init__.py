@@ -117,7 +117,7 @@ def batched_variant(scene_seed):
     return w
 
 
-def paper_like(seed=0, n_scat=20_000, n_rays=512_000):
+def paper_like(seed=0, n_scat=20_000, n_rays=512_000, convex=False):
     """The acquisition of the paper's experiments (Sec. 4) on a synthetic bone-surface stand-in
     (the CT spine mesh is not available): 128 elements, 5 MHz, fs 50 MHz, 5 cycles, 4 mm
     elevation, directivity 2 degrees, 25 plane waves over [-30, 30] degrees, 10 bounces, 20 cm
@@ -125,7 +125,8 @@ def paper_like(seed=0, n_scat=20_000, n_rays=512_000):
     0.5): a vertebral body (sphere r = 10 mm at 45 mm depth) and two processes (cylinders along
     elevation, r = 3 mm, at x = +-12 mm, 28 mm depth); n_scat scatterers uniform inside the bone,
     none in the water.  n_rays per transmit (25 x 512k = 12.8M rays per acquisition, the paper's
-    128 elements x 100k rays)."""
+    128 elements x 100k rays).  convex: the paper's probe geometry, 128 elements over a 70-degree
+    arc of radius 50 mm (arc pitch 0.477 mm), instead of a linear array with 0.3 mm pitch."""
     rng = np.random.default_rng(seed)
     water = (1540.0, 1.54, 0.0, 0.0)
     bone = (3500.0, 7.8, 10.0, 0.5)
@@ -142,7 +143,13 @@ def paper_like(seed=0, n_scat=20_000, n_rays=512_000):
         pts.append(q[inside])
     xyz = np.concatenate(pts)[:n_scat]
     sc = np.column_stack([xyz, rng.standard_normal(n_scat)]).astype(np.float32)
-    arr = array_params(128, 4096, fs=50e6, c_bf=1540.0, alpha_m_deg=2.0, alpha_c_deg=2.0)
+    if convex:
+        radius = 0.05
+        arr = array_params(128, 4096, pitch=np.deg2rad(70.0) * radius / 128, fs=50e6, c_bf=1540.0,
+                           alpha_m_deg=2.0, alpha_c_deg=2.0)
+        arr["radius"] = float(np.float32(radius))
+    else:
+        arr = array_params(128, 4096, fs=50e6, c_bf=1540.0, alpha_m_deg=2.0, alpha_c_deg=2.0)
     x, z = image_grid(arr, 512, 256, z0=1e-3, z1=60e-3)
     ang = np.deg2rad(np.linspace(-30.0, 30.0, 25)).astype(np.float32)
     return {"name": "paper_like", "scene": _scene([water, bone], bnd, 0, 0.080, sc, 1e-4), "array": arr,

@@ -118,3 +118,17 @@ def test_convex_refused_where_unsupported(ur):
         with pytest.raises(ur.URError):
             sim.set_array(a)
     sim.close()
+
+
+def test_paper_settings_on_the_convex_probe(ur):
+    """The paper's acquisition with its probe geometry (128 elements over 70 degrees, R = 50 mm):
+    all 25 plane waves against the oracle; time bar of the paper-settings test (rough curved bone,
+    50 MHz), amplitude floor of the rough tests (the 2-degree directivity here is a step)."""
+    from test_gpu_rough import ROUGH_AMP_FLOOR
+    w = phantoms.paper_like(n_rays=4000, convex=True)
+    G = run_gpu(ur, w, capacity=4 * 25 * w["n_rays"])
+    assert G["stats"]["rays"] == 25 * w["n_rays"]
+    arr, topo, _ = run_oracle(w)
+    check_trace_parity(w, G, arr, topo, "paper settings, convex", amp_floor=ROUGH_AMP_FLOOR, dt_max=1e-2,
+                       dt_q99=1e-3)
+    assert len(arr) > 100
