@@ -349,12 +349,12 @@ ur_status ur_graph_launch(ur_ctx *ctx);
 
 /* Scatterer-grid and launch tuning (0 fields keep the defaults).  Cell sizes in
  * metres along x (cell_xy), y (cell_y) and z (cell_z), applied at the next
- * ur_scene_upload.  Defaults: 8 r_s, 0.5 r_s and 60 r_s when every boundary is
+ * ur_scene_upload.  Defaults: 8 r_s, 0.3 r_s and 60 r_s when every boundary is
  * a plane z = c or a cylinder along y (plane waves of a linear array then never
  * gain a y component, so thin y cells add few cell steps and hold fewer
  * scatterers); 3 r_s, 3 r_s and 40 r_s when the scene holds a sphere.  block (multiple of 32, <= 256), blocks_per_sm and
  * resolve_batch (1..32: the tracer finishes segments and starts rays once this
- * many lanes of a warp wait) apply at the next trace. */
+ * many lanes of a warp wait; default 20) apply at the next trace. */
 typedef struct {
     float cell_xy, cell_z;
     int32_t block, blocks_per_sm, resolve_batch;

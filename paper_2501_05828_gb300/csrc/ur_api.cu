@@ -59,7 +59,8 @@ constexpr uint32_t kChunkMin = 512;    // fewest (work items are sized for sever
 // and cylinders along y keep them there (their normals have no y component), so
 // in such scenes thin y cells hold few scatterers at almost no extra cell
 // steps; a sphere tilts rays out of the plane, and cubic-ish cells serve better.
-constexpr float kCellSlab[3] = {8.f, 0.5f, 60.f};
+constexpr float kCellSlab[3] = {8.f, 0.3f, 60.f};
+constexpr int kResolveBatch = 20;   // default: lanes that must wait before a tracer warp resolves segments
 constexpr float kCellIso[3] = {3.f, 3.f, 40.f};
 
 struct SceneData {
@@ -549,7 +550,7 @@ ur::TraceP make_trace_params(ur_ctx *c, uint64_t seed, int max_b, float max_path
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.max_b = max_b;
     P.max_path = max_path;
-    P.resolve_batch = c->tune.resolve_batch > 0 ? c->tune.resolve_batch : 16;
+    P.resolve_batch = c->tune.resolve_batch > 0 ? c->tune.resolve_batch : kResolveBatch;
     c->grow(c->counters, 8 * sizeof(unsigned long long));
     unsigned long long *cnt = (unsigned long long *)c->counters.p;
     P.arr_count = cnt;
@@ -1401,7 +1402,7 @@ ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int 
         if (cur.cell_xy <= 0.f) cur.cell_xy = default_cell(sd, 0);
         if (cur.cell_y <= 0.f) cur.cell_y = default_cell(sd, 1);
         if (cur.cell_z <= 0.f) cur.cell_z = default_cell(sd, 2);
-        if (cur.resolve_batch <= 0) cur.resolve_batch = 16;
+        if (cur.resolve_batch <= 0) cur.resolve_batch = kResolveBatch;
         if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = ur::trace_occupancy(256, false);
         float t_cur = measure(cur);
         // coordinate descent over the knobs
