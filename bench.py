@@ -49,7 +49,7 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), per primary ray, valid only while the tracer sources
 # hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "a201500c7571b88c", "bytes_per_ray": 13.77, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+TRACE_TRAFFIC = {"src_sha": "a201500c7571b88c", "bytes_per_ray": 13.77, "warp_inst_per_ray": 1039.5, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
 
 
 def tracer_sha():
@@ -77,6 +77,16 @@ def algorithmic_flops(stats, arr):
 def trace_flops(stats):
     return (stats["segments"] * FLOPS_PER_SEGMENT + stats["candidates"] * FLOPS_PER_CANDIDATE
             + stats["connections"] * FLOPS_PER_CONNECTION)
+
+
+def issue_slots(rays, t_launch, n_sm, sm_mhz):
+    """What bounds the tracer: warp instructions it issues (captured per ray with ncu, same source
+    hash as the traffic) against 4 schedulers x 1 instruction per clock per SM.  Implementation
+    work, not the method's arithmetic: reported beside the algorithmic ALU roofline."""
+    got = TRACE_TRAFFIC["warp_inst_per_ray"] * rays / t_launch
+    peak = n_sm * 4 * sm_mhz * 1e6
+    return {"achieved_warp_inst_per_s": got, "peak_warp_inst_per_s": peak, "frac": got / peak,
+            "peak_note": "%d SMs x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % (n_sm, sm_mhz)}
 
 
 def binning_roofline(st, arr, phase_ms, alu_peak, peaks, n_sm, sm_mhz):
@@ -365,7 +375,9 @@ def run_ours(args, rank, world, local_rank):
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
                              props.multi_processor_count, FP32_LANES_PER_SM, sm_mhz),
                          "trace_ms_per_launch": t_launch * 1e3,
-                         "algorithmic_flops_per_launch": trace_flops(st)},
+                         "algorithmic_flops_per_launch": trace_flops(st),
+                         "issue_slots": issue_slots(N * n_tx, t_launch, props.multi_processor_count, sm_mhz)
+                         if traffic is not None else None},
             "roofline_binning": binning_roofline(st, A, phase_ms, peak, peaks, props.multi_processor_count, sm_mhz),
             "stats_per_frame": st,
             "gpu_launches": launches,
