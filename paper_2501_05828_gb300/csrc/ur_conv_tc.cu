@@ -758,10 +758,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = false;
                     break;
                 }
+                // K steps run down the image rows fastest: the rows a step loads for ky = 0, 1, 2 are
+                // loaded again by the next two steps (ky shifted by one), while still in L2
                 int q = s_begin + kt;
-                const int xb = q % a.nxb;
-                q /= a.nxb;
-                const int y = q % a.H, n = q / a.H, x0 = xb * kWK;
+                const int y = q % a.H;
+                q /= a.H;
+                const int xb = q % a.nxb, n = q / a.nxb, x0 = xb * kWK;
                 mbar_expect_tx(full0 + 8 * st, bytes);
                 for (int g = 0; g < n_groups; ++g) {
                     const int r = r0 + 32 * g, tap = r / a.Cin, ci0 = r - tap * a.Cin;
