@@ -166,3 +166,32 @@ def test_autotune_keeps_parity(env):
     arr, _, _ = oracle.trace(w["scene"], w["array"], w["angles"], w["n_rays"], 0, w["max_bounces"])
     orf, oq = oracle.deposit(w["array"], 1, arr)
     assert rel_l2(rf.double().cpu().numpy(), orf) <= 1e-3        # raw, all paths
+
+
+def test_batch_with_rough_scene_and_point_source_transmits(env):
+    """A batch whose scenes include a rough one and whose transmits include diverging and focused
+    waves runs on the extended tracer; each item equals the single-scene trace."""
+    torch, ur, a, b, items = env
+    rough = dict(a)
+    s = dict(a["scene"])
+    med = [list(m) for m in s["media"]]
+    med[2][3] = 0.5                                   # rough bone sphere
+    s["media"] = [tuple(m) for m in med]
+    rough["scene"] = s
+    tx = [(ur.TX_DIVERGING, -2e-3, -10e-3), (ur.TX_PLANE, float(ANGLES[1]), 0.0), (ur.TX_FOCUSED, 1e-3, 20e-3),
+          (ur.TX_PLANE, float(ANGLES[3]), 0.0)]
+    for w in (rough, b):
+        w["transmits"] = tx
+    sim = ur.Simulator(0)
+    sim.load(rough, slot=0)
+    sim.load(b, slot=1)
+    its = [(0, 0, 20_000), (1, 2, 15_000), (0, 2, 9_000), (1, 0, 12_000)]
+    sim.batch_plan(its, a["x_px"], a["z_px"])
+    rf, q = sim.batch_trace(0, 4)
+    n, st = sim.batch_status()
+    assert st["rays"] == sum(it[2] for it in its)
+    for k, (scene, t, nr) in enumerate(its):
+        srf, sq = single(ur, rough if scene == 0 else b, nr, t)
+        assert rel_l2(rf[k].double().cpu().numpy(), srf) <= 1e-6, (k, scene, t)
+        assert rel_l2(q[k].double().cpu().numpy(), sq) <= 1e-6
+    sim.close()
