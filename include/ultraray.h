@@ -176,19 +176,36 @@ ur_status ur_set_plane_waves(ur_ctx *ctx, const float *angles_rad, int n_tx);
  *                    (|c_e - v| - min_e' |c_e' - v|) / c_bf and its rays leave along the line
  *                    from v through the emission point;
  *   UR_TX_FOCUSED:   focus (x, 0, z) in front of the array (z > 0): element e fires at
- *                    (max_e' |c_e' - f| - |c_e - f|) / c_bf and its rays head for f.
+ *                    (max_e' |c_e' - f| - |c_e - f|) / c_bf and its rays head for f;
+ *   UR_TX_SYNTHETIC: synthetic aperture (Sec. 1): element x (an integer value in [0, n_el))
+ *                    alone fires, at t = 0; every ray of the transmit leaves a uniform point
+ *                    of its face at an angle to its normal drawn uniformly in (-pi/2, pi/2)
+ *                    from the ray's emission counter (third word).
  * Directions lie in the xz plane (the delays act laterally); the emission weight is the
  * cosine to the element normal over the rays of the transmit (Eq. 6).  ur_beamform uses
- * the matching transmit delays.  Host or device array of n_tx entries, 1 <= n_tx <= 65536.
- * The adjoint and ur_beamform_noalloc take plane waves (and linear arrays) only.
+ * the matching transmit delays (synthetic aperture: distance from the firing element's
+ * centre).  Host or device array of n_tx entries, 1 <= n_tx <= 65536.  The adjoint,
+ * ur_beamform_noalloc and frozen sampling media take plane waves (and linear arrays) only.
  * Errors: UR_ERR_INVALID_ARG, UR_ERR_STATE (array not set). */
-enum { UR_TX_PLANE = 0, UR_TX_DIVERGING = 1, UR_TX_FOCUSED = 2 };
+enum { UR_TX_PLANE = 0, UR_TX_DIVERGING = 1, UR_TX_FOCUSED = 2, UR_TX_SYNTHETIC = 3 };
 typedef struct {
     int32_t kind;
     float angle;     /* UR_TX_PLANE */
-    float x, z;      /* UR_TX_DIVERGING: virtual source; UR_TX_FOCUSED: focus (m) */
+    float x, z;      /* UR_TX_DIVERGING: virtual source; UR_TX_FOCUSED: focus (m);
+                        UR_TX_SYNTHETIC: x = index of the firing element */
 } ur_transmit;
 ur_status ur_set_transmits(ur_ctx *ctx, const ur_transmit *tx, int n_tx);
+
+/* Per-ray transmit mixing (Sec. 2.3: rays of different acquisition events leave
+ * together, each with a randomly selected transmit).  With enabled = 1, ur_trace and
+ * ur_trace_debug trace one sequence of n_tx * n_rays_per_tx rays (below 2^32); ray i
+ * draws its transmit k = ((x0 >> 8) * n_tx) >> 24 from x = Philox(counter (i, 0, 0, 1))
+ * and is from then on ray i of transmit k (emission counter (i, k, 0, 0), weight over
+ * n_rays_per_tx, the expected rays per transmit).  Path hashes are indexed by i alone.
+ * enabled = 0 (the default) traces n_rays_per_tx rays of each transmit.  Batches are not
+ * affected; the adjoint and frozen sampling media refuse mixing.
+ * Errors: UR_ERR_INVALID_ARG (enabled not 0 or 1). */
+ur_status ur_set_transmit_mixing(ur_ctx *ctx, int enabled);
 
 /* Trace n_rays_per_tx primary rays for every transmit (Eqs. 4-11, 13) and
  * deposit the pulse-shaped arrivals (Eq. 14) into the analytic channel data

@@ -27,7 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 PLANE_Z, SPHERE, CYL_Y = 0, 1, 2
-TX_PLANE, TX_DIVERGING, TX_FOCUSED = 0, 1, 2
+TX_PLANE, TX_DIVERGING, TX_FOCUSED, TX_SYNTHETIC = 0, 1, 2, 3
 MODE_MC, MODE_EXPECT = 0, 1
 END_APERTURE, END_ARRAY_MISS, END_BOTTOM, END_PATH, END_TIME, END_MAXB, END_ROUGH = 1, 2, 3, 4, 5, 6, 7
 
@@ -68,7 +68,8 @@ class TraceCfg(C.Structure):
                 ("n_rays", C.c_uint64), ("ray_begin", C.c_uint64), ("ray_end", C.c_uint64),
                 ("seed", C.c_uint64), ("max_bounces", C.c_int32), ("max_path", C.c_float),
                 ("mode", C.c_int32), ("rough_bsdf_only", C.c_int32),
-                ("tx_kind", C.POINTER(C.c_int32)), ("tx_x", C.POINTER(C.c_float)), ("tx_z", C.POINTER(C.c_float))]
+                ("tx_kind", C.POINTER(C.c_int32)), ("tx_x", C.POINTER(C.c_float)), ("tx_z", C.POINTER(C.c_float)),
+                ("mix", C.c_int32)]
 
 
 class Arrival(C.Structure):
@@ -187,7 +188,8 @@ def philox4x32_10(ctr, key):
 
 
 def _transmit_arrays(transmits, n_tx):
-    """transmits: None (plane waves of `angles`) or a sequence of (kind, x, z) per transmit."""
+    """transmits: None (plane waves of `angles`) or a sequence of (kind, x, z) per transmit
+    (TX_SYNTHETIC: x = the firing element's index)."""
     if transmits is None:
         return None
     t = list(transmits)
@@ -199,22 +201,25 @@ def _transmit_arrays(transmits, n_tx):
 
 
 def trace(scene, array, angles, n_rays, seed, max_bounces, max_path=0.2, ray_begin=0, ray_end=None,
-          mode=MODE_MC, topo=False, threads=None, rough_bsdf_only=False, transmits=None):
-    """Trace rays [ray_begin, ray_end) of every transmit.
+          mode=MODE_MC, topo=False, threads=None, rough_bsdf_only=False, transmits=None, mix=False):
+    """Trace rays [ray_begin, ray_end) of every transmit; with mix, rays [ray_begin, ray_end) of
+    one sequence of n_tx * n_rays rays that draw their transmits.
 
-    Returns (arrivals structured array, topology hashes [n_tx, n_sub] or None, stats dict)."""
+    Returns (arrivals structured array, topology hashes [n_tx, n_sub] ([n_sub] with mix) or None,
+    stats dict)."""
     L = lib()
+    ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
     if ray_end is None:
-        ray_end = n_rays
+        ray_end = n_rays * (ang.size if mix else 1)
     s, keep_s = make_scene(scene)
     a = make_array(array)
-    ang = np.ascontiguousarray(angles, dtype=np.float32).reshape(-1)
     txa = _transmit_arrays(transmits, ang.size)
     cfg = TraceCfg(ang.size, _fp(ang), int(n_rays), int(ray_begin), int(ray_end), int(seed),
                    int(max_bounces), float(max_path), int(mode), int(bool(rough_bsdf_only)),
-                   _ip(txa[0]) if txa else None, _fp(txa[1]) if txa else None, _fp(txa[2]) if txa else None)
+                   _ip(txa[0]) if txa else None, _fp(txa[1]) if txa else None, _fp(txa[2]) if txa else None,
+                   int(bool(mix)))
     n_sub = int(ray_end) - int(ray_begin)
-    topo_arr = np.zeros((ang.size, n_sub), np.uint64) if topo else None
+    topo_arr = (np.zeros(n_sub, np.uint64) if mix else np.zeros((ang.size, n_sub), np.uint64)) if topo else None
     threads = threads or (os.cpu_count() or 1)
     cap = max(1024, n_sub * ang.size // 2)
     while True:

@@ -20,6 +20,17 @@
  *    the virtual source, or toward the focus, projected on the xz plane (the
  *    delays act laterally only, so directions keep y = 0 as for plane waves);
  *    the Eq. 6 weight is the cosine to the element normal over N.
+ *  - Synthetic aperture (named among the acquisition schemes of Sec. 1 without
+ *    formulas): one element fires at t = 0 and every element receives.  All N
+ *    rays of the transmit leave uniform points of that element's face, at an
+ *    angle to its normal drawn uniformly in (-pi/2, pi/2) in the xz plane (the
+ *    angle the plane-wave scheme fixes is drawn here, Sec. 2.3); the Eq. 6 weight
+ *    is the cosine of that angle over N.
+ *  - Transmit mixing (Sec. 2.3: rays of different acquisition events leave
+ *    together, each with a randomly selected angle): in this mode n_tx * N rays
+ *    are traced and ray i draws its transmit k uniformly from its own counter;
+ *    from there it is ray i of transmit k, with the Eq. 6 weight over N, the
+ *    expected number of rays per transmit.
  *  - Convex array (Sec. 2.3 describes the transducer by its elements, elevation,
  *    radius and opening angle): element centres lie `pitch` apart on the arc of
  *    radius R about (0, 0, -R), apex at the origin, normals radial; the probe is
@@ -758,7 +769,8 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
 static uint64_t trace_ray(const ctx_t *C, ray_job *J)
 {
     const or_array *ar = C->ar;
-    int e = (int)(J->i % (uint32_t)ar->n_el);
+    const int sa = C->kind[J->k] == OR_TX_SYNTHETIC;
+    int e = sa ? (int)C->vx[J->k] : (int)(J->i % (uint32_t)ar->n_el);
     uint32_t x[4];
     draw(C->cfg->seed, J->i, (uint32_t)J->k, 0u, 0u, x);
     double o[3] = {elem_x(C, e) + (u24(x[0]) - 0.5) * C->pitch, (u24(x[1]) - 0.5) * C->H, 0.0};
@@ -769,7 +781,11 @@ static uint64_t trace_ray(const ctx_t *C, ray_job *J)
         o[0] = C->R * nrm[0]; o[2] = C->R * (nrm[2] - 1.0);
     }
     double d[3] = {C->sin_t[J->k], 0.0, C->cos_t[J->k]};
-    if (C->kind[J->k] != OR_TX_PLANE) {   /* along the line from the virtual source / toward the focus */
+    if (sa) {                                      /* at a uniform angle to the face normal */
+        double th = ((double)(x[2] >> 8) + 0.5) * 0x1p-24 * OR_PI - 0.5 * OR_PI;
+        double st = sin(th), ct = cos(th);
+        d[0] = nrm[0] * ct + nrm[2] * st; d[1] = 0.0; d[2] = nrm[2] * ct - nrm[0] * st;
+    } else if (C->kind[J->k] != OR_TX_PLANE) {   /* along the line from the virtual source / toward the focus */
         double sg = C->kind[J->k] == OR_TX_DIVERGING ? 1.0 : -1.0;
         double dx = sg * (o[0] - C->vx[J->k]), dz = sg * (o[2] - C->vz[J->k]);
         double l = sqrt(dx * dx + dz * dz);
@@ -832,6 +848,7 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
             elem_frame(C, e, ce, ne);
             double dx = ce[0] - C->vx[k], dz = ce[2] - C->vz[k];
             if (C->kind[k] == OR_TX_PLANE) len[e] = ce[0] * C->sin_t[k] + ce[2] * C->cos_t[k];
+            else if (C->kind[k] == OR_TX_SYNTHETIC) len[e] = 0.0;   /* the one element fires at t = 0 */
             else if (C->kind[k] == OR_TX_DIVERGING) len[e] = sqrt(dx * dx + dz * dz);
             else len[e] = -sqrt(dx * dx + dz * dz);
             if (len[e] < mn) mn = len[e];
@@ -874,8 +891,10 @@ static int scene_is_rough(const or_scene *sc)
 int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg,
                  or_arrival *out, int64_t cap, uint64_t *topo, or_stats *st, int n_threads)
 {
-    if (!sc || !ar || !cfg || cfg->ray_end < cfg->ray_begin || cfg->ray_end > cfg->n_rays ||
-        cfg->n_rays == 0 || cfg->n_rays > 0xFFFFFFFFull || ar->n_el <= 0 || cfg->n_tx <= 0 ||
+    if (!sc || !ar || !cfg || cfg->n_tx <= 0 || cfg->n_rays == 0 || cfg->n_rays > 0xFFFFFFFFull ||
+        cfg->mix < 0 || cfg->mix > 1 ||
+        cfg->n_rays * (cfg->mix ? (uint64_t)cfg->n_tx : 1u) > 0xFFFFFFFFull || cfg->ray_end < cfg->ray_begin ||
+        cfg->ray_end > cfg->n_rays * (cfg->mix ? (uint64_t)cfg->n_tx : 1u) || ar->n_el <= 0 ||
         cfg->max_bounces < 0 || cfg->max_bounces > 127 || sc->n_scat > (1 << 24))
         return -1;
     for (int m = 0; m < sc->n_med; ++m)
@@ -887,7 +906,9 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
         for (int k = 0; k < cfg->n_tx; ++k) {
             int kd = cfg->tx_kind[k];
             if (kd == OR_TX_DIVERGING ? !(cfg->tx_z[k] < 0.0f) : kd == OR_TX_FOCUSED ? !(cfg->tx_z[k] > 0.0f)
-                                                                                     : kd != OR_TX_PLANE)
+                : kd == OR_TX_SYNTHETIC ? !(cfg->tx_x[k] >= 0.0f && cfg->tx_x[k] < (float)ar->n_el &&
+                                            cfg->tx_x[k] == floorf(cfg->tx_x[k]))
+                : kd != OR_TX_PLANE)
                 return -1;
         }
     }
@@ -896,7 +917,7 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
     ctx_t C;
     setup(&C, sc, ar, cfg);
     uint64_t n_sub = cfg->ray_end - cfg->ray_begin;
-    int64_t total = (int64_t)(n_sub * (uint64_t)cfg->n_tx);
+    int64_t total = (int64_t)(n_sub * (cfg->mix ? 1u : (uint64_t)cfg->n_tx));
     if (n_threads <= 0) n_threads = 1;
     abuf_t *bufs = (abuf_t *)calloc((size_t)n_threads, sizeof(abuf_t));
     or_stats *sts = (or_stats *)calloc((size_t)n_threads, sizeof(or_stats));
@@ -916,6 +937,11 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
             memset(&J, 0, sizeof J);
             J.k = (int)(g / (int64_t)n_sub);
             J.i = (uint32_t)(cfg->ray_begin + (uint64_t)(g % (int64_t)n_sub));
+            if (cfg->mix) {   /* the ray's transmit, uniform over n_tx, from counter (i, 0, EMIT, 1) */
+                uint32_t y[4];
+                draw(cfg->seed, J.i, 0u, 0u, 1u, y);
+                J.k = (int)(((uint64_t)(y[0] >> 8) * (uint64_t)cfg->n_tx) >> 24);
+            }
             J.buf = &bufs[tid];
             uint64_t h = trace_ray(&C, &J);
             if (topo) topo[g] = h;
@@ -1035,13 +1061,17 @@ void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const
                 double vx = tx_kind ? tx_x[k] : 0.0, vz = tx_kind ? tx_z[k] : 0.0;
                 double mn = INFINITY, mx = -INFINITY;
                 for (int e = 0; e < n_el; ++e) {
+                    if (kd == OR_TX_SYNTHETIC) break;
                     double v = kd == OR_TX_PLANE ? cx[e] * st + cz[e] * ct
                                                  : sqrt((cx[e] - vx) * (cx[e] - vx) + (cz[e] - vz) * (cz[e] - vz));
                     if (v < mn) mn = v;
                     if (v > mx) mx = v;
                 }
                 double t_tx;
-                if (kd == OR_TX_PLANE) {
+                if (kd == OR_TX_SYNTHETIC) {                         /* from the firing element */
+                    int f = (int)vx;
+                    t_tx = sqrt((x - cx[f]) * (x - cx[f]) + (z - cz[f]) * (z - cz[f])) / c;
+                } else if (kd == OR_TX_PLANE) {
                     t_tx = (x * st + z * ct - mn) / c;               /* plane wave reaches the pixel */
                 } else if (kd == OR_TX_DIVERGING) {                  /* from the virtual source */
                     t_tx = (sqrt((x - vx) * (x - vx) + (z - vz) * (z - vz)) - mn) / c;
@@ -1406,7 +1436,7 @@ int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, con
 {
     if (!sc || !ar || !cfg || !g_rf || !g_q || !grad_media || sc->n_med > 4 || cfg->mode != OR_MODE_MC ||
         cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling || scene_is_rough(sc) ||
-        ar->radius != 0.0f || cfg->tx_kind)
+        ar->radius != 0.0f || cfg->tx_kind || cfg->mix)
         return -1;
     ctx_t C;
     setup(&C, sc, ar, cfg);

@@ -28,7 +28,7 @@ extern "C" {
 #endif
 
 enum { OR_PLANE_Z = 0, OR_SPHERE = 1, OR_CYL_Y = 2 };
-enum { OR_TX_PLANE = 0, OR_TX_DIVERGING = 1, OR_TX_FOCUSED = 2 };
+enum { OR_TX_PLANE = 0, OR_TX_DIVERGING = 1, OR_TX_FOCUSED = 2, OR_TX_SYNTHETIC = 3 };
 enum { OR_MODE_MC = 0, OR_MODE_EXPECT = 1 };
 enum { OR_END_APERTURE = 1, OR_END_ARRAY_MISS = 2, OR_END_BOTTOM = 3,  /* 2: missed the aperture or escaped past a convex probe */
        OR_END_PATH = 4, OR_END_TIME = 5, OR_END_MAXB = 6, OR_END_ROUGH = 7 };
@@ -74,7 +74,11 @@ typedef struct {
                                 direct aperture hits (the method); 1: BSDF sampling alone (for tests) */
     const int32_t *tx_kind;  /* nullable [n_tx]: OR_TX_* per transmit (default: plane waves of angles[]) */
     const float *tx_x, *tx_z;/* [n_tx] with tx_kind: virtual source (diverging, z < 0) or focus
-                                (focused, z > 0) in the xz plane (m) */
+                                (focused, z > 0) in the xz plane (m); synthetic aperture: tx_x is the
+                                index of the one element that fires (an integer value), tx_z unused */
+    int32_t mix;             /* 0: n_rays rays per transmit, ray_begin/ray_end index each transmit's rays.
+                                1: n_tx * n_rays rays in all, each drawing its transmit (Sec. 2.3);
+                                ray_begin/ray_end index that one sequence and topo is [ray_end - ray_begin] */
 } or_trace_cfg;
 
 typedef struct {
@@ -115,7 +119,8 @@ void or_beamform(const or_array *ar, int32_t n_tx, const float *angles,
 
 /* The same with transmit kinds (tx_kind, tx_x, tx_z nullable as in or_trace_cfg): the
  * transmit delay of a diverging wave is the distance from its virtual source, that of a
- * focused wave the arrival of the converging then diverging wave through its focus. */
+ * focused wave the arrival of the converging then diverging wave through its focus, that
+ * of a synthetic-aperture transmit the distance from the firing element's centre. */
 void or_beamform_tx(const or_array *ar, int32_t n_tx, const float *angles, const int32_t *tx_kind,
                     const float *tx_x, const float *tx_z, const double *rf, const double *quad,
                     const float *x_px, int32_t nx, const float *z_px, int32_t nz,

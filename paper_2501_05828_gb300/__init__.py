@@ -30,7 +30,7 @@ EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_se
            "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune",
            "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint", "ur_nn_create", "ur_nn_destroy",
            "ur_nn_last_error", "ur_nn_param_count", "ur_nn_launch_count", "ur_nn_params", "ur_nn_set_scale", "ur_nn_forward",
-           "ur_nn_train_step", "ur_set_transmits")
+           "ur_nn_train_step", "ur_set_transmits", "ur_set_transmit_mixing")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log", "adjoint")
 
 
@@ -74,7 +74,7 @@ class BatchItem(C.Structure):
                 ("n_rays", C.c_uint64)]
 
 
-TX_PLANE, TX_DIVERGING, TX_FOCUSED = 0, 1, 2
+TX_PLANE, TX_DIVERGING, TX_FOCUSED, TX_SYNTHETIC = 0, 1, 2, 3
 
 
 class Transmit(C.Structure):
@@ -107,6 +107,7 @@ def lib():
             L.ur_set_array.argtypes = [vp, C.POINTER(Array)]
             L.ur_set_plane_waves.argtypes = [vp, vp, i32]
             L.ur_set_transmits.argtypes = [vp, C.POINTER(Transmit), i32]
+            L.ur_set_transmit_mixing.argtypes = [vp, i32]
             L.ur_trace.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats)]
             L.ur_trace_debug.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats), C.POINTER(Debug)]
             L.ur_beamform.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, vp, vp]
@@ -225,7 +226,7 @@ class Simulator:
 
     def set_transmits(self, transmits):
         """transmits: sequence of (kind, x, z) with kind TX_DIVERGING / TX_FOCUSED (virtual source /
-        focus at (x, z) in metres) or (TX_PLANE, angle_rad, 0)."""
+        focus at (x, z) in metres), (TX_SYNTHETIC, element, 0) or (TX_PLANE, angle_rad, 0)."""
         t = list(transmits)
         arr = (Transmit * len(t))()
         for k, (kind, a, b) in enumerate(t):
@@ -233,6 +234,11 @@ class Simulator:
                               float(a) if int(kind) != TX_PLANE else 0.0, float(b) if int(kind) != TX_PLANE else 0.0)
         self._call(lib().ur_set_transmits(self._ctx, arr, len(t)))
         self.n_tx = len(t)
+
+    def set_transmit_mixing(self, enabled):
+        """True: trace() and trace_debug() trace n_tx * n_rays rays, each drawing its transmit."""
+        self._call(lib().ur_set_transmit_mixing(self._ctx, int(bool(enabled))))
+        self.mix = bool(enabled)
 
     def set_tuning(self, cell_xy=0.0, cell_z=0.0, block=0, blocks_per_sm=0, resolve_batch=0, cell_y=0.0):
         """Grid cell sizes along x (cell_xy), y and z in metres, launch shape; 0 keeps a default."""
@@ -248,6 +254,8 @@ class Simulator:
             self.set_transmits(workload["transmits"])
         else:
             self.set_plane_waves(workload["angles"])
+        if workload.get("mix") is not None or getattr(self, "mix", False):
+            self.set_transmit_mixing(bool(workload.get("mix")))
 
     # -- simulation ---------------------------------------------------------
     def _channel_shape(self):
@@ -268,7 +276,8 @@ class Simulator:
         return rf, quad
 
     def trace_debug(self, n_rays, seed, max_bounces, max_path=0.2, capacity=None, path_hash=True):
-        """Trace plus every arrival record and per-path hashes (device tensors)."""
+        """Trace plus every arrival record and per-path hashes (device tensors; [n_tx, n_rays], with
+        transmit mixing [n_tx * n_rays] indexed by the ray)."""
         torch = self._torch
         shape = self._channel_shape()
         rf = torch.empty(shape, dtype=torch.float32, device=self.device)
@@ -278,7 +287,8 @@ class Simulator:
         dev = self.device
         out = {k: torch.empty(capacity, dtype=torch.int32, device=dev) for k in ("ray", "event", "row")}
         out.update({k: torch.empty(capacity, dtype=torch.float32, device=dev) for k in ("t_hi", "t_lo", "amp")})
-        ph = torch.empty((self.n_tx, int(n_rays)), dtype=torch.int64, device=dev) if path_hash else None
+        hs = (self.n_tx * int(n_rays),) if getattr(self, "mix", False) else (self.n_tx, int(n_rays))
+        ph = torch.empty(hs, dtype=torch.int64, device=dev) if path_hash else None
         dbg = Debug(capacity, 0, _ptr(out["ray"]), _ptr(out["event"]), _ptr(out["row"]), _ptr(out["t_hi"]),
                     _ptr(out["t_lo"]), _ptr(out["amp"]), _ptr(ph))
         st = Stats()

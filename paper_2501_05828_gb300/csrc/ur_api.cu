@@ -95,8 +95,9 @@ struct ur_ctx {
     ur_array arr{};
     std::vector<float> angles;              // plane-wave angle per transmit (0 for the other kinds)
     std::vector<int> tx_kinds;              // UR_TX_* per transmit
-    std::vector<float> tx_vx, tx_vz;        // virtual source / focus per transmit
+    std::vector<float> tx_vx, tx_vz;        // virtual source / focus (synthetic aperture: element) per transmit
     bool tx_dirty = true;
+    bool mix_tx = false;                    // ur_trace: each ray draws its transmit
     DevBuf delay, tx_sin, tx_cos, tx_m, tx_kind, elem_xz;
 
     // work items of the last trace or batch plan
@@ -244,9 +245,18 @@ void prepare_transmits(ur_ctx *c) {
         cx[e] = R > 0.0 ? R * std::sin(phi0 + e * dphi) : x0 + e * pitch;
         cz[e] = R > 0.0 ? R * (std::cos(phi0 + e * dphi) - 1.0) : 0.0;
     }
+    std::vector<int> das_kind(c->tx_kinds);
     for (int k = 0; k < nt; ++k) {
-        const int kind = c->tx_kinds[k];
-        const double th = c->angles[k], vx = c->tx_vx[k], vz = c->tx_vz[k];
+        int kind = c->tx_kinds[k];
+        double vx = c->tx_vx[k], vz = c->tx_vz[k];
+        if (kind == UR_TX_SYNTHETIC) {   // to the delay-and-sum, a wave diverging from the element's centre
+            if (!(vx < (double)ne)) fail(UR_ERR_INVALID_ARG, "a synthetic-aperture transmit names an element past the array");
+            const int f = (int)vx;
+            vx = cx[f];
+            vz = cz[f];
+            das_kind[k] = UR_TX_DIVERGING;
+        }
+        const double th = c->angles[k];
         const double sn = std::sin(th), cs = std::cos(th);
         // path from the wave's reference to element e: c_e . (sin, cos) (plane), |c_e - v|
         // (diverging), -|c_e - f| (focused); each element fires when the wavefront through the
@@ -254,7 +264,9 @@ void prepare_transmits(ur_ctx *c) {
         double mn = INFINITY;
         for (int e = 0; e < ne; ++e) {
             const double r = std::sqrt((cx[e] - vx) * (cx[e] - vx) + (cz[e] - vz) * (cz[e] - vz));
-            len[e] = kind == UR_TX_PLANE ? cx[e] * sn + cz[e] * cs : (kind == UR_TX_DIVERGING ? r : -r);
+            len[e] = kind == UR_TX_PLANE ? cx[e] * sn + cz[e] * cs
+                   : kind == UR_TX_SYNTHETIC ? 0.0   // the one element fires at t = 0
+                   : kind == UR_TX_DIVERGING ? r : -r;
             mn = std::min(mn, len[e]);
         }
         for (int e = 0; e < ne; ++e)
@@ -275,7 +287,7 @@ void prepare_transmits(ur_ctx *c) {
         ck(cudaStreamSynchronize(c->stream), "element centres");
     }
     c->grow(c->tx_kind, sizeof(int) * std::max(nt, 1));
-    ck(cudaMemcpyAsync(c->tx_kind.p, c->tx_kinds.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->stream),
+    ck(cudaMemcpyAsync(c->tx_kind.p, das_kind.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, c->stream),
        "copy kinds");
     c->grow(c->delay, sizeof(ur::ff) * delay.size());
     c->grow(c->tx_sin, sizeof(ur::ff) * nt);
@@ -474,7 +486,9 @@ void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
 }
 
 // Items -> slot ranges (element-major, padded to the tracer's pool size) and hash offsets.
-void set_items(ur_ctx *c, const std::vector<ur_batch_item> &in) {
+// mix_rays > 0: item 0 holds the slots of one sequence of mix_rays rays that draw their
+// item (transmit mixing); the other items hold none and every item's hashes start at 0.
+void set_items(ur_ctx *c, const std::vector<ur_batch_item> &in, uint64_t mix_rays = 0) {
     c->no_capture("setting work items");
     const int n_el = c->arr.n_el;
     std::vector<ur::ItemP> it(in.size());
@@ -499,6 +513,16 @@ void set_items(ur_ctx *c, const std::vector<ur_batch_item> &in) {
         const uint64_t s = (uint64_t)I.rays_per_el * (uint64_t)n_el;
         slot += (s + ur::kTracePool - 1) / ur::kTracePool * ur::kTracePool;
         hash += b.n_rays;
+    }
+    if (mix_rays > 0) {
+        const uint32_t per_el = (uint32_t)((mix_rays + (uint64_t)n_el - 1) / (uint64_t)n_el);
+        slot = ((uint64_t)per_el * (uint64_t)n_el + ur::kTracePool - 1) / ur::kTracePool * ur::kTracePool;
+        for (size_t q = 0; q < it.size(); ++q) {
+            it[q].slot_begin = q == 0 ? 0 : slot;
+            it[q].hash_begin = 0;
+        }
+        it[0].n_rays = (uint32_t)mix_rays;
+        it[0].rays_per_el = per_el;
     }
     c->items = it;
     c->n_slots = slot;
@@ -599,8 +623,12 @@ void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
     P.arr_cap = c->arr_cap;
     ck(cudaMemsetAsync(P.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
     c->phase_begin(UR_PHASE_TRACE);
-    bool point_waves = false;   // diverging or focused transmits take the extended tracer
+    bool point_waves = P.mix_tx > 0;   // other transmit kinds and mixing take the extended tracer
     for (const ur::ItemP &it : c->items) point_waves = point_waves || it.kind != UR_TX_PLANE;
+    bool split = false;
+    for (int q = 0; q < P.n_scenes; ++q) split = split || P.S[q].split_sampling != 0;
+    if (split && (point_waves || P.radius > 0.f))
+        fail(UR_ERR_INVALID_ARG, "frozen sampling media need plane-wave transmits without mixing on a linear array");
     ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream, point_waves);
     ck(cudaGetLastError(), "trace kernel launch");
     c->phase_end(UR_PHASE_TRACE, 1);
@@ -682,6 +710,8 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     if (!rf || !quad) fail(UR_ERR_INVALID_ARG, "rf and quad are required");
     prepare_transmits(c);
     const int n_tx = (int)c->angles.size(), n_el = c->arr.n_el, n_s = c->arr.n_s;
+    const uint64_t mix_rays = c->mix_tx ? n_rays * (uint64_t)n_tx : 0;
+    if (mix_rays > 0xFFFFFFFFull) fail(UR_ERR_INVALID_ARG, "with transmit mixing n_tx * n_rays_per_tx must be below 2^32");
     const uint64_t n_rows = (uint64_t)n_tx * n_el;
     if (n_rows > (1ull << 26)) fail(UR_ERR_INVALID_ARG, "n_tx * n_el too large");
     const size_t out_elems = (size_t)n_rows * n_s;
@@ -689,11 +719,13 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     if (dbg_on && dbg->path_hash && !is_device_ptr(dbg->path_hash)) fail(UR_ERR_INVALID_ARG, "debug arrays must be device memory");
     std::vector<ur_batch_item> items(n_tx);
     for (int k = 0; k < n_tx; ++k) items[k] = ur_batch_item{0, k, (uint32_t)k, 0u, n_rays};
-    set_items(c, items);
+    set_items(c, items, mix_rays);
     c->batch_ok = false;
     ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
+    P.mix_tx = mix_rays > 0 ? n_tx : 0;
     P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
-    const bool record = c->want_rec && !dbg_on;   // (ray, event) of each arrival, for ur_trace_adjoint
+    // (ray, event) of each arrival, for ur_trace_adjoint (which refuses mixed traces)
+    const bool record = c->want_rec && !dbg_on && mix_rays == 0;
     P.record = record ? 1 : 0;
 
     const double want = c->arr_per_ray * (double)n_rays * (double)n_tx * 1.25 + 4096.0;
@@ -956,6 +988,10 @@ ur_status ur_set_transmits(ur_ctx *c, const ur_transmit *tx, int n_tx) {
                     fail(UR_ERR_INVALID_ARG, "a focused wave's focus lies in front of the array (z > 0)");
                 vx[k] = q.x;
                 vz[k] = q.z;
+            } else if (q.kind == UR_TX_SYNTHETIC) {
+                if (!(q.x >= 0.f && q.x < (float)c->arr.n_el && q.x == std::floor(q.x)))
+                    fail(UR_ERR_INVALID_ARG, "a synthetic-aperture transmit names an element index in [0, n_el)");
+                vx[k] = q.x;
             } else {
                 fail(UR_ERR_INVALID_ARG, "unknown transmit kind");
             }
@@ -967,6 +1003,13 @@ ur_status ur_set_transmits(ur_ctx *c, const ur_transmit *tx, int n_tx) {
         c->tx_vz = vz;
         c->tx_dirty = true;
         c->batch_ok = false;
+    });
+}
+
+ur_status ur_set_transmit_mixing(ur_ctx *c, int enabled) {
+    return guarded(c, [&] {
+        if (enabled != 0 && enabled != 1) fail(UR_ERR_INVALID_ARG, "enabled must be 0 or 1");
+        c->mix_tx = enabled == 1;
     });
 }
 
@@ -1120,6 +1163,7 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
             if (m.roughness != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports smooth boundaries only");
         for (int k : c->tx_kinds)
             if (k != UR_TX_PLANE) fail(UR_ERR_INVALID_ARG, "the adjoint supports plane-wave transmits only");
+        if (c->mix_tx) fail(UR_ERR_INVALID_ARG, "the adjoint does not support transmit mixing");
         if (c->arr.radius != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports linear arrays only");
         prepare_transmits(c);
         const int n_tx = (int)c->angles.size();

@@ -157,8 +157,9 @@ struct ItemP {
     int scene, angle;
     float sin_t, cos_t, inv_n;
     uint32_t stream;        // Philox counter word identifying the transmit's random stream
-    int kind;               // UR_TX_*: plane wave (sin_t, cos_t), diverging or focused wave
-    float vx, vz;           // virtual source or focus in the xz plane (m)
+    int kind;               // UR_TX_*: plane wave (sin_t, cos_t), diverging, focused or synthetic aperture
+    float vx, vz;           // virtual source or focus in the xz plane (m); synthetic aperture: vx = the
+                            // firing element's index
 };
 
 struct TraceP {
@@ -179,6 +180,8 @@ struct TraceP {
     int max_b;
     float max_path;
     int resolve_batch;              // lanes that must wait before a warp resolves segments
+    int mix_tx;                     // > 0: the rays of item 0's slots draw their transmit among items
+                                    // 0 .. mix_tx - 1 (extended tracer only)
     // outputs
     uint4 *arr;                     // (row, t_hi, t_lo, amp), row = item * n_el + element
     uint2 *arr_dbg;                 // (ray, event), debug only

@@ -315,9 +315,17 @@ __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Co
 }
 
 // Emission (Eq. 6) of ray i of item `item` (a transmit of one scene) from element e.
+// With transmit mixing the ray first draws its transmit (Sec. 2.3); a synthetic-
+// aperture transmit emits every ray from its one element.
 template <bool DBG, bool EXT, bool CVX>
-__device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &IT, uint32_t i,
-                                          uint32_t e, Counters &cn) {
+__device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &slot_item,
+                                          uint32_t i, uint32_t e, Counters &cn) {
+    if (EXT && P.mix_tx > 0) {
+        const uint4 y = philox(make_uint4(i, 0u, 0u, 1u), P.key);
+        item = (uint32_t)(((uint64_t)(y.x >> 8) * (uint64_t)P.mix_tx) >> 24);
+    }
+    const ItemP &IT = EXT && P.mix_tx > 0 ? P.items[item] : slot_item;
+    if (EXT && IT.kind == UR_TX_SYNTHETIC) e = (uint32_t)IT.vx;
     const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
@@ -332,6 +340,11 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
     }
     if (!EXT || IT.kind == UR_TX_PLANE) {
         R.d = make_float3(IT.sin_t, 0.f, IT.cos_t);
+    } else if (IT.kind == UR_TX_SYNTHETIC) {   // uniform angle to the face normal in (-pi/2, pi/2)
+        const float th = ((float)(int)((x.z >> 8) - (1u << 23)) + 0.5f) * (kPiF * 0x1p-24f);
+        float st, ct;
+        sincosf(th, &st, &ct);
+        R.d = make_float3(nrm.x * ct + nrm.z * st, 0.f, nrm.z * ct - nrm.x * st);
     } else {   // along the line from the virtual source, or toward the focus, in the xz plane
         const float sg = IT.kind == UR_TX_DIVERGING ? 1.f : -1.f;
         const float dx = sg * (R.o.x - IT.vx), dz = sg * (R.o.z - IT.vz);

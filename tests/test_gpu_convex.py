@@ -132,3 +132,17 @@ def test_paper_settings_on_the_convex_probe(ur):
     check_trace_parity(w, G, arr, topo, "paper settings, convex", amp_floor=ROUGH_AMP_FLOOR, dt_max=1e-2,
                        dt_q99=1e-3)
     assert len(arr) > 100
+
+
+def test_convex_synthetic_aperture_parity(ur):
+    """Synthetic-aperture transmits of a convex array: rays at angles to the local normal of an
+    edge element and of an inner one."""
+    w = convex(phantoms.tiny(n_rays=30_000), alpha_deg=10.0)
+    tx = [(oracle.TX_SYNTHETIC, 0.0, 0.0), (oracle.TX_SYNTHETIC, 17.0, 0.0)]
+    w["angles"] = np.zeros(len(tx), np.float32)
+    w["transmits"] = tx
+    G = run_gpu(ur, w, capacity=4 * len(tx) * w["n_rays"])
+    arr, topo, _ = oracle.trace(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"],
+                                w["max_path"], topo=True, transmits=tx)
+    res = check_trace_parity(w, G, arr, topo, "convex synthetic aperture", amp_floor=CONVEX_AMP_FLOOR)
+    assert res["n_matched"] >= 0.999 * len(arr) and len(arr) > 200
