@@ -212,16 +212,19 @@ def oracle_rate(w, target_s, threads=None):
     import oracle
     threads = threads or (os.cpu_count() or 1)
     t0 = time.perf_counter()
-    tx = w.get("transmits")   # (kind, x, z) of diverging / focused waves (the oracle's form)
+    tx = w.get("transmits")   # (kind, x, z) of other transmit kinds (the oracle's form)
+    mix = bool(w.get("mix"))  # with transmit mixing the sample is rays 0 .. n * n_tx - 1 of the one sequence
+    n_tx = len(np.atleast_1d(w["angles"]))
+    per = n_tx if mix else 1
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
-                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, 4096, threads=threads, transmits=tx)
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, 4096 * per, threads=threads, transmits=tx, mix=mix)
     probe = time.perf_counter() - t0
     n = int(max(1024, min(w["n_rays"], 4096 * target_s / max(probe, 1e-3))))
     t0 = time.perf_counter()
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
-                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, n, threads=threads, transmits=tx)
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, n * per, threads=threads, transmits=tx, mix=mix)
     dt = time.perf_counter() - t0
-    return n * len(np.atleast_1d(w["angles"])) / dt, n, dt, threads
+    return n * n_tx / dt, n, dt, threads
 
 
 def run_reference(args, rank):
@@ -368,8 +371,8 @@ def run_ours(args, rank, world, local_rank):
             "acquisitions_per_s": whole_job_rate(1, world, ms_max * 1e-3),
             "phase_ms": phase_ms,
             "roofline": {"bound": "alu",
-                         "kernel": "k_trace" + (" (extended instantiation: rough boundaries, diverging and focused "
-                                                "waves, convex arrays)" if args.workload != "layered" else ""),
+                         "kernel": "k_trace" + (" (extended instantiation: rough boundaries, transmit kinds other "
+                                                "than plane waves, transmit mixing, convex arrays)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
@@ -405,16 +408,32 @@ PAPER_WORKLOAD = ("paper settings (Sec. 4) on a synthetic vertebra stand-in: 128
 DIVERGING_WORKLOAD = ("layered phantom imaged with 9 diverging waves: virtual sources 10 mm behind the array at "
                       "x = -12..12 mm, 1.11M rays each (1e7 rays per acquisition), compounded DAS to 512x256, 60 dB")
 CONVEX_WORKLOAD = PAPER_WORKLOAD.replace("128 el,", "128 el on a 70-deg convex arc (R 50 mm, the paper's probe),", 1)
+SYNTHETIC_WORKLOAD = ("layered phantom imaged by synthetic aperture: 16 transmits, each firing one element (every "
+                      "8th, 4..124) at t = 0, 625k rays each at uniform angles to the element normal (1e7 rays per "
+                      "acquisition), compounded DAS to 512x256, 60 dB")
+MIXED_WORKLOAD = PAPER_WORKLOAD.replace("25 plane waves -30..30 deg x 512k rays (12.8M rays per acquisition)",
+                                        "25 plane waves -30..30 deg, 12.8M rays per acquisition, each drawing its "
+                                        "plane wave (per-ray transmit mixing)", 1)
 FRAME_WORKLOADS = {"layered": WORKLOAD, "rough": ROUGH_WORKLOAD, "paper": PAPER_WORKLOAD,
-                   "diverging": DIVERGING_WORKLOAD, "convex": CONVEX_WORKLOAD}
+                   "diverging": DIVERGING_WORKLOAD, "convex": CONVEX_WORKLOAD, "synthetic": SYNTHETIC_WORKLOAD,
+                   "mixed": MIXED_WORKLOAD}
 
 
 def frame_workload(args):
     """The phantom of a frame workload: layered (default), rough or paper."""
     import phantoms
-    if args.workload in ("paper", "convex"):
-        return phantoms.paper_like(convex=args.workload == "convex")
+    if args.workload in ("paper", "convex", "mixed"):
+        w = phantoms.paper_like(convex=args.workload == "convex")
+        w["mix"] = args.workload == "mixed"
+        return w
     w = phantoms.layered()
+    if args.workload == "synthetic":
+        import numpy as np
+        els = np.arange(4, w["array"]["n_el"], 8)
+        w["angles"] = np.zeros(els.size, np.float32)
+        w["transmits"] = [(3, float(e), 0.0) for e in els]   # (synthetic aperture, element, unused)
+        w["n_rays"] = 10_000_000 // els.size
+        return w
     if args.workload == "diverging":
         import numpy as np
         xs = np.linspace(-12e-3, 12e-3, 9)
@@ -553,8 +572,8 @@ def run_batched(args, rank, world, local_rank):
             "arrivals_per_step": n_arr2, "stats_per_step": st,
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
             "roofline": {"bound": "alu",
-                         "kernel": "k_trace" + (" (extended instantiation: rough boundaries, diverging and focused "
-                                                "waves, convex arrays)" if args.workload != "layered" else ""),
+                         "kernel": "k_trace" + (" (extended instantiation: rough boundaries, transmit kinds other "
+                                                "than plane waves, transmit mixing, convex arrays)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
             "gpu_launches": 7 * args.steps, "clocks": clk,
@@ -874,7 +893,8 @@ def main():
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
     ap.add_argument("--workload", default="layered",
-                    choices=("layered", "rough", "paper", "convex", "diverging", "batched", "adjoint", "denoiser"))
+                    choices=("layered", "rough", "paper", "convex", "diverging", "synthetic", "mixed", "batched",
+                             "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -882,8 +902,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     args.warmup = max(3, args.warmup)
     if args.steps <= 0:
-        args.steps = {"layered": 150, "rough": 60, "paper": 30, "convex": 30, "diverging": 60, "batched": 5,
-                      "adjoint": 30, "denoiser": 30}[args.workload]
+        args.steps = {"layered": 150, "rough": 60, "paper": 30, "convex": 30, "diverging": 60, "synthetic": 60,
+                      "mixed": 30, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "batched":

@@ -366,10 +366,10 @@ def connection(scene, array, p, med, x_e):
 
 
 def simulate(scene, array, angles, n_rays, seed, max_bounces, x_px, z_px, dyn_range_db=60.0,
-             max_path=0.2, ray_begin=0, ray_end=None, threads=None, transmits=None):
+             max_path=0.2, ray_begin=0, ray_end=None, threads=None, transmits=None, mix=False):
     """Whole chain for one frame: trace, deposit, beamform, envelope, log."""
     arr, _, st = trace(scene, array, angles, n_rays, seed, max_bounces, max_path, ray_begin, ray_end,
-                       threads=threads, transmits=transmits)
+                       threads=threads, transmits=transmits, mix=mix)
     rf, quad = deposit(array, len(np.atleast_1d(angles)), arr)
     iq = beamform(array, angles, rf, quad, x_px, z_px, threads=threads, transmits=transmits)
     env, db = envelope_log(iq, dyn_range_db)

@@ -98,6 +98,8 @@ struct ur_ctx {
     std::vector<float> tx_vx, tx_vz;        // virtual source / focus (synthetic aperture: element) per transmit
     bool tx_dirty = true;
     bool mix_tx = false;                    // ur_trace: each ray draws its transmit
+    ur::MixP mix{};                         // ray order of the last mixed trace (list null: none)
+    DevBuf mix_list, mix_bins;
     DevBuf delay, tx_sin, tx_cos, tx_m, tx_kind, elem_xz;
 
     // work items of the last trace or batch plan
@@ -623,6 +625,7 @@ void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
     P.arr_cap = c->arr_cap;
     ck(cudaMemsetAsync(P.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
     c->phase_begin(UR_PHASE_TRACE);
+    if (P.mix_list) ck(ur::launch_mix_plan(c->mix, c->sms, c->stream), "mixed ray order");
     bool point_waves = P.mix_tx > 0;   // other transmit kinds and mixing take the extended tracer
     for (const ur::ItemP &it : c->items) point_waves = point_waves || it.kind != UR_TX_PLANE;
     bool split = false;
@@ -631,7 +634,7 @@ void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
         fail(UR_ERR_INVALID_ARG, "frozen sampling media need plane-wave transmits without mixing on a linear array");
     ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream, point_waves);
     ck(cudaGetLastError(), "trace kernel launch");
-    c->phase_end(UR_PHASE_TRACE, 1);
+    c->phase_end(UR_PHASE_TRACE, P.mix_list ? 4 : 1);
 }
 
 // Sort the arrival queue by row and deposit the pulses (asynchronous).
@@ -723,6 +726,26 @@ void do_trace(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b, float max_pa
     c->batch_ok = false;
     ur::TraceP P = make_trace_params(c, seed, max_b, max_path);
     P.mix_tx = mix_rays > 0 ? n_tx : 0;
+    if (mix_rays > 0) {   // counting sort of the mixed sequence by (drawn transmit, element)
+        bool per_el = false;
+        const int bins = ur::mix_bins(n_tx, n_el, &per_el);
+        if (bins > 0) {
+            c->grow(c->mix_list, sizeof(uint32_t) * mix_rays);
+            c->grow(c->mix_bins, sizeof(uint32_t) * 3 * (size_t)bins);
+            ur::MixP &M = c->mix;
+            M.key = P.key;
+            M.n_rays = (uint32_t)mix_rays;
+            M.n_tx = (uint32_t)n_tx;
+            M.n_el = (uint32_t)n_el;
+            M.n_bins = (uint32_t)bins;
+            M.per_element = per_el;
+            M.count = (uint32_t *)c->mix_bins.p;
+            M.offset = M.count + bins;
+            M.fill = M.offset + bins;
+            M.list = (uint32_t *)c->mix_list.p;
+            P.mix_list = M.list;
+        }
+    }
     P.path_hash = dbg_on ? (unsigned long long *)dbg->path_hash : nullptr;
     // (ray, event) of each arrival, for ur_trace_adjoint (which refuses mixed traces)
     const bool record = c->want_rec && !dbg_on && mix_rays == 0;

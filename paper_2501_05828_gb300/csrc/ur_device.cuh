@@ -182,6 +182,7 @@ struct TraceP {
     int resolve_batch;              // lanes that must wait before a warp resolves segments
     int mix_tx;                     // > 0: the rays of item 0's slots draw their transmit among items
                                     // 0 .. mix_tx - 1 (extended tracer only)
+    const uint32_t *mix_list;       // with mix_tx: the ray index of each of item 0's slots (null: slot order)
     // outputs
     uint4 *arr;                     // (row, t_hi, t_lo, amp), row = item * n_el + element
     uint2 *arr_dbg;                 // (ray, event), debug only
@@ -421,5 +422,18 @@ struct CtxView {
     bool linear;            // the array is linear
 };
 bool ctx_view(const ur_ctx *c, CtxView *v);
+
+// Counting sort of a mixed transmit sequence's rays by (drawn transmit, emitting element).
+constexpr uint32_t kMixMaxBins = 12288;   // bins held in shared memory (48 KB)
+struct MixP {
+    uint2 key;
+    uint32_t n_rays, n_tx, n_el, n_bins;
+    bool per_element;                     // bins are (transmit, element); else transmits
+    uint32_t *count, *offset, *fill;      // [n_bins]
+    uint32_t *list;                       // [n_rays]: ray indices in bin order
+};
+// Bins for n_tx transmits of n_el elements (0: too many transmits to sort).
+int mix_bins(int n_tx, int n_el, bool *per_element);
+cudaError_t launch_mix_plan(const MixP &M, int sms, cudaStream_t s);
 
 }  // namespace ur

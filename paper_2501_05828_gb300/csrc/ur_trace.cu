@@ -697,10 +697,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 if (my_slot < P.items[item].slot_begin) item = item_of(P, my_slot);
                 const ItemP &IT = P.items[item];
                 const uint64_t local = my_slot - IT.slot_begin;
-                const uint32_t m = (uint32_t)(local % IT.rays_per_el);
-                const uint64_t e = local / IT.rays_per_el;
-                const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-                if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH, CVX>(P, R, item, IT, i, (uint32_t)e, cn);
+                if (ROUGH && P.mix_list) {   // a mixed sequence in (drawn transmit, element) order
+                    if (local < IT.n_rays) {
+                        const uint32_t i = P.mix_list[local];
+                        start_ray<DBG, ROUGH, CVX>(P, R, item, IT, i, i % (uint32_t)P.n_el, cn);
+                    }
+                } else {
+                    const uint32_t m = (uint32_t)(local % IT.rays_per_el);
+                    const uint64_t e = local / IT.rays_per_el;
+                    const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
+                    if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH, CVX>(P, R, item, IT, i, (uint32_t)e, cn);
+                }
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }

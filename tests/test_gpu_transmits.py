@@ -194,3 +194,23 @@ def test_synthetic_aperture_and_mixing_refused_where_unsupported(ur):
     with pytest.raises(ur.URError):
         sim.trace(1000, 0, 4)
     sim.close()
+
+
+def test_transmit_mixing_many_transmits(ur):
+    """400 transmits x 32 elements exceed the (transmit, element) bins of the ray-order sort, which
+    then orders the mixed sequence by transmit alone: same paths as the oracle, every ray once."""
+    w = phantoms.tiny(n_rays=100)
+    w["array"] = dict(w["array"], alpha_m_deg=12.0, alpha_c_deg=12.0)
+    w["angles"] = np.deg2rad(np.linspace(-20.0, 20.0, 400)).astype(np.float32)
+    w["mix"] = True
+    n_tx, N = w["angles"].size, w["n_rays"]
+    G = run_gpu(ur, w, capacity=4 * n_tx * N)
+    assert G["stats"]["rays"] == n_tx * N
+    arr, topo, _ = oracle.trace(w["scene"], w["array"], w["angles"], N, w["seed"], w["max_bounces"], w["max_path"],
+                                topo=True, mix=True)
+    assert np.mean(G["hash"] == topo) >= PATH_FRAC
+    from _parity import compare
+    res = compare(G["rec"], arr)
+    assert res["n_matched"] >= 0.999 * len(arr) and len(arr) > 50
+    assert res["el_mismatch"] == 0 and res["max_dt"] <= 1e-3 and res["max_amp_rel"] <= 1e-4
+    G["sim"].close()
