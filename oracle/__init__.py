@@ -53,7 +53,8 @@ class Scene(C.Structure):
                 ("bnd_p", C.POINTER(C.c_float)), ("bnd_med", C.POINTER(C.c_int32)),
                 ("med_array", C.c_int32), ("z_max", C.c_float),
                 ("n_scat", C.c_int32), ("scat", C.POINTER(C.c_float)), ("r_s", C.c_float),
-                ("med_sampling", C.POINTER(C.c_float))]
+                ("med_sampling", C.POINTER(C.c_float)),
+                ("n_tri", C.c_int32), ("tri", C.POINTER(C.c_float)), ("tri_med", C.POINTER(C.c_int32))]
 
 
 class Array(C.Structure):
@@ -166,10 +167,17 @@ def make_scene(scene):
         sc_buf = sc
     ms = scene.get("media_sampling")
     ms = None if ms is None else np.ascontiguousarray(ms, dtype=np.float32).reshape(-1, 4)
+    tris = scene.get("triangles")   # (vertices [n, 9] float32, media [n, 2]: behind, in front)
+    tv = tm = None
+    if tris is not None:
+        tv = np.ascontiguousarray(tris[0], dtype=np.float32).reshape(-1, 9)
+        tm = np.ascontiguousarray(tris[1], dtype=np.int32).reshape(-1, 2)
     s = Scene(med.shape[0], _fp(med), len(scene["boundaries"]), _ip(kinds), _fp(bp), _ip(bm),
               int(scene["med_array"]), float(scene["z_max"]), sc.shape[0], _fp(sc_buf),
-              float(scene["r_s"]), _fp(ms) if ms is not None else None)
-    return s, _Keep(med=med, kinds=kinds, bp=bp, bm=bm, sc=sc_buf, ms=ms)
+              float(scene["r_s"]), _fp(ms) if ms is not None else None,
+              0 if tv is None else tv.shape[0], _fp(tv) if tv is not None else None,
+              _ip(tm) if tm is not None else None)
+    return s, _Keep(med=med, kinds=kinds, bp=bp, bm=bm, sc=sc_buf, ms=ms, tv=tv, tm=tm)
 
 
 def make_array(arr):

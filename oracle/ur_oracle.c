@@ -26,6 +26,13 @@
  *    angle to its normal drawn uniformly in (-pi/2, pi/2) in the xz plane (the
  *    angle the plane-wave scheme fixes is drawn here, Sec. 2.3); the Eq. 6 weight
  *    is the cosine of that angle over N.
+ *  - Triangle meshes (the paper's bone is a CT-derived mesh, Sec. 4; the method
+ *    handles its triangles like any other surface): each triangle separates the
+ *    medium behind it (negative side of (v1 - v0) x (v2 - v0)) from the one in
+ *    front, with that unit normal, a Fresnel interface like the analytic
+ *    boundaries and the GGX roughness of the rougher medium; a ray leaving a
+ *    triangle does not meet it again.  Intersections: Moeller-Trumbore (1997)
+ *    over every triangle, brute force.
  *  - Transmit mixing (Sec. 2.3: rays of different acquisition events leave
  *    together, each with a randomly selected angle): in this mode n_tx * N rays
  *    are traced and ray i draws its transmit k uniformly from its own counter;
@@ -202,6 +209,7 @@ typedef struct {
     int esc;                    /* id of the escape plane z = -R (convex arrays) */
     int *kind;                  /* per transmit: OR_TX_* */
     double *vx, *vz;            /* per transmit: virtual source or focus (m) */
+    int tri0;                   /* hit id of triangle 0 */
 } ctx_t;
 
 static double elem_x(const ctx_t *C, int e) { return C->x0 + (double)e * C->pitch; }
@@ -217,6 +225,33 @@ static void elem_frame(const ctx_t *C, int e, double c[3], double n[3])
         c[0] = elem_x(C, e); c[1] = 0.0; c[2] = 0.0;
         n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
     }
+}
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Distance along o + t d to triangle t (Moeller-Trumbore: barycentric u, v of the
+ * hit from Cramer's rule on o + t d = v0 + u e1 + v e2), INFINITY if none. */
+static double triangle_hit(const or_scene *sc, int t, const double o[3], const double d[3])
+{
+    const float *v = &sc->tri[9 * t];
+    double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+    double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
+    double p[3], q[3];
+    cross3(d, e2, p);
+    double det = dot3(e1, p);
+    if (det == 0.0) return INFINITY;             /* ray parallel to the triangle's plane */
+    double s[3] = {o[0] - v[0], o[1] - v[1], o[2] - v[2]};
+    double u = dot3(s, p) / det;
+    if (u < 0.0 || u > 1.0) return INFINITY;
+    cross3(s, e1, q);
+    double w = dot3(d, q) / det;
+    if (w < 0.0 || u + w > 1.0) return INFINITY;
+    return dot3(e2, q) / det;
 }
 
 /* Nearest boundary along o + t d with t in (OR_TMIN, inf).  `skip` is the
@@ -266,6 +301,11 @@ static int nearest_boundary(const ctx_t *C, const double o[3], const double d[3]
         }
         if (t > OR_TMIN && t < best) { best = t; hit = p; }
     }
+    for (int q = 0; q < sc->n_tri; ++q) {        /* triangles: brute force */
+        if (C->tri0 + q == skip) continue;
+        double t = triangle_hit(sc, q, o, d);
+        if (t > OR_TMIN && t < best) { best = t; hit = C->tri0 + q; }
+    }
     if (terminals && C->R > 0.0) {   /* convex probe: its cylinder, the escape plane z = -R, the bottom */
         double ox = o[0], oz = o[2] + C->R;
         double a = d[0] * d[0] + d[2] * d[2];
@@ -300,6 +340,14 @@ static int nearest_boundary(const ctx_t *C, const double o[3], const double d[3]
 /* Outward normal of primitive p at point h (unit). */
 static void outward_normal(const ctx_t *C, int p, const double h[3], double n[3])
 {
+    if (p >= C->tri0) {                          /* triangle: (v1 - v0) x (v2 - v0) */
+        const float *v = &C->sc->tri[9 * (p - C->tri0)];
+        double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+        double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
+        cross3(e1, e2, n);
+        normalize3(n);
+        return;
+    }
     const float *q = &C->sc->bnd_p[4 * p];
     if (C->sc->bnd_kind[p] == OR_PLANE_Z) {
         n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
@@ -315,7 +363,8 @@ static void outward_normal(const ctx_t *C, int p, const double h[3], double n[3]
 /* Medium on the far side of primitive p for a ray moving along d at h. */
 static int far_medium(const ctx_t *C, int p, const double d[3], const double n_out[3])
 {
-    return dot3(d, n_out) > 0.0 ? C->sc->bnd_med[2 * p + 1] : C->sc->bnd_med[2 * p];
+    const int32_t *m = p >= C->tri0 ? &C->sc->tri_med[2 * (p - C->tri0)] : &C->sc->bnd_med[2 * p];
+    return dot3(d, n_out) > 0.0 ? m[1] : m[0];
 }
 
 /* Connection (secondary) ray: straight from p to the element centre; `skip0` is
@@ -340,7 +389,7 @@ static double connection_to(const ctx_t *C, const double p[3], int med, int skip
         t += th * C->slow[m];
         att += C->a[m] * th;
         double h[3] = {o[0] + th * w[0], o[1] + th * w[1], o[2] + th * w[2]};
-        if (C->sc->bnd_kind[hit] == OR_PLANE_Z) h[2] = C->sc->bnd_p[4 * hit];
+        if (hit < C->sc->n_bnd && C->sc->bnd_kind[hit] == OR_PLANE_Z) h[2] = C->sc->bnd_p[4 * hit];
         double n_out[3];
         outward_normal(C, hit, h, n_out);
         int m2 = far_medium(C, hit, w, n_out);
@@ -693,7 +742,7 @@ static int follow(const ctx_t *C, ray_job *J, double o[3], double d[3], double t
             return OR_END_ARRAY_MISS;
         }
         if (hit == C->bot) return OR_END_BOTTOM;
-        if (sc->bnd_kind[hit] == OR_PLANE_Z) o[2] = sc->bnd_p[4 * hit];
+        if (hit < sc->n_bnd && sc->bnd_kind[hit] == OR_PLANE_Z) o[2] = sc->bnd_p[4 * hit];
         if (t > C->t_last) return OR_END_TIME;
         if (b >= cfg->max_bounces) return OR_END_MAXB;
         /* interaction (Eqs. 7-11) */
@@ -865,10 +914,12 @@ static int setup(ctx_t *C, const or_scene *sc, const or_array *ar, const or_trac
     C->top = sc->n_bnd;
     C->bot = sc->n_bnd + 1;
     C->esc = sc->n_bnd + 2;
-    C->alpha_b = (double *)malloc(sizeof(double) * (size_t)(sc->n_bnd > 0 ? sc->n_bnd : 1));
-    for (int p = 0; p < sc->n_bnd; ++p) {
-        double a0 = sc->med[4 * sc->bnd_med[2 * p] + 3], a1 = sc->med[4 * sc->bnd_med[2 * p + 1] + 3];
-        C->alpha_b[p] = a0 > a1 ? a0 : a1;
+    C->tri0 = sc->n_bnd + 3;
+    C->alpha_b = (double *)calloc((size_t)C->tri0 + (size_t)sc->n_tri, sizeof(double));   /* by hit id */
+    for (int p = 0; p < sc->n_bnd + sc->n_tri; ++p) {
+        const int32_t *m = p < sc->n_bnd ? &sc->bnd_med[2 * p] : &sc->tri_med[2 * (p - sc->n_bnd)];
+        double a0 = sc->med[4 * m[0] + 3], a1 = sc->med[4 * m[1] + 3];
+        C->alpha_b[p < sc->n_bnd ? p : C->tri0 + (p - sc->n_bnd)] = a0 > a1 ? a0 : a1;
     }
     return 0;
 }
@@ -899,6 +950,16 @@ int64_t or_trace(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg
         return -1;
     for (int m = 0; m < sc->n_med; ++m)
         if (!(sc->med[4 * m + 3] >= 0.0f && sc->med[4 * m + 3] <= 4.0f)) return -1;
+    if (sc->n_tri < 0 || sc->n_tri > (1 << 22) || (sc->n_tri > 0 && (!sc->tri || !sc->tri_med))) return -1;
+    for (int q = 0; q < sc->n_tri; ++q) {
+        const int32_t *m = &sc->tri_med[2 * q];
+        if (m[0] < 0 || m[0] >= sc->n_med || m[1] < 0 || m[1] >= sc->n_med) return -1;
+        const float *v = &sc->tri[9 * q];
+        double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
+        double e2[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]}, n[3];
+        cross3(e1, e2, n);
+        if (!(dot3(n, n) > 0.0)) return -1;      /* degenerate triangle */
+    }
     if (!(ar->radius >= 0.0f) || (ar->radius > 0.0f && !((double)ar->n_el * ar->pitch < 3.0 * ar->radius)))
         return -1;   /* convex: the aperture spans less than about 170 degrees */
     if (cfg->tx_kind) {
@@ -1286,7 +1347,7 @@ static dnum dual_connection(const gctx_t *G, const double p[3], int med, double 
         t = dn_add(t, dn_scale(G->slow[m], th));
         att = dn_add(att, dn_scale(G->a[m], th));
         double h[3] = {o[0] + th * w[0], o[1] + th * w[1], o[2] + th * w[2]};
-        if (C->sc->bnd_kind[hit] == OR_PLANE_Z) h[2] = C->sc->bnd_p[4 * hit];
+        if (hit < C->sc->n_bnd && C->sc->bnd_kind[hit] == OR_PLANE_Z) h[2] = C->sc->bnd_p[4 * hit];
         double n_out[3];
         outward_normal(C, hit, h, n_out);
         int m2 = far_medium(C, hit, w, n_out);
@@ -1436,7 +1497,7 @@ int or_grad(const or_scene *sc, const or_array *ar, const or_trace_cfg *cfg, con
 {
     if (!sc || !ar || !cfg || !g_rf || !g_q || !grad_media || sc->n_med > 4 || cfg->mode != OR_MODE_MC ||
         cfg->ray_end > cfg->n_rays || cfg->ray_end < cfg->ray_begin || sc->med_sampling || scene_is_rough(sc) ||
-        ar->radius != 0.0f || cfg->tx_kind || cfg->mix)
+        ar->radius != 0.0f || cfg->tx_kind || cfg->mix || sc->n_tri)
         return -1;
     ctx_t C;
     setup(&C, sc, ar, cfg);

@@ -50,6 +50,11 @@ typedef struct {
     float r_s;               /* scatterer capture radius (m) */
     const float *med_sampling; /* nullable [n_med][4]: c, Z used for the Monte Carlo branch decisions
                                   and the branch probabilities in the weights (default: med) */
+    int32_t n_tri;           /* triangle-mesh boundaries (0 <= n_tri <= 2^22); triangle t has hit id
+                                n_bnd + 3 + t (after the terminal planes) */
+    const float *tri;        /* [n_tri][9]: vertices v0, v1, v2 (m) */
+    const int32_t *tri_med;  /* [n_tri][2]: medium behind the triangle (negative side of its normal
+                                (v1 - v0) x (v2 - v0)), medium in front */
 } or_scene;
 
 typedef struct {

@@ -174,3 +174,129 @@ def single_scatterer(pos, amp=1.0, medium=WATER, n_el=32, n_s=1536, n_rays=1_000
     sc = _scene([medium], [], 0, z_max, np.asarray([[pos[0], pos[1], pos[2], amp]], np.float32), r_s)
     return {"name": "scatterer", "scene": sc, "array": arr, "angles": np.zeros(1, np.float32),
             "n_rays": int(n_rays), "seed": 0, "max_bounces": 4, "max_path": 0.2}
+
+
+# ------------------------------------------------------------------ triangle meshes
+# Triangles are [n, 9] float32 vertex triples (v0, v1, v2) wound so that
+# (v1 - v0) x (v2 - v0) points out of the enclosed region; with them goes an
+# [n, 2] int32 table of (medium inside / behind, medium outside / in front).
+
+def _outward(tris, inner):
+    """Reorder each triangle's vertices so that its normal points away from inner(centroid)."""
+    t = tris.reshape(-1, 3, 3).copy()
+    n = np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0])
+    c = t.mean(axis=1)
+    flip = np.einsum("ij,ij->i", n, c - inner(c)) < 0
+    t[flip, 1], t[flip, 2] = t[flip, 2].copy(), t[flip, 1].copy()
+    return t.reshape(-1, 9)
+
+
+def mesh_quad(z, x0, x1, y0, y1):
+    """Rectangle z = const over [x0, x1] x [y0, y1] as two triangles, normal +z."""
+    t = np.array([[x0, y0, z, x1, y0, z, x1, y1, z], [x0, y0, z, x1, y1, z, x0, y1, z]], np.float64)
+    return t.astype(np.float32)
+
+
+def mesh_tilted_quad(p0, beta, half_x, half_y):
+    """Rectangle through p0 = (x, z) with unit normal (sin beta, 0, cos beta), 2 half_x along the
+    tilted x direction and 2 half_y along y, as two triangles facing the normal."""
+    u = np.array([np.cos(beta), 0.0, -np.sin(beta)]) * half_x
+    v = np.array([0.0, half_y, 0.0])
+    c = np.array([p0[0], 0.0, p0[1]])
+    a, b, cc, d = c - u - v, c + u - v, c + u + v, c - u + v
+    t = np.array([np.concatenate([a, b, cc]), np.concatenate([a, cc, d])])
+    n = np.cross(t[:, 3:6] - t[:, 0:3], t[:, 6:9] - t[:, 0:3])
+    want = np.array([np.sin(beta), 0.0, np.cos(beta)])
+    flip = n @ want < 0
+    t[flip, 3:6], t[flip, 6:9] = t[flip, 6:9].copy(), t[flip, 3:6].copy()
+    return t.astype(np.float32)
+
+
+def mesh_box(lo, hi):
+    """Closed axis-aligned box, 12 triangles, outward normals."""
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    corner = lambda i: np.where([(i >> 0) & 1, (i >> 1) & 1, (i >> 2) & 1], hi, lo)
+    faces = [(0, 1, 3, 2), (4, 5, 7, 6), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
+    t = []
+    for a, b, c, d in faces:
+        t.append(np.concatenate([corner(a), corner(b), corner(c)]))
+        t.append(np.concatenate([corner(a), corner(c), corner(d)]))
+    mid = 0.5 * (lo + hi)
+    return _outward(np.array(t), lambda c: mid).astype(np.float32)
+
+
+def mesh_icosphere(centre, radius, subdiv):
+    """Sphere approximated by a subdivided icosahedron (20 * 4^subdiv triangles, vertices on the
+    sphere), outward normals."""
+    g = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, g, 0), (1, g, 0), (-1, -g, 0), (1, -g, 0), (0, -1, g), (0, 1, g), (0, -1, -g), (0, 1, -g),
+         (g, 0, -1), (g, 0, 1), (-g, 0, -1), (-g, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(p, np.float64) / np.linalg.norm(p) for p in v]
+    for _ in range(subdiv):
+        cache, nf = {}, []
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+        for a, b, c in f:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    P = np.array(verts) * radius + np.asarray(centre, np.float64)
+    t = np.array([np.concatenate([P[a], P[b], P[c]]) for a, b, c in f])
+    ctr = np.asarray(centre, np.float64)
+    return _outward(t, lambda c: ctr).astype(np.float32)
+
+
+def mesh_cylinder_y(x, z, r, y0, y1, n_seg):
+    """Closed prism with n_seg sides about the axis through (x, z) along y from y0 to y1 (vertices
+    on the circle of radius r), with end caps; outward normals."""
+    a = np.linspace(0.0, 2 * np.pi, n_seg, endpoint=False)
+    ring = np.column_stack([x + r * np.cos(a), np.zeros(n_seg), z + r * np.sin(a)])
+    t = []
+    for i in range(n_seg):
+        j = (i + 1) % n_seg
+        p, q = ring[i], ring[j]
+        lo_p, lo_q, hi_p, hi_q = p + [0, y0, 0], q + [0, y0, 0], p + [0, y1, 0], q + [0, y1, 0]
+        t += [np.concatenate([lo_p, lo_q, hi_q]), np.concatenate([lo_p, hi_q, hi_p])]
+        for yy in (y0, y1):
+            t.append(np.concatenate([[x, yy, z], p + [0, yy, 0], q + [0, yy, 0]]))
+    axis = lambda c: np.column_stack([np.full(len(c), x), c[:, 1], np.full(len(c), z)])
+    tt = np.array(t)
+    n = np.cross(tt[:, 3:6] - tt[:, 0:3], tt[:, 6:9] - tt[:, 0:3])
+    cen = tt.reshape(-1, 3, 3).mean(axis=1)
+    cap = np.abs(n[:, 1]) > 0.5 * np.linalg.norm(n, axis=1)
+    out = np.where(cap[:, None], np.column_stack([np.zeros(len(cen)), cen[:, 1] - 0.5 * (y0 + y1),
+                                                  np.zeros(len(cen))]), cen - axis(cen))
+    flip = np.einsum("ij,ij->i", n, out) < 0
+    tt[flip, 3:6], tt[flip, 6:9] = tt[flip, 6:9].copy(), tt[flip, 3:6].copy()
+    return tt.astype(np.float32)
+
+
+def triangles(*parts):
+    """Concatenate (triangles, inside medium, outside medium) parts into a scene's mesh entry."""
+    tri = np.concatenate([p[0] for p in parts]).astype(np.float32)
+    med = np.concatenate([np.tile(np.array([[p[1], p[2]]], np.int32), (len(p[0]), 1)) for p in parts])
+    return tri, med
+
+
+def paper_mesh_like(seed=0, n_scat=20_000, n_rays=512_000, subdiv=4, n_seg=96):
+    """paper_like with the bone as triangle meshes, as the paper's CT-derived bone is: the vertebral
+    body an icosphere (20 * 4^subdiv triangles, 5120 by default), the processes closed prisms along
+    elevation (n_seg sides, y in [-15, 15] mm); same acquisition, media and scatterers."""
+    w = paper_like(seed=seed, n_scat=n_scat, n_rays=n_rays)
+    body = mesh_icosphere((0.0, 0.0, 45e-3), 10e-3, subdiv)
+    procs = [mesh_cylinder_y(x, 28e-3, 3e-3, -15e-3, 15e-3, n_seg) for x in (-12e-3, 12e-3)]
+    s = dict(w["scene"])
+    s["boundaries"] = []
+    s["triangles"] = triangles((body, 1, 0), *[(p, 1, 0) for p in procs])
+    w["scene"] = s
+    w["name"] = "paper_mesh_like"
+    return w
