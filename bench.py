@@ -341,8 +341,14 @@ def run_ours(args, rank, world, local_rank):
     h2d = sc_host.numel() * 4 + x_h.numel() * 4 + z_h.numel() * 4 + len(s["media"]) * 16 + len(s["boundaries"]) * 28 + 4
     d2h = db_h.numel() * 4
 
+    tri_h = s.get("triangles")   # a new scene upload clears the triangles: set them again (BVH on the host)
+    if tri_h is not None:
+        h2d += tri_h[0].size * 4 + tri_h[1].size * 4
+
     def e2e_step():
         sim.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], sc_host, s["r_s"])
+        if tri_h is not None:
+            sim.set_triangles(tri_h[0], tri_h[1])
         sim.trace(N, seed, w["max_bounces"], w["max_path"], rf=rf, quad=quad)
         sim.beamform(rf, quad, x_h, z_h, w["dyn_range_db"], iq=None, env=None, db=db_h)
         torch.cuda.synchronize()
@@ -372,7 +378,7 @@ def run_ours(args, rank, world, local_rank):
             "phase_ms": phase_ms,
             "roofline": {"bound": "alu",
                          "kernel": "k_trace" + (" (extended instantiation: rough boundaries, transmit kinds other "
-                                                "than plane waves, transmit mixing, convex arrays)" if args.workload != "layered" else ""),
+                                                "than plane waves, transmit mixing, convex arrays, triangle meshes)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (sm_max_mhz)" % (
@@ -414,14 +420,20 @@ SYNTHETIC_WORKLOAD = ("layered phantom imaged by synthetic aperture: 16 transmit
 MIXED_WORKLOAD = PAPER_WORKLOAD.replace("25 plane waves -30..30 deg x 512k rays (12.8M rays per acquisition)",
                                         "25 plane waves -30..30 deg, 12.8M rays per acquisition, each drawing its "
                                         "plane wave (per-ray transmit mixing)", 1)
+MESH_WORKLOAD = PAPER_WORKLOAD.replace("a rough bone sphere (r 10 mm, 45 mm) and two rough bone cylinders (GGX 0.5)",
+                                       "rough bone (GGX 0.5) as triangle meshes: an icosphere body (r 10 mm, 45 mm, "
+                                       "5120 triangles) and two closed 96-sided prisms along elevation (768 "
+                                       "triangles), traced through a BVH", 1)
 FRAME_WORKLOADS = {"layered": WORKLOAD, "rough": ROUGH_WORKLOAD, "paper": PAPER_WORKLOAD,
                    "diverging": DIVERGING_WORKLOAD, "convex": CONVEX_WORKLOAD, "synthetic": SYNTHETIC_WORKLOAD,
-                   "mixed": MIXED_WORKLOAD}
+                   "mixed": MIXED_WORKLOAD, "mesh": MESH_WORKLOAD}
 
 
 def frame_workload(args):
     """The phantom of a frame workload: layered (default), rough or paper."""
     import phantoms
+    if args.workload == "mesh":
+        return phantoms.paper_mesh_like()
     if args.workload in ("paper", "convex", "mixed"):
         w = phantoms.paper_like(convex=args.workload == "convex")
         w["mix"] = args.workload == "mixed"
@@ -573,7 +585,7 @@ def run_batched(args, rank, world, local_rank):
             "phase_ms_direct_run": {k: v[0] / max(v[2], 1) for k, v in prof.items() if v[2]},
             "roofline": {"bound": "alu",
                          "kernel": "k_trace" + (" (extended instantiation: rough boundaries, transmit kinds other "
-                                                "than plane waves, transmit mixing, convex arrays)" if args.workload != "layered" else ""),
+                                                "than plane waves, transmit mixing, convex arrays, triangle meshes)" if args.workload != "layered" else ""),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "trace_ms_per_launch": trace_ms},
             "gpu_launches": 7 * args.steps, "clocks": clk,
@@ -893,7 +905,7 @@ def main():
     ap.add_argument("--rays", type=int, default=0, help="rays per frame override (profiling captures only)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures only)")
     ap.add_argument("--workload", default="layered",
-                    choices=("layered", "rough", "paper", "convex", "diverging", "synthetic", "mixed", "batched",
+                    choices=("layered", "rough", "paper", "convex", "diverging", "synthetic", "mixed", "mesh", "batched",
                              "adjoint", "denoiser"))
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched workload's ray counts")
     args = ap.parse_args()
@@ -903,7 +915,7 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.steps <= 0:
         args.steps = {"layered": 150, "rough": 60, "paper": 30, "convex": 30, "diverging": 60, "synthetic": 60,
-                      "mixed": 30, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
+                      "mixed": 30, "mesh": 30, "batched": 5, "adjoint": 30, "denoiser": 30}[args.workload]
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "batched":

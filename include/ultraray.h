@@ -158,6 +158,20 @@ ur_status ur_scene_upload_slot(ur_ctx *ctx, int slot, const ur_medium *media, in
                                const ur_boundary *bnd, int n_bnd, int med_array, float z_max,
                                const float *scat_xyza, int n_scat, float r_s);
 
+/* Triangle-mesh boundaries of scene slot `slot` (the paper's bone is a CT-derived
+ * mesh, Sec. 4), replacing any set before; an upload of the slot clears them.
+ * tri[n_tri][9] = vertices v0, v1, v2 (m); tri_med[n_tri][2] = medium behind the
+ * triangle (negative side of its normal (v1 - v0) x (v2 - v0)) and in front.  A
+ * triangle is an interface like the analytic boundaries (Eqs. 7-11; GGX with the
+ * rougher medium's roughness, Eq. 12) with that unit normal; a ray leaving it does not
+ * meet it again.  Triangle t has hit id n_bnd + 3 + t in path hashes and debug
+ * events.  Host or device arrays; 0 <= n_tri <= 2^22 (0 removes the mesh).  A bounding
+ * volume hierarchy is built on the host; scenes with triangles are traced by the
+ * extended tracer and refused by the adjoint.
+ * Errors: UR_ERR_STATE (no scene in the slot), UR_ERR_INVALID_ARG (non-finite or
+ * degenerate triangles, media out of range), UR_ERR_OOM, UR_ERR_CUDA. */
+ur_status ur_scene_set_triangles(ur_ctx *ctx, int slot, const float *tri, const int32_t *tri_med, int n_tri);
+
 /* Transducer description (Sec. 2.3 "Ray Emission").  1 <= n_el <= 4096,
  * 16 <= n_s <= 8192, positive geometry and frequencies, 0 <= alpha_m <= alpha_c < 90.
  * Errors: UR_ERR_INVALID_ARG. */

@@ -30,7 +30,8 @@ EXPORTS = ("ur_create", "ur_destroy", "ur_last_error", "ur_scene_upload", "ur_se
            "ur_batch_status", "ur_batch_beamform", "ur_graph_begin", "ur_graph_end", "ur_graph_launch", "ur_autotune",
            "ur_scene_set_media", "ur_scene_set_amplitudes", "ur_trace_adjoint", "ur_nn_create", "ur_nn_destroy",
            "ur_nn_last_error", "ur_nn_param_count", "ur_nn_launch_count", "ur_nn_params", "ur_nn_set_scale", "ur_nn_forward",
-           "ur_nn_train_step", "ur_set_transmits", "ur_set_transmit_mixing")
+           "ur_nn_train_step", "ur_set_transmits", "ur_set_transmit_mixing",
+           "ur_scene_set_triangles")
 PHASES = ("grid", "trace", "sort", "deposit", "das", "log", "adjoint")
 
 
@@ -108,6 +109,7 @@ def lib():
             L.ur_set_plane_waves.argtypes = [vp, vp, i32]
             L.ur_set_transmits.argtypes = [vp, C.POINTER(Transmit), i32]
             L.ur_set_transmit_mixing.argtypes = [vp, i32]
+            L.ur_scene_set_triangles.argtypes = [vp, i32, vp, vp, i32]
             L.ur_trace.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats)]
             L.ur_trace_debug.argtypes = [vp, u64, u64, i32, f32, vp, vp, C.POINTER(Stats), C.POINTER(Debug)]
             L.ur_beamform.argtypes = [vp, vp, vp, vp, i32, vp, i32, f32, vp, vp, vp]
@@ -235,6 +237,12 @@ class Simulator:
         self._call(lib().ur_set_transmits(self._ctx, arr, len(t)))
         self.n_tx = len(t)
 
+    def set_triangles(self, tri, tri_med, slot=0):
+        """Triangle-mesh boundaries: tri [n, 9] vertices (m), tri_med [n, 2] (behind, in front)."""
+        v = np.ascontiguousarray(tri, np.float32).reshape(-1, 9)
+        m = np.ascontiguousarray(tri_med, np.int32).reshape(-1, 2)
+        self._call(lib().ur_scene_set_triangles(self._ctx, int(slot), _ptr(v), _ptr(m), v.shape[0]))
+
     def set_transmit_mixing(self, enabled):
         """True: trace() and trace_debug() trace n_tx * n_rays rays, each drawing its transmit."""
         self._call(lib().ur_set_transmit_mixing(self._ctx, int(bool(enabled))))
@@ -249,6 +257,8 @@ class Simulator:
         """Scene, array and transmits of a phantoms.* workload dictionary."""
         s = workload["scene"]
         self.upload_scene(s["media"], s["boundaries"], s["med_array"], s["z_max"], s["scatterers"], s["r_s"], slot)
+        if s.get("triangles") is not None:
+            self.set_triangles(s["triangles"][0], s["triangles"][1], slot)
         self.set_array(workload["array"])
         if workload.get("transmits") is not None:
             self.set_transmits(workload["transmits"])

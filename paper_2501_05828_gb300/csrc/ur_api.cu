@@ -76,6 +76,8 @@ struct SceneData {
     float3 g_lo{}, g_h{}, g_inv_h{};
     int3 g_dim{};
     DevBuf scat, amp, refs, cell_count, cell_start, cell_fill, scan_tmp, bbox;
+    int n_tri = 0;                     // triangle-mesh boundaries (ur_scene_set_triangles)
+    DevBuf bvh, tri, tri_nrm;
 };
 
 }  // namespace
@@ -402,6 +404,7 @@ void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const 
     if (slot < 0 || slot >= ur::kMaxScenes) fail(UR_ERR_INVALID_ARG, "scene slot must be in [0, 16)");
     SceneData &sd = c->scenes[slot];
     sd.ok = false;
+    sd.n_tri = 0;   // a new scene starts without triangles
     c->batch_ok = false;
     if (!media || n_med < 1 || n_med > ur::kMaxMed) fail(UR_ERR_INVALID_ARG, "n_med must be in [1, 16]");
     if (n_bnd < 0 || n_bnd > ur::kMaxBnd || (n_bnd > 0 && !bnd)) fail(UR_ERR_INVALID_ARG, "n_bnd must be in [0, 16]");
@@ -449,6 +452,112 @@ void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const 
     sd.version = ++c->versions;
 }
 
+// Bounding volume hierarchy over a scene's triangles, built on the host: each node splits its
+// triangles at the median centroid along the longest axis of their centroid bounds (depth at
+// most ceil(log2 n) + 1, within the tracer's traversal stack), leaves hold up to 4 triangles,
+// boxes are padded outward so that FP32 slab tests cannot cut off a triangle's edge.  Device
+// layout: see ur::SceneP (bvh, tri in leaf order, tri_nrm by triangle id).
+struct MeshBuild {
+    std::vector<float4> bvh, tri, nrm;
+};
+
+void build_mesh(const float *v, const int32_t *med, int n, int n_med, MeshBuild &B) {
+    std::vector<double> cen(3 * (size_t)n);
+    B.nrm.resize(n);
+    for (int t = 0; t < n; ++t) {
+        const float *p = v + 9 * (size_t)t;
+        for (int q = 0; q < 9; ++q)
+            if (!std::isfinite(p[q])) fail(UR_ERR_INVALID_ARG, "triangle vertices must be finite");
+        if (med[2 * t] < 0 || med[2 * t] >= n_med || med[2 * t + 1] < 0 || med[2 * t + 1] >= n_med)
+            fail(UR_ERR_INVALID_ARG, "triangle media out of range");
+        const double e1[3] = {(double)p[3] - p[0], (double)p[4] - p[1], (double)p[5] - p[2]};
+        const double e2[3] = {(double)p[6] - p[0], (double)p[7] - p[1], (double)p[8] - p[2]};
+        const double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+                     nz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double l = std::sqrt(nx * nx + ny * ny + nz * nz);
+        if (!(l > 0.0)) fail(UR_ERR_INVALID_ARG, "degenerate triangle");
+        int bits = med[2 * t] | (med[2 * t + 1] << 8);
+        float wf;
+        std::memcpy(&wf, &bits, 4);
+        B.nrm[t] = make_float4((float)(nx / l), (float)(ny / l), (float)(nz / l), wf);
+        for (int a = 0; a < 3; ++a) cen[3 * t + a] = ((double)p[a] + p[3 + a] + p[6 + a]) / 3.0;
+    }
+    std::vector<int> idx(n);
+    for (int t = 0; t < n; ++t) idx[t] = t;
+    struct Node { double lo[3], hi[3]; int a, b; };
+    struct Task { int node, begin, end, depth; };
+    std::vector<Node> nodes(1);
+    std::vector<Task> todo{{0, 0, n, 1}};
+    int depth = 0;
+    while (!todo.empty()) {
+        const Task k = todo.back();
+        todo.pop_back();
+        depth = std::max(depth, k.depth);
+        Node &N = nodes[k.node];
+        double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int a = 0; a < 3; ++a) {
+            N.lo[a] = INFINITY;
+            N.hi[a] = -INFINITY;
+        }
+        for (int q = k.begin; q < k.end; ++q) {
+            const float *p = v + 9 * (size_t)idx[q];
+            for (int a = 0; a < 3; ++a) {
+                for (int c3 = 0; c3 < 3; ++c3) {
+                    N.lo[a] = std::min(N.lo[a], (double)p[3 * c3 + a]);
+                    N.hi[a] = std::max(N.hi[a], (double)p[3 * c3 + a]);
+                }
+                clo[a] = std::min(clo[a], cen[3 * idx[q] + a]);
+                chi[a] = std::max(chi[a], cen[3 * idx[q] + a]);
+            }
+        }
+        int axis = 0;
+        for (int a = 1; a < 3; ++a)
+            if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+        if (k.end - k.begin <= 4 || !(chi[axis] > clo[axis])) {   // leaf
+            N.a = k.begin;
+            N.b = k.end - k.begin;
+            continue;
+        }
+        const int mid = (k.begin + k.end) / 2;
+        std::nth_element(idx.begin() + k.begin, idx.begin() + mid, idx.begin() + k.end,
+                         [&](int x, int y) { return cen[3 * x + axis] < cen[3 * y + axis]; });
+        const int left = (int)nodes.size();
+        nodes[k.node].a = left;   // N may move when nodes grows
+        nodes[k.node].b = 0;
+        nodes.resize(nodes.size() + 2);
+        todo.push_back({left, k.begin, mid, k.depth + 1});
+        todo.push_back({left + 1, mid, k.end, k.depth + 1});
+    }
+    if (depth >= ur::kBvhStack) fail(UR_ERR_INVALID_ARG, "triangle hierarchy deeper than the traversal stack");
+    B.bvh.resize(2 * nodes.size());
+    for (size_t q = 0; q < nodes.size(); ++q) {
+        const Node &N = nodes[q];
+        float f[2][3];
+        for (int a = 0; a < 3; ++a) {
+            const double pad = 1e-7 + 1e-6 * std::max(std::fabs(N.lo[a]), std::fabs(N.hi[a]));
+            f[0][a] = std::nextafter((float)(N.lo[a] - pad), -INFINITY);
+            f[1][a] = std::nextafter((float)(N.hi[a] + pad), INFINITY);
+        }
+        float wa, wb;
+        std::memcpy(&wa, &N.a, 4);
+        std::memcpy(&wb, &N.b, 4);
+        B.bvh[2 * q] = make_float4(f[0][0], f[0][1], f[0][2], wa);
+        B.bvh[2 * q + 1] = make_float4(f[1][0], f[1][1], f[1][2], wb);
+    }
+    B.tri.resize(3 * (size_t)n);
+    for (int q = 0; q < n; ++q) {
+        const int t = idx[q];
+        const float *p = v + 9 * (size_t)t;
+        float wt;
+        std::memcpy(&wt, &t, 4);
+        B.tri[3 * q] = make_float4(p[0], p[1], p[2], wt);
+        B.tri[3 * q + 1] = make_float4((float)((double)p[3] - p[0]), (float)((double)p[4] - p[1]),
+                                       (float)((double)p[5] - p[2]), 0.f);
+        B.tri[3 * q + 2] = make_float4((float)((double)p[6] - p[0]), (float)((double)p[7] - p[1]),
+                                       (float)((double)p[8] - p[2]), 0.f);
+    }
+}
+
 void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
     const ur_array &A = c->arr;
     S.n_med = (int)sd.media.size();
@@ -475,6 +584,12 @@ void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
         S.bnd[b].alpha = std::max(sd.media[sd.bnd[b].med_neg].roughness, sd.media[sd.bnd[b].med_pos].roughness);
         for (int q = 0; q < 4; ++q) S.bnd[b].p[q] = sd.bnd[b].p[q];
     }
+    S.n_tri = sd.n_tri;
+    S.tri_base = S.n_bnd + 3;
+    S.bvh = (const float4 *)sd.bvh.p;
+    S.tri = (const float4 *)sd.tri.p;
+    S.tri_nrm = (const float4 *)sd.tri_nrm.p;
+    for (int m = 0; m < S.n_med; ++m) S.rough[m] = sd.media[m].roughness;
     S.n_scat = sd.n_scat;
     S.r2 = sd.r_s * sd.r_s;
     S.g_lo = sd.g_lo;
@@ -930,6 +1045,41 @@ ur_status ur_scene_set_media(ur_ctx *c, int slot, const ur_medium *media, int n_
     });
 }
 
+ur_status ur_scene_set_triangles(ur_ctx *c, int slot, const float *tri, const int32_t *tri_med, int n_tri) {
+    return guarded(c, [&] {
+        c->set_device();
+        c->no_capture("ur_scene_set_triangles");
+        if (slot < 0 || slot >= ur::kMaxScenes || !c->scenes[slot].ok) fail(UR_ERR_STATE, "scene slot holds no scene");
+        if (n_tri < 0 || n_tri > ur::kMaxTri) fail(UR_ERR_INVALID_ARG, "n_tri must be in [0, 2^22]");
+        if (n_tri > 0 && (!tri || !tri_med)) fail(UR_ERR_INVALID_ARG, "triangles need vertices and media");
+        SceneData &sd = c->scenes[slot];
+        c->batch_ok = false;
+        if (n_tri == 0) {
+            sd.n_tri = 0;
+            sd.version = ++c->versions;
+            return;
+        }
+        std::vector<float> v(9 * (size_t)n_tri);
+        std::vector<int32_t> m(2 * (size_t)n_tri);
+        ck(cudaMemcpy(v.data(), tri, sizeof(float) * v.size(), cudaMemcpyDefault), "copy triangles");
+        ck(cudaMemcpy(m.data(), tri_med, sizeof(int32_t) * m.size(), cudaMemcpyDefault), "copy triangle media");
+        MeshBuild B;
+        build_mesh(v.data(), m.data(), n_tri, (int)sd.media.size(), B);
+        c->grow(sd.bvh, sizeof(float4) * B.bvh.size());
+        c->grow(sd.tri, sizeof(float4) * B.tri.size());
+        c->grow(sd.tri_nrm, sizeof(float4) * B.nrm.size());
+        ck(cudaMemcpyAsync(sd.bvh.p, B.bvh.data(), sizeof(float4) * B.bvh.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy hierarchy");
+        ck(cudaMemcpyAsync(sd.tri.p, B.tri.data(), sizeof(float4) * B.tri.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy triangles");
+        ck(cudaMemcpyAsync(sd.tri_nrm.p, B.nrm.data(), sizeof(float4) * B.nrm.size(), cudaMemcpyHostToDevice,
+                           c->stream), "copy normals");
+        ck(cudaStreamSynchronize(c->stream), "triangles");
+        sd.n_tri = n_tri;
+        sd.version = ++c->versions;
+    });
+}
+
 ur_status ur_scene_set_amplitudes(ur_ctx *c, int slot, const float *amp, int n_scat) {
     return guarded(c, [&] {
         c->set_device();
@@ -1187,6 +1337,7 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
         for (int k : c->tx_kinds)
             if (k != UR_TX_PLANE) fail(UR_ERR_INVALID_ARG, "the adjoint supports plane-wave transmits only");
         if (c->mix_tx) fail(UR_ERR_INVALID_ARG, "the adjoint does not support transmit mixing");
+        if (sd.n_tri > 0) fail(UR_ERR_INVALID_ARG, "the adjoint supports analytic boundaries only");
         if (c->arr.radius != 0.f) fail(UR_ERR_INVALID_ARG, "the adjoint supports linear arrays only");
         prepare_transmits(c);
         const int n_tx = (int)c->angles.size();

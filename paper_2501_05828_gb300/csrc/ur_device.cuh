@@ -19,6 +19,10 @@ constexpr int kMaxNs = 8192;
 constexpr int kMaxSeg = 4096;      // safety bound on primary segments per path
 constexpr int kMaxCross = 64;      // boundaries a connection ray may cross
 constexpr float kTmin = 1e-7f;     // smallest admissible hit distance (m)
+constexpr int kMaxTri = 1 << 22;   // triangles per scene (hit ids stay below 2^24)
+constexpr int kBvhStack = 32;      // traversal stack; the host's BVH is never deeper
+constexpr int kGeoConvex = 1;      // tracer geometry bits: convex array,
+constexpr int kGeoMesh = 2;        // triangle-mesh boundaries
 constexpr uint64_t kFnvOffset = 0xcbf29ce484222325ull;
 constexpr uint64_t kFnvPrime = 0x100000001b3ull;
 
@@ -146,6 +150,13 @@ struct SceneP {
     // rarely read (after the fields every segment reads, which keep their offsets):
     int split_sampling;               // 1 if some (cs, Zs) differs from the media
     float cs[kMaxMed], Zs[kMaxMed];   // c and Z that decide Monte Carlo branches (normally = med)
+    // triangle meshes (tracer instantiations with kGeoMesh): triangle t has hit id tri_base + t
+    int n_tri, tri_base;              // tri_base = n_bnd + 3, after the terminal planes
+    const float4 *bvh;                // 2 per node: (lo, bits(first child | first triangle)),
+                                      // (hi, bits(0 for an inner node | triangle count)); children adjacent
+    const float4 *tri;                // 3 per triangle in leaf order: (v0, bits(id)), (v1 - v0), (v2 - v0)
+    const float4 *tri_nrm;            // per id: unit normal (v1 - v0) x (v2 - v0), bits(behind | front << 8)
+    float rough[kMaxMed];             // GGX roughness per medium (a triangle takes the larger of its two)
 };
 
 // One transmit of one scene: a contiguous range of ray slots (element-major,
@@ -200,6 +211,95 @@ struct TraceP {
 // cylinder only at its far root.  With `terminals`, the array plane z = 0
 // (id n_bnd, upward rays) and the absorbing plane z = z_max (id n_bnd + 1,
 // downward rays) take part.
+// Moeller-Trumbore: distance along o + t d to the triangle (v0, e1 = v1 - v0, e2 = v2 - v0).
+__device__ __forceinline__ bool tri_hit(float4 v0, float4 e1, float4 e2, float3 o, float3 d, float &t) {
+    const float px = d.y * e2.z - d.z * e2.y, py = d.z * e2.x - d.x * e2.z, pz = d.x * e2.y - d.y * e2.x;
+    const float det = e1.x * px + e1.y * py + e1.z * pz;
+    if (det == 0.f) return false;
+    const float inv = 1.f / det;
+    const float sx = o.x - v0.x, sy = o.y - v0.y, sz = o.z - v0.z;
+    const float u = (sx * px + sy * py + sz * pz) * inv;
+    if (u < 0.f || u > 1.f) return false;
+    const float qx = sy * e1.z - sz * e1.y, qy = sz * e1.x - sx * e1.z, qz = sx * e1.y - sy * e1.x;
+    const float v = (d.x * qx + d.y * qy + d.z * qz) * inv;
+    if (v < 0.f || u + v > 1.f) return false;
+    t = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
+    return true;
+}
+
+// Slab test of a BVH box against (0, t_max); axes the ray runs parallel to test the origin.
+__device__ __forceinline__ bool box_hit(float4 lo, float4 hi, float3 o, float3 inv, int3 par, float t_max,
+                                        float &t_near) {
+    float tn = 0.f, tf = t_max;
+    if (par.x) {
+        if (o.x < lo.x || o.x > hi.x) return false;
+    } else {
+        const float a = (lo.x - o.x) * inv.x, b = (hi.x - o.x) * inv.x;
+        tn = fmaxf(tn, fminf(a, b));
+        tf = fminf(tf, fmaxf(a, b));
+    }
+    if (par.y) {
+        if (o.y < lo.y || o.y > hi.y) return false;
+    } else {
+        const float a = (lo.y - o.y) * inv.y, b = (hi.y - o.y) * inv.y;
+        tn = fmaxf(tn, fminf(a, b));
+        tf = fminf(tf, fmaxf(a, b));
+    }
+    if (par.z) {
+        if (o.z < lo.z || o.z > hi.z) return false;
+    } else {
+        const float a = (lo.z - o.z) * inv.z, b = (hi.z - o.z) * inv.z;
+        tn = fmaxf(tn, fminf(a, b));
+        tf = fminf(tf, fmaxf(a, b));
+    }
+    t_near = tn;
+    return tn <= tf;
+}
+
+// Nearest triangle along o + t d with t in (kTmin, best): BVH walk, near child first.
+__device__ __forceinline__ void nearest_triangle(const SceneP &S, float3 o, float3 d, int skip, float &best,
+                                                 int &hit) {
+    const int3 par = make_int3(d.x == 0.f, d.y == 0.f, d.z == 0.f);
+    const float3 inv = make_float3(par.x ? 0.f : 1.f / d.x, par.y ? 0.f : 1.f / d.y, par.z ? 0.f : 1.f / d.z);
+    int stack[kBvhStack];
+    int sp = 0, node = 0;
+    float t0;
+    if (!box_hit(S.bvh[0], S.bvh[1], o, inv, par, best, t0)) return;
+    for (;;) {
+        const float4 a = S.bvh[2 * node], b = S.bvh[2 * node + 1];
+        const int first = __float_as_int(a.w), cnt = __float_as_int(b.w);
+        if (cnt > 0) {
+            for (int q = first; q < first + cnt; ++q) {
+                const float4 v0 = S.tri[3 * q];
+                const int id = S.tri_base + __float_as_int(v0.w);
+                float t;
+                if (id != skip && tri_hit(v0, S.tri[3 * q + 1], S.tri[3 * q + 2], o, d, t) && t > kTmin &&
+                    t < best) {
+                    best = t;
+                    hit = id;
+                }
+            }
+        } else {
+            float tl, tr;
+            const bool hl = box_hit(S.bvh[2 * first], S.bvh[2 * first + 1], o, inv, par, best, tl);
+            const bool hr = box_hit(S.bvh[2 * first + 2], S.bvh[2 * first + 3], o, inv, par, best, tr);
+            if (hl && hr) {
+                const bool left_first = tl <= tr;
+                if (sp < kBvhStack) stack[sp++] = left_first ? first + 1 : first;
+                node = left_first ? first : first + 1;
+                continue;
+            }
+            if (hl || hr) {
+                node = hl ? first : first + 1;
+                continue;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+}
+
+template <bool MESH = false>
 __device__ __forceinline__ int nearest(const SceneP &S, float3 o, float3 d, int skip, bool terminals,
                                        float &t_out, float radius = 0.f) {
     float best = INFINITY;
@@ -244,6 +344,7 @@ __device__ __forceinline__ int nearest(const SceneP &S, float3 o, float3 d, int 
             hit = p;
         }
     }
+    if (MESH && S.n_tri > 0) nearest_triangle(S, o, d, skip, best, hit);
     if (terminals && radius > 0.f) {   // convex probe: its cylinder (id n_bnd), the escape plane z = -R (n_bnd + 2)
         const float ox = o.x, oz = o.z + radius;
         const float a = d.x * d.x + d.z * d.z;
@@ -294,6 +395,34 @@ __device__ __forceinline__ float3 outward(const Bnd &B, float3 h) {
     if (B.kind == kPlaneZ) return make_float3(0.f, 0.f, 1.f);
     if (B.kind == kSphere) return unit3(make_float3(h.x - B.p[0], h.y - B.p[1], h.z - B.p[2]));
     return unit3(make_float3(h.x - B.p[0], 0.f, h.z - B.p[1]));
+}
+
+// Triangle hit id -> unit outward normal, media behind and in front, GGX roughness.
+__device__ __forceinline__ void surface_tri(const SceneP &S, int hit, float3 &n_out, int &m_neg, int &m_pos,
+                                            float &alpha) {
+    const float4 q = S.tri_nrm[hit - S.tri_base];
+    const int m = __float_as_int(q.w);
+    n_out = make_float3(q.x, q.y, q.z);
+    m_neg = m & 0xff;
+    m_pos = (m >> 8) & 0xff;
+    alpha = fmaxf(S.rough[m_neg], S.rough[m_pos]);
+}
+
+// The surface a ray met (hit id from nearest): unit outward normal at h (a plane's hit point is
+// put on the plane), the media behind and in front, and the GGX roughness.
+template <bool MESH>
+__device__ __forceinline__ void surface(const SceneP &S, int hit, float3 &h, float3 &n_out, int &m_neg, int &m_pos,
+                                        float &alpha) {
+    if (MESH && hit >= S.tri_base) {
+        surface_tri(S, hit, n_out, m_neg, m_pos, alpha);
+        return;
+    }
+    const Bnd &B = S.bnd[hit];
+    if (B.kind == kPlaneZ) h.z = B.p[0];
+    n_out = outward(B, h);
+    m_neg = B.med_neg;
+    m_pos = B.med_pos;
+    alpha = B.alpha;
 }
 
 // Snell (speed ratio) and the fluid-fluid pressure reflection coefficient.

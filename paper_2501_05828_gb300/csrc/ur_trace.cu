@@ -12,6 +12,7 @@ namespace {
 // sqrt(1 - R) over the boundaries it crosses (0 if one reflects totally),
 // travel time (samples) and attenuation exponent.  skip0: the boundary p lies
 // on (-1 inside a medium).
+template <bool MESH>
 __device__ float connection(const SceneP &S, float3 p, int med, int skip0, float xe, ff &t_conn, float &att) {
     float3 o = p;
     float3 w = make_float3(xe - p.x, -p.y, -p.z);
@@ -22,7 +23,7 @@ __device__ float connection(const SceneP &S, float3 p, int med, int skip0, float
     int m = med, skip = skip0;
     for (int it = 0; it < kMaxCross; ++it) {
         float th;
-        const int hit = nearest(S, o, w, skip, false, th);
+        const int hit = nearest<MESH>(S, o, w, skip, false, th);
         const Medium &M = S.med[m];
         if (hit < 0 || th >= rem) {
             t = ff_add(t, ff_mul_f(rem, M.slow));
@@ -31,12 +32,12 @@ __device__ float connection(const SceneP &S, float3 p, int med, int skip0, float
         }
         t = ff_add(t, ff_mul_f(th, M.slow));
         a += M.a * th;
-        float3 h = o + th * w;
-        const Bnd &B = S.bnd[hit];
-        if (B.kind == kPlaneZ) h.z = B.p[0];
-        const float3 n = outward(B, h);
+        float3 h = o + th * w, n;
+        int m_neg, m_pos;
+        float alpha;
+        surface<MESH>(S, hit, h, n, m_neg, m_pos, alpha);
         const float dn = dot3(w, n);
-        const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
+        const int m2 = dn > 0.f ? m_pos : m_neg;
         float r, ct;
         if (!fresnel(fabsf(dn), M.c, M.Z, S.med[m2].c, S.med[m2].Z, r, ct)) return 0.f;
         fac *= sqrtf(1.f - r * r);
@@ -134,6 +135,7 @@ __device__ float rough_eval(float3 d, float3 n, float3 o, float a2, const Medium
 }
 
 // The same toward an arbitrary element centre q (convex arrays).
+template <bool MESH>
 __device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, float3 q, ff &t_conn, float &att) {
     float3 o = p;
     float3 w = make_float3(q.x - p.x, q.y - p.y, q.z - p.z);
@@ -144,7 +146,7 @@ __device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, fl
     int m = med, skip = skip0;
     for (int it = 0; it < kMaxCross; ++it) {
         float th;
-        const int hit = nearest(S, o, w, skip, false, th);
+        const int hit = nearest<MESH>(S, o, w, skip, false, th);
         const Medium &M = S.med[m];
         if (hit < 0 || th >= rem) {
             t = ff_add(t, ff_mul_f(rem, M.slow));
@@ -153,12 +155,12 @@ __device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, fl
         }
         t = ff_add(t, ff_mul_f(th, M.slow));
         a += M.a * th;
-        float3 h = o + th * w;
-        const Bnd &B = S.bnd[hit];
-        if (B.kind == kPlaneZ) h.z = B.p[0];
-        const float3 n = outward(B, h);
+        float3 h = o + th * w, n;
+        int m_neg, m_pos;
+        float alpha;
+        surface<MESH>(S, hit, h, n, m_neg, m_pos, alpha);
         const float dn = dot3(w, n);
-        const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
+        const int m2 = dn > 0.f ? m_pos : m_neg;
         float r, ct;
         if (!fresnel(fabsf(dn), M.c, M.Z, S.med[m2].c, S.med[m2].Z, r, ct)) return 0.f;
         fac *= sqrtf(1.f - r * r);
@@ -248,11 +250,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x &
 
 // Segment from the current position to the nearest boundary (clipped by the
 // path-length budget); set up the grid walk over the part inside the grid box.
-template <bool CVX>
+template <int GEO>
 __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
     const SceneP &S = P.S[R.scene];
     float th;
-    R.hit = nearest(S, R.o, R.d, R.prev, true, th, CVX ? P.radius : 0.f);
+    R.hit = nearest<MESH>(S, R.o, R.d, R.prev, true, th, CVX ? P.radius : 0.f);
     R.seg = th;
     R.clipped = false;
     if (R.L + R.seg > P.max_path) {
@@ -317,9 +320,10 @@ __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Co
 // Emission (Eq. 6) of ray i of item `item` (a transmit of one scene) from element e.
 // With transmit mixing the ray first draws its transmit (Sec. 2.3); a synthetic-
 // aperture transmit emits every ray from its one element.
-template <bool DBG, bool EXT, bool CVX>
+template <bool DBG, bool EXT, int GEO>
 __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &slot_item,
                                           uint32_t i, uint32_t e, Counters &cn) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0;
     if (EXT && P.mix_tx > 0) {
         const uint4 y = philox(make_uint4(i, 0u, 0u, 1u), P.key);
         item = (uint32_t)(((uint64_t)(y.x >> 8) * (uint64_t)P.mix_tx) >> 24);
@@ -367,14 +371,15 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
         end_ray<DBG>(P, R, kEndArrayMiss, cn);
         return;
     }
-    start_segment<CVX>(P, R, cn);
+    start_segment<GEO>(P, R, cn);
 }
 
 // Secondary ray of a rough vertex to a uniformly drawn element centre, weighted
 // against BSDF sampling of the same direction by the balance heuristic.
-template <bool DBG, bool REC, bool CVX>
+template <bool DBG, bool REC, int GEO>
 __device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R, float3 n, int m2, float a2,
                                  Counters &cn) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
     const uint4 x = philox(make_uint4(R.i, R.stream, 4u | ((uint32_t)R.b << 8), 0u), P.key);
     const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     float3 ce, ne;
@@ -392,7 +397,7 @@ __device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R
     cn.connections++;
     ff tc;
     float att;
-    const float fac = connection_to(S, R.o, dot3(o, n) > 0.f ? R.med : m2, R.hit, ce, tc, att);
+    const float fac = connection_to<MESH>(S, R.o, dot3(o, n) > 0.f ? R.med : m2, R.hit, ce, tc, att);
     if (fac == 0.f) return;
     const ff ta = ff_add(R.t, tc);
     if (ff_gt(ta, P.t_last)) return;
@@ -463,8 +468,9 @@ __device__ bool rough_scatter(const TraceP &P, const SceneP &S, Lane &R, float3 
 // End of a segment: time of flight and attenuation along it, then the array
 // plane (aperture return), the absorbing bottom, the time window, the bounce
 // budget, or a boundary interaction (Eqs. 7-11) and the next segment.
-template <bool DBG, bool SPLIT, bool REC, bool ROUGH, bool CVX>
+template <bool DBG, bool SPLIT, bool REC, bool ROUGH, int GEO>
 __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
     const SceneP &S = P.S[R.scene];
     const Medium &M = S.med[R.med];
     R.t = ff_add(R.t, ff_mul_f(R.seg, M.slow));
@@ -518,8 +524,8 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         end_ray<DBG>(P, R, kEndBottom, cn);
         return;
     }
-    const Bnd &B = S.bnd[R.hit];
-    if (B.kind == kPlaneZ) R.o.z = B.p[0];
+    const bool on_tri = MESH && R.hit >= S.tri_base;
+    if (!on_tri && S.bnd[R.hit].kind == kPlaneZ) R.o.z = S.bnd[R.hit].p[0];
     if (ff_gt(R.t, P.t_last)) {
         end_ray<DBG>(P, R, kEndTime, cn);
         return;
@@ -528,13 +534,24 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         end_ray<DBG>(P, R, kEndMaxB, cn);
         return;
     }
-    const float3 n_out = outward(B, R.o);
+    float3 n_out;
+    int m_neg, m_pos;
+    float alpha;
+    if (on_tri) {
+        surface_tri(S, R.hit, n_out, m_neg, m_pos, alpha);
+    } else {
+        const Bnd &B = S.bnd[R.hit];
+        n_out = outward(B, R.o);
+        m_neg = B.med_neg;
+        m_pos = B.med_pos;
+        alpha = B.alpha;
+    }
     const float dn = dot3(R.d, n_out);
-    const int m2 = dn > 0.f ? B.med_pos : B.med_neg;
+    const int m2 = dn > 0.f ? m_pos : m_neg;
     const float3 n = dn > 0.f ? make_float3(-n_out.x, -n_out.y, -n_out.z) : n_out;
-    if (ROUGH && B.alpha > 0.f) {   // rough boundary: secondary ray first, then the BSDF sample
-        const float a2 = B.alpha * B.alpha;
-        rough_connection<DBG, REC, CVX>(P, S, R, n, m2, a2, cn);
+    if (ROUGH && alpha > 0.f) {   // rough boundary: secondary ray first, then the BSDF sample
+        const float a2 = alpha * alpha;
+        rough_connection<DBG, REC, GEO>(P, S, R, n, m2, a2, cn);
         cn.interactions++;
         uint32_t rb = 0;
         if (!rough_scatter(P, S, R, n, m2, a2, rb)) {
@@ -544,7 +561,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | rb);
         R.b += 1;
         R.prev = R.hit;
-        start_segment<CVX>(P, R, cn);
+        start_segment<GEO>(P, R, cn);
         return;
     }
     const float cos_i = -dot3(n, R.d);
@@ -584,13 +601,14 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | branch);
     R.b += 1;
     R.prev = R.hit;
-    start_segment<CVX>(P, R, cn);
+    start_segment<GEO>(P, R, cn);
 }
 
 // A queued scatterer event: element drawn uniformly (Philox keyed by ray,
 // transmit, segment and scatterer), receive directivity (Eq. 13), connection ray.
-template <bool DBG, bool REC, bool EXT, bool CVX>
+template <bool DBG, bool REC, bool EXT, int GEO>
 __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &Q, int slot, Counters &cn) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
     const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
     const float tca = Q.tca[slot], w = Q.w[slot];
     const ff t = {Q.t_hi[slot], Q.t_lo[slot]};
@@ -617,8 +635,8 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     cn.connections++;
     ff tc;
     float att;
-    const float fac = CVX ? connection_to(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att)
-                                              : connection(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
+    const float fac = CVX ? connection_to<MESH>(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att)
+                          : connection<MESH>(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
     if (fac == 0.f) return;
     const Medium &M = S.med[med];
     const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
@@ -645,7 +663,7 @@ __device__ __forceinline__ uint32_t item_of(const TraceP &P, uint64_t slot) {
 // a time with all lanes busy.  Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
-template <bool DBG, bool SPLIT, bool REC, bool ROUGH, bool CVX>
+template <bool DBG, bool SPLIT, bool REC, bool ROUGH, int GEO>
 __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
@@ -664,7 +682,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
         const unsigned waiting = __ballot_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay);
         const bool resolve = __popc(waiting) >= P.resolve_batch || __ballot_sync(0xffffffffu, R.state == kInSeg) == 0u;
         for (int guard = 0; resolve && guard < 256; ++guard) {
-            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC, ROUGH, CVX>(P, R, cn);
+            if (R.state == kSegDone) finish_segment<DBG, SPLIT, REC, ROUGH, GEO>(P, R, cn);
             unsigned need = __ballot_sync(0xffffffffu, R.state == kNeedRay);
             uint64_t my_slot = ~0ull;
             while (need) {
@@ -700,13 +718,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 if (ROUGH && P.mix_list) {   // a mixed sequence in (drawn transmit, element) order
                     if (local < IT.n_rays) {
                         const uint32_t i = P.mix_list[local];
-                        start_ray<DBG, ROUGH, CVX>(P, R, item, IT, i, i % (uint32_t)P.n_el, cn);
+                        start_ray<DBG, ROUGH, GEO>(P, R, item, IT, i, i % (uint32_t)P.n_el, cn);
                     }
                 } else {
                     const uint32_t m = (uint32_t)(local % IT.rays_per_el);
                     const uint64_t e = local / IT.rays_per_el;
                     const uint32_t i = m * (uint32_t)P.n_el + (uint32_t)e;
-                    if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH, CVX>(P, R, item, IT, i, (uint32_t)e, cn);
+                    if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH, GEO>(P, R, item, IT, i, (uint32_t)e, cn);
                 }
             }
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
@@ -770,7 +788,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
                 qn += __popc(m);
                 if (qn >= 32) {
                     __syncwarp();
-                    process_event<DBG, REC, ROUGH, CVX>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+                    process_event<DBG, REC, ROUGH, GEO>(P, Q, (qhead + lane) & (kQueue - 1), cn);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
@@ -797,7 +815,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
     }
     // (3) drain the queue
     __syncwarp();
-    if (lane < qn) process_event<DBG, REC, ROUGH, CVX>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+    if (lane < qn) process_event<DBG, REC, ROUGH, GEO>(P, Q, (qhead + lane) & (kQueue - 1), cn);
 
     if (P.stats) {
         const uint32_t v[6] = {cn.rays, cn.segments, cn.interactions, cn.candidates, cn.connections, cn.arrivals};
@@ -814,42 +832,48 @@ __global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ Tra
 int trace_occupancy(int block, bool debug) {
     int n = 0;
     if (debug)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, false, false, false, 0>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, false, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, false, false, false, 0>, block, 0);
     return n > 0 ? n : 1;
 }
 
 // Variants with frozen sampling media, with recorded (ray, event) words and the
-// extended variant (rough boundaries, diverging and focused transmits) are
-// compiled separately so the usual kernel carries none of their code.  The
-// extended variant never records or freezes sampling media (the adjoint and
-// ur_scene_set_media refuse such scenes and transmits).
+// extended variants (rough boundaries, transmit kinds other than plane waves,
+// transmit mixing; one per geometry: linear or convex array, with or without
+// triangle meshes) are compiled separately so the usual kernel carries none of
+// their code.  The extended variants never record or freeze sampling media (the
+// adjoint and ur_scene_set_media refuse such scenes and transmits).
+template <int GEO>
+void launch_extended(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
+    debug ? k_trace<true, false, false, true, GEO><<<grid, block, 0, s>>>(P)
+          : k_trace<false, false, false, true, GEO><<<grid, block, 0, s>>>(P);
+}
+
 void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves) {
-    bool split = false, rough = point_waves || P.radius > 0.f;   // convex arrays take the extended tracer too
+    bool split = false, mesh = false, rough = point_waves || P.radius > 0.f;   // convex arrays: extended tracer
     for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) {
         split = split || P.S[q].split_sampling != 0;
+        mesh = mesh || P.S[q].n_tri > 0;
         for (int b = 0; b < P.S[q].n_bnd; ++b) rough = rough || P.S[q].bnd[b].alpha > 0.f;
     }
-    if (rough && P.radius > 0.f) {   // convex arrays: their own extended instantiation
-        debug ? k_trace<true, false, false, true, true><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, false, true, true><<<grid, block, 0, s>>>(P);
-        return;
-    }
-    if (rough) {
-        debug ? k_trace<true, false, false, true, false><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, false, true, false><<<grid, block, 0, s>>>(P);
+    if (rough || mesh) {
+        const int geo = (P.radius > 0.f ? kGeoConvex : 0) | (mesh ? kGeoMesh : 0);
+        if (geo == kGeoConvex) launch_extended<kGeoConvex>(P, debug, block, grid, s);
+        else if (geo == kGeoMesh) launch_extended<kGeoMesh>(P, debug, block, grid, s);
+        else if (geo == (kGeoConvex | kGeoMesh)) launch_extended<kGeoConvex | kGeoMesh>(P, debug, block, grid, s);
+        else launch_extended<0>(P, debug, block, grid, s);
         return;
     }
     if (debug) {
-        split ? k_trace<true, true, false, false, false><<<grid, block, 0, s>>>(P)
-              : k_trace<true, false, false, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<true, true, false, false, 0><<<grid, block, 0, s>>>(P)
+              : k_trace<true, false, false, false, 0><<<grid, block, 0, s>>>(P);
     } else if (P.record) {
-        split ? k_trace<false, true, true, false, false><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, true, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, true, false, 0><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, true, false, 0><<<grid, block, 0, s>>>(P);
     } else {
-        split ? k_trace<false, true, false, false, false><<<grid, block, 0, s>>>(P)
-              : k_trace<false, false, false, false, false><<<grid, block, 0, s>>>(P);
+        split ? k_trace<false, true, false, false, 0><<<grid, block, 0, s>>>(P)
+              : k_trace<false, false, false, false, 0><<<grid, block, 0, s>>>(P);
     }
 }
 
