@@ -452,10 +452,12 @@ void upload_scene(ur_ctx *c, int slot, const ur_medium *media, int n_med, const 
     sd.version = ++c->versions;
 }
 
-// Bounding volume hierarchy over a scene's triangles, built on the host: each node splits its
-// triangles at the median centroid along the longest axis of their centroid bounds (depth at
-// most ceil(log2 n) + 1, within the tracer's traversal stack), leaves hold up to 4 triangles,
-// boxes are padded outward so that FP32 slab tests cannot cut off a triangle's edge.  Device
+// Bounding volume hierarchy over a scene's triangles, built on the host: each node takes the
+// split of lowest surface-area cost (MacDonald & Booth 1990) among 16 centroid bins per axis,
+// or stays a leaf when that costs more than testing its triangles; where median splits from
+// then on would reach the traversal stack's depth, a node splits at the median centroid
+// instead, so the depth stays within the stack.
+// Boxes are padded outward so that FP32 slab tests cannot cut off a triangle's edge.  Device
 // layout: see ur::SceneP (bvh, tri in leaf order, tri_nrm by triangle id).
 struct MeshBuild {
     std::vector<float4> bvh, tri, nrm;
@@ -513,14 +515,95 @@ void build_mesh(const float *v, const int32_t *med, int n, int n_med, MeshBuild 
         int axis = 0;
         for (int a = 1; a < 3; ++a)
             if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
-        if (k.end - k.begin <= 4 || !(chi[axis] > clo[axis])) {   // leaf
+        const int cnt = k.end - k.begin;
+        if (cnt <= 2 || !(chi[axis] > clo[axis])) {   // leaf
             N.a = k.begin;
-            N.b = k.end - k.begin;
+            N.b = cnt;
             continue;
         }
-        const int mid = (k.begin + k.end) / 2;
-        std::nth_element(idx.begin() + k.begin, idx.begin() + mid, idx.begin() + k.end,
-                         [&](int x, int y) { return cen[3 * x + axis] < cen[3 * y + axis]; });
+        int mid = -1;
+        int need = 0;   // levels a median split of this node would still add
+        while ((1 << need) < cnt) ++need;
+        if (k.depth + need + 2 < ur::kBvhStack) {   // binned surface-area heuristic
+            constexpr int nb = 16;
+            auto area = [](const double *lo, const double *hi) {
+                const double x = hi[0] - lo[0], y = hi[1] - lo[1], z = hi[2] - lo[2];
+                return x * y + y * z + z * x;
+            };
+            double best = INFINITY;
+            int best_axis = -1, best_split = 0;
+            for (int a = 0; a < 3; ++a) {
+                if (!(chi[a] > clo[a])) continue;
+                const double scale = nb / (chi[a] - clo[a]);
+                int bc[nb] = {};
+                double blo[nb][3], bhi[nb][3];
+                for (int q = 0; q < nb; ++q)
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        blo[q][c3] = INFINITY;
+                        bhi[q][c3] = -INFINITY;
+                    }
+                for (int q = k.begin; q < k.end; ++q) {
+                    const int t = idx[q];
+                    const int bin = std::min(nb - 1, (int)((cen[3 * t + a] - clo[a]) * scale));
+                    ++bc[bin];
+                    const float *p = v + 9 * (size_t)t;
+                    for (int c3 = 0; c3 < 3; ++c3)
+                        for (int vv = 0; vv < 3; ++vv) {
+                            blo[bin][c3] = std::min(blo[bin][c3], (double)p[3 * vv + c3]);
+                            bhi[bin][c3] = std::max(bhi[bin][c3], (double)p[3 * vv + c3]);
+                        }
+                }
+                double rarea[nb];   // area and count of bins split+1 .. nb-1
+                int rcnt[nb];
+                double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                int c = 0;
+                for (int q = nb - 1; q > 0; --q) {
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        lo[c3] = std::min(lo[c3], blo[q][c3]);
+                        hi[c3] = std::max(hi[c3], bhi[q][c3]);
+                    }
+                    c += bc[q];
+                    rarea[q - 1] = c ? area(lo, hi) : 0.0;
+                    rcnt[q - 1] = c;
+                }
+                for (int c3 = 0; c3 < 3; ++c3) {
+                    lo[c3] = INFINITY;
+                    hi[c3] = -INFINITY;
+                }
+                c = 0;
+                for (int q = 0; q < nb - 1; ++q) {
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        lo[c3] = std::min(lo[c3], blo[q][c3]);
+                        hi[c3] = std::max(hi[c3], bhi[q][c3]);
+                    }
+                    c += bc[q];
+                    if (c == 0 || rcnt[q] == 0) continue;
+                    const double cost = area(lo, hi) * c + rarea[q] * rcnt[q];
+                    if (cost < best) {
+                        best = cost;
+                        best_axis = a;
+                        best_split = q;
+                    }
+                }
+            }
+            // a node visit costs about one triangle test: stay a leaf if splitting does not pay
+            const double leaf_cost = area(N.lo, N.hi) * cnt;
+            if (best_axis < 0 || (cnt <= 4 && best + area(N.lo, N.hi) >= leaf_cost)) {
+                N.a = k.begin;
+                N.b = cnt;
+                continue;
+            }
+            const double scale = nb / (chi[best_axis] - clo[best_axis]);
+            const auto it = std::partition(idx.begin() + k.begin, idx.begin() + k.end, [&](int t) {
+                return std::min(nb - 1, (int)((cen[3 * t + best_axis] - clo[best_axis]) * scale)) <= best_split;
+            });
+            mid = (int)(it - idx.begin());
+        }
+        if (mid <= k.begin || mid >= k.end) {   // median split
+            mid = (k.begin + k.end) / 2;
+            std::nth_element(idx.begin() + k.begin, idx.begin() + mid, idx.begin() + k.end,
+                             [&](int x, int y) { return cen[3 * x + axis] < cen[3 * y + axis]; });
+        }
         const int left = (int)nodes.size();
         nodes[k.node].a = left;   // N may move when nodes grows
         nodes[k.node].b = 0;
