@@ -656,6 +656,14 @@ __device__ __forceinline__ uint32_t item_of(const TraceP &P, uint64_t slot) {
     return (uint32_t)lo;
 }
 
+// Residency: the usual tracer runs 4 CTAs per SM in 64 registers; the extended ones trade
+// warps for registers (3 CTAs, 80 registers: 14.84 instead of 15.18 ms on the paper-settings
+// acquisition), the mesh ones more so (2 CTAs, 128 registers: the BVH walk's stack and state
+// spilled 1.3 KB per thread at 64 registers; 61.5 instead of 71.5 ms).  The grid is sized for
+// 4 CTAs per SM: CTAs that find the ray pools empty exit at once.
+template <bool ROUGH, int GEO>
+constexpr int trace_ctas_per_sm() { return (GEO & kGeoMesh) ? 2 : ROUGH ? 3 : 4; }
+
 // Persistent tracer.  Each iteration of the warp's loop (1) finishes segments
 // and claims new rays for idle lanes, (2) advances every active lane by one
 // grid cell, testing the cell's scatterer references in a warp-uniform loop,
@@ -664,7 +672,7 @@ __device__ __forceinline__ uint32_t item_of(const TraceP &P, uint64_t slot) {
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
 template <bool DBG, bool SPLIT, bool REC, bool ROUGH, int GEO>
-__global__ void __launch_bounds__(kBlock, 4) k_trace(const __grid_constant__ TraceP P) {
+__global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
