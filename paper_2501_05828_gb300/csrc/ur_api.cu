@@ -824,13 +824,16 @@ void launch_trace_kernel(ur_ctx *c, ur::TraceP &P, bool dbg, uint2 *arr_dbg) {
     ck(cudaMemsetAsync(P.arr_count, 0, 8 * sizeof(unsigned long long), c->stream), "memset counters");
     c->phase_begin(UR_PHASE_TRACE);
     if (P.mix_list) ck(ur::launch_mix_plan(c->mix, c->sms, c->stream), "mixed ray order");
-    bool point_waves = P.mix_tx > 0;   // other transmit kinds and mixing take the extended tracer
-    for (const ur::ItemP &it : c->items) point_waves = point_waves || it.kind != UR_TX_PLANE;
+    bool point_waves = P.mix_tx > 0, emit = P.mix_tx > 0;   // other transmit kinds and mixing: extended tracer
+    for (const ur::ItemP &it : c->items) {
+        point_waves = point_waves || it.kind != UR_TX_PLANE;
+        emit = emit || it.kind == UR_TX_SYNTHETIC;
+    }
     bool split = false;
     for (int q = 0; q < P.n_scenes; ++q) split = split || P.S[q].split_sampling != 0;
     if (split && (point_waves || P.radius > 0.f))
         fail(UR_ERR_INVALID_ARG, "frozen sampling media need plane-wave transmits without mixing on a linear array");
-    ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream, point_waves);
+    ur::launch_trace(P, dbg, c->tune.block > 0 ? c->tune.block : 256, trace_grid(c, dbg), c->stream, point_waves, emit);
     ck(cudaGetLastError(), "trace kernel launch");
     c->phase_end(UR_PHASE_TRACE, P.mix_list ? 4 : 1);
 }

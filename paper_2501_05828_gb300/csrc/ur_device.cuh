@@ -21,8 +21,9 @@ constexpr int kMaxCross = 64;      // boundaries a connection ray may cross
 constexpr float kTmin = 1e-7f;     // smallest admissible hit distance (m)
 constexpr int kMaxTri = 1 << 22;   // triangles per scene (hit ids stay below 2^24)
 constexpr int kBvhStack = 32;      // traversal stack; the host's BVH is never deeper
-constexpr int kGeoConvex = 1;      // tracer geometry bits: convex array,
-constexpr int kGeoMesh = 2;        // triangle-mesh boundaries
+constexpr int kGeoConvex = 1;      // tracer instantiation bits: convex array,
+constexpr int kGeoMesh = 2;        // triangle-mesh boundaries,
+constexpr int kGeoEmit = 4;        // synthetic-aperture transmits or transmit mixing
 constexpr uint64_t kFnvOffset = 0xcbf29ce484222325ull;
 constexpr uint64_t kFnvPrime = 0x100000001b3ull;
 
@@ -447,7 +448,8 @@ __device__ __forceinline__ float directivity(const TraceP &P, float cos_a) {
 
 
 // ---------------------------------------------------------------- launchers
-void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves);
+void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves,
+                  bool emit);
 int trace_occupancy(int block, bool debug);   // resident tracer CTAs per SM
 
 // Path-replay adjoint: loss sensitivities in, parameter gradients out.

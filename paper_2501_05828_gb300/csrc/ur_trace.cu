@@ -323,13 +323,13 @@ __device__ __forceinline__ void end_ray(const TraceP &P, Lane &R, int reason, Co
 template <bool DBG, bool EXT, int GEO>
 __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t item, const ItemP &slot_item,
                                           uint32_t i, uint32_t e, Counters &cn) {
-    constexpr bool CVX = (GEO & kGeoConvex) != 0;
-    if (EXT && P.mix_tx > 0) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0, EMIT = EXT && (GEO & kGeoEmit) != 0;
+    if (EMIT && P.mix_tx > 0) {
         const uint4 y = philox(make_uint4(i, 0u, 0u, 1u), P.key);
         item = (uint32_t)(((uint64_t)(y.x >> 8) * (uint64_t)P.mix_tx) >> 24);
     }
-    const ItemP &IT = EXT && P.mix_tx > 0 ? P.items[item] : slot_item;
-    if (EXT && IT.kind == UR_TX_SYNTHETIC) e = (uint32_t)IT.vx;
+    const ItemP &IT = EMIT && P.mix_tx > 0 ? P.items[item] : slot_item;
+    if (EMIT && IT.kind == UR_TX_SYNTHETIC) e = (uint32_t)IT.vx;
     const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
@@ -344,7 +344,7 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
     }
     if (!EXT || IT.kind == UR_TX_PLANE) {
         R.d = make_float3(IT.sin_t, 0.f, IT.cos_t);
-    } else if (IT.kind == UR_TX_SYNTHETIC) {   // uniform angle to the face normal in (-pi/2, pi/2)
+    } else if (EMIT && IT.kind == UR_TX_SYNTHETIC) {   // uniform angle to the face normal in (-pi/2, pi/2)
         const float th = ((float)(int)((x.z >> 8) - (1u << 23)) + 0.5f) * (kPiF * 0x1p-24f);
         float st, ct;
         sincosf(th, &st, &ct);
@@ -658,7 +658,7 @@ __device__ __forceinline__ uint32_t item_of(const TraceP &P, uint64_t slot) {
 
 // Residency: the usual tracer runs 4 CTAs per SM in 64 registers; the extended ones trade
 // warps for registers (3 CTAs, 80 registers: 14.84 instead of 15.18 ms on the paper-settings
-// acquisition), the mesh ones more so (2 CTAs, 128 registers: the BVH walk's stack and state
+// acquisition, 29.6 instead of 32.0 ms on the rough layered frame), the mesh ones more so (2 CTAs, 128 registers: the BVH walk's stack and state
 // spilled 1.3 KB per thread at 64 registers; 61.5 instead of 71.5 ms).  The grid is sized for
 // 4 CTAs per SM: CTAs that find the ray pools empty exit at once.
 template <bool ROUGH, int GEO>
@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 if (my_slot < P.items[item].slot_begin) item = item_of(P, my_slot);
                 const ItemP &IT = P.items[item];
                 const uint64_t local = my_slot - IT.slot_begin;
-                if (ROUGH && P.mix_list) {   // a mixed sequence in (drawn transmit, element) order
+                if (ROUGH && (GEO & kGeoEmit) && P.mix_list) {   // a mixed sequence in (drawn transmit, element) order
                     if (local < IT.n_rays) {
                         const uint32_t i = P.mix_list[local];
                         start_ray<DBG, ROUGH, GEO>(P, R, item, IT, i, i % (uint32_t)P.n_el, cn);
@@ -847,10 +847,12 @@ int trace_occupancy(int block, bool debug) {
 }
 
 // Variants with frozen sampling media, with recorded (ray, event) words and the
-// extended variants (rough boundaries, transmit kinds other than plane waves,
-// transmit mixing; one per geometry: linear or convex array, with or without
-// triangle meshes) are compiled separately so the usual kernel carries none of
-// their code.  The extended variants never record or freeze sampling media (the
+// extended variants (rough boundaries, diverging and focused transmits; one per
+// geometry: linear or convex array, with or without triangle meshes; with or
+// without synthetic-aperture emission and transmit mixing, whose code cost the
+// rough layered frame 6 % and the paper-settings acquisition 9 % when every
+// extended trace carried it) are compiled separately so the usual kernel carries
+// none of their code.  Mesh variants always carry the emission code.  The extended variants never record or freeze sampling media (the
 // adjoint and ur_scene_set_media refuse such scenes and transmits).
 template <int GEO>
 void launch_extended(const TraceP &P, bool debug, int block, int grid, cudaStream_t s) {
@@ -858,19 +860,25 @@ void launch_extended(const TraceP &P, bool debug, int block, int grid, cudaStrea
           : k_trace<false, false, false, true, GEO><<<grid, block, 0, s>>>(P);
 }
 
-void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves) {
+void launch_trace(const TraceP &P, bool debug, int block, int grid, cudaStream_t s, bool point_waves, bool emit) {
     bool split = false, mesh = false, rough = point_waves || P.radius > 0.f;   // convex arrays: extended tracer
     for (int q = 0; q < P.n_scenes && q < kMaxScenes; ++q) {
         split = split || P.S[q].split_sampling != 0;
         mesh = mesh || P.S[q].n_tri > 0;
         for (int b = 0; b < P.S[q].n_bnd; ++b) rough = rough || P.S[q].bnd[b].alpha > 0.f;
     }
-    if (rough || mesh) {
-        const int geo = (P.radius > 0.f ? kGeoConvex : 0) | (mesh ? kGeoMesh : 0);
-        if (geo == kGeoConvex) launch_extended<kGeoConvex>(P, debug, block, grid, s);
-        else if (geo == kGeoMesh) launch_extended<kGeoMesh>(P, debug, block, grid, s);
-        else if (geo == (kGeoConvex | kGeoMesh)) launch_extended<kGeoConvex | kGeoMesh>(P, debug, block, grid, s);
-        else launch_extended<0>(P, debug, block, grid, s);
+    if (rough || mesh || emit) {
+        const int cvx = P.radius > 0.f ? kGeoConvex : 0;
+        if (mesh) {
+            if (cvx) launch_extended<kGeoConvex | kGeoMesh | kGeoEmit>(P, debug, block, grid, s);
+            else launch_extended<kGeoMesh | kGeoEmit>(P, debug, block, grid, s);
+        } else if (emit) {
+            if (cvx) launch_extended<kGeoConvex | kGeoEmit>(P, debug, block, grid, s);
+            else launch_extended<kGeoEmit>(P, debug, block, grid, s);
+        } else {
+            if (cvx) launch_extended<kGeoConvex>(P, debug, block, grid, s);
+            else launch_extended<0>(P, debug, block, grid, s);
+        }
         return;
     }
     if (debug) {
