@@ -49,7 +49,7 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), per primary ray, valid only while the tracer sources
 # hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "a201500c7571b88c", "bytes_per_ray": 13.77, "warp_inst_per_ray": 1039.5, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+TRACE_TRAFFIC = {"src_sha": "f602c735f47ce64e", "bytes_per_ray": 13.65, "warp_inst_per_ray": 1038.8, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
 
 
 def tracer_sha():
