@@ -1075,14 +1075,15 @@ ur_status ur_destroy(ur_ctx *c) {
     }
     cudaStreamSynchronize(c->stream);
     for (SceneData &sd : c->scenes) {
-        DevBuf *bs[] = {&sd.scat, &sd.amp, &sd.refs, &sd.cell_count, &sd.cell_start, &sd.cell_fill, &sd.scan_tmp, &sd.bbox};
+        DevBuf *bs[] = {&sd.scat, &sd.amp, &sd.refs, &sd.cell_count, &sd.cell_start, &sd.cell_fill, &sd.scan_tmp, &sd.bbox,
+                        &sd.bvh, &sd.tri, &sd.tri_nrm};
         for (DevBuf *b : bs) c->release(*b);
     }
     DevBuf *all[] = {&c->delay, &c->tx_sin, &c->tx_cos, &c->tx_m, &c->tx_kind, &c->elem_xz, &c->items_dev, &c->arrivals, &c->arr_dbg, &c->sorted,
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
                      &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
-                     &c->adj_g};
+                     &c->adj_g, &c->mix_list, &c->mix_bins};
     for (DevBuf *b : all) c->release(*b);
     for (int p = 0; p < UR_N_PHASES; ++p) {
         if (c->ev0[p]) cudaEventDestroy(c->ev0[p]);

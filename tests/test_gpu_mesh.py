@@ -149,3 +149,25 @@ def test_meshes_refused_where_unsupported(ur):
     assert rel_l2(rf0.double().cpu().numpy(), rf1.double().cpu().numpy()) <= 1e-6   # atomics' order aside
     sim.close()
     ref.close()
+
+
+def test_contexts_release_mesh_and_mixing_buffers(ur):
+    """Creating, using and destroying contexts with meshes and mixed traces returns the device memory
+    (the hierarchy, the triangles, the mixed ray order)."""
+    import torch
+    w = icosphere_workload(20_000)
+    w["mix"] = True
+
+    def cycle():
+        sim = ur.Simulator(0)
+        sim.load(w)
+        sim.trace(w["n_rays"], 1, 4)
+        sim.close()
+    cycle()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        cycle()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (16 << 20)
