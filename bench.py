@@ -216,10 +216,12 @@ def oracle_rate(w, target_s, threads=None):
     mix = bool(w.get("mix"))  # with transmit mixing the sample is rays 0 .. n * n_tx - 1 of the one sequence
     n_tx = len(np.atleast_1d(w["angles"]))
     per = n_tx if mix else 1
+    n_probe = min(4096, w["n_rays"])
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
-                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, 4096 * per, threads=threads, transmits=tx, mix=mix)
+                    w["z_px"], w["dyn_range_db"], w["max_path"], 0, n_probe * per, threads=threads, transmits=tx,
+                    mix=mix)
     probe = time.perf_counter() - t0
-    n = int(max(1024, min(w["n_rays"], 4096 * target_s / max(probe, 1e-3))))
+    n = int(min(w["n_rays"], max(1024, n_probe * target_s / max(probe, 1e-3))))
     t0 = time.perf_counter()
     oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
                     w["z_px"], w["dyn_range_db"], w["max_path"], 0, n * per, threads=threads, transmits=tx, mix=mix)
