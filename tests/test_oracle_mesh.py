@@ -39,13 +39,14 @@ def canonical_events(ev):
     return ev
 
 
-@pytest.mark.parametrize("roughness", [0.0, 0.4])
-def test_quad_mesh_equals_the_analytic_plane(roughness):
+@pytest.mark.parametrize("roughness,radius", [(0.0, 0.0), (0.4, 0.0), (0.0, 0.04)])
+def test_quad_mesh_equals_the_analytic_plane(roughness, radius):
     """Tiny phantom (plane at 15 mm, sphere, scatterers), steered plane waves, Monte Carlo mode: the
     plane replaced by a quad covering every ray's crossing gives the same arrivals bit for bit
-    (times and amplitudes to rounding), smooth and with the medium below it rough (GGX)."""
+    (times and amplitudes to rounding), smooth, with the medium below it rough (GGX), and under a
+    convex array."""
     w = phantoms.tiny(n_rays=20_000)
-    a = dict(w["array"], alpha_m_deg=10.0, alpha_c_deg=15.0)
+    a = dict(w["array"], alpha_m_deg=10.0, alpha_c_deg=15.0, radius=float(np.float32(radius)))
     ang = np.deg2rad([-8.0, 5.0]).astype(np.float32)
     s = dict(w["scene"])
     med = [list(m) for m in s["media"]]
