@@ -419,27 +419,30 @@ ur_status ur_get_profile(ur_ctx *ctx, ur_profile *out);
 
 /* Allocation-free variant of ur_beamform (the paper has no counterpart).
  *
- * Some callers cannot let a library call cudaMalloc: code that runs while a
- * CUDA stream is being captured into a graph (allocation is not permitted
- * there), real-time acquisition loops that forbid allocation after start-up,
- * and hosts that hand the GPU's memory to their own pool up front.  This entry
- * point computes exactly what ur_beamform computes (same kernels) but allocates
- * nothing: its scratch (transmit tables, pixel coordinates, the envelope
- * maximum and, when env is NULL, the envelope) lives in a fixed device array
- * of UR_NOALLOC_SCRATCH_BYTES (4.5 MiB) that every GPU loading the library
- * holds until the process exits.
+ * Some callers cannot let a library call cudaMalloc: real-time acquisition
+ * loops that forbid allocation after start-up (cudaMalloc can synchronise the
+ * device and stall a frame by milliseconds), hosts that hand all of the GPU's
+ * memory to their own pool up front (a library allocation would fail or
+ * fragment that pool), and plug-ins inside frameworks that own every device
+ * buffer themselves.  This entry point computes exactly what ur_beamform
+ * computes (same kernels) but allocates nothing: its scratch (transmit tables,
+ * pixel coordinates, the envelope maximum and, when env is NULL, the envelope)
+ * lives in a fixed device array of UR_NOALLOC_SCRATCH_BYTES (4.5 MiB) that
+ * every GPU loading the library holds until the process exits.
  *
  * Requirements: the context's array and transmits are set (UR_ERR_STATE
  * otherwise), the transmits are plane waves and the array is linear
- * (UR_ERR_INVALID_ARG otherwise); rf, quad and every non-NULL output are device memory; x_px / z_px
- * may be host or device memory.  Limits: n_tx <= UR_NOALLOC_MAX_TX,
- * nx, nz <= UR_NOALLOC_MAX_AXIS, and nx * nz <= UR_NOALLOC_MAX_PIXELS when env
- * is NULL; larger requests return UR_ERR_INVALID_ARG without launching work.
- * The first call on a device looks up the scratch's device address (once per
- * device), so make that first call before any stream capture.  All calls share
- * the one scratch array, which keeps the last call's contents (the envelope
- * maximum is cleared by each call): calls whose work overlaps on the GPU (for
- * example on two streams) race and must be serialised by the caller.
+ * (UR_ERR_INVALID_ARG otherwise); rf, quad and every non-NULL output are
+ * device memory of the context's GPU (or managed memory; UR_ERR_INVALID_ARG
+ * otherwise); x_px / z_px may be host or device memory.  Limits:
+ * n_tx <= UR_NOALLOC_MAX_TX, nx, nz <= UR_NOALLOC_MAX_AXIS, and
+ * nx * nz <= UR_NOALLOC_MAX_PIXELS when env is NULL; larger requests return
+ * UR_ERR_INVALID_ARG without launching work.  The first call on a device looks
+ * up the scratch's device address (once per device).  All calls share the one
+ * scratch array, which keeps the last call's contents (the envelope maximum is
+ * cleared by each call): calls whose work overlaps on the GPU (for example on
+ * two streams) race and must be serialised by the caller.  A CUDA error left
+ * pending by earlier work is reported as UR_ERR_CUDA and not cleared.
  * Works asynchronously on the context's stream; reports errors through the
  * status only (ur_last_error is not updated). */
 #define UR_NOALLOC_MAX_TX 1024

@@ -2,7 +2,9 @@
 // that may not allocate device memory.  All per-call scratch (transmit tables,
 // pixel coordinates, the envelope maximum and, if the caller passes no envelope
 // buffer, the envelope itself) lives in one file-scope device array that every
-// GPU loading the library holds until the process exits.
+// GPU loading the library holds until the process exits.  The transmit angles
+// travel to the table kernel as a by-value kernel parameter, so no copy reads
+// the context's host memory.
 #include "ultraray.h"
 #include "ur_device.cuh"
 
@@ -16,7 +18,6 @@ constexpr int kMaxDevices = 64;
 struct Scratch {
     unsigned int env_max;
     unsigned int pad[63];
-    float angles[UR_NOALLOC_MAX_TX];
     ur::ff tx_sin[UR_NOALLOC_MAX_TX], tx_cos[UR_NOALLOC_MAX_TX], tx_m[UR_NOALLOC_MAX_TX];
     float px[2 * UR_NOALLOC_MAX_AXIS];
     float env[UR_NOALLOC_MAX_PIXELS];
@@ -50,11 +51,16 @@ __device__ __forceinline__ ur::ff split_dev(double v) {
     return {hi, (float)(v - (double)hi)};
 }
 
+// The transmit angles, passed by value (4 KiB of kernel parameters).
+struct Angles {
+    float a[UR_NOALLOC_MAX_TX];
+};
+
 // Per-transmit tables of the delay-and-sum (sin, cos, min_e x_e sin) in double,
 // split into float-float, like the context's own tables.
-__global__ void k_tables(Scratch *S, int n_tx, int n_el, float pitch) {
+__global__ void k_tables(Scratch *S, const __grid_constant__ Angles ang, int n_tx, int n_el, float pitch) {
     for (int k = threadIdx.x; k < n_tx; k += blockDim.x) {
-        const double th = (double)S->angles[k];
+        const double th = (double)ang.a[k];
         const double sn = sin(th), cs = cos(th);
         const double x0 = -0.5 * (double)(n_el - 1) * (double)pitch;
         double mn = INFINITY;
@@ -65,13 +71,16 @@ __global__ void k_tables(Scratch *S, int n_tx, int n_el, float pitch) {
     }
 }
 
-bool on_device(const void *p) {
+// Device (or managed) memory of `device`: memory of another GPU would be a peer
+// access the kernels are not set up for.
+bool on_device(const void *p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -88,24 +97,29 @@ extern "C" ur_status ur_beamform_noalloc(ur_ctx *ctx, const float *rf, const flo
         return UR_ERR_INVALID_ARG;
     if (!env && (long long)nx * nz > UR_NOALLOC_MAX_PIXELS) return UR_ERR_INVALID_ARG;
     if (db && !(dyn_range_db > 0.f)) return UR_ERR_INVALID_ARG;
-    if (!on_device(rf) || !on_device(quad) || (iq && !on_device(iq)) || (env && !on_device(env)) ||
-        (db && !on_device(db)))
+    const int dev = v.device;
+    if (!on_device(rf, dev) || !on_device(quad, dev) || (iq && !on_device(iq, dev)) ||
+        (env && !on_device(env, dev)) || (db && !on_device(db, dev)))
         return UR_ERR_INVALID_ARG;
-    if (cudaSetDevice(v.device) != cudaSuccess) return UR_ERR_CUDA;
+    if (cudaSetDevice(dev) != cudaSuccess) return UR_ERR_CUDA;
+    // An error left by earlier, unrelated work stays where it is: it is reported, not cleared.
+    if (cudaPeekAtLastError() != cudaSuccess) return UR_ERR_CUDA;
     Scratch *S = nullptr;
     if (scratch_on(v.device, &S) != cudaSuccess) {
         cudaGetLastError();
         return UR_ERR_CUDA;
     }
     cudaStream_t s = (cudaStream_t)v.stream;
-    if (cudaMemcpyAsync(S->angles, v.angles, sizeof(float) * v.n_tx, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(S->px, x_px, sizeof(float) * nx, cudaMemcpyDefault, s) != cudaSuccess ||
+    Angles ang;
+    for (int k = 0; k < v.n_tx; ++k) ang.a[k] = v.angles[k];
+    if (cudaMemcpyAsync(S->px, x_px, sizeof(float) * nx, cudaMemcpyDefault, s) != cudaSuccess ||
         cudaMemcpyAsync(S->px + nx, z_px, sizeof(float) * nz, cudaMemcpyDefault, s) != cudaSuccess ||
         cudaMemsetAsync(&S->env_max, 0, sizeof(unsigned int), s) != cudaSuccess) {
         cudaGetLastError();
         return UR_ERR_CUDA;
     }
-    k_tables<<<1, 256, 0, s>>>(S, v.n_tx, v.arr.n_el, v.arr.pitch);
+    k_tables<<<1, 256, 0, s>>>(S, ang, v.n_tx, v.arr.n_el, v.arr.pitch);
+    if (cudaGetLastError() != cudaSuccess) return UR_ERR_CUDA;
     ur::ImageP I{};
     I.rf = rf;
     I.quad = quad;
@@ -130,6 +144,10 @@ extern "C" ur_status ur_beamform_noalloc(ur_ctx *ctx, const float *rf, const flo
     I.env_max = &S->env_max;
     I.dyn_range_db = dyn_range_db;
     ur::launch_das(I, s);
-    if (db) ur::launch_log(I, s);
-    return cudaGetLastError() == cudaSuccess ? UR_OK : UR_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return UR_ERR_CUDA;
+    if (db) {
+        ur::launch_log(I, s);
+        if (cudaGetLastError() != cudaSuccess) return UR_ERR_CUDA;
+    }
+    return UR_OK;
 }

@@ -1,6 +1,7 @@
 """ur_beamform_noalloc: the allocation-free beamforming entry point for callers
-that cannot let the library call cudaMalloc (inside stream capture, in
-real-time loops, under a fixed memory pool).  Its output must equal
+that cannot let the library call cudaMalloc (real-time loops that forbid
+allocation after start-up, hosts that give all device memory to their own pool,
+plug-ins inside frameworks that own every device buffer).  Its output must equal
 ur_beamform's on the same channel data, call after call, and a repeated call
 must not change the device's free memory.  Collected last on purpose."""
 import numpy as np
@@ -77,3 +78,41 @@ def test_noalloc_rejects_oversized_requests(setup):
     assert e.value.code == 1
     with pytest.raises(ur.URError):                               # host outputs are refused
         sim.beamform_noalloc(rf, quad, w["x_px"], w["z_px"], 60.0, db=torch.empty(env_ref.shape))
+
+
+def _cplx(t):
+    a = t.double().cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def test_noalloc_single_outputs(setup):
+    """Only the complex image, then only the envelope: each equals ur_beamform's."""
+    torch, ur, w, sim, rf, quad, iq_ref, env_ref, db_ref = setup
+    nz, nx = env_ref.shape
+    for call in range(2):
+        iq = torch.full((nz, nx, 2), float("nan"), device=rf.device)
+        sim.beamform_noalloc(rf, quad, w["x_px"], w["z_px"], 60.0, iq=iq)
+        env = torch.full((nz, nx), float("nan"), device=rf.device)
+        sim.beamform_noalloc(rf, quad, w["x_px"], w["z_px"], 60.0, env=env)
+        torch.cuda.synchronize()
+        assert rel_l2(_cplx(iq), _cplx(iq_ref)) <= 1e-5
+        assert rel_l2(env.double().cpu().numpy(), env_ref.double().cpu().numpy()) <= 1e-5
+
+
+def test_noalloc_follows_changed_transmits(setup):
+    """The per-transmit tables are rebuilt by every call: after new plane-wave angles the
+    output equals ur_beamform's for the new angles, and after restoring them, for the old."""
+    torch, ur, w, sim, rf, quad, iq_ref, env_ref, db_ref = setup
+    nz, nx = env_ref.shape
+    new = np.deg2rad(np.array([-11.0, 2.0, 9.0])).astype(np.float32)
+    try:
+        for angles in (new, w["angles"]):
+            sim.set_plane_waves(angles)
+            ref, _, _ = sim.beamform(rf, quad, w["x_px"], w["z_px"], 60.0, env=False, db=False)
+            iq = torch.full((nz, nx, 2), float("nan"), device=rf.device)
+            sim.beamform_noalloc(rf, quad, w["x_px"], w["z_px"], 60.0, iq=iq)
+            torch.cuda.synchronize()
+            assert rel_l2(_cplx(iq), _cplx(ref)) <= 1e-5
+        assert rel_l2(_cplx(iq), _cplx(iq_ref)) <= 1e-5
+    finally:
+        sim.set_plane_waves(w["angles"])
