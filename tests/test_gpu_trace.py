@@ -127,14 +127,53 @@ def test_layered_full_size_sampled(ur):
     assert rel_l2(rf.double().cpu().numpy(), drf) <= 1e-5
     assert rel_l2(quad.double().cpu().numpy(), dq) <= 1e-5
     assert rel_l2(rf_plain.double().cpu().numpy(), rf.double().cpu().numpy()) <= 1e-6
-    # sampled rays, traced independently by the oracle
-    for b0, b1 in ((0, 3000), (N // 2, N // 2 + 2000), (N - 3000, N)):
+    # sampled rays (3 x 20k), traced independently by the oracle: >= 99.99 % identical paths
+    bad, n_paths = 0, 0
+    for b0, b1 in ((0, 20_000), (N // 2, N // 2 + 20_000), (N - 20_000, N)):
         arr, topo, _ = run_oracle(w, ray_begin=b0, ray_end=b1)
         sel = g[(g["ray"] >= b0) & (g["ray"] < b1)]
         res = compare(sel, arr, hashes[:, b0:b1], topo, ray_begin=b0)
-        assert res["frac_paths"] >= 0.999, res["frac_paths"]      # 1 mismatch in 1000-3000 rays allowed
         assert res["max_dt"] <= DT_MAX and res["el_mismatch"] == 0
         assert res["max_amp_rel"] <= AMP_REL
+        bad += len(res["bad_rays"])
+        n_paths += b1 - b0
+    assert 1.0 - bad / n_paths >= PATH_FRAC, (bad, n_paths)
+
+
+def matched_channel_data(w, G, arr, bad):
+    """Channel data of both sides over the paths they agree on: the GPU's minus the deposit of
+    its records of mismatched rays, the oracle's without those rays."""
+    n_tx = len(w["angles"])
+    if not bad:
+        orf, oq = oracle.deposit(w["array"], n_tx, arr)
+        return G["rf"], G["quad"], orf, oq
+    mask = np.array([(int(t), int(r)) in bad for t, r in zip(G["rec"]["tx"], G["rec"]["ray"])], bool)
+    gb_rf, gb_q = oracle.deposit(w["array"], n_tx, G["rec"][mask])
+    om_rf, om_q = oracle.deposit(w["array"], n_tx, drop_rays(arr, bad))
+    return G["rf"] - gb_rf, G["quad"] - gb_q, om_rf, om_q
+
+
+def image_parity(ur, w, G, arr, topo, x=None, z=None, amp_floor=0.0):
+    """Channel data and image (complex DAS, envelope, dB) over matched paths; the GPU image is
+    the GPU beamformer applied to the GPU's matched channel data."""
+    import torch
+    x = w["x_px"] if x is None else x
+    z = w["z_px"] if z is None else z
+    res = compare(G["rec"], arr, G["hash"], topo, amp_floor=amp_floor)
+    assert res["frac_paths"] >= PATH_FRAC, (res["frac_paths"], len(res["bad_rays"]))
+    g_rf, g_q, o_rf, o_q = matched_channel_data(w, G, arr, res["bad_rays"])
+    assert rel_l2(g_rf, o_rf) <= REL_L2 and rel_l2(g_q, o_q) <= REL_L2
+    iq, env, db = G["sim"].beamform(torch.from_numpy(g_rf.astype(np.float32)).cuda(),
+                                    torch.from_numpy(g_q.astype(np.float32)).cuda(), x, z, w["dyn_range_db"])
+    oiq = oracle.beamform(w["array"], w["angles"], o_rf, o_q, x, z)
+    oenv, odb = oracle.envelope_log(oiq, w["dyn_range_db"])
+    giq = iq.double().cpu().numpy()
+    e_iq = rel_l2(giq[..., 0] + 1j * giq[..., 1], oiq)
+    e_env = rel_l2(env.double().cpu().numpy(), oenv)
+    assert e_iq <= REL_L2 and e_env <= REL_L2, (e_iq, e_env)
+    strong = oenv > 1e-2 * oenv.max()
+    assert np.abs(db.double().cpu().numpy() - odb)[strong].max() <= 1e-2
+    return res, e_iq, e_env
 
 
 def test_beamform_parity(ur):
@@ -177,18 +216,34 @@ def test_beamform_compounding_parity(ur):
 
 
 def test_end_to_end_image_parity(ur):
-    """Whole chain on the tiny phantom: GPU image vs oracle image."""
+    """Whole chain on the tiny phantom: channel data, complex image and envelope within 1e-4
+    relative L2 of the oracle's over matched paths (unconditionally: mismatched rays, if any,
+    are removed from both sides)."""
     w = phantoms.tiny()
     G = run_gpu(ur, w)
-    _, env, db = G["sim"].beamform(
-        __import__("torch").from_numpy(G["rf"].astype(np.float32)).cuda(),
-        __import__("torch").from_numpy(G["quad"].astype(np.float32)).cuda(), w["x_px"], w["z_px"], 60.0)
     arr, topo, _ = run_oracle(w)
-    O = oracle.simulate(w["scene"], w["array"], w["angles"], w["n_rays"], w["seed"], w["max_bounces"], w["x_px"],
-                        w["z_px"], 60.0)
-    res = compare(G["rec"], arr, G["hash"], topo)
-    if not res["bad_rays"]:
-        assert rel_l2(env.double().cpu().numpy(), O["env"]) <= REL_L2
+    image_parity(ur, w, G, arr, topo)
+
+
+def test_layered_1e6_rays_end_to_end(ur):
+    """The layered phantom (50k scatterers, 8 bounces) at 1e6 rays: path topology, channel data,
+    complex 512 x 256 image and envelope against the oracle's full trace of the same rays.
+
+    Per-arrival amplitudes below 1e-4 of the largest are compared against that floor: a connection
+    ray that crosses the bone cylinder within a few milliradians of its critical angle carries a
+    transmission factor sqrt(1 - R) near zero (arrivals of 1e-13 where typical ones are 1e-7), and
+    FP32 fixes cos_t = sqrt(1 - eta^2 sin^2) there only to about 2^-24 / cos_t^2 relative (cos_i
+    itself comes from FP32 unit vectors), so such arrivals reach 1e-3 relative error while their
+    share of the channel data stays far below the 1e-4 bar."""
+    w = phantoms.layered(n_rays=1_000_000)
+    G = run_gpu(ur, w, capacity=600_000)
+    arr, topo, _ = run_oracle(w)
+    res, e_iq, e_env = image_parity(ur, w, G, arr, topo, amp_floor=1e-4)
+    print("1e6 layered: paths %.6f, matched %d, max dt %.2e, max amp %.2e %s, image %.2e / %.2e"
+          % (res["frac_paths"], res["n_matched"], res["max_dt"], res["max_amp_rel"], res["worst_amp"], e_iq, e_env))
+    assert res["max_dt"] <= DT_MAX and res["el_mismatch"] == 0
+    assert res["max_amp_rel"] <= AMP_REL, (res["max_amp_rel"], res["worst_amp"])
+    assert res["n_matched"] >= 0.999 * len(arr)
 
 
 @pytest.mark.parametrize("case", ["empty_scene", "few_rays", "ragged", "no_bounce", "short_window", "one_element",
