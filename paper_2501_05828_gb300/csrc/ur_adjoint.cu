@@ -117,10 +117,11 @@ __device__ float connection_tan(const AdjP &A, const SceneP &S, float3 p, int me
         float r, ct;
         const Medium &M2 = S.med[m2];
         if (!fresnel(ci, M.c, M.Z, M2.c, M2.Z, r, ct)) return 0.f;
-        fac *= sqrtf(1.f - r * r);
+        const float Tr = transmitted(ci, ct, M.Z, M2.Z);   // 1 - r^2
+        fac *= sqrtf(Tr);
         const float eta = M2.c / M.c;
         const RDeriv D = r_partials(ci, ct, eta, M.Z, M2.Z);
-        const float coef = -r / (1.f - r * r);          // d log sqrt(1 - r^2) / dr
+        const float coef = -r / Tr;                        // d log sqrt(1 - r^2) / dr
         const float r_eta = D.r_ct * D.ct_eta;
         lwc[3 * m + 0] += coef * r_eta * (-M2.c / (M.c * M.c));
         lwc[3 * m2 + 0] += coef * r_eta * (1.f / M.c);
@@ -348,13 +349,12 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
         }
         const float3 dr = unit3(V.d + (2.f * ci) * n);
         const Medium &M2 = S.med[m2];
-        float r, ct, Rs;
+        float r, ct, Rs, rs, cts = 0.f;
         bool tir;
         if (!S.split_sampling) {
             tir = !fresnel(ci, M.c, M.Z, M2.c, M2.Z, r, ct);
             Rs = r * r;
         } else {   // frozen sampling media decide the branch and its probability
-            float rs, cts;
             tir = !fresnel(ci, S.cs[V.med], S.Zs[V.med], S.cs[m2], S.Zs[m2], rs, cts) ||
                   !fresnel(ci, M.c, M.Z, M2.c, M2.Z, r, ct);
             Rs = rs * rs;
@@ -376,7 +376,8 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
             const uint4 y = philox(make_uint4(i, IT.stream, 1u | ((uint32_t)V.b << 8), 0u), P.key);
             // d log(branch factor) / dr: 1/r on reflection, -r/(1 - r^2) on transmission
             const bool refl = u24(y.x) < Rs;
-            const float coef = refl ? 1.f / r : -r / (1.f - r * r);
+            const float Tr = refl ? 0.f : transmitted(ci, ct, M.Z, M2.Z);   // 1 - r^2
+            const float coef = refl ? 1.f / r : -r / Tr;
 #pragma unroll
             for (int m = 0; m < kAM; ++m) T.lw[3 * m] += coef * drc[m];
             if (V.med < kAM) T.lw[3 * V.med + 1] += coef * D.r_Z1;
@@ -387,7 +388,7 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
                 for (int m = 0; m < kAM; ++m) T.dD[m] = T.dD[m] + (2.f * dci[m]) * n + (2.f * ci) * dn[m];
                 V.d = dr;
             } else {
-                V.w *= sqrtf(1.f - r * r) / (1.f - Rs);
+                V.w *= S.split_sampling ? sqrtf(Tr) / transmitted(ci, cts, S.Zs[V.med], S.Zs[m2]) : 1.f / sqrtf(Tr);
 #pragma unroll
                 for (int m = 0; m < kAM; ++m)
                     T.dD[m] = deta[m] * V.d + eta * T.dD[m] + (deta[m] * ci + eta * dci[m] - dct[m]) * n +

@@ -55,13 +55,15 @@ constexpr uint32_t kChunkMin = 512;    // fewest (work items are sized for sever
 
 // One uploaded scene: host copies of media and boundaries, device scatterers and grid.
 // Default scatterer-grid cell sizes (x, y, z) in units of the capture radius
-// r_s.  Plane waves of a linear array travel in the xz plane, and planes z = c
-// and cylinders along y keep them there (their normals have no y component), so
-// in such scenes thin y cells hold few scatterers at almost no extra cell
-// steps; a sphere tilts rays out of the plane, and cubic-ish cells serve better.
-constexpr float kCellSlab[3] = {8.f, 0.3f, 60.f};
+// r_s.  The tracer walks columns in x and y; z cells only index each column's
+// references by depth (a visit reads the z cells within r_s of the depths it
+// spans).  Plane waves of a linear array travel in the xz plane, and planes
+// z = c and cylinders along y keep them there (their normals have no y
+// component), so in such scenes thin y columns hold few scatterers and cost no
+// steps; a sphere tilts rays out of the plane, and square columns serve better.
+constexpr float kCellSlab[3] = {6.f, 0.3f, 4.f};
 constexpr int kResolveBatch = 20;   // default: lanes that must wait before a tracer warp resolves segments
-constexpr float kCellIso[3] = {3.f, 3.f, 40.f};
+constexpr float kCellIso[3] = {3.f, 3.f, 5.f};
 
 struct SceneData {
     bool ok = false;
@@ -73,6 +75,7 @@ struct SceneData {
     float z_max = 0.f;
     int n_scat = 0;
     float r_s = 1e-4f;
+    float g_rm = 0.f;
     float3 g_lo{}, g_h{}, g_inv_h{};
     int3 g_dim{};
     DevBuf scat, amp, refs, cell_count, cell_start, cell_fill, scan_tmp, bbox;
@@ -356,6 +359,7 @@ void build_grid(ur_ctx *c, SceneData &sd, const float *src) {
         h_y *= 1.5f;
         h_z *= 1.5f;
     }
+    sd.g_rm = r_m;
     sd.g_lo = make_float3(lo[0] - r_m, lo[1] - r_m, lo[2] - r_m);
     sd.g_h = make_float3(h_x, h_y, h_z);
     sd.g_inv_h = make_float3(1.f / h_x, 1.f / h_y, 1.f / h_z);
@@ -675,6 +679,7 @@ void fill_scene(const ur_ctx *c, const SceneData &sd, ur::SceneP &S) {
     for (int m = 0; m < S.n_med; ++m) S.rough[m] = sd.media[m].roughness;
     S.n_scat = sd.n_scat;
     S.r2 = sd.r_s * sd.r_s;
+    S.g_rm = sd.g_rm;
     S.g_lo = sd.g_lo;
     S.g_h = sd.g_h;
     S.g_inv_h = sd.g_inv_h;
@@ -1711,9 +1716,9 @@ ur_status ur_autotune(ur_ctx *c, int scene, uint64_t n_rays, uint64_t seed, int 
         if (cur.blocks_per_sm <= 0) cur.blocks_per_sm = ur::trace_occupancy(256, false);
         float t_cur = measure(cur);
         // coordinate descent over the knobs
-        const float z_mult[] = {20.f, 40.f, 60.f, 80.f, 120.f};
-        const float xy_mult[] = {2.f, 3.f, 4.f, 6.f, 8.f, 10.f};
-        const float y_mult[] = {0.3f, 0.5f, 1.f, 2.f, 3.f, 4.f};
+        const float z_mult[] = {2.f, 3.f, 5.f, 8.f, 12.f};
+        const float xy_mult[] = {1.f, 1.5f, 2.f, 3.f, 4.f, 6.f};
+        const float y_mult[] = {0.2f, 0.3f, 0.5f, 1.f, 2.f, 3.f};
         const int batches[] = {8, 12, 16, 20, 24};
         for (int pass = 0; pass < 2; ++pass) {
             for (float m : z_mult) {

@@ -142,9 +142,12 @@ struct SceneP {
     // scatterer grid
     int n_scat;
     float r2;               // capture radius squared
+    float g_rm;             // grid margin: r_s plus slack above FP32 rounding
     float3 g_lo, g_inv_h, g_h;
     int3 g_dim;
-    const float4 *refs;     // (x, y, z, bits(index)) per cell reference; cells (x, y, z) with z fastest
+    const float4 *refs;     // (x, y, z, bits(index)) per cell reference; cells (x, y, z) with z fastest;
+                            // a scatterer is referenced from the columns within g_rm of it in x and y,
+                            // in its own z cell only
     const uint32_t *cell_start;
     const float *amp;
     const float4 *scat;     // (x, y, z, amplitude) by scatterer index
@@ -436,6 +439,14 @@ __device__ __forceinline__ bool fresnel(float cos_i, float c1, float Z1, float c
     cos_t = sqrtf(k);
     r = (Z2 * cos_i - Z1 * cos_t) / (Z2 * cos_i + Z1 * cos_t);
     return true;
+}
+
+// Transmitted intensity fraction 1 - r^2 of the fluid-fluid interface, written as
+// 4 Z1 Z2 cos_i cos_t / (Z2 cos_i + Z1 cos_t)^2, without the cancellation of
+// 1 - r^2 near the critical angle.
+__device__ __forceinline__ float transmitted(float cos_i, float cos_t, float Z1, float Z2) {
+    const float s = fmaf(Z2, cos_i, Z1 * cos_t);
+    return 4.f * Z1 * Z2 * cos_i * cos_t / (s * s);
 }
 
 // Eq. 13 through cosines: 1 inside the main beam, 0 beyond the cutoff, linear in angle between.

@@ -1,8 +1,11 @@
-// Uniform grid over the point scatterers, cells numbered with z fastest so that
-// a near-vertical ray walks consecutive cells and consecutive references.  Each scatterer is referenced by every
-// cell its capture box [p - r_m, p + r_m] overlaps (r_m slightly above r_s), so a
-// ray segment only has to visit the cells it passes through.  Built on the
-// device: bounding box, per-cell counts, exclusive scan, fill.
+// Scatterer grid: columns in x and y, each indexed by z cells, cells numbered
+// with z fastest.  A scatterer is referenced by every column its capture square
+// [p - r_m, p + r_m] (r_m slightly above r_s) overlaps in x and y, but only in
+// the z cell that holds it, so the references of one column are grouped by z
+// and a range of z cells is one contiguous range of references.  A ray segment
+// visits the columns it passes and, in each, the references whose z lies within
+// r_m of the z it spans there.  Built on the device: bounding box, per-cell
+// counts, exclusive scan, fill.
 #include "ur_device.cuh"
 
 namespace ur {
@@ -32,23 +35,22 @@ __global__ void k_bbox(const float4 *scat, int n, unsigned int *lohi) {
     }
 }
 
+// Columns (x, y) whose cells a scatterer at p is referenced from, and its z cell.
 __device__ __forceinline__ void cell_range(const GridBuildP &G, float4 p, int3 &c0, int3 &c1) {
     c0.x = min(max((int)floorf((p.x - G.r_m - G.lo.x) * G.inv_h.x), 0), G.dim.x - 1);
     c0.y = min(max((int)floorf((p.y - G.r_m - G.lo.y) * G.inv_h.y), 0), G.dim.y - 1);
-    c0.z = min(max((int)floorf((p.z - G.r_m - G.lo.z) * G.inv_h.z), 0), G.dim.z - 1);
     c1.x = min(max((int)floorf((p.x + G.r_m - G.lo.x) * G.inv_h.x), 0), G.dim.x - 1);
     c1.y = min(max((int)floorf((p.y + G.r_m - G.lo.y) * G.inv_h.y), 0), G.dim.y - 1);
-    c1.z = min(max((int)floorf((p.z + G.r_m - G.lo.z) * G.inv_h.z), 0), G.dim.z - 1);
+    c0.z = c1.z = min(max((int)floorf((p.z - G.lo.z) * G.inv_h.z), 0), G.dim.z - 1);
 }
 
 __global__ void k_grid_count(const GridBuildP G) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < G.n_scat; j += gridDim.x * blockDim.x) {
         int3 c0, c1;
         cell_range(G, G.scat[j], c0, c1);
-        for (int z = c0.z; z <= c1.z; ++z)
-            for (int y = c0.y; y <= c1.y; ++y)
-                for (int x = c0.x; x <= c1.x; ++x)
-                    atomicAdd(&G.cell_count[((uint32_t)x * G.dim.y + y) * G.dim.z + z], 1u);
+        for (int y = c0.y; y <= c1.y; ++y)
+            for (int x = c0.x; x <= c1.x; ++x)
+                atomicAdd(&G.cell_count[((uint32_t)x * G.dim.y + y) * G.dim.z + c0.z], 1u);
     }
 }
 
@@ -58,13 +60,12 @@ __global__ void k_grid_fill(const GridBuildP G) {
         G.amp[j] = p.w;
         int3 c0, c1;
         cell_range(G, p, c0, c1);
-        for (int z = c0.z; z <= c1.z; ++z)
-            for (int y = c0.y; y <= c1.y; ++y)
-                for (int x = c0.x; x <= c1.x; ++x) {
-                    const uint32_t c = ((uint32_t)x * G.dim.y + y) * G.dim.z + z;
-                    const uint32_t slot = atomicAdd(&G.cell_fill[c], 1u);
-                    G.refs[G.cell_start[c] + slot] = make_float4(p.x, p.y, p.z, __uint_as_float((uint32_t)j));
-                }
+        for (int y = c0.y; y <= c1.y; ++y)
+            for (int x = c0.x; x <= c1.x; ++x) {
+                const uint32_t c = ((uint32_t)x * G.dim.y + y) * G.dim.z + c0.z;
+                const uint32_t slot = atomicAdd(&G.cell_fill[c], 1u);
+                G.refs[G.cell_start[c] + slot] = make_float4(p.x, p.y, p.z, __uint_as_float((uint32_t)j));
+            }
     }
 }
 

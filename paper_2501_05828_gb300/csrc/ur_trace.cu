@@ -40,7 +40,7 @@ __device__ float connection(const SceneP &S, float3 p, int med, int skip0, float
         const int m2 = dn > 0.f ? m_pos : m_neg;
         float r, ct;
         if (!fresnel(fabsf(dn), M.c, M.Z, S.med[m2].c, S.med[m2].Z, r, ct)) return 0.f;
-        fac *= sqrtf(1.f - r * r);
+        fac *= sqrtf(transmitted(fabsf(dn), ct, M.Z, S.med[m2].Z));
         m = m2;
         o = h;
         rem -= th;
@@ -83,13 +83,6 @@ __device__ __forceinline__ float3 ggx_sample(float3 n, float a2, float xi1, floa
     const float3 t1 = make_float3(1.f + sg * n.x * n.x * a, sg * b, -sg * n.x);
     const float3 t2 = make_float3(b, sg + n.y * n.y * a, -n.y);
     return (st * cp) * t1 + (st * sp) * t2 + ct * n;
-}
-
-// Transmitted intensity fraction 1 - r^2 of the fluid-fluid interface, written
-// without the cancellation of 1 - r^2 near the critical angle.
-__device__ __forceinline__ float transmitted(float cos_i, float cos_t, float Z1, float Z2) {
-    const float s = fmaf(Z2, cos_i, Z1 * cos_t);
-    return 4.f * Z1 * Z2 * cos_i * cos_t / (s * s);
 }
 
 // Scattering of a rough boundary from incident direction d (n: unit macro normal
@@ -163,7 +156,7 @@ __device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, fl
         const int m2 = dn > 0.f ? m_pos : m_neg;
         float r, ct;
         if (!fresnel(fabsf(dn), M.c, M.Z, S.med[m2].c, S.med[m2].Z, r, ct)) return 0.f;
-        fac *= sqrtf(1.f - r * r);
+        fac *= sqrtf(transmitted(fabsf(dn), ct, M.Z, S.med[m2].Z));
         m = m2;
         o = h;
         rem -= th;
@@ -225,7 +218,20 @@ struct WarpQueue {
     float tca[kQueue], t_hi[kQueue], t_lo[kQueue], w[kQueue];
 };
 
-// Per-lane state: the primary ray, its current segment and the grid walk over it.
+// One lane's current column visit, staged in shared memory so that any lane of
+// the warp can test one of its references: the ray (o, d), the accepted range
+// [lo, hi) of the closest-approach distance, the address its references start
+// from (offset by the visit's first index in the warp-wide numbering), the
+// capture radius squared, and what a scatterer event copies into the ring.
+struct Visit {
+    float4 a;           // o, lo
+    float4 b;           // d, hi
+    uint4 ev;           // ray, item | medium | bounces, t_hi, t_lo
+    float w, r2;
+    unsigned long long refs;
+};
+
+// Per-lane state: the primary ray, its current segment and the column walk over it.
 struct Lane {
     float3 o, d;
     ff t;
@@ -236,8 +242,8 @@ struct Lane {
     float seg;
     int hit;
     bool clipped;
-    int cx, cy, cz, sx, sy, sz;
-    float tmx, tmy, tmz, tdx, tdy, tdz, t_enter, t_end;
+    int cx, cy, sx, sy;
+    float tmx, tmy, tdx, tdy, t_enter, t_end;
     int state;
     // rough boundaries: the path left a rough vertex mp with direction density mpdf and has
     // crossed only by transmission since (its aperture hit takes a balance-heuristic weight)
@@ -249,7 +255,11 @@ struct Lane {
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
 // Segment from the current position to the nearest boundary (clipped by the
-// path-length budget); set up the grid walk over the part inside the grid box.
+// path-length budget); set up the column walk over the part inside the grid box.
+// The walk steps in x and y only: a column visit covers the segment's stretch
+// through the column, and its references are those within g_rm of the z that
+// stretch spans.  The first visit accepts closest approaches from g_rm before the
+// grid box on (none can lie there; the margin only keeps rounding out of play).
 template <int GEO>
 __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
     constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
@@ -295,17 +305,13 @@ __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters
     if (!(t0 < t1)) return;
     R.cx = min(max((int)floorf((o.x + t0 * d.x - S.g_lo.x) * S.g_inv_h.x), 0), S.g_dim.x - 1);
     R.cy = min(max((int)floorf((o.y + t0 * d.y - S.g_lo.y) * S.g_inv_h.y), 0), S.g_dim.y - 1);
-    R.cz = min(max((int)floorf((o.z + t0 * d.z - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
     R.sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
     R.sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
-    R.sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
     R.tdx = R.sx ? S.g_h.x * fabsf(ix) : INFINITY;
     R.tdy = R.sy ? S.g_h.y * fabsf(iy) : INFINITY;
-    R.tdz = R.sz ? S.g_h.z * fabsf(iz) : INFINITY;
     R.tmx = R.sx ? (S.g_lo.x + (float)(R.cx + (R.sx > 0)) * S.g_h.x - o.x) * ix : INFINITY;
     R.tmy = R.sy ? (S.g_lo.y + (float)(R.cy + (R.sy > 0)) * S.g_h.y - o.y) * iy : INFINITY;
-    R.tmz = R.sz ? (S.g_lo.z + (float)(R.cz + (R.sz > 0)) * S.g_h.z - o.z) * iz : INFINITY;
-    R.t_enter = -INFINITY;
+    R.t_enter = t0 - S.g_rm;
     R.t_end = t1;
     R.state = kInSeg;
 }
@@ -567,14 +573,13 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     const float cos_i = -dot3(n, R.d);
     const float3 dr = unit3(R.d + (2.f * cos_i) * n);
     const Medium &M2 = S.med[m2];
-    float r, cos_t, Rs;
+    float r, cos_t, Rs, rs, cts = 0.f;
     bool tir;
     uint32_t branch;
     if (!SPLIT) {   // the media decide their own branches
         tir = !fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t);
         Rs = r * r;
     } else {        // frozen sampling media decide the branch and its probability
-        float rs, cts;
         tir = !fresnel(cos_i, S.cs[R.med], S.Zs[R.med], S.cs[m2], S.Zs[m2], rs, cts) ||
               !fresnel(cos_i, M.c, M.Z, M2.c, M2.Z, r, cos_t);
         Rs = rs * rs;
@@ -591,7 +596,9 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         } else {
             branch = 1;
             const float eta = M2.c / M.c;
-            R.w *= SPLIT ? sqrtf(1.f - r * r) / (1.f - Rs) : 1.f / sqrtf(1.f - Rs);
+            // 1 - R as 4 Z1 Z2 cos_i cos_t / (Z2 cos_i + Z1 cos_t)^2: no cancellation near the critical angle
+            const float T = transmitted(cos_i, cos_t, M.Z, M2.Z);
+            R.w *= SPLIT ? sqrtf(T) / transmitted(cos_i, cts, S.Zs[R.med], S.Zs[m2]) : 1.f / sqrtf(T);
             R.d = unit3(eta * R.d + (eta * cos_i - cos_t) * n);
             R.med = m2;
         }
@@ -665,16 +672,18 @@ template <bool ROUGH, int GEO>
 constexpr int trace_ctas_per_sm() { return (GEO & kGeoMesh) ? 2 : ROUGH ? 3 : 4; }
 
 // Persistent tracer.  Each iteration of the warp's loop (1) finishes segments
-// and claims new rays for idle lanes, (2) advances every active lane by one
-// grid cell, testing the cell's scatterer references in a warp-uniform loop,
-// (3) hands scatterer events to a per-warp queue that is drained 32 events at
-// a time with all lanes busy.  Ray slots are element-major: a freshly claimed
+// and claims new rays for idle lanes, (2) moves every active lane through one
+// grid column, the references of all lanes' visits tested 32 at a time across
+// the warp, (3) hands scatterer events to a per-warp queue that is drained 32
+// events at a time with all lanes busy.  Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
 template <bool DBG, bool SPLIT, bool REC, bool ROUGH, int GEO>
 __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
+    __shared__ Visit s_vis[kWarps][32];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
+    Visit *vis = s_vis[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint64_t n_slots = P.n_slots;
     Counters cn = {0, 0, 0, 0, 0, 0};
@@ -739,58 +748,83 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
         }
         if (__all_sync(0xffffffffu, R.state == kFinished)) break;
 
-        // (2) one grid cell per active lane
+        // (2) one column visit per active lane; the references of all visits are numbered
+        // across the warp (prefix sum of their counts) and tested 32 at a time
         const bool active = R.state == kInSeg;
-        const SceneP &S = P.S[active ? R.scene : 0];
-        uint32_t r0 = 0, cnt = 0;
+        uint32_t cnt = 0;
         int axis = 0;
-        float t_exit = 0.f, t_acc = 0.f;
+        float t_exit = 0.f;
         bool last = false;
         if (active) {
-            axis = (R.tmx <= R.tmy && R.tmx <= R.tmz) ? 0 : (R.tmy <= R.tmz ? 1 : 2);
-            t_exit = axis == 0 ? R.tmx : (axis == 1 ? R.tmy : R.tmz);
+            const SceneP &S = P.S[R.scene];
+            axis = R.tmx <= R.tmy ? 0 : 1;
+            t_exit = axis == 0 ? R.tmx : R.tmy;
             last = !(t_exit < R.t_end);
             if (!last) {
-                const int nc = axis == 0 ? R.cx + R.sx : (axis == 1 ? R.cy + R.sy : R.cz + R.sz);
-                const int dm = axis == 0 ? S.g_dim.x : (axis == 1 ? S.g_dim.y : S.g_dim.z);
-                last = nc < 0 || nc >= dm;
+                const int nc = axis == 0 ? R.cx + R.sx : R.cy + R.sy;
+                last = nc < 0 || nc >= (axis == 0 ? S.g_dim.x : S.g_dim.y);
             }
-            t_acc = last ? INFINITY : t_exit;
-            const uint32_t cell =
-                ((uint32_t)R.cx * (uint32_t)S.g_dim.y + (uint32_t)R.cy) * (uint32_t)S.g_dim.z + (uint32_t)R.cz;
-            r0 = S.cell_start[cell];
-            cnt = S.cell_start[cell + 1] - r0;
+            const float t_out = last ? R.t_end : t_exit;
+            const float za = fmaf(R.t_enter, R.d.z, R.o.z), zb = fmaf(t_out, R.d.z, R.o.z);
+            const int cza = min(max((int)floorf((fminf(za, zb) - S.g_rm - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
+            const int czb = min(max((int)floorf((fmaxf(za, zb) + S.g_rm - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
+            const uint32_t col = ((uint32_t)R.cx * (uint32_t)S.g_dim.y + (uint32_t)R.cy) * (uint32_t)S.g_dim.z;
+            const uint32_t rb = S.cell_start[col + (uint32_t)cza];
+            cnt = S.cell_start[col + (uint32_t)czb + 1u] - rb;
+            Visit &V = vis[lane];
+            V.a = make_float4(R.o.x, R.o.y, R.o.z, R.t_enter);
+            V.b = make_float4(R.d.x, R.d.y, R.d.z, last ? R.seg : t_exit);
+            V.ev = make_uint4(R.i, (R.item << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b, __float_as_uint(R.t.hi),
+                              __float_as_uint(R.t.lo));
+            V.w = R.w;
+            V.r2 = S.r2;
+            V.refs = (unsigned long long)(uintptr_t)(S.refs + rb);
         }
-        const uint32_t maxc = __reduce_max_sync(0xffffffffu, cnt);
-        const uint32_t kmb = (R.item << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b;
-        float4 q_next = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (cnt > 0) q_next = S.refs[r0];
-        for (uint32_t r = 0; r < maxc; ++r) {
+        uint32_t incl = cnt;   // inclusive prefix sum of the visits' reference counts
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (cnt) vis[lane].refs -= (unsigned long long)(incl - cnt) * sizeof(float4);
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t k = base + (uint32_t)lane;
+            int owner = 0;   // the lane whose visit holds reference k: the first with incl > k
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t v = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+                if (v <= k) owner += step;
+            }
             bool cand = false;
             float tca = 0.f;
             uint32_t j = 0;
-            const float4 q = q_next;                 // reference r, loaded one step ahead
-            if (r + 1 < cnt) q_next = S.refs[r0 + r + 1];
-            if (r < cnt) {
-                const float3 v = make_float3(q.x - R.o.x, q.y - R.o.y, q.z - R.o.z);
-                tca = dot3(v, R.d);
-                if (tca > 0.f && tca < R.seg && tca >= R.t_enter && tca < t_acc) {
-                    const float3 pe = v - tca * R.d;
-                    cand = dot3(pe, pe) < S.r2;
+            if (k < total) {
+                const Visit &V = vis[owner];
+                const float4 A = V.a, B = V.b;
+                const float4 q = reinterpret_cast<const float4 *>((uintptr_t)V.refs)[k];
+                const float3 v = make_float3(q.x - A.x, q.y - A.y, q.z - A.z);
+                tca = v.x * B.x + v.y * B.y + v.z * B.z;
+                if (tca > 0.f && tca >= A.w && tca < B.w) {
+                    const float3 pe = make_float3(v.x - tca * B.x, v.y - tca * B.y, v.z - tca * B.z);
+                    cand = dot3(pe, pe) < V.r2;
                     j = __float_as_uint(q.w);
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, cand);
             if (m) {
                 if (cand) {
+                    const Visit &V = vis[owner];
+                    const uint4 ev = V.ev;
                     const int slot = (qhead + qn + __popc(m & lanemask_lt())) & (kQueue - 1);
-                    Q.ray[slot] = R.i;
-                    Q.kmb[slot] = kmb;
+                    Q.ray[slot] = ev.x;
+                    Q.kmb[slot] = ev.y;
                     Q.j[slot] = j;
                     Q.tca[slot] = tca;
-                    Q.t_hi[slot] = R.t.hi;
-                    Q.t_lo[slot] = R.t.lo;
-                    Q.w[slot] = R.w;
+                    Q.t_hi[slot] = __uint_as_float(ev.z);
+                    Q.t_lo[slot] = __uint_as_float(ev.w);
+                    Q.w[slot] = V.w;
                     cn.candidates++;
                 }
                 qn += __popc(m);
@@ -803,6 +837,7 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 }
             }
         }
+        __syncwarp();   // the visits are restaged by the next iteration
         if (active) {
             if (last) {
                 R.state = kSegDone;
@@ -811,12 +846,9 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 if (axis == 0) {
                     R.cx += R.sx;
                     R.tmx += R.tdx;
-                } else if (axis == 1) {
+                } else {
                     R.cy += R.sy;
                     R.tmy += R.tdy;
-                } else {
-                    R.cz += R.sz;
-                    R.tmz += R.tdz;
                 }
             }
         }
