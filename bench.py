@@ -34,22 +34,37 @@ UNIT = "rays/s"
 WORKLOAD = ("layered phantom: 128 el, pitch 0.3 mm, f0 5 MHz, fs 40 MHz, 0-deg plane wave, skin/fat/muscle + "
             "bone cylinder r=6 mm, 50k scatterers, 1e7 rays/frame, 8 bounces, 3200 samples, DAS 512x256, 60 dB")
 
-# Algorithmic FP32 operations per unit of work counted by the tracer's counters
-# (formula arithmetic of one step of the method, independent of the search
-# structure): per primary segment (extend against the scene's primitives,
-# advance, attenuation, interaction), per scatterer event (closest-approach
-# tube test, element draw, directivity), per connection ray (crossings with
-# transmission factors, time and amplitude), per deposited pulse tap.
-FLOPS_PER_SEGMENT = 120
-FLOPS_PER_CANDIDATE = 30
-FLOPS_PER_CONNECTION = 200
-FLOPS_PER_TAP = 30
+# Algorithmic floating-point operations per unit of work the tracer counts, taken
+# from the FP64 oracle's own steps on the layered phantom (2 planes, 1 cylinder,
+# 2 terminal planes): every add, subtract, multiply, divide and square root is 1,
+# every exp / sin / cos / acos is 1, comparisons and integer work (Philox, element
+# indices) are 0.  Independent of the GPU's search structure (no reference tests,
+# no grid steps).
+#   segment:      nearest boundary (2 planes x 2, cylinder 21, terminal 2) + advance
+#                 (time 2, attenuation 3, path length 1, position 6, clip 1)      = 40
+#   interaction:  medium side 5 + Eqs. 7-11 (cos_i 5, orientation 5, reflected
+#                 direction 7 + normalise 9, eta 1, k 5, sqrt 1, transmitted 11 +
+#                 normalise 9, r 7, R 1) + branch weight and uniform 6             = 72
+#   scatterer event: tube test (v 3, t_ca 5, offset 6, |offset|^2 5) + element
+#                 centre 2, direction 3, distance 6, angle 7, directivity 1      = 38
+#   connection:   direction 12 + per boundary crossed 105 (nearest 25, time 2,
+#                 attenuation 2, point 6, side 5, Eqs. 7-11 61, sqrt(1-R) 3,
+#                 remaining 1) x 1.8 crossings (skin/fat and fat/muscle planes
+#                 above a scatterer uniform in depth) + last leg 29 + arrival
+#                 time 3 and amplitude 10                                         = 243
+#   pulse tap (Eq. 14): tau 1, Gaussian 3, phase 1, sin 1, cos 1, amp g 1,
+#                 rf 2, quad 2                                                    = 12
+FLOPS_PER_SEGMENT = 40
+FLOPS_PER_INTERACTION = 72
+FLOPS_PER_CANDIDATE = 38
+FLOPS_PER_CONNECTION = 243
+FLOPS_PER_TAP = 12
 FP32_LANES_PER_SM = 128
 
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), per primary ray, valid only while the tracer sources
-# hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "f602c735f47ce64e", "bytes_per_ray": 13.65, "warp_inst_per_ray": 1038.8, "profile": "profiles/k_trace_layered_1e6rays_full.md"}
+# dram__bytes_write.sum), per primary ray, and its warp instructions per ray; valid
+# only while the tracer sources hash to `src_sha`.
+TRACE_TRAFFIC = {"src_sha": "f602c735f47ce64e", "bytes_per_ray": 13.65, "warp_inst_per_ray": 1038.8}
 
 
 def tracer_sha():
@@ -69,14 +84,13 @@ def taps_per_arrival(arr):
     return 2 * int(arr["tcut_sigmas"] * s) + 1
 
 
-def algorithmic_flops(stats, arr):
-    return (stats["segments"] * FLOPS_PER_SEGMENT + stats["candidates"] * FLOPS_PER_CANDIDATE
-            + stats["connections"] * FLOPS_PER_CONNECTION + stats["arrivals"] * taps_per_arrival(arr) * FLOPS_PER_TAP)
-
-
 def trace_flops(stats):
-    return (stats["segments"] * FLOPS_PER_SEGMENT + stats["candidates"] * FLOPS_PER_CANDIDATE
-            + stats["connections"] * FLOPS_PER_CONNECTION)
+    return (stats["segments"] * FLOPS_PER_SEGMENT + stats["interactions"] * FLOPS_PER_INTERACTION
+            + stats["candidates"] * FLOPS_PER_CANDIDATE + stats["connections"] * FLOPS_PER_CONNECTION)
+
+
+def algorithmic_flops(stats, arr):
+    return trace_flops(stats) + stats["arrivals"] * taps_per_arrival(arr) * FLOPS_PER_TAP
 
 
 def issue_slots(rays, t_launch, n_sm, sm_mhz):
