@@ -612,10 +612,13 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
 }
 
 // A queued scatterer event: element drawn uniformly (Philox keyed by ray,
-// transmit, segment and scatterer), receive directivity (Eq. 13), connection ray.
-template <bool DBG, bool REC, bool EXT, int GEO>
-__device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &Q, int slot, Counters &cn) {
-    constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
+// transmit, segment and scatterer) and the receive directivity (Eq. 13).  An
+// event the element receives goes on to the warp's connection ring with its
+// arrival time and amplitude so far (the connection ray's part follows there).
+template <bool EXT, int GEO>
+__device__ __forceinline__ bool event_element(const TraceP &P, const WarpQueue &Q, int slot, uint32_t &e, ff &t_pre,
+                                              float &amp_pre) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0;
     const uint32_t ray = Q.ray[slot], kmb = Q.kmb[slot], j = Q.j[slot];
     const float tca = Q.tca[slot], w = Q.w[slot];
     const ff t = {Q.t_hi[slot], Q.t_lo[slot]};
@@ -625,32 +628,90 @@ __device__ __forceinline__ void process_event(const TraceP &P, const WarpQueue &
     const SceneP &S = P.S[IT.scene];
     const float4 q = S.scat[j];
     const uint4 x = philox(make_uint4(ray, IT.stream, 2u | ((uint32_t)b << 8), j), P.key);
-    const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
-    const float xe = P.x_first + (float)e * P.pitch;
-    float3 ce, ne;
+    e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     float fd;
     if (CVX) {   // convex array: directivity to the element's normal
+        float3 ce, ne;
         elem_frame<CVX>(P, e, ce, ne);
         const float3 v = make_float3(q.x - ce.x, q.y - ce.y, q.z - ce.z);
         fd = directivity(P, dot3(v, ne) / sqrtf(dot3(v, v)));
     } else {
-        const float vx = xe - q.x;
+        const float vx = P.x_first + (float)e * P.pitch - q.x;
         const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
         fd = directivity(P, q.z / D);
     }
-    if (!(fd > 0.f)) return;
+    if (!(fd > 0.f)) return false;
+    const Medium &M = S.med[med];
+    t_pre = ff_add(t, ff_mul_f(tca, M.slow));
+    amp_pre = w * expf(-M.a * tca) * q.w * (float)P.n_el * fd;
+    return true;
+}
+
+// Scatterer events waiting for their connection ray to the drawn element, one ring per warp (SoA).
+struct ConnQueue {
+    uint32_t ray[kQueue], kmb[kQueue], j[kQueue], e[kQueue];
+    float t_hi[kQueue], t_lo[kQueue], amp[kQueue];
+};
+
+// A queued connection: the straight ray from the scatterer to the element centre,
+// its transmission factors, time and attenuation; the arrival goes to the queue.
+template <bool DBG, bool REC, bool EXT, int GEO>
+__device__ __forceinline__ void process_connection(const TraceP &P, const ConnQueue &C, int slot, Counters &cn) {
+    constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
+    const uint32_t ray = C.ray[slot], kmb = C.kmb[slot], j = C.j[slot], e = C.e[slot];
+    const uint32_t item = kmb >> 16;
+    const int med = (int)((kmb >> 8) & 0xffu), b = (int)(kmb & 0xffu);
+    const ItemP &IT = P.items[item];
+    const SceneP &S = P.S[IT.scene];
+    const float4 q = S.scat[j];
     cn.connections++;
     ff tc;
-    float att;
-    const float fac = CVX ? connection_to<MESH>(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att)
-                          : connection<MESH>(S, make_float3(q.x, q.y, q.z), med, -1, xe, tc, att);
+    float att, fac;
+    if (CVX) {
+        float3 ce, ne;
+        elem_frame<CVX>(P, e, ce, ne);
+        fac = connection_to<MESH>(S, make_float3(q.x, q.y, q.z), med, -1, ce, tc, att);
+    } else {
+        fac = connection<MESH>(S, make_float3(q.x, q.y, q.z), med, -1, P.x_first + (float)e * P.pitch, tc, att);
+    }
     if (fac == 0.f) return;
-    const Medium &M = S.med[med];
-    const ff ta = ff_add(ff_add(t, ff_mul_f(tca, M.slow)), tc);
+    const ff ta = ff_add({C.t_hi[slot], C.t_lo[slot]}, tc);
     if (ff_gt(ta, P.t_last)) return;
-    const float amp = w * expf(-M.a * tca) * q.w * (float)P.n_el * fd * fac * expf(-att);
+    const float amp = C.amp[slot] * fac * expf(-att);
     emit<DBG, REC>(P, item * (uint32_t)P.n_el + e, ta, amp, ray, ((uint32_t)b << 24) | j);
     cn.arrivals++;
+}
+
+// Events [qhead + lane] for the lanes below n: element draw and directivity; the ones the
+// element receives join the connection ring, which is traced 32 at a time with all lanes.
+template <bool DBG, bool REC, bool EXT, int GEO>
+__device__ __forceinline__ void drain_events(const TraceP &P, const WarpQueue &Q, ConnQueue &CQ, int qhead, int n,
+                                             int &chead, int &cn_q, Counters &cn) {
+    const int lane = threadIdx.x & 31;
+    uint32_t e = 0;
+    ff t_pre = {0.f, 0.f};
+    float amp_pre = 0.f;
+    const int slot = (qhead + lane) & (kQueue - 1);
+    const bool go = lane < n && event_element<EXT, GEO>(P, Q, slot, e, t_pre, amp_pre);
+    const unsigned m = __ballot_sync(0xffffffffu, go);
+    if (go) {
+        const int c = (chead + cn_q + __popc(m & ((1u << lane) - 1u))) & (kQueue - 1);
+        CQ.ray[c] = Q.ray[slot];
+        CQ.kmb[c] = Q.kmb[slot];
+        CQ.j[c] = Q.j[slot];
+        CQ.e[c] = e;
+        CQ.t_hi[c] = t_pre.hi;
+        CQ.t_lo[c] = t_pre.lo;
+        CQ.amp[c] = amp_pre;
+    }
+    cn_q += __popc(m);
+    if (cn_q >= 32) {
+        __syncwarp();
+        process_connection<DBG, REC, EXT, GEO>(P, CQ, (chead + lane) & (kQueue - 1), cn);
+        __syncwarp();
+        chead = (chead + 32) & (kQueue - 1);
+        cn_q -= 32;
+    }
 }
 
 // The item whose slot range holds `slot` (item slot ranges are pool-aligned and ascending).
@@ -675,14 +736,18 @@ constexpr int trace_ctas_per_sm() { return (GEO & kGeoMesh) ? 2 : ROUGH ? 3 : 4;
 // and claims new rays for idle lanes, (2) moves every active lane through one
 // grid column, the references of all lanes' visits tested 32 at a time across
 // the warp, (3) hands scatterer events to a per-warp queue that is drained 32
-// events at a time with all lanes busy.  Ray slots are element-major: a freshly claimed
+// events at a time with all lanes busy; the events the drawn element receives
+// wait in a second ring for their connection rays, traced 32 at a time as well.
+// Ray slots are element-major: a freshly claimed
 // batch of lanes traces neighbouring rays of one element; slot -> ray
 // i = m * n_el + e.
 template <bool DBG, bool SPLIT, bool REC, bool ROUGH, int GEO>
 __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
+    __shared__ ConnQueue s_c[kWarps];
     __shared__ Visit s_vis[kWarps][32];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
+    ConnQueue &CQ = s_c[threadIdx.x >> 5];
     Visit *vis = s_vis[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint64_t n_slots = P.n_slots;
@@ -692,7 +757,8 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
     uint64_t pool_next = 0;
     uint32_t pool_cnt = 0, pool_item = 0;
     bool pool_dry = false;
-    int qhead = 0, qn = 0;   // warp-uniform ring bookkeeping
+    int qhead = 0, qn = 0;     // warp-uniform ring bookkeeping: scatterer events
+    int chead = 0, cqn = 0;    // and connections
 
     for (;;) {
         // (1) resolve finished segments and idle lanes, once enough lanes wait
@@ -830,7 +896,7 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 qn += __popc(m);
                 if (qn >= 32) {
                     __syncwarp();
-                    process_event<DBG, REC, ROUGH, GEO>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+                    drain_events<DBG, REC, ROUGH, GEO>(P, Q, CQ, qhead, 32, chead, cqn, cn);
                     __syncwarp();
                     qhead = (qhead + 32) & (kQueue - 1);
                     qn -= 32;
@@ -853,9 +919,11 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
             }
         }
     }
-    // (3) drain the queue
+    // (3) drain the queues
     __syncwarp();
-    if (lane < qn) process_event<DBG, REC, ROUGH, GEO>(P, Q, (qhead + lane) & (kQueue - 1), cn);
+    drain_events<DBG, REC, ROUGH, GEO>(P, Q, CQ, qhead, qn, chead, cqn, cn);
+    __syncwarp();
+    if (lane < cqn) process_connection<DBG, REC, ROUGH, GEO>(P, CQ, (chead + lane) & (kQueue - 1), cn);
 
     if (P.stats) {
         const uint32_t v[6] = {cn.rays, cn.segments, cn.interactions, cn.candidates, cn.connections, cn.arrivals};
