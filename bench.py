@@ -64,7 +64,7 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), per primary ray, and its warp instructions per ray; valid
 # only while the tracer sources hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "f602c735f47ce64e", "bytes_per_ray": 13.65, "warp_inst_per_ray": 1038.8}
+TRACE_TRAFFIC = {"src_sha": "c8ffb2a6d5702fb3", "bytes_per_ray": 14.03, "warp_inst_per_ray": 538.4}
 
 
 def tracer_sha():
@@ -103,15 +103,22 @@ def issue_slots(rays, t_launch, n_sm, sm_mhz):
             "peak_note": "%d SMs x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % (n_sm, sm_mhz)}
 
 
+# Shared-memory float atomics: ncu counts two data-stage wavefronts per 32-lane ATOMS
+# (l1tex__data_pipe_lsu_wavefronts_mem_shared_op_atom / smsp__inst_executed_op_shared_atom = 2.00
+# on k_bin_deposit), so the unit completes at most 16 lane atomics per SM per clock.
+SHARED_ATOMIC_LANES_PER_CLOCK = 16
+
+
 def binning_roofline(st, arr, phase_ms, alu_peak, peaks, n_sm, sm_mhz):
     """Binning of one frame: the deposit kernel against the FP32 ALU peak (FLOPS_PER_TAP per
-    pulse tap), its shared-memory atomics against one 32-lane atomic per SM per clock, and the
-    counting sort's algorithmic bytes (arrival read by count and scatter, sorted write) against HBM."""
+    pulse tap), its shared-memory atomics against the atomic unit's 16 lanes per SM per clock,
+    and the counting sort's algorithmic bytes (arrival read by count and scatter, sorted write)
+    against HBM."""
     taps = st["arrivals"] * taps_per_arrival(arr)
     t_dep = phase_ms.get("deposit", float("nan")) * 1e-3
     t_sort = phase_ms.get("sort", float("nan")) * 1e-3
     ach = taps * FLOPS_PER_TAP / t_dep / 1e12
-    atom_peak = n_sm * 32 * sm_mhz * 1e6
+    atom_peak = n_sm * SHARED_ATOMIC_LANES_PER_CLOCK * sm_mhz * 1e6
     sort_bytes = st["arrivals"] * 48
     hbm = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "alu", "kernel": "k_bin_deposit", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
@@ -119,8 +126,8 @@ def binning_roofline(st, arr, phase_ms, alu_peak, peaks, n_sm, sm_mhz):
             "deposit_ms_per_launch": t_dep * 1e3,
             "shared_atomics": {"achieved_per_s": 2 * taps / t_dep, "peak_per_s": atom_peak,
                                "frac": 2 * taps / t_dep / atom_peak,
-                               "peak_note": "%d SMs x 32 lanes x %.0f MHz (one warp-wide shared atomic per clock)"
-                                            % (n_sm, sm_mhz)},
+                               "peak_note": "%d SMs x %d lane atomics x %.0f MHz (two data-stage wavefronts per "
+                                            "32-lane float atomic, ncu)" % (n_sm, SHARED_ATOMIC_LANES_PER_CLOCK, sm_mhz)},
             "sort": {"bound": "hbm", "kernels": "k_bin_count + k_bin_plan + k_bin_scatter",
                      "algorithmic_bytes": sort_bytes, "achieved": sort_bytes / t_sort / 1e9, "peak": hbm,
                      "unit": "GB/s", "frac": sort_bytes / t_sort / 1e9 / hbm, "ms": t_sort * 1e3,
