@@ -7,8 +7,10 @@ cos(theta) / N (Eq. 6, N = rays per transmit), both are unbiased estimates of
 the same expected channel data and differ only in Monte Carlo noise, so the
 network learns E[channel data] from a noisy sample.  Evaluation compares, on
 held-out scenes and against a much higher-ray reference, (a) the noisy input,
-(b) the denoised input and (c) the plain tracer given the same wall time as
-trace + network; (c) is also the fallback when no trained network exists.
+(b) the denoised input, (c) the plain tracer given the same wall time as
+trace + network and (d) the rays and wall time the plain tracer needs to reach
+the denoised error; the plain tracer is also the fallback when no trained
+network exists.
 
 Everything here is orchestration: tracing runs in ur_trace, the network in
 ur_nn_*; errors for reporting are computed on the host in float64.
@@ -110,7 +112,8 @@ def _timed(torch, fn, reps=3):
 def evaluate(sim, net, scene_fn, scene_seeds, n_in, n_ref, max_bounces=8, ray_seed_offset=0):
     """Held-out comparison per scene: errors of the noisy input, the denoised
     input and the plain tracer at equal wall time, all against an n_ref-ray
-    reference.  Returns a list of dicts."""
+    reference, and the rays and time the plain tracer needs for the denoised
+    error.  Returns a list of dicts."""
     torch = sim._torch
     rows = []
     for s in scene_seeds:
@@ -126,9 +129,21 @@ def evaluate(sim, net, scene_fn, scene_seeds, n_in, n_ref, max_bounces=8, ray_se
             _, t_eq = _timed(torch, lambda: sim.trace(n_eq, seed_in + 1, max_bounces), reps=1)
             n_eq = max(int(n_in), int(n_eq * (t_trace + t_nn) / t_eq))
         (er, eq), t_eq = _timed(torch, lambda: sim.trace(n_eq, seed_in + 1, max_bounces))
-        rows.append({"seed": int(s), "err_input": rel_err(xr, xq, rr, rq), "err_denoised": rel_err(yr, yq, rr, rq),
+        err_den = rel_err(yr, yq, rr, rq)
+        # plain tracer at equal error: Monte Carlo error falls as n^-1/2, so n is rescaled by
+        # (err(n) / err_denoised)^2 until the traced error is within 2 % of the denoised one
+        n_ee, err_ee = int(n_in), rel_err(xr, xq, rr, rq)
+        for _ in range(8):
+            if abs(err_ee / err_den - 1.0) <= 0.02:
+                break
+            n_ee = int(min(max(n_ee * (err_ee / err_den) ** 2, 1e4), 0.5 * n_ref))
+            r_ee, q_ee = sim.trace(n_ee, seed_in + 2, max_bounces)
+            err_ee = rel_err(r_ee, q_ee, rr, rq)
+        _, t_ee = _timed(torch, lambda: sim.trace(n_ee, seed_in + 2, max_bounces))
+        rows.append({"seed": int(s), "err_input": rel_err(xr, xq, rr, rq), "err_denoised": err_den,
                      "err_equal_time": rel_err(er, eq, rr, rq), "n_equal_time": n_eq,
-                     "t_trace_s": t_trace, "t_net_s": t_nn, "t_equal_time_s": t_eq})
+                     "t_trace_s": t_trace, "t_net_s": t_nn, "t_equal_time_s": t_eq,
+                     "n_equal_error": n_ee, "err_equal_error": err_ee, "t_equal_error_s": t_ee})
     return rows
 
 
@@ -153,16 +168,21 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="JSON report path")
     a = ap.parse_args(argv)
     sim = Simulator(0)
+    print("tracing %d pairs (%.0e / %.0e rays)" % (a.pairs, a.n_in, a.n_tgt), flush=True)
     xr, xq, tr, tq, gen_s = make_pairs(sim, phantoms.batched_variant, range(1, a.pairs + 1), a.n_in, a.n_tgt)
+    print("pairs traced in %.1f s" % gen_s, flush=True)
     net = Denoiser(0, max_batch=a.batch, n_el=int(xr.shape[1]), n_s=int(xr.shape[2]), width=32, seed=1)
     net.set_scale(channel_scale(tr, tq))
     t0 = time.perf_counter()
     hist = train(net, xr, xq, tr, tq, a.epochs, a.batch, a.lr, log=lambda m: print(m, flush=True))
     train_s = time.perf_counter() - t0
     rows = evaluate(sim, net, phantoms.batched_variant, range(2001, 2001 + a.eval), a.n_in, a.n_ref)
-    keys = ("err_input", "err_denoised", "err_equal_time")
+    keys = ("err_input", "err_denoised", "err_equal_time", "err_equal_error", "n_equal_error", "t_equal_error_s",
+            "t_trace_s", "t_net_s")
     rep = {"args": vars(a), "generation_s": gen_s, "training_s": train_s, "loss": hist, "eval": rows,
            "mean": {k: float(np.mean([r[k] for r in rows])) for k in keys}}
+    for r in rows:
+        print(json.dumps(r), flush=True)
     print(json.dumps(rep["mean"]))
     if a.out:
         with open(a.out, "w") as f:
