@@ -218,19 +218,6 @@ struct WarpQueue {
     float tca[kQueue], t_hi[kQueue], t_lo[kQueue], w[kQueue];
 };
 
-// One lane's current column visit, staged in shared memory so that any lane of
-// the warp can test one of its references: the ray (o, d), the accepted range
-// [lo, hi) of the closest-approach distance, the address its references start
-// from (offset by the visit's first index in the warp-wide numbering), the
-// capture radius squared, and what a scatterer event copies into the ring.
-struct Visit {
-    float4 a;           // o, lo
-    float4 b;           // d, hi
-    uint4 ev;           // ray, item | medium | bounces, t_hi, t_lo
-    float w, r2;
-    unsigned long long refs;
-};
-
 // Per-lane state: the primary ray, its current segment and the column walk over it.
 struct Lane {
     float3 o, d;
@@ -745,10 +732,8 @@ template <bool DBG, bool SPLIT, bool REC, bool ROUGH, int GEO>
 __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_trace(const __grid_constant__ TraceP P) {
     __shared__ WarpQueue s_q[kWarps];
     __shared__ ConnQueue s_c[kWarps];
-    __shared__ Visit s_vis[kWarps][32];
     WarpQueue &Q = s_q[threadIdx.x >> 5];
     ConnQueue &CQ = s_c[threadIdx.x >> 5];
-    Visit *vis = s_vis[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint64_t n_slots = P.n_slots;
     Counters cn = {0, 0, 0, 0, 0, 0};
@@ -815,9 +800,14 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
         if (__all_sync(0xffffffffu, R.state == kFinished)) break;
 
         // (2) one column visit per active lane; the references of all visits are numbered
-        // across the warp (prefix sum of their counts) and tested 32 at a time
+        // across the warp (prefix sum of their counts) and tested 32 at a time, each lane
+        // reading the visiting ray of its reference from the owner lane's registers by
+        // shuffles (staging the visits in shared memory instead cost L1 capacity: the
+        // kernel's register spills and scatterer references live there)
         const bool active = R.state == kInSeg;
         uint32_t cnt = 0;
+        float v_hi = 0.f, v_r2 = 0.f;
+        unsigned long long v_refs = 0ull;
         int axis = 0;
         float t_exit = 0.f;
         bool last = false;
@@ -837,14 +827,9 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
             const uint32_t col = ((uint32_t)R.cx * (uint32_t)S.g_dim.y + (uint32_t)R.cy) * (uint32_t)S.g_dim.z;
             const uint32_t rb = S.cell_start[col + (uint32_t)cza];
             cnt = S.cell_start[col + (uint32_t)czb + 1u] - rb;
-            Visit &V = vis[lane];
-            V.a = make_float4(R.o.x, R.o.y, R.o.z, R.t_enter);
-            V.b = make_float4(R.d.x, R.d.y, R.d.z, last ? R.seg : t_exit);
-            V.ev = make_uint4(R.i, (R.item << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b, __float_as_uint(R.t.hi),
-                              __float_as_uint(R.t.lo));
-            V.w = R.w;
-            V.r2 = S.r2;
-            V.refs = (unsigned long long)(uintptr_t)(S.refs + rb);
+            v_hi = last ? R.seg : t_exit;
+            v_refs = (unsigned long long)(uintptr_t)(S.refs + rb);
+            v_r2 = S.r2;
         }
         uint32_t incl = cnt;   // inclusive prefix sum of the visits' reference counts
 #pragma unroll
@@ -853,8 +838,8 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
             if (lane >= off) incl += y;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        if (cnt) vis[lane].refs -= (unsigned long long)(incl - cnt) * sizeof(float4);
-        __syncwarp();
+        v_refs -= (unsigned long long)(incl - cnt) * sizeof(float4);
+        const uint32_t v_kmb = (R.item << 16) | ((uint32_t)R.med << 8) | (uint32_t)R.b;
         for (uint32_t base = 0; base < total; base += 32) {
             const uint32_t k = base + (uint32_t)lane;
             int owner = 0;   // the lane whose visit holds reference k: the first with incl > k
@@ -866,31 +851,36 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
             bool cand = false;
             float tca = 0.f;
             uint32_t j = 0;
+            const float4 A = make_float4(__shfl_sync(0xffffffffu, R.o.x, owner), __shfl_sync(0xffffffffu, R.o.y, owner),
+                                         __shfl_sync(0xffffffffu, R.o.z, owner), __shfl_sync(0xffffffffu, R.t_enter, owner));
+            const float4 B = make_float4(__shfl_sync(0xffffffffu, R.d.x, owner), __shfl_sync(0xffffffffu, R.d.y, owner),
+                                         __shfl_sync(0xffffffffu, R.d.z, owner), __shfl_sync(0xffffffffu, v_hi, owner));
+            const unsigned long long rp = __shfl_sync(0xffffffffu, v_refs, owner);
+            const float r2 = __shfl_sync(0xffffffffu, v_r2, owner);
             if (k < total) {
-                const Visit &V = vis[owner];
-                const float4 A = V.a, B = V.b;
-                const float4 q = reinterpret_cast<const float4 *>((uintptr_t)V.refs)[k];
+                const float4 q = reinterpret_cast<const float4 *>((uintptr_t)rp)[k];
                 const float3 v = make_float3(q.x - A.x, q.y - A.y, q.z - A.z);
                 tca = v.x * B.x + v.y * B.y + v.z * B.z;
                 if (tca > 0.f && tca >= A.w && tca < B.w) {
                     const float3 pe = make_float3(v.x - tca * B.x, v.y - tca * B.y, v.z - tca * B.z);
-                    cand = dot3(pe, pe) < V.r2;
+                    cand = dot3(pe, pe) < r2;
                     j = __float_as_uint(q.w);
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, cand);
             if (m) {
+                const uint32_t e_ray = __shfl_sync(0xffffffffu, R.i, owner), e_kmb = __shfl_sync(0xffffffffu, v_kmb, owner);
+                const float e_thi = __shfl_sync(0xffffffffu, R.t.hi, owner), e_tlo = __shfl_sync(0xffffffffu, R.t.lo, owner);
+                const float e_w = __shfl_sync(0xffffffffu, R.w, owner);
                 if (cand) {
-                    const Visit &V = vis[owner];
-                    const uint4 ev = V.ev;
                     const int slot = (qhead + qn + __popc(m & lanemask_lt())) & (kQueue - 1);
-                    Q.ray[slot] = ev.x;
-                    Q.kmb[slot] = ev.y;
+                    Q.ray[slot] = e_ray;
+                    Q.kmb[slot] = e_kmb;
                     Q.j[slot] = j;
                     Q.tca[slot] = tca;
-                    Q.t_hi[slot] = __uint_as_float(ev.z);
-                    Q.t_lo[slot] = __uint_as_float(ev.w);
-                    Q.w[slot] = V.w;
+                    Q.t_hi[slot] = e_thi;
+                    Q.t_lo[slot] = e_tlo;
+                    Q.w[slot] = e_w;
                     cn.candidates++;
                 }
                 qn += __popc(m);
@@ -903,7 +893,6 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 }
             }
         }
-        __syncwarp();   // the visits are restaged by the next iteration
         if (active) {
             if (last) {
                 R.state = kSegDone;
