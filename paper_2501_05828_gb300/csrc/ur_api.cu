@@ -57,13 +57,19 @@ constexpr uint32_t kChunkMin = 512;    // fewest (work items are sized for sever
 // Default scatterer-grid cell sizes (x, y, z) in units of the capture radius
 // r_s.  The tracer walks columns in x and y; z cells only index each column's
 // references by depth (a visit reads the z cells within r_s of the depths it
-// spans).  Plane waves of a linear array travel in the xz plane, and planes
-// z = c and cylinders along y keep them there (their normals have no y
+// spans).  Plane waves of a linear array travel in the xz plane, and smooth
+// planes z = c and cylinders along y keep them there (their normals have no y
 // component), so in such scenes thin y columns hold few scatterers and cost no
-// steps; a sphere tilts rays out of the plane, and square columns serve better.
+// steps.  Rough boundaries scatter part of the rays out of the plane (wider y
+// columns), and spheres and triangle meshes turn every ray in 3D (square
+// columns).  Measured on the layered frame (smooth: 10.6 ms at 6 x 0.3 x 4 r_s),
+// its rough-bone version (17.7 ms at 4 x 2 x 4 against 20.0 at 6 x 0.3 x 4) and
+// the paper-settings and mesh-bone acquisitions (9.1 and 23.9 ms at 6 x 6 x 4
+// against 10.9 and 26.6 at 3 x 3 x 5).
 constexpr float kCellSlab[3] = {6.f, 0.3f, 4.f};
+constexpr float kCellRough[3] = {4.f, 2.f, 4.f};
+constexpr float kCellIso[3] = {6.f, 6.f, 4.f};
 constexpr int kResolveBatch = 20;   // default: lanes that must wait before a tracer warp resolves segments
-constexpr float kCellIso[3] = {3.f, 3.f, 5.f};
 
 struct SceneData {
     bool ok = false;
@@ -76,6 +82,7 @@ struct SceneData {
     int n_scat = 0;
     float r_s = 1e-4f;
     float g_rm = 0.f;
+    float cell_req[3] = {0.f, 0.f, 0.f};   // cell sizes the grid was built for (before any enlargement)
     float3 g_lo{}, g_h{}, g_inv_h{};
     int3 g_dim{};
     DevBuf scat, amp, refs, cell_count, cell_start, cell_fill, scan_tmp, bbox;
@@ -310,9 +317,24 @@ void prepare_transmits(ur_ctx *c) {
 
 // Default cell size along axis a (0 x, 1 y, 2 z) for a scene, in metres.
 float default_cell(const SceneData &sd, int a) {
-    bool y_invariant = true;
-    for (const ur_boundary &b : sd.bnd) y_invariant &= b.kind != UR_SPHERE;
-    return (y_invariant ? kCellSlab : kCellIso)[a] * sd.r_s;
+    bool planar = sd.n_tri == 0, rough = false;
+    for (const ur_boundary &b : sd.bnd) {
+        planar &= b.kind != UR_SPHERE;
+        rough |= sd.media[b.med_neg].roughness > 0.f || sd.media[b.med_pos].roughness > 0.f;
+    }
+    return (!planar ? kCellIso : rough ? kCellRough : kCellSlab)[a] * sd.r_s;
+}
+
+void build_grid(ur_ctx *c, SceneData &sd, const float *src);
+
+// Rebuild a scene's grid when its default cells changed (triangles or roughness set after the
+// upload) and no tuning overrides them.
+void regrid_if_default_changed(ur_ctx *c, SceneData &sd) {
+    if (sd.n_scat == 0) return;
+    const float want[3] = {c->tune.cell_xy > 0.f ? c->tune.cell_xy : default_cell(sd, 0),
+                           c->tune.cell_y > 0.f ? c->tune.cell_y : default_cell(sd, 1),
+                           c->tune.cell_z > 0.f ? c->tune.cell_z : default_cell(sd, 2)};
+    if (want[0] != sd.cell_req[0] || want[1] != sd.cell_req[1] || want[2] != sd.cell_req[2]) build_grid(c, sd, nullptr);
 }
 
 // Build (or rebuild) a scene's scatterer grid; src == nullptr reuses the device copy.
@@ -349,6 +371,9 @@ void build_grid(ur_ctx *c, SceneData &sd, const float *src) {
     float h_x = c->tune.cell_xy > 0.f ? c->tune.cell_xy : default_cell(sd, 0);
     float h_y = c->tune.cell_y > 0.f ? c->tune.cell_y : default_cell(sd, 1);
     float h_z = c->tune.cell_z > 0.f ? c->tune.cell_z : default_cell(sd, 2);
+    sd.cell_req[0] = h_x;
+    sd.cell_req[1] = h_y;
+    sd.cell_req[2] = h_z;
     int3 dim;
     for (;;) {
         dim.x = std::max(1, (int)std::ceil((hi[0] - lo[0] + 2.f * r_m) / h_x));
@@ -1134,6 +1159,8 @@ ur_status ur_scene_set_media(ur_ctx *c, int slot, const ur_medium *media, int n_
         sd.media = M;
         sd.sampling = Ms;
         sd.version = ++c->versions;
+        c->set_device();
+        regrid_if_default_changed(c, sd);
     });
 }
 
@@ -1149,6 +1176,7 @@ ur_status ur_scene_set_triangles(ur_ctx *c, int slot, const float *tri, const in
         if (n_tri == 0) {
             sd.n_tri = 0;
             sd.version = ++c->versions;
+            regrid_if_default_changed(c, sd);
             return;
         }
         std::vector<float> v(9 * (size_t)n_tri);
@@ -1169,6 +1197,7 @@ ur_status ur_scene_set_triangles(ur_ctx *c, int slot, const float *tri, const in
         ck(cudaStreamSynchronize(c->stream), "triangles");
         sd.n_tri = n_tri;
         sd.version = ++c->versions;
+        regrid_if_default_changed(c, sd);
     });
 }
 
