@@ -210,7 +210,9 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kQueue = 64;     // scatterer-event ring per warp (power of two, >= 63 entries needed)
 constexpr int kPool = kTracePool;
 
-enum { kInSeg = 0, kSegDone = 1, kNeedRay = 2, kFinished = 3 };
+// Lane states: walking a segment's columns, segment walked (to be finished), waiting for a
+// new ray, ray placed or redirected (its next segment to be set up), no rays left.
+enum { kInSeg = 0, kSegDone = 1, kNeedRay = 2, kFinished = 3, kNeedSeg = 4 };
 
 // Scatterer events waiting for their connection ray, one ring per warp (SoA).
 struct WarpQueue {
@@ -364,7 +366,7 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
         end_ray<DBG>(P, R, kEndArrayMiss, cn);
         return;
     }
-    start_segment<GEO>(P, R, cn);
+    R.state = kNeedSeg;   // set up by the resolve loop, with the other lanes that need a segment
 }
 
 // Secondary ray of a rough vertex to a uniformly drawn element centre, weighted
@@ -554,7 +556,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | rb);
         R.b += 1;
         R.prev = R.hit;
-        start_segment<GEO>(P, R, cn);
+        R.state = kNeedSeg;   // set up by the resolve loop, with the other lanes that need a segment
         return;
     }
     const float cos_i = -dot3(n, R.d);
@@ -595,7 +597,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
     if (DBG) R.h = fnv_step(R.h, 0x10000u | ((uint32_t)R.hit << 4) | branch);
     R.b += 1;
     R.prev = R.hit;
-    start_segment<GEO>(P, R, cn);
+    R.state = kNeedSeg;   // set up by the resolve loop, with the other lanes that need a segment
 }
 
 // A queued scatterer event: element drawn uniformly (Philox keyed by ray,
@@ -795,6 +797,8 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                     if (e < (uint64_t)P.n_el && i < IT.n_rays) start_ray<DBG, ROUGH, GEO>(P, R, item, IT, i, (uint32_t)e, cn);
                 }
             }
+            // one call site for every lane that continues its ray or starts a new one
+            if (R.state == kNeedSeg) start_segment<GEO>(P, R, cn);
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
         if (__all_sync(0xffffffffu, R.state == kFinished)) break;
