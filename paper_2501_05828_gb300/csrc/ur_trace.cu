@@ -8,6 +8,14 @@
 namespace ur {
 namespace {
 
+// Philox blocks of the plane-wave tracer come from one out-of-line copy: the kernel's hot loop
+// stays smaller, and instruction fetch is its first stall (layered frame 8.59 -> 8.17 ms); the
+// extended tracers keep them inline (there the call cost more than the code it saved).
+__device__ __noinline__ uint4 philox_outline(uint4 c, uint2 k) { return philox(c, k); }
+
+template <bool INLINE>
+__device__ __forceinline__ uint4 draw(uint4 c, uint2 k) { return INLINE ? philox(c, k) : philox_outline(c, k); }
+
 // Straight connection ray from p to the element centre (x_e, 0, 0): product of
 // sqrt(1 - R) over the boundaries it crosses (0 if one reflects totally),
 // travel time (samples) and attenuation exponent.  skip0: the boundary p lies
@@ -325,7 +333,7 @@ __device__ __forceinline__ void start_ray(const TraceP &P, Lane &R, uint32_t ite
     }
     const ItemP &IT = EMIT && P.mix_tx > 0 ? P.items[item] : slot_item;
     if (EMIT && IT.kind == UR_TX_SYNTHETIC) e = (uint32_t)IT.vx;
-    const uint4 x = philox(make_uint4(i, IT.stream, 0u, 0u), P.key);
+    const uint4 x = draw<EXT>(make_uint4(i, IT.stream, 0u, 0u), P.key);
     const float xe = P.x_first + (float)e * P.pitch;
     R.o = make_float3(xe + (u24(x.x) - 0.5f) * P.pitch, (u24(x.y) - 0.5f) * P.H, 0.f);
     float3 nrm = make_float3(0.f, 0.f, 1.f);   // normal at the emission point
@@ -577,7 +585,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         branch = 2;
         R.d = dr;
     } else {
-        const uint4 y = philox(make_uint4(R.i, R.stream, 1u | ((uint32_t)R.b << 8), 0u), P.key);
+        const uint4 y = draw<ROUGH>(make_uint4(R.i, R.stream, 1u | ((uint32_t)R.b << 8), 0u), P.key);
         if (u24(y.x) < Rs) {
             branch = 0;
             R.w *= r / Rs;
@@ -616,7 +624,7 @@ __device__ __forceinline__ bool event_element(const TraceP &P, const WarpQueue &
     const ItemP &IT = P.items[item];
     const SceneP &S = P.S[IT.scene];
     const float4 q = S.scat[j];
-    const uint4 x = philox(make_uint4(ray, IT.stream, 2u | ((uint32_t)b << 8), j), P.key);
+    const uint4 x = draw<EXT>(make_uint4(ray, IT.stream, 2u | ((uint32_t)b << 8), j), P.key);
     e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     float fd;
     if (CVX) {   // convex array: directivity to the element's normal
