@@ -402,7 +402,63 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
     }
 }
 
-// One thread per recorded arrival (only depositing paths have a gradient).
+// Arrivals are replayed grouped by path shape, so that the lanes of a warp replay the same
+// number of interactions and end in the same kind of event: key = (aperture return or
+// scatterer event, interactions before it), counting-sorted (per-CTA shared-memory
+// histograms, one scan, a scatter of the arrival indices).
+__device__ __forceinline__ uint32_t shape_key(uint32_t ev) { return ((ev >> 31) << 7) | ((ev >> 24) & 0x7Fu); }
+
+__device__ __forceinline__ void arrival_range(const AdjP &A, uint64_t &b, uint64_t &e) {
+    const uint64_t n = min((uint64_t)*A.n_arr, A.arr_cap);
+    const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+    b = min(n, (uint64_t)blockIdx.x * per);
+    e = min(n, b + per);
+}
+
+__global__ void k_adj_count(const AdjP A) {
+    __shared__ uint32_t h[kAdjKeys];
+    for (int q = threadIdx.x; q < kAdjKeys; q += blockDim.x) h[q] = 0u;
+    __syncthreads();
+    uint64_t b, e;
+    arrival_range(A, b, e);
+    for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) atomicAdd(&h[shape_key(A.rec[k].y)], 1u);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kAdjKeys; q += blockDim.x)
+        if (h[q]) atomicAdd(&A.key_count[q], h[q]);
+}
+
+__global__ void k_adj_scan(const AdjP A) {   // one CTA of kAdjKeys threads: exclusive scan into the offsets
+    __shared__ uint32_t part[kAdjKeys];
+    const uint32_t v = A.key_count[threadIdx.x];
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < kAdjKeys; off <<= 1) {
+        const uint32_t y = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    A.key_count[kAdjKeys + threadIdx.x] = part[threadIdx.x] - v;
+}
+
+__global__ void k_adj_scatter(const AdjP A) {
+    __shared__ uint32_t pos[kAdjKeys];
+    for (int q = threadIdx.x; q < kAdjKeys; q += blockDim.x) pos[q] = 0u;
+    __syncthreads();
+    uint64_t b, e;
+    arrival_range(A, b, e);
+    for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) atomicAdd(&pos[shape_key(A.rec[k].y)], 1u);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kAdjKeys; q += blockDim.x)
+        if (pos[q]) pos[q] = A.key_count[kAdjKeys + q] + atomicAdd(&A.key_count[2 * kAdjKeys + q], pos[q]);
+    __syncthreads();
+    for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+        const uint32_t p = atomicAdd(&pos[shape_key(A.rec[k].y)], 1u);
+        if (p < A.arr_cap) A.order[p] = (uint32_t)k;
+    }
+}
+
+// One thread per recorded arrival (only depositing paths have a gradient), in path-shape order.
 __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A) {
     const TraceP &P = A.T;
     float acc[kNP];
@@ -410,7 +466,8 @@ __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A)
     for (int k = 0; k < kNP; ++k) acc[k] = 0.f;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t n = min((uint64_t)*A.n_arr, A.arr_cap);
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const uint64_t k = A.order[q];
         const uint32_t row = A.arr[k].x;
         const uint2 rec = A.rec[k];
         const uint32_t item = row / (uint32_t)P.n_el;
@@ -430,6 +487,10 @@ __global__ void __launch_bounds__(128) k_adjoint(const __grid_constant__ AdjP A)
 }  // namespace
 
 void launch_adjoint(const AdjP &A, int sms, cudaStream_t s) {
+    if (cudaMemsetAsync(A.key_count, 0, sizeof(uint32_t) * 3 * kAdjKeys, s) != cudaSuccess) return;
+    k_adj_count<<<sms * 4, 256, 0, s>>>(A);
+    k_adj_scan<<<1, kAdjKeys, 0, s>>>(A);
+    k_adj_scatter<<<sms * 4, 256, 0, s>>>(A);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint, 128, 0);
     k_adjoint<<<sms * (per_sm > 0 ? per_sm : 1), 128, 0, s>>>(A);

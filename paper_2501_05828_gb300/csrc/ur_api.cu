@@ -112,6 +112,7 @@ struct ur_ctx {
     bool mix_tx = false;                    // ur_trace: each ray draws its transmit
     ur::MixP mix{};                         // ray order of the last mixed trace (list null: none)
     DevBuf mix_list, mix_bins;
+    DevBuf adj_order, adj_keys;        // arrivals of the adjoint in path-shape order, and that sort's counts
     DevBuf delay, tx_sin, tx_cos, tx_m, tx_kind, elem_xz;
 
     // work items of the last trace or batch plan
@@ -1113,7 +1114,7 @@ ur_status ur_destroy(ur_ctx *c) {
                      &c->counters, &c->row_count, &c->row_fill, &c->row_off, &c->work, &c->n_work, &c->stage_rf,
                      &c->stage_quad, &c->pix, &c->stage_iq, &c->stage_env, &c->stage_db, &c->env_max, &c->img_lists,
                      &c->batch_pix, &c->batch_lists, &c->batch_env, &c->batch_max, &c->adj_grad, &c->adj_amp,
-                     &c->adj_g, &c->mix_list, &c->mix_bins};
+                     &c->adj_g, &c->mix_list, &c->mix_bins, &c->adj_order, &c->adj_keys};
     for (DevBuf *b : all) c->release(*b);
     for (int p = 0; p < UR_N_PHASES; ++p) {
         if (c->ev0[p]) cudaEventDestroy(c->ev0[p]);
@@ -1507,10 +1508,14 @@ ur_status ur_trace_adjoint(ur_ctx *c, uint64_t n_rays, uint64_t seed, int max_b,
         A.rec = (const uint2 *)c->arr_dbg.p;
         A.n_arr = (const unsigned long long *)c->counters.p;
         A.arr_cap = c->arr_cap;
+        c->grow(c->adj_order, sizeof(uint32_t) * std::max<uint64_t>(c->arr_cap, 1));
+        c->grow(c->adj_keys, sizeof(uint32_t) * 3 * ur::kAdjKeys);
+        A.order = (uint32_t *)c->adj_order.p;
+        A.key_count = (uint32_t *)c->adj_keys.p;
         c->phase_begin(UR_PHASE_ADJOINT);
         ur::launch_adjoint(A, c->sms, c->stream);
         ck(cudaGetLastError(), "adjoint kernel");
-        c->phase_end(UR_PHASE_ADJOINT, 1);
+        c->phase_end(UR_PHASE_ADJOINT, 4);
         double g[3 * ur::kAdjMed];
         ck(cudaMemcpyAsync(c->host_scratch, c->adj_grad.p, sizeof g, cudaMemcpyDeviceToHost, c->stream), "read grad");
         ck(cudaStreamSynchronize(c->stream), "adjoint");

@@ -475,7 +475,10 @@ struct AdjP {
     const uint2 *rec;           // their (ray, event) words
     const unsigned long long *n_arr;
     uint64_t arr_cap;
+    uint32_t *order;            // [arr_cap]: arrival indices grouped by path shape (filled by launch_adjoint)
+    uint32_t *key_count;        // [3 * kAdjKeys] scratch of that counting sort
 };
+constexpr int kAdjKeys = 256;   // path shapes: aperture return or scatterer event x interactions before it
 void launch_adjoint(const AdjP &A, int sms, cudaStream_t s);
 
 struct BinP {
