@@ -10,6 +10,7 @@
 #include "ultraray.h"
 #include "ur_conv_tc.cuh"
 #include "ur_device.cuh"
+#include "ur_fastdiv.h"
 
 #include <cuda_bf16.h>
 
@@ -21,6 +22,10 @@
 #include <vector>
 
 typedef __nv_bfloat16 bf16;
+
+using ur::Div32;
+using ur::divmod32;
+using ur::make_div32;
 
 namespace {
 
@@ -56,16 +61,23 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 #define GRID_STRIDE(i, n) \
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
+// The same over 32-bit indices: the activations' element counts stay below 2^32 (checked when
+// a network is created), and pixel and channel indices come from division by invariant
+// integers (ur_fastdiv.h) rather than 64-bit division.
+#define GRID_STRIDE32(i, n) \
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
 // rf, quad [B][H][W] (fp32, the tracer's layout) -> the normalised BF16-rounded
 // input xn [B][H][W][2] (fp32) and its 3x3 neighbourhood as 32 BF16 channels per
 // pixel (channel 2 t + c = input channel c at tap t = 3 ky + kx, zero outside the
 // image and from channel 18 on), so the first convolution is one K = 32 GEMM.
-__global__ void k_prep(const float *rf, const float *quad, int B, int H, int W, float inv_scale, bf16 *xcol,
-                       float *xn) {
-    GRID_STRIDE(p, (long long)B * H * W) {
-        const int x = (int)(p % W);
-        const long long r = p / W;
-        const int y = (int)(r % H), b = (int)(r / H);
+__global__ void k_prep(const float *rf, const float *quad, int B, int H, int W, Div32 dW, Div32 dH, float inv_scale,
+                       bf16 *xcol, float *xn) {
+    GRID_STRIDE32(p, (uint32_t)B * H * W) {
+        uint32_t xu, yu;
+        const uint32_t r = divmod32(p, dW, xu);
+        const int b = (int)divmod32(r, dH, yu);
+        const int x = (int)xu, y = (int)yu;
         float v[32];
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
@@ -112,14 +124,15 @@ __global__ void k_unpack_first_grad(const float *dwp, int C, float *dw) {
 
 // Decoder input: cat[b, y, x, 0:c1] = low[b, y/2, x/2, :] (nearest-neighbour
 // upsampling), cat[b, y, x, c1:c1+c2] = skip[b, y, x, :]; 16-byte granules.
-__global__ void k_upcat(const bf16 *low, int c1, const bf16 *skip, int c2, int B, int H, int W, bf16 *cat) {
+__global__ void k_upcat(const bf16 *low, int c1, const bf16 *skip, int c2, int B, int H, int W, Div32 dG, Div32 dW,
+                        Div32 dH, bf16 *cat) {
     const int g1 = c1 / 8, G = (c1 + c2) / 8;
-    GRID_STRIDE(i, (long long)B * H * W * G) {
-        const int g = (int)(i % G);
-        const long long p = i / G;
-        const int x = (int)(p % W);
-        const long long r = p / W;
-        const int y = (int)(r % H), b = (int)(r / H);
+    GRID_STRIDE32(i, (uint32_t)B * H * W * G) {
+        uint32_t gu, xu, yu;
+        const uint32_t p = divmod32(i, dG, gu);
+        const uint32_t r = divmod32(p, dW, xu);
+        const int b = (int)divmod32(r, dH, yu);
+        const int g = (int)gu, x = (int)xu, y = (int)yu;
         const bf16 *src = g < g1 ? low + (((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * c1 + g * 8
                                  : skip + (size_t)p * c2 + (g - g1) * 8;
         reinterpret_cast<uint4 *>(cat)[i] = *reinterpret_cast<const uint4 *>(src);
@@ -127,15 +140,14 @@ __global__ void k_upcat(const bf16 *low, int c1, const bf16 *skip, int c2, int B
 }
 
 // 2x2 average pooling, NHWC bf16, 8 channels per thread.
-__global__ void k_pool2(const bf16 *x, bf16 *y, int B, int H, int W, int C) {
+__global__ void k_pool2(const bf16 *x, bf16 *y, int B, int H, int W, int C, Div32 dG, Div32 dWo, Div32 dHo) {
     const int Ho = H / 2, Wo = W / 2, G = C / 8;
     const uint4 *xg = reinterpret_cast<const uint4 *>(x);
-    GRID_STRIDE(i, (long long)B * Ho * Wo * G) {
-        const int g = (int)(i % G);
-        long long r = i / G;
-        const int xo = (int)(r % Wo);
-        r /= Wo;
-        const int yo = (int)(r % Ho), b = (int)(r / Ho);
+    GRID_STRIDE32(i, (uint32_t)B * Ho * Wo * G) {
+        uint32_t gu, xu, yu;
+        const uint32_t r = divmod32(divmod32(i, dG, gu), dWo, xu);
+        const int b = (int)divmod32(r, dHo, yu);
+        const int g = (int)gu, xo = (int)xu, yo = (int)yu;
         const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * G + g;
         float s[8], t[8];
         unpack8(xg[base], s);
@@ -177,17 +189,17 @@ __device__ __forceinline__ void flush_channel_sums(float (&acc)[8], int G, float
 // level's last ReLU output, so it is masked by that activation `act` here and
 // its column sums (that layer's bias gradient) go to db.
 __global__ void __launch_bounds__(256) k_unconcat_low(const bf16 *dcat, int B, int H, int W, int C1, int C2,
-                                                      const bf16 *act, bf16 *dlow, float *db) {
+                                                      Div32 dWo, Div32 dHo, const bf16 *act, bf16 *dlow, float *db) {
     const int Ho = H / 2, Wo = W / 2, G1 = C1 / 8, G = (C1 + C2) / 8;
     const int gi = threadIdx.x % G1, lanes = blockDim.x / G1, pl = threadIdx.x / G1;
     const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
     const uint4 *ag = reinterpret_cast<const uint4 *>(act);
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const long long P = (long long)B * Ho * Wo;
-    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
-        const int xo = (int)(p % Wo);
-        const long long r = p / Wo;
-        const int yo = (int)(r % Ho), b = (int)(r / Ho);
+    const uint32_t P = (uint32_t)B * Ho * Wo;
+    for (uint32_t p = blockIdx.x * (uint32_t)lanes + pl; p < P; p += gridDim.x * (uint32_t)lanes) {
+        uint32_t xu, yu;
+        const int b = (int)divmod32(divmod32(p, dWo, xu), dHo, yu);
+        const int xo = (int)xu, yo = (int)yu;
         const size_t base = (((size_t)b * H + 2 * yo) * W + 2 * xo) * G + gi;
         float v[8], t[8], m[8];
         unpack8(dg[base], v);
@@ -210,12 +222,13 @@ __global__ void __launch_bounds__(256) k_unconcat_low(const bf16 *dcat, int B, i
 }
 
 // Second part: the skip channels [C1, C1 + C2), copied.
-__global__ void k_unconcat_skip(const bf16 *dcat, int B, int H, int W, int C1, int C2, bf16 *dskip) {
+__global__ void k_unconcat_skip(const bf16 *dcat, int B, int H, int W, int C1, int C2, Div32 dG2, bf16 *dskip) {
     const int G1 = C1 / 8, G2 = C2 / 8, G = G1 + G2;
     const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
-    GRID_STRIDE(j, (long long)B * H * W * G2) {
-        const int g = (int)(j % G2);
-        const long long p = j / G2;
+    GRID_STRIDE32(j, (uint32_t)B * H * W * G2) {
+        uint32_t gu;
+        const uint32_t p = divmod32(j, dG2, gu);
+        const int g = (int)gu;
         reinterpret_cast<uint4 *>(dskip)[j] = dg[(size_t)p * G + G1 + g];
     }
 }
@@ -224,17 +237,17 @@ __global__ void k_unconcat_skip(const bf16 *dcat, int B, int H, int W, int C1, i
 // the gradient at the encoder block's last ReLU output, so it is masked by that
 // activation `act` and its column sums (the layer's bias gradient) go to db.
 __global__ void __launch_bounds__(256) k_pool2_bwd_mask(bf16 *d, const bf16 *dp, const bf16 *act, int B, int H,
-                                                        int W, int C, float *db) {
+                                                        int W, int C, Div32 dW, Div32 dH, float *db) {
     const int G = C / 8, gi = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
     uint4 *dg = reinterpret_cast<uint4 *>(d);
     const uint4 *pg = reinterpret_cast<const uint4 *>(dp);
     const uint4 *ag = reinterpret_cast<const uint4 *>(act);
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const long long P = (long long)B * H * W;
-    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
-        const int x = (int)(p % W);
-        const long long r = p / W;
-        const int y = (int)(r % H), b = (int)(r / H);
+    const uint32_t P = (uint32_t)B * H * W;
+    for (uint32_t p = blockIdx.x * (uint32_t)lanes + pl; p < P; p += gridDim.x * (uint32_t)lanes) {
+        uint32_t xu, yu;
+        const int b = (int)divmod32(divmod32(p, dW, xu), dH, yu);
+        const int x = (int)xu, y = (int)yu;
         const size_t i = (size_t)p * G + gi;
         float v[8], a[8], m[8];
         unpack8(dg[i], v);
@@ -554,7 +567,8 @@ const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
     if (build) {
         ++nn->launches;
         k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(
-            L.in.x1, L.in.c1, L.in.x2, L.in.c2, B, L.H, L.W, cat);
+            L.in.x1, L.in.c1, L.in.x2, L.in.c2, B, L.H, L.W, make_div32((uint32_t)(nn->cin[l] / 8)),
+            make_div32((uint32_t)L.W), make_div32((uint32_t)L.H), cat);
         ck(cudaGetLastError(), "upcat kernel");
     }
     return cat;
@@ -563,7 +577,8 @@ const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
 void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad) {
     const long long P = (long long)B * nn->H * nn->W;
     ++nn->launches;
-    k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, 1.f / nn->scale, nn->x, nn->xn);
+    k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, make_div32((uint32_t)nn->W),
+                                                make_div32((uint32_t)nn->H), 1.f / nn->scale, nn->x, nn->xn);
     ck(cudaGetLastError(), "prep kernel");
     ++nn->launches;
     k_pack_first<<<grid_for(32ll * nn->width), 256, 0, nn->stream>>>(nn->pbf + nn->woff[0], nn->width, nn->wfirst);
@@ -581,7 +596,8 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
             const int q = l / 2;
             ++nn->launches;
             k_pool2<<<grid_for((long long)B * L.H * L.W * nn->cout[l] / 4), 256, 0, nn->stream>>>(
-                nn->act[l].p, nn->pool[q].p, B, L.H, L.W, nn->cout[l]);
+                nn->act[l].p, nn->pool[q].p, B, L.H, L.W, nn->cout[l], make_div32((uint32_t)(nn->cout[l] / 8)),
+                make_div32((uint32_t)(L.W / 2)), make_div32((uint32_t)(L.H / 2)));
             ck(cudaGetLastError(), "pool kernel");
         }
     }
@@ -628,9 +644,11 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
 void unconcat(ur_nn *nn, int B, int H, int W, int C1, int C2, int l_low, bf16 *dskip) {
     ++nn->launches;
     k_unconcat_low<<<channel_grid((long long)B * (H / 2) * (W / 2), C1), 256, 0, nn->stream>>>(
-        nn->gcat, B, H, W, C1, C2, nn->act[l_low].p, nn->gLow, nn->grads + nn->boff[l_low]);
+        nn->gcat, B, H, W, C1, C2, make_div32((uint32_t)(W / 2)), make_div32((uint32_t)(H / 2)), nn->act[l_low].p,
+        nn->gLow, nn->grads + nn->boff[l_low]);
     ++nn->launches;
-    k_unconcat_skip<<<grid_for((long long)B * H * W * C2 / 8), 256, 0, nn->stream>>>(nn->gcat, B, H, W, C1, C2, dskip);
+    k_unconcat_skip<<<grid_for((long long)B * H * W * C2 / 8), 256, 0, nn->stream>>>(
+        nn->gcat, B, H, W, C1, C2, make_div32((uint32_t)(C2 / 8)), dskip);
     ck(cudaGetLastError(), "unconcat");
 }
 
@@ -638,7 +656,7 @@ void unconcat(ur_nn *nn, int B, int H, int W, int C1, int C2, int l_low, bf16 *d
 void pool_bwd(ur_nn *nn, int B, int H, int W, int C, int l, bf16 *d) {
     ++nn->launches;
     k_pool2_bwd_mask<<<channel_grid((long long)B * H * W, C), 256, 0, nn->stream>>>(
-        d, nn->gcat, nn->act[l].p, B, H, W, C, nn->grads + nn->boff[l]);
+        d, nn->gcat, nn->act[l].p, B, H, W, C, make_div32((uint32_t)W), make_div32((uint32_t)H), nn->grads + nn->boff[l]);
     ck(cudaGetLastError(), "pooling backward");
 }
 
@@ -719,6 +737,10 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
     ur_status st = nn_guard(nn, [&] {
         if (max_batch < 1 || max_batch > 64 || n_el < 8 || n_s < 8 || n_el % 8 || n_s % 8 || (width != 32 && width != 64))
             fail(UR_ERR_INVALID_ARG, "need 1 <= batch <= 64, n_el and n_s multiples of 8, width 32 or 64");
+        // the elementwise kernels index 16-byte granules of the largest activation (3 width
+        // channels at full resolution) and pixels with 32-bit integers
+        if ((uint64_t)max_batch * (uint64_t)n_el * (uint64_t)n_s * 3ull * (uint64_t)width / 8ull >= (1ull << 32))
+            fail(UR_ERR_INVALID_ARG, "batch x n_el x n_s too large for the network's 32-bit indexing");
         int n = 0;
         ck(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
         if (device < 0 || device >= n) fail(UR_ERR_INVALID_ARG, "bad device index");
