@@ -149,6 +149,11 @@ struct SceneP {
                             // a scatterer is referenced from the columns within g_rm of it in x and y,
                             // in its own z cell only
     const uint32_t *cell_start;
+    // the same structure on narrow columns, walked by exactly vertical segments (null: none)
+    float3 f_lo, f_inv_h;
+    int3 f_dim;
+    const float4 *f_refs;
+    const uint32_t *f_cell_start;
     const float *amp;
     const float4 *scat;     // (x, y, z, amplitude) by scatterer index
     // rarely read (after the fields every segment reads, which keep their offsets):

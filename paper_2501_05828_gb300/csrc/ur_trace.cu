@@ -228,6 +228,9 @@ struct WarpQueue {
     float tca[kQueue], t_hi[kQueue], t_lo[kQueue], w[kQueue];
 };
 
+// Step direction marking a segment that walks one of the fine columns (vertical segments).
+constexpr int kFineColumn = 2;
+
 // Per-lane state: the primary ray, its current segment and the column walk over it.
 struct Lane {
     float3 o, d;
@@ -257,7 +260,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x &
 // through the column, and its references are those within g_rm of the z that
 // stretch spans.  The first visit accepts closest approaches from g_rm before the
 // grid box on (none can lie there; the margin only keeps rounding out of play).
-template <int GEO>
+template <int GEO, bool FINE>
 __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters &cn) {
     constexpr bool CVX = (GEO & kGeoConvex) != 0, MESH = (GEO & kGeoMesh) != 0;
     const SceneP &S = P.S[R.scene];
@@ -300,14 +303,22 @@ __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters
         return;
     }
     if (!(t0 < t1)) return;
-    R.cx = min(max((int)floorf((o.x + t0 * d.x - S.g_lo.x) * S.g_inv_h.x), 0), S.g_dim.x - 1);
-    R.cy = min(max((int)floorf((o.y + t0 * d.y - S.g_lo.y) * S.g_inv_h.y), 0), S.g_dim.y - 1);
-    R.sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
-    R.sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
-    R.tdx = R.sx ? S.g_h.x * fabsf(ix) : INFINITY;
-    R.tdy = R.sy ? S.g_h.y * fabsf(iy) : INFINITY;
-    R.tmx = R.sx ? (S.g_lo.x + (float)(R.cx + (R.sx > 0)) * S.g_h.x - o.x) * ix : INFINITY;
-    R.tmy = R.sy ? (S.g_lo.y + (float)(R.cy + (R.sy > 0)) * S.g_h.y - o.y) * iy : INFINITY;
+    if (FINE && d.x == 0.f && d.y == 0.f && S.f_refs) {   // vertical: one visit of a fine column
+        R.cx = min(max((int)floorf((o.x - S.f_lo.x) * S.f_inv_h.x), 0), S.f_dim.x - 1);
+        R.cy = min(max((int)floorf((o.y - S.f_lo.y) * S.f_inv_h.y), 0), S.f_dim.y - 1);
+        R.sx = kFineColumn;
+        R.sy = 0;
+        R.tdx = R.tdy = R.tmx = R.tmy = INFINITY;
+    } else {
+        R.cx = min(max((int)floorf((o.x + t0 * d.x - S.g_lo.x) * S.g_inv_h.x), 0), S.g_dim.x - 1);
+        R.cy = min(max((int)floorf((o.y + t0 * d.y - S.g_lo.y) * S.g_inv_h.y), 0), S.g_dim.y - 1);
+        R.sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
+        R.sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
+        R.tdx = R.sx ? S.g_h.x * fabsf(ix) : INFINITY;
+        R.tdy = R.sy ? S.g_h.y * fabsf(iy) : INFINITY;
+        R.tmx = R.sx ? (S.g_lo.x + (float)(R.cx + (R.sx > 0)) * S.g_h.x - o.x) * ix : INFINITY;
+        R.tmy = R.sy ? (S.g_lo.y + (float)(R.cy + (R.sy > 0)) * S.g_h.y - o.y) * iy : INFINITY;
+    }
     R.t_enter = t0 - S.g_rm;
     R.t_end = t1;
     R.state = kInSeg;
@@ -806,7 +817,7 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 }
             }
             // one call site for every lane that continues its ray or starts a new one
-            if (R.state == kNeedSeg) start_segment<GEO>(P, R, cn);
+            if (R.state == kNeedSeg) start_segment<GEO, !ROUGH>(P, R, cn);
             if (!__any_sync(0xffffffffu, R.state == kSegDone || R.state == kNeedRay)) break;
         }
         if (__all_sync(0xffffffffu, R.state == kFinished)) break;
@@ -833,14 +844,21 @@ __global__ void __launch_bounds__(kBlock, trace_ctas_per_sm<ROUGH, GEO>()) k_tra
                 last = nc < 0 || nc >= (axis == 0 ? S.g_dim.x : S.g_dim.y);
             }
             const float t_out = last ? R.t_end : t_exit;
+            // the column's grid: fine (a vertical segment of the plane-wave tracer) or the usual; the
+            // extended tracers keep to the usual columns (the selection cost the paper-settings
+            // trace more than their vertical segments gained)
+            const bool fine = !ROUGH && R.sx == kFineColumn;
+            const float lo_z = fine ? S.f_lo.z : S.g_lo.z, inv_hz = fine ? S.f_inv_h.z : S.g_inv_h.z;
+            const int dim_y = fine ? S.f_dim.y : S.g_dim.y, dim_z = fine ? S.f_dim.z : S.g_dim.z;
+            const uint32_t *cs = fine ? S.f_cell_start : S.cell_start;
             const float za = fmaf(R.t_enter, R.d.z, R.o.z), zb = fmaf(t_out, R.d.z, R.o.z);
-            const int cza = min(max((int)floorf((fminf(za, zb) - S.g_rm - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
-            const int czb = min(max((int)floorf((fmaxf(za, zb) + S.g_rm - S.g_lo.z) * S.g_inv_h.z), 0), S.g_dim.z - 1);
-            const uint32_t col = ((uint32_t)R.cx * (uint32_t)S.g_dim.y + (uint32_t)R.cy) * (uint32_t)S.g_dim.z;
-            const uint32_t rb = S.cell_start[col + (uint32_t)cza];
-            cnt = S.cell_start[col + (uint32_t)czb + 1u] - rb;
+            const int cza = min(max((int)floorf((fminf(za, zb) - S.g_rm - lo_z) * inv_hz), 0), dim_z - 1);
+            const int czb = min(max((int)floorf((fmaxf(za, zb) + S.g_rm - lo_z) * inv_hz), 0), dim_z - 1);
+            const uint32_t col = ((uint32_t)R.cx * (uint32_t)dim_y + (uint32_t)R.cy) * (uint32_t)dim_z;
+            const uint32_t rb = cs[col + (uint32_t)cza];
+            cnt = cs[col + (uint32_t)czb + 1u] - rb;
             v_hi = last ? R.seg : t_exit;
-            v_refs = (unsigned long long)(uintptr_t)(S.refs + rb);
+            v_refs = (unsigned long long)(uintptr_t)((fine ? S.f_refs : S.refs) + rb);
             v_r2 = S.r2;
         }
         uint32_t incl = cnt;   // inclusive prefix sum of the visits' reference counts
