@@ -61,10 +61,10 @@ FLOPS_PER_CONNECTION = 243
 FLOPS_PER_TAP = 12
 FP32_LANES_PER_SM = 128
 
-# DRAM traffic of the tracer kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), per primary ray, and its warp instructions per ray; valid
-# only while the tracer sources hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "c8ffb2a6d5702fb3", "bytes_per_ray": 14.03, "warp_inst_per_ray": 538.4}
+# DRAM traffic of the tracer kernel (dram__bytes_read.sum + dram__bytes_write.sum) and its warp
+# instructions (smsp__inst_executed.sum), from one single-pass ncu capture of the benchmarked
+# 1e7-ray launch, per primary ray; valid only while the tracer sources hash to `src_sha`.
+TRACE_TRAFFIC = {"src_sha": "7702b7dd42d095c3", "bytes_per_ray": 5.312, "warp_inst_per_ray": 477.3}
 
 
 def tracer_sha():
