@@ -280,7 +280,11 @@ __device__ __forceinline__ void start_segment(const TraceP &P, Lane &R, Counters
     const float hi_y = S.g_lo.y + (float)S.g_dim.y * S.g_h.y;
     const float hi_z = S.g_lo.z + (float)S.g_dim.z * S.g_h.z;
     float t0 = 0.f, t1 = R.seg;
-    const float ix = 1.f / d.x, iy = 1.f / d.y, iz = 1.f / d.z;
+    // Reciprocals of the direction for the box clip and the column steps.  They only place
+    // column boundaries, which the g_rm margin of the references absorbs, so the approximate
+    // form serves (a few ulp, and no slow path for the zero components of in-plane and
+    // vertical rays: in a y-invariant scene every ray has d.y = 0).
+    const float ix = __fdividef(1.f, d.x), iy = __fdividef(1.f, d.y), iz = __fdividef(1.f, d.z);
     if (d.x != 0.f) {
         const float ta = (S.g_lo.x - o.x) * ix, tb = (hi_x - o.x) * ix;
         t0 = fmaxf(t0, fminf(ta, tb));
