@@ -64,7 +64,7 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of the tracer kernel (dram__bytes_read.sum + dram__bytes_write.sum) and its warp
 # instructions (smsp__inst_executed.sum), from one single-pass ncu capture of the benchmarked
 # 1e7-ray launch, per primary ray; valid only while the tracer sources hash to `src_sha`.
-TRACE_TRAFFIC = {"src_sha": "7702b7dd42d095c3", "bytes_per_ray": 5.312, "warp_inst_per_ray": 477.3}
+TRACE_TRAFFIC = {"src_sha": "1b78d85b6f5ad132", "bytes_per_ray": 5.548, "warp_inst_per_ray": 428.6}
 
 
 def tracer_sha():

@@ -176,8 +176,7 @@ __device__ void event(const AdjP &A, const SceneP &S, uint32_t item, uint32_t st
     const uint32_t e = (uint32_t)(((uint64_t)(x.x >> 8) * (uint64_t)P.n_el) >> 24);
     const float xe = P.x_first + (float)e * P.pitch;
     const float vx = xe - q.x;
-    const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
-    const float fd = directivity(P, q.z / D);
+    const float fd = directivity(P, q.z, vx * vx + q.y * q.y);
     if (!(fd > 0.f)) return;
     float lw[kNP], dTa[kAM];
 #pragma unroll
@@ -287,15 +286,15 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
             if (fabsf(V.o.y) <= 0.5f * P.H && V.o.x >= xl && V.o.x < xl + (float)P.n_el * P.pitch) {
                 int el = (int)floorf((V.o.x - xl) / P.pitch);
                 if (el > P.n_el - 1) el = P.n_el - 1;
-                const float cos_a = -V.d.z;
-                const float fd = directivity(P, cos_a);
+                const float ax = -V.d.z, tr2 = V.d.x * V.d.x + V.d.y * V.d.y;
+                const float fd = directivity(P, ax, tr2);
                 if (fd > 0.f && !ff_gt(V.t, P.t_last)) {
                     float lw[kNP];
 #pragma unroll
                     for (int k = 0; k < kNP; ++k) lw[k] = T.lw[k];
-                    if (cos_a < P.cos_am) {      // linear part of Eq. 13: f_d depends on the angle
-                        const float al = acosf(fminf(cos_a, 1.f));
-                        const float s = sqrtf(fmaxf(1.f - V.d.z * V.d.z, 1e-20f));
+                    if (tr2 > P.t2am * ax * ax) {      // linear part of Eq. 13: f_d depends on the angle
+                        const float s = sqrtf(tr2);    // sin of the angle (unit d)
+                        const float al = atan2f(s, ax);
 #pragma unroll
                         for (int m = 0; m < kAM; ++m) lw[3 * m] += -(T.dD[m].z / s) / (P.ac - al);
                     }
@@ -329,7 +328,7 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
                 vrel = make_float3(V.o.x - B.p[0], V.o.y - B.p[1], V.o.z - B.p[2]);
             else
                 vrel = make_float3(V.o.x - B.p[0], 0.f, V.o.z - B.p[1]);
-            const float inv_len = 1.f / sqrtf(dot3(vrel, vrel));
+            const float inv_len = rsqrtf(dot3(vrel, vrel));
 #pragma unroll
             for (int m = 0; m < kAM; ++m) {
                 float3 dv = T.dO[m];
@@ -388,7 +387,7 @@ __device__ void replay(const AdjP &A, uint32_t item, const ItemP &IT, uint32_t i
                 for (int m = 0; m < kAM; ++m) T.dD[m] = T.dD[m] + (2.f * dci[m]) * n + (2.f * ci) * dn[m];
                 V.d = dr;
             } else {
-                V.w *= S.split_sampling ? sqrtf(Tr) / transmitted(ci, cts, S.Zs[V.med], S.Zs[m2]) : 1.f / sqrtf(Tr);
+                V.w *= S.split_sampling ? sqrtf(Tr) / transmitted(ci, cts, S.Zs[V.med], S.Zs[m2]) : rsqrtf(Tr);   // as the tracer
 #pragma unroll
                 for (int m = 0; m < kAM; ++m)
                     T.dD[m] = deta[m] * V.d + eta * T.dD[m] + (deta[m] * ci + eta * dci[m] - dct[m]) * n +

@@ -862,8 +862,8 @@ ur::TraceP make_trace_params(ur_ctx *c, uint64_t seed, int max_b, float max_path
     const double am = (double)A.alpha_m_deg * kPi / 180.0, ac = (double)A.alpha_c_deg * kPi / 180.0;
     P.am = (float)am;
     P.ac = (float)ac;
-    P.cos_am = (float)std::cos(am);
-    P.cos_ac = (float)std::cos(ac);
+    P.t2am = (float)(std::tan(am) * std::tan(am));
+    P.t2ac = (float)(std::tan(ac) * std::tan(ac));
     P.items = (const ur::ItemP *)c->items_dev.p;
     P.n_items = (int)c->items.size();
     P.n_slots = c->n_slots;

@@ -117,9 +117,11 @@ __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_fl
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// Unit vector by the hardware reciprocal square root (a few ulp; the tracer's directions feed
+// geometry whose error budget is set by FP32 positions, and no slow path of an IEEE divide runs).
 __device__ __forceinline__ float3 unit3(float3 a) {
-    float l = sqrtf(dot3(a, a));
-    return make_float3(a.x / l, a.y / l, a.z / l);
+    const float il = rsqrtf(dot3(a, a));
+    return make_float3(a.x * il, a.y * il, a.z * il);
 }
 
 // ---------------------------------------------------------------- parameters
@@ -190,7 +192,7 @@ struct TraceP {
     float pitch, H, x_first;        // element 0 centre (linear array)
     float radius, dphi, phi0;       // convex array (radius > 0): angle between centres, angle of element 0
     float K, t_last;                // pulse half-width and latest useful arrival (samples)
-    float cos_am, cos_ac, am, ac;   // directivity (Eq. 13)
+    float t2am, t2ac, am, ac;   // directivity (Eq. 13): tan^2 of the main-beam and cutoff angles, the angles
     // work: items (transmit x scene) and their slots
     const ItemP *items;
     int n_items;
@@ -454,12 +456,24 @@ __device__ __forceinline__ float transmitted(float cos_i, float cos_t, float Z1,
     return 4.f * Z1 * Z2 * cos_i * cos_t / (s * s);
 }
 
-// Eq. 13 through cosines: 1 inside the main beam, 0 beyond the cutoff, linear in angle between.
-__device__ __forceinline__ float directivity(const TraceP &P, float cos_a) {
-    if (cos_a >= P.cos_am) return 1.f;
-    if (cos_a < P.cos_ac) return 0.f;
-    const float al = acosf(fminf(cos_a, 1.f));
-    return (P.ac - al) / (P.ac - P.am);
+// Eq. 13 for a direction given by its part ax along the element normal and the squared length
+// tr2 of its part across it (any scale): 1 inside the main beam, 0 beyond the cutoff (< 90
+// degrees, so ax <= 0 is beyond it), linear in the angle between.  The beam tests compare tan^2,
+// with no square root or division; in the taper the angle is atan2(tr, ax), which keeps a few
+// ulp of the angle itself where acos of a rounded cosine loses ulp(cos) / sin(angle), an error the
+// taper divides by its own small value near the cutoff.
+__device__ __forceinline__ float directivity(const TraceP &P, float ax, float tr2) {
+    if (!(ax > 0.f)) return 0.f;
+    const float ax2 = ax * ax;
+    if (tr2 <= P.t2am * ax2) return 1.f;
+    if (tr2 > P.t2ac * ax2) return 0.f;
+    return (P.ac - atan2f(sqrtf(tr2), ax)) / (P.ac - P.am);
+}
+
+// Squared length of v x n for a unit n: the part of v across n, from products that do not cancel.
+__device__ __forceinline__ float cross2(float3 v, float3 n) {
+    const float a = v.y * n.z - v.z * n.y, b = v.z * n.x - v.x * n.z, c = v.x * n.y - v.y * n.x;
+    return a * a + b * b + c * c;
 }
 
 

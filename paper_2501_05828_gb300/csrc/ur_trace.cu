@@ -24,8 +24,9 @@ template <bool MESH>
 __device__ float connection(const SceneP &S, float3 p, int med, int skip0, float xe, ff &t_conn, float &att) {
     float3 o = p;
     float3 w = make_float3(xe - p.x, -p.y, -p.z);
-    float rem = sqrtf(dot3(w, w));
-    w = make_float3(w.x / rem, w.y / rem, w.z / rem);
+    const float w2 = dot3(w, w), iw = rsqrtf(w2);
+    float rem = sqrtf(w2);   // the length sets the travel time: correctly rounded
+    w = make_float3(w.x * iw, w.y * iw, w.z * iw);
     float fac = 1.f, a = 0.f;
     ff t = {0.f, 0.f};
     int m = med, skip = skip0;
@@ -140,8 +141,9 @@ template <bool MESH>
 __device__ float connection_to(const SceneP &S, float3 p, int med, int skip0, float3 q, ff &t_conn, float &att) {
     float3 o = p;
     float3 w = make_float3(q.x - p.x, q.y - p.y, q.z - p.z);
-    float rem = sqrtf(dot3(w, w));
-    w = make_float3(w.x / rem, w.y / rem, w.z / rem);
+    const float w2 = dot3(w, w), iw = rsqrtf(w2);
+    float rem = sqrtf(w2);   // the length sets the travel time: correctly rounded
+    w = make_float3(w.x * iw, w.y * iw, w.z * iw);
     float fac = 1.f, a = 0.f;
     ff t = {0.f, 0.f};
     int m = med, skip = skip0;
@@ -406,7 +408,7 @@ __device__ void rough_connection(const TraceP &P, const SceneP &S, const Lane &R
     const float D = sqrtf(dot3(v, v));
     const float3 o = make_float3(v.x / D, v.y / D, v.z / D);
     const float cos_e = -dot3(o, ne);   // at the element, to its normal
-    const float fd = directivity(P, cos_e);
+    const float fd = directivity(P, -dot3(v, ne), cross2(v, ne));
     if (!(fd > 0.f)) return;
     const Medium &M = S.med[R.med], &M2 = S.med[m2];
     float pdf;
@@ -520,7 +522,8 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
         if (el >= 0) {
             float3 ce = make_float3(0.f, 0.f, 0.f), ne = make_float3(0.f, 0.f, 1.f);
             if (ROUGH) elem_frame<CVX>(P, (uint32_t)el, ce, ne);
-            const float fd = directivity(P, ROUGH ? -dot3(R.d, ne) : -R.d.z);
+            const float fd = ROUGH ? directivity(P, -dot3(R.d, ne), cross2(R.d, ne))
+                                   : directivity(P, -R.d.z, R.d.x * R.d.x + R.d.y * R.d.y);
             if (fd > 0.f && !ff_gt(R.t, P.t_last)) {
                 float wa = R.w * fd;
                 if (ROUGH && R.mis) {   // balance heuristic against the rough vertex's secondary ray
@@ -610,7 +613,7 @@ __device__ void finish_segment(const TraceP &P, Lane &R, Counters &cn) {
             const float eta = M2.c / M.c;
             // 1 - R as 4 Z1 Z2 cos_i cos_t / (Z2 cos_i + Z1 cos_t)^2: no cancellation near the critical angle
             const float T = transmitted(cos_i, cos_t, M.Z, M2.Z);
-            R.w *= SPLIT ? sqrtf(T) / transmitted(cos_i, cts, S.Zs[R.med], S.Zs[m2]) : 1.f / sqrtf(T);
+            R.w *= SPLIT ? sqrtf(T) / transmitted(cos_i, cts, S.Zs[R.med], S.Zs[m2]) : rsqrtf(T);
             R.d = unit3(eta * R.d + (eta * cos_i - cos_t) * n);
             R.med = m2;
         }
@@ -646,11 +649,10 @@ __device__ __forceinline__ bool event_element(const TraceP &P, const WarpQueue &
         float3 ce, ne;
         elem_frame<CVX>(P, e, ce, ne);
         const float3 v = make_float3(q.x - ce.x, q.y - ce.y, q.z - ce.z);
-        fd = directivity(P, dot3(v, ne) / sqrtf(dot3(v, v)));
+        fd = directivity(P, dot3(v, ne), cross2(v, ne));
     } else {
         const float vx = P.x_first + (float)e * P.pitch - q.x;
-        const float D = sqrtf(vx * vx + q.y * q.y + q.z * q.z);
-        fd = directivity(P, q.z / D);
+        fd = directivity(P, q.z, vx * vx + q.y * q.y);
     }
     if (!(fd > 0.f)) return false;
     const Medium &M = S.med[med];
