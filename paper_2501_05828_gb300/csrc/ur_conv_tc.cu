@@ -175,6 +175,7 @@ struct Cfg {
 
 struct Args {
     int N, H, W, C, Cout, nxb, relu, taps, n_tiles, n_ntiles;
+    int stages, wres;   // kx-fused kernel: input stages per CTA, weights resident in shared memory
     const float *bias;
     const bf16 *mask;
     bf16 *y;
@@ -409,60 +410,64 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 
 // ------------------------------------------------------------------ kx-fused convolution
 //
-// For C_out = BN in {32, 64}: the three kx taps of one kernel row ky are consecutive rows of
-// the weight view [9 C_out][C_in], so one MMA with N = 3 BN computes, for the 128 pixels
-// x0 - 1 .. x0 + 126 of input row y + ky - 1, the three partial products P_kx[r] side by
-// side in TMEM.  Output pixel x0 + j takes P_0[j] + P_1[j + 1] + P_2[j + 2] (summed over
-// ky and channel chunks by the MMAs), so a tile yields 126 outputs; the epilogue adds the
-// shifted rows with warp shuffles and, across TMEM lane quadrants, through shared memory.
-// The input is read once per kernel row instead of once per tap.
-constexpr int kKxOut = kBM - 2;   // valid outputs per tile
+// For C_out = BN in {32, 64}: a stage holds the input pixels x0 - 1 .. x0 + 128 of row
+// y + ky - 1 (130 rows of BK channels) and the weights of the three kx taps of kernel row ky
+// (consecutive rows 3 ky C_out .. of the weight view [9 C_out][C_in]).  Tap kx reads the
+// A operand from row kx of the staged tile: the tensor core applies the swizzle from the
+// shared-memory address bits, so a descriptor that starts one or two 128- (or 64-) byte rows
+// into a tile written by TMA still reads the rows TMA wrote there.  The three taps accumulate
+// into one accumulator of 128 output pixels, and the input is read once per kernel row instead
+// of once per tap; the epilogue is the plain one (bias, ReLU, mask, BF16 store).
+constexpr int kKxRows = kBM + 2;   // staged input pixels per kernel row
 
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Weights: when all 3 kc blocks of one C_out tile fit beside a few input stages they are
+// loaded once per CTA and stay in shared memory (every CTA reads the same few KB, which
+// otherwise come from a handful of L2 slices at every stage); otherwise each stage carries its
+// kernel row's block.  The stage count and this choice are set per launch.
+constexpr int kKxMaxStages = 8;
 
 template <int BN, int BK>
 struct KxCfg {
     static constexpr int ROW = BK * 2;
-    static constexpr int NB = 3 * BN;                      // MMA N: three taps
-    static constexpr int A_BYTES = kBM * ROW;
+    static constexpr int NB = 3 * BN;                      // weight rows per block: the three kx taps
+    static constexpr int A_BYTES = kKxRows * ROW;
     static constexpr int B_BYTES = NB * ROW;
     static constexpr int A_PAD = (A_BYTES + 1023) / 1024 * 1024;
     static constexpr int B_PAD = (B_BYTES + 1023) / 1024 * 1024;
-    static constexpr int BUDGET = BN == 64 ? 200 * 1024 : 100 * 1024;
-    static constexpr int S_RAW = BUDGET / (A_PAD + B_PAD);
-    static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 8 ? 8 : S_RAW);
-    static constexpr int ACC_COLS = NB <= 128 ? 128 : 256;
-    static constexpr int TMEM_COLS = 2 * ACC_COLS;
-    static constexpr int N_BARS = 2 * S + 4;
-    static constexpr int XCH = 2 * 4 * 2 * 2 * 32 * 4;     // 2 x [quadrant][lane 0/1][P1/P2][32 columns] floats
-    static constexpr int SMEM = S * (A_PAD + B_PAD) + 1024 + 8 * N_BARS + 16 + XCH;
+    static constexpr int ACC_COLS = BN;
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;         // double-buffered
+    static constexpr int N_BARS = 2 * kKxMaxStages + 5;    // full, empty, acc_full[2], acc_empty[2], weights
+    static constexpr int TAIL = 8 * N_BARS + 16;           // barriers and the TMEM address slot
+    // shared memory of a launch: alignment slack, resident weights, stages, tail
+    static int smem(int kc, bool wres, int stages) {
+        return 1024 + (wres ? 3 * kc * B_PAD : 0) + stages * (A_PAD + (wres ? 0 : B_PAD)) + TAIL;
+    }
 };
 
-template <int NB>
-__host__ __device__ constexpr uint32_t idesc_bf16_n() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-
 template <int BN, int BK>
-__global__ void __launch_bounds__(kConvThreads, 1)
+__global__ void __launch_bounds__(kConvThreads, 2)
     k_conv_kx(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, const Args a) {
     using K = KxCfg<BN, BK>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = s_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *sm = smem_raw + (base - raw);
-    const uint32_t sA = base, sB = base + K::S * K::A_PAD;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + K::S * (K::A_PAD + K::B_PAD));
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + K::N_BARS);
-    float *xch = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tslot) + 16);
-    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + K::S);
-    const uint32_t accf0 = s_addr(bars + 2 * K::S), acce0 = s_addr(bars + 2 * K::S + 2);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kc = a.C / BK, nk = 3 * kc;   // stages per tile: kernel rows x channel chunks
+    const bool wres = a.wres != 0;
+    const int S = a.stages;
+    const uint32_t w_bytes = wres ? (uint32_t)(3 * kc * K::B_PAD) : 0u;
+    const uint32_t stage = (uint32_t)(K::A_PAD + (wres ? 0 : K::B_PAD));
+    const uint32_t sW = base, sS = base + w_bytes;   // resident weights; stage s: A at sS + s stage, then B
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + w_bytes + (uint32_t)S * stage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + K::N_BARS);
+    const uint32_t full0 = s_addr(bars), empty0 = s_addr(bars + kKxMaxStages);
+    const uint32_t accf0 = s_addr(bars + 2 * kKxMaxStages), acce0 = s_addr(bars + 2 * kKxMaxStages + 2);
+    const uint32_t wfull = s_addr(bars + 2 * kKxMaxStages + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t deadline = now_ns() + kWaitNs;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < K::S; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
@@ -470,6 +475,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
             mbar_init(accf0 + 8 * b, 1);
             mbar_init(acce0 + 8 * b, 4);
         }
+        mbar_init(wfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -485,36 +491,52 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         const int m = t / a.nxb;
         y = m % a.H;
         n = m / a.H;
-        x0 = xb * kKxOut;
+        x0 = xb * kBM;
     };
 
     if (warp == 0) {
         if (lane == 0) {   // TMA producer
-            int it = 0;
+            if (wres) {    // every weight block once: block kt = (ky, channel chunk) at sW + kt B_PAD
+                mbar_expect_tx(wfull, (uint32_t)(nk * K::B_BYTES));
+                for (int kt = 0; kt < nk; ++kt) {
+                    const int ky = kt / kc, c0 = (kt - ky * kc) * BK;
+                    tma_load_2d(sW + (uint32_t)(kt * K::B_PAD), &tmw, c0, 3 * ky * BN, wfull);
+                }
+            }
+            int it = 0, s = 0;
+            uint32_t ph = 0;
             for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
                 int n, y, x0;
                 decode(t, n, y, x0);
                 for (int kt = 0; kt < nk; ++kt, ++it) {
-                    const int s = it % K::S;
-                    if (!mbar_wait(empty0 + 8 * s, ((uint32_t)(it / K::S) & 1u) ^ 1u, deadline)) {
+                    if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, deadline)) {
                         ok = false;
                         break;
                     }
                     const int ky = kt / kc, c0 = (kt - ky * kc) * BK;
-                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + K::B_BYTES));
-                    tma_load_4d(sA + s * K::A_PAD, &tmx, c0, x0 - 1, y + ky - 1, n, full0 + 8 * s);
-                    tma_load_2d(sB + s * K::B_PAD, &tmw, c0, 3 * ky * BN, full0 + 8 * s);
+                    const uint32_t sa = sS + (uint32_t)s * stage;
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + (wres ? 0 : K::B_BYTES)));
+                    tma_load_4d(sa, &tmx, c0, x0 - 1, y + ky - 1, n, full0 + 8 * s);
+                    if (!wres) tma_load_2d(sa + K::A_PAD, &tmw, c0, 3 * ky * BN, full0 + 8 * s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
+            // let the copies already in flight land before the block can exit
+            if (wres) mbar_wait(wfull, 0u, deadline + kWaitNs / 20);
             if (!ok)
-                for (int j = it > K::S ? it - K::S : 0; j < it; ++j)
-                    mbar_wait(full0 + 8 * (j % K::S), (uint32_t)(j / K::S) & 1u, deadline + kWaitNs / 20);
+                for (int j = it > S ? it - S : 0; j < it; ++j)
+                    mbar_wait(full0 + 8 * (j % S), (uint32_t)(j / S) & 1u, deadline + kWaitNs / 20);
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
-            constexpr uint32_t idesc = idesc_bf16_n<K::NB>();
-            int it = 0, i = 0;
+            constexpr uint32_t idesc = idesc_bf16<BN>();
+            if (wres && !mbar_wait(wfull, 0u, deadline)) ok = false;
+            int i = 0, s = 0;
+            uint32_t ph = 0;
             for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x, ++i) {
                 const int b = i & 1;
                 if (!mbar_wait(acce0 + 8 * b, ((uint32_t)(i >> 1) & 1u) ^ 1u, deadline)) {
@@ -523,25 +545,33 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * K::ACC_COLS);
-                for (int kt = 0; kt < nk; ++kt, ++it) {
-                    const int s = it % K::S;
-                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(it / K::S) & 1u, deadline)) {
+                for (int kt = 0; kt < nk; ++kt) {
+                    if (!mbar_wait(full0 + 8 * s, ph, deadline)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = sA + s * K::A_PAD, b0 = sB + s * K::B_PAD;
+                    const uint32_t a0 = sS + (uint32_t)s * stage;
+                    const uint32_t b0 = wres ? sW + (uint32_t)(kt * K::B_PAD) : a0 + K::A_PAD;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        mma_bf16(d, sdesc(a0 + 32 * k, K::ROW), sdesc(b0 + 32 * k, K::ROW), idesc, (kt | k) != 0);
+                    for (int kx = 0; kx < 3; ++kx)   // output pixel x0 + r reads input row r + kx of the stage
+#pragma unroll
+                        for (int k = 0; k < BK / 16; ++k)
+                            mma_bf16(d, sdesc(a0 + (uint32_t)(kx * K::ROW) + 32 * k, K::ROW),
+                                     sdesc(b0 + (uint32_t)(kx * BN * K::ROW) + 32 * k, K::ROW), idesc,
+                                     (kt | kx | k) != 0);
                     mma_commit(empty0 + 8 * s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 mma_commit(accf0 + 8 * b);
             }
         }
         __syncwarp();
-    } else {   // epilogue warps; every warp runs the same tiles and barriers (no early exit)
-        const int q = warp & 3, r = q * 32 + lane;
+    } else {   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31
+        const int q = warp & 3;
         float dsum[BN / 32];
 #pragma unroll
         for (int c = 0; c < BN / 32; ++c) dsum[c] = 0.f;
@@ -549,57 +579,26 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
             const int b = i & 1;
             const bool ready = mbar_wait(accf0 + 8 * b, (uint32_t)(i >> 1) & 1u, deadline);
-            if (__all_sync(0xffffffffu, ready) == 0) ok = false;
+            if (__all_sync(0xffffffffu, ready) == 0) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
             int n, y, x0;
             decode(t, n, y, x0);
-            const int o = x0 + r;
-            const bool in = r < kKxOut && o < a.W;
-            const size_t pix = ((size_t)n * a.H + y) * a.W + o;
-            const uint32_t tb = tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16);
+            const int x = x0 + q * 32 + lane;
+            const bool in = x < a.W;
+            const size_t pix = ((size_t)n * a.H + y) * a.W + x;
 #pragma unroll
             for (int c = 0; c < BN; c += 32) {
-                // v[j] = P_1[r + 1] + P_2[r + 2] + P_0[r]; rows beyond this quadrant come from shared memory
-                float *xb = xch + ((i * (BN / 32) + c / 32) & 1) * (4 * 2 * 2 * 32);   // double-buffered
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
                 float v[32];
-                {
-                    uint32_t p[32];
-                    tmem_ld32(tb + (uint32_t)(BN + c), p);
-                    if (lane < 2)
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) xb[((q * 2 + lane) * 2 + 0) * 32 + j] = __uint_as_float(p[j]);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float n1 = __shfl_down_sync(0xffffffffu, __uint_as_float(p[j]), 1);
-                        v[j] = lane < 31 ? n1 : 0.f;
-                    }
-                    tmem_ld32(tb + (uint32_t)(2 * BN + c), p);
-                    if (lane < 2)
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) xb[((q * 2 + lane) * 2 + 1) * 32 + j] = __uint_as_float(p[j]);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float n2 = __shfl_down_sync(0xffffffffu, __uint_as_float(p[j]), 2);
-                        v[j] += lane < 30 ? n2 : 0.f;
-                    }
-                    tmem_ld32(tb + (uint32_t)c, p);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] += __uint_as_float(p[j]);
-                }
-                epi_barrier();   // the neighbouring quadrant's first two rows are in shared memory
-                if (q < 3 && lane >= 30) {
-                    const float *n1 = xb + (((q + 1) * 2 + 0) * 2 + 0) * 32;
-                    const float *n2 = xb + (((q + 1) * 2 + (lane - 30)) * 2 + 1) * 32;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] += (lane == 31 ? n1[j] : 0.f) + n2[j];
-                }
-                if (!in)
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                for (int j = 0; j < 32; ++j) v[j] = in ? __uint_as_float(r[j]) : 0.f;
                 if (in) {
-                    const int co = c;
                     if (a.bias) {
-                        const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + co);
+                        const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + c);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const float4 bb = b4[j];
@@ -614,7 +613,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
                     }
                     if (a.mask) {
-                        const uint4 *m4 = reinterpret_cast<const uint4 *>(a.mask + pix * a.Cout + co);
+                        const uint4 *m4 = reinterpret_cast<const uint4 *>(a.mask + pix * a.Cout + c);
 #pragma unroll
                         for (int g = 0; g < 4; ++g) {
                             const uint4 mv = m4[g];
@@ -627,7 +626,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                             }
                         }
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + co);
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + c);
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         uint4 o4;
@@ -891,18 +890,51 @@ cudaError_t ctas_per_sm(KernelT kernel, int smem, int tmem_cols, int *occ) {
     return cudaSuccess;
 }
 
+// Stages and weight residency of a kx-fused launch: two CTAs per SM (the epilogues of two tiles
+// overlap), with resident weights when two input stages fit beside them, else with the weights
+// streamed with the input; one CTA per SM only when neither fits.
 template <int BN, int BK>
-cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, const Args &a, int n_sm, cudaStream_t stream) {
+cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, Args a, int n_sm, cudaStream_t stream) {
     using K = KxCfg<BN, BK>;
-    cudaError_t e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    int dev = 0, smem_sm = 0, reserve = 0, optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    const int kc = a.C / BK, two = smem_sm / 2 - reserve;
+    auto fit = [&](int budget, bool w) {
+        const int n = (budget - K::smem(kc, w, 0)) / (K::A_PAD + (w ? 0 : K::B_PAD));
+        return std::min(n, kKxMaxStages);
+    };
+    bool wres = true;
+    int stages = fit(two, true);
+    if (stages < 2) {
+        wres = false;
+        stages = fit(two, false);
+    }
+    if (stages < 2) {
+        wres = true;
+        stages = fit(optin, true);
+    }
+    if (stages < 2) {
+        wres = false;
+        stages = fit(optin, false);
+    }
+    if (stages < 2) return cudaErrorInvalidValue;
+    a.stages = stages;
+    a.wres = wres ? 1 : 0;
+    const int smem = K::smem(kc, wres, stages);
+    e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     int occ = 1;
-    if (e == cudaSuccess) e = ctas_per_sm(k_conv_kx<BN, BK>, K::SMEM, K::TMEM_COLS, &occ);
+    if (e == cudaSuccess) e = ctas_per_sm(k_conv_kx<BN, BK>, smem, K::TMEM_COLS, &occ);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long long>(a.n_tiles, (long long)occ * std::max(1, n_sm));
-    k_conv_kx<BN, BK><<<grid, kConvThreads, K::SMEM, stream>>>(mx, mw, a);
+    k_conv_kx<BN, BK><<<grid, kConvThreads, smem, stream>>>(mx, mw, a);
     return cudaGetLastError();
 }
 
@@ -948,7 +980,8 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
     {
         const cuuint64_t dims[4] = {(cuuint64_t)p.C, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.N};
         const cuuint64_t strides[3] = {(cuuint64_t)p.C * 2, (cuuint64_t)p.W * p.C * 2, (cuuint64_t)p.H * p.W * p.C * 2};
-        const cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)kBM, 1, 1};
+        const bool kx = p.taps == 9 && (p.Cout == 32 || p.Cout == 64);   // kx-fused: 130 staged input pixels
+        const cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)(kx ? kKxRows : kBM), 1, 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
         const CUresult r = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(p.x), dims, strides, box, es,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -983,13 +1016,13 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
             if (why) *why = "tensor map of the stacked weights rejected";
             return cudaErrorInvalidValue;
         }
-        const int nxk = (p.W + kKxOut - 1) / kKxOut;
+        const int nxk = (p.W + kBM - 1) / kBM;
         const long long nt = (long long)p.N * p.H * nxk;
         if (nt > 0x7fffffffll) {
             if (why) *why = "conv3x3_tc: too many tiles";
             return cudaErrorInvalidValue;
         }
-        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, p.bias, p.mask, p.y, p.dbias, d_err};
+        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, 0, 0, p.bias, p.mask, p.y, p.dbias, d_err};
         if (p.Cout == 32) return BK == 64 ? launch_kx<32, 64>(mx, mw2, a, n_sm, stream) : launch_kx<32, 32>(mx, mw2, a, n_sm, stream);
         return BK == 64 ? launch_kx<64, 64>(mx, mw2, a, n_sm, stream) : launch_kx<64, 32>(mx, mw2, a, n_sm, stream);
     }
@@ -999,8 +1032,8 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
         if (why) *why = "conv3x3_tc: too many tiles";
         return cudaErrorInvalidValue;
     }
-    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, p.bias, p.mask, p.y, p.dbias,
-           d_err};
+    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, 0, 0, p.bias, p.mask, p.y,
+           p.dbias, d_err};
     return BK == 64 ? launch_bn<64>(BN, mx, mw, a, n_sm, stream) : launch_bn<32>(BN, mx, mw, a, n_sm, stream);
 }
 
