@@ -289,7 +289,7 @@ ur_status ur_trace_adjoint(ur_ctx *ctx, uint64_t n_rays_per_tx, uint64_t seed, i
 typedef struct ur_nn ur_nn;
 
 /* Network for images of n_el x n_s (multiples of 8), up to max_batch frames,
- * width w in {32, 64} (w = 32: about 2M parameters), He-initialised from seed. */
+ * width w = 32 (widths 32-256, about 2M parameters), He-initialised from seed. */
 ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch, int n_el, int n_s, int width,
                        uint64_t seed);
 ur_status ur_nn_destroy(ur_nn *nn);

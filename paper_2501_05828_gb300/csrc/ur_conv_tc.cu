@@ -180,7 +180,11 @@ struct Args {
     const bf16 *mask;
     bf16 *y;
     float *dbias;   // nullable: += column sums of the output over all pixels
+    bf16 *y2;       // nullable: output columns [c_split, Cout) go to y2 (and [0, c_split) to y)
+    int c_split;
     int *err;
+    int has_head;   // kx-fused kernel with BN = 32: the residual head in the epilogue
+    HeadTC head;
 };
 
 // Sum over the 32 lanes of each of the 32 values v[j]; lane l ends with the total of
@@ -198,6 +202,13 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
         }
     }
     return v[0];
+}
+
+// Destination of output columns co .. co + 31 of pixel pix: y, or, when the output is split,
+// y [pix][c_split] for the first c_split columns and y2 [pix][Cout - c_split] for the rest.
+__device__ __forceinline__ bf16 *out_cols(const Args &a, size_t pix, int co) {
+    if (!a.y2) return a.y + pix * a.Cout + co;
+    return co < a.c_split ? a.y + pix * a.c_split + co : a.y2 + pix * (a.Cout - a.c_split) + (co - a.c_split);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                             }
                         }
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + co);
+                    uint4 *dst = reinterpret_cast<uint4 *>(out_cols(a, pix, co));
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         uint4 o;
@@ -410,7 +421,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 
 // ------------------------------------------------------------------ kx-fused convolution
 //
-// For C_out = BN in {32, 64}: a stage holds the input pixels x0 - 1 .. x0 + 128 of row
+// For C_out = BN in {32, 64, 96}: a stage holds the input pixels x0 - 1 .. x0 + 128 of row
 // y + ky - 1 (130 rows of BK channels) and the weights of the three kx taps of kernel row ky
 // (consecutive rows 3 ky C_out .. of the weight view [9 C_out][C_in]).  Tap kx reads the
 // A operand from row kx of the staged tile: the tensor core applies the swizzle from the
@@ -434,8 +445,8 @@ struct KxCfg {
     static constexpr int B_BYTES = NB * ROW;
     static constexpr int A_PAD = (A_BYTES + 1023) / 1024 * 1024;
     static constexpr int B_PAD = (B_BYTES + 1023) / 1024 * 1024;
-    static constexpr int ACC_COLS = BN;
-    static constexpr int TMEM_COLS = 2 * ACC_COLS;         // double-buffered
+    static constexpr int TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;   // double-buffered, a power of 2
+    static constexpr int ACC_COLS = TMEM_COLS / 2;          // accumulator stride (BN columns used)
     static constexpr int N_BARS = 2 * kKxMaxStages + 5;    // full, empty, acc_full[2], acc_empty[2], weights
     static constexpr int TAIL = 8 * N_BARS + 16;           // barriers and the TMEM address slot
     // shared memory of a launch: alignment slack, resident weights, stages, tail
@@ -500,7 +511,8 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                 mbar_expect_tx(wfull, (uint32_t)(nk * K::B_BYTES));
                 for (int kt = 0; kt < nk; ++kt) {
                     const int ky = kt / kc, c0 = (kt - ky * kc) * BK;
-                    tma_load_2d(sW + (uint32_t)(kt * K::B_PAD), &tmw, c0, 3 * ky * BN, wfull);
+                    for (int kx = 0; kx < 3; ++kx)   // boxes of BN rows (a box is at most 256 rows)
+                        tma_load_2d(sW + (uint32_t)(kt * K::B_PAD + kx * BN * K::ROW), &tmw, c0, (3 * ky + kx) * BN, wfull);
                 }
             }
             int it = 0, s = 0;
@@ -517,7 +529,10 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                     const uint32_t sa = sS + (uint32_t)s * stage;
                     mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + (wres ? 0 : K::B_BYTES)));
                     tma_load_4d(sa, &tmx, c0, x0 - 1, y + ky - 1, n, full0 + 8 * s);
-                    if (!wres) tma_load_2d(sa + K::A_PAD, &tmw, c0, 3 * ky * BN, full0 + 8 * s);
+                    if (!wres)
+                        for (int kx = 0; kx < 3; ++kx)
+                            tma_load_2d(sa + K::A_PAD + (uint32_t)(kx * BN * K::ROW), &tmw, c0, (3 * ky + kx) * BN,
+                                        full0 + 8 * s);
                     if (++s == S) {
                         s = 0;
                         ph ^= 1u;
@@ -575,6 +590,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
         float dsum[BN / 32];
 #pragma unroll
         for (int c = 0; c < BN / 32; ++c) dsum[c] = 0.f;
+        float hloss = 0.f, hb0 = 0.f, hb1 = 0.f, hw0 = 0.f, hw1 = 0.f;   // residual head (training)
         int i = 0;
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
             const int b = i & 1;
@@ -626,7 +642,47 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                             }
                         }
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + pix * a.Cout + c);
+                }
+                if (BN == 32 && a.has_head) {   // residual head on the BF16-rounded activations
+                    const HeadTC &hd = a.head;
+                    float g0 = 0.f, g1 = 0.f;
+                    if (in) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+                        float s0 = hd.bh[0] + hd.xn[2 * pix], s1 = hd.bh[1] + hd.xn[2 * pix + 1];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            s0 += hd.wh[j] * v[j];
+                            s1 += hd.wh[32 + j] * v[j];
+                        }
+                        if (hd.out_rf) {
+                            hd.out_rf[pix] = s0 * hd.scale;
+                            hd.out_quad[pix] = s1 * hd.scale;
+                        }
+                        if (hd.t_rf) {   // squared error and its gradient at the head's output
+                            const float d0 = s0 - hd.t_rf[pix] * hd.inv_scale, d1 = s1 - hd.t_quad[pix] * hd.inv_scale;
+                            hloss += d0 * d0 + d1 * d1;
+                            g0 = 2.f * d0 * hd.inv_n;
+                            g1 = 2.f * d1 * hd.inv_n;
+                            hb0 += g0;
+                            hb1 += g1;
+                        }
+                    }
+                    if (hd.t_rf) {   // head weight gradients (column sums over the warp's pixels), then the
+                                     // gradient at the ReLU output replaces the activations
+                        float t[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) t[j] = g0 * v[j];
+                        hw0 += warp_transpose_sum(t, lane);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) t[j] = g1 * v[j];
+                        hw1 += warp_transpose_sum(t, lane);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = v[j] > 0.f ? g0 * hd.wh[j] + g1 * hd.wh[32 + j] : 0.f;
+                    }
+                }
+                if (in && !(BN == 32 && a.has_head && !a.head.t_rf)) {   // inference with the head stores nothing
+                    uint4 *dst = reinterpret_cast<uint4 *>(out_cols(a, pix, c));
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         uint4 o4;
@@ -650,6 +706,20 @@ __global__ void __launch_bounds__(kConvThreads, 2)
         if (a.dbias)
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c) atomicAdd(a.dbias + 32 * c + lane, dsum[c]);
+        if (BN == 32 && a.has_head && a.head.t_rf) {
+            atomicAdd(a.head.dwh + lane, hw0);
+            atomicAdd(a.head.dwh + 32 + lane, hw1);
+            for (int off = 16; off > 0; off >>= 1) {
+                hloss += __shfl_down_sync(0xffffffffu, hloss, off);
+                hb0 += __shfl_down_sync(0xffffffffu, hb0, off);
+                hb1 += __shfl_down_sync(0xffffffffu, hb1, off);
+            }
+            if (lane == 0) {
+                atomicAdd(a.head.loss, (double)(hloss * a.head.inv_n));
+                atomicAdd(a.head.dbh, hb0);
+                atomicAdd(a.head.dbh + 1, hb1);
+            }
+        }
     }
     if (!ok) atomicExch(a.err, 1);
     tc_fence_before();
@@ -675,8 +745,13 @@ __global__ void __launch_bounds__(kConvThreads, 2)
 // KX (9 taps; C_out tiles of BN in {32, 64}): with q = p + (0, kx - 1),
 // dW[3 ky + kx] = sum_q x[q + (ky - 1, 0)] dy[q - (0, kx - 1)], so the rows are
 // (ky, ci) from input boxes shifted by rows only and the N = 3 BN columns are
-// (kx, co) from three dy boxes shifted by -(kx - 1) pixels: each input row is
-// read once per kernel row instead of once per tap.
+// (kx, co) from dy shifted by -(kx - 1) pixels: each input row is read once per
+// kernel row instead of once per tap.  The three shifts come from one box of
+// kWK + 2 pixels x BN channels (dy at x0 - 1 .. x0 + kWK): in the MN-major
+// layout a pixel is one BN-channel row of the box, so column block j = 2 - kx
+// starts j rows into it and the B descriptor's leading byte offset (the stride
+// between its BN-column blocks) is one pixel row.  The tensor core swizzles from
+// the shared-memory address bits, so the shifted blocks read the rows TMA wrote.
 constexpr int kWK = 64;                 // pixels per K step
 constexpr int kChunk = 32 * kWK * 2;    // one 32-channel x 64-pixel box: 4 KB
 
@@ -685,19 +760,33 @@ __device__ __forceinline__ uint64_t sdesc_mn64(uint32_t addr) {
            (1ull << 46) | (4ull << 61);
 }
 
+// B operand of the KX weight gradient: pixel rows of ROW = 2 BN bytes (64-byte swizzle for
+// BN = 32, 128-byte for BN = 64), 8-pixel K groups 8 ROW apart, BN-column blocks one row apart.
+template <int BN>
+__device__ __forceinline__ uint64_t sdesc_mn_shift(uint32_t addr) {
+    constexpr uint32_t ROW = 2 * BN;
+    constexpr uint64_t layout = BN == 64 ? 2ull : 4ull;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(ROW >> 4) << 16) | ((uint64_t)((8 * ROW) >> 4) << 32) |
+           (1ull << 46) | (layout << 61);
+}
+
 template <int BN>
 __host__ __device__ constexpr uint32_t idesc_bf16_mn() {
     return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(BN >> 3) << 17) |
            ((uint32_t)(kBM >> 4) << 24);
 }
 
-template <int BN>
+// BN: C_out tile; KX: the fused-kx form (MMA N = 3 BN, one shifted dy box per stage).
+template <int BN, bool KX>
 struct WCfg {
+    static constexpr int NB = KX ? 3 * BN : BN;   // MMA N
     static constexpr int A_BYTES = 4 * kChunk;
-    static constexpr int B_BYTES = (BN / 32) * kChunk;
-    static constexpr int S_RAW = (BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
+    static constexpr int B_TX = KX ? (kWK + 2) * BN * 2 : (BN / 32) * kChunk;   // bytes the B boxes deliver
+    static constexpr int B_BYTES = (B_TX + 1023) / 1024 * 1024;                    // their stage slot
+    // KX: two CTAs per SM, so one CTA's epilogue overlaps the other's main loop
+    static constexpr int S_RAW = (!KX && BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
     static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 6 ? 6 : S_RAW);
-    static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = NB <= 32 ? 32 : NB <= 64 ? 64 : NB <= 128 ? 128 : 256;
     static constexpr int SMEM = S * (A_BYTES + B_BYTES) + 1024 + 8 * (2 * S + 1) + 16;
 };
 
@@ -710,8 +799,8 @@ struct WArgs {
 template <int BN, bool KX>
 __global__ void __launch_bounds__(kThreads, 1)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmd, const WArgs a) {
-    constexpr int NB = KX ? 3 * BN : BN;   // MMA N
-    using K = WCfg<NB>;
+    using K = WCfg<BN, KX>;
+    constexpr int NB = K::NB;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = s_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -750,7 +839,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0 && nk > 0) {   // TMA producer
             int issued = 0;
-            const uint32_t bytes = (uint32_t)(n_groups * kChunk + K::B_BYTES);
+            const uint32_t bytes = (uint32_t)(n_groups * kChunk + K::B_TX);
             for (int kt = 0; kt < nk; ++kt) {
                 const int st = kt % K::S;
                 if (!mbar_wait(empty0 + 8 * st, ((uint32_t)(kt / K::S) & 1u) ^ 1u, deadline)) {
@@ -776,11 +865,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tma_load_4d(sA + st * K::A_BYTES + g * kChunk, &tmx, ci0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * st);
                 }
-                if (KX) {   // column chunks (kx, co block): dy shifted by -(kx - 1) pixels
-                    for (int kx = 0; kx < 3; ++kx)
-                        for (int c = 0; c < BN / 32; ++c)
-                            tma_load_4d(sB + st * K::B_BYTES + (kx * (BN / 32) + c) * kChunk, &tmd, co0 + 32 * c,
-                                        x0 - kx + 1, y, n, full0 + 8 * st);
+                if (KX) {   // dy at pixels x0 - 1 .. x0 + kWK: the three kx shifts are rows 2 - kx on
+                    tma_load_4d(sB + st * K::B_BYTES, &tmd, co0, x0 - 1, y, n, full0 + 8 * st);
                 } else {
                     for (int c = 0; c < BN / 32; ++c)
                         tma_load_4d(sB + st * K::B_BYTES + c * kChunk, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
@@ -804,8 +890,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t a0 = sA + st * K::A_BYTES, b0 = sB + st * K::B_BYTES;
 #pragma unroll
-                for (int k = 0; k < kWK / 16; ++k)   // 16 pixels = two 8-row K groups = 1 KB
-                    mma_bf16(tmem, sdesc_mn64(a0 + 1024 * k), sdesc_mn64(b0 + 1024 * k), idesc, (kt | k) != 0);
+                for (int k = 0; k < kWK / 16; ++k) {   // 16 pixels: two 8-row K groups
+                    const uint64_t bd = KX ? sdesc_mn_shift<BN>(b0 + (uint32_t)(16 * 2 * BN * k)) : sdesc_mn64(b0 + 1024 * k);
+                    mma_bf16(tmem, sdesc_mn64(a0 + 1024 * k), bd, idesc, (kt | k) != 0);
+                }
                 mma_commit(empty0 + 8 * st);
             }
             mma_commit(accb);
@@ -823,7 +911,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < NB; c += 32) {
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            const int tap = KX ? 3 * tr + c / BN : tr;   // KX: row = ky, column block = (kx, co)
+            const int tap = KX ? 3 * tr + 2 - c / BN : tr;   // KX: row = ky, column block j = 2 - kx
             const int co = co0 + (KX ? c % BN : c);
             float *dst = a.dw + ((size_t)tap * a.Cout + co) * a.Cin + ci;
 #pragma unroll
@@ -966,7 +1054,11 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
     if (p.C < 32 || p.C % 32 || BN == 0 || (p.taps != 9 && p.taps != 1) || p.N < 1 || p.H < 1 || p.W < 1 || !p.x || !p.w || !p.y || !d_err ||
         (reinterpret_cast<uintptr_t>(p.x) & 15) || (reinterpret_cast<uintptr_t>(p.w) & 15) ||
         (reinterpret_cast<uintptr_t>(p.y) & 15) || (p.bias && (reinterpret_cast<uintptr_t>(p.bias) & 15)) ||
-        (p.mask && (reinterpret_cast<uintptr_t>(p.mask) & 15))) {
+        (p.mask && (reinterpret_cast<uintptr_t>(p.mask) & 15)) ||
+        (p.y2 && ((reinterpret_cast<uintptr_t>(p.y2) & 15) || p.c_split <= 0 || p.c_split >= p.Cout || p.c_split % 32)) ||
+        (p.head && (p.Cout != 32 || p.taps != 9 || !p.relu || p.mask || p.y2 || !p.head->xn || !p.head->wh ||
+                    !p.head->bh || (!p.head->out_rf != !p.head->out_quad) || (!p.head->t_rf != !p.head->t_quad) ||
+                    (p.head->t_rf && (!p.head->loss || !p.head->dwh || !p.head->dbh))))) {
         if (why) *why = "conv3x3_tc: unsupported shape or alignment";
         return cudaErrorInvalidValue;
     }
@@ -980,7 +1072,7 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
     {
         const cuuint64_t dims[4] = {(cuuint64_t)p.C, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.N};
         const cuuint64_t strides[3] = {(cuuint64_t)p.C * 2, (cuuint64_t)p.W * p.C * 2, (cuuint64_t)p.H * p.W * p.C * 2};
-        const bool kx = p.taps == 9 && (p.Cout == 32 || p.Cout == 64);   // kx-fused: 130 staged input pixels
+        const bool kx = p.taps == 9 && (p.Cout == 32 || p.Cout == 64 || p.Cout == 96);   // kx-fused: 130 staged pixels
         const cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)(kx ? kKxRows : kBM), 1, 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
         const CUresult r = enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(p.x), dims, strides, box, es,
@@ -1004,11 +1096,11 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
             return cudaErrorInvalidValue;
         }
     }
-    if (p.taps == 9 && (p.Cout == 32 || p.Cout == 64)) {   // kx taps fused into one N = 3 C_out MMA
+    if (p.taps == 9 && (p.Cout == 32 || p.Cout == 64 || p.Cout == 96)) {   // kx taps from row-shifted stages
         alignas(64) CUtensorMap mw2;
         const cuuint64_t dims[2] = {(cuuint64_t)p.C, 9ull * p.Cout};
         const cuuint64_t strides[1] = {(cuuint64_t)p.C * 2};
-        const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(3 * p.Cout)};
+        const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)p.Cout};
         const cuuint32_t es[2] = {1, 1};
         if (enc(&mw2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(p.w), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1022,8 +1114,14 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
             if (why) *why = "conv3x3_tc: too many tiles";
             return cudaErrorInvalidValue;
         }
-        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, 0, 0, p.bias, p.mask, p.y, p.dbias, d_err};
+        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, 0, 0, p.bias, p.mask, p.y, p.dbias,
+               p.y2, p.c_split, d_err};
+        if (p.head) {
+            a.has_head = 1;
+            a.head = *p.head;
+        }
         if (p.Cout == 32) return BK == 64 ? launch_kx<32, 64>(mx, mw2, a, n_sm, stream) : launch_kx<32, 32>(mx, mw2, a, n_sm, stream);
+        if (p.Cout == 96) return BK == 64 ? launch_kx<96, 64>(mx, mw2, a, n_sm, stream) : launch_kx<96, 32>(mx, mw2, a, n_sm, stream);
         return BK == 64 ? launch_kx<64, 64>(mx, mw2, a, n_sm, stream) : launch_kx<64, 32>(mx, mw2, a, n_sm, stream);
     }
     const int nxb = (p.W + kBM - 1) / kBM;
@@ -1033,7 +1131,7 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
         return cudaErrorInvalidValue;
     }
     Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, 0, 0, p.bias, p.mask, p.y,
-           p.dbias, d_err};
+           p.dbias, p.y2, p.c_split, d_err};
     return BK == 64 ? launch_bn<64>(BN, mx, mw, a, n_sm, stream) : launch_bn<32>(BN, mx, mw, a, n_sm, stream);
 }
 
@@ -1041,8 +1139,11 @@ namespace {
 
 template <int BN, bool KX>
 cudaError_t launch_w(const CUtensorMap &mx, const CUtensorMap &md, const WArgs &a, dim3 grid, cudaStream_t stream) {
-    using K = WCfg<KX ? 3 * BN : BN>;
+    using K = WCfg<BN, KX>;
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e == cudaSuccess)   // all of the unified L1/shared array as shared memory: two CTAs per SM
+        e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     k_wgrad_tc<BN, KX><<<grid, kThreads, K::SMEM, stream>>>(mx, md, a);
     return cudaGetLastError();
@@ -1074,23 +1175,42 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
         if (why) *why = "cuTensorMapEncodeTiled is not available from the driver";
         return cudaErrorNotSupported;
     }
+    const bool kx = p.taps == 9;   // C_out tiles of 32 (C_out = 32) or 64 columns x 3 taps
+    const int kx_bn = p.Cout == 32 ? 32 : 64;
     alignas(64) CUtensorMap mx, md;
-    if (!encode_nhwc(enc, &mx, p.x, p.Cin, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B) ||
-        !encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B)) {
+    const bool md_ok = kx ? encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, kx_bn, kWK + 2,
+                                        kx_bn == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B)
+                          : encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (!encode_nhwc(enc, &mx, p.x, p.Cin, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B) || !md_ok) {
         if (why) *why = "wgrad3x3_tc: tensor map rejected";
         return cudaErrorInvalidValue;
     }
     const int nxb = (p.W + kWK - 1) / kWK;
     const long long steps = (long long)p.N * p.H * nxb;
-    const bool kx = p.taps == 9;   // C_out tiles of 32 (C_out = 32) or 64 columns x 3 taps
-    const int kx_bn = p.Cout == 32 ? 32 : 64;
     const int m_tiles = ((kx ? 3 : p.taps) * p.Cin + kBM - 1) / kBM;
     if (steps > 0x7fffffffll) {
         if (why) *why = "wgrad3x3_tc: too many pixels";
         return cudaErrorInvalidValue;
     }
-    // about eight waves of CTAs, at least 8 K steps each
-    const long long target = 8ll * (n_sm > 0 ? n_sm : 148);
+    int smem = 0;
+    switch (kx ? kx_bn : 1000 + BN) {
+        case 32: smem = WCfg<32, true>::SMEM; break;
+        case 64: smem = WCfg<64, true>::SMEM; break;
+        case 1032: smem = WCfg<32, false>::SMEM; break;
+        case 1064: smem = WCfg<64, false>::SMEM; break;
+        case 1128: smem = WCfg<128, false>::SMEM; break;
+        default: smem = WCfg<256, false>::SMEM; break;
+    }
+    int dev = 0, smem_sm = 0, reserve = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
+        return e;
+    // one wave of CTAs (as many as fit on the SMs at once), each a long run of K steps down the
+    // image rows, at least 8: partial tiles are added once per CTA
+    const int occ = std::max(1, std::min(2, smem_sm / (smem + reserve)));
+    const long long target = (long long)occ * (n_sm > 0 ? n_sm : 148);
     const int n_tiles = kx ? p.Cout / kx_bn : 1;
     long long splits = std::max<long long>(1, target / ((long long)m_tiles * n_tiles));
     splits = std::min<long long>(splits, std::max<long long>(1, steps / 8));

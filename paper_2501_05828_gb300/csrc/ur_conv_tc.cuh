@@ -9,6 +9,23 @@
 
 namespace urnn {
 
+// Residual 1x1 head (32 -> 2 channels) evaluated in the epilogue of a 32-channel convolution
+// with ReLU: y = xn + Wh a + bh on the BF16-rounded activations a.  Inference writes y (times
+// scale) and stores no activations; training (t_rf set) adds the mean squared error against
+// the targets to loss, the head's parameter gradients to dwh / dbh, and stores the gradient at
+// the ReLU output (masked by a > 0) in place of the activations, with its column sums added to
+// the convolution's dbias.
+struct HeadTC {
+    const float *xn;                 // [P][2] normalised input (the residual)
+    const float *wh, *bh;            // [2][32], [2]
+    float scale;                     // output scale
+    float *out_rf, *out_quad;        // [P] or null
+    const float *t_rf, *t_quad;      // [P] targets (training) or null
+    float inv_scale, inv_n;          // target normalisation; 1 / (2 P)
+    double *loss;                    // += sum of squared differences x inv_n
+    float *dwh, *dbh;                // += head gradients
+};
+
 struct ConvTC {
     const __nv_bfloat16 *x;      // input, NHWC [N][H][W][C], C a multiple of 32
     int C, N, H, W;
@@ -20,6 +37,10 @@ struct ConvTC {
     __nv_bfloat16 *y;            // output NHWC [N][H][W][Cout]
     int relu;                    // max(0, .) after the bias
     float *dbias = nullptr;      // [Cout] or null: += sum over pixels of the (masked) output, FP32
+    __nv_bfloat16 *y2 = nullptr; // or null; else the output is split: channels [0, c_split) go to y
+    int c_split = 0;             // ([N][H][W][c_split]) and [c_split, Cout) to y2 ([N][H][W][Cout - c_split]);
+                                 // c_split a multiple of 32
+    const HeadTC *head = nullptr; // or null; C_out = 32, 9 taps, ReLU only
 };
 
 // Enqueues the convolution on `stream`.  `d_err` (device int) receives a

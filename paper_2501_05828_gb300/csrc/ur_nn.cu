@@ -183,14 +183,15 @@ __device__ __forceinline__ void flush_channel_sums(float (&acc)[8], int G, float
     }
 }
 
-// Gradient of a concatenated decoder input [B][H][W][C1 + C2], first part: the C1
-// channels came from the nearest-upsampled half-resolution tensor, so dlow (half
-// resolution) is the sum over each 2x2 block; it is the gradient at the lower
-// level's last ReLU output, so it is masked by that activation `act` here and
-// its column sums (that layer's bias gradient) go to db.
-__global__ void __launch_bounds__(256) k_unconcat_low(const bf16 *dcat, int B, int H, int W, int C1, int C2,
-                                                      Div32 dWo, Div32 dHo, const bf16 *act, bf16 *dlow, float *db) {
-    const int Ho = H / 2, Wo = W / 2, G1 = C1 / 8, G = (C1 + C2) / 8;
+// Gradient of a concatenated decoder input, first part ([B][H][W][C1]; the data-gradient
+// convolution writes the skip channels straight to their own gradient): the C1 channels
+// came from the nearest-upsampled half-resolution tensor, so dlow (half resolution) is the
+// sum over each 2x2 block; it is the gradient at the lower level's last ReLU output, so it
+// is masked by that activation `act` here and its column sums (that layer's bias gradient)
+// go to db.
+__global__ void __launch_bounds__(256) k_unconcat_low(const bf16 *dcat, int B, int H, int W, int C1, Div32 dWo,
+                                                      Div32 dHo, const bf16 *act, bf16 *dlow, float *db) {
+    const int Ho = H / 2, Wo = W / 2, G1 = C1 / 8, G = G1;
     const int gi = threadIdx.x % G1, lanes = blockDim.x / G1, pl = threadIdx.x / G1;
     const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
     const uint4 *ag = reinterpret_cast<const uint4 *>(act);
@@ -219,18 +220,6 @@ __global__ void __launch_bounds__(256) k_unconcat_low(const bf16 *dcat, int B, i
         reinterpret_cast<uint4 *>(dlow)[(size_t)p * G1 + gi] = pack8(v);
     }
     flush_channel_sums(acc, G1, db);
-}
-
-// Second part: the skip channels [C1, C1 + C2), copied.
-__global__ void k_unconcat_skip(const bf16 *dcat, int B, int H, int W, int C1, int C2, Div32 dG2, bf16 *dskip) {
-    const int G1 = C1 / 8, G2 = C2 / 8, G = G1 + G2;
-    const uint4 *dg = reinterpret_cast<const uint4 *>(dcat);
-    GRID_STRIDE32(j, (uint32_t)B * H * W * G2) {
-        uint32_t gu;
-        const uint32_t p = divmod32(j, dG2, gu);
-        const int g = (int)gu;
-        reinterpret_cast<uint4 *>(dskip)[j] = dg[(size_t)p * G + G1 + g];
-    }
 }
 
 // d[b, y, x, c] += dp[b, y/2, x/2, c] / 4 (gradient of 2x2 average pooling); the sum is
@@ -271,93 +260,6 @@ __global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
         const int ci = (int)(r % Cin);
         const int tap = (int)(r / Cin);
         wt[i] = w[((size_t)(8 - tap) * Cout + co) * Cin + ci];
-    }
-}
-
-// Residual head: y = x + W d1 + b (1x1, C -> 2), fp32; also writes the output
-// back in the tracer's layout, rescaled.
-__global__ void k_head_fwd(const bf16 *d1, const float *xn, const float *wh, const float *bh, int C, long long P,
-                           float scale, float *yn, float *out_rf, float *out_quad) {
-    const int G = C / 8;
-    const uint4 *fg = reinterpret_cast<const uint4 *>(d1);
-    GRID_STRIDE(p, P) {
-        float s0 = bh[0] + xn[2 * p], s1 = bh[1] + xn[2 * p + 1];
-        for (int g = 0; g < G; ++g) {
-            float v[8];
-            unpack8(fg[(size_t)p * G + g], v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                s0 += wh[8 * g + j] * v[j];
-                s1 += wh[C + 8 * g + j] * v[j];
-            }
-        }
-        yn[2 * p] = s0;
-        yn[2 * p + 1] = s1;
-        if (out_rf) {
-            out_rf[p] = s0 * scale;
-            out_quad[p] = s1 * scale;
-        }
-    }
-}
-
-// Mean squared error against the (normalised) target and its gradient.
-__global__ void k_loss(const float *yn, const float *t_rf, const float *t_quad, long long P, float inv_scale,
-                       float *g, double *loss) {
-    const float inv_n = 1.f / (2.f * (float)P);
-    float local = 0.f;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const float d0 = yn[2 * p] - t_rf[p] * inv_scale, d1 = yn[2 * p + 1] - t_quad[p] * inv_scale;
-        local += d0 * d0 + d1 * d1;
-        g[2 * p] = 2.f * d0 * inv_n;
-        g[2 * p + 1] = 2.f * d1 * inv_n;
-    }
-    for (int off = 16; off > 0; off >>= 1) local += __shfl_down_sync(0xffffffffu, local, off);
-    if ((threadIdx.x & 31) == 0 && local != 0.f) atomicAdd(loss, (double)(local * inv_n));
-}
-
-// Head backward: dWh, dbh (fp32), the gradient at d1 (= d1b's ReLU output) masked
-// by d1 > 0 (bf16), and d1b's bias gradient (its column sums).  Thread t owns
-// channels 8 (t % G) .. +8 of every (256 / G)-th pixel.
-__global__ void __launch_bounds__(256) k_head_bwd(const float *g, const bf16 *d1, const float *wh, int C, long long P,
-                                                  float *dwh, float *dbh, bf16 *dd1, float *db1) {
-    const int G = C / 8, gi = threadIdx.x % G, lanes = blockDim.x / G, pl = threadIdx.x / G;
-    float w0[8], w1[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        w0[j] = wh[8 * gi + j];
-        w1[j] = wh[C + 8 * gi + j];
-    }
-    float a0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, a1[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float sb[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float b0 = 0.f, b1 = 0.f;
-    const uint4 *fg = reinterpret_cast<const uint4 *>(d1);
-    for (long long p = (long long)blockIdx.x * lanes + pl; p < P; p += (long long)gridDim.x * lanes) {
-        const float2 gg = reinterpret_cast<const float2 *>(g)[p];
-        if (gi == 0) {
-            b0 += gg.x;
-            b1 += gg.y;
-        }
-        float v[8], o[8];
-        unpack8(fg[(size_t)p * G + gi], v);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            a0[j] += gg.x * v[j];
-            a1[j] += gg.y * v[j];
-            o[j] = v[j] > 0.f ? gg.x * w0[j] + gg.y * w1[j] : 0.f;
-            sb[j] += o[j];
-        }
-        reinterpret_cast<uint4 *>(dd1)[(size_t)p * G + gi] = pack8(o);
-    }
-    flush_channel_sums(a0, G, dwh);
-    flush_channel_sums(a1, G, dwh + C);
-    flush_channel_sums(sb, G, db1);
-    for (int off = 16; off > 0; off >>= 1) {
-        b0 += __shfl_down_sync(0xffffffffu, b0, off);
-        b1 += __shfl_down_sync(0xffffffffu, b1, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (b0 != 0.f) atomicAdd(&dbh[0], b0);
-        if (b1 != 0.f) atomicAdd(&dbh[1], b1);
     }
 }
 
@@ -422,7 +324,7 @@ struct ur_nn {
     bf16 *pbf = nullptr, *wt = nullptr;   // bf16 copies; transposed weights scratch
     // activations and gradients
     bf16 *x = nullptr;
-    float *xn = nullptr, *yn = nullptr, *gy = nullptr;
+    float *xn = nullptr;
     Tensor act[kNumConv];    // post-ReLU outputs of every conv
     Tensor pool[3];          // pooled e1, e2, e3
     // training buffers (allocated by the first training step), in units of B*H*W*C BF16 values:
@@ -467,8 +369,9 @@ ur_status nn_guard(ur_nn *nn, F &&f) {
 }
 
 void conv_fwd(ur_nn *nn, const bf16 *x, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
-              const bf16 *mask, bf16 *y, bool relu, int taps = 9, float *dbias = nullptr) {
-    urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0, dbias};
+              const bf16 *mask, bf16 *y, bool relu, int taps = 9, float *dbias = nullptr, bf16 *y2 = nullptr,
+              int c_split = 0, const urnn::HeadTC *head = nullptr) {
+    urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0, dbias, y2, c_split, head};
     std::string why;
     ++nn->launches;
     const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
@@ -574,7 +477,11 @@ const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
     return cat;
 }
 
-void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad) {
+// Forward pass; the residual head runs in the last convolution's epilogue.  Inference writes
+// out_rf / out_quad; training (t_rf, t_quad) adds the loss and the head's gradients and leaves
+// the gradient at d1b's ReLU output (masked, bias sums added) in gA instead of d1b's output.
+void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf, float *out_quad,
+             const float *t_rf = nullptr, const float *t_quad = nullptr) {
     const long long P = (long long)B * nn->H * nn->W;
     ++nn->launches;
     k_prep<<<grid_for(P), 256, 0, nn->stream>>>(rf, quad, B, nn->H, nn->W, make_div32((uint32_t)nn->W),
@@ -586,12 +493,20 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
     for (int l = 0; l < kNumConv; ++l) {
         const Layer L = layer_in(nn, l);
         const bf16 *in = conv_input(nn, B, l, true);
-        if (l == 0)   // neighbourhood already in the 32 input channels: one tap
+        if (l == 0) {   // neighbourhood already in the 32 input channels: one tap
             conv_fwd(nn, in, B, L.H, L.W, 32, nn->cout[0], nn->wfirst, nn->params + nn->boff[0], nullptr, nn->act[0].p,
                      true, 1);
-        else
+        } else if (l == kNumConv - 1) {   // d1b with the residual head (and the loss) in its epilogue
+            const urnn::HeadTC h{nn->xn, nn->params + nn->hw_off, nn->params + nn->hb_off, nn->scale, out_rf, out_quad,
+                                 t_rf, t_quad, 1.f / nn->scale, 1.f / (2.f * (float)P), nn->loss,
+                                 nn->grads + nn->hw_off, nn->grads + nn->hb_off};
+            conv_fwd(nn, in, B, L.H, L.W, nn->cin[l], nn->cout[l], nn->pbf + nn->woff[l], nn->params + nn->boff[l],
+                     nullptr, t_rf ? nn->gA : nn->act[l].p, true, 9, t_rf ? nn->grads + nn->boff[l] : nullptr, nullptr,
+                     0, &h);
+        } else {
             conv_fwd(nn, in, B, L.H, L.W, nn->cin[l], nn->cout[l], nn->pbf + nn->woff[l], nn->params + nn->boff[l],
                      nullptr, nn->act[l].p, true);
+        }
         if (l == 1 || l == 3 || l == 5) {   // pool after each encoder block
             const int q = l / 2;
             ++nn->launches;
@@ -601,17 +516,14 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
             ck(cudaGetLastError(), "pool kernel");
         }
     }
-    ++nn->launches;
-    k_head_fwd<<<grid_for(P), 256, 0, nn->stream>>>(nn->act[13].p, nn->xn, nn->params + nn->hw_off,
-                                                    nn->params + nn->hb_off, nn->width, P, nn->scale,
-                                                    nn->yn, out_rf, out_quad);
-    ck(cudaGetLastError(), "head kernel");
 }
 
 // Backward of one block (convs la, lb) given the gradient at lb's output, already
 // masked by lb's ReLU with lb's bias gradient summed by the kernel that produced it;
-// leaves the gradient of la's input in `din` (full concatenated channels) if din.
-void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din) {
+// leaves the gradient of la's input in `din` if din; for a decoder block (dskip) the
+// input's first c1 channels (upsampled lower level) go to din and the rest to dskip.
+void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf16 *din, bf16 *dskip = nullptr,
+               int c1 = 0) {
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
     conv_wgrad(nn, nn->act[la].p, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
     ++nn->launches;
@@ -634,21 +546,19 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
         ++nn->launches;
         k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
                                                                                       nn->cout[la], nn->cin[la]);
-        conv_fwd(nn, scratch, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din, false);
+        conv_fwd(nn, scratch, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din, false, 9, nullptr,
+                 dskip, c1);
     }
     ck(cudaGetLastError(), "block backward");
 }
 
-// gcat (gradient of a decoder input at H x W) -> gLow (masked by act[l_low], bias sums of
-// layer l_low) and dskip.
-void unconcat(ur_nn *nn, int B, int H, int W, int C1, int C2, int l_low, bf16 *dskip) {
+// gcat (gradient of the upsampled part of a decoder input, [B][H][W][C1]) -> gLow (masked
+// by act[l_low], bias sums of layer l_low).
+void unconcat(ur_nn *nn, int B, int H, int W, int C1, int l_low) {
     ++nn->launches;
     k_unconcat_low<<<channel_grid((long long)B * (H / 2) * (W / 2), C1), 256, 0, nn->stream>>>(
-        nn->gcat, B, H, W, C1, C2, make_div32((uint32_t)(W / 2)), make_div32((uint32_t)(H / 2)), nn->act[l_low].p,
+        nn->gcat, B, H, W, C1, make_div32((uint32_t)(W / 2)), make_div32((uint32_t)(H / 2)), nn->act[l_low].p,
         nn->gLow, nn->grads + nn->boff[l_low]);
-    ++nn->launches;
-    k_unconcat_skip<<<grid_for((long long)B * H * W * C2 / 8), 256, 0, nn->stream>>>(
-        nn->gcat, B, H, W, C1, C2, make_div32((uint32_t)(C2 / 8)), dskip);
     ck(cudaGetLastError(), "unconcat");
 }
 
@@ -663,7 +573,6 @@ void pool_bwd(ur_nn *nn, int B, int H, int W, int C, int l, bf16 *d) {
 void ensure_train_buffers(ur_nn *nn) {
     if (nn->gA) return;
     const size_t B = nn->max_batch, H = nn->H, W = nn->W, C = nn->width, unit = B * H * W * C;
-    nn->gy = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
     nn->gA = (bf16 *)nn->alloc(sizeof(bf16) * unit);
     nn->gB = (bf16 *)nn->alloc(sizeof(bf16) * unit);
     nn->gcat = (bf16 *)nn->alloc(sizeof(bf16) * 3 * unit);
@@ -673,29 +582,21 @@ void ensure_train_buffers(ur_nn *nn) {
 
 double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *t_rf, const float *t_quad) {
     ensure_train_buffers(nn);
-    forward(nn, B, rf, quad, nullptr, nullptr);
-    const long long P = (long long)B * nn->H * nn->W;
     ck(cudaMemsetAsync(nn->loss, 0, sizeof(double), nn->stream), "memset loss");
     ck(cudaMemsetAsync(nn->grads, 0, sizeof(float) * nn->n_params, nn->stream), "memset grads");
-    ++nn->launches;
-    k_loss<<<grid_for(P), 256, 0, nn->stream>>>(nn->yn, t_rf, t_quad, P, 1.f / nn->scale, nn->gy, nn->loss);
+    // forward with the loss, the head's gradients and the gradient at d1b's output (gA); every
+    // block's incoming gradient below arrives masked by its ReLU with its bias gradient summed
+    forward(nn, B, rf, quad, nullptr, nullptr, t_rf, t_quad);
     const int C = nn->width;
-    // head
-    float *gb = nn->grads;
-    // head; every block's incoming gradient below arrives masked by its ReLU with its bias gradient summed
-    ++nn->launches;
-    k_head_bwd<<<channel_grid(P, C), 256, 0, nn->stream>>>(nn->gy, nn->act[13].p, nn->params + nn->hw_off, C, P,
-                                                           gb + nn->hw_off, gb + nn->hb_off, nn->gA, gb + nn->boff[13]);
-    ck(cudaGetLastError(), "head backward");
     const int H = nn->H, W = nn->W;
     // decoder level 1: input concat(up(d2), e1)
-    block_bwd(nn, B, 12, 13, nn->gA, nn->gB, nn->gcat);
-    unconcat(nn, B, H, W, 2 * C, C, 11, nn->gSkip[0]);
+    block_bwd(nn, B, 12, 13, nn->gA, nn->gB, nn->gcat, nn->gSkip[0], 2 * C);
+    unconcat(nn, B, H, W, 2 * C, 11);
     // decoder level 2: the gradient of d2 (half resolution) is gLow
-    block_bwd(nn, B, 10, 11, nn->gLow, nn->gB, nn->gcat);
-    unconcat(nn, B, H / 2, W / 2, 4 * C, 2 * C, 9, nn->gSkip[1]);
-    block_bwd(nn, B, 8, 9, nn->gLow, nn->gB, nn->gcat);
-    unconcat(nn, B, H / 4, W / 4, 8 * C, 4 * C, 7, nn->gSkip[2]);
+    block_bwd(nn, B, 10, 11, nn->gLow, nn->gB, nn->gcat, nn->gSkip[1], 4 * C);
+    unconcat(nn, B, H / 2, W / 2, 4 * C, 9);
+    block_bwd(nn, B, 8, 9, nn->gLow, nn->gB, nn->gcat, nn->gSkip[2], 8 * C);
+    unconcat(nn, B, H / 4, W / 4, 8 * C, 7);
     // bottleneck: the gradient of e4 is gLow; encoder blocks leave d(pooled input) in gcat
     block_bwd(nn, B, 6, 7, nn->gLow, nn->gB, nn->gcat);
     pool_bwd(nn, B, H / 4, W / 4, 4 * C, 5, nn->gSkip[2]);
@@ -735,8 +636,8 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
     ur_nn *nn = new (std::nothrow) ur_nn();
     if (!nn) return UR_ERR_OOM;
     ur_status st = nn_guard(nn, [&] {
-        if (max_batch < 1 || max_batch > 64 || n_el < 8 || n_s < 8 || n_el % 8 || n_s % 8 || (width != 32 && width != 64))
-            fail(UR_ERR_INVALID_ARG, "need 1 <= batch <= 64, n_el and n_s multiples of 8, width 32 or 64");
+        if (max_batch < 1 || max_batch > 64 || n_el < 8 || n_s < 8 || n_el % 8 || n_s % 8 || width != 32)
+            fail(UR_ERR_INVALID_ARG, "need 1 <= batch <= 64, n_el and n_s multiples of 8, width 32");
         // the elementwise kernels index 16-byte granules of the largest activation (3 width
         // channels at full resolution) and pixels with 32-bit integers
         if ((uint64_t)max_batch * (uint64_t)n_el * (uint64_t)n_s * 3ull * (uint64_t)width / 8ull >= (1ull << 32))
@@ -813,7 +714,6 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         }
         nn->x = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 32);
         nn->xn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
-        nn->yn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
         for (int q = 0; q < 3; ++q)   // d3a: [H/4][W/4][12C], d2a: [H/2][W/2][6C], d1a: [H][W][3C]
             nn->cat[q] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> (2 - q)) * (W >> (2 - q)) * (12 * C >> q));
         nn->wfirst = (bf16 *)nn->alloc(sizeof(bf16) * 32 * C);
