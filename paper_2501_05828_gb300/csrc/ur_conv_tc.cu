@@ -81,6 +81,18 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+// Row of a half-resolution tensor that nearest upsampling maps to full-resolution row yy (>= -1).
+__device__ __forceinline__ int low_row(int yy) { return yy >= 0 ? yy >> 1 : -1; }
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -176,6 +188,7 @@ struct Cfg {
 struct Args {
     int N, H, W, C, Cout, nxb, relu, taps, n_tiles, n_ntiles;
     int stages, wres;   // kx-fused kernel: input stages per CTA, weights resident in shared memory
+    int rows, nyb;      // kx-fused kernel: output rows per tile (several only with resident weights), row blocks
     const float *bias;
     const bf16 *mask;
     bf16 *y;
@@ -185,6 +198,7 @@ struct Args {
     int *err;
     int has_head;   // kx-fused kernel with BN = 32: the residual head in the epilogue
     HeadTC head;
+    int c1;         // kx-fused kernel: input channels [0, c1) from the upsampled half-resolution map
 };
 
 // Sum over the 32 lanes of each of the 32 values v[j]; lane l ends with the total of
@@ -429,6 +443,17 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 // into a tile written by TMA still reads the rows TMA wrote there.  The three taps accumulate
 // into one accumulator of 128 output pixels, and the input is read once per kernel row instead
 // of once per tap; the epilogue is the plain one (bias, ReLU, mask, BF16 store).
+//
+// Row-stacked tiles (BN in {32, 64} when the weights fit): a tile is R = 128 / BN output rows
+// y .. y + R - 1, their accumulators side by side (N = R BN = 128 columns).  Input row y - 1 + r
+// (r = 0 .. R + 1) contributes to output row y + o with kernel row ky = r - o, so one MMA with
+// N = 128 adds it to all R output rows if its B operand is the stack W(ky = r), W(r - 1), ...,
+// W(r - R + 1) of BN-row weight blocks, zero where ky is outside 0..2.  The resident weights of a
+// channel chunk hold, per kx, the blocks W(2), W(1), W(0) between runs of R - 1 zero blocks
+// (shared by neighbouring kx), so every such stack is one contiguous run of blocks.  An input row
+// is staged (R + 2) / R times per output row instead of 3, and each staged row costs 3 BK / 16
+// MMAs of N = 128 instead of up to 3 x 3 BK / 16 of N = BN (the tensor core re-reads the A
+// operand for every MMA).
 constexpr int kKxRows = kBM + 2;   // staged input pixels per kernel row
 
 // Weights: when all 3 kc blocks of one C_out tile fit beside a few input stages they are
@@ -443,12 +468,19 @@ struct KxCfg {
     static constexpr int NB = 3 * BN;                      // weight rows per block: the three kx taps
     static constexpr int A_BYTES = kKxRows * ROW;
     static constexpr int B_BYTES = NB * ROW;
-    static constexpr int A_PAD = (A_BYTES + 1023) / 1024 * 1024;
+    static constexpr int A_PAD = (A_BYTES + 2 * ROW + 1023) / 1024 * 1024;   // room for 132 upsampled rows
     static constexpr int B_PAD = (B_BYTES + 1023) / 1024 * 1024;
-    static constexpr int TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;   // double-buffered, a power of 2
-    static constexpr int ACC_COLS = TMEM_COLS / 2;          // accumulator stride (BN columns used)
+    static constexpr int MAX_ROWS = 128 / BN;              // output rows per tile: R BN <= 128 columns
+    static constexpr int TMEM_COLS = 256;                  // two accumulator sets of 128 columns
+    static constexpr int ACC_COLS = 128;
     static constexpr int N_BARS = 2 * kKxMaxStages + 5;    // full, empty, acc_full[2], acc_empty[2], weights
     static constexpr int TAIL = 8 * N_BARS + 16;           // barriers and the TMEM address slot
+    static constexpr int BLK = BN * ROW;                    // one BN-row weight block
+    // row-stacked weights of one channel chunk: R - 1 zero blocks, then per kx W(2), W(1), W(0) and R - 1 zero blocks
+    __host__ __device__ static constexpr int stacked_blocks(int R) { return (R - 1) + 3 * (R + 2); }
+    __host__ __device__ static constexpr int stacked_bytes(int R) { return (stacked_blocks(R) * BLK + 1023) / 1024 * 1024; }
+    // block index of W(ky = 2) of kx in the stacked layout
+    __host__ __device__ static constexpr int stacked_w2(int R, int kx) { return (R - 1) + kx * (R + 2); }
     // shared memory of a launch: alignment slack, resident weights, stages, tail
     static int smem(int kc, bool wres, int stages) {
         return 1024 + (wres ? 3 * kc * B_PAD : 0) + stages * (A_PAD + (wres ? 0 : B_PAD)) + TAIL;
@@ -457,7 +489,8 @@ struct KxCfg {
 
 template <int BN, int BK>
 __global__ void __launch_bounds__(kConvThreads, 2)
-    k_conv_kx(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, const Args a) {
+    k_conv_kx(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+              const __grid_constant__ CUtensorMap tml, const Args a) {
     using K = KxCfg<BN, BK>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = s_addr(smem_raw);
@@ -466,7 +499,9 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const int kc = a.C / BK, nk = 3 * kc;   // stages per tile: kernel rows x channel chunks
     const bool wres = a.wres != 0;
     const int S = a.stages;
-    const uint32_t w_bytes = wres ? (uint32_t)(3 * kc * K::B_PAD) : 0u;
+    const int R = a.rows;   // R > 1: row-stacked tile (resident stacked weights)
+    const uint32_t wb_stk = R > 1 ? (uint32_t)K::stacked_bytes(R) : 0u;   // stacked weights per channel chunk
+    const uint32_t w_bytes = R > 1 ? (uint32_t)kc * wb_stk : wres ? (uint32_t)(3 * kc * K::B_PAD) : 0u;
     const uint32_t stage = (uint32_t)(K::A_PAD + (wres ? 0 : K::B_PAD));
     const uint32_t sW = base, sS = base + w_bytes;   // resident weights; stage s: A at sS + s stage, then B
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + w_bytes + (uint32_t)S * stage);
@@ -477,6 +512,17 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t deadline = now_ns() + kWaitNs;
 
+    if (R > 1) {   // the zero blocks of the stacked weights, written before the tensor core reads them
+        const int zb = R - 1, per = 4 * zb * K::BLK / 16;   // 16-byte words of zeros per channel chunk
+        for (int i = threadIdx.x; i < kc * per; i += blockDim.x) {
+            const int cc = i / per, w = i - cc * per;
+            const int run = w / (zb * K::BLK / 16), off = w - run * (zb * K::BLK / 16);   // run 0: leading zeros
+            const int blk0 = run == 0 ? 0 : K::stacked_w2(R, run - 1) + 3;
+            uint4 *dst = reinterpret_cast<uint4 *>(sm + (size_t)cc * wb_stk + (size_t)blk0 * K::BLK) + off;
+            *dst = make_uint4(0u, 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -497,17 +543,24 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
     bool ok = true;
 
-    auto decode = [&](int t, int &n, int &y, int &x0) {
+    auto decode = [&](int t, int &n, int &y, int &x0) {   // y: the tile's first output row
         const int xb = t % a.nxb;
         const int m = t / a.nxb;
-        y = m % a.H;
-        n = m / a.H;
+        y = (m % a.nyb) * R;
+        n = m / a.nyb;
         x0 = xb * kBM;
     };
 
     if (warp == 0) {
         if (lane == 0) {   // TMA producer
-            if (wres) {    // every weight block once: block kt = (ky, channel chunk) at sW + kt B_PAD
+            if (R > 1) {   // stacked: W(ky) of (chunk, kx) at block stacked_w2(kx) + 2 - ky of the chunk
+                mbar_expect_tx(wfull, (uint32_t)(kc * 9 * K::BLK));
+                for (int cc = 0; cc < kc; ++cc)
+                    for (int kx = 0; kx < 3; ++kx)
+                        for (int ky = 0; ky < 3; ++ky)
+                            tma_load_2d(sW + (uint32_t)cc * wb_stk + (uint32_t)((K::stacked_w2(R, kx) + 2 - ky) * K::BLK),
+                                        &tmw, cc * BK, (3 * ky + kx) * BN, wfull);
+            } else if (wres) {   // every weight block once: block kt = (ky, channel chunk) at sW + kt B_PAD
                 mbar_expect_tx(wfull, (uint32_t)(nk * K::B_BYTES));
                 for (int kt = 0; kt < nk; ++kt) {
                     const int ky = kt / kc, c0 = (kt - ky * kc) * BK;
@@ -517,18 +570,24 @@ __global__ void __launch_bounds__(kConvThreads, 2)
             }
             int it = 0, s = 0;
             uint32_t ph = 0;
+            const int nr = (R + 2) * kc;   // stages per tile: input rows x channel chunks
             for (int t = blockIdx.x; t < a.n_tiles && ok; t += gridDim.x) {
                 int n, y, x0;
                 decode(t, n, y, x0);
-                for (int kt = 0; kt < nk; ++kt, ++it) {
+                for (int kt = 0; kt < nr; ++kt, ++it) {
                     if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, deadline)) {
                         ok = false;
                         break;
                     }
-                    const int ky = kt / kc, c0 = (kt - ky * kc) * BK;
+                    const int ky = kt / kc, c0 = (kt - ky * kc) * BK;   // ky: input row y - 1 + ky (= kernel row if R = 1)
                     const uint32_t sa = sS + (uint32_t)s * stage;
-                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(K::A_BYTES + (wres ? 0 : K::B_BYTES)));
-                    tma_load_4d(sa, &tmx, c0, x0 - 1, y + ky - 1, n, full0 + 8 * s);
+                    const bool low = c0 < a.c1;   // upsampled chunk: 132 pixels from x0 - 2, each low pixel twice
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)((low ? K::A_BYTES + 2 * K::ROW : K::A_BYTES) +
+                                                             (wres ? 0 : K::B_BYTES)));
+                    if (low)
+                        tma_load_5d(sa, &tml, c0, 0, x0 / 2 - 1, low_row(y + ky - 1), n, full0 + 8 * s);
+                    else
+                        tma_load_4d(sa, &tmx, c0 - a.c1, x0 - 1, y + ky - 1, n, full0 + 8 * s);
                     if (!wres)
                         for (int kx = 0; kx < 3; ++kx)
                             tma_load_2d(sa + K::A_PAD + (uint32_t)(kx * BN * K::ROW), &tmw, c0, (3 * ky + kx) * BN,
@@ -549,6 +608,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
             constexpr uint32_t idesc = idesc_bf16<BN>();
+            constexpr uint32_t idesc_stk = idesc_bf16<128>();   // row-stacked: R BN = 128 columns
             if (wres && !mbar_wait(wfull, 0u, deadline)) ok = false;
             int i = 0, s = 0;
             uint32_t ph = 0;
@@ -560,21 +620,37 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * K::ACC_COLS);
-                for (int kt = 0; kt < nk; ++kt) {
+                const int nr = (R + 2) * kc;
+                for (int kt = 0; kt < nr; ++kt) {
                     if (!mbar_wait(full0 + 8 * s, ph, deadline)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = sS + (uint32_t)s * stage;
-                    const uint32_t b0 = wres ? sW + (uint32_t)(kt * K::B_PAD) : a0 + K::A_PAD;
+                    const int r = kt / kc, kcc = kt - r * kc;   // staged input row y - 1 + r, channel chunk kcc
+                    // stage row i is pixel x0 - 1 + i, or x0 - 2 + i for an upsampled chunk
+                    const uint32_t st0 = sS + (uint32_t)s * stage;
+                    const uint32_t a0 = st0 + (kcc * BK < a.c1 ? (uint32_t)K::ROW : 0u);
+                    if (R > 1) {   // one N = 128 MMA per tap column and K slice: all R output rows at once
+                        const uint32_t wc = sW + (uint32_t)kcc * wb_stk;
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)   // output pixel x0 + r reads input row r + kx of the stage
+                        for (int kx = 0; kx < 3; ++kx) {
+                            const uint32_t b0 = wc + (uint32_t)((K::stacked_w2(R, kx) + 2 - r) * K::BLK);
 #pragma unroll
-                        for (int k = 0; k < BK / 16; ++k)
-                            mma_bf16(d, sdesc(a0 + (uint32_t)(kx * K::ROW) + 32 * k, K::ROW),
-                                     sdesc(b0 + (uint32_t)(kx * BN * K::ROW) + 32 * k, K::ROW), idesc,
-                                     (kt | kx | k) != 0);
+                            for (int k = 0; k < BK / 16; ++k)
+                                mma_bf16(d, sdesc(a0 + (uint32_t)(kx * K::ROW) + 32 * k, K::ROW),
+                                         sdesc(b0 + 32 * k, K::ROW), idesc_stk, (kt | kx | k) != 0);
+                        }
+                    } else {
+                        const uint32_t b0 = wres ? sW + (uint32_t)((r * kc + kcc) * K::B_PAD) : st0 + K::A_PAD;
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx)   // output pixel x0 + i reads input row i + kx of the stage
+#pragma unroll
+                            for (int k = 0; k < BK / 16; ++k)
+                                mma_bf16(d, sdesc(a0 + (uint32_t)(kx * K::ROW) + 32 * k, K::ROW),
+                                         sdesc(b0 + (uint32_t)(kx * BN * K::ROW) + 32 * k, K::ROW), idesc,
+                                         (kt | kx | k) != 0);
+                    }
                     mma_commit(empty0 + 8 * s);
                     if (++s == S) {
                         s = 0;
@@ -592,23 +668,39 @@ __global__ void __launch_bounds__(kConvThreads, 2)
         for (int c = 0; c < BN / 32; ++c) dsum[c] = 0.f;
         float hloss = 0.f, hb0 = 0.f, hb1 = 0.f, hw0 = 0.f, hw1 = 0.f;   // residual head (training)
         int i = 0;
+        constexpr int HR = BN == 32 ? K::MAX_ROWS : 1;   // rows of head inputs fetched per tile
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
             const int b = i & 1;
+            int n, y0, x0;
+            decode(t, n, y0, x0);
+            const int x = x0 + q * 32 + lane;
+            const bool in = x < a.W;
+            // the head's per-pixel inputs of every row of the tile, requested before the accumulator wait
+            float2 hx[HR], ht[HR];
+            if (BN == 32 && a.has_head) {
+#pragma unroll
+                for (int o = 0; o < HR; ++o) {
+                    hx[o] = ht[o] = make_float2(0.f, 0.f);
+                    if (o < R && y0 + o < a.H && in) {
+                        const size_t p = ((size_t)n * a.H + y0 + o) * a.W + x;
+                        hx[o] = reinterpret_cast<const float2 *>(a.head.xn)[p];
+                        if (a.head.t_rf) ht[o] = make_float2(a.head.t_rf[p], a.head.t_quad[p]);
+                    }
+                }
+            }
             const bool ready = mbar_wait(accf0 + 8 * b, (uint32_t)(i >> 1) & 1u, deadline);
             if (__all_sync(0xffffffffu, ready) == 0) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            int n, y, x0;
-            decode(t, n, y, x0);
-            const int x = x0 + q * 32 + lane;
-            const bool in = x < a.W;
-            const size_t pix = ((size_t)n * a.H + y) * a.W + x;
+#pragma unroll 1
+            for (int o = 0; o < R && y0 + o < a.H; ++o) {   // output row y0 + o: accumulator columns o BN ..
+            const size_t pix = ((size_t)n * a.H + y0 + o) * a.W + x;
 #pragma unroll
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+                tmem_ld32(tmem + (uint32_t)(b * K::ACC_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)(o * BN + c), r);
                 float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = in ? __uint_as_float(r[j]) : 0.f;
@@ -649,7 +741,14 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                     if (in) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-                        float s0 = hd.bh[0] + hd.xn[2 * pix], s1 = hd.bh[1] + hd.xn[2 * pix + 1];
+                        float2 xo = hx[0], to = ht[0];   // row o's inputs (selected, not indexed: registers)
+#pragma unroll
+                        for (int u = 1; u < HR; ++u)
+                            if (o == u) {
+                                xo = hx[u];
+                                to = ht[u];
+                            }
+                        float s0 = hd.bh[0] + xo.x, s1 = hd.bh[1] + xo.y;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             s0 += hd.wh[j] * v[j];
@@ -660,7 +759,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                             hd.out_quad[pix] = s1 * hd.scale;
                         }
                         if (hd.t_rf) {   // squared error and its gradient at the head's output
-                            const float d0 = s0 - hd.t_rf[pix] * hd.inv_scale, d1 = s1 - hd.t_quad[pix] * hd.inv_scale;
+                            const float d0 = s0 - to.x * hd.inv_scale, d1 = s1 - to.y * hd.inv_scale;
                             hloss += d0 * d0 + d1 * d1;
                             g0 = 2.f * d0 * hd.inv_n;
                             g1 = 2.f * d1 * hd.inv_n;
@@ -699,6 +798,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                 }
                 if (a.dbias) dsum[c / 32] += warp_transpose_sum(v, lane);
             }
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * b);
@@ -735,8 +835,9 @@ __global__ void __launch_bounds__(kConvThreads, 2)
 // dW[tap][co][ci] = sum_p dy[p][co] x[p + offset(tap)][ci] as D = A B^T with
 // M = (tap, ci) rows, N = co, K = pixels.  Both operands are read MN-major from
 // the NHWC tensors: a K step is 64 consecutive pixels of one image row; A is
-// made of four 32-row groups, each the TMA box of the tap-shifted input for 32
-// input channels (zero padding from the out-of-bounds fill), B of BN/32 boxes
+// made of three or four 32-row groups (the MMA's other rows are not read back),
+// each the TMA box of the tap-shifted input for 32 input channels (zero padding
+// from the out-of-bounds fill), B of BN/32 boxes
 // of dy.  Boxes are 64 pixels x 32 channels with 64-byte swizzle: 32-element
 // MN chunks 4 KB apart (leading byte offset), 8-pixel K groups 512 B apart
 // (stride byte offset).  K is split across CTAs; partial tiles are added into
@@ -783,8 +884,9 @@ struct WCfg {
     static constexpr int A_BYTES = 4 * kChunk;
     static constexpr int B_TX = KX ? (kWK + 2) * BN * 2 : (BN / 32) * kChunk;   // bytes the B boxes deliver
     static constexpr int B_BYTES = (B_TX + 1023) / 1024 * 1024;                    // their stage slot
-    // KX: two CTAs per SM, so one CTA's epilogue overlaps the other's main loop
-    static constexpr int S_RAW = (!KX && BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
+    // KX: two CTAs per SM (stages within half the SM's shared memory), so one CTA's epilogue
+    // overlaps the other's main loop
+    static constexpr int S_RAW = (KX ? 110 * 1024 : BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
     static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 6 ? 6 : S_RAW);
     static constexpr int TMEM_COLS = NB <= 32 ? 32 : NB <= 64 ? 64 : NB <= 128 ? 128 : 256;
     static constexpr int SMEM = S * (A_BYTES + B_BYTES) + 1024 + 8 * (2 * S + 1) + 16;
@@ -792,13 +894,16 @@ struct WCfg {
 
 struct WArgs {
     int N, H, W, Cin, Cout, taps, nxb, steps, per_split;
+    int gpt;   // 32-row groups per M tile (3 or 4)
     float *dw;
     int *err;
+    int c1;   // input channels [0, c1) from the upsampled half-resolution map
 };
 
 template <int BN, bool KX>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmd, const WArgs a) {
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmd,
+               const __grid_constant__ CUtensorMap tml, const WArgs a) {
     using K = WCfg<BN, KX>;
     constexpr int NB = K::NB;
     extern __shared__ uint8_t smem_raw[];
@@ -812,8 +917,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int rows = (KX ? 3 : a.taps) * a.Cin;
-    const int r0 = blockIdx.x * kBM;
-    const int n_groups = min(4, (rows - r0) / 32);
+    const int r0 = blockIdx.x * 32 * a.gpt;
+    const int n_groups = min(a.gpt, (rows - r0) / 32);
     const int co0 = blockIdx.y * BN;
     const int s_begin = blockIdx.z * a.per_split;
     const int s_end = min(a.steps, s_begin + a.per_split);
@@ -863,7 +968,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ky = a.taps == 1 ? 1 : tap / 3;
                         kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
                     }
-                    tma_load_4d(sA + st * K::A_BYTES + g * kChunk, &tmx, ci0, x0 + kx - 1, y + ky - 1, n, full0 + 8 * st);
+                    if (ci0 < a.c1)   // upsampled: 32 low pixels, each twice (kx = 1 here: no pixel shift)
+                        tma_load_5d(sA + st * K::A_BYTES + g * kChunk, &tml, ci0, 0, x0 / 2, low_row(y + ky - 1), n,
+                                    full0 + 8 * st);
+                    else
+                        tma_load_4d(sA + st * K::A_BYTES + g * kChunk, &tmx, ci0 - a.c1, x0 + kx - 1, y + ky - 1, n,
+                                    full0 + 8 * st);
                 }
                 if (KX) {   // dy at pixels x0 - 1 .. x0 + kWK: the three kx shifts are rows 2 - kx on
                     tma_load_4d(sB + st * K::B_BYTES, &tmd, co0, x0 - 1, y, n, full0 + 8 * st);
@@ -982,7 +1092,8 @@ cudaError_t ctas_per_sm(KernelT kernel, int smem, int tmem_cols, int *occ) {
 // overlap), with resident weights when two input stages fit beside them, else with the weights
 // streamed with the input; one CTA per SM only when neither fits.
 template <int BN, int BK>
-cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, Args a, int n_sm, cudaStream_t stream) {
+cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, const CUtensorMap &ml, Args a, int n_sm,
+                      cudaStream_t stream) {
     using K = KxCfg<BN, BK>;
     int dev = 0, smem_sm = 0, reserve = 0, optin = 0;
     cudaError_t e;
@@ -992,28 +1103,49 @@ cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, Args a, int 
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
     const int kc = a.C / BK, two = smem_sm / 2 - reserve;
-    auto fit = [&](int budget, bool w) {
-        const int n = (budget - K::smem(kc, w, 0)) / (K::A_PAD + (w ? 0 : K::B_PAD));
-        return std::min(n, kKxMaxStages);
-    };
+    // Row-stacked tiles (R = 128 / BN output rows) when the stacked weights and three input stages
+    // fit twice per SM (at one CTA per SM they were slower than single-row tiles at two, measured
+    // on the denoiser's layers).  Otherwise one output row per tile with the weights resident (two
+    // CTAs per SM, else one) or streamed with each stage.
+    int R = 1, stages = 0, smem = 0;
     bool wres = true;
-    int stages = fit(two, true);
-    if (stages < 2) {
-        wres = false;
-        stages = fit(two, false);
+    if (K::MAX_ROWS > 1) {
+        const int fixed = 1024 + kc * K::stacked_bytes(K::MAX_ROWS) + K::TAIL;
+        const int n = std::min((two - fixed) / K::A_PAD, kKxMaxStages);
+        if (n >= 3) {
+            R = K::MAX_ROWS;
+            stages = n;
+            smem = fixed + n * K::A_PAD;
+        }
     }
-    if (stages < 2) {
-        wres = true;
-        stages = fit(optin, true);
+    if (R == 1) {
+        auto fit = [&](int budget, bool w) {
+            const int n = (budget - K::smem(kc, w, 0)) / (K::A_PAD + (w ? 0 : K::B_PAD));
+            return std::min(n, kKxMaxStages);
+        };
+        stages = fit(two, true);
+        if (stages < 2) {
+            wres = false;
+            stages = fit(two, false);
+        }
+        if (stages < 2) {
+            wres = true;
+            stages = fit(optin, true);
+        }
+        if (stages < 2) {
+            wres = false;
+            stages = fit(optin, false);
+        }
+        if (stages < 2) return cudaErrorInvalidValue;
+        smem = K::smem(kc, wres, stages);
     }
-    if (stages < 2) {
-        wres = false;
-        stages = fit(optin, false);
-    }
-    if (stages < 2) return cudaErrorInvalidValue;
     a.stages = stages;
     a.wres = wres ? 1 : 0;
-    const int smem = K::smem(kc, wres, stages);
+    a.rows = R;
+    a.nyb = (a.H + R - 1) / R;
+    const long long row_tiles = (long long)a.N * a.nxb;
+    if (row_tiles * a.nyb > 0x7fffffffll) return cudaErrorInvalidValue;
+    a.n_tiles = (int)(row_tiles * a.nyb);
     e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv_kx<BN, BK>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1022,7 +1154,7 @@ cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, Args a, int 
     if (e == cudaSuccess) e = ctas_per_sm(k_conv_kx<BN, BK>, smem, K::TMEM_COLS, &occ);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long long>(a.n_tiles, (long long)occ * std::max(1, n_sm));
-    k_conv_kx<BN, BK><<<grid, kConvThreads, smem, stream>>>(mx, mw, a);
+    k_conv_kx<BN, BK><<<grid, kConvThreads, smem, stream>>>(mx, mw, ml, a);
     return cudaGetLastError();
 }
 
@@ -1058,7 +1190,10 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
         (p.y2 && ((reinterpret_cast<uintptr_t>(p.y2) & 15) || p.c_split <= 0 || p.c_split >= p.Cout || p.c_split % 32)) ||
         (p.head && (p.Cout != 32 || p.taps != 9 || !p.relu || p.mask || p.y2 || !p.head->xn || !p.head->wh ||
                     !p.head->bh || (!p.head->out_rf != !p.head->out_quad) || (!p.head->t_rf != !p.head->t_quad) ||
-                    (p.head->t_rf && (!p.head->loss || !p.head->dwh || !p.head->dbh))))) {
+                    (p.head->t_rf && (!p.head->loss || !p.head->dwh || !p.head->dbh)))) ||
+        (p.x_low && (p.taps != 9 || !(p.Cout == 32 || p.Cout == 64 || p.Cout == 96) || (p.H | p.W) & 1 ||
+                     p.c1 <= 0 || p.c1 >= p.C || p.c1 % BK || (p.C - p.c1) % BK ||
+                     (reinterpret_cast<uintptr_t>(p.x_low) & 15)))) {
         if (why) *why = "conv3x3_tc: unsupported shape or alignment";
         return cudaErrorInvalidValue;
     }
@@ -1068,10 +1203,11 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
         return cudaErrorNotSupported;
     }
     const CUtensorMapSwizzle sw = BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-    alignas(64) CUtensorMap mx, mw;
+    alignas(64) CUtensorMap mx, mw, mlow;
     {
-        const cuuint64_t dims[4] = {(cuuint64_t)p.C, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.N};
-        const cuuint64_t strides[3] = {(cuuint64_t)p.C * 2, (cuuint64_t)p.W * p.C * 2, (cuuint64_t)p.H * p.W * p.C * 2};
+        const int cx = p.x_low ? p.C - p.c1 : p.C;   // channels of x itself
+        const cuuint64_t dims[4] = {(cuuint64_t)cx, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.N};
+        const cuuint64_t strides[3] = {(cuuint64_t)cx * 2, (cuuint64_t)p.W * cx * 2, (cuuint64_t)p.H * p.W * cx * 2};
         const bool kx = p.taps == 9 && (p.Cout == 32 || p.Cout == 64 || p.Cout == 96);   // kx-fused: 130 staged pixels
         const cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)(kx ? kKxRows : kBM), 1, 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
@@ -1080,6 +1216,20 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             if (why) *why = "tensor map of the convolution input rejected (" + std::to_string((int)r) + ")";
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (p.x_low) {   // (c, repeat 2 with stride 0, x / 2, y / 2, n): a box of 66 low pixels gives 132 upsampled rows
+        const int c1 = p.c1, wl = p.W / 2, hl = p.H / 2;
+        const cuuint64_t dims[5] = {(cuuint64_t)c1, 2, (cuuint64_t)wl, (cuuint64_t)hl, (cuuint64_t)p.N};
+        const cuuint64_t strides[4] = {0, (cuuint64_t)c1 * 2, (cuuint64_t)wl * c1 * 2, (cuuint64_t)hl * wl * c1 * 2};
+        const cuuint32_t box[5] = {(cuuint32_t)BK, 2, (cuuint32_t)(kKxRows / 2 + 1), 1, 1};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        const CUresult r = enc(&mlow, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(p.x_low), dims, strides, box,
+                               es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            if (why) *why = "tensor map of the upsampled input rejected (" + std::to_string((int)r) + ")";
             return cudaErrorInvalidValue;
         }
     }
@@ -1114,15 +1264,19 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
             if (why) *why = "conv3x3_tc: too many tiles";
             return cudaErrorInvalidValue;
         }
-        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, 0, 0, p.bias, p.mask, p.y, p.dbias,
+        Args a{p.N, p.H, p.W, p.C, p.Cout, nxk, p.relu, p.taps, (int)nt, 1, 0, 0, 1, p.H, p.bias, p.mask, p.y, p.dbias,
                p.y2, p.c_split, d_err};
         if (p.head) {
             a.has_head = 1;
             a.head = *p.head;
         }
-        if (p.Cout == 32) return BK == 64 ? launch_kx<32, 64>(mx, mw2, a, n_sm, stream) : launch_kx<32, 32>(mx, mw2, a, n_sm, stream);
-        if (p.Cout == 96) return BK == 64 ? launch_kx<96, 64>(mx, mw2, a, n_sm, stream) : launch_kx<96, 32>(mx, mw2, a, n_sm, stream);
-        return BK == 64 ? launch_kx<64, 64>(mx, mw2, a, n_sm, stream) : launch_kx<64, 32>(mx, mw2, a, n_sm, stream);
+        a.c1 = p.x_low ? p.c1 : 0;
+        const CUtensorMap &ml = p.x_low ? mlow : mx;
+        if (p.Cout == 32)
+            return BK == 64 ? launch_kx<32, 64>(mx, mw2, ml, a, n_sm, stream) : launch_kx<32, 32>(mx, mw2, ml, a, n_sm, stream);
+        if (p.Cout == 96)
+            return BK == 64 ? launch_kx<96, 64>(mx, mw2, ml, a, n_sm, stream) : launch_kx<96, 32>(mx, mw2, ml, a, n_sm, stream);
+        return BK == 64 ? launch_kx<64, 64>(mx, mw2, ml, a, n_sm, stream) : launch_kx<64, 32>(mx, mw2, ml, a, n_sm, stream);
     }
     const int nxb = (p.W + kBM - 1) / kBM;
     const long long n_tiles = (long long)p.N * p.H * nxb * (p.Cout / BN);
@@ -1130,7 +1284,7 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
         if (why) *why = "conv3x3_tc: too many tiles";
         return cudaErrorInvalidValue;
     }
-    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, 0, 0, p.bias, p.mask, p.y,
+    Args a{p.N, p.H, p.W, p.C, p.Cout, nxb, p.relu, p.taps, (int)n_tiles, p.Cout / BN, 0, 0, 1, p.H, p.bias, p.mask, p.y,
            p.dbias, p.y2, p.c_split, d_err};
     return BK == 64 ? launch_bn<64>(BN, mx, mw, a, n_sm, stream) : launch_bn<32>(BN, mx, mw, a, n_sm, stream);
 }
@@ -1138,14 +1292,15 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
 namespace {
 
 template <int BN, bool KX>
-cudaError_t launch_w(const CUtensorMap &mx, const CUtensorMap &md, const WArgs &a, dim3 grid, cudaStream_t stream) {
+cudaError_t launch_w(const CUtensorMap &mx, const CUtensorMap &md, const CUtensorMap &ml, const WArgs &a, dim3 grid,
+                     cudaStream_t stream) {
     using K = WCfg<BN, KX>;
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
     if (e == cudaSuccess)   // all of the unified L1/shared array as shared memory: two CTAs per SM
         e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    k_wgrad_tc<BN, KX><<<grid, kThreads, K::SMEM, stream>>>(mx, md, a);
+    k_wgrad_tc<BN, KX><<<grid, kThreads, K::SMEM, stream>>>(mx, md, ml, a);
     return cudaGetLastError();
 }
 
@@ -1166,7 +1321,9 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     const int BN = p.Cout <= 256 ? p.Cout : 0;
     if (p.Cin < 32 || p.Cin % 32 || (BN != 32 && BN != 64 && BN != 128 && BN != 256) || (p.taps != 9 && p.taps != 1) ||
         p.N < 1 || p.H < 1 || p.W < 1 || !p.x || !p.dy || !p.dw || !d_err || (reinterpret_cast<uintptr_t>(p.x) & 15) ||
-        (reinterpret_cast<uintptr_t>(p.dy) & 15)) {
+        (reinterpret_cast<uintptr_t>(p.dy) & 15) ||
+        (p.x_low && (p.taps != 9 || (p.H | p.W) & 1 || p.c1 <= 0 || p.c1 >= p.Cin || p.c1 % 32 ||
+                     (reinterpret_cast<uintptr_t>(p.x_low) & 15)))) {
         if (why) *why = "wgrad3x3_tc: unsupported shape or alignment";
         return cudaErrorInvalidValue;
     }
@@ -1177,17 +1334,35 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     const bool kx = p.taps == 9;   // C_out tiles of 32 (C_out = 32) or 64 columns x 3 taps
     const int kx_bn = p.Cout == 32 ? 32 : 64;
-    alignas(64) CUtensorMap mx, md;
+    alignas(64) CUtensorMap mx, md, mlow;
+    if (p.x_low) {   // (c, repeat 2 with stride 0, x / 2, y / 2, n): 32 low pixels give a 64-pixel box
+        const int c1 = p.c1, wl = p.W / 2, hl = p.H / 2;
+        const cuuint64_t dims[5] = {(cuuint64_t)c1, 2, (cuuint64_t)wl, (cuuint64_t)hl, (cuuint64_t)p.N};
+        const cuuint64_t strides[4] = {0, (cuuint64_t)c1 * 2, (cuuint64_t)wl * c1 * 2, (cuuint64_t)hl * wl * c1 * 2};
+        const cuuint32_t box[5] = {32, 2, (cuuint32_t)(kWK / 2), 1, 1};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&mlow, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(p.x_low), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            if (why) *why = "wgrad3x3_tc: tensor map of the upsampled input rejected";
+            return cudaErrorInvalidValue;
+        }
+    }
+    const int cx = p.x_low ? p.Cin - p.c1 : p.Cin;   // channels of x itself
     const bool md_ok = kx ? encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, kx_bn, kWK + 2,
                                         kx_bn == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B)
                           : encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B);
-    if (!encode_nhwc(enc, &mx, p.x, p.Cin, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B) || !md_ok) {
+    if (!encode_nhwc(enc, &mx, p.x, cx, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B) || !md_ok) {
         if (why) *why = "wgrad3x3_tc: tensor map rejected";
         return cudaErrorInvalidValue;
     }
     const int nxb = (p.W + kWK - 1) / kWK;
     const long long steps = (long long)p.N * p.H * nxb;
-    const int m_tiles = ((kx ? 3 : p.taps) * p.Cin + kBM - 1) / kBM;
+    // M tiles of 4 groups of 32 (tap, ci) rows, or of 3 where that gives as many tiles with equal
+    // work (96 input channels: three tiles of 96 rows instead of 128, 128 and 32)
+    const int groups = (kx ? 3 : p.taps) * p.Cin / 32;
+    const int gpt = (groups % 4 != 0 && groups % 3 == 0 && groups / 3 == (groups + 3) / 4) ? 3 : 4;
+    const int m_tiles = (groups + gpt - 1) / gpt;
     if (steps > 0x7fffffffll) {
         if (why) *why = "wgrad3x3_tc: too many pixels";
         return cudaErrorInvalidValue;
@@ -1207,8 +1382,8 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
         (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
         return e;
-    // one wave of CTAs (as many as fit on the SMs at once), each a long run of K steps down the
-    // image rows, at least 8: partial tiles are added once per CTA
+    // one wave of CTAs (as many as fit on the SMs at once), each a run of at least 8 K steps down
+    // the image rows: partial tiles are added once per CTA
     const int occ = std::max(1, std::min(2, smem_sm / (smem + reserve)));
     const long long target = (long long)occ * (n_sm > 0 ? n_sm : 148);
     const int n_tiles = kx ? p.Cout / kx_bn : 1;
@@ -1216,14 +1391,15 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     splits = std::min<long long>(splits, std::max<long long>(1, steps / 8));
     const int per = (int)((steps + splits - 1) / splits);
     splits = (steps + per - 1) / per;
-    WArgs a{p.N, p.H, p.W, p.Cin, p.Cout, p.taps, nxb, (int)steps, per, p.dw, d_err};
+    WArgs a{p.N, p.H, p.W, p.Cin, p.Cout, p.taps, nxb, (int)steps, per, gpt, p.dw, d_err, p.x_low ? p.c1 : 0};
+    const CUtensorMap &ml = p.x_low ? mlow : mx;
     const dim3 grid((unsigned)m_tiles, (unsigned)n_tiles, (unsigned)splits);
-    if (kx) return kx_bn == 32 ? launch_w<32, true>(mx, md, a, grid, stream) : launch_w<64, true>(mx, md, a, grid, stream);
+    if (kx) return kx_bn == 32 ? launch_w<32, true>(mx, md, ml, a, grid, stream) : launch_w<64, true>(mx, md, ml, a, grid, stream);
     switch (BN) {
-        case 32: return launch_w<32, false>(mx, md, a, grid, stream);
-        case 64: return launch_w<64, false>(mx, md, a, grid, stream);
-        case 128: return launch_w<128, false>(mx, md, a, grid, stream);
-        default: return launch_w<256, false>(mx, md, a, grid, stream);
+        case 32: return launch_w<32, false>(mx, md, ml, a, grid, stream);
+        case 64: return launch_w<64, false>(mx, md, ml, a, grid, stream);
+        case 128: return launch_w<128, false>(mx, md, ml, a, grid, stream);
+        default: return launch_w<256, false>(mx, md, ml, a, grid, stream);
     }
 }
 

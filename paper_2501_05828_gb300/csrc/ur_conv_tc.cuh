@@ -27,7 +27,7 @@ struct HeadTC {
 };
 
 struct ConvTC {
-    const __nv_bfloat16 *x;      // input, NHWC [N][H][W][C], C a multiple of 32
+    const __nv_bfloat16 *x;      // input, NHWC [N][H][W][C], C a multiple of 32 (see x_low)
     int C, N, H, W;
     const __nv_bfloat16 *w;      // weights [taps][Cout][C], tap = 3 ky + kx
     int Cout;                    // a multiple of 32
@@ -41,6 +41,11 @@ struct ConvTC {
     int c_split = 0;             // ([N][H][W][c_split]) and [c_split, Cout) to y2 ([N][H][W][Cout - c_split]);
                                  // c_split a multiple of 32
     const HeadTC *head = nullptr; // or null; C_out = 32, 9 taps, ReLU only
+    // Decoder input read from two tensors (9 taps, C_out in {32, 64, 96}, H and W even): channels
+    // [0, c1) are x_low [N][H/2][W/2][c1] upsampled 2x (nearest), channels [c1, C) are
+    // x [N][H][W][C - c1]; c1 a multiple of the channel chunk (64 if C % 64 == 0, else 32).
+    const __nv_bfloat16 *x_low = nullptr;
+    int c1 = 0;
 };
 
 // Enqueues the convolution on `stream`.  `d_err` (device int) receives a
@@ -54,11 +59,14 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
 // added into dw (the caller zeroes it).  taps = 1 uses the centre tap only and
 // writes dw[0][co][ci].
 struct WgradTC {
-    const __nv_bfloat16 *x;      // forward input NHWC [N][H][W][Cin]
+    const __nv_bfloat16 *x;      // forward input NHWC [N][H][W][Cin] (see x_low)
     int Cin, N, H, W;
     const __nv_bfloat16 *dy;     // gradient at the convolution's output NHWC [N][H][W][Cout], Cout in {32, 64, 128, 256}
     int Cout, taps;
     float *dw;                   // [taps][Cout][Cin]
+    // two-source input as in ConvTC (9 taps): channels [0, c1) from x_low upsampled, c1 % 32 == 0
+    const __nv_bfloat16 *x_low = nullptr;
+    int c1 = 0;
 };
 
 cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t stream, std::string *why);

@@ -5,8 +5,9 @@
 // Forward, data-gradient and weight-gradient convolutions run on the
 // 5th-generation tensor cores (TMA-fed tcgen05.mma with TMEM accumulators,
 // ur_conv_tc.cu).  Decoder inputs (nearest-neighbour upsampling of the lower
-// level concatenated with the skip tensor) are gathered into one NHWC buffer
-// before their convolution.
+// level concatenated with the skip tensor) are read by the convolutions from
+// the two tensors, the upsampling done by the tensor map; only the quarter-
+// resolution one is gathered into one NHWC buffer first.
 #include "ultraray.h"
 #include "ur_conv_tc.cuh"
 #include "ur_device.cuh"
@@ -331,7 +332,7 @@ struct ur_nn {
     // gA gradient at d1b's output (1), gB block scratch (1), gcat input gradient of a block (3),
     // gLow gradient of the half-resolution decoder input (1/2), gSkip skip-tensor gradients (1, 1/2, 1/4)
     bf16 *gcat = nullptr, *gA = nullptr, *gB = nullptr, *gSkip[3] = {nullptr, nullptr, nullptr}, *gLow = nullptr;
-    bf16 *cat[3] = {nullptr, nullptr, nullptr};   // decoder inputs (upsampled lower level ++ skip) of d3a, d2a, d1a
+    bf16 *cat[1] = {nullptr};   // decoder input (upsampled lower level ++ skip) of d3a
     bf16 *wfirst = nullptr;  // first convolution as one tap over the 32 neighbourhood channels [C][32]
     float *dwfirst = nullptr;
     double *loss = nullptr;
@@ -368,10 +369,18 @@ ur_status nn_guard(ur_nn *nn, F &&f) {
     }
 }
 
-void conv_fwd(ur_nn *nn, const bf16 *x, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
+// Input of a convolution: x, or for a decoder input read from two tensors the skip tensor x and
+// the half-resolution x_low whose upsampling gives channels [0, c1).
+struct In {
+    const bf16 *x, *x_low;
+    int c1;
+};
+
+void conv_fwd(ur_nn *nn, In in, int B, int H, int W, int Cin, int Cout, const bf16 *w, const float *bias,
               const bf16 *mask, bf16 *y, bool relu, int taps = 9, float *dbias = nullptr, bf16 *y2 = nullptr,
               int c_split = 0, const urnn::HeadTC *head = nullptr) {
-    urnn::ConvTC P{x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0, dbias, y2, c_split, head};
+    urnn::ConvTC P{in.x, Cin, B, H, W, w, Cout, taps, bias, mask, y, relu ? 1 : 0, dbias, y2, c_split, head,
+                   in.x_low, in.c1};
     std::string why;
     ++nn->launches;
     const cudaError_t e = urnn::conv3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
@@ -416,8 +425,8 @@ void sync_check(ur_nn *nn, const char *what) {
 }
 
 void conv_wgrad(ur_nn *nn, const bf16 *x, const bf16 *dy, int B, int H, int W, int Cin, int Cout, float *dw,
-                int taps = 9) {
-    urnn::WgradTC P{x, Cin, B, H, W, dy, Cout, taps, dw};
+                int taps = 9, const bf16 *x_low = nullptr, int c1 = 0) {
+    urnn::WgradTC P{x, Cin, B, H, W, dy, Cout, taps, dw, x_low, c1};
     std::string why;
     ++nn->launches;
     const cudaError_t e = urnn::wgrad3x3_tc(P, nn->d_err, nn->sms, nn->stream, &why);
@@ -428,10 +437,12 @@ void conv_wgrad(ur_nn *nn, const bf16 *x, const bf16 *dy, int B, int H, int W, i
     }
 }
 
-// Grid of a kernel whose threads own 8 of C channels of every (256 / (C / 8))-th pixel.
-int channel_grid(long long P, int C) {
+// Grid of a kernel whose threads own 8 of C channels of every (256 / (C / 8))-th pixel and whose
+// blocks end by adding their per-channel sums atomically: four blocks per SM, so each block
+// covers many pixels and the C atomics per block (all to the same C addresses) stay few.
+int channel_grid(const ur_nn *nn, long long P, int C) {
     const int lanes = 256 / (C / 8);
-    return (int)std::min<long long>(2048, (P + lanes - 1) / lanes);
+    return (int)std::min<long long>(4ll * std::max(1, nn->sms), (P + lanes - 1) / lanes);
 }
 
 // Inputs of every conv of the network at batch B.
@@ -461,12 +472,15 @@ Layer layer_in(ur_nn *nn, int l) {
     }
 }
 
-// Plain NHWC input of conv l; a decoder input (upsample ++ skip) lives in nn->cat[(l - 8) / 2],
-// built by the forward pass (build = true) and reused by the backward pass.
-const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
+// Input of conv l.  The decoder inputs of d2a and d1a are read by their convolutions straight
+// from the lower level (upsampled by the tensor map) and the skip tensor; that of d3a (quarter
+// resolution, 384 channels: the per-tap kernel) lives in nn->cat[0], built by the forward pass
+// (build = true) and reused by the backward pass.
+In conv_input(ur_nn *nn, int B, int l, bool build) {
     const Layer L = layer_in(nn, l);
-    if (!L.in.x2) return L.in.x1;
-    bf16 *cat = nn->cat[(l - 8) / 2];
+    if (!L.in.x2) return In{L.in.x1, nullptr, 0};
+    if (l != 8) return In{L.in.x2, L.in.x1, L.in.c1};
+    bf16 *cat = nn->cat[0];
     if (build) {
         ++nn->launches;
         k_upcat<<<grid_for((long long)B * L.H * L.W * nn->cin[l] / 8), 256, 0, nn->stream>>>(
@@ -474,7 +488,7 @@ const bf16 *conv_input(ur_nn *nn, int B, int l, bool build) {
             make_div32((uint32_t)L.W), make_div32((uint32_t)L.H), cat);
         ck(cudaGetLastError(), "upcat kernel");
     }
-    return cat;
+    return In{cat, nullptr, 0};
 }
 
 // Forward pass; the residual head runs in the last convolution's epilogue.  Inference writes
@@ -492,7 +506,7 @@ void forward(ur_nn *nn, int B, const float *rf, const float *quad, float *out_rf
     ck(cudaGetLastError(), "pack kernel");
     for (int l = 0; l < kNumConv; ++l) {
         const Layer L = layer_in(nn, l);
-        const bf16 *in = conv_input(nn, B, l, true);
+        const In in = conv_input(nn, B, l, true);
         if (l == 0) {   // neighbourhood already in the 32 input channels: one tap
             conv_fwd(nn, in, B, L.H, L.W, 32, nn->cout[0], nn->wfirst, nn->params + nn->boff[0], nullptr, nn->act[0].p,
                      true, 1);
@@ -530,8 +544,8 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
     k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
                                                                                   nn->cout[lb], nn->cin[lb]);
     // gradient at la's output, masked by la's ReLU in the epilogue, which also sums la's bias gradient
-    conv_fwd(nn, d_out, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p, scratch, false, 9,
-             nn->grads + nn->boff[la]);
+    conv_fwd(nn, In{d_out, nullptr, 0}, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p,
+             scratch, false, 9, nn->grads + nn->boff[la]);
     if (la == 0) {   // first layer: single-tap gradient over the neighbourhood channels, then back to [9][C][32]
         ck(cudaMemsetAsync(nn->dwfirst, 0, sizeof(float) * 32 * nn->width, nn->stream), "memset");
         conv_wgrad(nn, nn->x, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
@@ -539,14 +553,16 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
         k_unpack_first_grad<<<grid_for(18ll * nn->width), 256, 0, nn->stream>>>(nn->dwfirst, nn->width,
                                                                                nn->grads + nn->woff[0]);
     } else {
-        conv_wgrad(nn, conv_input(nn, B, la, false), scratch, B, La.H, La.W, nn->cin[la], nn->cout[la],
-                   nn->grads + nn->woff[la]);
+        const In in = conv_input(nn, B, la, false);
+        conv_wgrad(nn, in.x, scratch, B, La.H, La.W, nn->cin[la], nn->cout[la], nn->grads + nn->woff[la], 9, in.x_low,
+                   in.c1);
     }
     if (din) {
         ++nn->launches;
         k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
                                                                                       nn->cout[la], nn->cin[la]);
-        conv_fwd(nn, scratch, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din, false, 9, nullptr,
+        conv_fwd(nn, In{scratch, nullptr, 0}, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din,
+                 false, 9, nullptr,
                  dskip, c1);
     }
     ck(cudaGetLastError(), "block backward");
@@ -556,7 +572,7 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
 // by act[l_low], bias sums of layer l_low).
 void unconcat(ur_nn *nn, int B, int H, int W, int C1, int l_low) {
     ++nn->launches;
-    k_unconcat_low<<<channel_grid((long long)B * (H / 2) * (W / 2), C1), 256, 0, nn->stream>>>(
+    k_unconcat_low<<<channel_grid(nn, (long long)B * (H / 2) * (W / 2), C1), 256, 0, nn->stream>>>(
         nn->gcat, B, H, W, C1, make_div32((uint32_t)(W / 2)), make_div32((uint32_t)(H / 2)), nn->act[l_low].p,
         nn->gLow, nn->grads + nn->boff[l_low]);
     ck(cudaGetLastError(), "unconcat");
@@ -565,7 +581,7 @@ void unconcat(ur_nn *nn, int B, int H, int W, int C1, int l_low) {
 // d (gradient at layer l's output, H x W) += pooling gradient of gcat, masked by act[l], bias sums.
 void pool_bwd(ur_nn *nn, int B, int H, int W, int C, int l, bf16 *d) {
     ++nn->launches;
-    k_pool2_bwd_mask<<<channel_grid((long long)B * H * W, C), 256, 0, nn->stream>>>(
+    k_pool2_bwd_mask<<<channel_grid(nn, (long long)B * H * W, C), 256, 0, nn->stream>>>(
         d, nn->gcat, nn->act[l].p, B, H, W, C, make_div32((uint32_t)W), make_div32((uint32_t)H), nn->grads + nn->boff[l]);
     ck(cudaGetLastError(), "pooling backward");
 }
@@ -714,8 +730,7 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         }
         nn->x = (bf16 *)nn->alloc(sizeof(bf16) * B * H * W * 32);
         nn->xn = (float *)nn->alloc(sizeof(float) * B * H * W * 2);
-        for (int q = 0; q < 3; ++q)   // d3a: [H/4][W/4][12C], d2a: [H/2][W/2][6C], d1a: [H][W][3C]
-            nn->cat[q] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> (2 - q)) * (W >> (2 - q)) * (12 * C >> q));
+        nn->cat[0] = (bf16 *)nn->alloc(sizeof(bf16) * B * (H >> 2) * (W >> 2) * 12 * C);   // d3a: [H/4][W/4][12C]
         nn->wfirst = (bf16 *)nn->alloc(sizeof(bf16) * 32 * C);
         nn->dwfirst = (float *)nn->alloc(sizeof(float) * 32 * C);
         nn->loss = (double *)nn->alloc(sizeof(double));
