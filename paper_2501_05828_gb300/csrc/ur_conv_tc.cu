@@ -608,7 +608,9 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
             constexpr uint32_t idesc = idesc_bf16<BN>();
-            constexpr uint32_t idesc_stk = idesc_bf16<128>();   // row-stacked: R BN = 128 columns
+            // row-stacked: N = R BN columns (kind::f16, FP32 accumulator, BF16 operands, M = 128)
+            const uint32_t idesc_stk = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((R * BN) >> 3) << 17) |
+                                       ((uint32_t)(kBM >> 4) << 24);
             if (wres && !mbar_wait(wfull, 0u, deadline)) ok = false;
             int i = 0, s = 0;
             uint32_t ph = 0;
@@ -1103,17 +1105,17 @@ cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, const CUtens
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
     const int kc = a.C / BK, two = smem_sm / 2 - reserve;
-    // Row-stacked tiles (R = 128 / BN output rows) when the stacked weights and three input stages
-    // fit twice per SM (at one CTA per SM they were slower than single-row tiles at two, measured
-    // on the denoiser's layers).  Otherwise one output row per tile with the weights resident (two
-    // CTAs per SM, else one) or streamed with each stage.
+    // Row-stacked tiles (R = 128 / BN output rows, else half as many) when the stacked weights and
+    // three input stages fit twice per SM (at one CTA per SM they were slower than single-row tiles
+    // at two, measured on the denoiser's layers).  Otherwise one output row per tile with the
+    // weights resident (two CTAs per SM, else one) or streamed with each stage.
     int R = 1, stages = 0, smem = 0;
     bool wres = true;
-    if (K::MAX_ROWS > 1) {
-        const int fixed = 1024 + kc * K::stacked_bytes(K::MAX_ROWS) + K::TAIL;
+    for (int Rt = K::MAX_ROWS; Rt > 1 && R == 1; Rt /= 2) {
+        const int fixed = 1024 + kc * K::stacked_bytes(Rt) + K::TAIL;
         const int n = std::min((two - fixed) / K::A_PAD, kKxMaxStages);
         if (n >= 3) {
-            R = K::MAX_ROWS;
+            R = Rt;
             stages = n;
             smem = fixed + n * K::A_PAD;
         }
