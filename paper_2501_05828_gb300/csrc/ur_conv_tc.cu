@@ -855,11 +855,12 @@ __global__ void __launch_bounds__(kConvThreads, 2)
 // starts j rows into it and the B descriptor's leading byte offset (the stride
 // between its BN-column blocks) is one pixel row.  The tensor core swizzles from
 // the shared-memory address bits, so the shifted blocks read the rows TMA wrote.
-constexpr int kWK = 64;                 // pixels per K step
+constexpr int kWK = 64;                 // pixels per K step (128 for the fused-kx form on wide images)
 constexpr int kChunk = 32 * kWK * 2;    // one 32-channel x 64-pixel box: 4 KB
 
-__device__ __forceinline__ uint64_t sdesc_mn64(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kChunk >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+// A operand: 32-channel MN chunks `chunk` bytes apart (one box of 32 channels x the step's pixels)
+__device__ __forceinline__ uint64_t sdesc_mn64(uint32_t addr, uint32_t chunk = kChunk) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(chunk >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
            (1ull << 46) | (4ull << 61);
 }
 
@@ -879,16 +880,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16_mn() {
            ((uint32_t)(kBM >> 4) << 24);
 }
 
-// BN: C_out tile; KX: the fused-kx form (MMA N = 3 BN, one shifted dy box per stage).
-template <int BN, bool KX>
+// BN: C_out tile; KX: the fused-kx form (MMA N = 3 BN, one shifted dy box per stage); WK: pixels
+// per K step.
+template <int BN, bool KX, int WK = kWK>
 struct WCfg {
     static constexpr int NB = KX ? 3 * BN : BN;   // MMA N
-    static constexpr int A_BYTES = 4 * kChunk;
-    static constexpr int B_TX = KX ? (kWK + 2) * BN * 2 : (BN / 32) * kChunk;   // bytes the B boxes deliver
-    static constexpr int B_BYTES = (B_TX + 1023) / 1024 * 1024;                    // their stage slot
-    // KX: two CTAs per SM (stages within half the SM's shared memory), so one CTA's epilogue
-    // overlaps the other's main loop
-    static constexpr int S_RAW = (KX ? 110 * 1024 : BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
+    static constexpr int CHUNK = 32 * WK * 2;      // one 32-channel box
+    static constexpr int A_BYTES = 4 * CHUNK;
+    static constexpr int B_TX = KX ? (WK + 2) * BN * 2 : (BN / 32) * CHUNK;   // bytes the B boxes deliver
+    static constexpr int B_BYTES = (B_TX + 1023) / 1024 * 1024;                  // their stage slot
+    // KX with 64-pixel steps: two CTAs per SM (stages within half the SM's shared memory), so one
+    // CTA's epilogue overlaps the other's main loop; 128-pixel steps: one CTA per SM, four stages
+    static constexpr int S_RAW =
+        (KX ? (WK > 64 ? 200 * 1024 : 110 * 1024) : BN >= 128 ? 200 * 1024 : 100 * 1024) / (A_BYTES + B_BYTES);
     static constexpr int S = S_RAW < 2 ? 2 : (S_RAW > 6 ? 6 : S_RAW);
     static constexpr int TMEM_COLS = NB <= 32 ? 32 : NB <= 64 ? 64 : NB <= 128 ? 128 : 256;
     static constexpr int SMEM = S * (A_BYTES + B_BYTES) + 1024 + 8 * (2 * S + 1) + 16;
@@ -902,11 +906,11 @@ struct WArgs {
     int c1;   // input channels [0, c1) from the upsampled half-resolution map
 };
 
-template <int BN, bool KX>
+template <int BN, bool KX, int WK>
 __global__ void __launch_bounds__(kThreads, 1)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmd,
                const __grid_constant__ CUtensorMap tml, const WArgs a) {
-    using K = WCfg<BN, KX>;
+    using K = WCfg<BN, KX, WK>;
     constexpr int NB = K::NB;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = s_addr(smem_raw);
@@ -946,7 +950,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0 && nk > 0) {   // TMA producer
             int issued = 0;
-            const uint32_t bytes = (uint32_t)(n_groups * kChunk + K::B_TX);
+            const uint32_t bytes = (uint32_t)(n_groups * K::CHUNK + K::B_TX);
             for (int kt = 0; kt < nk; ++kt) {
                 const int st = kt % K::S;
                 if (!mbar_wait(empty0 + 8 * st, ((uint32_t)(kt / K::S) & 1u) ^ 1u, deadline)) {
@@ -958,7 +962,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int q = s_begin + kt;
                 const int y = q % a.H;
                 q /= a.H;
-                const int xb = q % a.nxb, n = q / a.nxb, x0 = xb * kWK;
+                const int xb = q % a.nxb, n = q / a.nxb, x0 = xb * WK;
                 mbar_expect_tx(full0 + 8 * st, bytes);
                 for (int g = 0; g < n_groups; ++g) {
                     const int r = r0 + 32 * g, tap = r / a.Cin, ci0 = r - tap * a.Cin;
@@ -971,17 +975,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         kx = a.taps == 1 ? 1 : tap - 3 * (tap / 3);
                     }
                     if (ci0 < a.c1)   // upsampled: 32 low pixels, each twice (kx = 1 here: no pixel shift)
-                        tma_load_5d(sA + st * K::A_BYTES + g * kChunk, &tml, ci0, 0, x0 / 2, low_row(y + ky - 1), n,
+                        tma_load_5d(sA + st * K::A_BYTES + g * K::CHUNK, &tml, ci0, 0, x0 / 2, low_row(y + ky - 1), n,
                                     full0 + 8 * st);
                     else
-                        tma_load_4d(sA + st * K::A_BYTES + g * kChunk, &tmx, ci0 - a.c1, x0 + kx - 1, y + ky - 1, n,
+                        tma_load_4d(sA + st * K::A_BYTES + g * K::CHUNK, &tmx, ci0 - a.c1, x0 + kx - 1, y + ky - 1, n,
                                     full0 + 8 * st);
                 }
-                if (KX) {   // dy at pixels x0 - 1 .. x0 + kWK: the three kx shifts are rows 2 - kx on
+                if (KX) {   // dy at pixels x0 - 1 .. x0 + WK: the three kx shifts are rows 2 - kx on
                     tma_load_4d(sB + st * K::B_BYTES, &tmd, co0, x0 - 1, y, n, full0 + 8 * st);
                 } else {
                     for (int c = 0; c < BN / 32; ++c)
-                        tma_load_4d(sB + st * K::B_BYTES + c * kChunk, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
+                        tma_load_4d(sB + st * K::B_BYTES + c * K::CHUNK, &tmd, co0 + 32 * c, x0, y, n, full0 + 8 * st);
                 }
                 issued = kt + 1;
             }
@@ -1002,9 +1006,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t a0 = sA + st * K::A_BYTES, b0 = sB + st * K::B_BYTES;
 #pragma unroll
-                for (int k = 0; k < kWK / 16; ++k) {   // 16 pixels: two 8-row K groups
-                    const uint64_t bd = KX ? sdesc_mn_shift<BN>(b0 + (uint32_t)(16 * 2 * BN * k)) : sdesc_mn64(b0 + 1024 * k);
-                    mma_bf16(tmem, sdesc_mn64(a0 + 1024 * k), bd, idesc, (kt | k) != 0);
+                for (int k = 0; k < WK / 16; ++k) {   // 16 pixels: two 8-row K groups
+                    const uint64_t bd =
+                        KX ? sdesc_mn_shift<BN>(b0 + (uint32_t)(16 * 2 * BN * k)) : sdesc_mn64(b0 + 1024 * k, K::CHUNK);
+                    mma_bf16(tmem, sdesc_mn64(a0 + 1024 * k, K::CHUNK), bd, idesc, (kt | k) != 0);
                 }
                 mma_commit(empty0 + 8 * st);
             }
@@ -1293,16 +1298,16 @@ cudaError_t conv3x3_tc(const ConvTC &p, int *d_err, int n_sm, cudaStream_t strea
 
 namespace {
 
-template <int BN, bool KX>
+template <int BN, bool KX, int WK = kWK>
 cudaError_t launch_w(const CUtensorMap &mx, const CUtensorMap &md, const CUtensorMap &ml, const WArgs &a, dim3 grid,
                      cudaStream_t stream) {
-    using K = WCfg<BN, KX>;
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    using K = WCfg<BN, KX, WK>;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
     if (e == cudaSuccess)   // all of the unified L1/shared array as shared memory: two CTAs per SM
-        e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_wgrad_tc<BN, KX, WK>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    k_wgrad_tc<BN, KX><<<grid, kThreads, K::SMEM, stream>>>(mx, md, ml, a);
+    k_wgrad_tc<BN, KX, WK><<<grid, kThreads, K::SMEM, stream>>>(mx, md, ml, a);
     return cudaGetLastError();
 }
 
@@ -1336,12 +1341,15 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     const bool kx = p.taps == 9;   // C_out tiles of 32 (C_out = 32) or 64 columns x 3 taps
     const int kx_bn = p.Cout == 32 ? 32 : 64;
+    // pixels per K step: 128 for the fused-kx form where the image width fills 128-pixel blocks
+    // (half as many K steps, each twice the MMAs per pipeline round trip), else 64
+    const int wk = kx && p.W % 128 == 0 ? 128 : kWK;
     alignas(64) CUtensorMap mx, md, mlow;
     if (p.x_low) {   // (c, repeat 2 with stride 0, x / 2, y / 2, n): 32 low pixels give a 64-pixel box
         const int c1 = p.c1, wl = p.W / 2, hl = p.H / 2;
         const cuuint64_t dims[5] = {(cuuint64_t)c1, 2, (cuuint64_t)wl, (cuuint64_t)hl, (cuuint64_t)p.N};
         const cuuint64_t strides[4] = {0, (cuuint64_t)c1 * 2, (cuuint64_t)wl * c1 * 2, (cuuint64_t)hl * wl * c1 * 2};
-        const cuuint32_t box[5] = {32, 2, (cuuint32_t)(kWK / 2), 1, 1};
+        const cuuint32_t box[5] = {32, 2, (cuuint32_t)(wk / 2), 1, 1};
         const cuuint32_t es[5] = {1, 1, 1, 1, 1};
         if (enc(&mlow, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(p.x_low), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1351,14 +1359,14 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
         }
     }
     const int cx = p.x_low ? p.Cin - p.c1 : p.Cin;   // channels of x itself
-    const bool md_ok = kx ? encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, kx_bn, kWK + 2,
+    const bool md_ok = kx ? encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, kx_bn, wk + 2,
                                         kx_bn == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B)
                           : encode_nhwc(enc, &md, p.dy, p.Cout, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B);
-    if (!encode_nhwc(enc, &mx, p.x, cx, p.N, p.H, p.W, 32, kWK, CU_TENSOR_MAP_SWIZZLE_64B) || !md_ok) {
+    if (!encode_nhwc(enc, &mx, p.x, cx, p.N, p.H, p.W, 32, wk, CU_TENSOR_MAP_SWIZZLE_64B) || !md_ok) {
         if (why) *why = "wgrad3x3_tc: tensor map rejected";
         return cudaErrorInvalidValue;
     }
-    const int nxb = (p.W + kWK - 1) / kWK;
+    const int nxb = (p.W + wk - 1) / wk;
     const long long steps = (long long)p.N * p.H * nxb;
     // M tiles of 4 groups of 32 (tap, ci) rows, or of 3 where that gives as many tiles with equal
     // work (96 input channels: three tiles of 96 rows instead of 128, 128 and 32)
@@ -1371,8 +1379,8 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     int smem = 0;
     switch (kx ? kx_bn : 1000 + BN) {
-        case 32: smem = WCfg<32, true>::SMEM; break;
-        case 64: smem = WCfg<64, true>::SMEM; break;
+        case 32: smem = wk == 128 ? WCfg<32, true, 128>::SMEM : WCfg<32, true>::SMEM; break;
+        case 64: smem = wk == 128 ? WCfg<64, true, 128>::SMEM : WCfg<64, true>::SMEM; break;
         case 1032: smem = WCfg<32, false>::SMEM; break;
         case 1064: smem = WCfg<64, false>::SMEM; break;
         case 1128: smem = WCfg<128, false>::SMEM; break;
@@ -1396,6 +1404,9 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     WArgs a{p.N, p.H, p.W, p.Cin, p.Cout, p.taps, nxb, (int)steps, per, gpt, p.dw, d_err, p.x_low ? p.c1 : 0};
     const CUtensorMap &ml = p.x_low ? mlow : mx;
     const dim3 grid((unsigned)m_tiles, (unsigned)n_tiles, (unsigned)splits);
+    if (kx && wk == 128)
+        return kx_bn == 32 ? launch_w<32, true, 128>(mx, md, ml, a, grid, stream)
+                           : launch_w<64, true, 128>(mx, md, ml, a, grid, stream);
     if (kx) return kx_bn == 32 ? launch_w<32, true>(mx, md, ml, a, grid, stream) : launch_w<64, true>(mx, md, ml, a, grid, stream);
     switch (BN) {
         case 32: return launch_w<32, false>(mx, md, ml, a, grid, stream);

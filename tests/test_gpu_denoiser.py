@@ -180,14 +180,17 @@ def test_forward_matches_oracle_across_tiles():
     dn.close()
 
 
-def test_gradient_matches_oracle_across_tiles():
-    """Parameter gradients on an 8 x 320 frame: several 64-pixel K steps per image row, so the
-    x-shifted boxes of the fused-kx weight gradient cross block seams and the image edges."""
+@pytest.mark.parametrize("w", [320, 256])
+def test_gradient_matches_oracle_across_tiles(w):
+    """Parameter gradients on an 8 x w frame: several K steps per image row, so the x-shifted
+    boxes of the fused-kx weight gradient cross block seams and the image edges (w = 320: 64-pixel
+    steps at every level; w = 256: 128-pixel steps at the two upper levels, whose widths are
+    multiples of 128)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2501_05828_gb300 as ur
-    h, w = 8, 320
+    h = 8
     dn = ur.Denoiser(0, max_batch=1, n_el=h, n_s=w, width=32, seed=11)
     lay = ur.nn_layout(32)
     rng = np.random.default_rng(12)
@@ -209,6 +212,6 @@ def test_gradient_matches_oracle_across_tiles():
     for name in ("e1b", "e2a", "e2b", "d2a", "d2b", "d1a", "d1b", "e3b", "d3a"):
         wo, ws, bo, co = lay[name]
         e = rel_l2(g[wo:wo + int(np.prod(ws))].reshape(ws).astype(np.float64), G[name + ".w"])
-        print(f"wide {name}.w: rel_l2 {e:.2e}")
+        print(f"wide ({w}) {name}.w: rel_l2 {e:.2e}")
         assert e <= 5e-2, (name, e)
     dn.close()
