@@ -1341,9 +1341,10 @@ cudaError_t wgrad3x3_tc(const WgradTC &p, int *d_err, int n_sm, cudaStream_t str
     }
     const bool kx = p.taps == 9;   // C_out tiles of 32 (C_out = 32) or 64 columns x 3 taps
     const int kx_bn = p.Cout == 32 ? 32 : 64;
-    // pixels per K step: 128 for the fused-kx form where the image width fills 128-pixel blocks
-    // (half as many K steps, each twice the MMAs per pipeline round trip), else 64
-    const int wk = kx && p.W % 128 == 0 ? 128 : kWK;
+    // pixels per K step: 128 for the fused-kx form where the image width fills 128-pixel blocks or
+    // is wide enough that a ragged last block costs little (half as many K steps, each twice the
+    // MMAs per pipeline round trip), else 64
+    const int wk = kx && (p.W % 128 == 0 || p.W >= 1024) ? 128 : kWK;
     alignas(64) CUtensorMap mx, md, mlow;
     if (p.x_low) {   // (c, repeat 2 with stride 0, x / 2, y / 2, n): 32 low pixels give a 64-pixel box
         const int c1 = p.c1, wl = p.W / 2, hl = p.H / 2;

@@ -180,12 +180,12 @@ def test_forward_matches_oracle_across_tiles():
     dn.close()
 
 
-@pytest.mark.parametrize("w", [320, 256])
+@pytest.mark.parametrize("w", [320, 256, 1088])
 def test_gradient_matches_oracle_across_tiles(w):
     """Parameter gradients on an 8 x w frame: several K steps per image row, so the x-shifted
     boxes of the fused-kx weight gradient cross block seams and the image edges (w = 320: 64-pixel
     steps at every level; w = 256: 128-pixel steps at the two upper levels, whose widths are
-    multiples of 128)."""
+    multiples of 128; w = 1088: 128-pixel steps with a ragged last block at the top level)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
