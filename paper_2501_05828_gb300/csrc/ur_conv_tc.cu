@@ -445,15 +445,16 @@ __global__ void __launch_bounds__(kConvThreads, 1)
 // of once per tap; the epilogue is the plain one (bias, ReLU, mask, BF16 store).
 //
 // Row-stacked tiles (BN in {32, 64} when the weights fit): a tile is R = 128 / BN output rows
-// y .. y + R - 1, their accumulators side by side (N = R BN = 128 columns).  Input row y - 1 + r
-// (r = 0 .. R + 1) contributes to output row y + o with kernel row ky = r - o, so one MMA with
-// N = 128 adds it to all R output rows if its B operand is the stack W(ky = r), W(r - 1), ...,
-// W(r - R + 1) of BN-row weight blocks, zero where ky is outside 0..2.  The resident weights of a
-// channel chunk hold, per kx, the blocks W(2), W(1), W(0) between runs of R - 1 zero blocks
-// (shared by neighbouring kx), so every such stack is one contiguous run of blocks.  An input row
-// is staged (R + 2) / R times per output row instead of 3, and each staged row costs 3 BK / 16
-// MMAs of N = 128 instead of up to 3 x 3 BK / 16 of N = BN (the tensor core re-reads the A
-// operand for every MMA).
+// y .. y + R - 1, their accumulators side by side in TMEM.  Input row y - 1 + r (r = 0 .. R + 1)
+// contributes to the output rows y + o, o = max(0, r - 2) .. min(R - 1, r), with kernel rows
+// ky = r - o, so one MMA adds it to all of them if its B operand is the run W(ky = r - o_lo),
+// W(ky - 1), ... of BN-row weight blocks (N = BN x the rows it touches, D at column o_lo BN).  The
+// resident weights of a channel chunk hold, per kx, the blocks W(2), W(1), W(0) in that order, so
+// every such run is contiguous.  The first K slice of an input row that starts a new output row
+// (o = r) is issued as two MMAs: the rows already under way accumulate, the new one is
+// initialised.  An input row is staged (R + 2) / R times per output row instead of 3, and each
+// staged row costs 3 BK / 16 MMAs of up to 3 BN columns instead of up to 3 x 3 BK / 16 of BN
+// columns (the tensor core re-reads the A operand for every MMA).
 constexpr int kKxRows = kBM + 2;   // staged input pixels per kernel row
 
 // Weights: when all 3 kc blocks of one C_out tile fit beside a few input stages they are
@@ -476,11 +477,8 @@ struct KxCfg {
     static constexpr int N_BARS = 2 * kKxMaxStages + 5;    // full, empty, acc_full[2], acc_empty[2], weights
     static constexpr int TAIL = 8 * N_BARS + 16;           // barriers and the TMEM address slot
     static constexpr int BLK = BN * ROW;                    // one BN-row weight block
-    // row-stacked weights of one channel chunk: R - 1 zero blocks, then per kx W(2), W(1), W(0) and R - 1 zero blocks
-    __host__ __device__ static constexpr int stacked_blocks(int R) { return (R - 1) + 3 * (R + 2); }
-    __host__ __device__ static constexpr int stacked_bytes(int R) { return (stacked_blocks(R) * BLK + 1023) / 1024 * 1024; }
-    // block index of W(ky = 2) of kx in the stacked layout
-    __host__ __device__ static constexpr int stacked_w2(int R, int kx) { return (R - 1) + kx * (R + 2); }
+    // row-stacked weights of one channel chunk: per kx the blocks W(2), W(1), W(0)
+    static constexpr int STK_BYTES = (9 * BLK + 1023) / 1024 * 1024;
     // shared memory of a launch: alignment slack, resident weights, stages, tail
     static int smem(int kc, bool wres, int stages) {
         return 1024 + (wres ? 3 * kc * B_PAD : 0) + stages * (A_PAD + (wres ? 0 : B_PAD)) + TAIL;
@@ -500,7 +498,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const bool wres = a.wres != 0;
     const int S = a.stages;
     const int R = a.rows;   // R > 1: row-stacked tile (resident stacked weights)
-    const uint32_t wb_stk = R > 1 ? (uint32_t)K::stacked_bytes(R) : 0u;   // stacked weights per channel chunk
+    const uint32_t wb_stk = R > 1 ? (uint32_t)K::STK_BYTES : 0u;   // stacked weights per channel chunk
     const uint32_t w_bytes = R > 1 ? (uint32_t)kc * wb_stk : wres ? (uint32_t)(3 * kc * K::B_PAD) : 0u;
     const uint32_t stage = (uint32_t)(K::A_PAD + (wres ? 0 : K::B_PAD));
     const uint32_t sW = base, sS = base + w_bytes;   // resident weights; stage s: A at sS + s stage, then B
@@ -512,17 +510,6 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t deadline = now_ns() + kWaitNs;
 
-    if (R > 1) {   // the zero blocks of the stacked weights, written before the tensor core reads them
-        const int zb = R - 1, per = 4 * zb * K::BLK / 16;   // 16-byte words of zeros per channel chunk
-        for (int i = threadIdx.x; i < kc * per; i += blockDim.x) {
-            const int cc = i / per, w = i - cc * per;
-            const int run = w / (zb * K::BLK / 16), off = w - run * (zb * K::BLK / 16);   // run 0: leading zeros
-            const int blk0 = run == 0 ? 0 : K::stacked_w2(R, run - 1) + 3;
-            uint4 *dst = reinterpret_cast<uint4 *>(sm + (size_t)cc * wb_stk + (size_t)blk0 * K::BLK) + off;
-            *dst = make_uint4(0u, 0u, 0u, 0u);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -553,12 +540,12 @@ __global__ void __launch_bounds__(kConvThreads, 2)
 
     if (warp == 0) {
         if (lane == 0) {   // TMA producer
-            if (R > 1) {   // stacked: W(ky) of (chunk, kx) at block stacked_w2(kx) + 2 - ky of the chunk
+            if (R > 1) {   // stacked: W(ky) of (chunk, kx) at block 3 kx + 2 - ky of the chunk
                 mbar_expect_tx(wfull, (uint32_t)(kc * 9 * K::BLK));
                 for (int cc = 0; cc < kc; ++cc)
                     for (int kx = 0; kx < 3; ++kx)
                         for (int ky = 0; ky < 3; ++ky)
-                            tma_load_2d(sW + (uint32_t)cc * wb_stk + (uint32_t)((K::stacked_w2(R, kx) + 2 - ky) * K::BLK),
+                            tma_load_2d(sW + (uint32_t)cc * wb_stk + (uint32_t)((3 * kx + 2 - ky) * K::BLK),
                                         &tmw, cc * BK, (3 * ky + kx) * BN, wfull);
             } else if (wres) {   // every weight block once: block kt = (ky, channel chunk) at sW + kt B_PAD
                 mbar_expect_tx(wfull, (uint32_t)(nk * K::B_BYTES));
@@ -608,9 +595,11 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
             constexpr uint32_t idesc = idesc_bf16<BN>();
-            // row-stacked: N = R BN columns (kind::f16, FP32 accumulator, BF16 operands, M = 128)
-            const uint32_t idesc_stk = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((R * BN) >> 3) << 17) |
-                                       ((uint32_t)(kBM >> 4) << 24);
+            // row-stacked: N = BN x rows columns (kind::f16, FP32 accumulator, BF16 operands, M = 128)
+            auto idesc_rows = [](int rows) {
+                return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((rows * BN) >> 3) << 17) |
+                       ((uint32_t)(kBM >> 4) << 24);
+            };
             if (wres && !mbar_wait(wfull, 0u, deadline)) ok = false;
             int i = 0, s = 0;
             uint32_t ph = 0;
@@ -633,15 +622,26 @@ __global__ void __launch_bounds__(kConvThreads, 2)
                     // stage row i is pixel x0 - 1 + i, or x0 - 2 + i for an upsampled chunk
                     const uint32_t st0 = sS + (uint32_t)s * stage;
                     const uint32_t a0 = st0 + (kcc * BK < a.c1 ? (uint32_t)K::ROW : 0u);
-                    if (R > 1) {   // one N = 128 MMA per tap column and K slice: all R output rows at once
+                    if (R > 1) {   // one MMA per tap column and K slice: every output row this input row touches
                         const uint32_t wc = sW + (uint32_t)kcc * wb_stk;
+                        const int o_lo = r > 2 ? r - 2 : 0, o_hi = r < R - 1 ? r : R - 1, nr_o = o_hi - o_lo + 1;
+                        const uint32_t dst = d + (uint32_t)(o_lo * BN);
+                        const bool opens = kcc == 0 && o_hi == r;   // output row y + r starts here
 #pragma unroll
                         for (int kx = 0; kx < 3; ++kx) {
-                            const uint32_t b0 = wc + (uint32_t)((K::stacked_w2(R, kx) + 2 - r) * K::BLK);
+                            const uint32_t b0 = wc + (uint32_t)((3 * kx + 2 - (r - o_lo)) * K::BLK);   // W(ky = r - o_lo)
 #pragma unroll
-                            for (int k = 0; k < BK / 16; ++k)
-                                mma_bf16(d, sdesc(a0 + (uint32_t)(kx * K::ROW) + 32 * k, K::ROW),
-                                         sdesc(b0 + 32 * k, K::ROW), idesc_stk, (kt | kx | k) != 0);
+                            for (int k = 0; k < BK / 16; ++k) {
+                                const uint64_t ad = sdesc(a0 + (uint32_t)(kx * K::ROW) + 32 * k, K::ROW);
+                                if (opens && kx == 0 && k == 0) {   // older rows accumulate, row r is initialised
+                                    if (nr_o > 1)
+                                        mma_bf16(dst, ad, sdesc(b0, K::ROW), idesc_rows(nr_o - 1), 1u);
+                                    mma_bf16(d + (uint32_t)(r * BN), ad, sdesc(wc + (uint32_t)(2 * K::BLK), K::ROW),
+                                             idesc_rows(1), 0u);
+                                } else {
+                                    mma_bf16(dst, ad, sdesc(b0 + 32 * k, K::ROW), idesc_rows(nr_o), 1u);
+                                }
+                            }
                         }
                     } else {
                         const uint32_t b0 = wres ? sW + (uint32_t)((r * kc + kcc) * K::B_PAD) : st0 + K::A_PAD;
@@ -1110,17 +1110,17 @@ cudaError_t launch_kx(const CUtensorMap &mx, const CUtensorMap &mw, const CUtens
         (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
     const int kc = a.C / BK, two = smem_sm / 2 - reserve;
-    // Row-stacked tiles (R = 128 / BN output rows, else half as many) when the stacked weights and
-    // three input stages fit twice per SM (at one CTA per SM they were slower than single-row tiles
-    // at two, measured on the denoiser's layers).  Otherwise one output row per tile with the
-    // weights resident (two CTAs per SM, else one) or streamed with each stage.
+    // Row-stacked tiles (R = 128 / BN output rows) when the stacked weights and two input stages fit
+    // twice per SM (at one CTA per SM stacked tiles were slower than single-row tiles at two,
+    // measured on the denoiser's layers).  Otherwise one output row per tile with the weights
+    // resident (two CTAs per SM, else one) or streamed with each stage.
     int R = 1, stages = 0, smem = 0;
     bool wres = true;
-    for (int Rt = K::MAX_ROWS; Rt > 1 && R == 1; Rt /= 2) {
-        const int fixed = 1024 + kc * K::stacked_bytes(Rt) + K::TAIL;
+    if (K::MAX_ROWS > 1) {
+        const int fixed = 1024 + kc * K::STK_BYTES + K::TAIL;
         const int n = std::min((two - fixed) / K::A_PAD, kKxMaxStages);
-        if (n >= 3) {
-            R = Rt;
+        if (n >= 2) {
+            R = K::MAX_ROWS;
             stages = n;
             smem = fixed + n * K::A_PAD;
         }
