@@ -16,6 +16,10 @@
 // an optional ReLU mask (for data gradients) before storing BF16, while the
 // next tile's MMAs run.
 //
+// Below it: k_conv_kx, the 3x3 form for C_out <= 96 with the three kx taps read
+// from one staged input row (and row-stacked tiles), and k_wgrad_tc, the weight
+// gradient.
+//
 // Every mbarrier wait is bounded by the global timer; a wait that gives up
 // records an error code for the host and the block still frees its TMEM.
 #include "ur_conv_tc.cuh"
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(kConvThreads, 2)
     const uint32_t raw = s_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *sm = smem_raw + (base - raw);
-    const int kc = a.C / BK, nk = 3 * kc;   // stages per tile: kernel rows x channel chunks
+    const int kc = a.C / BK, nk = 3 * kc;   // weight blocks of the layer: kernel rows x channel chunks
     const bool wres = a.wres != 0;
     const int S = a.stages;
     const int R = a.rows;   // R > 1: row-stacked tile (resident stacked weights)
