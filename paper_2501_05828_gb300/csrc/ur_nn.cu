@@ -253,14 +253,25 @@ __global__ void __launch_bounds__(256) k_pool2_bwd_mask(bf16 *d, const bf16 *dp,
     flush_channel_sums(acc, G, db);
 }
 
-// W'[tap][ci][co] = W[8 - tap][co][ci]: weights of the data gradient.
-__global__ void k_wtrans(const bf16 *w, bf16 *wt, int Cout, int Cin) {
-    GRID_STRIDE(i, 9ll * Cout * Cin) {
-        const int co = (int)(i % Cout);
-        long long r = i / Cout;
+// Weights of the data gradients, every layer in one launch: for layer l (table entry j),
+// W'[tap][ci][co] = W[8 - tap][co][ci], both at the layer's offset of the packed vector.
+struct WtransTable {
+    int n;
+    long long start[15];   // prefix sums of 9 C_in C_out over the entries
+    long long off[14];
+    int cin[14], cout[14];
+};
+__global__ void k_wtrans_all(const bf16 *w, bf16 *wt, const WtransTable T) {
+    GRID_STRIDE(i, T.start[T.n]) {
+        int j = 0;
+        while (j + 1 < T.n && i >= T.start[j + 1]) ++j;
+        const long long li = i - T.start[j];
+        const int Cout = T.cout[j], Cin = T.cin[j];
+        const int co = (int)(li % Cout);
+        const long long r = li / Cout;
         const int ci = (int)(r % Cin);
         const int tap = (int)(r / Cin);
-        wt[i] = w[((size_t)(8 - tap) * Cout + co) * Cin + ci];
+        wt[T.off[j] + li] = w[T.off[j] + ((long long)(8 - tap) * Cout + co) * Cin + ci];
     }
 }
 
@@ -322,7 +333,7 @@ struct ur_nn {
     int cin[kNumConv], cout[kNumConv];
     size_t woff[kNumConv], boff[kNumConv], hw_off = 0, hb_off = 0, n_params = 0;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *pbf = nullptr, *wt = nullptr;   // bf16 copies; transposed weights scratch
+    bf16 *pbf = nullptr, *wt = nullptr;   // bf16 copies; the data gradients' (transposed) weights
     // activations and gradients
     bf16 *x = nullptr;
     float *xn = nullptr;
@@ -540,12 +551,9 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
                int c1 = 0) {
     const Layer La = layer_in(nn, la), Lb = layer_in(nn, lb);
     conv_wgrad(nn, nn->act[la].p, d_out, B, Lb.H, Lb.W, nn->cin[lb], nn->cout[lb], nn->grads + nn->woff[lb]);
-    ++nn->launches;
-    k_wtrans<<<grid_for(9ll * nn->cin[lb] * nn->cout[lb]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[lb], nn->wt,
-                                                                                  nn->cout[lb], nn->cin[lb]);
     // gradient at la's output, masked by la's ReLU in the epilogue, which also sums la's bias gradient
-    conv_fwd(nn, In{d_out, nullptr, 0}, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt, nullptr, nn->act[la].p,
-             scratch, false, 9, nn->grads + nn->boff[la]);
+    conv_fwd(nn, In{d_out, nullptr, 0}, B, Lb.H, Lb.W, nn->cout[lb], nn->cin[lb], nn->wt + nn->woff[lb], nullptr,
+             nn->act[la].p, scratch, false, 9, nn->grads + nn->boff[la]);
     if (la == 0) {   // first layer: single-tap gradient over the neighbourhood channels, then back to [9][C][32]
         ck(cudaMemsetAsync(nn->dwfirst, 0, sizeof(float) * 32 * nn->width, nn->stream), "memset");
         conv_wgrad(nn, nn->x, scratch, B, La.H, La.W, 32, nn->cout[0], nn->dwfirst, 1);
@@ -558,12 +566,8 @@ void block_bwd(ur_nn *nn, int B, int la, int lb, bf16 *d_out, bf16 *scratch, bf1
                    in.c1);
     }
     if (din) {
-        ++nn->launches;
-        k_wtrans<<<grid_for(9ll * nn->cin[la] * nn->cout[la]), 256, 0, nn->stream>>>(nn->pbf + nn->woff[la], nn->wt,
-                                                                                      nn->cout[la], nn->cin[la]);
-        conv_fwd(nn, In{scratch, nullptr, 0}, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt, nullptr, nullptr, din,
-                 false, 9, nullptr,
-                 dskip, c1);
+        conv_fwd(nn, In{scratch, nullptr, 0}, B, La.H, La.W, nn->cout[la], nn->cin[la], nn->wt + nn->woff[la], nullptr,
+                 nullptr, din, false, 9, nullptr, dskip, c1);
     }
     ck(cudaGetLastError(), "block backward");
 }
@@ -603,6 +607,20 @@ double train(ur_nn *nn, int B, const float *rf, const float *quad, const float *
     // forward with the loss, the head's gradients and the gradient at d1b's output (gA); every
     // block's incoming gradient below arrives masked by its ReLU with its bias gradient summed
     forward(nn, B, rf, quad, nullptr, nullptr, t_rf, t_quad);
+    {   // the data gradients' weights of layers 1..13 (layer 0 has no data gradient), one launch
+        WtransTable T{};
+        T.n = kNumConv - 1;
+        for (int j = 0; j < T.n; ++j) {
+            const int l = j + 1;
+            T.off[j] = (long long)nn->woff[l];
+            T.cin[j] = nn->cin[l];
+            T.cout[j] = nn->cout[l];
+            T.start[j + 1] = T.start[j] + 9ll * nn->cin[l] * nn->cout[l];
+        }
+        ++nn->launches;
+        k_wtrans_all<<<grid_for(T.start[T.n]), 256, 0, nn->stream>>>(nn->pbf, nn->wt, T);
+        ck(cudaGetLastError(), "weight transpose");
+    }
     const int C = nn->width;
     const int H = nn->H, W = nn->W;
     // decoder level 1: input concat(up(d2), e1)
@@ -708,9 +726,7 @@ ur_status ur_nn_create(ur_nn **out, int device, void *cuda_stream, int max_batch
         nn->m = (float *)nn->alloc(sizeof(float) * nn->n_params);
         nn->v = (float *)nn->alloc(sizeof(float) * nn->n_params);
         nn->pbf = (bf16 *)nn->alloc(sizeof(bf16) * nn->n_params);
-        size_t wt_max = 0;
-        for (int l = 0; l < kNumConv; ++l) wt_max = std::max<size_t>(wt_max, (size_t)9 * ci[l] * co[l]);
-        nn->wt = (bf16 *)nn->alloc(sizeof(bf16) * wt_max);
+        nn->wt = (bf16 *)nn->alloc(sizeof(bf16) * nn->n_params);   // data-gradient weights at the same offsets
         ck(cudaMemcpy(nn->params, h.data(), sizeof(float) * nn->n_params, cudaMemcpyHostToDevice), "copy params");
         ck(cudaMemset(nn->m, 0, sizeof(float) * nn->n_params), "memset");
         ck(cudaMemset(nn->v, 0, sizeof(float) * nn->n_params), "memset");
