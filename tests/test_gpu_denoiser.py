@@ -180,6 +180,49 @@ def test_forward_matches_oracle_across_tiles():
     dn.close()
 
 
+def test_forward_full_size_sampled_columns():
+    """The forward pass at the benchmarked frame size [128 x 3200] (batch 1, the launch
+    configuration of the benchmark's convolutions) against the oracle on crops.  An output pixel
+    depends only on the inputs in its receptive field: on the oracle itself, a crop's outputs
+    equal the full frame's from 46 columns inside each crop edge that is not an image edge (four
+    levels of two 3x3 convolutions with 2x pooling and nearest upsampling).  So a crop of 384
+    columns aligned to the pooling grid (a multiple of 8) gives the full frame's exact outputs on
+    all but 96 columns at each inner edge.  Three crops: the left image edge, the middle, the
+    right image edge."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05828_gb300 as ur
+    h, w, cw, margin = 128, 3200, 384, 96
+    dn = ur.Denoiser(0, max_batch=1, n_el=h, n_s=w, width=32, seed=13)
+    lay = ur.nn_layout(32)
+    rng = np.random.default_rng(14)
+    p = dn.params()
+    for name, (wo, ws, bo, co) in lay.items():
+        p[bo:bo + co] = rng.standard_normal(co).astype(np.float32) * 0.05
+    wo, ws, bo, co = lay["head"]
+    p[wo:wo + 64] = rng.standard_normal(64).astype(np.float32) * 0.3
+    dn.set_params(p)
+    x = rng.standard_normal((1, h, w, 2)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    orf, oq = dn.forward(dev(x[..., 0]), dev(x[..., 1]))
+    torch.cuda.synchronize()
+    gpu = np.stack([orf.cpu().numpy(), oq.cpu().numpy()], -1)
+    P = to_oracle(dn.params(), lay)
+    for x0 in (0, 1408, w - cw):
+        assert x0 % 8 == 0
+        y, _ = D.forward(P, x[:, :, x0:x0 + cw].astype(np.float64), q=D.bf16)
+        lo = 0 if x0 == 0 else margin
+        hi = cw if x0 + cw == w else cw - margin
+        g, o = gpu[:, :, x0 + lo:x0 + hi], y[:, :, lo:hi]
+        xb = D.bf16(x[:, :, x0 + lo:x0 + hi].astype(np.float64))
+        e_all, e_res = rel_l2(g, o), rel_l2(g - xb, o - xb)
+        print(f"full size, columns {x0 + lo}..{x0 + hi - 1}: output {e_all:.2e}, learned part {e_res:.2e}")
+        assert e_all <= 5e-3
+        assert e_res <= 2e-2
+    dn.close()
+
+
 @pytest.mark.parametrize("w", [320, 256, 1088])
 def test_gradient_matches_oracle_across_tiles(w):
     """Parameter gradients on an 8 x w frame: several K steps per image row, so the x-shifted
