@@ -92,3 +92,24 @@ def test_adam_step_by_hand():
     D.adam_step(p, g, st, lr=0.01)
     # first step: m_hat = g, v_hat = g^2 -> update lr * sign(g) (up to eps)
     assert np.allclose(p["w"], [1.0 - 0.01, -2.0 - 0.01], atol=1e-9)
+
+
+def test_receptive_field_of_the_unet():
+    """An output column depends only on the inputs within 46 columns of it, for a crop aligned to
+    the pooling grid: the oracle on a crop reproduces the full frame's outputs exactly from the
+    46th column inside each inner crop edge on, and not nearer (the full-size GPU parity test
+    compares crops with a 96-column margin on the strength of this)."""
+    rng = np.random.default_rng(1)
+    P = D.init_params(rng)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = rng.standard_normal(P[k].shape) * 0.05
+    P["head.w"] = rng.standard_normal(P["head.w"].shape) * 0.3
+    x = rng.standard_normal((1, 32, 512, 2))
+    y, _ = D.forward(P, x, q=D.bf16)
+    x0, cw = 128, 256
+    yc, _ = D.forward(P, x[:, :, x0:x0 + cw], q=D.bf16)
+    same = np.all(yc == y[:, :, x0:x0 + cw], axis=(0, 1, 3))
+    exact = np.nonzero(same)[0]
+    assert exact[0] == 46 and exact[-1] == cw - 1 - 46
+    assert same[46:cw - 46].all()
